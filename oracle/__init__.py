@@ -1,0 +1,332 @@
+"""FP64 CPU oracle for the graph-construction path (test infrastructure only).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The CUDA library never calls it and
+shares no code with it.  The arithmetic lives in ``oracle.c``; this module
+compiles it (gcc, ``-ffp-contract=off``), marshals numpy arrays and composes
+the hierarchical build of Algorithm 7 from the C pieces.
+
+Every function names the passage of arXiv 2410.01231 it restates.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+METRICS = {"l2": 0, "cosine": 1, "ip": 2}
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so next to it (gcc, OpenMP)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
+               "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _get():
+    global _lib
+    if _lib is None:
+        build()
+        lib = C.CDLL(_LIB)
+        P = C.c_void_p
+        i64, i32, dbl = C.c_int64, C.c_int, C.c_double
+        lib.or_dist.restype = dbl
+        lib.or_dist.argtypes = [P, P, i32, i32]
+        lib.or_knn.restype = i32
+        lib.or_knn.argtypes = [P, i64, i32, i32, P, i64, P, i32, P, P]
+        lib.or_prune.restype = i32
+        lib.or_prune.argtypes = [P, i64, i32, i32, P, P, i32, dbl, i32, P, P]
+        lib.or_reverse_union.restype = i64
+        lib.or_reverse_union.argtypes = [P, P, i64, i32, P, P]
+        lib.or_medoid.restype = i64
+        lib.or_medoid.argtypes = [P, i64, i32, i32, P]
+        lib.or_connect.restype = i64
+        lib.or_connect.argtypes = [P, i64, i32, i32, P, P, i32, i64]
+        lib.or_search.restype = i32
+        lib.or_search.argtypes = [P, i64, i32, i32, P, P, i32, P, P, i64, P, i32, i32, i32,
+                                  i32, P, P, P]
+        lib.or_acquire.restype = i32
+        lib.or_acquire.argtypes = [P, i64, i32, i32, P, P, i32, i32, P, P]
+        lib.or_build_rng.restype = i64
+        lib.or_build_rng.argtypes = [P, i64, i32, i32, i32, i32, i32, dbl, i32, dbl, i32, i32,
+                                     i32, P, P]
+        lib.or_levels.restype = None
+        lib.or_levels.argtypes = [i64, C.c_uint64, i32, P]
+        lib.or_splitmix64.restype = C.c_uint64
+        lib.or_splitmix64.argtypes = [C.c_uint64]
+        lib.or_num_threads.restype = i32
+        lib.or_set_threads.argtypes = [i32]
+        _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray | None):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _f32(D):
+    return np.ascontiguousarray(D, dtype=np.float32)
+
+
+def num_threads() -> int:
+    return _get().or_num_threads()
+
+
+def set_threads(t: int) -> None:
+    _get().or_set_threads(int(t))
+
+
+def cos_alpha(alpha_deg: float) -> float:
+    """cos(alpha) for the angle clause of alpha-pruning (Section 4.1)."""
+    return math.cos(alpha_deg * math.pi / 180.0)
+
+
+# --------------------------------------------------------------------------
+def dist(x: np.ndarray, y: np.ndarray, metric: str = "l2") -> float:
+    """s(x, y) in FP64 (Section 2; squared chord for unit-norm metrics)."""
+    x, y = _f32(x), _f32(y)
+    return _get().or_dist(_p(x), _p(y), x.shape[0], METRICS[metric])
+
+
+def knn(D, K: int, metric: str = "l2", Q=None):
+    """Exact K nearest neighbours by (s, id); self excluded when Q is None."""
+    D = _f32(D)
+    n, d = D.shape
+    if Q is None:
+        Qa, excl = D, np.arange(n, dtype=np.int64)
+    else:
+        Qa, excl = _f32(Q), None
+    nq = Qa.shape[0]
+    ids = np.empty((nq, K), np.int32)
+    ds = np.empty((nq, K), np.float64)
+    rc = _get().or_knn(_p(D), n, d, METRICS[metric], _p(Qa), nq, _p(excl), K, _p(ids), _p(ds))
+    assert rc == 0
+    return ids, ds
+
+
+def prune(D, off, cand, R: int, alpha_deg: float, metric: str = "l2"):
+    """alpha-pruning of every CSR row (Section 4.1 rule, Algorithm 3 scan)."""
+    D = _f32(D)
+    n, d = D.shape
+    off = np.ascontiguousarray(off, np.int64)
+    cand = np.ascontiguousarray(cand, np.int32)
+    nbr = np.empty((n, R), np.int32)
+    deg = np.empty(n, np.int32)
+    rc = _get().or_prune(_p(D), n, d, METRICS[metric], _p(off), _p(cand), R,
+                         cos_alpha(alpha_deg), int(alpha_deg == 60.0), _p(nbr), _p(deg))
+    assert rc == 0
+    return nbr, deg
+
+
+def reverse_union(nbr, deg):
+    """Row u = N(u) then {v : u in N(v)} (Algorithm 2 lines 7-8)."""
+    nbr = np.ascontiguousarray(nbr, np.int32)
+    deg = np.ascontiguousarray(deg, np.int32)
+    n, R = nbr.shape
+    off = np.empty(n + 1, np.int64)
+    tot = _get().or_reverse_union(_p(nbr), _p(deg), n, R, _p(off), None)
+    ids = np.empty(max(tot, 1), np.int32)
+    _get().or_reverse_union(_p(nbr), _p(deg), n, R, _p(off), _p(ids))
+    return off, ids[:tot]
+
+
+def medoid(D, metric: str = "l2") -> int:
+    """Point nearest the centroid (Section 3.1, search phase)."""
+    D = _f32(D)
+    return int(_get().or_medoid(_p(D), D.shape[0], D.shape[1], METRICS[metric], None))
+
+
+def connect(D, nbr, deg, ep: int, metric: str = "l2"):
+    """Link unreachable components (Algorithm 2 lines 10-11); returns copies."""
+    D = _f32(D)
+    nbr = np.array(nbr, np.int32, copy=True)
+    deg = np.array(deg, np.int32, copy=True)
+    n, R = nbr.shape
+    added = _get().or_connect(_p(D), n, D.shape[1], METRICS[metric], _p(nbr), _p(deg), R, ep)
+    return nbr, deg, int(added)
+
+
+def search(D, nbr, deg, Q, starts, k: int, L: int, metric: str = "l2", rows=None,
+           policy: int = 0, return_expanded: bool = False):
+    """KANNSearch (Algorithm 1) for every query row.
+
+    ``starts`` is an int, a 1-D array (one entry point per query) or a 2-D
+    array (several per query).
+    """
+    D = _f32(D)
+    Q = _f32(Q)
+    nbr = np.ascontiguousarray(nbr, np.int32)
+    deg = np.ascontiguousarray(deg, np.int32)
+    n, d = D.shape
+    nq = Q.shape[0]
+    st = np.asarray(starts, dtype=np.int32)
+    if st.ndim == 0:
+        st = np.full((nq, 1), int(st), np.int32)
+    elif st.ndim == 1:
+        st = st.reshape(nq, 1)
+    st = np.ascontiguousarray(st)
+    rows_a = None if rows is None else np.ascontiguousarray(rows, np.int32)
+    ids = np.empty((nq, k), np.int32)
+    ds = np.empty((nq, k), np.float64)
+    ne = np.zeros(1, np.int64)
+    rc = _get().or_search(_p(D), n, d, METRICS[metric], _p(nbr), _p(deg), nbr.shape[1],
+                          _p(rows_a), _p(Q), nq, _p(st), st.shape[1], k, L, policy, _p(ids),
+                          _p(ds), _p(ne))
+    assert rc == 0
+    if return_expanded:
+        return ids, ds, int(ne[0])
+    return ids, ds
+
+
+def acquire(D, nbr, deg, L: int, metric: str = "l2"):
+    """C(u) <- KANNSearch(G, u, L, L, u) minus u (Algorithm 5 lines 7-8)."""
+    D = _f32(D)
+    nbr = np.ascontiguousarray(nbr, np.int32)
+    deg = np.ascontiguousarray(deg, np.int32)
+    n, d = D.shape
+    cand = np.empty((n, L), np.int32)
+    rc = _get().or_acquire(_p(D), n, d, METRICS[metric], _p(nbr), _p(deg), nbr.shape[1], L,
+                           _p(cand), None)
+    assert rc == 0
+    return cand
+
+
+def build_rng(D, K: int, L: int, R: int, alpha_deg: float = 66.0, alpha_final_deg: float = 60.0,
+              iters: int = 2, metric: str = "l2", connect_final: bool = True):
+    """IterNSG with fixed I (Algorithm 6 + Algorithm 5); returns (nbr, deg, ep)."""
+    D = _f32(D)
+    n, d = D.shape
+    nbr = np.empty((n, R), np.int32)
+    deg = np.empty(n, np.int32)
+    ep = _get().or_build_rng(_p(D), n, d, METRICS[metric], K, L, R, cos_alpha(alpha_deg),
+                             int(alpha_deg == 60.0), cos_alpha(alpha_final_deg),
+                             int(alpha_final_deg == 60.0), iters, int(connect_final),
+                             _p(nbr), _p(deg))
+    if ep < 0:
+        raise RuntimeError(f"oracle build_rng failed ({ep})")
+    return nbr, deg, int(ep)
+
+
+def splitmix64(x: int) -> int:
+    """One SplitMix64 output for state x (the generator behind the levels)."""
+    return int(_get().or_splitmix64(x))
+
+
+def levels(n: int, seed: int, M: int) -> np.ndarray:
+    """HNSW levels floor(-ln U / ln M), U from SplitMix64 (Algorithm 7 line 2)."""
+    out = np.empty(n, np.int32)
+    _get().or_levels(n, seed, M, _p(out))
+    return out
+
+
+# --------------------------------------------------------------------------
+# Hierarchical (NSWG) build, Algorithm 7, and its layered query.
+# --------------------------------------------------------------------------
+class Layer:
+    __slots__ = ("gid", "nbr", "deg", "R")
+
+    def __init__(self, gid, nbr, deg, R):
+        self.gid, self.nbr, self.deg, self.R = gid, nbr, deg, R
+
+
+def build_nswg(D, K: int, L: int, M: int, R0: int, alpha_deg: float = 66.0,
+               alpha_final_deg: float = 60.0, iters: int = 2, metric: str = "cosine",
+               seed: int = 0, lev=None):
+    """OptHNSW (Algorithm 7).
+
+    Levels are drawn for every point up front; layer i holds
+    D_i = {u : l(u) >= i} (ascending ids).  A layer with |D_i| <= M_i is a
+    complete graph (every other member, by (s, id)); any other layer is the
+    IterNSG build of D_i with pool width ef = L, whose final refinement
+    skips the connectivity step (Section 5.3).  M_0 = R0 and M_i = M for
+    i >= 1.  ep is the smallest id on the top layer (reading of "randomly
+    select ep"; deterministic).  Layer adjacency holds global ids.
+    """
+    D = _f32(D)
+    n = D.shape[0]
+    lev = levels(n, seed, M) if lev is None else np.asarray(lev, np.int32)
+    top = int(lev.max())
+    layers = []
+    for i in range(top + 1):
+        gid = np.nonzero(lev >= i)[0].astype(np.int32)
+        Ri = R0 if i == 0 else M
+        m = gid.shape[0]
+        Di = D[gid]
+        if m <= Ri:
+            nbr = np.full((m, Ri), -1, np.int32)
+            deg = np.zeros(m, np.int32)
+            for a in range(m):
+                others = [(dist(Di[a], Di[b], metric), int(gid[b])) for b in range(m) if b != a]
+                others.sort()
+                for j, (_, g) in enumerate(others):
+                    nbr[a, j] = g
+                deg[a] = len(others)
+        else:
+            lnbr, deg, _ = build_rng(Di, K, L, Ri, alpha_deg, alpha_final_deg, iters, metric,
+                                     connect_final=False)
+            nbr = np.where(lnbr >= 0, gid[np.maximum(lnbr, 0)], -1).astype(np.int32)
+        layers.append(Layer(gid, nbr, deg, Ri))
+    ep = int(layers[top].gid[0])
+    return layers, ep, lev
+
+
+def search_nswg(D, layers, ep: int, Q, k: int, ef: int, metric: str = "cosine"):
+    """Layered query: greedy KANNSearch(G_i, q, 1, 1, w) from the top layer
+    down to layer 1, then KANNSearch(G_0, q, k, ef, w) (pattern of
+    Algorithm 4 lines 8-12)."""
+    D = _f32(D)
+    Q = _f32(Q)
+    n = D.shape[0]
+    nq = Q.shape[0]
+    w = np.full(nq, ep, np.int32)
+    for i in range(len(layers) - 1, 0, -1):
+        lay = layers[i]
+        rows = np.full(n, -1, np.int32)
+        rows[lay.gid] = np.arange(lay.gid.shape[0], dtype=np.int32)
+        ids, _ = search(D, lay.nbr, lay.deg, Q, w, 1, 1, metric, rows=rows)
+        w = ids[:, 0].copy()
+    base = layers[0]
+    return search(D, base.nbr, base.deg, Q, w, k, ef, metric)
+
+
+# --------------------------------------------------------------------------
+def recall_at_k(found_ids, Q, D, k: int, metric: str = "l2", gt=None):
+    """Recall@k = |N*(q) cap N(q)| / k (Section 6, performance indicators).
+
+    Reading for ties: a returned id counts when its FP64 distance is at most
+    the exact k-th distance; repeated or negative ids count once / never;
+    the count is capped at k.  Returns the mean over queries.
+    """
+    D = _f32(D)
+    Q = _f32(Q)
+    if gt is None:
+        gt = knn(D, k, metric, Q=Q)
+    gt_ids, gt_d = gt
+    kth = gt_d[:, k - 1]
+    total = 0.0
+    for qi in range(Q.shape[0]):
+        seen = set()
+        hit = 0
+        for v in found_ids[qi, :k]:
+            v = int(v)
+            if v < 0 or v in seen:
+                continue
+            seen.add(v)
+            if dist(Q[qi], D[v], metric) <= kth[qi]:
+                hit += 1
+        total += min(hit, k) / k
+    return total / Q.shape[0]

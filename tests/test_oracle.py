@@ -1,0 +1,451 @@
+"""Pins for the FP64 oracle: each test checks it against something other than
+itself (exact integer arithmetic, an independent geometric computation, a
+literal reading of a printed algorithm, published constants, closed forms).
+CPU only."""
+from __future__ import annotations
+
+import math
+import os
+from decimal import Decimal, getcontext
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+import synthetic
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def int_data(n, d, seed, hi=16):
+    rng = np.random.default_rng(seed)
+    return rng.integers(0, hi, size=(n, d)).astype(np.float32)
+
+
+def exact_s(x, y):
+    """Squared L2 in exact integer arithmetic (integer-valued rows)."""
+    return sum((int(a) - int(b)) ** 2 for a, b in zip(x, y))
+
+
+# --------------------------------------------------------------------------
+# distances
+# --------------------------------------------------------------------------
+def test_dist_l2_exact_on_integers():
+    D = int_data(20, 37, 1, hi=256)
+    for i in range(0, 20, 3):
+        for j in range(20):
+            assert oracle.dist(D[i], D[j]) == exact_s(D[i], D[j])
+
+
+def test_dist_cosine_is_squared_chord():
+    rng = np.random.default_rng(2)
+    X = rng.normal(size=(30, 24))
+    X /= np.linalg.norm(X, axis=1, keepdims=True)
+    X = X.astype(np.float32)
+    for i in range(10):
+        for j in range(30):
+            c = oracle.dist(X[i], X[j], "cosine")
+            e = float(np.sum((X[i].astype(np.float64) - X[j].astype(np.float64)) ** 2))
+            assert abs(c - e) < 1e-6
+        # 2 - 2|x|^2: float32 rows are unit only to rounding
+        assert 0.0 <= oracle.dist(X[i], X[i], "cosine") < 1e-6
+
+
+# --------------------------------------------------------------------------
+# exact kNN: brute force in exact integer arithmetic, ties by id
+# --------------------------------------------------------------------------
+def test_knn_matches_exact_integer_bruteforce():
+    D = int_data(150, 9, 3, hi=6)  # small range: many exact ties
+    K = 12
+    ids, ds = oracle.knn(D, K)
+    for u in range(D.shape[0]):
+        pairs = sorted((exact_s(D[u], D[v]), v) for v in range(D.shape[0]) if v != u)[:K]
+        assert [v for _, v in pairs] == ids[u].tolist()
+        assert [float(s) for s, _ in pairs] == ds[u].tolist()
+
+
+def test_knn_external_queries_and_padding():
+    D = int_data(7, 4, 4)
+    Q = int_data(3, 4, 5)
+    ids, ds = oracle.knn(D, 10, Q=Q)
+    assert (ids[:, 7:] == -1).all() and np.isinf(ds[:, 7:]).all()
+    for q in range(3):
+        pairs = sorted((exact_s(Q[q], D[v]), v) for v in range(7))
+        assert [v for _, v in pairs] == ids[q, :7].tolist()
+
+
+# --------------------------------------------------------------------------
+# alpha-pruning
+# --------------------------------------------------------------------------
+def _read_golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+def test_prune_hand_worked_triangle():
+    D = np.array([[0.0, 0.0], [1.0, 0.0], [1.2, 1.0]], np.float32)
+    off = np.array([0, 2, 2, 2], np.int64)
+    cand = np.array([2, 1], np.int32)
+    for alpha, kept in _read_golden("prune_triangle_2d.txt"):
+        nbr, deg = oracle.prune(D, off, cand, 4, float(alpha))
+        want = [int(x) for x in kept.split(",")]
+        assert nbr[0, : deg[0]].tolist() == want, alpha
+
+
+def _angle_deg(u, w, v):
+    a = np.asarray(u, np.float64) - np.asarray(w, np.float64)
+    b = np.asarray(v, np.float64) - np.asarray(w, np.float64)
+    return math.degrees(abs(math.atan2(a[0] * b[1] - a[1] * b[0], a[0] * b[0] + a[1] * b[1])))
+
+
+def test_prune_angle_clause_against_atan2_geometry():
+    """For random planar triangles where both distance clauses hold, v is
+    pruned exactly when the angle at w (measured with atan2) exceeds alpha."""
+    rng = np.random.default_rng(6)
+    checked = 0
+    for _ in range(3000):
+        P = rng.uniform(-10, 10, size=(3, 2)).astype(np.float32)
+        u, w, v = P
+        suw, suv, svw = (oracle.dist(u, w), oracle.dist(u, v), oracle.dist(v, w))
+        if not (suw < suv and svw < suv):
+            continue
+        ang = _angle_deg(u, w, v)
+        alpha = float(rng.uniform(55, 125))
+        if abs(ang - alpha) < 1e-6:
+            continue
+        off = np.array([0, 2, 2, 2], np.int64)
+        nbr, deg = oracle.prune(P, off, np.array([2, 1], np.int32), 4, alpha)
+        assert nbr[0, : deg[0]].tolist() == ([1] if ang > alpha else [1, 2])
+        checked += 1
+    assert checked > 500
+
+
+def _literal_alg3(D, u, cand, M):
+    """Algorithm 3 as printed: ascending dist(u,v); v dominated iff some
+    selected w has dist(v,w) < dist(u,v); stop at M selected."""
+    xs = D.astype(np.float64)
+    order = sorted(set(c for c in cand if c != u),
+                   key=lambda v: (np.linalg.norm(xs[u] - xs[v]), v))
+    kept = []
+    for v in order:
+        dom = any(np.linalg.norm(xs[v] - xs[w]) < np.linalg.norm(xs[u] - xs[v]) for w in kept)
+        if not dom:
+            kept.append(v)
+        if len(kept) >= M:
+            break
+    return kept
+
+
+def test_prune_alpha60_equals_rng_algorithm3():
+    """alpha = 60 degrees is RNG pruning (Section 4.2) on tie-free data."""
+    rng = np.random.default_rng(7)
+    D = rng.normal(size=(120, 6)).astype(np.float32)
+    ids, _ = oracle.knn(D, 40)
+    off = np.arange(121, dtype=np.int64) * 40
+    for M in (5, 12, 40):
+        nbr, deg = oracle.prune(D, off, ids.ravel(), M, 60.0)
+        for u in range(120):
+            assert nbr[u, : deg[u]].tolist() == _literal_alg3(D, u, ids[u].tolist(), M)
+
+
+def test_prune_alpha180_keeps_first_R():
+    """No triangle has an angle above 180 degrees, so alpha = 180 prunes
+    nothing: the first min(R, |C|) distinct candidates by (s, id) stay."""
+    rng = np.random.default_rng(8)
+    D = rng.normal(size=(80, 5)).astype(np.float32)
+    cand = rng.integers(-1, 80, size=(80, 30)).astype(np.int32)
+    off = np.arange(81, dtype=np.int64) * 30
+    nbr, deg = oracle.prune(D, off, cand.ravel(), 10, 180.0)
+    for u in range(80):
+        ok = sorted({(oracle.dist(D[u], D[v]), v) for v in cand[u] if v >= 0 and v != u})
+        assert nbr[u, : deg[u]].tolist() == [v for _, v in ok[:10]]
+
+
+def _exact_occludes(D, u, w, v, cos_a):
+    """Occlusion decided in exact/high-precision arithmetic (integer rows)."""
+    suw, suv, svw = exact_s(D[u], D[w]), exact_s(D[u], D[v]), exact_s(D[v], D[w])
+    if not (suw < suv and svw < suv):
+        return False, 0
+    getcontext().prec = 60
+    lhs = Decimal(suw + svw - suv)
+    rhs = 2 * Decimal(cos_a) * (Decimal(suw) * Decimal(svw)).sqrt()
+    # lhs is an exact integer; when it is 0 only the sign of rhs decides,
+    # which FP64 reproduces exactly, so such decisions are never tight
+    margin = Decimal(1) if lhs == 0 else abs(lhs - rhs) / Decimal(suw + svw + suv)
+    return lhs < rhs, margin
+
+
+@pytest.mark.parametrize("alpha", [60.0, 66.0, 75.0, 90.0])
+def test_prune_output_is_the_defined_set(alpha):
+    """Independent check of the definition on integer data with many ties:
+    kept rows follow (s, id) order; no kept v is occluded by an earlier kept
+    w; every skipped candidate before the stop is occluded by a kept w."""
+    D = int_data(200, 8, 9, hi=5)
+    rng = np.random.default_rng(10)
+    cand = rng.integers(0, 200, size=(200, 60)).astype(np.int32)
+    off = np.arange(201, dtype=np.int64) * 60
+    R = 9
+    cos_a = oracle.cos_alpha(alpha)
+    nbr, deg = oracle.prune(D, off, cand.ravel(), R, alpha)
+    ambiguous = 0
+    for u in range(200):
+        order = sorted({(exact_s(D[u], D[v]), v) for v in cand[u] if v != u})
+        kept = nbr[u, : deg[u]].tolist()
+        assert deg[u] <= R
+        kept_list = []
+        for s, v in order:
+            if len(kept_list) == R:
+                break
+            occ, tight = False, False
+            for w in kept_list:
+                o, margin = _exact_occludes(D, u, w, v, cos_a)
+                if margin != 0 and margin < 1e-12:
+                    tight = True  # FP64 may round either way here
+                occ = occ or o
+            if tight:
+                ambiguous += 1
+                if v in kept:
+                    kept_list.append(v)
+                continue
+            if occ:
+                assert v not in kept
+            else:
+                assert v in kept
+                kept_list.append(v)
+        assert kept_list == kept
+    assert ambiguous < 20
+
+
+def test_prune_drops_self_negative_and_repeats():
+    D = int_data(10, 3, 11)
+    off = np.array([0, 8] + [8] * 9, np.int64)
+    cand = np.array([0, -1, 3, 3, 5, -1, 0, 5], np.int32)
+    nbr, deg = oracle.prune(D, off, cand, 8, 180.0)
+    assert sorted(nbr[0, : deg[0]].tolist()) == [3, 5]
+    assert (deg[1:] == 0).all()
+
+
+def test_lemma1_probability_planar_monte_carlo():
+    """Lemma 1: for a pruning triangle with angle alpha at w, a uniformly
+    random query ranks w behind both u and v with probability
+    (pi - alpha) / (2 pi).  Planar check with the oracle's distance."""
+    rng = np.random.default_rng(12)
+    for alpha in (60.0, 90.0, 120.0):
+        a = math.radians(alpha)
+        w = np.array([0.0, 0.0])
+        u = np.array([1.0, 0.0])
+        v = np.array([math.cos(a), math.sin(a)])
+        nq = 20000
+        Qs = rng.uniform(-400, 400, size=(nq, 2)).astype(np.float32)
+        U, V, W = (p.astype(np.float32) for p in (u, v, w))
+        hits = 0
+        for q in Qs:
+            dw = oracle.dist(q, W)
+            if dw > oracle.dist(q, U) and dw > oracle.dist(q, V):
+                hits += 1
+        p = (math.pi - a) / (2 * math.pi)
+        sigma = math.sqrt(p * (1 - p) / nq)
+        assert abs(hits / nq - p) < 4 * sigma + 2e-3, alpha
+
+
+# --------------------------------------------------------------------------
+# reverse-edge union
+# --------------------------------------------------------------------------
+def test_reverse_union_is_out_plus_in_edges():
+    rng = np.random.default_rng(13)
+    n, R = 50, 6
+    nbr = np.full((n, R), -1, np.int32)
+    deg = rng.integers(0, R + 1, size=n).astype(np.int32)
+    for u in range(n):
+        nbr[u, : deg[u]] = rng.choice([x for x in range(n) if x != u], deg[u], replace=False)
+    off, ids = oracle.reverse_union(nbr, deg)
+    inn = {u: [] for u in range(n)}
+    for v in range(n):
+        for w in nbr[v, : deg[v]]:
+            inn[int(w)].append(v)
+    for u in range(n):
+        row = ids[off[u]: off[u + 1]].tolist()
+        assert sorted(row) == sorted(nbr[u, : deg[u]].tolist() + inn[u])
+
+
+# --------------------------------------------------------------------------
+# medoid and connectivity
+# --------------------------------------------------------------------------
+def test_medoid_is_point_nearest_exact_centroid():
+    D = int_data(3000, 5, 14, hi=100)
+    c = [Fraction(int(s), 3000) for s in D.astype(np.int64).sum(axis=0)]
+    best = min(range(3000), key=lambda v: (sum((Fraction(int(x)) - ci) ** 2
+                                               for x, ci in zip(D[v], c)), v))
+    assert oracle.medoid(D) == best
+
+
+def _reach(nbr, deg, src):
+    seen = {src}
+    st = [src]
+    while st:
+        x = st.pop()
+        for y in nbr[x, : deg[x]]:
+            if int(y) not in seen:
+                seen.add(int(y))
+                st.append(int(y))
+    return seen
+
+
+def test_connect_links_from_nearest_reached_node():
+    rng = np.random.default_rng(15)
+    A = rng.normal(0, 1, size=(20, 3))
+    B = rng.normal(50, 1, size=(15, 3))
+    D = np.vstack([B, A]).astype(np.float32)  # B holds ids 0..14
+    n, R = 35, 4
+    nbr = np.full((n, R), -1, np.int32)
+    deg = np.zeros(n, np.int32)
+    for u in range(n):  # a directed ring inside each group
+        grp = range(0, 15) if u < 15 else range(15, 35)
+        lo, hi = grp.start, grp.stop
+        nbr[u, 0] = lo + (u - lo + 1) % (hi - lo)
+        deg[u] = 1
+    deg[16] = R
+    nbr[16] = [17, 18, 19, 20]
+    ep = 20
+    out_nbr, out_deg, added = oracle.connect(D, nbr, deg, ep)
+    assert added == 1
+    assert _reach(out_nbr, out_deg, ep) == set(range(n))
+    xs = D.astype(np.float64)
+    cands = [x for x in range(15, 35) if deg[x] < R]
+    p = min(cands, key=lambda x: (float(np.sum((xs[x] - xs[0]) ** 2)), x))
+    assert out_deg[p] == deg[p] + 1 and out_nbr[p, deg[p]] == 0
+
+
+def test_connect_reaches_everything_on_a_real_build():
+    D, _, _ = synthetic.workload(1, n=1500, nq=1)
+    ids, _ = oracle.knn(D, 10)
+    off = np.arange(1501, dtype=np.int64) * 10
+    nbr, deg = oracle.prune(D, off, ids.ravel(), 16, 60.0)
+    ep = oracle.medoid(D)
+    out_nbr, out_deg, added = oracle.connect(D, nbr, deg, ep)
+    assert added > 0
+    assert _reach(out_nbr, out_deg, ep) == set(range(1500))
+    assert (out_deg <= 16).all()
+
+
+# --------------------------------------------------------------------------
+# beam search
+# --------------------------------------------------------------------------
+def test_search_on_complete_graph_is_exact_knn():
+    D = int_data(40, 4, 16, hi=9)
+    Q = int_data(6, 4, 17, hi=9)
+    n = 40
+    nbr = np.array([[v for v in range(n) if v != u] for u in range(n)], np.int32)
+    deg = np.full(n, n - 1, np.int32)
+    ids, ds = oracle.search(D, nbr, deg, Q, 3, 7, n)
+    for q in range(6):
+        pairs = sorted((exact_s(Q[q], D[v]), v) for v in range(n))[:7]
+        assert ids[q].tolist() == [v for _, v in pairs]
+
+
+def test_search_on_path_graph_walks_to_the_target():
+    n = 60
+    D = np.arange(n, dtype=np.float32).reshape(n, 1)
+    nbr = np.full((n, 2), -1, np.int32)
+    deg = np.zeros(n, np.int32)
+    for u in range(n):
+        row = [x for x in (u - 1, u + 1) if 0 <= x < n]
+        nbr[u, : len(row)] = row
+        deg[u] = len(row)
+    Q = np.array([[41.2], [3.9], [58.6]], np.float32)
+    ids, ds, ne = oracle.search(D, nbr, deg, Q, 0, 2, 2, return_expanded=True)
+    assert ids.tolist() == [[41, 42], [4, 3], [59, 58]]
+
+
+def test_search_visited_policy_does_not_change_the_pool():
+    D, Q, _ = synthetic.workload(1, n=1200, nq=40)
+    ids, _ = oracle.knn(D, 8)
+    off = np.arange(1201, dtype=np.int64) * 8
+    nbr, deg = oracle.prune(D, off, ids.ravel(), 8, 70.0)
+    starts = np.random.default_rng(18).integers(0, 1200, size=40)
+    for L in (4, 17, 50):
+        a = oracle.search(D, nbr, deg, Q, starts, L, L, policy=0)
+        b = oracle.search(D, nbr, deg, Q, starts, L, L, policy=1)
+        assert (a[0] == b[0]).all() and (a[1] == b[1]).all()
+
+
+def test_acquire_on_complete_graph_is_exact_knn_minus_self():
+    D = int_data(30, 3, 19, hi=7)
+    n = 30
+    nbr = np.array([[v for v in range(n) if v != u] for u in range(n)], np.int32)
+    deg = np.full(n, n - 1, np.int32)
+    cand = oracle.acquire(D, nbr, deg, 12)
+    ids, _ = oracle.knn(D, 11)
+    assert (cand[:, :11] == ids).all() and (cand[:, 11] == -1).all()
+
+
+# --------------------------------------------------------------------------
+# IterNSG composition and the hierarchical build
+# --------------------------------------------------------------------------
+def test_build_rng_equals_composed_steps():
+    D, _, _ = synthetic.workload(1, n=800, nq=1)
+    K, L, R = 10, 24, 12
+    nbr, deg, ep = oracle.build_rng(D, K, L, R, 66.0, 60.0, iters=1)
+    ids, _ = oracle.knn(D, K)
+    assert ep == oracle.medoid(D)
+
+    def refine(off, cand, alpha, do_connect):
+        n1, d1 = oracle.prune(D, off, cand, R, alpha)
+        uo, ui = oracle.reverse_union(n1, d1)
+        n2, d2 = oracle.prune(D, uo, ui, R, alpha)
+        if do_connect:
+            n2, d2, _ = oracle.connect(D, n2, d2, ep)
+        return n2, d2
+
+    g, gd = refine(np.arange(801, dtype=np.int64) * K, ids.ravel(), 66.0, True)
+    cand = oracle.acquire(D, g, gd, L)
+    g2, gd2 = refine(np.arange(801, dtype=np.int64) * L, cand.ravel(), 60.0, True)
+    assert (g2 == nbr).all() and (gd2 == deg).all()
+    assert _reach(nbr, deg, ep) == set(range(800))
+
+
+def test_splitmix64_published_outputs():
+    for state, out in _read_golden("splitmix64_seed0.txt"):
+        assert oracle.splitmix64(int(state, 16)) == int(out, 16)
+
+
+def test_levels_follow_the_geometric_law():
+    n, M = 200_000, 16
+    lev = oracle.levels(n, 99, M)
+    for i in (1, 2, 3):
+        p = M ** (-i)
+        frac = float((lev >= i).mean())
+        assert abs(frac - p) < 5 * math.sqrt(p * (1 - p) / n), i
+
+
+def test_nswg_small_layers_are_complete_and_nested():
+    D = synthetic.unit_gaussian(900, 8, 20)
+    layers, ep, lev = oracle.build_nswg(D, 10, 20, 4, 8, iters=1, seed=3)
+    assert len(layers) == int(lev.max()) + 1
+    for i, lay in enumerate(layers):
+        assert (lay.gid == np.nonzero(lev >= i)[0]).all()
+        if i > 0:
+            assert set(lay.gid.tolist()) <= set(layers[i - 1].gid.tolist())
+        m = lay.gid.shape[0]
+        if m <= lay.R:
+            for a in range(m):
+                assert sorted(lay.nbr[a, : lay.deg[a]].tolist()) == sorted(
+                    int(x) for x in lay.gid if x != lay.gid[a])
+        assert (lay.deg <= lay.R).all()
+    assert ep == int(layers[-1].gid[0])
+
+
+def test_recall_helper_on_hand_made_lists():
+    D = np.array([[0.0], [1.0], [2.0], [2.0], [5.0]], np.float32)
+    Q = np.array([[0.0]], np.float32)
+    gt = oracle.knn(D, 3, Q=Q)
+    # the 3rd distance is a tie between ids 2 and 3: either counts
+    assert oracle.recall_at_k(np.array([[0, 1, 3]]), Q, D, 3, gt=gt) == 1.0
+    assert oracle.recall_at_k(np.array([[0, 0, 4]]), Q, D, 3, gt=gt) == pytest.approx(1 / 3)
+    assert oracle.recall_at_k(np.array([[-1, 2, 1]]), Q, D, 3, gt=gt) == pytest.approx(2 / 3)
