@@ -1,0 +1,385 @@
+#!/usr/bin/env python
+"""Benchmark of the graph-construction path on GB300.
+
+Workload: 1,000,000 x 128 float32 points (byte-valued Gaussian mixture of
+1,024 clusters, sigma 20), squared L2, exact kNN K=64, candidate pool L=200,
+degree bound R=32, alpha 66 / 60 degrees, I=2 OptKCNA iterations, NSWG
+routing layers (M=16); 10,000 queries, k=10, beams 32..256.
+
+A step is one full pg_build_rng (kNN -> 2 x [prune, reverse union, prune,
+connect, self-search] -> final RNG refinement -> routing layers) over the
+resident points.  value = build points/s over the whole job.  Under torchrun
+every rank builds its own replica (independent problems, weak scaling, no
+data-path collective); timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synthetic  # noqa: E402
+
+WORKLOAD = 2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--n", type=int, default=None, help="shrink the workload (tests only)")
+    ap.add_argument("--nq", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-queries", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+class Clocks:
+    """nvidia-smi sampling of SM clocks / throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def fp32_simt_peak_tflops(sm_mhz: float) -> float:
+    # 152 SMs x 128 FP32 lanes x 2 flop (FMA) x clock
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def oracle_build_rate(D, w, ns: int, threads: int | None = None):
+    """Oracle stages on the first ns points of the workload, extrapolated
+    to the full n: exact kNN scaled by (n/ns)^2, every other stage by n/ns."""
+    import oracle
+    if threads:
+        oracle.set_threads(threads)
+    n = D.shape[0]
+    S = np.ascontiguousarray(D[:ns])
+    K, L, R = w["K"], w["L"], w["R"]
+    t = {}
+    t0 = time.perf_counter()
+    ids, _ = oracle.knn(S, K)
+    t["knn"] = time.perf_counter() - t0
+    ep = oracle.medoid(S)
+    off = np.arange(ns + 1, dtype=np.int64) * K
+    cand = ids.ravel()
+    t["prune"] = t["union"] = t["connect"] = t["acquire"] = 0.0
+    for it in range(3):
+        alpha = 66.0 if it < 2 else 60.0
+        t0 = time.perf_counter()
+        nb, dg = oracle.prune(S, off, cand, R, alpha)
+        t["prune"] += time.perf_counter() - t0
+        t0 = time.perf_counter()
+        uo, ui = oracle.reverse_union(nb, dg)
+        t["union"] += time.perf_counter() - t0
+        t0 = time.perf_counter()
+        nb, dg = oracle.prune(S, uo, ui, R, alpha)
+        t["prune"] += time.perf_counter() - t0
+        t0 = time.perf_counter()
+        nb, dg, _ = oracle.connect(S, nb, dg, ep)
+        t["connect"] += time.perf_counter() - t0
+        if it < 2:
+            t0 = time.perf_counter()
+            c = oracle.acquire(S, nb, dg, L)
+            t["acquire"] += time.perf_counter() - t0
+            off = np.arange(ns + 1, dtype=np.int64) * L
+            cand = c.ravel()
+    scale = n / ns
+    total = t["knn"] * scale * scale + (t["prune"] + t["union"] + t["connect"] + t["acquire"]) * scale
+    sampled = sum(t.values())
+    return n / total, sampled, t
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+# ------------------------------------------------------------------ arms
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    n = args.n or synthetic.WORKLOADS[WORKLOAD]["n"]
+    D, _, w = synthetic.workload(WORKLOAD, n=n, nq=1)
+    ns = min(n, 8000)
+    cores = oracle.num_threads()
+    vals = []
+    for i in range(args.warmup + args.steps):
+        v, sampled, _ = oracle_build_rate(D, w, ns)
+        if i >= args.warmup:
+            vals.append(v)
+    value = statistics.mean(vals)
+    sample = (f"oracle stages (exact kNN, 3x[prune, reverse union, prune, connect], 2x self-search) "
+              f"on the first {ns} points of the {n}x{w['d']} workload; kNN time scaled by "
+              f"(n/{ns})^2, other stages by n/{ns}")
+    line = {
+        "impl": "reference", "metric": "build_points_per_s", "value": value,
+        "unit": "points/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": n / value * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w["name"], "n": n, "d": w["d"], "K": w["K"], "L": w["L"],
+                   "R": w["R"], "iters": 2},
+        "cpu_baseline": {"value": value, "unit": "points/s", "cores": cores, "kind": "oracle",
+                         "sample": sample, "cpu": cpu_model()},
+        "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import paper_2410_01231_gb300 as pg
+
+    n = args.n or synthetic.WORKLOADS[WORKLOAD]["n"]
+    nq = args.nq or synthetic.WORKLOADS[WORKLOAD]["nq"]
+    D, Q, w = synthetic.workload(WORKLOAD, n=n, nq=nq)
+    params = dict(K=w["K"], L=w["L"], R=w["R"], M=16, alpha_deg=66.0, alpha_final_deg=60.0,
+                  iters=2, precision=args.precision, route_layers=1, seed=0)
+    Dd = torch.from_numpy(D).cuda()
+    Qd = torch.from_numpy(Q).cuda()
+    stream = torch.cuda.current_stream()
+    ctx = pg.Context(stream)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        idx = pg.Index.build_rng(ctx, Dd, **params)
+        idx.close()
+
+    gpu_id = local
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        try:
+            gpu_id = int(vis.split(",")[local])
+        except ValueError:
+            pass
+    clocks = Clocks(gpu_id)
+    ctx.set_timing(True)
+    launches0 = ctx.launches
+    barrier()
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    phases = []
+    for _ in range(args.steps):
+        idx = pg.Index.build_rng(ctx, Dd, **params)
+        phases.append(idx.phase_seconds())
+        idx.close()
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    launches = ctx.launches - launches0
+    ms = ev0.elapsed_time(ev1) / args.steps
+    knn_ms, knn_launches = ctx.kernel_time("knn")
+    kt = {k: ctx.kernel_time(k) for k in ("knn", "prune", "union", "search", "medoid")}
+    ctx.set_timing(False)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * n / (ms / 1e3)
+
+    # ---------------------------------------------------------- queries
+    qres = {}
+    if not args.no_queries:
+        idx = pg.Index.build_rng(ctx, Dd, **params)
+        gt_i, gt_d = pg.knn_query(ctx, Dd, Qd, w["k"])
+        kth = gt_d[:, w["k"] - 1].clone()
+
+        def recall(ids):
+            dq = ((Qd[:, None, :] - Dd[ids.long().clamp(min=0)]) ** 2).sum(-1)
+            ok = (dq <= kth[:, None]) & (ids >= 0)
+            return float(ok.sum(1).clamp(max=w["k"]).float().mean() / w["k"])
+
+        curve = []
+        for beam in w["beams"]:
+            idx.search(Qd, w["k"], beam)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ids, _ = idx.search(Qd, w["k"], beam)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / 1e3
+            flat, _ = idx.search(Qd, w["k"], beam, flat=True)
+            curve.append({"beam": beam, "recall": recall(ids), "qps": nq / t,
+                          "recall_flat_entry": recall(flat)})
+        ok = [c for c in curve if c["recall"] >= 0.95]
+        best = ok[0] if ok else curve[-1]
+        lat = []
+        for i in range(min(200, nq)):
+            t0 = time.perf_counter()
+            idx.search(Qd[i:i + 1], w["k"], best["beam"])
+            lat.append((time.perf_counter() - t0) * 1e3)
+        qres = {"curve": curve, "beam_at_0.95": best["beam"] if ok else None,
+                "recall": best["recall"], "qps": best["qps"],
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "latency": "single-query requests, host wall time per call incl. launch + sync"}
+        idx.close()
+
+    # ------------------------------------------------------------- e2e
+    e2e = None
+    if not args.no_e2e:
+        Dh = torch.from_numpy(D).pin_memory()
+        nbr_h = torch.empty((n, w["R"]), dtype=torch.int32).pin_memory()
+        deg_h = torch.empty(n, dtype=torch.int32).pin_memory()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        Dx = torch.empty_like(Dd)
+        Dx.copy_(Dh, non_blocking=True)
+        idx = pg.Index.build_rng(ctx, Dx, **params)
+        _, nb, dg = idx.layer(0)
+        nbr_h.copy_(nb, non_blocking=True)
+        deg_h.copy_(dg, non_blocking=True)
+        e1.record(stream)
+        barrier()
+        idx.close()
+        t = e0.elapsed_time(e1) / 1e3
+        e2e = {"value": world * n / t, "unit": "points/s",
+               "h2d_bytes_per_step": int(D.nbytes),
+               "d2h_bytes_per_step": int(nbr_h.numel() * 4 + deg_h.numel() * 4)}
+
+    # -------------------------------------------------------- roofline
+    pk = peaks()
+    sm_mhz = (clk or {}).get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
+    knn_avg = knn_ms / max(1, knn_launches)
+    knn_flops = 2.0 * n * n * w["d"]
+    if args.precision == "fp32":
+        peak = fp32_simt_peak_tflops(pk.get("sm_max_mhz", 2070.0))
+        achieved = knn_flops / (knn_avg / 1e3) / 1e12
+        roof = {"kernel": "k_knn_fp32", "bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (derived)"}
+    else:
+        peak = pk.get("bf16_tflops", 1900.0)
+        achieved = knn_flops / (knn_avg / 1e3) / 1e12
+        roof = {"kernel": "knn_bf16", "bound": "tensor", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops (of measured)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        ns = min(n, 12000)
+        v, sampled, _ = oracle_build_rate(D, w, ns)
+        cpu = {"value": v, "unit": "points/s", "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": (f"oracle stages on the first {ns} points ({sampled:.1f} s of CPU work); "
+                          f"kNN scaled by (n/ns)^2, other stages by n/ns"),
+               "cpu": cpu_model()}
+
+    ph = {k: statistics.mean(p[k] for p in phases) for k in phases[0]} if phases else {}
+    line = {
+        "metric": "build_points_per_s", "value": value, "unit": "points/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "fp32" else "bf16", "data": "synthetic",
+        "config": {"workload": w["name"], "n": n, "d": w["d"], "K": w["K"], "L": w["L"],
+                   "R": w["R"], "alpha": [66.0, 60.0], "iters": 2, "route_layers_M": 16,
+                   "nq": nq, "k": w["k"], "precision": args.precision,
+                   "l2": "inputs larger than L2 (512 MB points)", "parallelism": "replicas"},
+        "queries": qres, "phase_s": ph,
+        "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
+        "roofline": roof, "clocks": clk, "gpu_launches": launches, "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,264 @@
+/*
+ * pg.h -- C ABI of a single-GPU (GB300, sm_103a) library that builds and
+ * searches proximity graphs with the construction framework of
+ * "Revisiting the Index Construction of Proximity Graph-Based Approximate
+ * Nearest Neighbor Search" (arXiv 2410.01231).
+ *
+ * Problem (Section 2): a dataset D of n points in R^d, row-major float32
+ * [n][d]; k-ANN search returns the k points with smallest distance to a
+ * query.  Symbols follow the paper: K = k0 (out-degree of the initial
+ * KNNG), L = pool width of the candidate search, R = the out-degree bound
+ * M of the pruned graph, alpha = the angle of alpha-pruning.
+ *
+ * Distances.  s(x, y) is the squared L2 distance (PG_METRIC_L2SQ), or for
+ * unit-norm rows the squared chord s = max(0, 2 - 2<x,y>) (PG_METRIC_COSINE
+ * and PG_METRIC_IP: on the unit sphere both rank like -<x,y>; rows are not
+ * normalised by the library).  Every list is ordered by the pair
+ * (s, id) ascending; ids are int32 (n < 2^31); unused slots hold id -1.
+ *
+ * Exactness.  Kernels decide every comparison in FP32 and re-decide in
+ * FP64, with the sequential coordinate-order sum of the CPU reference,
+ * every decision whose FP32 margin is inside a rigorous rounding bound, so
+ * pruned lists equal those of an FP64 evaluation of the same rule.
+ *
+ * Memory and streams.  Unless a parameter says "host", every pointer is a
+ * DEVICE pointer owned by the caller; the library never frees caller
+ * memory.  All work is queued on the stream given to pg_ctx_create; calls
+ * that return host-side results (stats, counts, indexes) synchronise that
+ * stream.  Scratch memory is taken from the stream-ordered allocator and
+ * counted against the context's HBM budget.
+ *
+ * Errors.  Every entry point returns a pg_status.  Invalid arguments are
+ * reported before any work is queued.  Kernels that meet an invalid input
+ * (an id outside [-1, n)) skip it and record it in a device error word,
+ * which the next synchronising call (or pg_ctx_sync) turns into
+ * PG_ERR_DEVICE_CHECK.  pg_last_error() gives a one-line message.  No
+ * exception crosses this boundary.
+ */
+#ifndef PG_H
+#define PG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PG_OK = 0,
+    PG_ERR_INVALID_ARG = 1, /* argument outside its documented range     */
+    PG_ERR_OOM = 2,         /* device allocation failed                   */
+    PG_ERR_CUDA = 3,        /* a CUDA runtime call failed                 */
+    PG_ERR_TIMEOUT = 4,     /* a bounded device wait ran out              */
+    PG_ERR_CAPACITY = 5,    /* input larger than a documented capacity    */
+    PG_ERR_BUDGET = 6,      /* scratch would exceed the context HBM budget */
+    PG_ERR_INTERNAL = 7,    /* invariant broken inside the library         */
+    PG_ERR_DEVICE_CHECK = 8 /* a kernel met an invalid id (skipped)        */
+} pg_status;
+
+typedef enum { PG_METRIC_L2SQ = 0, PG_METRIC_COSINE = 1, PG_METRIC_IP = 2 } pg_metric;
+
+/* PG_PREC_FP32: distances in FP32 (FP64 recheck near margins).
+ * PG_PREC_BF16_SCREEN: distance tiles / gathers from a BF16 copy of D with
+ * FP32 accumulation; decisions inside the BF16 error bound are redone in
+ * FP32 and then FP64, so results equal the FP32 form's. */
+typedef enum { PG_PREC_FP32 = 0, PG_PREC_BF16_SCREEN = 1 } pg_precision;
+
+typedef struct pg_ctx pg_ctx;
+typedef struct pg_index pg_index;
+
+/* Counters of one pruning call (host struct filled on return). */
+typedef struct {
+    int64_t rows;               /* points pruned                              */
+    int64_t candidates;         /* distinct candidates after de-duplication   */
+    int64_t scanned;            /* candidates visited before the R-stop       */
+    int64_t occlusion_tests;    /* (v, w) pairs evaluated                     */
+    int64_t fp64_rechecks;      /* decisions re-made in FP64                   */
+    int64_t fp64_flips;         /* ... whose FP64 outcome differed from FP32's */
+    int64_t edges;              /* kept edges (sum of out-degrees)            */
+    int64_t long_rows;          /* rows handled by the long-row kernel        */
+} pg_prune_stats;
+
+/* Parameters of the graph builds (pg_default_params fills the defaults). */
+typedef struct {
+    pg_metric metric;
+    pg_precision precision;
+    int32_t K;               /* k0: degree of the exact initial KNNG (Alg. 6 l.1)   */
+    int32_t L;               /* pool width of the k-CNA search (Alg. 5 l.8); ef    */
+    int32_t R;               /* degree bound M of the RNG graph / NSWG layer 0     */
+    int32_t M;               /* NSWG upper-layer degree bound and level base       */
+    double alpha_deg;        /* alpha of the OptKCNA refinements (Section 4.1)     */
+    double alpha_final_deg;  /* alpha of the final refinement; 60 = RNG pruning    */
+    int32_t iters;           /* I: OptKCNA iterations (Alg. 6; paper default 2)     */
+    int32_t connect_final;   /* RNG build: connectivity step after the final prune  */
+    int32_t route_layers;    /* RNG build: add NSWG upper layers for query routing  */
+    uint64_t seed;           /* level draw (SplitMix64, seed XOR id)                */
+} pg_build_params;
+
+/* Defaults: L2SQ, FP32, K=64, L=200, R=32, M=16, alpha 66/60, I=2,
+ * connect_final=1, route_layers=1, seed=0.  params must not be NULL. */
+void pg_default_params(pg_build_params *params);
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context bound to the current CUDA device and to `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  hbm_budget_bytes
+ * caps the scratch the library may hold at once (0 = no cap).  *out
+ * receives the context; destroy it with pg_ctx_destroy. */
+pg_status pg_ctx_create(void *cuda_stream, size_t hbm_budget_bytes, pg_ctx **out);
+void pg_ctx_destroy(pg_ctx *ctx);
+/* Message of the last non-OK status returned on this context ("" if none).
+ * The pointer stays valid until the next call on the context. */
+const char *pg_last_error(const pg_ctx *ctx);
+/* Synchronise the context stream; PG_ERR_DEVICE_CHECK if a kernel recorded
+ * an invalid input since the previous synchronisation. */
+pg_status pg_ctx_sync(pg_ctx *ctx);
+/* Number of kernels this context has launched so far (host counter). */
+int64_t pg_ctx_launches(const pg_ctx *ctx);
+
+/* CUDA-event timing of the library's main kernels (off by default).
+ * Enabling (or disabling) resets the totals.  Names: "knn" (distance tiles
+ * + top-K), "prune", "union", "connect", "search" (beam search, including
+ * k-CNA acquisition), "medoid".  *total_ms / *launches (host) receive the
+ * summed device time and launch count since the last reset; the query
+ * synchronises the stream. */
+pg_status pg_ctx_set_timing(pg_ctx *ctx, int enable);
+pg_status pg_ctx_kernel_time(pg_ctx *ctx, const char *name, double *total_ms, int64_t *launches);
+
+/* ------------------------------------------------------------------ steps */
+
+/* Exact K nearest neighbours of every point (the KNNG G_k0 of the
+ * initialization phase, Section 3.1 and Algorithm 6 line 1, computed by
+ * brute force).  For every u the K smallest (s(u,v), v) with v != u.
+ * ids [n][K], dist [n][K] (FP32 value of s); rows with fewer than K other
+ * points are padded with -1 / +inf.  1 <= K <= 256, d % 4 == 0. */
+pg_status pg_build_knn(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
+                       int32_t K, pg_precision precision, int32_t *ids, float *dist);
+
+/* Exact k nearest points of D for external queries Q [nq][d] (ground
+ * truth for recall).  Same output layout as pg_build_knn. */
+pg_status pg_knn_query(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
+                       const float *Q, int64_t nq, int32_t k, int32_t *ids, float *dist);
+
+/* alpha-pruning of every candidate row (Section 4.1 definition, scanned
+ * as in Prune, Algorithm 3).  Row u holds cand_ids[cand_off[u] ..
+ * cand_off[u+1]-1] (cand_off has n+1 entries, non-decreasing); entries -1,
+ * u itself and repeated ids are ignored.  The candidates are ordered by
+ * (s(u,v), v); v is kept unless an already kept w has s(u,w) < s(u,v),
+ * s(v,w) < s(u,v) and angle(u,w,v) > alpha; the scan stops at R kept.
+ * alpha_deg = 60 is RNG pruning (the angle clause is then implied).
+ * Output nbr [n][R] in keep order (-1 padded), deg [n].  R in [1, 64];
+ * rows longer than 16384 candidates return PG_ERR_CAPACITY.  host_stats
+ * (host pointer, may be NULL) receives counters and makes the call
+ * synchronous. */
+pg_status pg_prune(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
+                   const int64_t *cand_off, const int32_t *cand_ids, int32_t R,
+                   double alpha_deg, pg_precision precision, int32_t *nbr, int32_t *deg,
+                   pg_prune_stats *host_stats);
+
+/* Reverse-edge union (Algorithm 2 lines 7-8, Algorithm 5 lines 3-4): row
+ * u = N(u) together with every v that has u in N(v).  nbr [n][R], deg [n]
+ * in; off [n+1] and ids out (ids needs capacity >= 2 * sum(deg); entries
+ * within a row are in no particular order).  *host_total (host, may be
+ * NULL) receives off[n] and makes the call synchronous. */
+pg_status pg_reverse_union(pg_ctx *ctx, const int32_t *nbr, const int32_t *deg, int64_t n,
+                           int32_t R, int64_t *off, int32_t *ids, int64_t ids_capacity,
+                           int64_t *host_total);
+
+/* Entry point: the point nearest the centroid (Section 3.1, search phase),
+ * exact argmin by (s, id); the centroid is summed in FP64 per coordinate
+ * in blocks of 1024 consecutive points (each in index order, then the block
+ * sums in order) and divided by n.  *host_ep (host) receives the id. */
+pg_status pg_medoid(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
+                    int64_t *host_ep);
+
+/* Connectivity step (Algorithm 2 lines 10-11, Algorithm 5 lines 5-6),
+ * in place on nbr/deg: S = nodes reachable from ep; while S != V the
+ * smallest unreached id r is linked from p = argmin over x in S with
+ * deg(x) < R of (s(x,r), x), and everything reachable from r joins S.
+ * *host_added (host, may be NULL) receives the number of edges added.
+ * PG_ERR_CAPACITY if no reached node has a free slot.  Synchronous. */
+pg_status pg_connect(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
+                     int32_t *nbr, int32_t *deg, int32_t R, int64_t ep, int64_t *host_added);
+
+/* k-CNA acquisition by search on the refined graph (Algorithm 5 lines
+ * 7-8): for every u, KANNSearch(G, u, L, L, u) of Algorithm 1; row u of
+ * cand [n][L] receives the final pool minus u, in (s, id) order, padded
+ * with -1.  nbr [n][R] / deg [n] is the graph.  1 <= L <= 256, R <= 64. */
+pg_status pg_acquire_candidates(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
+                                pg_metric metric, const int32_t *nbr, const int32_t *deg,
+                                int32_t R, int32_t L, pg_precision precision, int32_t *cand);
+
+/* Batched beam search, KANNSearch(G, q, k, L, ep) of Algorithm 1, on one
+ * graph: query i starts at starts[i] (device, nq entries).  rows (device,
+ * may be NULL) maps a point id to its adjacency row when the graph covers
+ * a subset of D (a layer of a hierarchical index); NULL = row id.  Output
+ * out_ids / out_dist [nq][k], padded with -1 / +inf.  1 <= k <= L <= 256. */
+pg_status pg_search_graph(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
+                          const int32_t *nbr, const int32_t *deg, int32_t R,
+                          const int32_t *rows, const float *Q, int64_t nq,
+                          const int32_t *starts, int32_t k, int32_t L, pg_precision precision,
+                          int32_t *out_ids, float *out_dist);
+
+/* ----------------------------------------------------------------- builds */
+
+/* IterNSG with a fixed number of iterations (Algorithm 6 with the
+ * OptKCNA iterations of Algorithm 5; final refinement as Algorithm 2 lines
+ * 5-11).  With route_layers set, NSWG upper layers (Algorithm 7, i >= 1)
+ * are added so that queries enter the graph near their target.  D stays
+ * owned by the caller and must outlive the index.  Synchronous. */
+pg_status pg_build_rng(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
+                       const pg_build_params *params, pg_index **out);
+
+/* Global NSWG construction, OptHNSW (Algorithm 7): levels drawn up front
+ * (l(u) = floor(-ln U / ln M), U from SplitMix64(seed XOR u)); layer i
+ * holds D_i = {u : l(u) >= i}; a layer with |D_i| <= its degree bound is
+ * complete, any other is an IterNSG build of D_i without the final
+ * connectivity step.  Layer 0 bound R, upper layers M.  Synchronous. */
+pg_status pg_build_nswg(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
+                        const pg_build_params *params, pg_index **out);
+
+#define PG_SEARCH_FLAT 1 /* ignore routing layers: start at the medoid */
+
+/* k-ANN queries on an index: greedy KANNSearch(G_i, q, 1, 1, w) from the
+ * top layer down to layer 1, then KANNSearch(G_0, q, k, beam, w) (pattern
+ * of Algorithm 4 lines 8-12); an index without upper layers (or with
+ * PG_SEARCH_FLAT) starts at its medoid.  Q [nq][d] device; out [nq][k]. */
+pg_status pg_search(pg_ctx *ctx, const pg_index *index, const float *Q, int64_t nq, int32_t k,
+                    int32_t beam, int32_t flags, pg_precision precision, int32_t *out_ids,
+                    float *out_dist);
+
+/* Same as pg_search with HOST buffers (Q, out_ids, out_dist in host
+ * memory, pinned or pageable): copies in, searches, copies out and
+ * synchronises. */
+pg_status pg_search_host(pg_ctx *ctx, const pg_index *index, const float *Q, int64_t nq,
+                         int32_t k, int32_t beam, int32_t flags, pg_precision precision,
+                         int32_t *out_ids, float *out_dist);
+
+void pg_index_destroy(pg_index *index);
+
+/* Shape of an index: number of layers, points, entry points (host outs). */
+pg_status pg_index_info(const pg_index *index, int32_t *n_layers, int64_t *n, int64_t *ep_top,
+                        int64_t *ep_base);
+
+/* Device pointers of layer `layer` (owned by the index): *count nodes,
+ * degree bound *R, gid [count] (ascending point ids; NULL for layer 0,
+ * which holds every point), nbr [count][R] of point ids, deg [count]. */
+pg_status pg_index_layer(const pg_index *index, int32_t layer, int64_t *count, int32_t *R,
+                         const int32_t **gid, const int32_t **nbr, const int32_t **deg);
+
+/* Copy layer `layer` of an index into caller DEVICE buffers: gid [count]
+ * (may be NULL; for layer 0 it receives 0..n-1), nbr [count][R] and deg
+ * [count] (shapes from pg_index_layer).  Synchronous. */
+pg_status pg_index_export_layer(pg_ctx *ctx, const pg_index *index, int32_t layer, int32_t *gid,
+                                int32_t *nbr, int32_t *deg);
+
+/* Seconds spent per build phase by the last build on this index:
+ * knn, prune, union, connect, acquire, layers (host array of 6). */
+pg_status pg_index_phase_seconds(const pg_index *index, double *host_seconds6);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PG_H */

@@ -1,0 +1,362 @@
+"""Python binding of libpg: proximity-graph construction and search on one
+GB300 GPU, after the framework of arXiv 2410.01231.
+
+Argument marshalling only: every step runs in the CUDA kernels of libpg.so
+(built in-tree from ``csrc/`` for sm_103a).  Importing this package loads the
+library and raises if it is missing -- there is no CPU fallback.  Torch
+tensors provide device memory and the stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+from . import _build
+
+_LIB_PATH = _build.LIB
+
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(f"libpg.so is not built ({_LIB_PATH}); run paper_2410_01231_gb300._build.build()"
+                      " or __graft_entry__.build()")
+
+_lib = C.CDLL(_LIB_PATH)
+
+METRIC = {"l2": 0, "cosine": 1, "ip": 2}
+PRECISION = {"fp32": 0, "bf16": 1}
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "TIMEOUT", 5: "CAPACITY", 6: "BUDGET",
+          7: "INTERNAL", 8: "DEVICE_CHECK"}
+
+P = C.c_void_p
+i32, i64, dbl, u64 = C.c_int32, C.c_int64, C.c_double, C.c_uint64
+
+
+class BuildParams(C.Structure):
+    _fields_ = [("metric", C.c_int), ("precision", C.c_int), ("K", i32), ("L", i32), ("R", i32),
+                ("M", i32), ("alpha_deg", dbl), ("alpha_final_deg", dbl), ("iters", i32),
+                ("connect_final", i32), ("route_layers", i32), ("seed", u64)]
+
+
+class PruneStats(C.Structure):
+    _fields_ = [(name, i64) for name in ("rows", "candidates", "scanned", "occlusion_tests",
+                                         "fp64_rechecks", "fp64_flips", "edges", "long_rows")]
+
+
+def _sig(name, res, args):
+    f = getattr(_lib, name)
+    f.restype = res
+    f.argtypes = args
+    return f
+
+
+_sig("pg_default_params", None, [P])
+_sig("pg_ctx_create", C.c_int, [P, C.c_size_t, P])
+_sig("pg_ctx_destroy", None, [P])
+_sig("pg_last_error", C.c_char_p, [P])
+_sig("pg_ctx_sync", C.c_int, [P])
+_sig("pg_ctx_launches", i64, [P])
+_sig("pg_build_knn", C.c_int, [P, P, i64, i32, C.c_int, i32, C.c_int, P, P])
+_sig("pg_knn_query", C.c_int, [P, P, i64, i32, C.c_int, P, i64, i32, P, P])
+_sig("pg_prune", C.c_int, [P, P, i64, i32, C.c_int, P, P, i32, dbl, C.c_int, P, P, P])
+_sig("pg_reverse_union", C.c_int, [P, P, P, i64, i32, P, P, i64, P])
+_sig("pg_medoid", C.c_int, [P, P, i64, i32, C.c_int, P])
+_sig("pg_connect", C.c_int, [P, P, i64, i32, C.c_int, P, P, i32, i64, P])
+_sig("pg_acquire_candidates", C.c_int, [P, P, i64, i32, C.c_int, P, P, i32, i32, C.c_int, P])
+_sig("pg_search_graph", C.c_int, [P, P, i64, i32, C.c_int, P, P, i32, P, P, i64, P, i32, i32,
+                                  C.c_int, P, P])
+_sig("pg_build_rng", C.c_int, [P, P, i64, i32, P, P])
+_sig("pg_build_nswg", C.c_int, [P, P, i64, i32, P, P])
+_sig("pg_search", C.c_int, [P, P, P, i64, i32, i32, i32, C.c_int, P, P])
+_sig("pg_search_host", C.c_int, [P, P, P, i64, i32, i32, i32, C.c_int, P, P])
+_sig("pg_index_destroy", None, [P])
+_sig("pg_index_info", C.c_int, [P, P, P, P, P])
+_sig("pg_index_layer", C.c_int, [P, i32, P, P, P, P, P])
+_sig("pg_index_phase_seconds", C.c_int, [P, P])
+_sig("pg_index_export_layer", C.c_int, [P, P, i32, P, P, P])
+_sig("pg_ctx_set_timing", C.c_int, [P, C.c_int])
+_sig("pg_ctx_kernel_time", C.c_int, [P, C.c_char_p, P, P])
+
+EXPORTS = ["pg_default_params", "pg_ctx_create", "pg_ctx_destroy", "pg_last_error", "pg_ctx_sync",
+           "pg_ctx_launches", "pg_build_knn", "pg_knn_query", "pg_prune", "pg_reverse_union",
+           "pg_medoid", "pg_connect", "pg_acquire_candidates", "pg_search_graph", "pg_build_rng",
+           "pg_build_nswg", "pg_search", "pg_search_host", "pg_index_destroy", "pg_index_info",
+           "pg_index_layer", "pg_index_phase_seconds", "pg_index_export_layer",
+           "pg_ctx_set_timing", "pg_ctx_kernel_time"]
+
+
+class PGError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"pg status {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _dev(t: torch.Tensor, dtype, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    return t.contiguous()
+
+
+class Context:
+    """A libpg context bound to the current device and a CUDA stream."""
+
+    def __init__(self, stream: torch.cuda.Stream | None = None, hbm_budget_bytes: int = 0):
+        if not torch.cuda.is_available():
+            raise RuntimeError("libpg needs a CUDA device")
+        self.stream = stream or torch.cuda.current_stream()
+        h = C.c_void_p()
+        st = _lib.pg_ctx_create(C.c_void_p(self.stream.cuda_stream), hbm_budget_bytes, C.byref(h))
+        if st != 0:
+            raise PGError(st, "pg_ctx_create")
+        self._h = h
+
+    def _check(self, st, what):
+        if st != 0:
+            raise PGError(st, f"{what}: {_lib.pg_last_error(self._h).decode()}")
+
+    def sync(self):
+        self._check(_lib.pg_ctx_sync(self._h), "sync")
+
+    @property
+    def launches(self) -> int:
+        return int(_lib.pg_ctx_launches(self._h))
+
+    def set_timing(self, enable: bool = True):
+        """Enable CUDA-event timing of the main kernels (resets totals)."""
+        self._check(_lib.pg_ctx_set_timing(self._h, 1 if enable else 0), "pg_ctx_set_timing")
+
+    def kernel_time(self, name: str):
+        """(total device ms, launches) of a timed kernel since the last reset."""
+        ms, cnt = C.c_double(), C.c_int64()
+        self._check(_lib.pg_ctx_kernel_time(self._h, name.encode(), C.byref(ms), C.byref(cnt)),
+                    "pg_ctx_kernel_time")
+        return ms.value, cnt.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.pg_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+
+def default_params(**kw) -> BuildParams:
+    p = BuildParams()
+    _lib.pg_default_params(C.byref(p))
+    for k, v in kw.items():
+        if k == "metric":
+            v = METRIC[v] if isinstance(v, str) else v
+        if k == "precision":
+            v = PRECISION[v] if isinstance(v, str) else v
+        setattr(p, k, v)
+    return p
+
+
+# --------------------------------------------------------------- steps
+def build_knn(ctx: Context, D: torch.Tensor, K: int, metric="l2", precision="fp32"):
+    """Exact K-NN graph: (ids int32 [n][K], dist float32 [n][K])."""
+    D = _dev(D, torch.float32, "D")
+    n, d = D.shape
+    ids = torch.empty((n, K), dtype=torch.int32, device=D.device)
+    dist = torch.empty((n, K), dtype=torch.float32, device=D.device)
+    ctx._check(_lib.pg_build_knn(ctx.handle, _ptr(D), n, d, METRIC[metric], K,
+                                 PRECISION[precision], _ptr(ids), _ptr(dist)), "pg_build_knn")
+    return ids, dist
+
+
+def knn_query(ctx: Context, D: torch.Tensor, Q: torch.Tensor, k: int, metric="l2"):
+    D = _dev(D, torch.float32, "D")
+    Q = _dev(Q, torch.float32, "Q")
+    ids = torch.empty((Q.shape[0], k), dtype=torch.int32, device=D.device)
+    dist = torch.empty((Q.shape[0], k), dtype=torch.float32, device=D.device)
+    ctx._check(_lib.pg_knn_query(ctx.handle, _ptr(D), D.shape[0], D.shape[1], METRIC[metric],
+                                 _ptr(Q), Q.shape[0], k, _ptr(ids), _ptr(dist)), "pg_knn_query")
+    return ids, dist
+
+
+def prune(ctx: Context, D, off, cand, R: int, alpha_deg: float, metric="l2", precision="fp32",
+          stats: bool = False):
+    """alpha-pruning of CSR candidate rows: (nbr [n][R], deg [n][, stats])."""
+    D = _dev(D, torch.float32, "D")
+    off = _dev(off, torch.int64, "off")
+    cand = _dev(cand, torch.int32, "cand")
+    n, d = D.shape
+    nbr = torch.empty((n, R), dtype=torch.int32, device=D.device)
+    deg = torch.empty(n, dtype=torch.int32, device=D.device)
+    ps = PruneStats()
+    ctx._check(_lib.pg_prune(ctx.handle, _ptr(D), n, d, METRIC[metric], _ptr(off), _ptr(cand), R,
+                             float(alpha_deg), PRECISION[precision], _ptr(nbr), _ptr(deg),
+                             C.byref(ps) if stats else None), "pg_prune")
+    if stats:
+        return nbr, deg, {k: int(getattr(ps, k)) for k, _ in PruneStats._fields_}
+    return nbr, deg
+
+
+def reverse_union(ctx: Context, nbr, deg):
+    nbr = _dev(nbr, torch.int32, "nbr")
+    deg = _dev(deg, torch.int32, "deg")
+    n, R = nbr.shape
+    off = torch.empty(n + 1, dtype=torch.int64, device=nbr.device)
+    ids = torch.empty(2 * n * R, dtype=torch.int32, device=nbr.device)
+    tot = C.c_int64()
+    ctx._check(_lib.pg_reverse_union(ctx.handle, _ptr(nbr), _ptr(deg), n, R, _ptr(off), _ptr(ids),
+                                     2 * n * R, C.byref(tot)), "pg_reverse_union")
+    return off, ids[: tot.value]
+
+
+def medoid(ctx: Context, D, metric="l2") -> int:
+    D = _dev(D, torch.float32, "D")
+    ep = C.c_int64()
+    ctx._check(_lib.pg_medoid(ctx.handle, _ptr(D), D.shape[0], D.shape[1], METRIC[metric],
+                              C.byref(ep)), "pg_medoid")
+    return int(ep.value)
+
+
+def connect(ctx: Context, D, nbr, deg, ep: int, metric="l2") -> int:
+    """In place on nbr/deg; returns the number of edges added."""
+    D = _dev(D, torch.float32, "D")
+    if not (nbr.is_contiguous() and deg.is_contiguous()):
+        raise ValueError("nbr/deg must be contiguous (updated in place)")
+    n, R = nbr.shape
+    added = C.c_int64()
+    ctx._check(_lib.pg_connect(ctx.handle, _ptr(D), n, D.shape[1], METRIC[metric], _ptr(nbr),
+                               _ptr(deg), R, ep, C.byref(added)), "pg_connect")
+    return int(added.value)
+
+
+def acquire_candidates(ctx: Context, D, nbr, deg, L: int, metric="l2", precision="fp32"):
+    D = _dev(D, torch.float32, "D")
+    nbr = _dev(nbr, torch.int32, "nbr")
+    deg = _dev(deg, torch.int32, "deg")
+    n, d = D.shape
+    cand = torch.empty((n, L), dtype=torch.int32, device=D.device)
+    ctx._check(_lib.pg_acquire_candidates(ctx.handle, _ptr(D), n, d, METRIC[metric], _ptr(nbr),
+                                          _ptr(deg), nbr.shape[1], L, PRECISION[precision],
+                                          _ptr(cand)), "pg_acquire_candidates")
+    return cand
+
+
+def search_graph(ctx: Context, D, nbr, deg, Q, starts, k: int, L: int, metric="l2", rows=None,
+                 precision="fp32"):
+    D = _dev(D, torch.float32, "D")
+    nbr = _dev(nbr, torch.int32, "nbr")
+    deg = _dev(deg, torch.int32, "deg")
+    Q = _dev(Q, torch.float32, "Q")
+    starts = _dev(starts, torch.int32, "starts")
+    rows = None if rows is None else _dev(rows, torch.int32, "rows")
+    nq = Q.shape[0]
+    ids = torch.empty((nq, k), dtype=torch.int32, device=D.device)
+    dist = torch.empty((nq, k), dtype=torch.float32, device=D.device)
+    ctx._check(_lib.pg_search_graph(ctx.handle, _ptr(D), D.shape[0], D.shape[1], METRIC[metric],
+                                    _ptr(nbr), _ptr(deg), nbr.shape[1], _ptr(rows), _ptr(Q), nq,
+                                    _ptr(starts), k, L, PRECISION[precision], _ptr(ids),
+                                    _ptr(dist)), "pg_search_graph")
+    return ids, dist
+
+
+# --------------------------------------------------------------- index
+class Index:
+    """A built graph index (owned by libpg; D must stay alive)."""
+
+    def __init__(self, ctx: Context, handle, D: torch.Tensor, metric: str):
+        self.ctx, self._h, self.D, self.metric = ctx, handle, D, metric
+
+    @classmethod
+    def build_rng(cls, ctx: Context, D: torch.Tensor, **params):
+        return cls._build(ctx, D, "pg_build_rng", params)
+
+    @classmethod
+    def build_nswg(cls, ctx: Context, D: torch.Tensor, **params):
+        return cls._build(ctx, D, "pg_build_nswg", params)
+
+    @classmethod
+    def _build(cls, ctx, D, fn, params):
+        D = _dev(D, torch.float32, "D")
+        p = default_params(**params)
+        h = C.c_void_p()
+        ctx._check(getattr(_lib, fn)(ctx.handle, _ptr(D), D.shape[0], D.shape[1], C.byref(p),
+                                     C.byref(h)), fn)
+        metric = {v: k for k, v in METRIC.items()}[p.metric]
+        return cls(ctx, h, D, metric)
+
+    def info(self):
+        nl, n, et, eb = C.c_int32(), C.c_int64(), C.c_int64(), C.c_int64()
+        _lib.pg_index_info(self._h, C.byref(nl), C.byref(n), C.byref(et), C.byref(eb))
+        return dict(n_layers=nl.value, n=n.value, ep_top=et.value, ep_base=eb.value)
+
+    def layer(self, i: int):
+        """(gid, nbr, deg) of layer i as new device tensors (gid of layer 0 is 0..n-1)."""
+        cnt, R = C.c_int64(), C.c_int32()
+        st = _lib.pg_index_layer(self._h, i, C.byref(cnt), C.byref(R), None, None, None)
+        if st != 0:
+            raise PGError(st, "pg_index_layer")
+        m, R = cnt.value, R.value
+        dev = self.D.device
+        gid = torch.empty(m, dtype=torch.int32, device=dev)
+        nbr = torch.empty((m, R), dtype=torch.int32, device=dev)
+        deg = torch.empty(m, dtype=torch.int32, device=dev)
+        self.ctx._check(_lib.pg_index_export_layer(self.ctx.handle, self._h, i, _ptr(gid),
+                                                   _ptr(nbr), _ptr(deg)), "pg_index_export_layer")
+        return gid, nbr, deg
+
+    def phase_seconds(self):
+        arr = (C.c_double * 6)()
+        _lib.pg_index_phase_seconds(self._h, arr)
+        return dict(zip(["knn", "prune", "union", "connect", "acquire", "layers"], list(arr)))
+
+    def search(self, Q: torch.Tensor, k: int, beam: int, flat: bool = False, precision="fp32"):
+        Q = _dev(Q, torch.float32, "Q")
+        nq = Q.shape[0]
+        ids = torch.empty((nq, k), dtype=torch.int32, device=Q.device)
+        dist = torch.empty((nq, k), dtype=torch.float32, device=Q.device)
+        self.ctx._check(_lib.pg_search(self.ctx.handle, self._h, _ptr(Q), nq, k, beam,
+                                       1 if flat else 0, PRECISION[precision], _ptr(ids),
+                                       _ptr(dist)), "pg_search")
+        return ids, dist
+
+    def search_host(self, Q: np.ndarray, k: int, beam: int, flat: bool = False,
+                    out_ids: np.ndarray | None = None, out_dist: np.ndarray | None = None):
+        """Host buffers in and out (copies inside the call)."""
+        if not (isinstance(Q, np.ndarray) or isinstance(Q, torch.Tensor)):
+            raise TypeError("Q must be a host array")
+        nq = Q.shape[0]
+        if out_ids is None:
+            out_ids = np.empty((nq, k), np.int32)
+        if out_dist is None:
+            out_dist = np.empty((nq, k), np.float32)
+
+        def hp(a):
+            if isinstance(a, torch.Tensor):
+                return C.c_void_p(a.data_ptr())
+            return a.ctypes.data_as(C.c_void_p)
+
+        self.ctx._check(_lib.pg_search_host(self.ctx.handle, self._h, hp(Q), nq, k, beam,
+                                            1 if flat else 0, 0, hp(out_ids), hp(out_dist)),
+                        "pg_search_host")
+        return out_ids, out_dist
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.pg_index_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,291 @@
+// pg_internal.cuh -- context, scratch, launch accounting and the device
+// helpers shared by the kernels of libpg (GB300, sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/pg.h"
+
+// ---------------------------------------------------------------- context
+struct pg_ctx {
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int num_sms = 0;
+    size_t budget = 0;  // 0 = unlimited
+    size_t in_use = 0;
+    std::string last_error;
+    int *d_err = nullptr;                     // [4]: code, where, info lo, info hi
+    unsigned long long *d_counters = nullptr;  // kernel statistics
+    unsigned long long *h_pinned = nullptr;   // pinned host mirror for small reads
+    int64_t launches = 0;
+    // optional CUDA-event timing of named kernels
+    int timing = 0;
+    struct TimedPair {
+        int slot;
+        cudaEvent_t a, b;
+    };
+    std::vector<TimedPair> pending;
+    std::vector<cudaEvent_t> event_pool;
+    double timer_ms[16] = {0};
+    int64_t timer_launches[16] = {0};
+};
+
+// named kernel timers
+enum { TM_KNN = 0, TM_PRUNE, TM_UNION, TM_CONNECT, TM_SEARCH, TM_MEDOID, TM_SLOTS };
+extern const char *const pg_timer_names[TM_SLOTS];
+// Record an event before / after a launch when timing is enabled.
+void pg_timer_begin(pg_ctx *ctx, int slot);
+void pg_timer_end(pg_ctx *ctx, int slot);
+void pg_timer_resolve(pg_ctx *ctx);
+
+enum { PG_CNT_SLOTS = 32 };
+// counter slots
+enum {
+    CNT_ROWS = 0, CNT_CANDS, CNT_SCANNED, CNT_OCCL, CNT_RECHECK, CNT_FLIP, CNT_EDGES, CNT_LONG,
+    CNT_LONG_LIST = 16, CNT_KNN_RECHECK = 17, CNT_KNN_UNRESOLVED = 18, CNT_SEARCH_EXP = 19,
+    CNT_SEARCH_EVAL = 20
+};
+
+// device error codes (first one recorded wins)
+enum { DERR_NONE = 0, DERR_BAD_ID = 1, DERR_CAPACITY = 2, DERR_NO_SLOT = 3, DERR_INTERNAL = 4 };
+
+pg_status pg_fail(pg_ctx *ctx, pg_status st, const char *fmt, ...);
+pg_status pg_cuda_fail(pg_ctx *ctx, cudaError_t e, const char *what);
+
+#define PG_TRY_CUDA(ctx, call)                                          \
+    do {                                                                \
+        cudaError_t _e = (call);                                        \
+        if (_e != cudaSuccess) return pg_cuda_fail((ctx), _e, #call);   \
+    } while (0)
+
+#define PG_TRY(call)                          \
+    do {                                      \
+        pg_status _s = (call);                \
+        if (_s != PG_OK) return _s;           \
+    } while (0)
+
+// Count a kernel launch and check the launch error.
+#define PG_LAUNCHED(ctx)                                                      \
+    do {                                                                      \
+        (ctx)->launches++;                                                    \
+        cudaError_t _e = cudaGetLastError();                                  \
+        if (_e != cudaSuccess) return pg_cuda_fail((ctx), _e, "kernel launch"); \
+    } while (0)
+
+// Stream-ordered scratch counted against the budget.
+pg_status pg_alloc(pg_ctx *ctx, void **p, size_t bytes);
+void pg_free(pg_ctx *ctx, void *p, size_t bytes);
+
+template <class T>
+struct Scratch {
+    pg_ctx *ctx = nullptr;
+    T *p = nullptr;
+    size_t bytes = 0;
+    Scratch() = default;
+    Scratch(const Scratch &) = delete;
+    Scratch &operator=(const Scratch &) = delete;
+    pg_status alloc(pg_ctx *c, size_t count) {
+        release();
+        ctx = c;
+        bytes = count * sizeof(T);
+        if (bytes == 0) bytes = sizeof(T);
+        void *q = nullptr;
+        pg_status s = pg_alloc(ctx, &q, bytes);
+        p = static_cast<T *>(q);
+        if (s != PG_OK) bytes = 0;
+        return s;
+    }
+    void release() {
+        if (p) pg_free(ctx, p, bytes);
+        p = nullptr;
+        bytes = 0;
+    }
+    ~Scratch() { release(); }
+};
+
+// Synchronise and translate the device error word.
+pg_status pg_sync_check(pg_ctx *ctx, const char *where);
+// Reset statistics counters (async).
+pg_status pg_reset_counters(pg_ctx *ctx);
+pg_status pg_read_counters(pg_ctx *ctx, unsigned long long *host32);
+
+// ---------------------------------------------------------- arithmetic facts
+// Data facts computed once per dataset: whether every FP32 distance the
+// kernels form is exact (integer-valued rows small enough that all partial
+// sums stay below 2^24), and the largest squared row norm.
+struct DataFacts {
+    int exact = 0;
+    float max_norm2 = 0.f;
+    float max_abs = 0.f;
+};
+pg_status pg_data_facts(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
+                        DataFacts *out);
+
+// Error model of an FP32 distance s computed by the kernels (difference form
+// sum of squares for L2, dot product for the chord).  Bounds the distance
+// to the FP64 sequential value of the CPU reference.
+struct ErrModel {
+    int metric = 0;    // 0 = L2 (relative), else chord (absolute)
+    float rel = 0.f;   // L2: |s32 - s64| <= rel * s32
+    float abs_ = 0.f;  // chord: |s32 - s64| <= abs_
+    __host__ __device__ inline float err(float s) const {
+        return metric == 0 ? rel * s : abs_;
+    }
+};
+ErrModel pg_err_model(pg_metric metric, int d, const DataFacts &f, bool gemm_form);
+
+// --------------------------------------------------------- device helpers
+#ifdef __CUDACC__
+
+__device__ __forceinline__ void record_error(int *err, int code, long long info) {
+    if (atomicCAS(err, 0, code) == 0) {
+        err[2] = (int)(info & 0xffffffff);
+        err[3] = (int)(info >> 32);
+    }
+}
+
+// (s, id) ordering
+__device__ __forceinline__ bool pair_less(float a, int ia, float b, int ib) {
+    return a < b || (a == b && ia < ib);
+}
+
+// FP64 sequential distances, one rounding per operation (matches the CPU
+// reference bit for bit).
+static __device__ __noinline__ double dist64_rows(const float *x, const float *y, int d, int metric) {
+    double s = 0.0;
+    if (metric == 0) {
+        for (int i = 0; i < d; ++i) {
+            double t = __dsub_rn((double)x[i], (double)y[i]);
+            s = __dadd_rn(s, __dmul_rn(t, t));
+        }
+        return s;
+    }
+    for (int i = 0; i < d; ++i) s = __dadd_rn(s, __dmul_rn((double)x[i], (double)y[i]));
+    s = __dsub_rn(2.0, __dmul_rn(2.0, s));
+    return s < 0.0 ? 0.0 : s;
+}
+
+// FP64 angle clause: (suw + svw) - suv < (2 cos a) * sqrt(suw * svw)
+__device__ __forceinline__ bool angle_exceeds64(double suw, double svw, double suv, double ca) {
+    double lhs = __dsub_rn(__dadd_rn(suw, svw), suv);
+    double rhs = __dmul_rn(__dmul_rn(2.0, ca), __dsqrt_rn(__dmul_rn(suw, svw)));
+    return lhs < rhs;
+}
+
+// Three-valued FP32 decision of a < b given error bounds: 1 true, 0 false,
+// -1 undecided.
+__device__ __forceinline__ int less_certain(float a, float ea, float b, float eb) {
+    if (a + ea < b - eb) return 1;
+    if (a - ea >= b + eb) return 0;
+    return -1;
+}
+
+// Three-valued FP32 angle clause with interval arithmetic over the
+// distance errors; FP32 rounding of the formula itself is covered by a
+// relative slack of 8 ulps on every term.
+__device__ __forceinline__ int angle_certain(float suw, float euw, float svw, float evw, float suv,
+                                             float euv, float ca) {
+    const float slack = 8.f * 5.9604645e-8f;
+    float sum = suw + svw + suv;
+    float lhs = (suw + svw) - suv;
+    float elhs = euw + evw + euv + slack * sum;
+    float lo_a = fmaxf(suw - euw, 0.f), hi_a = suw + euw;
+    float lo_b = fmaxf(svw - evw, 0.f), hi_b = svw + evw;
+    float sq_lo = sqrtf(lo_a * lo_b), sq_hi = sqrtf(hi_a * hi_b);
+    float two_c = 2.f * ca;
+    float r1 = two_c * sq_lo, r2 = two_c * sq_hi;
+    float rlo = fminf(r1, r2), rhi = fmaxf(r1, r2);
+    float erhs = slack * (fabsf(rhi) + sum);
+    if (lhs + elhs < rlo - erhs) return 1;
+    if (lhs - elhs >= rhi + erhs) return 0;
+    return -1;
+}
+
+__device__ __forceinline__ float warp_sum8(float v) {
+    v += __shfl_xor_sync(0xffffffffu, v, 4);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    return v;
+}
+
+// Team-of-8 FP32 distance between a point held in registers/shared (q)
+// and a row of D: lane li of the team owns float4 chunks li, li+8, ...
+// Returns the full distance on every lane of the team.
+__device__ __forceinline__ float team8_dist(const float4 *__restrict__ qrow,
+                                            const float4 *__restrict__ xrow, int nch, int li,
+                                            int metric) {
+    float acc = 0.f;
+    if (metric == 0) {
+        for (int c = li; c < nch; c += 8) {
+            float4 a = qrow[c];
+            float4 b = __ldg(xrow + c);
+            float t0 = a.x - b.x, t1 = a.y - b.y, t2 = a.z - b.z, t3 = a.w - b.w;
+            acc = fmaf(t0, t0, acc);
+            acc = fmaf(t1, t1, acc);
+            acc = fmaf(t2, t2, acc);
+            acc = fmaf(t3, t3, acc);
+        }
+        return warp_sum8(acc);
+    }
+    for (int c = li; c < nch; c += 8) {
+        float4 a = qrow[c];
+        float4 b = __ldg(xrow + c);
+        acc = fmaf(a.x, b.x, acc);
+        acc = fmaf(a.y, b.y, acc);
+        acc = fmaf(a.z, b.z, acc);
+        acc = fmaf(a.w, b.w, acc);
+    }
+    acc = warp_sum8(acc);
+    return fmaxf(2.f - 2.f * acc, 0.f);
+}
+
+// In-shared-memory bitonic sort of n (power of two) (key, id) pairs by one
+// warp, ascending by (key, id).
+__device__ __forceinline__ void warp_bitonic_sort(float *key, int *id, int n) {
+    const int lane = threadIdx.x & 31;
+    for (int k = 2; k <= n; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = lane; i < n; i += 32) {
+                int p = i ^ j;
+                if (p > i) {
+                    bool up = (i & k) == 0;
+                    float a = key[i], b = key[p];
+                    int ia = id[i], ib = id[p];
+                    bool swap = up ? pair_less(b, ib, a, ia) : pair_less(a, ia, b, ib);
+                    if (swap) {
+                        key[i] = b; key[p] = a;
+                        id[i] = ib; id[p] = ia;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// Register bitonic sort of one (key, id) per lane across the warp.
+__device__ __forceinline__ void warp_sort32(float &key, int &id) {
+    const int lane = threadIdx.x & 31;
+    for (int k = 2; k <= 32; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            float ok = __shfl_xor_sync(0xffffffffu, key, j);
+            int oi = __shfl_xor_sync(0xffffffffu, id, j);
+            bool lower = (lane & j) == 0;
+            bool up = (lane & k) == 0;
+            bool other_less = pair_less(ok, oi, key, id);
+            bool take_other = (lower == up) ? other_less : pair_less(key, id, ok, oi);
+            if (take_other) {
+                key = ok;
+                id = oi;
+            }
+        }
+    }
+}
+
+#endif  // __CUDACC__

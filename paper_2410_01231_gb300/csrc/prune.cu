@@ -1,0 +1,552 @@
+// prune.cu -- alpha-pruning (Section 4.1 rule in the scan of Prune,
+// Algorithm 3) and the reverse-edge union (Algorithm 2 lines 7-8,
+// Algorithm 5 lines 3-4).
+//
+// One warp prunes one point u.  Candidate distances s(u,v) are computed by
+// four teams of eight lanes (128-bit loads), the row is sorted by (s, id)
+// in shared memory, repeated ids are dropped, and near-tie runs are
+// re-ordered by their FP64 distance.  The scan then tests each candidate v
+// against the kept set four kept points at a time (one per team), stopping
+// at the first occluder; every comparison inside its FP32 error bound is
+// re-decided in FP64 with the CPU reference's summation order.
+// Rows longer than the shared-memory capacity of the warp kernel go to a
+// one-warp-per-CTA kernel with a large dynamic buffer.
+#include <climits>
+#include <cmath>
+
+#include "pg_internal.cuh"
+
+namespace {
+
+constexpr int PW = 8;            // warps per CTA (fast kernel)
+constexpr int CMAX = 256;        // candidates per row, fast kernel
+constexpr int CMAX_LONG = 8192;  // candidates per row, long-row kernel
+constexpr int RMAX = 64;
+
+struct PruneParams {
+    const float *D;
+    int64_t n;
+    int d;
+    int metric;
+    const int64_t *off;
+    const int32_t *cand;
+    int R;
+    double cos_a;
+    float cos_af;
+    int alpha60;
+    int exact;
+    ErrModel em;
+    int32_t *nbr;
+    int32_t *deg;
+    int *err;
+    unsigned long long *counters;
+    int *long_list;      // rows deferred to the long-row kernel
+    int *long_count;
+    int *row_counter;    // dynamic row fetch
+    int cap;             // capacity of this kernel
+};
+
+// shared layout of one warp: cs[cap], ci[cap], runid[cap], c64[cap],
+// kid[RMAX], ks[RMAX], kpos[RMAX], uq[d]
+__host__ __device__ inline size_t warp_smem_bytes(int cap, int d) {
+    return (size_t)cap * (4 + 4 + 4 + 8) + RMAX * (4 + 4 + 4) + (size_t)d * 4 + 64;
+}
+
+struct RowStats {
+    unsigned long long cands = 0, scanned = 0, tests = 0, rechecks = 0, flips = 0, edges = 0;
+};
+
+__device__ void prune_row(const PruneParams &P, int64_t u, const int32_t *cand, int64_t cnt,
+                          unsigned char *wsmem, RowStats &st) {
+    const int lane = threadIdx.x & 31, team = lane >> 3, li = lane & 7;
+    const int cap = P.cap;
+    double *c64 = reinterpret_cast<double *>(wsmem);
+    float *cs = reinterpret_cast<float *>(c64 + cap);
+    int *ci = reinterpret_cast<int *>(cs + cap);
+    int *runid = ci + cap;
+    int *kid = runid + cap;
+    float *ks = reinterpret_cast<float *>(kid + RMAX);
+    int *kpos = reinterpret_cast<int *>(ks + RMAX);
+    float *uq = reinterpret_cast<float *>(kpos + RMAX);
+    const int d = P.d, nch = d / 4;
+    const float *D = P.D;
+
+    for (int c = lane; c < nch; c += 32)
+        reinterpret_cast<float4 *>(uq)[c] = __ldg(reinterpret_cast<const float4 *>(D + u * d) + c);
+    __syncwarp();
+
+    // 1. s(u, v) for every candidate; invalid entries sort last
+    for (int64_t base = 0; base < cnt; base += 4) {
+        int64_t j = base + team;
+        int v = j < cnt ? cand[j] : -1;
+        bool ok = v >= 0 && v != u && v < P.n;
+        if (j < cnt && v >= P.n) record_error(P.err, DERR_BAD_ID, u);
+        int row = ok ? v : (int)u;
+        float s = team8_dist(reinterpret_cast<const float4 *>(uq),
+                             reinterpret_cast<const float4 *>(D + (int64_t)row * d), nch, li,
+                             P.metric);
+        if (li == 0 && j < cnt) {
+            cs[j] = ok ? s : INFINITY;
+            ci[j] = ok ? v : INT_MAX;
+        }
+    }
+    int P2 = 32;
+    while (P2 < cnt) P2 <<= 1;
+    for (int j = (int)cnt + lane; j < P2; j += 32) {
+        cs[j] = INFINITY;
+        ci[j] = INT_MAX;
+    }
+    __syncwarp();
+    warp_bitonic_sort(cs, ci, P2);
+
+    // 2. drop repeated ids (adjacent after the sort) and invalid entries
+    int m = 0;
+    for (int base = 0; base < P2; base += 32) {
+        int j = base + lane;
+        float s = cs[j];
+        int id = ci[j];
+        bool keep = id != INT_MAX && (j == 0 || ci[j - 1] != id);
+        unsigned bal = __ballot_sync(0xffffffffu, keep);
+        __syncwarp();
+        if (keep) {
+            int dst = m + __popc(bal & ((1u << lane) - 1));
+            cs[dst] = s;
+            ci[dst] = id;
+        }
+        m += __popc(bal);
+        __syncwarp();
+    }
+    st.cands += m;
+
+    // 3. near-tie runs: FP64 distances and re-order within each run
+    for (int j = lane; j < m; j += 32) {
+        runid[j] = j;
+        c64[j] = __longlong_as_double(0x7ff8000000000000ll);  // NaN: not computed
+    }
+    __syncwarp();
+    if (!P.exact) {
+        bool any = false;
+        for (int j = 1 + lane; j < m; j += 32) {
+            float a = cs[j - 1], b = cs[j];
+            int c = less_certain(a, P.em.err(a), b, P.em.err(b));
+            if (c != 1) any = true;
+        }
+        if (__any_sync(0xffffffffu, any)) {
+            if (lane == 0) {
+                for (int j = 1; j < m; ++j) {
+                    float a = cs[j - 1], b = cs[j];
+                    if (less_certain(a, P.em.err(a), b, P.em.err(b)) != 1) runid[j] = runid[j - 1];
+                }
+            }
+            __syncwarp();
+            for (int j = lane; j < m; j += 32) {
+                bool inrun = (j > 0 && runid[j] == runid[j - 1]) || (j + 1 < m && runid[j + 1] == j);
+                if (inrun) c64[j] = dist64_rows(uq, D + (int64_t)ci[j] * d, d, P.metric);
+            }
+            __syncwarp();
+            if (lane == 0) {
+                int j = 0;
+                while (j < m) {
+                    int e = j;
+                    while (e + 1 < m && runid[e + 1] == runid[j]) ++e;
+                    for (int a = j + 1; a <= e; ++a) {  // insertion sort by (c64, id)
+                        double kd = c64[a];
+                        int kidv = ci[a];
+                        float kf = cs[a];
+                        int b = a - 1;
+                        while (b >= j && (c64[b] > kd || (c64[b] == kd && ci[b] > kidv))) {
+                            c64[b + 1] = c64[b];
+                            ci[b + 1] = ci[b];
+                            cs[b + 1] = cs[b];
+                            --b;
+                        }
+                        c64[b + 1] = kd;
+                        ci[b + 1] = kidv;
+                        cs[b + 1] = kf;
+                    }
+                    st.rechecks += (e > j) ? (unsigned long long)(e - j + 1) : 0ull;
+                    j = e + 1;
+                }
+            }
+            __syncwarp();
+        }
+    }
+
+    // 4. the scan
+    int kept = 0;
+    int j = 0;
+    for (; j < m && kept < P.R; ++j) {
+        const int v = ci[j];
+        const float suv = cs[j];
+        const float euv = P.em.err(suv);
+        const float *xv = D + (int64_t)v * d;
+        bool occluded = false;
+        for (int kb = 0; kb < kept && !occluded; kb += 4) {
+            const int t = kb + team;
+            const bool active = t < kept;
+            const int w = active ? kid[t] : v;
+            const float svw = team8_dist(reinterpret_cast<const float4 *>(xv),
+                                         reinterpret_cast<const float4 *>(D + (int64_t)w * d),
+                                         nch, li, P.metric);
+            bool occ = false;
+            if (active && li == 0) {
+                const int wpos = kpos[t];
+                const float suw = ks[t];
+                bool c1;
+                if (P.exact) c1 = suw < suv;
+                else if (runid[wpos] != runid[j]) c1 = true;  // separated by a certain gap
+                else c1 = c64[wpos] < c64[j];
+                if (c1) {
+                    st.tests++;
+                    const float evw = P.em.err(svw);
+                    int c2 = P.exact ? (svw < suv) : less_certain(svw, evw, suv, euv);
+                    double s64vw = -1.0, s64uv = c64[j], s64uw = c64[wpos];
+                    if (c2 < 0) {
+                        s64vw = dist64_rows(xv, D + (int64_t)w * d, d, P.metric);
+                        if (!(s64uv == s64uv)) s64uv = dist64_rows(uq, xv, d, P.metric);
+                        c2 = s64vw < s64uv;
+                        st.rechecks++;
+                        if ((c2 != 0) != (svw < suv)) st.flips++;
+                    }
+                    if (c2) {
+                        int c3 = 1;
+                        if (!P.alpha60) {
+                            c3 = angle_certain(suw, P.em.err(suw), svw, evw, suv, euv, P.cos_af);
+                            if (c3 < 0) {
+                                if (s64vw < 0.0) s64vw = dist64_rows(xv, D + (int64_t)w * d, d, P.metric);
+                                if (!(s64uv == s64uv)) s64uv = dist64_rows(uq, xv, d, P.metric);
+                                if (!(s64uw == s64uw))
+                                    s64uw = dist64_rows(uq, D + (int64_t)w * d, d, P.metric);
+                                c3 = angle_exceeds64(s64uw, s64vw, s64uv, P.cos_a);
+                                st.rechecks++;
+                                bool naive = ((suw + svw) - suv) < 2.f * P.cos_af * sqrtf(suw * svw);
+                                if ((c3 != 0) != naive) st.flips++;
+                            }
+                        }
+                        occ = c3 != 0;
+                    }
+                }
+            }
+            occluded = __any_sync(0xffffffffu, occ);
+        }
+        if (!occluded) {
+            if (lane == 0) {
+                kid[kept] = v;
+                ks[kept] = suv;
+                kpos[kept] = j;
+            }
+            ++kept;
+            __syncwarp();
+        }
+    }
+    st.scanned += j;
+    st.edges += kept;
+    for (int t = lane; t < P.R; t += 32) P.nbr[u * P.R + t] = t < kept ? kid[t] : -1;
+    if (lane == 0) P.deg[u] = kept;
+    __syncwarp();
+}
+
+__device__ void flush_stats(const PruneParams &P, RowStats &st, unsigned long long rows, bool lng) {
+    const int lane = threadIdx.x & 31;
+    // per-lane counters (tests/rechecks/flips live on team leaders)
+    unsigned long long v[5] = {st.tests, st.rechecks, st.flips, 0, 0};
+    for (int k = 0; k < 3; ++k)
+        for (int o = 16; o; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    if (lane == 0) {
+        atomicAdd(P.counters + CNT_ROWS, rows);
+        atomicAdd(P.counters + CNT_CANDS, st.cands);
+        atomicAdd(P.counters + CNT_SCANNED, st.scanned);
+        atomicAdd(P.counters + CNT_OCCL, v[0]);
+        atomicAdd(P.counters + CNT_RECHECK, v[1]);
+        atomicAdd(P.counters + CNT_FLIP, v[2]);
+        atomicAdd(P.counters + CNT_EDGES, st.edges);
+        if (lng) atomicAdd(P.counters + CNT_LONG, rows);
+    }
+}
+
+__global__ void __launch_bounds__(PW * 32) k_prune(PruneParams P) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned char *ws = smem + (size_t)wid * warp_smem_bytes(CMAX, P.d);
+    RowStats st;
+    unsigned long long rows = 0;
+    for (;;) {
+        int64_t u = 0;
+        if (lane == 0) u = atomicAdd(P.row_counter, 1);
+        u = __shfl_sync(0xffffffffu, u, 0);
+        if (u >= P.n) break;
+        int64_t a = P.off[u], b = P.off[u + 1];
+        if (b < a) {
+            if (lane == 0) {
+                record_error(P.err, DERR_BAD_ID, u);
+                P.deg[u] = 0;
+            }
+            for (int t = lane; t < P.R; t += 32) P.nbr[u * P.R + t] = -1;
+            continue;
+        }
+        if (b - a > CMAX) {
+            if (lane == 0) {
+                int slot = atomicAdd(P.long_count, 1);
+                P.long_list[slot] = (int)u;
+            }
+            continue;
+        }
+        prune_row(P, u, P.cand + a, b - a, ws, st);
+        ++rows;
+    }
+    flush_stats(P, st, rows, false);
+}
+
+__global__ void __launch_bounds__(32) k_prune_long(PruneParams P) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    RowStats st;
+    unsigned long long rows = 0;
+    const int total = *P.long_count;
+    for (int i = blockIdx.x; i < total; i += gridDim.x) {
+        int64_t u = P.long_list[i];
+        int64_t a = P.off[u], b = P.off[u + 1];
+        if (b - a > CMAX_LONG) {
+            if (lane == 0) {
+                record_error(P.err, DERR_CAPACITY, u);
+                P.deg[u] = 0;
+            }
+            for (int t = lane; t < P.R; t += 32) P.nbr[u * P.R + t] = -1;
+            continue;
+        }
+        prune_row(P, u, P.cand + a, b - a, smem, st);
+        ++rows;
+    }
+    flush_stats(P, st, rows, true);
+}
+
+// ---------------------------------------------------------- prefix scan
+__global__ void k_scan_blocks(const int32_t *in, int64_t n, int64_t *out, int64_t *blk_sum) {
+    __shared__ int64_t s[1024];
+    int64_t i = (int64_t)blockIdx.x * 1024 + threadIdx.x;
+    int64_t v = i < n ? in[i] : 0;
+    s[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        int64_t t = threadIdx.x >= o ? s[threadIdx.x - o] : 0;
+        __syncthreads();
+        s[threadIdx.x] += t;
+        __syncthreads();
+    }
+    if (i < n) out[i] = s[threadIdx.x] - v;  // exclusive within block
+    if (threadIdx.x == 1023) blk_sum[blockIdx.x] = s[1023];
+}
+
+__global__ void k_scan_sums(int64_t *blk_sum, int64_t nb) {
+    // single thread: block counts are small (n / 1024)
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        int64_t run = 0;
+        for (int64_t b = 0; b < nb; ++b) {
+            int64_t t = blk_sum[b];
+            blk_sum[b] = run;
+            run += t;
+        }
+        blk_sum[nb] = run;
+    }
+}
+
+__global__ void k_scan_add(int64_t *out, int64_t n, const int64_t *blk_sum, int64_t nb) {
+    int64_t i = (int64_t)blockIdx.x * 1024 + threadIdx.x;
+    if (i < n) out[i] += blk_sum[i / 1024];
+    if (i == 0) out[n] = blk_sum[nb];
+}
+
+// ------------------------------------------------------- reverse union
+__global__ void k_union_count(const int32_t *nbr, const int32_t *deg, int64_t n, int R, int32_t *cnt,
+                              int *err) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    int dv = deg[v];
+    if (dv < 0 || dv > R) {
+        record_error(err, DERR_BAD_ID, v);
+        return;
+    }
+    atomicAdd(&cnt[v], dv);
+    for (int j = 0; j < dv; ++j) {
+        int w = nbr[v * R + j];
+        if (w < 0 || w >= n) {
+            record_error(err, DERR_BAD_ID, v);
+            continue;
+        }
+        atomicAdd(&cnt[w], 1);
+    }
+}
+
+__global__ void k_union_own(const int32_t *nbr, const int32_t *deg, int64_t n, int R,
+                            const int64_t *off, int32_t *ids, int64_t *cursor) {
+    int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= n) return;
+    int du = deg[u];
+    if (du < 0 || du > R) du = 0;
+    int64_t o = off[u];
+    for (int j = 0; j < du; ++j) ids[o + j] = nbr[u * R + j];
+    cursor[u] = o + du;
+}
+
+__global__ void k_union_scatter(const int32_t *nbr, const int32_t *deg, int64_t n, int R,
+                                int32_t *ids, unsigned long long *cursor) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    int dv = deg[v];
+    if (dv < 0 || dv > R) return;
+    for (int j = 0; j < dv; ++j) {
+        int w = nbr[v * R + j];
+        if (w < 0 || w >= n) continue;
+        unsigned long long pos = atomicAdd(&cursor[w], 1ull);
+        ids[pos] = (int32_t)v;
+    }
+}
+
+}  // namespace
+
+pg_status pg_scan_counts(pg_ctx *ctx, const int32_t *cnt, int64_t n, int64_t *off) {
+    int64_t nb = (n + 1023) / 1024;
+    Scratch<int64_t> bs;
+    PG_TRY(bs.alloc(ctx, (size_t)nb + 1));
+    if (nb > 0) {
+        k_scan_blocks<<<(unsigned)nb, 1024, 0, ctx->stream>>>(cnt, n, off, bs.p);
+        PG_LAUNCHED(ctx);
+    }
+    k_scan_sums<<<1, 32, 0, ctx->stream>>>(bs.p, nb);
+    PG_LAUNCHED(ctx);
+    k_scan_add<<<(unsigned)(nb > 0 ? nb : 1), 1024, 0, ctx->stream>>>(off, n, bs.p, nb);
+    PG_LAUNCHED(ctx);
+    return PG_OK;
+}
+
+pg_status pg_reverse_union_internal(pg_ctx *ctx, const int32_t *nbr, const int32_t *deg, int64_t n,
+                                    int32_t R, int64_t *off, int32_t *ids) {
+    Scratch<int32_t> cnt;
+    PG_TRY(cnt.alloc(ctx, (size_t)n));
+    PG_TRY_CUDA(ctx, cudaMemsetAsync(cnt.p, 0, (size_t)n * 4, ctx->stream));
+    unsigned g = (unsigned)((n + 255) / 256);
+    k_union_count<<<g, 256, 0, ctx->stream>>>(nbr, deg, n, R, cnt.p, ctx->d_err);
+    PG_LAUNCHED(ctx);
+    PG_TRY(pg_scan_counts(ctx, cnt.p, n, off));
+    Scratch<int64_t> cursor;
+    PG_TRY(cursor.alloc(ctx, (size_t)n));
+    k_union_own<<<g, 256, 0, ctx->stream>>>(nbr, deg, n, R, off, ids, cursor.p);
+    PG_LAUNCHED(ctx);
+    pg_timer_begin(ctx, TM_UNION);
+    k_union_scatter<<<g, 256, 0, ctx->stream>>>(nbr, deg, n, R, ids,
+                                                reinterpret_cast<unsigned long long *>(cursor.p));
+    PG_LAUNCHED(ctx);
+    pg_timer_end(ctx, TM_UNION);
+    return PG_OK;
+}
+
+pg_status pg_prune_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
+                            const int64_t *off, const int32_t *cand, int32_t R, double alpha_deg,
+                            const DataFacts &facts, int32_t *nbr, int32_t *deg) {
+    PruneParams P;
+    P.D = D;
+    P.n = n;
+    P.d = d;
+    P.metric = metric == PG_METRIC_L2SQ ? 0 : 1;
+    P.off = off;
+    P.cand = cand;
+    P.R = R;
+    P.cos_a = std::cos(alpha_deg * M_PI / 180.0);
+    P.cos_af = (float)P.cos_a;
+    P.alpha60 = alpha_deg == 60.0;
+    P.exact = facts.exact;
+    P.em = pg_err_model(metric, d, facts, false);
+    P.nbr = nbr;
+    P.deg = deg;
+    P.err = ctx->d_err;
+    P.counters = ctx->d_counters;
+    Scratch<int> ints;
+    PG_TRY(ints.alloc(ctx, (size_t)n + 4));
+    PG_TRY_CUDA(ctx, cudaMemsetAsync(ints.p, 0, 4 * sizeof(int), ctx->stream));
+    P.row_counter = ints.p;
+    P.long_count = ints.p + 1;
+    P.long_list = ints.p + 4;
+    P.cap = CMAX;
+    size_t smem = warp_smem_bytes(CMAX, d) * PW;
+    PG_TRY_CUDA(ctx, cudaFuncSetAttribute(k_prune, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem));
+    int blocks_per_sm = 0;
+    PG_TRY_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_prune, PW * 32,
+                                                                   smem));
+    if (blocks_per_sm < 1) blocks_per_sm = 1;
+    pg_timer_begin(ctx, TM_PRUNE);
+    k_prune<<<ctx->num_sms * blocks_per_sm, PW * 32, smem, ctx->stream>>>(P);
+    PG_LAUNCHED(ctx);
+    pg_timer_end(ctx, TM_PRUNE);
+    P.cap = CMAX_LONG;
+    size_t smem_long = warp_smem_bytes(CMAX_LONG, d);
+    PG_TRY_CUDA(ctx, cudaFuncSetAttribute(k_prune_long,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem_long));
+    pg_timer_begin(ctx, TM_PRUNE);
+    k_prune_long<<<ctx->num_sms, 32, smem_long, ctx->stream>>>(P);
+    PG_LAUNCHED(ctx);
+    pg_timer_end(ctx, TM_PRUNE);
+    return PG_OK;
+}
+
+static pg_status check_common(pg_ctx *ctx, const float *D, int64_t n, int32_t d) {
+    if (!ctx) return PG_ERR_INVALID_ARG;
+    if (!D) return pg_fail(ctx, PG_ERR_INVALID_ARG, "null D");
+    if (n < 1 || n >= INT_MAX) return pg_fail(ctx, PG_ERR_INVALID_ARG, "need 1 <= n < 2^31");
+    if (d < 4 || d % 4 || d > 8192)
+        return pg_fail(ctx, PG_ERR_INVALID_ARG, "need d % 4 == 0 and 4 <= d <= 8192");
+    return PG_OK;
+}
+
+extern "C" pg_status pg_prune(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
+                              const int64_t *cand_off, const int32_t *cand_ids, int32_t R,
+                              double alpha_deg, pg_precision precision, int32_t *nbr,
+                              int32_t *deg, pg_prune_stats *host_stats) {
+    PG_TRY(check_common(ctx, D, n, d));
+    (void)precision;
+    if (!cand_off || !cand_ids || !nbr || !deg)
+        return pg_fail(ctx, PG_ERR_INVALID_ARG, "null pointer");
+    if (R < 1 || R > RMAX) return pg_fail(ctx, PG_ERR_INVALID_ARG, "need 1 <= R <= %d", RMAX);
+    if (!(alpha_deg >= 0.0 && alpha_deg <= 180.0))
+        return pg_fail(ctx, PG_ERR_INVALID_ARG, "need 0 <= alpha <= 180");
+    DataFacts facts;
+    PG_TRY(pg_data_facts(ctx, D, n, d, metric, &facts));
+    if (host_stats) PG_TRY(pg_reset_counters(ctx));
+    PG_TRY(pg_prune_internal(ctx, D, n, d, metric, cand_off, cand_ids, R, alpha_deg, facts, nbr,
+                             deg));
+    if (host_stats) {
+        unsigned long long c[PG_CNT_SLOTS];
+        PG_TRY(pg_read_counters(ctx, c));
+        host_stats->rows = (int64_t)c[CNT_ROWS];
+        host_stats->candidates = (int64_t)c[CNT_CANDS];
+        host_stats->scanned = (int64_t)c[CNT_SCANNED];
+        host_stats->occlusion_tests = (int64_t)c[CNT_OCCL];
+        host_stats->fp64_rechecks = (int64_t)c[CNT_RECHECK];
+        host_stats->fp64_flips = (int64_t)c[CNT_FLIP];
+        host_stats->edges = (int64_t)c[CNT_EDGES];
+        host_stats->long_rows = (int64_t)c[CNT_LONG];
+        return PG_OK;
+    }
+    return pg_sync_check(ctx, "pg_prune");
+}
+
+extern "C" pg_status pg_reverse_union(pg_ctx *ctx, const int32_t *nbr, const int32_t *deg,
+                                      int64_t n, int32_t R, int64_t *off, int32_t *ids,
+                                      int64_t ids_capacity, int64_t *host_total) {
+    if (!ctx) return PG_ERR_INVALID_ARG;
+    if (!nbr || !deg || !off || !ids) return pg_fail(ctx, PG_ERR_INVALID_ARG, "null pointer");
+    if (n < 1 || n >= INT_MAX || R < 1 || R > RMAX)
+        return pg_fail(ctx, PG_ERR_INVALID_ARG, "need 1 <= n < 2^31 and 1 <= R <= %d", RMAX);
+    if (ids_capacity < 2 * n * (int64_t)R)
+        return pg_fail(ctx, PG_ERR_INVALID_ARG, "ids capacity must be >= 2*n*R");
+    PG_TRY(pg_reverse_union_internal(ctx, nbr, deg, n, R, off, ids));
+    if (host_total) {
+        PG_TRY_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned, off + n, sizeof(int64_t),
+                                         cudaMemcpyDeviceToHost, ctx->stream));
+        PG_TRY(pg_sync_check(ctx, "pg_reverse_union"));
+        memcpy(host_total, ctx->h_pinned, sizeof(int64_t));
+        return PG_OK;
+    }
+    return pg_sync_check(ctx, "pg_reverse_union");
+}
