@@ -54,6 +54,7 @@ extern "C" pg_status pg_ctx_create(void *cuda_stream, size_t hbm_budget_bytes, p
         e = cudaMalloc(&ctx->d_counters, PG_CNT_SLOTS * sizeof(unsigned long long));
     if (e == cudaSuccess)
         e = cudaMallocHost(&ctx->h_pinned, PG_CNT_SLOTS * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_err, 4 * sizeof(int));
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_err, 0, 4 * sizeof(int), ctx->stream);
     if (e == cudaSuccess)
         e = cudaMemsetAsync(ctx->d_counters, 0, PG_CNT_SLOTS * sizeof(unsigned long long),
@@ -145,6 +146,7 @@ extern "C" void pg_ctx_destroy(pg_ctx *ctx) {
     if (ctx->d_err) cudaFree(ctx->d_err);
     if (ctx->d_counters) cudaFree(ctx->d_counters);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+    if (ctx->h_err) cudaFreeHost(ctx->h_err);
     delete ctx;
 }
 
@@ -175,11 +177,11 @@ void pg_free(pg_ctx *ctx, void *p, size_t bytes) {
 }
 
 pg_status pg_sync_check(pg_ctx *ctx, const char *where) {
-    PG_TRY_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned, ctx->d_err, 4 * sizeof(int),
+    PG_TRY_CUDA(ctx, cudaMemcpyAsync(ctx->h_err, ctx->d_err, 4 * sizeof(int),
                                      cudaMemcpyDeviceToHost, ctx->stream));
     PG_TRY_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     int err[4];
-    memcpy(err, ctx->h_pinned, sizeof err);
+    memcpy(err, ctx->h_err, sizeof err);
     if (err[0] != DERR_NONE) {
         long long info = (long long)(unsigned)err[2] | ((long long)err[3] << 32);
         PG_TRY_CUDA(ctx, cudaMemsetAsync(ctx->d_err, 0, 4 * sizeof(int), ctx->stream));

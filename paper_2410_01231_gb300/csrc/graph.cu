@@ -349,7 +349,12 @@ pg_status pg_connect_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
     const bool recheck = !facts.exact;
     size_t smem = (size_t)d * 4;
     int grid = ctx->num_sms * 8;
-    for (;;) {
+    // every round links one component, so at most n rounds can be needed
+    const int64_t max_batches = n / 16 + 2;
+    for (int64_t batch = 0;; ++batch) {
+        if (batch > max_batches)
+            return pg_fail(ctx, PG_ERR_INTERNAL, "connect: no progress after %lld rounds",
+                           (long long)(batch * 16));
         for (int round = 0; round < 16; ++round) {
             k_connect_argmin<<<grid, 256, smem, ctx->stream>>>(D, n, d, m, reached.p, deg, R, st.p);
             PG_LAUNCHED(ctx);

@@ -323,9 +323,13 @@ __global__ void k_knn_fix(const float *__restrict__ Q, const float *__restrict__
         if (unresolved) atomicAdd(counters + CNT_KNN_UNRESOLVED, unresolved);
     }
     __syncwarp();
+    // the norm form loses relative accuracy to cancellation: report every
+    // kept distance as the rounded FP64 value
     for (int t = lane; t < K; t += 32) {
-        out_i[q * K + t] = ri[t];
-        out_s[q * K + t] = rs[t];
+        int id = ri[t];
+        out_i[q * K + t] = id;
+        out_s[q * K + t] = id >= 0 ? (float)dist64_rows(qrow, X + (int64_t)id * d, d, metric)
+                                   : INFINITY;
     }
 }
 

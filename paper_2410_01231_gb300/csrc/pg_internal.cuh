@@ -23,6 +23,7 @@ struct pg_ctx {
     int *d_err = nullptr;                     // [4]: code, where, info lo, info hi
     unsigned long long *d_counters = nullptr;  // kernel statistics
     unsigned long long *h_pinned = nullptr;   // pinned host mirror for small reads
+    int *h_err = nullptr;                      // pinned mirror of the error word
     int64_t launches = 0;
     // optional CUDA-event timing of named kernels
     int timing = 0;

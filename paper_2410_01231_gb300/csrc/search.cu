@@ -120,9 +120,15 @@ __device__ void search_one(const SearchParams &P, int64_t qi, unsigned char *ws,
             cursor += 32;
         }
         if (cursor >= size) break;
+        // a node is expanded at most once, so n expansions bound any search
+        if (ex > (unsigned long long)P.n) {
+            if (lane == 0) record_error(P.err, DERR_INTERNAL, qi);
+            break;
+        }
         const int u = piA[cursor] & ID_MASK;
         __syncwarp();
         if (lane == 0) piA[cursor] |= EXP_BIT;
+        __syncwarp();
         ++ex;
         int row = u;
         if (P.rows) row = P.rows[u];

@@ -22,8 +22,8 @@ def test_header_declares_the_boundary():
 
 
 def test_library_exports_every_declared_symbol():
-    from paper_2410_01231_gb300 import _build
-    lib_path = _build.build()
+    import __graft_entry__
+    lib_path = __graft_entry__._build_module().build()
     lib = ctypes.CDLL(lib_path)
     missing = [s for s in declared_symbols() if not hasattr(lib, s)]
     assert not missing, missing

@@ -60,7 +60,7 @@ DATA = {
 # ----------------------------------------------------------------- kNN
 @pytest.mark.parametrize("kind", ["int", "float", "cosine"])
 def test_knn_matches_oracle(ctx, pg, kind):
-    D, metric = DATA[kind][0]()
+    D, metric = DATA[kind][0](), DATA[kind][1]
     K = 20
     gi, gd = pg.build_knn(ctx, dev(D), K, metric)
     oi, od = oracle.knn(D, K, metric)
@@ -100,7 +100,7 @@ def noisy_candidates(ids, n, seed):
 @pytest.mark.parametrize("kind", ["int", "float", "cosine"])
 @pytest.mark.parametrize("alpha", [60.0, 66.0, 90.0])
 def test_prune_bit_exact_given_identical_candidates(ctx, pg, kind, alpha):
-    D, metric = DATA[kind][0]()
+    D, metric = DATA[kind][0](), DATA[kind][1]
     ids, _ = oracle.knn(D, 40, metric)
     off, cand = noisy_candidates(ids, D.shape[0], 5)
     R = 16
@@ -153,14 +153,14 @@ def test_reverse_union_rows_are_the_same_sets(ctx, pg):
 
 @pytest.mark.parametrize("kind", ["int", "float", "cosine"])
 def test_medoid(ctx, pg, kind):
-    D, metric = DATA[kind][0]()
+    D, metric = DATA[kind][0](), DATA[kind][1]
     assert pg.medoid(ctx, dev(D), metric) == oracle.medoid(D, metric)
 
 
 # ------------------------------------------------------------- connect
 @pytest.mark.parametrize("kind", ["int", "float"])
 def test_connect_matches_oracle(ctx, pg, kind):
-    D, metric = DATA[kind][0]()
+    D, metric = DATA[kind][0](), DATA[kind][1]
     n = D.shape[0]
     ids, _ = oracle.knn(D, 10, metric)
     nbr, deg = oracle.prune(D, np.arange(n + 1, dtype=np.int64) * 10, ids.ravel(), 12, 60.0, metric)
@@ -250,9 +250,9 @@ def test_build_rng_c1_matches_oracle_and_recall(ctx, pg):
 
 def test_build_nswg_integer_matches_oracle(ctx, pg):
     D = int_points(4000)
-    p = dict(K=16, L=40, R=16, M=8, alpha_deg=70.0, iters=1, seed=5)
+    p = dict(K=16, L=40, R=16, M=16, alpha_deg=70.0, iters=1, seed=5)
     idx = pg.Index.build_nswg(ctx, dev(D), metric="l2", **p)
-    layers, ep, lev = oracle.build_nswg(D, 16, 40, 8, 16, 70.0, 60.0, 1, "l2", seed=5)
+    layers, ep, lev = oracle.build_nswg(D, 16, 40, 16, 16, 70.0, 60.0, 1, "l2", seed=5)
     info = idx.info()
     assert info["n_layers"] == len(layers) and info["ep_top"] == ep
     for i, lay in enumerate(layers):
