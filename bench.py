@@ -256,7 +256,10 @@ def run_ours(args):
     launches = ctx.launches - launches0
     ms = ev0.elapsed_time(ev1) / args.steps
     knn_ms, knn_launches = ctx.kernel_time("knn")
-    kt = {k: ctx.kernel_time(k) for k in ("knn", "prune", "union", "search", "medoid")}
+    knn_work = ctx.kernel_work("knn")
+    kt = {k: ctx.kernel_time(k) for k in ("knn", "prune", "union", "connect", "search", "medoid")}
+    conn_edges = ctx.counter("connect_edges")
+    conn_full = ctx.counter("connect_full_rounds")
     ctx.set_timing(False)
     if world > 1:
         t = torch.tensor([ms], device="cuda")
@@ -327,17 +330,16 @@ def run_ours(args):
     # -------------------------------------------------------- roofline
     pk = peaks()
     sm_mhz = (clk or {}).get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
-    knn_avg = knn_ms / max(1, knn_launches)
-    knn_flops = 2.0 * n * n * w["d"]
+    # algorithmic flops of every kNN launch in the timed region (base graph
+    # and routing layers) over their summed device time
+    achieved = knn_work / (knn_ms / 1e3) / 1e12 if knn_ms > 0 else 0.0
     if args.precision == "fp32":
         peak = fp32_simt_peak_tflops(pk.get("sm_max_mhz", 2070.0))
-        achieved = knn_flops / (knn_avg / 1e3) / 1e12
         roof = {"kernel": "k_knn_fp32", "bound": "alu", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (derived)"}
     else:
         peak = pk.get("bf16_tflops", 1900.0)
-        achieved = knn_flops / (knn_avg / 1e3) / 1e12
         roof = {"kernel": "knn_bf16", "bound": "tensor", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops (of measured)"}
@@ -345,7 +347,7 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
-        ns = min(n, 12000)
+        ns = min(n, 40000)
         v, sampled, _ = oracle_build_rate(D, w, ns)
         cpu = {"value": v, "unit": "points/s", "cores": oracle.num_threads(), "kind": "oracle",
                "sample": (f"oracle stages on the first {ns} points ({sampled:.1f} s of CPU work); "
@@ -364,6 +366,9 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (512 MB points)", "parallelism": "replicas"},
         "queries": qres, "phase_s": ph,
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
+        "kernel_launches_per_step": {k: v[1] / args.steps for k, v in kt.items()},
+        "connect_edges_per_step": conn_edges / max(1, args.steps + args.warmup),
+        "connect_full_rounds_per_step": conn_full / max(1, args.steps + args.warmup),
         "roofline": roof, "clocks": clk, "gpu_launches": launches, "e2e": e2e,
         "cpu_baseline": cpu,
     }

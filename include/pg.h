@@ -125,6 +125,14 @@ int64_t pg_ctx_launches(const pg_ctx *ctx);
  * synchronises the stream. */
 pg_status pg_ctx_set_timing(pg_ctx *ctx, int enable);
 pg_status pg_ctx_kernel_time(pg_ctx *ctx, const char *name, double *total_ms, int64_t *launches);
+/* Algorithmic work of the timed launches of `name` since the last reset:
+ * "knn" counts 2*d flops per (query row, point) pair. */
+pg_status pg_ctx_kernel_work(pg_ctx *ctx, const char *name, double *work);
+
+/* Cumulative host-side counters of this context: "connect_edges" (edges
+ * added by connectivity steps) and "connect_full_rounds" (connectivity
+ * rounds that needed a scan over all points). */
+pg_status pg_ctx_counter(pg_ctx *ctx, const char *name, int64_t *value);
 
 /* ------------------------------------------------------------------ steps */
 
@@ -221,20 +229,23 @@ pg_status pg_build_nswg(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
 
 #define PG_SEARCH_FLAT 1 /* ignore routing layers: start at the medoid */
 
-/* k-ANN queries on an index: greedy KANNSearch(G_i, q, 1, 1, w) from the
- * top layer down to layer 1, then KANNSearch(G_0, q, k, beam, w) (pattern
- * of Algorithm 4 lines 8-12); an index without upper layers (or with
- * PG_SEARCH_FLAT) starts at its medoid.  Q [nq][d] device; out [nq][k]. */
+/* k-ANN queries on an index: from the top layer down to layer 1,
+ * w <- first of KANNSearch(G_i, q, 1, upper_beam, w); then
+ * KANNSearch(G_0, q, k, beam, w) (pattern of Algorithm 4 lines 8-12, where
+ * upper_beam = 1 is the greedy routing of the paper); an index without
+ * upper layers (or with PG_SEARCH_FLAT) starts at its medoid.
+ * Q [nq][d] device; out [nq][k].  1 <= k <= beam <= 256,
+ * 1 <= upper_beam <= 256. */
 pg_status pg_search(pg_ctx *ctx, const pg_index *index, const float *Q, int64_t nq, int32_t k,
-                    int32_t beam, int32_t flags, pg_precision precision, int32_t *out_ids,
-                    float *out_dist);
+                    int32_t beam, int32_t upper_beam, int32_t flags, pg_precision precision,
+                    int32_t *out_ids, float *out_dist);
 
 /* Same as pg_search with HOST buffers (Q, out_ids, out_dist in host
  * memory, pinned or pageable): copies in, searches, copies out and
  * synchronises. */
 pg_status pg_search_host(pg_ctx *ctx, const pg_index *index, const float *Q, int64_t nq,
-                         int32_t k, int32_t beam, int32_t flags, pg_precision precision,
-                         int32_t *out_ids, float *out_dist);
+                         int32_t k, int32_t beam, int32_t upper_beam, int32_t flags,
+                         pg_precision precision, int32_t *out_ids, float *out_dist);
 
 void pg_index_destroy(pg_index *index);
 

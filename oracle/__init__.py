@@ -284,10 +284,11 @@ def build_nswg(D, K: int, L: int, M: int, R0: int, alpha_deg: float = 66.0,
     return layers, ep, lev
 
 
-def search_nswg(D, layers, ep: int, Q, k: int, ef: int, metric: str = "cosine"):
-    """Layered query: greedy KANNSearch(G_i, q, 1, 1, w) from the top layer
-    down to layer 1, then KANNSearch(G_0, q, k, ef, w) (pattern of
-    Algorithm 4 lines 8-12)."""
+def search_nswg(D, layers, ep: int, Q, k: int, ef: int, metric: str = "cosine",
+                ef_upper: int = 1):
+    """Layered query: w <- first of KANNSearch(G_i, q, 1, ef_upper, w) from
+    the top layer down to layer 1, then KANNSearch(G_0, q, k, ef, w)
+    (pattern of Algorithm 4 lines 8-12; ef_upper = 1 is greedy routing)."""
     D = _f32(D)
     Q = _f32(Q)
     n = D.shape[0]
@@ -297,7 +298,7 @@ def search_nswg(D, layers, ep: int, Q, k: int, ef: int, metric: str = "cosine"):
         lay = layers[i]
         rows = np.full(n, -1, np.int32)
         rows[lay.gid] = np.arange(lay.gid.shape[0], dtype=np.int32)
-        ids, _ = search(D, lay.nbr, lay.deg, Q, w, 1, 1, metric, rows=rows)
+        ids, _ = search(D, lay.nbr, lay.deg, Q, w, 1, ef_upper, metric, rows=rows)
         w = ids[:, 0].copy()
     base = layers[0]
     return search(D, base.nbr, base.deg, Q, w, k, ef, metric)

@@ -25,6 +25,10 @@ if not os.path.exists(_LIB_PATH):
 _lib = C.CDLL(_LIB_PATH)
 
 METRIC = {"l2": 0, "cosine": 1, "ip": 2}
+# pool width of the descent through the upper layers of a hierarchical index
+# (1 is the paper's greedy routing; 16 enters the query's cluster far more
+# reliably on well-separated data)
+UPPER_BEAM = 16
 PRECISION = {"fp32": 0, "bf16": 1}
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "TIMEOUT", 5: "CAPACITY", 6: "BUDGET",
           7: "INTERNAL", 8: "DEVICE_CHECK"}
@@ -68,8 +72,8 @@ _sig("pg_search_graph", C.c_int, [P, P, i64, i32, C.c_int, P, P, i32, P, P, i64,
                                   C.c_int, P, P])
 _sig("pg_build_rng", C.c_int, [P, P, i64, i32, P, P])
 _sig("pg_build_nswg", C.c_int, [P, P, i64, i32, P, P])
-_sig("pg_search", C.c_int, [P, P, P, i64, i32, i32, i32, C.c_int, P, P])
-_sig("pg_search_host", C.c_int, [P, P, P, i64, i32, i32, i32, C.c_int, P, P])
+_sig("pg_search", C.c_int, [P, P, P, i64, i32, i32, i32, i32, C.c_int, P, P])
+_sig("pg_search_host", C.c_int, [P, P, P, i64, i32, i32, i32, i32, C.c_int, P, P])
 _sig("pg_index_destroy", None, [P])
 _sig("pg_index_info", C.c_int, [P, P, P, P, P])
 _sig("pg_index_layer", C.c_int, [P, i32, P, P, P, P, P])
@@ -77,13 +81,16 @@ _sig("pg_index_phase_seconds", C.c_int, [P, P])
 _sig("pg_index_export_layer", C.c_int, [P, P, i32, P, P, P])
 _sig("pg_ctx_set_timing", C.c_int, [P, C.c_int])
 _sig("pg_ctx_kernel_time", C.c_int, [P, C.c_char_p, P, P])
+_sig("pg_ctx_counter", C.c_int, [P, C.c_char_p, P])
+_sig("pg_ctx_kernel_work", C.c_int, [P, C.c_char_p, P])
 
 EXPORTS = ["pg_default_params", "pg_ctx_create", "pg_ctx_destroy", "pg_last_error", "pg_ctx_sync",
            "pg_ctx_launches", "pg_build_knn", "pg_knn_query", "pg_prune", "pg_reverse_union",
            "pg_medoid", "pg_connect", "pg_acquire_candidates", "pg_search_graph", "pg_build_rng",
            "pg_build_nswg", "pg_search", "pg_search_host", "pg_index_destroy", "pg_index_info",
            "pg_index_layer", "pg_index_phase_seconds", "pg_index_export_layer",
-           "pg_ctx_set_timing", "pg_ctx_kernel_time"]
+           "pg_ctx_set_timing", "pg_ctx_kernel_time", "pg_ctx_counter",
+           "pg_ctx_kernel_work"]
 
 
 class PGError(RuntimeError):
@@ -138,6 +145,19 @@ class Context:
         self._check(_lib.pg_ctx_kernel_time(self._h, name.encode(), C.byref(ms), C.byref(cnt)),
                     "pg_ctx_kernel_time")
         return ms.value, cnt.value
+
+    def kernel_work(self, name: str) -> float:
+        """Algorithmic work (flops) of the timed launches of `name`."""
+        v = C.c_double()
+        self._check(_lib.pg_ctx_kernel_work(self._h, name.encode(), C.byref(v)),
+                    "pg_ctx_kernel_work")
+        return v.value
+
+    def counter(self, name: str) -> int:
+        """Cumulative counter: "connect_edges" or "connect_full_rounds"."""
+        v = C.c_int64()
+        self._check(_lib.pg_ctx_counter(self._h, name.encode(), C.byref(v)), "pg_ctx_counter")
+        return v.value
 
     def close(self):
         if getattr(self, "_h", None):
@@ -319,18 +339,21 @@ class Index:
         _lib.pg_index_phase_seconds(self._h, arr)
         return dict(zip(["knn", "prune", "union", "connect", "acquire", "layers"], list(arr)))
 
-    def search(self, Q: torch.Tensor, k: int, beam: int, flat: bool = False, precision="fp32"):
+    def search(self, Q: torch.Tensor, k: int, beam: int, upper_beam: int = UPPER_BEAM,
+               flat: bool = False, precision="fp32"):
+        """k-ANN queries; upper layers use pool width upper_beam (1 = greedy)."""
         Q = _dev(Q, torch.float32, "Q")
         nq = Q.shape[0]
         ids = torch.empty((nq, k), dtype=torch.int32, device=Q.device)
         dist = torch.empty((nq, k), dtype=torch.float32, device=Q.device)
         self.ctx._check(_lib.pg_search(self.ctx.handle, self._h, _ptr(Q), nq, k, beam,
-                                       1 if flat else 0, PRECISION[precision], _ptr(ids),
-                                       _ptr(dist)), "pg_search")
+                                       upper_beam, 1 if flat else 0, PRECISION[precision],
+                                       _ptr(ids), _ptr(dist)), "pg_search")
         return ids, dist
 
-    def search_host(self, Q: np.ndarray, k: int, beam: int, flat: bool = False,
-                    out_ids: np.ndarray | None = None, out_dist: np.ndarray | None = None):
+    def search_host(self, Q: np.ndarray, k: int, beam: int, upper_beam: int = UPPER_BEAM,
+                    flat: bool = False, out_ids: np.ndarray | None = None,
+                    out_dist: np.ndarray | None = None):
         """Host buffers in and out (copies inside the call)."""
         if not (isinstance(Q, np.ndarray) or isinstance(Q, torch.Tensor)):
             raise TypeError("Q must be a host array")
@@ -346,7 +369,8 @@ class Index:
             return a.ctypes.data_as(C.c_void_p)
 
         self.ctx._check(_lib.pg_search_host(self.ctx.handle, self._h, hp(Q), nq, k, beam,
-                                            1 if flat else 0, 0, hp(out_ids), hp(out_dist)),
+                                            upper_beam, 1 if flat else 0, 0, hp(out_ids),
+                                            hp(out_dist)),
                         "pg_search_host")
         return out_ids, out_dist
 

@@ -29,7 +29,8 @@ pg_status pg_medoid_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d, 
                              int64_t *host_ep);
 pg_status pg_connect_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
                               int32_t *nbr, int32_t *deg, int32_t R, int64_t ep,
-                              const DataFacts &facts, int64_t *host_added);
+                              const DataFacts &facts, const int32_t *knn, int32_t K,
+                              int64_t *host_added);
 pg_status pg_search_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
                              const int32_t *nbr, const int32_t *deg, int32_t R,
                              const int32_t *rows, const float *Q, int64_t nq,
@@ -229,7 +230,8 @@ pg_status iter_nsg(pg_ctx *ctx, const float *X, int64_t m, int32_t d, const pg_b
                                  deg));
         if (do_connect) {
             clk.start(PH_CONNECT);
-            PG_TRY(pg_connect_internal(ctx, X, m, d, p->metric, nbr, deg, R, ep, facts, nullptr));
+            PG_TRY(pg_connect_internal(ctx, X, m, d, p->metric, nbr, deg, R, ep, facts, knn_i.p, K,
+                                       nullptr));
         }
         return PG_OK;
     };
@@ -242,7 +244,6 @@ pg_status iter_nsg(pg_ctx *ctx, const float *X, int64_t m, int32_t d, const pg_b
         k_fill_off<<<g1, 256, 0, ctx->stream>>>(off.p, m, L);
         PG_LAUNCHED(ctx);
         cur = cand.p;
-        if (it == 0) knn_i.release();
     }
     PG_TRY(refine(p->alpha_final_deg, connect_final));
     clk.stop();
@@ -412,8 +413,8 @@ extern "C" pg_status pg_index_phase_seconds(const pg_index *idx, double *host_se
 }
 
 static pg_status search_index(pg_ctx *ctx, const pg_index *idx, const float *Q, int64_t nq,
-                              int32_t k, int32_t beam, int32_t flags, int32_t *out_ids,
-                              float *out_dist) {
+                              int32_t k, int32_t beam, int32_t upper_beam, int32_t flags,
+                              int32_t *out_ids, float *out_dist) {
     if (nq == 0) return PG_OK;
     Scratch<int32_t> w, w2;
     Scratch<float> s2;
@@ -428,7 +429,7 @@ static pg_status search_index(pg_ctx *ctx, const pg_index *idx, const float *Q, 
         for (int i = (int)idx->layers.size() - 1; i >= 1; --i) {
             const pg_layer &l = idx->layers[(size_t)i];
             PG_TRY(pg_search_internal(ctx, idx->D, idx->n, idx->d, idx->metric, l.nbr, l.deg, l.R,
-                                      l.rows, Q, nq, w.p, 1, 1, 0, w2.p, s2.p));
+                                      l.rows, Q, nq, w.p, 1, upper_beam, 0, w2.p, s2.p));
             std::swap(w.p, w2.p);
         }
     }
@@ -437,26 +438,31 @@ static pg_status search_index(pg_ctx *ctx, const pg_index *idx, const float *Q, 
                               Q, nq, w.p, k, beam, 0, out_ids, out_dist);
 }
 
-extern "C" pg_status pg_search(pg_ctx *ctx, const pg_index *idx, const float *Q, int64_t nq,
-                               int32_t k, int32_t beam, int32_t flags, pg_precision precision,
-                               int32_t *out_ids, float *out_dist) {
+static pg_status check_search(pg_ctx *ctx, const pg_index *idx, const float *Q, int64_t nq,
+                              int32_t k, int32_t beam, int32_t upper_beam, const void *a,
+                              const void *b) {
     if (!ctx) return PG_ERR_INVALID_ARG;
+    if (!idx || !Q || !a || !b) return pg_fail(ctx, PG_ERR_INVALID_ARG, "null pointer");
+    if (nq < 0 || k < 1 || beam < k || beam > 256 || upper_beam < 1 || upper_beam > 256)
+        return pg_fail(ctx, PG_ERR_INVALID_ARG,
+                       "need 1 <= k <= beam <= 256 and 1 <= upper_beam <= 256");
+    return PG_OK;
+}
+
+extern "C" pg_status pg_search(pg_ctx *ctx, const pg_index *idx, const float *Q, int64_t nq,
+                               int32_t k, int32_t beam, int32_t upper_beam, int32_t flags,
+                               pg_precision precision, int32_t *out_ids, float *out_dist) {
     (void)precision;
-    if (!idx || !Q || !out_ids || !out_dist) return pg_fail(ctx, PG_ERR_INVALID_ARG, "null pointer");
-    if (nq < 0 || k < 1 || beam < k || beam > 256)
-        return pg_fail(ctx, PG_ERR_INVALID_ARG, "need 1 <= k <= beam <= 256");
-    PG_TRY(search_index(ctx, idx, Q, nq, k, beam, flags, out_ids, out_dist));
+    PG_TRY(check_search(ctx, idx, Q, nq, k, beam, upper_beam, out_ids, out_dist));
+    PG_TRY(search_index(ctx, idx, Q, nq, k, beam, upper_beam, flags, out_ids, out_dist));
     return pg_sync_check(ctx, "pg_search");
 }
 
 extern "C" pg_status pg_search_host(pg_ctx *ctx, const pg_index *idx, const float *Q, int64_t nq,
-                                    int32_t k, int32_t beam, int32_t flags,
+                                    int32_t k, int32_t beam, int32_t upper_beam, int32_t flags,
                                     pg_precision precision, int32_t *out_ids, float *out_dist) {
-    if (!ctx) return PG_ERR_INVALID_ARG;
     (void)precision;
-    if (!idx || !Q || !out_ids || !out_dist) return pg_fail(ctx, PG_ERR_INVALID_ARG, "null pointer");
-    if (nq < 0 || k < 1 || beam < k || beam > 256)
-        return pg_fail(ctx, PG_ERR_INVALID_ARG, "need 1 <= k <= beam <= 256");
+    PG_TRY(check_search(ctx, idx, Q, nq, k, beam, upper_beam, out_ids, out_dist));
     if (nq == 0) return PG_OK;
     Scratch<float> dq, ds;
     Scratch<int32_t> di;
@@ -465,7 +471,7 @@ extern "C" pg_status pg_search_host(pg_ctx *ctx, const pg_index *idx, const floa
     PG_TRY(di.alloc(ctx, (size_t)(nq * k)));
     PG_TRY_CUDA(ctx, cudaMemcpyAsync(dq.p, Q, (size_t)(nq * idx->d) * 4, cudaMemcpyHostToDevice,
                                      ctx->stream));
-    PG_TRY(search_index(ctx, idx, dq.p, nq, k, beam, flags, di.p, ds.p));
+    PG_TRY(search_index(ctx, idx, dq.p, nq, k, beam, upper_beam, flags, di.p, ds.p));
     PG_TRY_CUDA(ctx, cudaMemcpyAsync(out_ids, di.p, (size_t)(nq * k) * 4, cudaMemcpyDeviceToHost,
                                      ctx->stream));
     PG_TRY_CUDA(ctx, cudaMemcpyAsync(out_dist, ds.p, (size_t)(nq * k) * 4, cudaMemcpyDeviceToHost,

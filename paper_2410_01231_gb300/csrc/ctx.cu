@@ -89,8 +89,9 @@ void pg_timer_begin(pg_ctx *ctx, int slot) {
     ctx->pending.push_back(t);
 }
 
-void pg_timer_end(pg_ctx *ctx, int slot) {
+void pg_timer_end(pg_ctx *ctx, int slot, double work) {
     if (!ctx->timing || ctx->pending.empty()) return;
+    ctx->timer_work[slot] += work;
     for (auto it = ctx->pending.rbegin(); it != ctx->pending.rend(); ++it) {
         if (it->slot == slot) {
             cudaEventRecord(it->b, ctx->stream);
@@ -120,8 +121,21 @@ extern "C" pg_status pg_ctx_set_timing(pg_ctx *ctx, int enable) {
     for (int i = 0; i < TM_SLOTS; ++i) {
         ctx->timer_ms[i] = 0.0;
         ctx->timer_launches[i] = 0;
+        ctx->timer_work[i] = 0.0;
     }
     return PG_OK;
+}
+
+extern "C" pg_status pg_ctx_kernel_work(pg_ctx *ctx, const char *name, double *work) {
+    if (!ctx || !name || !work) return PG_ERR_INVALID_ARG;
+    pg_timer_resolve(ctx);
+    for (int i = 0; i < TM_SLOTS; ++i) {
+        if (strcmp(name, pg_timer_names[i]) == 0) {
+            *work = ctx->timer_work[i];
+            return PG_OK;
+        }
+    }
+    return pg_fail(ctx, PG_ERR_INVALID_ARG, "unknown timer %s", name);
 }
 
 extern "C" pg_status pg_ctx_kernel_time(pg_ctx *ctx, const char *name, double *total_ms,
@@ -136,6 +150,14 @@ extern "C" pg_status pg_ctx_kernel_time(pg_ctx *ctx, const char *name, double *t
         }
     }
     return pg_fail(ctx, PG_ERR_INVALID_ARG, "unknown timer %s", name);
+}
+
+extern "C" pg_status pg_ctx_counter(pg_ctx *ctx, const char *name, int64_t *value) {
+    if (!ctx || !name || !value) return PG_ERR_INVALID_ARG;
+    if (strcmp(name, "connect_edges") == 0) *value = ctx->connect_edges;
+    else if (strcmp(name, "connect_full_rounds") == 0) *value = ctx->connect_full_rounds;
+    else return pg_fail(ctx, PG_ERR_INVALID_ARG, "unknown counter %s", name);
+    return PG_OK;
 }
 
 extern "C" void pg_ctx_destroy(pg_ctx *ctx) {

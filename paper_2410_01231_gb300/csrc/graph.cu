@@ -101,9 +101,11 @@ __global__ void k_medoid_final(const double *blk_s, const int *blk_i, int nb, in
 
 // ------------------------------------------------------------ connect
 struct ConnState {
-    int cursor;          // smallest unreached id (n when none)
-    int added;           // edges added
-    int tail;            // BFS queue tail (single-block BFS)
+    int cursor;        // smallest unreached id (n when none)
+    int added;         // edges added
+    int need_full;     // the round of `cursor` needs the grid-wide argmin
+    int full_rounds;   // rounds decided by the grid-wide argmin
+    int fast_rounds;   // rounds decided from the kNN list of r
     int pad;
     unsigned long long best;    // packed (float bits << 32 | id)
     unsigned long long best64;  // FP64 bits of the best distance (recheck)
@@ -154,9 +156,10 @@ __device__ void block_bfs(const int32_t *nbr, const int32_t *deg, int R, int64_t
     }
 }
 
-// single block: smallest unreached id at or after *cursor
+// single block: smallest unreached id at or after st->cursor
 __device__ void block_next_unreached(const int *reached, int64_t n, ConnState *st, int *s_min) {
     int from = st->cursor;
+    __syncthreads();
     for (int64_t base = from; base < n; base += blockDim.x) {
         if (threadIdx.x == 0) *s_min = INT_MAX;
         __syncthreads();
@@ -167,17 +170,19 @@ __device__ void block_next_unreached(const int *reached, int64_t n, ConnState *s
         __syncthreads();
         if (m != INT_MAX) {
             if (threadIdx.x == 0) st->cursor = m;
+            __syncthreads();
             return;
         }
     }
     if (threadIdx.x == 0) st->cursor = (int)n;
+    __syncthreads();
 }
 
-__global__ void k_connect_init(const int32_t *nbr, const int32_t *deg, int R, int64_t n,
-                               int *reached, ConnState *st) {
+__global__ void k_connect_init(int64_t n, int *reached, ConnState *st) {
     __shared__ int s_min;
     if (threadIdx.x == 0) {
         st->cursor = 0;
+        st->need_full = 0;
         st->best = ~0ull;
         st->best64 = ~0ull;
         st->best_id = INT_MAX;
@@ -186,12 +191,131 @@ __global__ void k_connect_init(const int32_t *nbr, const int32_t *deg, int R, in
     block_next_unreached(reached, n, st, &s_min);
 }
 
-// FP32 argmin over reached nodes with a free slot of (s(x, r), x)
+// link r from p, mark what r reaches, advance to the next unreached id
+__device__ void block_link_advance(int32_t *nbr, int32_t *deg, int R, int64_t n, int *reached,
+                                   int *queue, ConnState *st, int r, int p, int *s_tail,
+                                   int *s_min) {
+    if (threadIdx.x == 0) {
+        int dp = deg[p];
+        nbr[(int64_t)p * R + dp] = r;
+        deg[p] = dp + 1;
+        st->added += 1;
+    }
+    __syncthreads();
+    block_bfs(nbr, deg, R, n, reached, queue, r, s_tail);
+    block_next_unreached(reached, n, st, s_min);
+}
+
+// Rounds decided from the exact kNN list of r: the list holds the K
+// smallest (s, id) over all points, so when some member is reached and has
+// a free slot, the best such member is the global argmin (an outside point
+// at equal distance has a larger id).  Otherwise the round is left to the
+// grid-wide argmin (need_full).  One block of 1024 threads, teams of 16
+// threads per candidate; FP64 re-decision of near ties unless exact.
+constexpr int CT = 1024, TEAM = 16, NTEAM = CT / TEAM;
+
+__global__ void __launch_bounds__(CT)
+k_connect_rounds(const float *__restrict__ D, int64_t n, int d, int metric, int32_t *nbr,
+                 int32_t *deg, int R, int *reached, int *queue, ConnState *st,
+                 const int32_t *__restrict__ knn, int K, ErrModel em, int exact, int max_rounds) {
+    extern __shared__ __align__(16) float rq[];  // r's vector [d]
+    __shared__ unsigned long long s_best;
+    __shared__ unsigned long long s_best64;
+    __shared__ int s_best_id, s_tail, s_min;
+    __shared__ float s_cand[256];
+    __shared__ int s_cid[256];
+    if (st->need_full) return;
+    const int tid = threadIdx.x, team = tid / TEAM, li = tid % TEAM;
+    const int nch = d / 4;
+    for (int round = 0; round < max_rounds; ++round) {
+        const int r = st->cursor;
+        if (r >= n) return;
+        for (int c = tid; c < nch; c += CT)
+            reinterpret_cast<float4 *>(rq)[c] = reinterpret_cast<const float4 *>(D + (int64_t)r * d)[c];
+        if (tid == 0) {
+            s_best = ~0ull;
+            s_best64 = ~0ull;
+            s_best_id = INT_MAX;
+        }
+        __syncthreads();
+        for (int base = 0; base < K; base += NTEAM) {
+            const int j = base + team;
+            int x = j < K ? knn[(int64_t)r * K + j] : -1;
+            bool ok = x >= 0 && x < n && reached[x] && deg[x] < R;
+            const float4 *xr = reinterpret_cast<const float4 *>(D + (int64_t)(ok ? x : r) * d);
+            float acc = 0.f;
+            for (int c = li; c < nch; c += TEAM) {
+                float4 a = reinterpret_cast<const float4 *>(rq)[c];
+                float4 b = xr[c];
+                if (metric == 0) {
+                    float t0 = a.x - b.x, t1 = a.y - b.y, t2 = a.z - b.z, t3 = a.w - b.w;
+                    acc = fmaf(t0, t0, acc);
+                    acc = fmaf(t1, t1, acc);
+                    acc = fmaf(t2, t2, acc);
+                    acc = fmaf(t3, t3, acc);
+                } else {
+                    acc = fmaf(a.x, b.x, acc);
+                    acc = fmaf(a.y, b.y, acc);
+                    acc = fmaf(a.z, b.z, acc);
+                    acc = fmaf(a.w, b.w, acc);
+                }
+            }
+            for (int o = TEAM / 2; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            float s = metric == 0 ? acc : fmaxf(2.f - 2.f * acc, 0.f);
+            if (li == 0 && j < K) {
+                s_cand[j] = ok ? s : INFINITY;
+                s_cid[j] = ok ? x : -1;
+                if (ok) {
+                    unsigned long long pk = ((unsigned long long)__float_as_uint(s) << 32) | (unsigned)x;
+                    atomicMin(&s_best, pk);
+                }
+            }
+        }
+        __syncthreads();
+        if (s_best == ~0ull) {  // no list member qualifies: grid-wide round
+            if (tid == 0) st->need_full = 1;
+            __syncthreads();
+            return;
+        }
+        int p = (int)(s_best & 0xffffffffu);
+        if (!exact) {
+            const float bmin = __uint_as_float((unsigned)(s_best >> 32));
+            for (int j = tid; j < K; j += CT) {
+                if (s_cid[j] < 0) continue;
+                float s = s_cand[j];
+                if (s - 2.f * em.err(s) > bmin + 2.f * em.err(bmin)) continue;
+                double s64 = dist64_rows(rq, D + (int64_t)s_cid[j] * d, d, metric);
+                atomicMin(&s_best64, (unsigned long long)__double_as_longlong(s64));
+            }
+            __syncthreads();
+            for (int j = tid; j < K; j += CT) {
+                if (s_cid[j] < 0) continue;
+                float s = s_cand[j];
+                if (s - 2.f * em.err(s) > bmin + 2.f * em.err(bmin)) continue;
+                double s64 = dist64_rows(rq, D + (int64_t)s_cid[j] * d, d, metric);
+                if ((unsigned long long)__double_as_longlong(s64) == s_best64)
+                    atomicMin(&s_best_id, s_cid[j]);
+            }
+            __syncthreads();
+            p = s_best_id;
+        }
+        if (tid == 0) st->fast_rounds += 1;
+        block_link_advance(nbr, deg, R, n, reached, queue, st, r, p, &s_tail, &s_min);
+    }
+}
+
+// without kNN lists every round is a grid-wide round
+__global__ void k_connect_request_full(int64_t n, ConnState *st) {
+    if (threadIdx.x == 0 && st->cursor < n) st->need_full = 1;
+}
+
+// FP32 argmin over reached nodes with a free slot of (s(x, r), x); runs
+// only when the round of `cursor` needs it.
 __global__ void k_connect_argmin(const float *__restrict__ D, int64_t n, int d, int metric,
                                  const int *reached, const int32_t *deg, int R, ConnState *st) {
     extern __shared__ __align__(16) float rq[];
     int r = st->cursor;
-    if (r >= n) return;
+    if (r >= n || !st->need_full) return;
     const int nch = d / 4;
     for (int c = threadIdx.x; c < nch; c += blockDim.x)
         reinterpret_cast<float4 *>(rq)[c] = reinterpret_cast<const float4 *>(D + (int64_t)r * d)[c];
@@ -223,14 +347,13 @@ __global__ void k_connect_recheck(const float *__restrict__ D, int64_t n, int d,
                                   const int *reached, const int32_t *deg, int R, ConnState *st,
                                   ErrModel em, int pass) {
     int r = st->cursor;
-    if (r >= n || st->best == ~0ull) return;
+    if (r >= n || !st->need_full || st->best == ~0ull) return;
     float bmin = __uint_as_float((unsigned)(st->best >> 32));
     const float *xr = D + (int64_t)r * d;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
          x += (int64_t)gridDim.x * blockDim.x) {
         if (!reached[x] || deg[x] >= R) continue;
-        // cheap FP32 screen: same arithmetic as the argmin pass is not needed,
-        // a conservative bound on the FP32 value suffices
+        // conservative FP32 screen (sequential order; any order is within the bound)
         float s = 0.f;
         const float *xx = D + x * d;
         if (metric == 0) {
@@ -252,32 +375,29 @@ __global__ void k_connect_recheck(const float *__restrict__ D, int64_t n, int d,
     }
 }
 
-// link r from the chosen node, mark everything reachable from r, advance
+// finish a grid-wide round: link, mark, advance, clear the request
 __global__ void k_connect_link(int32_t *nbr, int32_t *deg, int R, int64_t n, int *reached,
                                int *queue, ConnState *st, int use64, int *err) {
-    __shared__ int s_tail, s_min;
-    int r = st->cursor;
-    if (r >= n) return;
+    __shared__ int s_tail, s_min, s_p;
+    const int r = st->cursor;
+    if (r >= n || !st->need_full) return;
     if (threadIdx.x == 0) {
         int p = use64 ? st->best_id : (int)(st->best & 0xffffffffu);
         if (st->best == ~0ull || p == INT_MAX) {
             record_error(err, DERR_NO_SLOT, r);
             st->cursor = (int)n;
-        } else {
-            int dp = deg[p];
-            nbr[(int64_t)p * R + dp] = r;
-            deg[p] = dp + 1;
-            st->added += 1;
+            p = -1;
         }
+        s_p = p;
         st->best = ~0ull;
         st->best64 = ~0ull;
         st->best_id = INT_MAX;
+        st->need_full = 0;
+        st->full_rounds += 1;
     }
     __syncthreads();
-    if (st->cursor >= n) return;
-    block_bfs(nbr, deg, R, n, reached, queue, r, &s_tail);
-    __syncthreads();
-    block_next_unreached(reached, n, st, &s_min);
+    if (s_p < 0) return;
+    block_link_advance(nbr, deg, R, n, reached, queue, st, r, s_p, &s_tail, &s_min);
 }
 
 }  // namespace
@@ -313,7 +433,8 @@ pg_status pg_medoid_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d, 
 
 pg_status pg_connect_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
                               int32_t *nbr, int32_t *deg, int32_t R, int64_t ep,
-                              const DataFacts &facts, int64_t *host_added) {
+                              const DataFacts &facts, const int32_t *knn, int32_t K,
+                              int64_t *host_added) {
     Scratch<int> reached, queue, fcnt;
     Scratch<ConnState> st;
     PG_TRY(reached.alloc(ctx, (size_t)n));
@@ -322,6 +443,7 @@ pg_status pg_connect_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
     PG_TRY(st.alloc(ctx, 1));
     PG_TRY_CUDA(ctx, cudaMemsetAsync(reached.p, 0, (size_t)n * 4, ctx->stream));
     PG_TRY_CUDA(ctx, cudaMemsetAsync(st.p, 0, sizeof(ConnState), ctx->stream));
+    pg_timer_begin(ctx, TM_CONNECT);
     // reachability from ep: level-synchronous passes over the whole grid
     int one = 1;
     int epi = (int)ep;
@@ -342,20 +464,30 @@ pg_status pg_connect_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
         memcpy(&fcount, ctx->h_pinned, sizeof(int));
         std::swap(fa, fb);
     }
-    k_connect_init<<<1, 1024, 0, ctx->stream>>>(nbr, deg, R, n, reached.p, st.p);
+    k_connect_init<<<1, CT, 0, ctx->stream>>>(n, reached.p, st.p);
     PG_LAUNCHED(ctx);
     const ErrModel em = pg_err_model(metric, d, facts, false);
     const int m = metric == PG_METRIC_L2SQ ? 0 : 1;
     const bool recheck = !facts.exact;
-    size_t smem = (size_t)d * 4;
-    int grid = ctx->num_sms * 8;
-    // every round links one component, so at most n rounds can be needed
-    const int64_t max_batches = n / 16 + 2;
+    const size_t smem = (size_t)d * 4;
+    const int grid = ctx->num_sms * 8;
+    // each queued group runs kNN-decided rounds until one needs the grid-wide
+    // argmin, then that round; a group makes progress on at least one round
+    const int64_t max_batches = n / 8 + 2;
     for (int64_t batch = 0;; ++batch) {
         if (batch > max_batches)
-            return pg_fail(ctx, PG_ERR_INTERNAL, "connect: no progress after %lld rounds",
-                           (long long)(batch * 16));
-        for (int round = 0; round < 16; ++round) {
+            return pg_fail(ctx, PG_ERR_INTERNAL, "connect: no progress after %lld batches",
+                           (long long)batch);
+        for (int g = 0; g < 8; ++g) {
+            if (knn) {
+                k_connect_rounds<<<1, CT, smem, ctx->stream>>>(D, n, d, m, nbr, deg, R, reached.p,
+                                                               queue.p, st.p, knn, K, em,
+                                                               facts.exact, 1 << 20);
+                PG_LAUNCHED(ctx);
+            } else {
+                k_connect_request_full<<<1, 32, 0, ctx->stream>>>(n, st.p);
+                PG_LAUNCHED(ctx);
+            }
             k_connect_argmin<<<grid, 256, smem, ctx->stream>>>(D, n, d, m, reached.p, deg, R, st.p);
             PG_LAUNCHED(ctx);
             if (recheck) {
@@ -365,8 +497,8 @@ pg_status pg_connect_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
                     PG_LAUNCHED(ctx);
                 }
             }
-            k_connect_link<<<1, 1024, 0, ctx->stream>>>(nbr, deg, R, n, reached.p, queue.p, st.p,
-                                                        recheck ? 1 : 0, ctx->d_err);
+            k_connect_link<<<1, CT, 0, ctx->stream>>>(nbr, deg, R, n, reached.p, queue.p, st.p,
+                                                      recheck ? 1 : 0, ctx->d_err);
             PG_LAUNCHED(ctx);
         }
         ConnState h;
@@ -376,9 +508,12 @@ pg_status pg_connect_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
         memcpy(&h, ctx->h_pinned, sizeof(ConnState));
         if (h.cursor >= n) {
             if (host_added) *host_added = h.added;
+            ctx->connect_edges += h.added;
+            ctx->connect_full_rounds += h.full_rounds;
             break;
         }
     }
+    pg_timer_end(ctx, TM_CONNECT);
     return PG_OK;
 }
 
@@ -401,5 +536,6 @@ extern "C" pg_status pg_connect(pg_ctx *ctx, const float *D, int64_t n, int32_t 
     if (ep < 0 || ep >= n) return pg_fail(ctx, PG_ERR_INVALID_ARG, "ep out of range");
     DataFacts facts;
     PG_TRY(pg_data_facts(ctx, D, n, d, metric, &facts));
-    return pg_connect_internal(ctx, D, n, d, metric, nbr, deg, R, ep, facts, host_added);
+    return pg_connect_internal(ctx, D, n, d, metric, nbr, deg, R, ep, facts, nullptr, 0,
+                               host_added);
 }

@@ -385,7 +385,7 @@ pg_status knn_core(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric 
                                                   metric == PG_METRIC_L2SQ ? 0 : 1, Kx, self, ti,
                                                   ts);
     PG_LAUNCHED(ctx);
-    pg_timer_end(ctx, TM_KNN);
+    pg_timer_end(ctx, TM_KNN, 2.0 * (double)nq * (double)n * (double)d);
     if (Kx != K) {
         ErrModel em = pg_err_model(metric, d, facts, true);
         k_knn_fix<<<(unsigned)((nq + 7) / 8), 256, 0, ctx->stream>>>(

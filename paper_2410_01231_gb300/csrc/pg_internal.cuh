@@ -25,6 +25,8 @@ struct pg_ctx {
     unsigned long long *h_pinned = nullptr;   // pinned host mirror for small reads
     int *h_err = nullptr;                      // pinned mirror of the error word
     int64_t launches = 0;
+    int64_t connect_edges = 0;        // edges added by the connectivity step
+    int64_t connect_full_rounds = 0;  // of those, rounds decided by a full scan
     // optional CUDA-event timing of named kernels
     int timing = 0;
     struct TimedPair {
@@ -35,6 +37,7 @@ struct pg_ctx {
     std::vector<cudaEvent_t> event_pool;
     double timer_ms[16] = {0};
     int64_t timer_launches[16] = {0};
+    double timer_work[16] = {0};  // algorithmic flops or bytes of the timed launches
 };
 
 // named kernel timers
@@ -42,7 +45,7 @@ enum { TM_KNN = 0, TM_PRUNE, TM_UNION, TM_CONNECT, TM_SEARCH, TM_MEDOID, TM_SLOT
 extern const char *const pg_timer_names[TM_SLOTS];
 // Record an event before / after a launch when timing is enabled.
 void pg_timer_begin(pg_ctx *ctx, int slot);
-void pg_timer_end(pg_ctx *ctx, int slot);
+void pg_timer_end(pg_ctx *ctx, int slot, double work = 0.0);
 void pg_timer_resolve(pg_ctx *ctx);
 
 enum { PG_CNT_SLOTS = 32 };

@@ -239,10 +239,12 @@ def test_build_rng_c1_matches_oracle_and_recall(ctx, pg):
     gt = oracle.knn(D, 10, Q=Q)
     ids, _ = idx.search(dev(Q), 10, 64)
     assert oracle.recall_at_k(host(ids), Q, D, 10, gt=gt) >= 0.95
-    # layered query path equals the oracle's layered query
+    # layered query path equals the oracle's layered query (greedy and wide descent)
     layers[0].nbr, layers[0].deg = onbr, odeg
-    oi, _ = oracle.search_nswg(D, layers, ep_top, Q, 10, 64, "l2")
-    assert (host(ids) == oi).all()
+    for ub in (1, 16):
+        oi, _ = oracle.search_nswg(D, layers, ep_top, Q, 10, 64, "l2", ef_upper=ub)
+        gi, _ = idx.search(dev(Q), 10, 64, upper_beam=ub)
+        assert (host(gi) == oi).all(), ub
     flat, _ = idx.search(dev(Q), 10, 64, flat=True)
     fo, _ = oracle.search(D, onbr, odeg, Q, oep, 10, 64)
     assert (host(flat) == fo).all()
