@@ -68,8 +68,10 @@ extern "C" pg_status pg_ctx_create(void *cuda_stream, size_t hbm_budget_bytes, p
     return PG_OK;
 }
 
-const char *const pg_timer_names[TM_SLOTS] = {"knn", "prune", "union", "connect", "search",
-                                               "medoid"};
+const char *const pg_timer_names[TM_SLOTS] = {"knn",    "prune",          "union",
+                                               "connect", "search",        "medoid",
+                                               "connect_select", "connect_fast",
+                                               "connect_scan",   "connect_commit"};
 
 static cudaEvent_t take_event(pg_ctx *ctx) {
     if (!ctx->event_pool.empty()) {
@@ -156,6 +158,7 @@ extern "C" pg_status pg_ctx_counter(pg_ctx *ctx, const char *name, int64_t *valu
     if (!ctx || !name || !value) return PG_ERR_INVALID_ARG;
     if (strcmp(name, "connect_edges") == 0) *value = ctx->connect_edges;
     else if (strcmp(name, "connect_full_rounds") == 0) *value = ctx->connect_full_rounds;
+    else if (strcmp(name, "connect_conflicts") == 0) *value = ctx->connect_why_full;
     else return pg_fail(ctx, PG_ERR_INVALID_ARG, "unknown counter %s", name);
     return PG_OK;
 }

@@ -100,17 +100,44 @@ __global__ void k_medoid_final(const double *blk_s, const int *blk_i, int nb, in
 }
 
 // ------------------------------------------------------------ connect
+// Rounds are processed in batches that reproduce the sequential order
+// exactly.  A batch takes the next B unreached ids r_1 < ... < r_B (no
+// unreached id lies between them).  Every round's candidate is computed in
+// parallel against the reached set S of the batch start: from r's exact
+// kNN list when one of its members is reached with a free slot (the list
+// holds the K smallest (s, id), so its best qualifying member is the global
+// argmin), otherwise by a scan over the nodes that had a free slot when the
+// step began (degrees only grow, so that list covers every candidate).
+// A single CTA then commits the rounds in id order; a round whose r was
+// reached meanwhile is skipped, a round whose candidate filled up ends the
+// batch (it is redone by the next one), and the nodes reached by earlier
+// commits of the batch are compared explicitly.  The result is the same as
+// deciding the rounds one at a time.
+constexpr int CB_B = 128;  // rounds per batch
+constexpr int CT = 1024;
+
 struct ConnState {
-    int cursor;        // smallest unreached id (n when none)
-    int added;         // edges added
-    int need_full;     // the round of `cursor` needs the grid-wide argmin
-    int full_rounds;   // rounds decided by the grid-wide argmin
-    int fast_rounds;   // rounds decided from the kNN list of r
-    int pad;
-    unsigned long long best;    // packed (float bits << 32 | id)
-    unsigned long long best64;  // FP64 bits of the best distance (recheck)
-    int best_id;
+    int cursor;       // smallest id that may be unreached (n: done)
+    int added;        // edges added
+    int full_rounds;  // rounds whose candidate came from the scan
+    int fast_rounds;  // rounds decided from the kNN list
+    int conflicts;    // batches cut short by a candidate that filled up
+    int b;            // rounds in the current batch
+    int nneed;        // rounds of the batch that need the scan
+    int nfree;        // length of the free list
+    int ns_cap;       // rounds of this batch the scan serves
+    int cut;          // the previous batch ended after a large reached set
+    int r[CB_B];
+    int flag[CB_B];   // 1: the round's kNN list had no qualifier at the batch start
+    int need[CB_B];   // the first ns_cap flagged rounds, ascending
+    unsigned long long best[CB_B];    // packed (FP32 bits << 32 | id)
+    unsigned long long best64[CB_B];  // FP64 bits of the minimum (non-exact data)
+    int best_id[CB_B];                // FP64-resolved argmin (non-exact data)
 };
+
+__device__ __forceinline__ unsigned long long pack_sid(float s, int id) {
+    return ((unsigned long long)__float_as_uint(s) << 32) | (unsigned)id;
+}
 
 // grid-wide BFS level from a frontier
 __global__ void k_bfs_level(const int32_t *nbr, const int32_t *deg, int R, int64_t n, int *reached,
@@ -126,18 +153,19 @@ __global__ void k_bfs_level(const int32_t *nbr, const int32_t *deg, int R, int64
     }
 }
 
-// single block: BFS from one source over unreached nodes
-__device__ void block_bfs(const int32_t *nbr, const int32_t *deg, int R, int64_t n, int *reached,
-                          int *queue, int src, int *s_tail) {
-    if (threadIdx.x == 0) {
-        *s_tail = 0;
-        if (atomicCAS(&reached[src], 0, 1) == 0) {
-            queue[0] = src;
-            *s_tail = 1;
-        }
-    }
+// nodes that have a free slot when the step begins
+__global__ void k_free_list(const int32_t *deg, int64_t n, int R, int *list, ConnState *st) {
+    int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x < n && deg[x] < R) list[atomicAdd(&st->nfree, 1)] = (int)x;
+}
+
+// single block: BFS from src over unreached nodes, appending to queue[*s_tail..]
+__device__ void block_bfs_append(const int32_t *nbr, const int32_t *deg, int R, int64_t n,
+                                 int *reached, int *queue, int src, int *s_tail) {
+    int head = *s_tail;
     __syncthreads();
-    int head = 0;
+    if (threadIdx.x == 0 && atomicCAS(&reached[src], 0, 1) == 0) queue[(*s_tail)++] = src;
+    __syncthreads();
     int tail = *s_tail;
     while (head < tail) {
         for (int i = head + threadIdx.x; i < tail; i += blockDim.x) {
@@ -156,249 +184,375 @@ __device__ void block_bfs(const int32_t *nbr, const int32_t *deg, int R, int64_t
     }
 }
 
-// single block: smallest unreached id at or after st->cursor
-__device__ void block_next_unreached(const int *reached, int64_t n, ConnState *st, int *s_min) {
-    int from = st->cursor;
-    __syncthreads();
-    for (int64_t base = from; base < n; base += blockDim.x) {
-        if (threadIdx.x == 0) *s_min = INT_MAX;
-        __syncthreads();
-        int64_t x = base + threadIdx.x;
-        if (x < n && !reached[x]) atomicMin(s_min, (int)x);
-        __syncthreads();
-        int m = *s_min;
-        __syncthreads();
-        if (m != INT_MAX) {
-            if (threadIdx.x == 0) st->cursor = m;
-            __syncthreads();
-            return;
-        }
-    }
-    if (threadIdx.x == 0) st->cursor = (int)n;
-    __syncthreads();
-}
-
-__global__ void k_connect_init(int64_t n, int *reached, ConnState *st) {
+__global__ void k_connect_init(int64_t n, const int *reached, ConnState *st) {
     __shared__ int s_min;
-    if (threadIdx.x == 0) {
-        st->cursor = 0;
-        st->need_full = 0;
-        st->best = ~0ull;
-        st->best64 = ~0ull;
-        st->best_id = INT_MAX;
-    }
+    if (threadIdx.x == 0) s_min = INT_MAX;
     __syncthreads();
-    block_next_unreached(reached, n, st, &s_min);
+    for (int64_t x = threadIdx.x; x < n; x += blockDim.x)
+        if (!reached[x]) {
+            atomicMin(&s_min, (int)x);
+            break;
+        }
+    __syncthreads();
+    if (threadIdx.x == 0) st->cursor = s_min == INT_MAX ? (int)n : s_min;
 }
 
-// link r from p, mark what r reaches, advance to the next unreached id
-__device__ void block_link_advance(int32_t *nbr, int32_t *deg, int R, int64_t n, int *reached,
-                                   int *queue, ConnState *st, int r, int p, int *s_tail,
-                                   int *s_min) {
-    if (threadIdx.x == 0) {
-        int dp = deg[p];
-        nbr[(int64_t)p * R + dp] = r;
-        deg[p] = dp + 1;
-        st->added += 1;
+// the next B unreached ids at or after the cursor, ascending
+__global__ void __launch_bounds__(CT) k_cb_select(const int *reached, int64_t n, ConnState *st) {
+    __shared__ int s_wcnt[CT / 32];
+    __shared__ int s_b;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int from = st->cursor;
+    if (tid == 0) {
+        s_b = 0;
+        st->nneed = 0;
+        // one scan covers at most ~8M (point, round) pairs; right after a
+        // batch was cut short only a few rounds are likely to be used
+        int cap = st->nfree > 0 ? (int)min(128ll, max(4ll, 8000000ll / st->nfree)) : 128;
+        st->ns_cap = st->cut ? 4 : cap;
+        st->cut = 0;
+    }
+    for (int i = tid; i < CB_B; i += CT) {
+        st->best[i] = ~0ull;
+        st->best64[i] = ~0ull;
+        st->best_id[i] = INT_MAX;
     }
     __syncthreads();
-    block_bfs(nbr, deg, R, n, reached, queue, r, s_tail);
-    block_next_unreached(reached, n, st, s_min);
+    for (int64_t base = from; base < n; base += CT) {
+        if (s_b >= CB_B) break;
+        int64_t x = base + tid;
+        bool un = x < n && !reached[x];
+        unsigned bal = __ballot_sync(0xffffffffu, un);
+        if (lane == 0) s_wcnt[wid] = __popc(bal);
+        __syncthreads();
+        int before = 0, total = 0;
+        for (int w = 0; w < CT / 32; ++w) {
+            int c = s_wcnt[w];
+            if (w < wid) before += c;
+            total += c;
+        }
+        int pos = s_b + before + __popc(bal & ((1u << lane) - 1));
+        if (un && pos < CB_B) st->r[pos] = (int)x;
+        __syncthreads();
+        if (tid == 0) s_b = min(CB_B, s_b + total);
+        __syncthreads();
+    }
+    if (tid == 0) {
+        st->b = s_b;
+        if (s_b == 0) st->cursor = (int)n;
+    }
 }
 
-// Rounds decided from the exact kNN list of r: the list holds the K
-// smallest (s, id) over all points, so when some member is reached and has
-// a free slot, the best such member is the global argmin (an outside point
-// at equal distance has a larger id).  Otherwise the round is left to the
-// grid-wide argmin (need_full).  One block of 1024 threads, teams of 16
-// threads per candidate; FP64 re-decision of near ties unless exact.
-constexpr int CT = 1024, TEAM = 16, NTEAM = CT / TEAM;
+// rounds whose kNN list has no reached member with a free slot at the batch
+// start need the scan (one warp per round)
+__global__ void k_cb_fast(int64_t n, const int *reached, const int32_t *deg, int R,
+                          const int32_t *__restrict__ knn, int K, ConnState *st) {
+    const int i = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x & 31;
+    if (i >= st->b) return;
+    const int r = st->r[i];
+    bool any = false;
+    for (int j = lane; j < K; j += 32) {
+        int x = knn[(int64_t)r * K + j];
+        any |= x >= 0 && x < n && reached[x] && deg[x] < R;
+    }
+    bool none = !__any_sync(0xffffffffu, any);
+    if (lane == 0) st->flag[i] = none ? 1 : 0;
+}
 
-__global__ void __launch_bounds__(CT)
-k_connect_rounds(const float *__restrict__ D, int64_t n, int d, int metric, int32_t *nbr,
-                 int32_t *deg, int R, int *reached, int *queue, ConnState *st,
-                 const int32_t *__restrict__ knn, int K, ErrModel em, int exact, int max_rounds) {
-    extern __shared__ __align__(16) float rq[];  // r's vector [d]
-    __shared__ unsigned long long s_best;
-    __shared__ unsigned long long s_best64;
-    __shared__ int s_best_id, s_tail, s_min;
-    __shared__ float s_cand[256];
-    __shared__ int s_cid[256];
-    if (st->need_full) return;
-    const int tid = threadIdx.x, team = tid / TEAM, li = tid % TEAM;
-    const int nch = d / 4;
-    for (int round = 0; round < max_rounds; ++round) {
-        const int r = st->cursor;
-        if (r >= n) return;
-        for (int c = tid; c < nch; c += CT)
-            reinterpret_cast<float4 *>(rq)[c] = reinterpret_cast<const float4 *>(D + (int64_t)r * d)[c];
-        if (tid == 0) {
-            s_best = ~0ull;
-            s_best64 = ~0ull;
-            s_best_id = INT_MAX;
+// Scan of the free list for the rounds that need it.  pass 0: FP32 argmin;
+// passes 1 and 2 (non-exact data): FP64 minimum, then smallest id at it,
+// among nodes inside the FP32 error bound of the pass-0 minimum.
+__global__ void k_cb_scan(const float *__restrict__ D, int64_t n, int d, int metric,
+                          const int *reached, const int32_t *deg, int R, const int *free_list,
+                          ConnState *st, ErrModel em, int pass, int rch) {
+    extern __shared__ __align__(16) unsigned char cb_smem[];
+    unsigned long long *sbest = reinterpret_cast<unsigned long long *>(cb_smem);
+    float *rv = reinterpret_cast<float *>(sbest + CB_B);
+    __shared__ int s_need[CB_B];
+    __shared__ int s_nneed;
+    if (threadIdx.x == 0) {
+        int c = 0;
+        for (int i = 0; i < st->b && c < st->ns_cap; ++i)
+            if (st->flag[i]) s_need[c++] = i;
+        s_nneed = c;
+        if (blockIdx.x == 0) {
+            for (int j = 0; j < c; ++j) st->need[j] = s_need[j];
+            st->nneed = c;
+        }
+    }
+    __syncthreads();
+    const int nneed = s_nneed, nfree = st->nfree;
+    if (nneed == 0) return;
+    const int tid = threadIdx.x, lane = tid & 31, team = tid >> 3, li = lane & 7;
+    const int nteam = blockDim.x / 8, nch = d / 4;
+    for (int c0 = 0; c0 < nneed; c0 += rch) {
+        const int cn = min(rch, nneed - c0);
+        for (int t = tid; t < cn * nch; t += blockDim.x) {
+            int j = t / nch, c = t % nch;
+            int r = st->r[s_need[c0 + j]];
+            reinterpret_cast<float4 *>(rv)[j * nch + c] =
+                reinterpret_cast<const float4 *>(D + (int64_t)r * d)[c];
+        }
+        for (int j = tid; j < cn; j += blockDim.x) sbest[j] = ~0ull;
+        __syncthreads();
+        for (int base = blockIdx.x * nteam; base < nfree; base += gridDim.x * nteam) {
+            const int t = base + team;
+            const int x = t < nfree ? free_list[t] : -1;
+            const bool ok = x >= 0 && reached[x] && deg[x] < R;
+            const float4 *xr = reinterpret_cast<const float4 *>(D + (int64_t)(ok ? x : 0) * d);
+            for (int j = 0; j < cn; ++j) {
+                float s = team8_dist(reinterpret_cast<const float4 *>(rv + (size_t)j * d), xr, nch, li,
+                                     metric);
+                if (!ok || li != 0) continue;
+                const int i = s_need[c0 + j];
+                if (pass > 0 && st->best[i] == ~0ull) continue;
+                if (pass == 0) {
+                    atomicMin(&sbest[j], pack_sid(s, x));
+                    continue;
+                }
+                float bmin = __uint_as_float((unsigned)(st->best[i] >> 32));
+                if (s - 2.f * em.err(s) > bmin + 2.f * em.err(bmin)) continue;
+                double s64 = dist64_rows(rv + (size_t)j * d, D + (int64_t)x * d, d, metric);
+                unsigned long long b64 = (unsigned long long)__double_as_longlong(s64);
+                if (pass == 1) atomicMin(&st->best64[i], b64);
+                else if (b64 == st->best64[i]) atomicMin(&st->best_id[i], x);
+            }
         }
         __syncthreads();
-        for (int base = 0; base < K; base += NTEAM) {
-            const int j = base + team;
-            int x = j < K ? knn[(int64_t)r * K + j] : -1;
-            bool ok = x >= 0 && x < n && reached[x] && deg[x] < R;
-            const float4 *xr = reinterpret_cast<const float4 *>(D + (int64_t)(ok ? x : r) * d);
-            float acc = 0.f;
-            for (int c = li; c < nch; c += TEAM) {
-                float4 a = reinterpret_cast<const float4 *>(rq)[c];
-                float4 b = xr[c];
-                if (metric == 0) {
-                    float t0 = a.x - b.x, t1 = a.y - b.y, t2 = a.z - b.z, t3 = a.w - b.w;
-                    acc = fmaf(t0, t0, acc);
-                    acc = fmaf(t1, t1, acc);
-                    acc = fmaf(t2, t2, acc);
-                    acc = fmaf(t3, t3, acc);
-                } else {
-                    acc = fmaf(a.x, b.x, acc);
-                    acc = fmaf(a.y, b.y, acc);
-                    acc = fmaf(a.z, b.z, acc);
-                    acc = fmaf(a.w, b.w, acc);
-                }
-            }
-            for (int o = TEAM / 2; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            float s = metric == 0 ? acc : fmaxf(2.f - 2.f * acc, 0.f);
-            if (li == 0 && j < K) {
-                s_cand[j] = ok ? s : INFINITY;
-                s_cid[j] = ok ? x : -1;
-                if (ok) {
-                    unsigned long long pk = ((unsigned long long)__float_as_uint(s) << 32) | (unsigned)x;
-                    atomicMin(&s_best, pk);
-                }
-            }
-        }
+        if (pass == 0)
+            for (int j = tid; j < cn; j += blockDim.x)
+                if (sbest[j] != ~0ull) atomicMin(&st->best[s_need[c0 + j]], sbest[j]);
         __syncthreads();
-        if (s_best == ~0ull) {  // no list member qualifies: grid-wide round
-            if (tid == 0) st->need_full = 1;
-            __syncthreads();
-            return;
-        }
-        int p = (int)(s_best & 0xffffffffu);
-        if (!exact) {
-            const float bmin = __uint_as_float((unsigned)(s_best >> 32));
-            for (int j = tid; j < K; j += CT) {
-                if (s_cid[j] < 0) continue;
-                float s = s_cand[j];
-                if (s - 2.f * em.err(s) > bmin + 2.f * em.err(bmin)) continue;
-                double s64 = dist64_rows(rq, D + (int64_t)s_cid[j] * d, d, metric);
-                atomicMin(&s_best64, (unsigned long long)__double_as_longlong(s64));
-            }
-            __syncthreads();
-            for (int j = tid; j < K; j += CT) {
-                if (s_cid[j] < 0) continue;
-                float s = s_cand[j];
-                if (s - 2.f * em.err(s) > bmin + 2.f * em.err(bmin)) continue;
-                double s64 = dist64_rows(rq, D + (int64_t)s_cid[j] * d, d, metric);
-                if ((unsigned long long)__double_as_longlong(s64) == s_best64)
-                    atomicMin(&s_best_id, s_cid[j]);
-            }
-            __syncthreads();
-            p = s_best_id;
-        }
-        if (tid == 0) st->fast_rounds += 1;
-        block_link_advance(nbr, deg, R, n, reached, queue, st, r, p, &s_tail, &s_min);
     }
 }
 
-// without kNN lists every round is a grid-wide round
-__global__ void k_connect_request_full(int64_t n, ConnState *st) {
-    if (threadIdx.x == 0 && st->cursor < n) st->need_full = 1;
-}
+// commit the batch's rounds in id order (one CTA).  For each round the
+// argmin over r's kNN list restricted to the nodes reached and free *now*
+// is recomputed: when it exists it is the global argmin (ball argument),
+// whatever was reached earlier in the batch.  Otherwise the scan result of
+// the batch start competes with the free nodes reached earlier in the batch
+// (measured by teams of eight threads); a round without a scan result whose
+// list qualifier filled up ends the batch.
+constexpr int CTC = 256;  // threads of the commit CTA
 
-// FP32 argmin over reached nodes with a free slot of (s(x, r), x); runs
-// only when the round of `cursor` needs it.
-__global__ void k_connect_argmin(const float *__restrict__ D, int64_t n, int d, int metric,
-                                 const int *reached, const int32_t *deg, int R, ConnState *st) {
-    extern __shared__ __align__(16) float rq[];
-    int r = st->cursor;
-    if (r >= n || !st->need_full) return;
-    const int nch = d / 4;
-    for (int c = threadIdx.x; c < nch; c += blockDim.x)
-        reinterpret_cast<float4 *>(rq)[c] = reinterpret_cast<const float4 *>(D + (int64_t)r * d)[c];
+__device__ void list_argmin(const float *__restrict__ D, int64_t n, int d, int metric,
+                            const int *reached, const int32_t *deg, int R,
+                            const int32_t *__restrict__ knn, int K, int r, const float *rq,
+                            ErrModel em, int exact, unsigned long long *s_b,
+                            unsigned long long *s_b64, int *s_bid, float *s_cs, int *s_ci) {
+    const int tid = threadIdx.x, lane = tid & 31, team = tid >> 3, li = lane & 7;
+    const int nteam = blockDim.x / 8, nch = d / 4;
+    if (tid == 0) {
+        *s_b = ~0ull;
+        *s_b64 = ~0ull;
+        *s_bid = INT_MAX;
+    }
     __syncthreads();
-    const int lane = threadIdx.x & 31, team = lane >> 3, li = lane & 7;
-    const int64_t teams = (int64_t)gridDim.x * (blockDim.x / 8);
-    unsigned long long best = ~0ull;
-    for (int64_t base = (int64_t)blockIdx.x * (blockDim.x / 8) + (threadIdx.x >> 5) * 4;
-         base < n; base += teams) {
-        int64_t x = base + team;
-        bool ok = x < n && reached[x] && deg[x] < R;
-        int64_t row = ok ? x : r;
+    for (int base = 0; base < K; base += nteam) {
+        const int j = base + team;
+        int x = j < K ? knn[(int64_t)r * K + j] : -1;
+        bool ok = x >= 0 && x < n && reached[x] && deg[x] < R;
+        if (!__any_sync(0xffffffffu, ok)) {
+            if (li == 0 && j < K) s_ci[j] = -1;
+            continue;
+        }
         float s = team8_dist(reinterpret_cast<const float4 *>(rq),
-                             reinterpret_cast<const float4 *>(D + row * d), nch, li, metric);
-        if (ok && li == 0) {
-            unsigned long long p = ((unsigned long long)__float_as_uint(s) << 32) | (unsigned)x;
-            if (p < best) best = p;
+                             reinterpret_cast<const float4 *>(D + (int64_t)(ok ? x : r) * d), nch,
+                             li, metric);
+        if (li == 0 && j < K) {
+            s_cs[j] = ok ? s : INFINITY;
+            s_ci[j] = ok ? x : -1;
+            if (ok) atomicMin(s_b, pack_sid(s, x));
         }
-    }
-    for (int o = 16; o; o >>= 1) {
-        unsigned long long t = __shfl_xor_sync(0xffffffffu, best, o);
-        if (t < best) best = t;
-    }
-    if (lane == 0 && best != ~0ull) atomicMin(&st->best, best);
-}
-
-// FP64 re-decision among candidates inside the FP32 error bound of the min
-__global__ void k_connect_recheck(const float *__restrict__ D, int64_t n, int d, int metric,
-                                  const int *reached, const int32_t *deg, int R, ConnState *st,
-                                  ErrModel em, int pass) {
-    int r = st->cursor;
-    if (r >= n || !st->need_full || st->best == ~0ull) return;
-    float bmin = __uint_as_float((unsigned)(st->best >> 32));
-    const float *xr = D + (int64_t)r * d;
-    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
-         x += (int64_t)gridDim.x * blockDim.x) {
-        if (!reached[x] || deg[x] >= R) continue;
-        // conservative FP32 screen (sequential order; any order is within the bound)
-        float s = 0.f;
-        const float *xx = D + x * d;
-        if (metric == 0) {
-            for (int i = 0; i < d; ++i) {
-                float t = xx[i] - xr[i];
-                s = fmaf(t, t, s);
-            }
-        } else {
-            for (int i = 0; i < d; ++i) s = fmaf(xx[i], xr[i], s);
-            s = fmaxf(2.f - 2.f * s, 0.f);
-        }
-        if (s - 2.f * em.err(s) > bmin + 2.f * em.err(bmin)) continue;
-        double s64 = dist64_rows(xx, xr, d, metric);
-        if (pass == 0) {
-            atomicMin(&st->best64, (unsigned long long)__double_as_longlong(s64));
-        } else if ((unsigned long long)__double_as_longlong(s64) == st->best64) {
-            atomicMin(&st->best_id, (int)x);
-        }
-    }
-}
-
-// finish a grid-wide round: link, mark, advance, clear the request
-__global__ void k_connect_link(int32_t *nbr, int32_t *deg, int R, int64_t n, int *reached,
-                               int *queue, ConnState *st, int use64, int *err) {
-    __shared__ int s_tail, s_min, s_p;
-    const int r = st->cursor;
-    if (r >= n || !st->need_full) return;
-    if (threadIdx.x == 0) {
-        int p = use64 ? st->best_id : (int)(st->best & 0xffffffffu);
-        if (st->best == ~0ull || p == INT_MAX) {
-            record_error(err, DERR_NO_SLOT, r);
-            st->cursor = (int)n;
-            p = -1;
-        }
-        s_p = p;
-        st->best = ~0ull;
-        st->best64 = ~0ull;
-        st->best_id = INT_MAX;
-        st->need_full = 0;
-        st->full_rounds += 1;
     }
     __syncthreads();
-    if (s_p < 0) return;
-    block_link_advance(nbr, deg, R, n, reached, queue, st, r, s_p, &s_tail, &s_min);
+    if (exact || *s_b == ~0ull) {
+        if (tid == 0 && *s_b != ~0ull) *s_bid = (int)(*s_b & 0xffffffffu);
+        __syncthreads();
+        return;
+    }
+    const float bmin = __uint_as_float((unsigned)(*s_b >> 32));
+    for (int j = tid; j < K; j += blockDim.x) {
+        if (s_ci[j] < 0) continue;
+        float s = s_cs[j];
+        if (s - 2.f * em.err(s) > bmin + 2.f * em.err(bmin)) continue;
+        double s64 = dist64_rows(rq, D + (int64_t)s_ci[j] * d, d, metric);
+        atomicMin(s_b64, (unsigned long long)__double_as_longlong(s64));
+    }
+    __syncthreads();
+    for (int j = tid; j < K; j += blockDim.x) {
+        if (s_ci[j] < 0) continue;
+        float s = s_cs[j];
+        if (s - 2.f * em.err(s) > bmin + 2.f * em.err(bmin)) continue;
+        double s64 = dist64_rows(rq, D + (int64_t)s_ci[j] * d, d, metric);
+        if ((unsigned long long)__double_as_longlong(s64) == *s_b64) atomicMin(s_bid, s_ci[j]);
+    }
+    __syncthreads();
 }
+
+__global__ void __launch_bounds__(CTC)
+k_cb_commit(const float *__restrict__ D, int64_t n, int d, int metric, int32_t *nbr, int32_t *deg,
+            int R, int *reached, int *queue, ConnState *st, const int32_t *__restrict__ knn,
+            int K, ErrModel em, int exact, int *err) {
+    extern __shared__ __align__(16) float cm_rq[];  // r's vector [d]
+    __shared__ int s_tail, s_stop, s_nb_id, s_lid, s_nfree;
+    __shared__ unsigned long long s_nb, s_nb64, s_lb, s_lb64;
+    __shared__ int s_r[CB_B], s_scan[CB_B], s_bid[CB_B];
+    __shared__ unsigned long long s_best64[CB_B], s_best[CB_B];
+    __shared__ float s_cs[256];
+    __shared__ int s_ci[256];
+    __shared__ int s_added, s_full, s_fast;
+    const int b = st->b;
+    if (b == 0) return;
+    const int tid = threadIdx.x, lane = tid & 31, team = tid >> 3, li = lane & 7;
+    const int nteam = CTC / 8, nch = d / 4;
+    for (int i = tid; i < b; i += CTC) {
+        s_r[i] = st->r[i];
+        s_best[i] = st->best[i];
+        s_best64[i] = st->best64[i];
+        s_bid[i] = st->best_id[i];
+        s_scan[i] = 0;
+    }
+    if (tid == 0) {
+        s_tail = 0;
+        s_stop = 0;
+        s_added = 0;
+        s_full = 0;
+        s_fast = 0;
+    }
+    __syncthreads();
+    for (int j = tid; j < st->nneed; j += CTC) s_scan[st->need[j]] = 1;
+    __syncthreads();
+    for (int i = 0; i < b; ++i) {
+        const int r = s_r[i];
+        if (reached[r]) continue;
+        for (int c = tid; c < nch; c += CTC)
+            reinterpret_cast<float4 *>(cm_rq)[c] = reinterpret_cast<const float4 *>(D + (int64_t)r * d)[c];
+        __syncthreads();
+        int q = -1;
+        // a scanned round had no list qualifier at the batch start: members
+        // that qualify now were reached in this batch and are among the
+        // nodes checked below, so its list need not be measured again
+        if (!s_scan[i]) {
+            list_argmin(D, n, d, metric, reached, deg, R, knn, knn ? K : 0, r, cm_rq, em, exact,
+                        &s_lb, &s_lb64, &s_lid, s_cs, s_ci);
+        } else if (tid == 0) {
+            s_lid = INT_MAX;
+        }
+        __syncthreads();
+        if (s_lid != INT_MAX) {
+            q = s_lid;
+            if (tid == 0) s_fast += 1;
+        } else if (!s_scan[i]) {  // its list qualifier filled up: redo in the next batch
+            if (tid == 0) {
+                st->cursor = r;
+                st->conflicts += 1;
+                s_stop = 1;
+            }
+            __syncthreads();
+            break;
+        } else {
+            int p;
+            float ps = INFINITY;
+            double ps64 = INFINITY;
+            if (exact) {
+                unsigned long long pk = s_best[i];
+                p = pk == ~0ull ? -1 : (int)(pk & 0xffffffffu);
+                if (p >= 0) ps = __uint_as_float((unsigned)(pk >> 32));
+            } else {
+                p = s_bid[i] == INT_MAX ? -1 : s_bid[i];
+                if (p >= 0) ps64 = __longlong_as_double((long long)s_best64[i]);
+            }
+            if (p >= 0 && deg[p] >= R) {  // filled by an earlier commit
+                if (tid == 0) {
+                    st->cursor = r;
+                    st->conflicts += 1;
+                    s_stop = 1;
+                }
+                __syncthreads();
+                break;
+            }
+            // free nodes reached earlier in this batch compete with p
+            const int nr = s_tail;
+            if (tid == 0) {
+                s_nb = ~0ull;
+                s_nb64 = ~0ull;
+                s_nb_id = INT_MAX;
+            }
+            __syncthreads();
+            for (int base = 0; base < nr; base += nteam) {
+                const int t = base + team;
+                const int x = t < nr ? queue[t] : -1;
+                const bool ok = x >= 0 && deg[x] < R;
+                if (!__any_sync(0xffffffffu, ok)) continue;
+                float s = team8_dist(reinterpret_cast<const float4 *>(cm_rq),
+                                     reinterpret_cast<const float4 *>(D + (int64_t)(ok ? x : r) * d),
+                                     nch, li, metric);
+                if (!ok || li != 0) continue;
+                if (exact) {
+                    atomicMin(&s_nb, pack_sid(s, x));
+                } else {
+                    double s64 = dist64_rows(D + (int64_t)x * d, cm_rq, d, metric);
+                    atomicMin(&s_nb64, (unsigned long long)__double_as_longlong(s64));
+                }
+            }
+            __syncthreads();
+            if (!exact && s_nb64 != ~0ull) {
+                for (int t = tid; t < nr; t += CTC) {
+                    int x = queue[t];
+                    if (deg[x] >= R) continue;
+                    double s64 = dist64_rows(D + (int64_t)x * d, cm_rq, d, metric);
+                    if ((unsigned long long)__double_as_longlong(s64) == s_nb64)
+                        atomicMin(&s_nb_id, x);
+                }
+                __syncthreads();
+            }
+            q = p;
+            if (exact) {
+                if (s_nb != ~0ull && (p < 0 || s_nb < pack_sid(ps, p))) q = (int)(s_nb & 0xffffffffu);
+            } else if (s_nb_id != INT_MAX) {
+                double qs = __longlong_as_double((long long)s_nb64);
+                if (p < 0 || qs < ps64 || (qs == ps64 && s_nb_id < p)) q = s_nb_id;
+            }
+            if (tid == 0 && q >= 0) s_full += 1;
+        }
+        if (tid == 0) {
+            if (q < 0) {
+                record_error(err, DERR_NO_SLOT, r);
+                st->cursor = (int)n;
+                s_stop = 2;
+            } else {
+                int dq = deg[q];
+                nbr[(int64_t)q * R + dq] = r;
+                deg[q] = dq + 1;
+                s_added += 1;
+            }
+        }
+        __syncthreads();
+        if (s_stop) break;
+        const int before = s_tail;
+        block_bfs_append(nbr, deg, R, n, reached, queue, r, &s_tail);
+        // a large reached set would make every later round of the batch
+        // measure against it: restart from a fresh batch instead
+        if (s_tail - before > 256 && i + 1 < b) {
+            if (tid == 0) {
+                st->cursor = s_r[i + 1];
+                st->cut = 1;
+                s_stop = 3;
+            }
+            __syncthreads();
+            break;
+        }
+    }
+    if (tid == 0) {
+        st->added += s_added;
+        st->full_rounds += s_full;
+        st->fast_rounds += s_fast;
+        if (!s_stop) st->cursor = s_r[b - 1] + 1 < n ? s_r[b - 1] + 1 : (int)n;
+    }
+    (void)s_nfree;
+}
+
 
 }  // namespace
 
@@ -435,15 +589,18 @@ pg_status pg_connect_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
                               int32_t *nbr, int32_t *deg, int32_t R, int64_t ep,
                               const DataFacts &facts, const int32_t *knn, int32_t K,
                               int64_t *host_added) {
-    Scratch<int> reached, queue, fcnt;
+    Scratch<int> reached, queue, fcnt, freel;
     Scratch<ConnState> st;
     PG_TRY(reached.alloc(ctx, (size_t)n));
     PG_TRY(queue.alloc(ctx, (size_t)n * 2));
     PG_TRY(fcnt.alloc(ctx, 2));
+    PG_TRY(freel.alloc(ctx, (size_t)n));
     PG_TRY(st.alloc(ctx, 1));
     PG_TRY_CUDA(ctx, cudaMemsetAsync(reached.p, 0, (size_t)n * 4, ctx->stream));
     PG_TRY_CUDA(ctx, cudaMemsetAsync(st.p, 0, sizeof(ConnState), ctx->stream));
     pg_timer_begin(ctx, TM_CONNECT);
+    k_free_list<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(deg, n, R, freel.p, st.p);
+    PG_LAUNCHED(ctx);
     // reachability from ep: level-synchronous passes over the whole grid
     int one = 1;
     int epi = (int)ep;
@@ -468,48 +625,54 @@ pg_status pg_connect_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
     PG_LAUNCHED(ctx);
     const ErrModel em = pg_err_model(metric, d, facts, false);
     const int m = metric == PG_METRIC_L2SQ ? 0 : 1;
-    const bool recheck = !facts.exact;
-    const size_t smem = (size_t)d * 4;
-    const int grid = ctx->num_sms * 8;
-    // each queued group runs kNN-decided rounds until one needs the grid-wide
-    // argmin, then that round; a group makes progress on at least one round
-    const int64_t max_batches = n / 8 + 2;
-    for (int64_t batch = 0;; ++batch) {
-        if (batch > max_batches)
+    const bool exact = facts.exact != 0;
+    const size_t smem_r = (size_t)d * 4;
+    int rch = (int)std::min<size_t>(CB_B, (size_t)(96 * 1024 - CB_B * 8) / ((size_t)d * 4));
+    if (rch < 1) rch = 1;
+    const size_t smem_scan = CB_B * 8 + (size_t)rch * d * 4;
+    PG_TRY_CUDA(ctx, cudaFuncSetAttribute(k_cb_scan, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem_scan));
+    const int grid = ctx->num_sms * 4;
+    // every batch commits at least its first round
+    const int64_t max_groups = n / 8 + 2;
+    for (int64_t group = 0;; ++group) {
+        if (group > max_groups)
             return pg_fail(ctx, PG_ERR_INTERNAL, "connect: no progress after %lld batches",
-                           (long long)batch);
+                           (long long)(group * 8));
         for (int g = 0; g < 8; ++g) {
-            if (knn) {
-                k_connect_rounds<<<1, CT, smem, ctx->stream>>>(D, n, d, m, nbr, deg, R, reached.p,
-                                                               queue.p, st.p, knn, K, em,
-                                                               facts.exact, 1 << 20);
-                PG_LAUNCHED(ctx);
-            } else {
-                k_connect_request_full<<<1, 32, 0, ctx->stream>>>(n, st.p);
-                PG_LAUNCHED(ctx);
-            }
-            k_connect_argmin<<<grid, 256, smem, ctx->stream>>>(D, n, d, m, reached.p, deg, R, st.p);
+            pg_timer_begin(ctx, TM_CSELECT);
+            k_cb_select<<<1, CT, 0, ctx->stream>>>(reached.p, n, st.p);
             PG_LAUNCHED(ctx);
-            if (recheck) {
-                for (int pass = 0; pass < 2; ++pass) {
-                    k_connect_recheck<<<grid, 256, 0, ctx->stream>>>(D, n, d, m, reached.p, deg, R,
-                                                                     st.p, em, pass);
-                    PG_LAUNCHED(ctx);
-                }
-            }
-            k_connect_link<<<1, CT, 0, ctx->stream>>>(nbr, deg, R, n, reached.p, queue.p, st.p,
-                                                      recheck ? 1 : 0, ctx->d_err);
+            pg_timer_end(ctx, TM_CSELECT);
+            pg_timer_begin(ctx, TM_CFAST);
+            k_cb_fast<<<CB_B / 8, 256, 0, ctx->stream>>>(n, reached.p, deg, R, knn, knn ? K : 0,
+                                                          st.p);
             PG_LAUNCHED(ctx);
+            pg_timer_end(ctx, TM_CFAST);
+            for (int pass = 0; pass < (exact ? 1 : 3); ++pass) {
+                pg_timer_begin(ctx, TM_CSCAN);
+                k_cb_scan<<<grid, 256, smem_scan, ctx->stream>>>(D, n, d, m, reached.p, deg, R,
+                                                                 freel.p, st.p, em, pass, rch);
+                PG_LAUNCHED(ctx);
+                pg_timer_end(ctx, TM_CSCAN);
+            }
+            pg_timer_begin(ctx, TM_CCOMMIT);
+            k_cb_commit<<<1, CTC, smem_r, ctx->stream>>>(D, n, d, m, nbr, deg, R, reached.p,
+                                                         queue.p, st.p, knn, knn ? K : 0, em,
+                                                         exact ? 1 : 0, ctx->d_err);
+            PG_LAUNCHED(ctx);
+            pg_timer_end(ctx, TM_CCOMMIT);
         }
-        ConnState h;
-        PG_TRY_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned, st.p, sizeof(ConnState),
-                                         cudaMemcpyDeviceToHost, ctx->stream));
+        int h[8];
+        PG_TRY_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned, st.p, sizeof h, cudaMemcpyDeviceToHost,
+                                         ctx->stream));
         PG_TRY(pg_sync_check(ctx, "connect"));
-        memcpy(&h, ctx->h_pinned, sizeof(ConnState));
-        if (h.cursor >= n) {
-            if (host_added) *host_added = h.added;
-            ctx->connect_edges += h.added;
-            ctx->connect_full_rounds += h.full_rounds;
+        memcpy(h, ctx->h_pinned, sizeof h);
+        if (h[0] >= n) {
+            if (host_added) *host_added = h[1];
+            ctx->connect_edges += h[1];
+            ctx->connect_full_rounds += h[2];
+            ctx->connect_why_full += h[4];
             break;
         }
     }

@@ -27,6 +27,7 @@ struct pg_ctx {
     int64_t launches = 0;
     int64_t connect_edges = 0;        // edges added by the connectivity step
     int64_t connect_full_rounds = 0;  // of those, rounds decided by a full scan
+    int64_t connect_why_full = 0;     // full rounds whose reached list members were all full
     // optional CUDA-event timing of named kernels
     int timing = 0;
     struct TimedPair {
@@ -41,7 +42,10 @@ struct pg_ctx {
 };
 
 // named kernel timers
-enum { TM_KNN = 0, TM_PRUNE, TM_UNION, TM_CONNECT, TM_SEARCH, TM_MEDOID, TM_SLOTS };
+enum {
+    TM_KNN = 0, TM_PRUNE, TM_UNION, TM_CONNECT, TM_SEARCH, TM_MEDOID, TM_CSELECT, TM_CFAST,
+    TM_CSCAN, TM_CCOMMIT, TM_SLOTS
+};
 extern const char *const pg_timer_names[TM_SLOTS];
 // Record an event before / after a launch when timing is enabled.
 void pg_timer_begin(pg_ctx *ctx, int slot);

@@ -252,14 +252,26 @@ def test_build_rng_c1_matches_oracle_and_recall(ctx, pg):
 
 def test_build_nswg_integer_matches_oracle(ctx, pg):
     D = int_points(4000)
-    p = dict(K=16, L=40, R=16, M=16, alpha_deg=70.0, iters=1, seed=5)
+    p = dict(K=24, L=48, R=32, M=16, alpha_deg=70.0, iters=1, seed=5)
     idx = pg.Index.build_nswg(ctx, dev(D), metric="l2", **p)
-    layers, ep, lev = oracle.build_nswg(D, 16, 40, 16, 16, 70.0, 60.0, 1, "l2", seed=5)
+    layers, ep, lev = oracle.build_nswg(D, 24, 48, 16, 32, 70.0, 60.0, 1, "l2", seed=5)
     info = idx.info()
     assert info["n_layers"] == len(layers) and info["ep_top"] == ep
     for i, lay in enumerate(layers):
         gid, nb, dg = _export(idx, i)
         assert (gid == lay.gid).all() and (dg == lay.deg).all() and (nb == lay.nbr).all(), i
+
+
+def test_connect_without_free_slot_is_reported_by_both_sides(ctx, pg):
+    """R=16 after alpha=70 pruning leaves every reached node full while some
+    node is still unreached: the oracle and the library both refuse."""
+    D = int_points(4000)
+    with pytest.raises(RuntimeError):
+        oracle.build_nswg(D, 16, 40, 16, 16, 70.0, 60.0, 1, "l2", seed=5)
+    with pytest.raises(pg.PGError) as e:
+        pg.Index.build_nswg(ctx, dev(D), metric="l2", K=16, L=40, R=16, M=16, alpha_deg=70.0,
+                            iters=1, seed=5)
+    assert e.value.status == 5
 
 
 def test_build_nswg_cosine_properties_and_recall(ctx, pg):
