@@ -140,14 +140,21 @@ pg_status pg_ctx_counter(pg_ctx *ctx, const char *name, int64_t *value);
  * initialization phase, Section 3.1 and Algorithm 6 line 1, computed by
  * brute force).  For every u the K smallest (s(u,v), v) with v != u.
  * ids [n][K], dist [n][K] (FP32 value of s); rows with fewer than K other
- * points are padded with -1 / +inf.  1 <= K <= 256, d % 4 == 0. */
+ * points are padded with -1 / +inf.  1 <= K <= 256, d % 4 == 0.
+ * PG_PREC_BF16_SCREEN runs the distance tiles on the tensor cores
+ * (tcgen05, BF16 inputs, FP32 accumulation) when the BF16 copy of D and all
+ * partial sums are exact (integer data with |x| <= 256 and d*(2^8)^2
+ * sums below 2^24, L2, d <= 128, K <= 64); otherwise it runs the FP32
+ * tiles, so the result never depends on the precision argument. */
 pg_status pg_build_knn(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
                        int32_t K, pg_precision precision, int32_t *ids, float *dist);
 
 /* Exact k nearest points of D for external queries Q [nq][d] (ground
- * truth for recall).  Same output layout as pg_build_knn. */
+ * truth for recall).  Same output layout and precision rules as
+ * pg_build_knn. */
 pg_status pg_knn_query(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
-                       const float *Q, int64_t nq, int32_t k, int32_t *ids, float *dist);
+                       const float *Q, int64_t nq, int32_t k, pg_precision precision,
+                       int32_t *ids, float *dist);
 
 /* alpha-pruning of every candidate row (Section 4.1 definition, scanned
  * as in Prune, Algorithm 3).  Row u holds cand_ids[cand_off[u] ..

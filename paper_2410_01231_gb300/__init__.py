@@ -62,7 +62,7 @@ _sig("pg_last_error", C.c_char_p, [P])
 _sig("pg_ctx_sync", C.c_int, [P])
 _sig("pg_ctx_launches", i64, [P])
 _sig("pg_build_knn", C.c_int, [P, P, i64, i32, C.c_int, i32, C.c_int, P, P])
-_sig("pg_knn_query", C.c_int, [P, P, i64, i32, C.c_int, P, i64, i32, P, P])
+_sig("pg_knn_query", C.c_int, [P, P, i64, i32, C.c_int, P, i64, i32, C.c_int, P, P])
 _sig("pg_prune", C.c_int, [P, P, i64, i32, C.c_int, P, P, i32, dbl, C.c_int, P, P, P])
 _sig("pg_reverse_union", C.c_int, [P, P, P, i64, i32, P, P, i64, P])
 _sig("pg_medoid", C.c_int, [P, P, i64, i32, C.c_int, P])
@@ -199,13 +199,15 @@ def build_knn(ctx: Context, D: torch.Tensor, K: int, metric="l2", precision="fp3
     return ids, dist
 
 
-def knn_query(ctx: Context, D: torch.Tensor, Q: torch.Tensor, k: int, metric="l2"):
+def knn_query(ctx: Context, D: torch.Tensor, Q: torch.Tensor, k: int, metric="l2",
+              precision="fp32"):
     D = _dev(D, torch.float32, "D")
     Q = _dev(Q, torch.float32, "Q")
     ids = torch.empty((Q.shape[0], k), dtype=torch.int32, device=D.device)
     dist = torch.empty((Q.shape[0], k), dtype=torch.float32, device=D.device)
     ctx._check(_lib.pg_knn_query(ctx.handle, _ptr(D), D.shape[0], D.shape[1], METRIC[metric],
-                                 _ptr(Q), Q.shape[0], k, _ptr(ids), _ptr(dist)), "pg_knn_query")
+                                 _ptr(Q), Q.shape[0], k, PRECISION[precision], _ptr(ids),
+                                 _ptr(dist)), "pg_knn_query")
     return ids, dist
 
 

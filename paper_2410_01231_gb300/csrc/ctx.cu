@@ -216,6 +216,9 @@ pg_status pg_sync_check(pg_ctx *ctx, const char *where) {
             return pg_fail(ctx, PG_ERR_DEVICE_CHECK, "%s: id out of range at %lld", where, info);
         case DERR_CAPACITY:
             return pg_fail(ctx, PG_ERR_CAPACITY, "%s: capacity exceeded (%lld)", where, info);
+        case DERR_TIMEOUT:
+            return pg_fail(ctx, PG_ERR_TIMEOUT, "%s: a bounded device wait expired (block %lld)",
+                           where, info);
         case DERR_NO_SLOT:
             return pg_fail(ctx, PG_ERR_CAPACITY,
                            "%s: connectivity found no reached node with a free slot "
@@ -323,6 +326,7 @@ pg_status pg_data_facts(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_me
     // the norm form |x|^2 + |y|^2 - 2<x,y>.
     double range = (double)mx - (double)mn;
     double lim = 16777216.0;
+    out->bf16_exact = integral && out->max_abs <= 256.f;
     out->exact = metric == PG_METRIC_L2SQ && integral && n > 0 &&
                  (double)d * range * range < lim &&
                  2.0 * (double)d * (double)out->max_abs * (double)out->max_abs < lim;

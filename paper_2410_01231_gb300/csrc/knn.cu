@@ -333,10 +333,18 @@ __global__ void k_knn_fix(const float *__restrict__ Q, const float *__restrict__
     }
 }
 
+}  // namespace
+
+bool pg_knn_tc_supported(int d, int K);
+pg_status pg_knn_tc(pg_ctx *ctx, const float *D, int64_t n, int32_t d, const float *Q, int64_t nq,
+                    int self, int32_t K, const float *xnorm, const float *qnorm, int32_t *ids,
+                    float *dist);
+
+namespace {
+
 pg_status knn_core(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
                    const float *Q, int64_t nq, int self, int32_t K, pg_precision precision,
                    int32_t *ids, float *dist) {
-    (void)precision;
     if (!D || !ids || !dist || (!Q && !self)) return pg_fail(ctx, PG_ERR_INVALID_ARG, "null pointer");
     if (n < 1 || nq < 0 || d < 4 || d % 4 || d > 8192)
         return pg_fail(ctx, PG_ERR_INVALID_ARG, "knn: need n >= 1, d % 4 == 0, 4 <= d <= 8192");
@@ -362,6 +370,11 @@ pg_status knn_core(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric 
         PG_LAUNCHED(ctx);
         qnp = qn.p;
     }
+    // BF16 tiles on the tensor cores when the BF16 copy and every partial
+    // sum are exact (integer data): the result equals the FP32 form's
+    if (precision == PG_PREC_BF16_SCREEN && metric == PG_METRIC_L2SQ && facts.exact &&
+        facts.bf16_exact && pg_knn_tc_supported(d, K))
+        return pg_knn_tc(ctx, D, n, d, self ? nullptr : Q, nq, self, K, xn.p, qnp, ids, dist);
     // rows hold Kx entries when ties must be resolved in FP64 afterwards
     int64_t avail = self ? n - 1 : n;
     int Kx = facts.exact ? K : (int)std::min<int64_t>((int64_t)K + 8, KMAX);
@@ -413,8 +426,9 @@ extern "C" pg_status pg_build_knn(pg_ctx *ctx, const float *D, int64_t n, int32_
 
 extern "C" pg_status pg_knn_query(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
                                   pg_metric metric, const float *Q, int64_t nq, int32_t k,
-                                  int32_t *ids, float *dist) {
+                                  pg_precision precision, int32_t *ids, float *dist) {
     if (!ctx) return PG_ERR_INVALID_ARG;
-    PG_TRY(knn_core(ctx, D, n, d, metric, Q, nq, 0, k, PG_PREC_FP32, ids, dist));
+    if (!Q) return pg_fail(ctx, PG_ERR_INVALID_ARG, "null Q");
+    PG_TRY(knn_core(ctx, D, n, d, metric, Q, nq, 0, k, precision, ids, dist));
     return pg_sync_check(ctx, "pg_knn_query");
 }

@@ -1,0 +1,482 @@
+// knn_tc.cu -- exact kNN distance tiles on the 5th-generation tensor cores
+// (tcgen05, sm_103a) with a fused per-row top-K.
+//
+// s(q, x) = |q|^2 + |x|^2 - 2<q, x>, the dot products on tcgen05.mma
+// kind::f16 (BF16 inputs, FP32 accumulation in TMEM).  Used when every value
+// of D is an integer of magnitude <= 256 and every partial sum stays below
+// 2^24: then the BF16 copy is exact and the tensor-core sums are exact
+// integers, so the result equals the FP32 and FP64 definitions bit for bit.
+//
+// CTA = 6 warps.  Warp 0 issues TMA loads (128B-swizzled K-major tiles):
+// the 128-row query tile once, then 128-row candidate tiles through a
+// 3-stage ring.  Warp 1 owns the TMEM allocation and issues the MMAs
+// (M128 N128 K16 steps) into a double-buffered FP32 accumulator (2 x 128
+// columns).  Warps 2-5 are the epilogue: thread t of the four owns query
+// row t; it reads its accumulator row with tcgen05.ld.32x32b.x32, screens
+// 32 columns at a time by their minimum against its current K-th distance
+// and keeps a private sorted top-K list in shared memory.  Every mbarrier
+// wait is bounded by a deadline; on expiry the kernel records an error,
+// drains its outstanding MMAs, frees TMEM and returns.
+#include <cuda.h>
+
+#include <climits>
+
+#include "pg_internal.cuh"
+
+namespace {
+
+constexpr int TM = 128;       // query rows per CTA = TMEM lanes
+constexpr int TN = 128;       // candidate columns per tile
+constexpr int STAGES = 3;     // candidate-tile ring
+constexpr int KTC = 64;       // largest K of this kernel
+constexpr int NTHREADS = 192;
+constexpr int ACC_COLS = 256;  // two accumulator buffers of TN columns
+
+// Instruction descriptor of tcgen05.mma kind::f16: D = F32 (bits 4-5),
+// A = B = BF16 (bits 7-9, 10-12), both K-major (bits 15, 16 = 0),
+// N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
+                           ((uint32_t)(TM >> 4) << 24);
+
+__device__ __forceinline__ uint32_t saddr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(saddr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase of `parity` to complete; false once the CTA aborted or
+// the 2-second deadline passed (which aborts the CTA and records the error).
+// `backoff` threads (the single-thread producer and MMA roles) sleep between
+// polls so that they leave issue slots to the epilogue warps.
+__device__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort, int *err,
+                          bool backoff = false) {
+    const uint64_t t0 = gtimer();
+    for (uint32_t it = 0;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (backoff) __nanosleep(64);
+        if ((it & 63) == 63) {
+            if (*abort) return false;
+            if (gtimer() - t0 > 2000000000ull) {
+                *abort = 1;
+                record_error(err, DERR_TIMEOUT, (long long)blockIdx.x);
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x,
+                                            int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(saddr(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(saddr(bar))
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (SBO); start address >> 4 in bits 0-13, LBO at 16-29
+// (unused for swizzled K-major), SBO at 32-45, fixed 0b001 at 46-48,
+// swizzle mode 2 (128B) at 61-63.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t a) {
+    uint64_t d = (uint64_t)((a & 0x3FFFF) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(dtmem),
+        "l"(ad), "l"(bd), "r"(IDESC), "r"(acc));
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            saddr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+        "%28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ void epi_barrier() {
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+}
+
+// Warp-cooperative sorted insertion of (s, col) into the list of `row`
+// (stored contiguously, KTC entries, `cnt` of them valid).  Columns arrive
+// in increasing order, so an equal distance already listed stays first.
+// The caller guarantees s is below the list's K-th entry when the list is
+// full.  Returns the new threshold: the K-th distance once full, +inf before.
+__device__ __noinline__ float warp_insert(float *Ls, int *Li, int row, int K, int cnt, float s,
+                                          int col) {
+    const int lane = threadIdx.x & 31;
+    float *rs = Ls + row * KTC;
+    int *ri = Li + row * KTC;
+    const bool v0 = lane < cnt, v1 = lane + 32 < cnt;
+    const float e0 = v0 ? rs[lane] : INFINITY, e1 = v1 ? rs[lane + 32] : INFINITY;
+    const int i0 = v0 ? ri[lane] : 0, i1 = v1 ? ri[lane + 32] : 0;
+    const int p = __popc(__ballot_sync(0xffffffffu, v0 && e0 <= s)) +
+                  __popc(__ballot_sync(0xffffffffu, v1 && e1 <= s));
+    __syncwarp();
+    if (v0 && lane >= p && lane + 1 < K) {
+        rs[lane + 1] = e0;
+        ri[lane + 1] = i0;
+    }
+    if (v1 && lane + 32 >= p && lane + 33 < K) {
+        rs[lane + 33] = e1;
+        ri[lane + 33] = i1;
+    }
+    __syncwarp();
+    if (lane == 0) {
+        rs[p] = s;
+        ri[p] = col;
+    }
+    __syncwarp();
+    return cnt + 1 >= K ? rs[K - 1] : INFINITY;
+}
+
+struct TcLayout {
+    uint32_t a, b, ls, li, nbuf, bars, misc, total;
+};
+
+__host__ __device__ inline TcLayout tc_layout(int dp) {
+    TcLayout L;
+    uint32_t o = 0;
+    L.a = o;
+    o += (uint32_t)TM * dp * 2;
+    L.b = o;
+    o += (uint32_t)STAGES * TN * dp * 2;
+    L.ls = o;  // [row][KTC] distances of each row's list
+    o += (uint32_t)KTC * TM * 4;
+    L.li = o;  // [row][KTC] ids
+    o += (uint32_t)KTC * TM * 4;
+    L.nbuf = o;
+    o += 2 * TN * 4;
+    L.bars = o;
+    o += 16 * 8;
+    L.misc = o;
+    o += 16;
+    L.total = o;
+    return L;
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUtensorMap mapX,
+         int64_t nq, int64_t n, int dp, const float *__restrict__ qnorm,
+         const float *__restrict__ xnorm, int K, int self_exclude, int32_t *__restrict__ out_i,
+         float *__restrict__ out_s, int *err) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *sm = reinterpret_cast<uint8_t *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const TcLayout Ly = tc_layout(dp);
+    uint8_t *A = sm + Ly.a;
+    uint8_t *B = sm + Ly.b;
+    float *Ls = reinterpret_cast<float *>(sm + Ly.ls);
+    int *Li = reinterpret_cast<int *>(sm + Ly.li);
+    float *nbuf = reinterpret_cast<float *>(sm + Ly.nbuf);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + Ly.bars);
+    uint64_t *a_full = bars, *b_full = bars + 1, *b_empty = bars + 1 + STAGES;
+    uint64_t *acc_full = bars + 1 + 2 * STAGES, *acc_empty = bars + 3 + 2 * STAGES;
+    uint64_t *drain = bars + 5 + 2 * STAGES;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + Ly.misc);
+    volatile int *abort = reinterpret_cast<volatile int *>(sm + Ly.misc + 4);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t row0 = (int64_t)blockIdx.x * TM;
+    const int nkb = dp / 64;
+    const int ntiles = (int)((n + TN - 1) / TN);
+    const uint32_t a_bytes = (uint32_t)TM * dp * 2, b_bytes = (uint32_t)TN * dp * 2;
+
+    if (threadIdx.x == 0) {
+        mbar_init(a_full, 1);
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(b_full + s, 1);
+            mbar_init(b_empty + s, 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(acc_full + a, 1);
+            mbar_init(acc_empty + a, 128);
+        }
+        mbar_init(drain, 1);
+        *abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         saddr(tmem_slot)),
+                     "r"(ACC_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {  // ---------------- TMA producer
+            mbar_expect_tx(a_full, a_bytes);
+            for (int kb = 0; kb < nkb; ++kb)
+                tma_load_2d(A + kb * TM * 128, &mapQ, a_full, kb * 64, (int)row0);
+            int issued = 0;
+            for (int t = 0; t < ntiles; ++t) {
+                const int s = t % STAGES;
+                if (!mbar_wait(b_empty + s, ((t / STAGES) & 1) ^ 1, abort, err, true)) break;
+                mbar_expect_tx(b_full + s, b_bytes);
+                for (int kb = 0; kb < nkb; ++kb)
+                    tma_load_2d(B + (size_t)s * TN * dp * 2 + kb * TN * 128, &mapX, b_full + s,
+                                kb * 64, t * TN);
+                issued = t + 1;
+            }
+            if (*abort) {  // let the copies already issued land before TMEM is freed
+                for (int t = max(0, issued - STAGES); t < issued; ++t) {
+                    uint64_t t0 = gtimer();
+                    while (!mbar_try_wait(b_full + t % STAGES, (t / STAGES) & 1) &&
+                           gtimer() - t0 < 1000000000ull) {
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {  // ---------------- MMA issuer
+            bool ok = mbar_wait(a_full, 0, abort, err, true);
+            int t = 0;
+            for (; ok && t < ntiles; ++t) {
+                const int s = t % STAGES, a = t & 1;
+                if (!mbar_wait(b_full + s, (t / STAGES) & 1, abort, err, true)) break;
+                if (!mbar_wait(acc_empty + a, ((t >> 1) & 1) ^ 1, abort, err, true)) break;
+                tc_fence_after();
+                const uint32_t a0 = saddr(A), b0 = saddr(B + (size_t)s * TN * dp * 2);
+                for (int k = 0; k < dp / 16; ++k) {
+                    const int kb = k >> 2, koff = (k & 3) * 32;
+                    umma_bf16(tmem + a * TN, sw128_desc(a0 + kb * TM * 128 + koff),
+                              sw128_desc(b0 + kb * TN * 128 + koff), k > 0 ? 1u : 0u);
+                }
+                umma_commit(b_empty + s);
+                umma_commit(acc_full + a);
+            }
+            // every MMA issued above has completed once `drain` flips
+            umma_commit(drain);
+            uint64_t t0 = gtimer();
+            while (!mbar_try_wait(drain, 0) && gtimer() - t0 < 1000000000ull) {
+            }
+        }
+    } else {  // ---------------------------------------- epilogue
+        const int q = warp & 3;
+        const int row = q * 32 + lane;
+        const int64_t g = row0 + row;
+        const bool live = g < nq;
+        const float nqr = live ? qnorm[g] : 0.f;
+        int count = 0;
+        float thr = INFINITY;
+        for (int t = 0; t < ntiles; ++t) {
+            const int a = t & 1;
+            const int64_t colbase = (int64_t)t * TN;
+            {
+                const int64_t c = colbase + row;
+                nbuf[a * TN + row] = c < n ? xnorm[c] : INFINITY;
+            }
+            mbar_wait(acc_full + a, (t >> 1) & 1, abort, err);
+            epi_barrier();
+            if (*abort) break;
+            tc_fence_after();
+            const float4 *nb4 = reinterpret_cast<const float4 *>(nbuf + a * TN);
+#pragma unroll 1
+            for (int c = 0; c < TN / 32; ++c) {
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * TN + c * 32), v);
+                float nbv[32];
+#pragma unroll
+                for (int j4 = 0; j4 < 8; ++j4) {
+                    const float4 t4 = nb4[c * 8 + j4];
+                    nbv[j4 * 4 + 0] = t4.x;
+                    nbv[j4 * 4 + 1] = t4.y;
+                    nbv[j4 * 4 + 2] = t4.z;
+                    nbv[j4 * 4 + 3] = t4.w;
+                }
+                float m = INFINITY;
+#pragma unroll
+                for (int j = 0; j < 32; ++j) m = fminf(m, fmaf(-2.f, v[j], nbv[j]));
+                // rare: some row of this warp accepts a column of the chunk; the
+                // warp then inserts every accepted (row, column) cooperatively,
+                // columns in increasing order
+                if (!__any_sync(0xffffffffu, live && nqr + m < thr)) continue;
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const float s = fmaxf(nqr + fmaf(-2.f, v[j], nbv[j]), 0.f);
+                    const int64_t col = colbase + c * 32 + j;
+                    const bool acc = live && s < thr && col < n && !(self_exclude && col == g);
+                    unsigned bal = __ballot_sync(0xffffffffu, acc);
+                    while (bal) {
+                        const int L = __ffs(bal) - 1;
+                        bal &= bal - 1;
+                        const float sL = __shfl_sync(0xffffffffu, s, L);
+                        const int cL = __shfl_sync(0xffffffffu, count, L);
+                        const float nt = warp_insert(Ls, Li, q * 32 + L, K, cL, sL, (int)col);
+                        if (lane == L) {
+                            count = min(count + 1, K);
+                            thr = nt;
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(acc_empty + a);
+        }
+        // the warp writes its 32 rows' lists (coalesced along each row)
+        for (int rr = 0; rr < 32; ++rr) {
+            const int r2 = q * 32 + rr;
+            const int64_t g2 = row0 + r2;
+            const int cnt2 = __shfl_sync(0xffffffffu, count, rr);
+            if (g2 >= nq) continue;
+            for (int j = lane; j < K; j += 32) {
+                out_i[g2 * K + j] = j < cnt2 ? Li[r2 * KTC + j] : -1;
+                out_s[g2 * K + j] = j < cnt2 ? Ls[r2 * KTC + j] : INFINITY;
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(ACC_COLS)
+                     : "memory");
+    }
+}
+
+// FP32 rows -> BF16 rows padded with zeros to dp columns
+__global__ void k_to_bf16(const float *__restrict__ X, int64_t n, int d, int dp,
+                          __nv_bfloat16 *__restrict__ out) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * dp) return;
+    int64_t r = t / dp;
+    int c = (int)(t % dp);
+    out[t] = __float2bfloat16_rn(c < d ? X[r * d + c] : 0.f);
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+pg_status make_map(pg_ctx *ctx, CUtensorMap *map, const __nv_bfloat16 *base, int64_t rows, int dp) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return pg_fail(ctx, PG_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+    cuuint64_t dims[2] = {(cuuint64_t)dp, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)dp * 2};
+    cuuint32_t box[2] = {64, 128};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)base, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return pg_fail(ctx, PG_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return PG_OK;
+}
+
+}  // namespace
+
+bool pg_knn_tc_supported(int d, int K) {
+    int dp = (d + 63) / 64 * 64;
+    return dp <= 256 && K >= 1 && K <= KTC && tc_layout(dp).total + 1024 <= 227 * 1024;
+}
+
+// Exact kNN of Q (or of D itself when self) on the tensor cores; the caller
+// guarantees BF16-exact integer data.  xnorm/qnorm are FP32 squared norms.
+pg_status pg_knn_tc(pg_ctx *ctx, const float *D, int64_t n, int32_t d, const float *Q, int64_t nq,
+                    int self, int32_t K, const float *xnorm, const float *qnorm, int32_t *ids,
+                    float *dist) {
+    const int dp = (d + 63) / 64 * 64;
+    Scratch<__nv_bfloat16> xb, qb;
+    PG_TRY(xb.alloc(ctx, (size_t)(n * dp)));
+    k_to_bf16<<<(unsigned)((n * dp + 255) / 256), 256, 0, ctx->stream>>>(D, n, d, dp, xb.p);
+    PG_LAUNCHED(ctx);
+    const __nv_bfloat16 *qp = xb.p;
+    if (!self) {
+        PG_TRY(qb.alloc(ctx, (size_t)(nq * dp)));
+        k_to_bf16<<<(unsigned)((nq * dp + 255) / 256), 256, 0, ctx->stream>>>(Q, nq, d, dp, qb.p);
+        PG_LAUNCHED(ctx);
+        qp = qb.p;
+    }
+    CUtensorMap mq, mx;
+    PG_TRY(make_map(ctx, &mx, xb.p, n, dp));
+    PG_TRY(make_map(ctx, &mq, qp, self ? n : nq, dp));
+    const size_t smem = tc_layout(dp).total + 1024;
+    PG_TRY_CUDA(ctx, cudaFuncSetAttribute(k_knn_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem));
+    const unsigned grid = (unsigned)((nq + TM - 1) / TM);
+    pg_timer_begin(ctx, TM_KNN);
+    k_knn_tc<<<grid, NTHREADS, smem, ctx->stream>>>(mq, mx, nq, n, dp, qnorm, xnorm, K, self, ids,
+                                                     dist, ctx->d_err);
+    PG_LAUNCHED(ctx);
+    pg_timer_end(ctx, TM_KNN, 2.0 * (double)nq * (double)n * (double)d);
+    return PG_OK;
+}

@@ -61,7 +61,10 @@ enum {
 };
 
 // device error codes (first one recorded wins)
-enum { DERR_NONE = 0, DERR_BAD_ID = 1, DERR_CAPACITY = 2, DERR_NO_SLOT = 3, DERR_INTERNAL = 4 };
+enum {
+    DERR_NONE = 0, DERR_BAD_ID = 1, DERR_CAPACITY = 2, DERR_NO_SLOT = 3, DERR_INTERNAL = 4,
+    DERR_TIMEOUT = 5
+};
 
 pg_status pg_fail(pg_ctx *ctx, pg_status st, const char *fmt, ...);
 pg_status pg_cuda_fail(pg_ctx *ctx, cudaError_t e, const char *what);
@@ -129,6 +132,7 @@ pg_status pg_read_counters(pg_ctx *ctx, unsigned long long *host32);
 // sums stay below 2^24), and the largest squared row norm.
 struct DataFacts {
     int exact = 0;
+    int bf16_exact = 0;  // integer rows with |x| <= 256: the BF16 copy is exact
     float max_norm2 = 0.f;
     float max_abs = 0.f;
 };

@@ -71,6 +71,20 @@ def test_knn_matches_oracle(ctx, pg, kind):
         assert (gd == od.astype(np.float32)).all()
 
 
+@pytest.mark.parametrize("n,K", [(2500, 20), (4100, 64), (130, 64)])
+def test_knn_bf16_tensor_cores_match_oracle(ctx, pg, n, K):
+    """BF16 tcgen05 tiles on byte-valued data are exact: equal to the oracle."""
+    D = int_points(n)
+    gi, gd = pg.build_knn(ctx, dev(D), K, precision="bf16")
+    oi, od = oracle.knn(D, K)
+    assert (host(gi) == oi).all()
+    assert (host(gd)[oi >= 0] == od[oi >= 0].astype(np.float32)).all()
+    Q, _ = synthetic.mixture_int(301, 128, 32, 98)
+    qi, qd = pg.knn_query(ctx, dev(D), dev(Q), min(K, 10), precision="bf16")
+    oqi, _ = oracle.knn(D, min(K, 10), Q=Q)
+    assert (host(qi) == oqi).all()
+
+
 def test_knn_queries_and_padding(ctx, pg):
     D = int_points(300)
     Q, _ = synthetic.mixture_int(37, 128, 32, 99)
