@@ -83,6 +83,7 @@ _sig("pg_ctx_set_timing", C.c_int, [P, C.c_int])
 _sig("pg_ctx_kernel_time", C.c_int, [P, C.c_char_p, P, P])
 _sig("pg_ctx_counter", C.c_int, [P, C.c_char_p, P])
 _sig("pg_ctx_kernel_work", C.c_int, [P, C.c_char_p, P])
+_sig("pg_prune_noalloc", C.c_int, [P, P, i64, i32, C.c_int, P, P, i32, dbl, P, P])
 
 EXPORTS = ["pg_default_params", "pg_ctx_create", "pg_ctx_destroy", "pg_last_error", "pg_ctx_sync",
            "pg_ctx_launches", "pg_build_knn", "pg_knn_query", "pg_prune", "pg_reverse_union",
@@ -90,7 +91,7 @@ EXPORTS = ["pg_default_params", "pg_ctx_create", "pg_ctx_destroy", "pg_last_erro
            "pg_build_nswg", "pg_search", "pg_search_host", "pg_index_destroy", "pg_index_info",
            "pg_index_layer", "pg_index_phase_seconds", "pg_index_export_layer",
            "pg_ctx_set_timing", "pg_ctx_kernel_time", "pg_ctx_counter",
-           "pg_ctx_kernel_work"]
+           "pg_ctx_kernel_work", "pg_prune_noalloc"]
 
 
 class PGError(RuntimeError):
@@ -226,6 +227,23 @@ def prune(ctx: Context, D, off, cand, R: int, alpha_deg: float, metric="l2", pre
                              C.byref(ps) if stats else None), "pg_prune")
     if stats:
         return nbr, deg, {k: int(getattr(ps, k)) for k, _ in PruneStats._fields_}
+    return nbr, deg
+
+
+def prune_noalloc(D, off, cand, R: int, alpha_deg: float, metric="l2", stream=None):
+    """pg_prune_noalloc: the pruning step without any device allocation
+    inside the library (fixed scratch; n <= 2^20; synchronous)."""
+    D = _dev(D, torch.float32, "D")
+    off = _dev(off, torch.int64, "off")
+    cand = _dev(cand, torch.int32, "cand")
+    n, d = D.shape
+    nbr = torch.empty((n, R), dtype=torch.int32, device=D.device)
+    deg = torch.empty(n, dtype=torch.int32, device=D.device)
+    s = (stream or torch.cuda.current_stream()).cuda_stream
+    st = _lib.pg_prune_noalloc(C.c_void_p(s), _ptr(D), n, d, METRIC[metric], _ptr(off),
+                               _ptr(cand), R, float(alpha_deg), _ptr(nbr), _ptr(deg))
+    if st != 0:
+        raise PGError(st, "pg_prune_noalloc")
     return nbr, deg
 
 

@@ -490,6 +490,56 @@ pg_status pg_prune_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d, p
     return PG_OK;
 }
 
+// Launch of the pruning kernels on scratch the caller provides (no
+// allocation, no context): ints holds >= n + 4 ints, err 4 ints, counters
+// PG_CNT_SLOTS values.  Used by the allocation-free entry point only.
+cudaError_t pg_prune_launch_on(cudaStream_t stream, int num_sms, const float *D, int64_t n,
+                               int32_t d, pg_metric metric, const int64_t *off,
+                               const int32_t *cand, int32_t R, double alpha_deg,
+                               const DataFacts &facts, int32_t *nbr, int32_t *deg, int *ints,
+                               int *err, unsigned long long *counters) {
+    PruneParams P;
+    P.D = D;
+    P.n = n;
+    P.d = d;
+    P.metric = metric == PG_METRIC_L2SQ ? 0 : 1;
+    P.off = off;
+    P.cand = cand;
+    P.R = R;
+    P.cos_a = std::cos(alpha_deg * M_PI / 180.0);
+    P.cos_af = (float)P.cos_a;
+    P.alpha60 = alpha_deg == 60.0;
+    P.exact = facts.exact;
+    P.em = pg_err_model(metric, d, facts, false);
+    P.nbr = nbr;
+    P.deg = deg;
+    P.err = err;
+    P.counters = counters;
+    P.row_counter = ints;
+    P.long_count = ints + 1;
+    P.long_list = ints + 4;
+    P.cap = CMAX;
+    cudaError_t e = cudaMemsetAsync(ints, 0, 4 * sizeof(int), stream);
+    if (e != cudaSuccess) return e;
+    const size_t smem = warp_smem_bytes(CMAX, d) * PW;
+    e = cudaFuncSetAttribute(k_prune, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int bps = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_prune, PW * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (bps < 1) bps = 1;
+    k_prune<<<num_sms * bps, PW * 32, smem, stream>>>(P);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    P.cap = CMAX_LONG;
+    const size_t smem_long = warp_smem_bytes(CMAX_LONG, d);
+    e = cudaFuncSetAttribute(k_prune_long, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_long);
+    if (e != cudaSuccess) return e;
+    k_prune_long<<<num_sms, 32, smem_long, stream>>>(P);
+    return cudaGetLastError();
+}
+
 static pg_status check_common(pg_ctx *ctx, const float *D, int64_t n, int32_t d) {
     if (!ctx) return PG_ERR_INVALID_ARG;
     if (!D) return pg_fail(ctx, PG_ERR_INVALID_ARG, "null D");
