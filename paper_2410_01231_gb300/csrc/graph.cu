@@ -168,14 +168,16 @@ __device__ void block_bfs_append(const int32_t *nbr, const int32_t *deg, int R, 
     __syncthreads();
     int tail = *s_tail;
     while (head < tail) {
-        for (int i = head + threadIdx.x; i < tail; i += blockDim.x) {
-            int x = queue[i];
-            int dx = min(deg[x], R);
-            for (int j = 0; j < dx; ++j) {
-                int y = nbr[(int64_t)x * R + j];
-                if (y < 0 || y >= n) continue;
-                if (atomicCAS(&reached[y], 0, 1) == 0) queue[atomicAdd(s_tail, 1)] = y;
-            }
+        // one (node, edge) pair per thread, so a frontier of one node still
+        // spreads its R edges over R threads
+        const int pairs = (tail - head) * R;
+        for (int t = threadIdx.x; t < pairs; t += blockDim.x) {
+            const int x = queue[head + t / R];
+            const int j = t % R;
+            if (j >= min(deg[x], R)) continue;
+            const int y = nbr[(int64_t)x * R + j];
+            if (y < 0 || y >= n || reached[y]) continue;
+            if (atomicCAS(&reached[y], 0, 1) == 0) queue[atomicAdd(s_tail, 1)] = y;
         }
         __syncthreads();
         head = tail;
