@@ -38,7 +38,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"],
+                    help="form of the timed build (the other form is timed once beside it)")
+    ap.add_argument("--no-other-form", action="store_true")
     ap.add_argument("--n", type=int, default=None, help="shrink the workload (tests only)")
     ap.add_argument("--nq", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -304,6 +306,27 @@ def run_ours(args):
                 "latency": "single-query requests, host wall time per call incl. launch + sync"}
         idx.close()
 
+    # ------------------------------------------------ the other precision form
+    forms = {args.precision: {"ms_per_build": ms, "points_per_s": value}}
+    identical = None
+    if not args.no_other_form:
+        other = "fp32" if args.precision == "bf16" else "bf16"
+        p2 = dict(params, precision=other)
+        a = pg.Index.build_rng(ctx, Dd, **params)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b = pg.Index.build_rng(ctx, Dd, **p2)
+        e1.record(stream)
+        barrier()
+        t = e0.elapsed_time(e1)
+        forms[other] = {"ms_per_build": t, "points_per_s": n / (t / 1e3)}
+        _, na, da = a.layer(0)
+        _, nb_, db = b.layer(0)
+        identical = bool(torch.equal(na, nb_) and torch.equal(da, db))
+        a.close()
+        b.close()
+
     # ------------------------------------------------------------- e2e
     e2e = None
     if not args.no_e2e:
@@ -364,6 +387,7 @@ def run_ours(args):
                    "R": w["R"], "alpha": [66.0, 60.0], "iters": 2, "route_layers_M": 16,
                    "nq": nq, "k": w["k"], "precision": args.precision,
                    "l2": "inputs larger than L2 (512 MB points)", "parallelism": "replicas"},
+        "forms": forms, "forms_identical_graph": identical,
         "queries": qres, "phase_s": ph,
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
         "kernel_launches_per_step": {k: v[1] / args.steps for k, v in kt.items()},

@@ -102,11 +102,15 @@ def dist(x: np.ndarray, y: np.ndarray, metric: str = "l2") -> float:
     return _get().or_dist(_p(x), _p(y), x.shape[0], METRICS[metric])
 
 
-def knn(D, K: int, metric: str = "l2", Q=None):
-    """Exact K nearest neighbours by (s, id); self excluded when Q is None."""
+def knn(D, K: int, metric: str = "l2", Q=None, rows=None):
+    """Exact K nearest neighbours by (s, id); self excluded when Q is None.
+    With ``rows`` only those points' rows of the graph are computed."""
     D = _f32(D)
     n, d = D.shape
-    if Q is None:
+    if rows is not None:
+        rows = np.ascontiguousarray(rows, np.int64)
+        Qa, excl = np.ascontiguousarray(D[rows]), rows
+    elif Q is None:
         Qa, excl = D, np.arange(n, dtype=np.int64)
     else:
         Qa, excl = _f32(Q), None

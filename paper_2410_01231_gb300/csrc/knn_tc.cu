@@ -14,7 +14,9 @@
 // columns).  Warps 2-5 are the epilogue: thread t of the four owns query
 // row t; it reads its accumulator row with tcgen05.ld.32x32b.x32, screens
 // 32 columns at a time by their minimum against its current K-th distance
-// and keeps a private sorted top-K list in shared memory.  Every mbarrier
+// and keeps a private max-heap of its K best in shared memory (sorted once
+// at the end).  For the graph the points are spatially ordered first, and
+// each CTA scans the tiles around its own rows before the rest.  Every mbarrier
 // wait is bounded by a deadline; on expiry the kernel records an error,
 // drains its outstanding MMAs, frees TMEM and returns.
 #include <cuda.h>
@@ -158,37 +160,84 @@ __device__ __forceinline__ void epi_barrier() {
     asm volatile("bar.sync 1, 128;" ::: "memory");
 }
 
-// Warp-cooperative sorted insertion of (s, col) into the list of `row`
-// (stored contiguously, KTC entries, `cnt` of them valid).  Columns arrive
-// in increasing order, so an equal distance already listed stays first.
-// The caller guarantees s is below the list's K-th entry when the list is
-// full.  Returns the new threshold: the K-th distance once full, +inf before.
-__device__ __noinline__ float warp_insert(float *Ls, int *Li, int row, int K, int cnt, float s,
-                                          int col) {
-    const int lane = threadIdx.x & 31;
-    float *rs = Ls + row * KTC;
-    int *ri = Li + row * KTC;
-    const bool v0 = lane < cnt, v1 = lane + 32 < cnt;
-    const float e0 = v0 ? rs[lane] : INFINITY, e1 = v1 ? rs[lane + 32] : INFINITY;
-    const int i0 = v0 ? ri[lane] : 0, i1 = v1 ? ri[lane + 32] : 0;
-    const int p = __popc(__ballot_sync(0xffffffffu, v0 && e0 <= s)) +
-                  __popc(__ballot_sync(0xffffffffu, v1 && e1 <= s));
-    __syncwarp();
-    if (v0 && lane >= p && lane + 1 < K) {
-        rs[lane + 1] = e0;
-        ri[lane + 1] = i0;
+// Per-row max-heap of the K best (s, id) pairs in shared memory, layout
+// [pos][TM]: element pos of row r at pos * TM + r, so a thread's accesses
+// always fall in its own bank.  The root is the K-th best once the heap is
+// full; thr / thr_id mirror it (+inf / INT_MAX while filling).
+__device__ __forceinline__ void heap_push(float *Hs, int *Hi, int row, int K, int &cnt, float s,
+                                          int id, float &thr, int &thr_id) {
+    int pos;
+    if (cnt < K) {
+        pos = cnt++;
+        while (pos > 0) {
+            const int par = (pos - 1) >> 1;
+            const float ps = Hs[par * TM + row];
+            const int pi = Hi[par * TM + row];
+            if (!pair_less(ps, pi, s, id)) break;
+            Hs[pos * TM + row] = ps;
+            Hi[pos * TM + row] = pi;
+            pos = par;
+        }
+    } else {
+        pos = 0;
+        for (;;) {
+            int c = 2 * pos + 1;
+            if (c >= K) break;
+            float cs = Hs[c * TM + row];
+            int ci = Hi[c * TM + row];
+            if (c + 1 < K) {
+                const float c2 = Hs[(c + 1) * TM + row];
+                const int i2 = Hi[(c + 1) * TM + row];
+                if (pair_less(cs, ci, c2, i2)) {
+                    c = c + 1;
+                    cs = c2;
+                    ci = i2;
+                }
+            }
+            if (!pair_less(s, id, cs, ci)) break;
+            Hs[pos * TM + row] = cs;
+            Hi[pos * TM + row] = ci;
+            pos = c;
+        }
     }
-    if (v1 && lane + 32 >= p && lane + 33 < K) {
-        rs[lane + 33] = e1;
-        ri[lane + 33] = i1;
+    Hs[pos * TM + row] = s;
+    Hi[pos * TM + row] = id;
+    if (cnt == K) {
+        thr = Hs[row];
+        thr_id = Hi[row];
     }
-    __syncwarp();
-    if (lane == 0) {
-        rs[p] = s;
-        ri[p] = col;
+}
+
+// In-place heap sort of a row's heap into ascending (s, id) order.
+__device__ __forceinline__ void heap_sort(float *Hs, int *Hi, int row, int cnt) {
+    for (int end = cnt - 1; end > 0; --end) {
+        const float ts = Hs[end * TM + row];
+        const int ti = Hi[end * TM + row];
+        Hs[end * TM + row] = Hs[row];
+        Hi[end * TM + row] = Hi[row];
+        int pos = 0;
+        for (;;) {
+            int c = 2 * pos + 1;
+            if (c >= end) break;
+            float cs = Hs[c * TM + row];
+            int ci = Hi[c * TM + row];
+            if (c + 1 < end) {
+                const float c2 = Hs[(c + 1) * TM + row];
+                const int i2 = Hi[(c + 1) * TM + row];
+                if (pair_less(cs, ci, c2, i2)) {
+                    c = c + 1;
+                    cs = c2;
+                    ci = i2;
+                }
+            }
+            if (!pair_less(ts, ti, cs, ci)) break;
+            Hs[pos * TM + row] = cs;
+            Hi[pos * TM + row] = ci;
+            pos = c;
+        }
+        Hs[pos * TM + row] = ts;
+        Hi[pos * TM + row] = ti;
     }
-    __syncwarp();
-    return cnt + 1 >= K ? rs[K - 1] : INFINITY;
 }
 
 struct TcLayout {
@@ -202,9 +251,9 @@ __host__ __device__ inline TcLayout tc_layout(int dp) {
     o += (uint32_t)TM * dp * 2;
     L.b = o;
     o += (uint32_t)STAGES * TN * dp * 2;
-    L.ls = o;  // [row][KTC] distances of each row's list
+    L.ls = o;  // [KTC][TM] per-row heaps: distances
     o += (uint32_t)KTC * TM * 4;
-    L.li = o;  // [row][KTC] ids
+    L.li = o;  // [KTC][TM] ids
     o += (uint32_t)KTC * TM * 4;
     L.nbuf = o;
     o += 2 * TN * 4;
@@ -216,11 +265,14 @@ __host__ __device__ inline TcLayout tc_layout(int dp) {
     return L;
 }
 
+// perm (nullable): position -> original id of spatially ordered points (Q
+// is D itself); lists hold original ids, rows are written back in original
+// order.  rotate: scan the tiles around the CTA's rows first.
 __global__ void __launch_bounds__(NTHREADS, 1)
 k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUtensorMap mapX,
          int64_t nq, int64_t n, int dp, const float *__restrict__ qnorm,
          const float *__restrict__ xnorm, int K, int self_exclude, int32_t *__restrict__ out_i,
-         float *__restrict__ out_s, int *err) {
+         float *__restrict__ out_s, int *err, const int32_t *__restrict__ perm, int rotate) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = reinterpret_cast<uint8_t *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const TcLayout Ly = tc_layout(dp);
@@ -241,6 +293,15 @@ k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUten
     const int nkb = dp / 64;
     const int ntiles = (int)((n + TN - 1) / TN);
     const uint32_t a_bytes = (uint32_t)TM * dp * 2, b_bytes = (uint32_t)TN * dp * 2;
+    // With `rotate` (spatially sorted points) the scan first covers a window
+    // of `pre` tiles around the CTA's own rows, where its nearest candidates
+    // are, so the thresholds tighten early; then every other tile in the
+    // common global order, so that concurrent CTAs read the same candidate
+    // tiles at about the same time and share them in L2.  Every role walks
+    // the same order.
+    const int pre = rotate ? min(16, ntiles) : 0;
+    const int w0 = rotate ? max(0, min((int)(row0 / TN) - pre / 2, ntiles - pre)) : 0;
+    auto tile_at = [&](int t) { return t < pre ? w0 + t : (t - pre < w0 ? t - pre : t); };
 
     if (threadIdx.x == 0) {
         mbar_init(a_full, 1);
@@ -280,7 +341,7 @@ k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUten
                 mbar_expect_tx(b_full + s, b_bytes);
                 for (int kb = 0; kb < nkb; ++kb)
                     tma_load_2d(B + (size_t)s * TN * dp * 2 + kb * TN * 128, &mapX, b_full + s,
-                                kb * 64, t * TN);
+                                kb * 64, tile_at(t) * TN);
                 issued = t + 1;
             }
             if (*abort) {  // let the copies already issued land before TMEM is freed
@@ -323,10 +384,11 @@ k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUten
         const bool live = g < nq;
         const float nqr = live ? qnorm[g] : 0.f;
         int count = 0;
-        float thr = INFINITY;
+        float thr = INFINITY;  // the heap's K-th pair once full
+        int thr_id = INT_MAX;
         for (int t = 0; t < ntiles; ++t) {
             const int a = t & 1;
-            const int64_t colbase = (int64_t)t * TN;
+            const int64_t colbase = (int64_t)tile_at(t) * TN;
             {
                 const int64_t c = colbase + row;
                 nbuf[a * TN + row] = c < n ? xnorm[c] : INFINITY;
@@ -352,41 +414,45 @@ k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUten
                 float m = INFINITY;
 #pragma unroll
                 for (int j = 0; j < 32; ++j) m = fminf(m, fmaf(-2.f, v[j], nbv[j]));
-                // rare: some row of this warp accepts a column of the chunk; the
-                // warp then inserts every accepted (row, column) cooperatively,
-                // columns in increasing order
-                if (!__any_sync(0xffffffffu, live && nqr + m < thr)) continue;
+                // rare: this row may accept a column of the chunk (ties with
+                // the K-th distance are decided by id); each thread pushes
+                // into its own row's heap, independently of the other lanes
+                if (!(live && nqr + m <= thr)) continue;
+                float sv[32];
+                unsigned mask = 0;
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
-                    const float s = fmaxf(nqr + fmaf(-2.f, v[j], nbv[j]), 0.f);
+                    sv[j] = fmaxf(nqr + fmaf(-2.f, v[j], nbv[j]), 0.f);
+                    if (sv[j] <= thr) mask |= 1u << j;
+                }
+                while (mask) {
+                    const int j = __ffs(mask) - 1;
+                    mask &= mask - 1;
+                    const float s = sv[j];
+                    if (!(s <= thr)) continue;
                     const int64_t col = colbase + c * 32 + j;
-                    const bool acc = live && s < thr && col < n && !(self_exclude && col == g);
-                    unsigned bal = __ballot_sync(0xffffffffu, acc);
-                    while (bal) {
-                        const int L = __ffs(bal) - 1;
-                        bal &= bal - 1;
-                        const float sL = __shfl_sync(0xffffffffu, s, L);
-                        const int cL = __shfl_sync(0xffffffffu, count, L);
-                        const float nt = warp_insert(Ls, Li, q * 32 + L, K, cL, sL, (int)col);
-                        if (lane == L) {
-                            count = min(count + 1, K);
-                            thr = nt;
-                        }
-                    }
+                    if (col >= n || (self_exclude && col == g)) continue;
+                    const int id = perm ? perm[col] : (int)col;
+                    if (!pair_less(s, id, thr, thr_id)) continue;
+                    heap_push(Ls, Li, row, K, count, s, id, thr, thr_id);
                 }
             }
             tc_fence_before();
             mbar_arrive(acc_empty + a);
         }
-        // the warp writes its 32 rows' lists (coalesced along each row)
+        heap_sort(Ls, Li, row, count);
+        __syncwarp();
+        // the warp writes its 32 rows (coalesced along each row); a permuted
+        // point's row goes back to its original position
         for (int rr = 0; rr < 32; ++rr) {
             const int r2 = q * 32 + rr;
-            const int64_t g2 = row0 + r2;
+            const int64_t gp = row0 + r2;
             const int cnt2 = __shfl_sync(0xffffffffu, count, rr);
-            if (g2 >= nq) continue;
+            if (gp >= nq) continue;
+            const int64_t g2 = perm ? (int64_t)perm[gp] : gp;
             for (int j = lane; j < K; j += 32) {
-                out_i[g2 * K + j] = j < cnt2 ? Li[r2 * KTC + j] : -1;
-                out_s[g2 * K + j] = j < cnt2 ? Ls[r2 * KTC + j] : INFINITY;
+                out_i[g2 * K + j] = j < cnt2 ? Li[j * TM + r2] : -1;
+                out_s[g2 * K + j] = j < cnt2 ? Ls[j * TM + r2] : INFINITY;
             }
         }
     }
@@ -449,13 +515,59 @@ bool pg_knn_tc_supported(int d, int K) {
     return dp <= 256 && K >= 1 && K <= KTC && tc_layout(dp).total + 1024 <= 227 * 1024;
 }
 
+pg_status pg_scan_counts(pg_ctx *ctx, const int32_t *cnt, int64_t n, int64_t *off);
+
+namespace {
+
+__global__ void k_gather_bf16(const __nv_bfloat16 *__restrict__ src, const int32_t *__restrict__ idx,
+                              int64_t m, int dp, __nv_bfloat16 *__restrict__ dst) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nch = dp / 8;  // 16-byte chunks
+    if (t >= m * nch) return;
+    const int64_t r = t / nch, c = t % nch;
+    reinterpret_cast<uint4 *>(dst)[r * nch + c] =
+        reinterpret_cast<const uint4 *>(src)[(int64_t)idx[r] * nch + c];
+}
+
+__global__ void k_gather_f32(const float *__restrict__ src, const int32_t *__restrict__ idx,
+                             int64_t m, float *__restrict__ dst) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < m) dst[t] = src[idx[t]];
+}
+
+__global__ void k_pivot_ids(int32_t *ids, int p, int64_t n) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < p) ids[t] = (int32_t)((int64_t)t * n / p);
+}
+
+__global__ void k_bucket_count(const int32_t *__restrict__ bucket, int64_t n, int32_t *cnt) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) atomicAdd(&cnt[max(bucket[t], 0)], 1);
+}
+
+__global__ void k_bucket_scatter(const int32_t *__restrict__ bucket, int64_t n,
+                                 unsigned long long *cursor, int32_t *perm) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) perm[atomicAdd(&cursor[max(bucket[t], 0)], 1ull)] = (int32_t)t;
+}
+
+}  // namespace
+
 // Exact kNN of Q (or of D itself when self) on the tensor cores; the caller
 // guarantees BF16-exact integer data.  xnorm/qnorm are FP32 squared norms.
+// For the graph (self) the points are first ordered by their nearest of
+// ~n/1024 pivots (a kNN with K = 1 on the same kernel), so that every CTA
+// meets its rows' neighbours in its first tiles; lists hold original ids and
+// rows are written back in original order, so the result does not depend
+// on the order.
 pg_status pg_knn_tc(pg_ctx *ctx, const float *D, int64_t n, int32_t d, const float *Q, int64_t nq,
                     int self, int32_t K, const float *xnorm, const float *qnorm, int32_t *ids,
                     float *dist) {
     const int dp = (d + 63) / 64 * 64;
-    Scratch<__nv_bfloat16> xb, qb;
+    Scratch<__nv_bfloat16> xb, qb, pb, xs;
+    Scratch<int32_t> pid, asg, perm, cnt;
+    Scratch<float> adist, pn, xsn;
+    Scratch<int64_t> boff;
     PG_TRY(xb.alloc(ctx, (size_t)(n * dp)));
     k_to_bf16<<<(unsigned)((n * dp + 255) / 256), 256, 0, ctx->stream>>>(D, n, d, dp, xb.p);
     PG_LAUNCHED(ctx);
@@ -466,16 +578,65 @@ pg_status pg_knn_tc(pg_ctx *ctx, const float *D, int64_t n, int32_t d, const flo
         PG_LAUNCHED(ctx);
         qp = qb.p;
     }
-    CUtensorMap mq, mx;
-    PG_TRY(make_map(ctx, &mx, xb.p, n, dp));
-    PG_TRY(make_map(ctx, &mq, qp, self ? n : nq, dp));
     const size_t smem = tc_layout(dp).total + 1024;
     PG_TRY_CUDA(ctx, cudaFuncSetAttribute(k_knn_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)smem));
+    const int32_t *permp = nullptr;
+    const __nv_bfloat16 *xp = xb.p;
+    const float *xnp = xnorm, *qnp = qnorm;
+    if (self && n >= 16384) {
+        // ---- spatial order: nearest pivot, then a counting sort by pivot
+        const int P = (int)std::min<int64_t>(4096, std::max<int64_t>(64, n / 1024));
+        PG_TRY(pid.alloc(ctx, (size_t)P));
+        PG_TRY(pb.alloc(ctx, (size_t)P * dp));
+        PG_TRY(pn.alloc(ctx, (size_t)P));
+        PG_TRY(asg.alloc(ctx, (size_t)n));
+        PG_TRY(adist.alloc(ctx, (size_t)n));
+        k_pivot_ids<<<(P + 255) / 256, 256, 0, ctx->stream>>>(pid.p, P, n);
+        PG_LAUNCHED(ctx);
+        k_gather_bf16<<<(unsigned)(((int64_t)P * dp / 8 + 255) / 256), 256, 0, ctx->stream>>>(
+            xb.p, pid.p, P, dp, pb.p);
+        PG_LAUNCHED(ctx);
+        k_gather_f32<<<(P + 255) / 256, 256, 0, ctx->stream>>>(xnorm, pid.p, P, pn.p);
+        PG_LAUNCHED(ctx);
+        CUtensorMap mqa, mpa;
+        PG_TRY(make_map(ctx, &mqa, xb.p, n, dp));
+        PG_TRY(make_map(ctx, &mpa, pb.p, P, dp));
+        k_knn_tc<<<(unsigned)((n + TM - 1) / TM), NTHREADS, smem, ctx->stream>>>(
+            mqa, mpa, n, P, dp, xnorm, pn.p, 1, 0, asg.p, adist.p, ctx->d_err, nullptr, 0);
+        PG_LAUNCHED(ctx);
+        PG_TRY(cnt.alloc(ctx, (size_t)P));
+        PG_TRY(boff.alloc(ctx, (size_t)P + 1));
+        PG_TRY(perm.alloc(ctx, (size_t)n));
+        PG_TRY_CUDA(ctx, cudaMemsetAsync(cnt.p, 0, (size_t)P * 4, ctx->stream));
+        const unsigned gn = (unsigned)((n + 255) / 256);
+        k_bucket_count<<<gn, 256, 0, ctx->stream>>>(asg.p, n, cnt.p);
+        PG_LAUNCHED(ctx);
+        PG_TRY(pg_scan_counts(ctx, cnt.p, P, boff.p));
+        k_bucket_scatter<<<gn, 256, 0, ctx->stream>>>(
+            asg.p, n, reinterpret_cast<unsigned long long *>(boff.p), perm.p);
+        PG_LAUNCHED(ctx);
+        PG_TRY(xs.alloc(ctx, (size_t)(n * dp)));
+        PG_TRY(xsn.alloc(ctx, (size_t)n));
+        k_gather_bf16<<<(unsigned)((n * dp / 8 + 255) / 256), 256, 0, ctx->stream>>>(
+            xb.p, perm.p, n, dp, xs.p);
+        PG_LAUNCHED(ctx);
+        k_gather_f32<<<gn, 256, 0, ctx->stream>>>(xnorm, perm.p, n, xsn.p);
+        PG_LAUNCHED(ctx);
+        xb.release();
+        permp = perm.p;
+        xp = xs.p;
+        qp = xs.p;
+        xnp = xsn.p;
+        qnp = xsn.p;
+    }
+    CUtensorMap mq, mx;
+    PG_TRY(make_map(ctx, &mx, xp, n, dp));
+    PG_TRY(make_map(ctx, &mq, qp, self ? n : nq, dp));
     const unsigned grid = (unsigned)((nq + TM - 1) / TM);
     pg_timer_begin(ctx, TM_KNN);
-    k_knn_tc<<<grid, NTHREADS, smem, ctx->stream>>>(mq, mx, nq, n, dp, qnorm, xnorm, K, self, ids,
-                                                     dist, ctx->d_err);
+    k_knn_tc<<<grid, NTHREADS, smem, ctx->stream>>>(mq, mx, nq, n, dp, qnp, xnp, K, self, ids,
+                                                     dist, ctx->d_err, permp, permp ? 1 : 0);
     PG_LAUNCHED(ctx);
     pg_timer_end(ctx, TM_KNN, 2.0 * (double)nq * (double)n * (double)d);
     return PG_OK;
