@@ -246,6 +246,11 @@ def run_ours(args):
     clocks.start()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
+    nvtx = getattr(torch.cuda, "nvtx", None)
+    try:  # names the timed region for profilers (ncu --nvtx-include timed/)
+        nvtx.range_push("timed")
+    except Exception:
+        nvtx = None
     ev0.record(stream)
     phases = []
     for _ in range(args.steps):
@@ -253,6 +258,8 @@ def run_ours(args):
         phases.append(idx.phase_seconds())
         idx.close()
     ev1.record(stream)
+    if nvtx is not None:
+        nvtx.range_pop()
     barrier()
     clk = clocks.stop()
     launches = ctx.launches - launches0
@@ -262,6 +269,8 @@ def run_ours(args):
     kt = {k: ctx.kernel_time(k) for k in ("knn", "prune", "union", "connect", "search", "medoid")}
     conn_edges = ctx.counter("connect_edges")
     conn_full = ctx.counter("connect_full_rounds")
+    work = {c: ctx.counter(c) for c in ("search_expansions", "search_evaluations", "prune_rows",
+                                        "prune_scanned")}
     ctx.set_timing(False)
     if world > 1:
         t = torch.tensor([ms], device="cuda")
@@ -351,21 +360,49 @@ def run_ours(args):
                "d2h_bytes_per_step": int(nbr_h.numel() * 4 + deg_h.numel() * 4)}
 
     # -------------------------------------------------------- roofline
+    # Every figure is algorithmic work over the summed CUDA-event time of the
+    # kernel's launches inside the timed region (base graph and routing
+    # layers).  kNN: 2 d flops per (row, point) pair.  Beam search: one
+    # d-float row per distance evaluation plus one R-entry adjacency row per
+    # expansion.  Prune: one d-float row plus (id, distance) per scanned
+    # candidate, plus the point's own row.
     pk = peaks()
-    sm_mhz = (clk or {}).get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
-    # algorithmic flops of every kNN launch in the timed region (base graph
-    # and routing layers) over their summed device time
-    achieved = knn_work / (knn_ms / 1e3) / 1e12 if knn_ms > 0 else 0.0
-    if args.precision == "fp32":
-        peak = fp32_simt_peak_tflops(pk.get("sm_max_mhz", 2070.0))
-        roof = {"kernel": "k_knn_fp32", "bound": "alu", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+    hbm = pk.get("hbm_gbs", 6800.0)
+    d = w["d"]
+    rooflines = {}
+    if knn_ms > 0:
+        a = knn_work / (knn_ms / 1e3) / 1e12
+        if args.precision == "fp32":
+            peak = fp32_simt_peak_tflops(pk.get("sm_max_mhz", 2070.0))
+            rooflines["knn"] = {
+                "kernel": "k_knn_fp32", "bound": "alu", "achieved": a, "peak": peak,
+                "unit": "TFLOP/s", "frac": a / peak, "traffic": None,
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (derived)"}
-    else:
-        peak = pk.get("bf16_tflops", 1900.0)
-        roof = {"kernel": "knn_bf16", "bound": "tensor", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+        else:
+            peak = pk.get("bf16_tflops", 1900.0)
+            rooflines["knn"] = {
+                "kernel": "k_knn_tc", "bound": "tensor", "achieved": a, "peak": peak,
+                "unit": "TFLOP/s", "frac": a / peak, "traffic": None,
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops (of measured)"}
+    s_ms = kt["search"][0]
+    if s_ms > 0:
+        b = work["search_evaluations"] * d * 4 + work["search_expansions"] * w["R"] * 4
+        a = b / (s_ms / 1e3) / 1e9
+        rooflines["search"] = {
+            "kernel": "k_search", "bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s",
+            "frac": a / hbm, "traffic": None, "algorithmic_bytes_per_step": b / args.steps,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    p_ms = kt["prune"][0]
+    if p_ms > 0:
+        b = work["prune_scanned"] * (d * 4 + 8) + work["prune_rows"] * d * 4
+        a = b / (p_ms / 1e3) / 1e9
+        rooflines["prune"] = {
+            "kernel": "k_prune", "bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s",
+            "frac": a / hbm, "traffic": None, "algorithmic_bytes_per_step": b / args.steps,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    # the dominant single kernel of the step (connect is a chain of kernels)
+    top = max(rooflines, key=lambda k: kt[k][0]) if rooflines else None
+    roof = dict(rooflines[top], share_of_step=kt[top][0] / args.steps / ms) if top else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -386,14 +423,15 @@ def run_ours(args):
         "config": {"workload": w["name"], "n": n, "d": w["d"], "K": w["K"], "L": w["L"],
                    "R": w["R"], "alpha": [66.0, 60.0], "iters": 2, "route_layers_M": 16,
                    "nq": nq, "k": w["k"], "precision": args.precision,
-                   "l2": "inputs larger than L2 (512 MB points)", "parallelism": "replicas"},
+                   "l2": (f"inputs larger than L2 ({D.nbytes >> 20} MB points)" if D.nbytes > 129e6
+                          else f"inputs smaller than L2 ({D.nbytes >> 20} MB points; test size)"), "parallelism": "replicas"},
         "forms": forms, "forms_identical_graph": identical,
         "queries": qres, "phase_s": ph,
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
         "kernel_launches_per_step": {k: v[1] / args.steps for k, v in kt.items()},
         "connect_edges_per_step": conn_edges / max(1, args.steps + args.warmup),
         "connect_full_rounds_per_step": conn_full / max(1, args.steps + args.warmup),
-        "roofline": roof, "clocks": clk, "gpu_launches": launches, "e2e": e2e,
+        "roofline": roof, "rooflines": rooflines, "clocks": clk, "gpu_launches": launches, "e2e": e2e,
         "cpu_baseline": cpu,
     }
     if rank == 0:

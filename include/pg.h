@@ -129,9 +129,14 @@ pg_status pg_ctx_kernel_time(pg_ctx *ctx, const char *name, double *total_ms, in
  * "knn" counts 2*d flops per (query row, point) pair. */
 pg_status pg_ctx_kernel_work(pg_ctx *ctx, const char *name, double *work);
 
-/* Cumulative host-side counters of this context: "connect_edges" (edges
- * added by connectivity steps) and "connect_full_rounds" (connectivity
- * rounds that needed a scan over all points). */
+/* Cumulative counters of this context.  Host side: "connect_edges" (edges
+ * added by connectivity steps), "connect_full_rounds" (connectivity rounds
+ * that needed a scan over all points), "connect_conflicts".  Device side
+ * (reading one synchronises the stream; reset by pg_ctx_set_timing and by
+ * pg_prune with host_stats): "search_expansions" and "search_evaluations"
+ * (nodes expanded / distances evaluated by every beam search, Algorithm 1),
+ * "prune_rows", "prune_candidates", "prune_scanned" (candidates visited by
+ * the Algorithm 3 scan) and "prune_occlusion_tests". */
 pg_status pg_ctx_counter(pg_ctx *ctx, const char *name, int64_t *value);
 
 /* ------------------------------------------------------------------ steps */

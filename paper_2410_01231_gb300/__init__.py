@@ -155,7 +155,9 @@ class Context:
         return v.value
 
     def counter(self, name: str) -> int:
-        """Cumulative counter: "connect_edges" or "connect_full_rounds"."""
+        """Cumulative counter (pg_ctx_counter): "connect_edges", "connect_full_rounds",
+        "connect_conflicts", "search_expansions", "search_evaluations", "prune_rows",
+        "prune_candidates", "prune_scanned", "prune_occlusion_tests"."""
         v = C.c_int64()
         self._check(_lib.pg_ctx_counter(self._h, name.encode(), C.byref(v)), "pg_ctx_counter")
         return v.value

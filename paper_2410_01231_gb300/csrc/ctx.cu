@@ -125,7 +125,8 @@ extern "C" pg_status pg_ctx_set_timing(pg_ctx *ctx, int enable) {
         ctx->timer_launches[i] = 0;
         ctx->timer_work[i] = 0.0;
     }
-    return PG_OK;
+    // the device work counters restart with the timers
+    return pg_reset_counters(ctx);
 }
 
 extern "C" pg_status pg_ctx_kernel_work(pg_ctx *ctx, const char *name, double *work) {
@@ -159,7 +160,23 @@ extern "C" pg_status pg_ctx_counter(pg_ctx *ctx, const char *name, int64_t *valu
     if (strcmp(name, "connect_edges") == 0) *value = ctx->connect_edges;
     else if (strcmp(name, "connect_full_rounds") == 0) *value = ctx->connect_full_rounds;
     else if (strcmp(name, "connect_conflicts") == 0) *value = ctx->connect_why_full;
-    else return pg_fail(ctx, PG_ERR_INVALID_ARG, "unknown counter %s", name);
+    else {
+        static const struct {
+            const char *name;
+            int slot;
+        } dev[] = {{"search_expansions", CNT_SEARCH_EXP}, {"search_evaluations", CNT_SEARCH_EVAL},
+                   {"prune_rows", CNT_ROWS},           {"prune_candidates", CNT_CANDS},
+                   {"prune_scanned", CNT_SCANNED},     {"prune_occlusion_tests", CNT_OCCL}};
+        for (const auto &e : dev) {
+            if (strcmp(name, e.name) == 0) {
+                unsigned long long c[PG_CNT_SLOTS];
+                PG_TRY(pg_read_counters(ctx, c));
+                *value = (int64_t)c[e.slot];
+                return PG_OK;
+            }
+        }
+        return pg_fail(ctx, PG_ERR_INVALID_ARG, "unknown counter %s", name);
+    }
     return PG_OK;
 }
 
