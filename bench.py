@@ -269,8 +269,8 @@ def run_ours(args):
     kt = {k: ctx.kernel_time(k) for k in ("knn", "prune", "union", "connect", "search", "medoid")}
     conn_edges = ctx.counter("connect_edges")
     conn_full = ctx.counter("connect_full_rounds")
-    work = {c: ctx.counter(c) for c in ("search_expansions", "search_evaluations", "prune_rows",
-                                        "prune_scanned")}
+    work = {c: ctx.counter(c) for c in ("search_expansions", "search_evaluations", "search_bytes",
+                                        "prune_rows", "prune_candidates", "prune_bytes")}
     ctx.set_timing(False)
     if world > 1:
         t = torch.tensor([ms], device="cuda")
@@ -362,10 +362,11 @@ def run_ours(args):
     # -------------------------------------------------------- roofline
     # Every figure is algorithmic work over the summed CUDA-event time of the
     # kernel's launches inside the timed region (base graph and routing
-    # layers).  kNN: 2 d flops per (row, point) pair.  Beam search: one
-    # d-float row per distance evaluation plus one R-entry adjacency row per
-    # expansion.  Prune: one d-float row plus (id, distance) per scanned
-    # candidate, plus the point's own row.
+    # layers).  kNN: 2 d flops per (row, point) pair.  Beam search: one data
+    # row per distance evaluation plus one R-entry adjacency row per
+    # expansion.  Prune: one data row plus (id, distance) per examined
+    # candidate, plus the point's own row.  A data row is 4d bytes, d bytes
+    # where the screened form gathers byte rows (counted by the kernels).
     pk = peaks()
     hbm = pk.get("hbm_gbs", 6800.0)
     d = w["d"]
@@ -386,7 +387,7 @@ def run_ours(args):
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops (of measured)"}
     s_ms = kt["search"][0]
     if s_ms > 0:
-        b = work["search_evaluations"] * d * 4 + work["search_expansions"] * w["R"] * 4
+        b = work["search_bytes"]
         a = b / (s_ms / 1e3) / 1e9
         rooflines["search"] = {
             "kernel": "k_search", "bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s",
@@ -394,7 +395,7 @@ def run_ours(args):
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
     p_ms = kt["prune"][0]
     if p_ms > 0:
-        b = work["prune_scanned"] * (d * 4 + 8) + work["prune_rows"] * d * 4
+        b = work["prune_bytes"]
         a = b / (p_ms / 1e3) / 1e9
         rooflines["prune"] = {
             "kernel": "k_prune", "bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s",

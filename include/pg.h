@@ -136,7 +136,11 @@ pg_status pg_ctx_kernel_work(pg_ctx *ctx, const char *name, double *work);
  * pg_prune with host_stats): "search_expansions" and "search_evaluations"
  * (nodes expanded / distances evaluated by every beam search, Algorithm 1),
  * "prune_rows", "prune_candidates", "prune_scanned" (candidates visited by
- * the Algorithm 3 scan) and "prune_occlusion_tests". */
+ * the Algorithm 3 scan), "prune_occlusion_tests", and the algorithmic bytes
+ * "search_bytes" (one data row per evaluation + one adjacency row per
+ * expansion) and "prune_bytes" (one data row + 8 bytes per examined
+ * candidate + the point's own row); a data row is 4d bytes, or d bytes
+ * when the screened form gathers byte rows. */
 pg_status pg_ctx_counter(pg_ctx *ctx, const char *name, int64_t *value);
 
 /* ------------------------------------------------------------------ steps */

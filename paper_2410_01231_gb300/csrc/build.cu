@@ -22,7 +22,8 @@ pg_status pg_knn_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_
                           int32_t K, pg_precision precision, int32_t *ids, float *dist);
 pg_status pg_prune_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
                             const int64_t *off, const int32_t *cand, int32_t R, double alpha_deg,
-                            const DataFacts &facts, int32_t *nbr, int32_t *deg);
+                            const DataFacts &facts, int32_t *nbr, int32_t *deg,
+                            const uint8_t *D8 = nullptr);
 pg_status pg_reverse_union_internal(pg_ctx *ctx, const int32_t *nbr, const int32_t *deg, int64_t n,
                                     int32_t R, int64_t *off, int32_t *ids);
 pg_status pg_medoid_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
@@ -35,7 +36,7 @@ pg_status pg_search_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d, 
                              const int32_t *nbr, const int32_t *deg, int32_t R,
                              const int32_t *rows, const float *Q, int64_t nq,
                              const int32_t *starts, int32_t k, int32_t L, int self,
-                             int32_t *out_i, float *out_s);
+                             int32_t *out_i, float *out_s, const uint8_t *D8 = nullptr);
 
 struct pg_layer {
     int64_t count = 0;
@@ -219,15 +220,18 @@ pg_status iter_nsg(pg_ctx *ctx, const float *X, int64_t m, int32_t d, const pg_b
     k_fill_off<<<g1, 256, 0, ctx->stream>>>(off.p, m, K);
     PG_LAUNCHED(ctx);
     const int32_t *cur = knn_i.p;
+    // the screened form gathers byte rows when the data are exact bytes
+    Scratch<uint8_t> x8;
+    if (pg_u8_usable(facts, p->metric, d, p->precision)) PG_TRY(pg_make_u8(ctx, X, m, d, x8));
     auto refine = [&](double alpha, int do_connect) -> pg_status {
         clk.start(PH_PRUNE);
         PG_TRY(pg_prune_internal(ctx, X, m, d, p->metric, off.p, cur, R, alpha, facts, nbr1.p,
-                                 deg1.p));
+                                 deg1.p, x8.p));
         clk.start(PH_UNION);
         PG_TRY(pg_reverse_union_internal(ctx, nbr1.p, deg1.p, m, R, uoff.p, uids.p));
         clk.start(PH_PRUNE);
         PG_TRY(pg_prune_internal(ctx, X, m, d, p->metric, uoff.p, uids.p, R, alpha, facts, nbr,
-                                 deg));
+                                 deg, x8.p));
         if (do_connect) {
             clk.start(PH_CONNECT);
             PG_TRY(pg_connect_internal(ctx, X, m, d, p->metric, nbr, deg, R, ep, facts, knn_i.p, K,
@@ -240,7 +244,7 @@ pg_status iter_nsg(pg_ctx *ctx, const float *X, int64_t m, int32_t d, const pg_b
         if (!cand.p) PG_TRY(cand.alloc(ctx, (size_t)(m * L)));
         clk.start(PH_ACQUIRE);
         PG_TRY(pg_search_internal(ctx, X, m, d, p->metric, nbr, deg, R, nullptr, nullptr, m,
-                                  nullptr, L, L, 1, cand.p, nullptr));
+                                  nullptr, L, L, 1, cand.p, nullptr, x8.p));
         k_fill_off<<<g1, 256, 0, ctx->stream>>>(off.p, m, L);
         PG_LAUNCHED(ctx);
         cur = cand.p;

@@ -166,7 +166,8 @@ extern "C" pg_status pg_ctx_counter(pg_ctx *ctx, const char *name, int64_t *valu
             int slot;
         } dev[] = {{"search_expansions", CNT_SEARCH_EXP}, {"search_evaluations", CNT_SEARCH_EVAL},
                    {"prune_rows", CNT_ROWS},           {"prune_candidates", CNT_CANDS},
-                   {"prune_scanned", CNT_SCANNED},     {"prune_occlusion_tests", CNT_OCCL}};
+                   {"prune_scanned", CNT_SCANNED},     {"prune_occlusion_tests", CNT_OCCL},
+                   {"search_bytes", CNT_SEARCH_BYTES}, {"prune_bytes", CNT_PRUNE_BYTES}};
         for (const auto &e : dev) {
             if (strcmp(name, e.name) == 0) {
                 unsigned long long c[PG_CNT_SLOTS];
@@ -344,9 +345,32 @@ pg_status pg_data_facts(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_me
     double range = (double)mx - (double)mn;
     double lim = 16777216.0;
     out->bf16_exact = integral && out->max_abs <= 256.f;
+    out->u8_exact = integral && n > 0 && mn >= 0.f && mx <= 255.f;
     out->exact = metric == PG_METRIC_L2SQ && integral && n > 0 &&
                  (double)d * range * range < lim &&
                  2.0 * (double)d * (double)out->max_abs * (double)out->max_abs < lim;
+    return PG_OK;
+}
+
+bool pg_u8_usable(const DataFacts &f, pg_metric metric, int d, pg_precision precision) {
+    return precision == PG_PREC_BF16_SCREEN && metric == PG_METRIC_L2SQ && f.exact && f.u8_exact &&
+           d % 16 == 0;
+}
+
+__global__ void k_to_u8(const float *__restrict__ D, int64_t count, uint8_t *__restrict__ out) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // 4 values per thread
+    if (t * 4 >= count) return;
+    const float4 v = reinterpret_cast<const float4 *>(D)[t];
+    const unsigned w = (unsigned)v.x | ((unsigned)v.y << 8) | ((unsigned)v.z << 16) |
+                       ((unsigned)v.w << 24);
+    reinterpret_cast<unsigned *>(out)[t] = w;
+}
+
+pg_status pg_make_u8(pg_ctx *ctx, const float *D, int64_t n, int32_t d, Scratch<uint8_t> &out) {
+    const int64_t count = n * d;  // d % 16 == 0
+    PG_TRY(out.alloc(ctx, (size_t)count));
+    k_to_u8<<<(unsigned)((count / 4 + 255) / 256), 256, 0, ctx->stream>>>(D, count, out.p);
+    PG_LAUNCHED(ctx);
     return PG_OK;
 }
 

@@ -57,7 +57,7 @@ enum { PG_CNT_SLOTS = 32 };
 enum {
     CNT_ROWS = 0, CNT_CANDS, CNT_SCANNED, CNT_OCCL, CNT_RECHECK, CNT_FLIP, CNT_EDGES, CNT_LONG,
     CNT_LONG_LIST = 16, CNT_KNN_RECHECK = 17, CNT_KNN_UNRESOLVED = 18, CNT_SEARCH_EXP = 19,
-    CNT_SEARCH_EVAL = 20
+    CNT_SEARCH_EVAL = 20, CNT_SEARCH_BYTES = 21, CNT_PRUNE_BYTES = 22
 };
 
 // device error codes (first one recorded wins)
@@ -133,11 +133,19 @@ pg_status pg_read_counters(pg_ctx *ctx, unsigned long long *host32);
 struct DataFacts {
     int exact = 0;
     int bf16_exact = 0;  // integer rows with |x| <= 256: the BF16 copy is exact
+    int u8_exact = 0;    // integer rows in [0, 255]: a byte copy is exact
     float max_norm2 = 0.f;
     float max_abs = 0.f;
 };
 pg_status pg_data_facts(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
                         DataFacts *out);
+
+// Byte shadow of D for the screened (BF16) form: when every FP32 distance is
+// exact and the rows are bytes, the gathers of prune / search read 16-byte
+// chunks of a u8 copy and form the same integer distances with __dp4a.
+// Leaves `out` empty (p == nullptr) when the data do not qualify.
+bool pg_u8_usable(const DataFacts &f, pg_metric metric, int d, pg_precision precision);
+pg_status pg_make_u8(pg_ctx *ctx, const float *D, int64_t n, int32_t d, Scratch<uint8_t> &out);
 
 // Error model of an FP32 distance s computed by the kernels (difference form
 // sum of squares for L2, dot product for the chord).  Bounds the distance
@@ -255,6 +263,71 @@ __device__ __forceinline__ float team8_dist(const float4 *__restrict__ qrow,
     }
     acc = warp_sum8(acc);
     return fmaxf(2.f - 2.f * acc, 0.f);
+}
+
+// Squared L2 distance of two byte rows held as 16-byte chunks, by a team of
+// eight lanes (lane li takes chunks li, li+8, ...); exact integer arithmetic.
+__device__ __forceinline__ unsigned sq_diff_u8(uint4 a, uint4 b, unsigned acc) {
+    unsigned t = __vabsdiffu4(a.x, b.x);
+    acc = __dp4a(t, t, acc);
+    t = __vabsdiffu4(a.y, b.y);
+    acc = __dp4a(t, t, acc);
+    t = __vabsdiffu4(a.z, b.z);
+    acc = __dp4a(t, t, acc);
+    t = __vabsdiffu4(a.w, b.w);
+    return __dp4a(t, t, acc);
+}
+
+__device__ __forceinline__ unsigned team8_sum_u(unsigned v) {
+    v += __shfl_xor_sync(0xffffffffu, v, 4);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    return v;
+}
+
+__device__ __forceinline__ float team8_dist_u8(const uint4 *__restrict__ q, const uint4 *__restrict__ x,
+                                               int nch16, int li) {
+    unsigned acc = 0;
+    for (int c = li; c < nch16; c += 8) acc = sq_diff_u8(q[c], __ldg(x + c), acc);
+    return (float)team8_sum_u(acc);
+}
+
+// Distances of up to 32 byte rows ids[0..cnt) (ids < 0 give +inf) to the
+// byte query q, written to out[0..cnt): four teams of eight lanes, and for
+// rows of at most 128 bytes every row's chunk is requested before the first
+// is used, so one expansion waits for one round trip to memory.
+__device__ __forceinline__ void batch_dist_u8(const uint8_t *__restrict__ D8, int d,
+                                              const uint4 *__restrict__ q, const int *ids, int cnt,
+                                              float *out) {
+    const int lane = threadIdx.x & 31, team = lane >> 3, li = lane & 7;
+    const int nch16 = d >> 4;
+    if (nch16 <= 8) {
+        const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+        const uint4 qa = li < nch16 ? q[li] : z;
+        uint4 r[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int i = k * 4 + team;
+            const int v = i < cnt ? ids[i] : -1;
+            r[k] = (v >= 0 && li < nch16)
+                       ? __ldg(reinterpret_cast<const uint4 *>(D8 + (int64_t)v * d) + li)
+                       : z;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int i = k * 4 + team;
+            const unsigned acc = team8_sum_u(sq_diff_u8(qa, r[k], 0u));
+            if (li == 0 && i < cnt) out[i] = ids[i] >= 0 ? (float)acc : INFINITY;
+        }
+        return;
+    }
+    for (int b0 = 0; b0 < cnt; b0 += 4) {
+        const int i = b0 + team;
+        const int v = i < cnt ? ids[i] : -1;
+        const float s = team8_dist_u8(q, reinterpret_cast<const uint4 *>(D8 + (int64_t)max(v, 0) * d),
+                                      nch16, li);
+        if (li == 0 && i < cnt) out[i] = v >= 0 ? s : INFINITY;
+    }
 }
 
 // In-shared-memory bitonic sort of n (power of two) (key, id) pairs by one

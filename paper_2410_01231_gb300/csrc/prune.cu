@@ -25,6 +25,7 @@ constexpr int RMAX = 64;
 
 struct PruneParams {
     const float *D;
+    const uint8_t *D8;  // byte shadow of D (exact byte data) or nullptr
     int64_t n;
     int d;
     int metric;
@@ -46,10 +47,26 @@ struct PruneParams {
     int cap;             // capacity of this kernel
 };
 
-// shared layout of one warp: cs[cap], ci[cap], runid[cap], c64[cap],
-// kid[RMAX], ks[RMAX], kpos[RMAX], uq[d]
+// shared layout of one warp: c64[cap], cs[cap], ci[cap], runid[cap],
+// kid[RMAX], ks[RMAX], kpos[RMAX], uq[d] (FP32 row, or the byte row)
 __host__ __device__ inline size_t warp_smem_bytes(int cap, int d) {
     return (size_t)cap * (4 + 4 + 4 + 8) + RMAX * (4 + 4 + 4) + (size_t)d * 4 + 64;
+}
+
+// s(v, w) of two byte rows (lane li's chunk of v already in vreg when
+// d <= 128); the kept rows are re-read through L1
+__device__ __forceinline__ float kept_dist_u8(const uint8_t *__restrict__ xv8, uint4 vreg,
+                                              const uint8_t *__restrict__ xw8, int d, int li) {
+    const int nch16 = d >> 4;
+    const uint4 *w16 = reinterpret_cast<const uint4 *>(xw8);
+    if (nch16 <= 8) {
+        const uint4 w = li < nch16 ? __ldg(w16 + li) : make_uint4(0u, 0u, 0u, 0u);
+        return (float)team8_sum_u(sq_diff_u8(vreg, w, 0u));
+    }
+    unsigned acc = 0;
+    for (int c = li; c < nch16; c += 8)
+        acc = sq_diff_u8(__ldg(reinterpret_cast<const uint4 *>(xv8) + c), __ldg(w16 + c), acc);
+    return (float)team8_sum_u(acc);
 }
 
 struct RowStats {
@@ -70,24 +87,45 @@ __device__ void prune_row(const PruneParams &P, int64_t u, const int32_t *cand, 
     float *uq = reinterpret_cast<float *>(kpos + RMAX);
     const int d = P.d, nch = d / 4;
     const float *D = P.D;
+    const uint8_t *D8 = P.D8;
 
-    for (int c = lane; c < nch; c += 32)
-        reinterpret_cast<float4 *>(uq)[c] = __ldg(reinterpret_cast<const float4 *>(D + u * d) + c);
+    if (D8) {
+        for (int c = lane; c < (d >> 4); c += 32)
+            reinterpret_cast<uint4 *>(uq)[c] = __ldg(reinterpret_cast<const uint4 *>(D8 + u * d) + c);
+    } else {
+        for (int c = lane; c < nch; c += 32)
+            reinterpret_cast<float4 *>(uq)[c] = __ldg(reinterpret_cast<const float4 *>(D + u * d) + c);
+    }
     __syncwarp();
 
     // 1. s(u, v) for every candidate; invalid entries sort last
-    for (int64_t base = 0; base < cnt; base += 4) {
-        int64_t j = base + team;
-        int v = j < cnt ? cand[j] : -1;
-        bool ok = v >= 0 && v != u && v < P.n;
-        if (j < cnt && v >= P.n) record_error(P.err, DERR_BAD_ID, u);
-        int row = ok ? v : (int)u;
-        float s = team8_dist(reinterpret_cast<const float4 *>(uq),
-                             reinterpret_cast<const float4 *>(D + (int64_t)row * d), nch, li,
-                             P.metric);
-        if (li == 0 && j < cnt) {
-            cs[j] = ok ? s : INFINITY;
-            ci[j] = ok ? v : INT_MAX;
+    if (D8) {
+        for (int64_t base = 0; base < cnt; base += 32) {
+            const int64_t j = base + lane;
+            int v = j < cnt ? cand[j] : -1;
+            if (j < cnt && v >= P.n) record_error(P.err, DERR_BAD_ID, u);
+            const bool ok = v >= 0 && v != u && v < P.n;
+            if (j < cnt) ci[j] = ok ? v : -1;
+            __syncwarp();
+            batch_dist_u8(D8, d, reinterpret_cast<const uint4 *>(uq), ci + base,
+                          (int)(cnt - base < 32 ? cnt - base : 32), cs + base);
+            __syncwarp();
+            if (j < cnt && ci[j] < 0) ci[j] = INT_MAX;
+        }
+    } else {
+        for (int64_t base = 0; base < cnt; base += 4) {
+            int64_t j = base + team;
+            int v = j < cnt ? cand[j] : -1;
+            bool ok = v >= 0 && v != u && v < P.n;
+            if (j < cnt && v >= P.n) record_error(P.err, DERR_BAD_ID, u);
+            int row = ok ? v : (int)u;
+            float s = team8_dist(reinterpret_cast<const float4 *>(uq),
+                                 reinterpret_cast<const float4 *>(D + (int64_t)row * d), nch, li,
+                                 P.metric);
+            if (li == 0 && j < cnt) {
+                cs[j] = ok ? s : INFINITY;
+                ci[j] = ok ? v : INT_MAX;
+            }
         }
     }
     int P2 = 32;
@@ -180,14 +218,20 @@ __device__ void prune_row(const PruneParams &P, int64_t u, const int32_t *cand, 
         const float suv = cs[j];
         const float euv = P.em.err(suv);
         const float *xv = D + (int64_t)v * d;
+        const uint8_t *xv8 = D8 ? D8 + (int64_t)v * d : nullptr;
+        uint4 vreg = make_uint4(0u, 0u, 0u, 0u);
+        if (D8 && li < (d >> 4) && (d >> 4) <= 8)
+            vreg = __ldg(reinterpret_cast<const uint4 *>(xv8) + li);
         bool occluded = false;
         for (int kb = 0; kb < kept && !occluded; kb += 4) {
             const int t = kb + team;
             const bool active = t < kept;
             const int w = active ? kid[t] : v;
-            const float svw = team8_dist(reinterpret_cast<const float4 *>(xv),
-                                         reinterpret_cast<const float4 *>(D + (int64_t)w * d),
-                                         nch, li, P.metric);
+            const float svw =
+                D8 ? kept_dist_u8(xv8, vreg, D8 + (int64_t)w * d, d, li)
+                   : team8_dist(reinterpret_cast<const float4 *>(xv),
+                                reinterpret_cast<const float4 *>(D + (int64_t)w * d), nch, li,
+                                P.metric);
             bool occ = false;
             if (active && li == 0) {
                 const int wpos = kpos[t];
@@ -213,6 +257,11 @@ __device__ void prune_row(const PruneParams &P, int64_t u, const int32_t *cand, 
                         if (!P.alpha60) {
                             c3 = angle_certain(suw, P.em.err(suw), svw, evw, suv, euv, P.cos_af);
                             if (c3 < 0) {
+                                if (P.exact) {  // the FP32 distances are the exact values
+                                    s64vw = (double)svw;
+                                    s64uv = (double)suv;
+                                    s64uw = (double)suw;
+                                }
                                 if (s64vw < 0.0) s64vw = dist64_rows(xv, D + (int64_t)w * d, d, P.metric);
                                 if (!(s64uv == s64uv)) s64uv = dist64_rows(uq, xv, d, P.metric);
                                 if (!(s64uw == s64uw))
@@ -261,6 +310,10 @@ __device__ void flush_stats(const PruneParams &P, RowStats &st, unsigned long lo
         atomicAdd(P.counters + CNT_FLIP, v[2]);
         atomicAdd(P.counters + CNT_EDGES, st.edges);
         if (lng) atomicAdd(P.counters + CNT_LONG, rows);
+        // algorithmic bytes: each examined candidate's row plus (id, distance),
+        // and the point's own row
+        const unsigned long long row = P.D8 ? (unsigned long long)P.d : 4ull * P.d;
+        atomicAdd(P.counters + CNT_PRUNE_BYTES, st.cands * (row + 8) + rows * row);
     }
 }
 
@@ -442,9 +495,11 @@ pg_status pg_reverse_union_internal(pg_ctx *ctx, const int32_t *nbr, const int32
 
 pg_status pg_prune_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
                             const int64_t *off, const int32_t *cand, int32_t R, double alpha_deg,
-                            const DataFacts &facts, int32_t *nbr, int32_t *deg) {
+                            const DataFacts &facts, int32_t *nbr, int32_t *deg,
+                            const uint8_t *D8) {
     PruneParams P;
     P.D = D;
+    P.D8 = D8;
     P.n = n;
     P.d = d;
     P.metric = metric == PG_METRIC_L2SQ ? 0 : 1;
@@ -500,6 +555,7 @@ cudaError_t pg_prune_launch_on(cudaStream_t stream, int num_sms, const float *D,
                                int *err, unsigned long long *counters) {
     PruneParams P;
     P.D = D;
+    P.D8 = nullptr;
     P.n = n;
     P.d = d;
     P.metric = metric == PG_METRIC_L2SQ ? 0 : 1;
@@ -554,7 +610,6 @@ extern "C" pg_status pg_prune(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
                               double alpha_deg, pg_precision precision, int32_t *nbr,
                               int32_t *deg, pg_prune_stats *host_stats) {
     PG_TRY(check_common(ctx, D, n, d));
-    (void)precision;
     if (!cand_off || !cand_ids || !nbr || !deg)
         return pg_fail(ctx, PG_ERR_INVALID_ARG, "null pointer");
     if (R < 1 || R > RMAX) return pg_fail(ctx, PG_ERR_INVALID_ARG, "need 1 <= R <= %d", RMAX);
@@ -562,9 +617,11 @@ extern "C" pg_status pg_prune(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
         return pg_fail(ctx, PG_ERR_INVALID_ARG, "need 0 <= alpha <= 180");
     DataFacts facts;
     PG_TRY(pg_data_facts(ctx, D, n, d, metric, &facts));
+    Scratch<uint8_t> d8;
+    if (pg_u8_usable(facts, metric, d, precision)) PG_TRY(pg_make_u8(ctx, D, n, d, d8));
     if (host_stats) PG_TRY(pg_reset_counters(ctx));
     PG_TRY(pg_prune_internal(ctx, D, n, d, metric, cand_off, cand_ids, R, alpha_deg, facts, nbr,
-                             deg));
+                             deg, d8.p));
     if (host_stats) {
         unsigned long long c[PG_CNT_SLOTS];
         PG_TRY(pg_read_counters(ctx, c));

@@ -30,6 +30,7 @@ constexpr int SW = 4;  // warps per CTA
 
 struct SearchParams {
     const float *D;
+    const uint8_t *D8;  // byte shadow of D (exact data, self mode) or nullptr
     int64_t n;
     int d;
     int metric;
@@ -86,9 +87,16 @@ __device__ void search_one(const SearchParams &P, int64_t qi, unsigned char *ws,
     float *q = reinterpret_cast<float *>(ni + 32);
     const float4 *q4 = reinterpret_cast<const float4 *>(q);
 
-    const float *qsrc = P.self ? P.D + qi * d : P.Q + qi * d;
-    for (int c = lane; c < nch; c += 32)
-        reinterpret_cast<float4 *>(q)[c] = __ldg(reinterpret_cast<const float4 *>(qsrc) + c);
+    const uint8_t *D8 = P.D8;
+    const uint4 *q16 = reinterpret_cast<const uint4 *>(q);
+    if (D8) {  // self mode: the query is row qi of the byte shadow
+        for (int c = lane; c < (d >> 4); c += 32)
+            reinterpret_cast<uint4 *>(q)[c] = __ldg(reinterpret_cast<const uint4 *>(D8 + qi * d) + c);
+    } else {
+        const float *qsrc = P.self ? P.D + qi * d : P.Q + qi * d;
+        for (int c = lane; c < nch; c += 32)
+            reinterpret_cast<float4 *>(q)[c] = __ldg(reinterpret_cast<const float4 *>(qsrc) + c);
+    }
     for (int h = lane; h < H; h += 32) htab[h] = -1;
     int start = P.self ? (int)qi : P.starts[qi];
     bool bad = start < 0 || start >= P.n;
@@ -97,8 +105,13 @@ __device__ void search_one(const SearchParams &P, int64_t qi, unsigned char *ws,
         start = 0;
     }
     __syncwarp();
-    float s0 = team8_dist(q4, reinterpret_cast<const float4 *>(P.D + (int64_t)start * d), nch, li,
-                          P.metric);
+    float s0;
+    if (D8) {
+        s0 = team8_dist_u8(q16, reinterpret_cast<const uint4 *>(D8 + (int64_t)start * d), d >> 4, li);
+    } else {
+        s0 = team8_dist(q4, reinterpret_cast<const float4 *>(P.D + (int64_t)start * d), nch, li,
+                        P.metric);
+    }
     int size = 1, cursor = 0;
     if (lane == 0) {
         pdA[0] = s0;
@@ -157,12 +170,16 @@ __device__ void search_one(const SearchParams &P, int64_t qi, unsigned char *ws,
             int cnt = __popc(fb);
             if (fresh) ni[__popc(fb & ((1u << lane) - 1))] = v;
             __syncwarp();
-            for (int b0 = 0; b0 < cnt; b0 += 4) {
-                int i = b0 + team;
-                int vv = ni[i < cnt ? i : 0];
-                float s = team8_dist(q4, reinterpret_cast<const float4 *>(P.D + (int64_t)vv * d),
-                                     nch, li, P.metric);
-                if (li == 0 && i < cnt) nd[i] = s;
+            if (D8) {
+                batch_dist_u8(D8, d, q16, ni, cnt, nd);
+            } else {
+                for (int b0 = 0; b0 < cnt; b0 += 4) {
+                    int i = b0 + team;
+                    int vv = ni[i < cnt ? i : 0];
+                    float s = team8_dist(q4, reinterpret_cast<const float4 *>(P.D + (int64_t)vv * d),
+                                         nch, li, P.metric);
+                    if (li == 0 && i < cnt) nd[i] = s;
+                }
             }
             ev += cnt;
             __syncwarp();
@@ -267,8 +284,11 @@ __global__ void __launch_bounds__(SW * 32) k_search(SearchParams P) {
         search_one(P, qi, ws, n_exp, n_eval);
     }
     if (lane == 0) {
+        // algorithmic bytes: one row per evaluation, one adjacency row per expansion
+        const unsigned long long row = P.D8 ? (unsigned long long)P.d : 4ull * P.d;
         atomicAdd(P.counters + CNT_SEARCH_EXP, n_exp);
         atomicAdd(P.counters + CNT_SEARCH_EVAL, n_eval);
+        atomicAdd(P.counters + CNT_SEARCH_BYTES, n_eval * row + n_exp * 4ull * P.R);
     }
 }
 
@@ -278,10 +298,11 @@ pg_status pg_search_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d, 
                              const int32_t *nbr, const int32_t *deg, int32_t R,
                              const int32_t *rows, const float *Q, int64_t nq,
                              const int32_t *starts, int32_t k, int32_t L, int self,
-                             int32_t *out_i, float *out_s) {
+                             int32_t *out_i, float *out_s, const uint8_t *D8) {
     if (nq == 0) return PG_OK;
     SearchParams P;
     P.D = D;
+    P.D8 = self ? D8 : nullptr;
     P.n = n;
     P.d = d;
     P.metric = metric == PG_METRIC_L2SQ ? 0 : 1;
@@ -295,8 +316,11 @@ pg_status pg_search_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d, 
     P.k = k;
     P.L = L;
     P.self = self;
+    // visited-table slots: with byte rows the distances of one expansion
+    // cost one round trip whatever their number, so a smaller table (more
+    // re-evaluations of forgotten nodes, more resident warps) pays off
     int hb = 9;
-    while ((1 << hb) < 8 * L && hb < 12) ++hb;
+    while ((1 << hb) < (D8 && self ? 4 : 8) * L && hb < 12) ++hb;
     P.hbits = hb;
     P.out_i = out_i;
     P.out_s = out_s;
@@ -340,10 +364,15 @@ extern "C" pg_status pg_acquire_candidates(pg_ctx *ctx, const float *D, int64_t 
                                            const int32_t *deg, int32_t R, int32_t L,
                                            pg_precision precision, int32_t *cand) {
     PG_TRY(check_graph_args(ctx, D, n, d, nbr, deg, R, L));
-    (void)precision;
     if (!cand) return pg_fail(ctx, PG_ERR_INVALID_ARG, "null cand");
+    Scratch<uint8_t> d8;
+    if (precision == PG_PREC_BF16_SCREEN) {
+        DataFacts facts;
+        PG_TRY(pg_data_facts(ctx, D, n, d, metric, &facts));
+        if (pg_u8_usable(facts, metric, d, precision)) PG_TRY(pg_make_u8(ctx, D, n, d, d8));
+    }
     PG_TRY(pg_search_internal(ctx, D, n, d, metric, nbr, deg, R, nullptr, nullptr, n, nullptr, L,
-                              L, 1, cand, nullptr));
+                              L, 1, cand, nullptr, d8.p));
     return pg_sync_check(ctx, "pg_acquire_candidates");
 }
 
@@ -358,6 +387,6 @@ extern "C" pg_status pg_search_graph(pg_ctx *ctx, const float *D, int64_t n, int
         return pg_fail(ctx, PG_ERR_INVALID_ARG, "null pointer");
     if (nq < 0 || k < 1 || k > L) return pg_fail(ctx, PG_ERR_INVALID_ARG, "need 1 <= k <= L");
     PG_TRY(pg_search_internal(ctx, D, n, d, metric, nbr, deg, R, rows, Q, nq, starts, k, L, 0,
-                              out_ids, out_dist));
+                              out_ids, out_dist, nullptr));
     return pg_sync_check(ctx, "pg_search_graph");
 }

@@ -128,7 +128,21 @@ def test_prune_bit_exact_given_identical_candidates(ctx, pg, kind, alpha):
     assert st["fp64_flips"] <= st["fp64_rechecks"]
 
 
-def test_prune_long_rows_and_empty_rows(ctx, pg):
+@pytest.mark.parametrize("alpha", [60.0, 66.0, 90.0])
+def test_prune_screened_form_byte_rows_match_oracle(ctx, pg, alpha):
+    """The screened form gathers byte rows (exact byte data); same lists."""
+    D = int_points(2500)
+    ids, _ = oracle.knn(D, 40)
+    off, cand = noisy_candidates(ids, D.shape[0], 8)
+    gn, gdg, st = pg.prune(ctx, dev(D), dev(off), dev(cand), 16, alpha, precision="bf16",
+                           stats=True)
+    on, odg = oracle.prune(D, off, cand, 16, alpha)
+    assert (host(gdg) == odg).all() and (host(gn) == on).all()
+    assert st["edges"] == int(odg.sum())
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_prune_long_rows_and_empty_rows(ctx, pg, precision):
     D = int_points(3000)
     rng = np.random.default_rng(6)
     lens = [0, 1, 300, 2000, 5, 257, 0, 800]
@@ -137,7 +151,8 @@ def test_prune_long_rows_and_empty_rows(ctx, pg):
     off = np.zeros(3001, np.int64)
     off[1:] = np.cumsum([len(r) for r in rows])
     cand = np.concatenate(rows).astype(np.int32)
-    gn, gdg, st = pg.prune(ctx, dev(D), dev(off), dev(cand), 32, 70.0, stats=True)
+    gn, gdg, st = pg.prune(ctx, dev(D), dev(off), dev(cand), 32, 70.0, precision=precision,
+                           stats=True)
     on, odg = oracle.prune(D, off, cand, 32, 70.0)
     assert (host(gn) == on).all() and (host(gdg) == odg).all()
     assert st["long_rows"] == 4
@@ -194,11 +209,12 @@ def _graph(D, metric, R=16, alpha=66.0):
     return nbr, deg
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
 @pytest.mark.parametrize("L", [1, 17, 64, 200])
-def test_acquire_matches_oracle_integer(ctx, pg, L):
+def test_acquire_matches_oracle_integer(ctx, pg, L, precision):
     D = int_points(2500)
     nbr, deg = _graph(D, "l2")
-    cand = pg.acquire_candidates(ctx, dev(D), dev(nbr), dev(deg), L)
+    cand = pg.acquire_candidates(ctx, dev(D), dev(nbr), dev(deg), L, precision=precision)
     ocand = oracle.acquire(D, nbr, deg, L)
     assert (host(cand) == ocand).all()
 
@@ -232,10 +248,11 @@ def _export(idx, i):
     return host(gid), host(nbr), host(deg)
 
 
-def test_build_rng_c1_matches_oracle_and_recall(ctx, pg):
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_build_rng_c1_matches_oracle_and_recall(ctx, pg, precision):
     D, Q, w = synthetic.workload(1)
     p = dict(K=w["K"], L=w["L"], R=w["R"], M=16, alpha_deg=66.0, alpha_final_deg=60.0, iters=2,
-             seed=0)
+             seed=0, precision=precision)
     idx = pg.Index.build_rng(ctx, dev(D), **p)
     onbr, odeg, oep = oracle.build_rng(D, w["K"], w["L"], w["R"], 66.0, 60.0, 2)
     info = idx.info()
