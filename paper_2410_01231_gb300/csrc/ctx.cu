@@ -160,6 +160,7 @@ extern "C" pg_status pg_ctx_counter(pg_ctx *ctx, const char *name, int64_t *valu
     if (strcmp(name, "connect_edges") == 0) *value = ctx->connect_edges;
     else if (strcmp(name, "connect_full_rounds") == 0) *value = ctx->connect_full_rounds;
     else if (strcmp(name, "connect_conflicts") == 0) *value = ctx->connect_why_full;
+    else if (strcmp(name, "connect_free_nodes") == 0) *value = ctx->connect_free;
     else {
         static const struct {
             const char *name;

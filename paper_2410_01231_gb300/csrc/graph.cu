@@ -556,6 +556,333 @@ k_cb_commit(const float *__restrict__ D, int64_t n, int d, int metric, int32_t *
 }
 
 
+
+// ------------------------------------------------- connect, exact data
+// For exact data the rounds of a batch are decided from work done for all
+// of them at once, again reproducing the one-round-at-a-time result:
+//  * the argmin over the nodes reached and free at the batch start, for
+//    every round, by one tensor-core pass over all points (pg_tc_argmin);
+//  * the closure of every round: the nodes BFS from r_i reaches through
+//    nodes unreached at the batch start.  Edges added during the batch start
+//    at reached nodes, so round i's BFS reaches exactly its closure minus
+//    what earlier rounds reached, and the nodes reached after round i are
+//    the batch-start set plus the closures of the committed rounds;
+//  * M[i][j]: the argmin over closure j (free at the batch start) for r_i.
+// One warp then walks the rounds in order: a round whose r lies in a
+// committed closure is skipped; otherwise its candidate is the smaller of
+// the batch-start argmin and M[i][j] over committed j < i.  Only the chosen
+// node's free slot needs checking (every other source is a superset of the
+// current free nodes); when it filled up during the batch, the batch ends
+// there.  A closure longer than CX_C nodes ends the batch after its round,
+// which is then reached by a full BFS.
+constexpr int CX_C = 2048;       // closure capacity per round
+constexpr int CX_H = 4096;       // hash slots of one closure BFS (> CX_C + threads)
+constexpr int CX_PAIRS = 32768;  // closure nodes one round compares against
+
+struct ConnX {
+    int cursor, added, full_rounds, fast_rounds, conflicts, b, big_rounds, nfree;
+    int r[CB_B];
+    int comp_n[CB_B];  // closure sizes; CX_C + 1: overflowed
+    int ready[CB_B];   // the pairwise pass covered this round
+    unsigned long long best[CB_B];
+    unsigned long long M[CB_B][CB_B];
+    unsigned in_comp[CB_B][CB_B / 32];  // bit j of row i: r_i lies in closure j
+};
+
+__global__ void __launch_bounds__(CT) k_cx_select(const int *reached, int64_t n, ConnX *st) {
+    __shared__ int s_wcnt[CT / 32];
+    __shared__ int s_b;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int from = st->cursor;
+    if (tid == 0) s_b = 0;
+    for (int i = tid; i < CB_B; i += CT) {
+        st->best[i] = ~0ull;
+        st->ready[i] = 0;
+        st->comp_n[i] = 0;
+    }
+    __syncthreads();
+    for (int64_t base = from; base < n; base += CT) {
+        if (s_b >= CB_B) break;
+        const int64_t x = base + tid;
+        const bool un = x < n && !reached[x];
+        const unsigned bal = __ballot_sync(0xffffffffu, un);
+        if (lane == 0) s_wcnt[wid] = __popc(bal);
+        __syncthreads();
+        int before = 0, total = 0;
+        for (int w = 0; w < CT / 32; ++w) {
+            const int c = s_wcnt[w];
+            if (w < wid) before += c;
+            total += c;
+        }
+        const int pos = s_b + before + __popc(bal & ((1u << lane) - 1));
+        if (un && pos < CB_B) st->r[pos] = (int)x;
+        __syncthreads();
+        if (tid == 0) s_b = min(CB_B, s_b + total);
+        __syncthreads();
+    }
+    if (tid == 0) {
+        st->b = s_b;
+        if (s_b == 0) st->cursor = (int)n;
+    }
+}
+
+// closure of round blockIdx.x: BFS from r over nodes unreached at the batch
+// start, with an exact hash set in shared memory
+__global__ void __launch_bounds__(256) k_cx_comp(const int32_t *nbr, const int32_t *deg, int R,
+                                                 int64_t n, const int *reached, ConnX *st,
+                                                 int *comp) {
+    __shared__ int set[CX_H];
+    __shared__ int s_tail, s_big;
+    const int i = blockIdx.x, tid = threadIdx.x;
+    if (i >= st->b) return;
+    int *q = comp + (size_t)i * CX_C;
+    volatile int *big = &s_big;
+    for (int h = tid; h < CX_H; h += blockDim.x) set[h] = -1;
+    __syncthreads();
+    const int r = st->r[i];
+    if (tid == 0) {
+        set[((unsigned)r * 2654435761u) >> 20] = r;
+        q[0] = r;
+        s_tail = 1;
+        s_big = 0;
+    }
+    __syncthreads();
+    int head = 0, tail = 1;
+    while (head < tail) {
+        const int pairs = (tail - head) * R;
+        for (int t = tid; t < pairs && !*big; t += blockDim.x) {
+            const int x = q[head + t / R];
+            const int j = t % R;
+            if (j >= min(deg[x], R)) continue;
+            const int y = nbr[(int64_t)x * R + j];
+            if (y < 0 || y >= n || reached[y]) continue;
+            unsigned h = ((unsigned)y * 2654435761u) >> 20;
+            int probe = 0;
+            for (; probe < CX_H; ++probe) {
+                const int old = atomicCAS(&set[h], -1, y);
+                if (old == -1) {
+                    const int pos = atomicAdd(&s_tail, 1);
+                    if (pos < CX_C) q[pos] = y;
+                    else *big = 1;
+                    break;
+                }
+                if (old == y) break;
+                h = (h + 1) & (CX_H - 1);
+            }
+            if (probe == CX_H) *big = 1;
+        }
+        __syncthreads();
+        if (*big) break;
+        head = tail;
+        tail = s_tail;
+        __syncthreads();
+    }
+    if (tid == 0) st->comp_n[i] = (s_big || s_tail > CX_C) ? CX_C + 1 : s_tail;
+}
+
+// M[i][j] and the membership bits of round blockIdx.x
+__global__ void __launch_bounds__(256) k_cx_pair(const float *__restrict__ D, int d, int metric,
+                                                 const int32_t *deg, int R, ConnX *st,
+                                                 const int *comp) {
+    extern __shared__ __align__(16) float px_rv[];  // r_i's vector [d]
+    __shared__ int s_pre[CB_B + 1];
+    __shared__ unsigned long long s_m[CB_B];
+    __shared__ unsigned s_bits[CB_B / 32];
+    __shared__ int s_ok;
+    const int i = blockIdx.x, tid = threadIdx.x, lane = tid & 31, team = tid >> 3, li = lane & 7;
+    if (i >= st->b) return;
+    if (tid == 0) {
+        int acc = 0, ok = 1;
+        for (int j = 0; j < i; ++j) {
+            s_pre[j] = acc;
+            const int c = st->comp_n[j];
+            if (c > CX_C) ok = 0;
+            acc += min(c, CX_C);
+        }
+        s_pre[i] = acc;
+        if (acc > CX_PAIRS) ok = 0;
+        s_ok = ok;
+    }
+    for (int j = tid; j < CB_B; j += blockDim.x) s_m[j] = ~0ull;
+    if (tid < CB_B / 32) s_bits[tid] = 0u;
+    const int r = st->r[i];
+    for (int c = tid; c < d / 4; c += blockDim.x)
+        reinterpret_cast<float4 *>(px_rv)[c] = reinterpret_cast<const float4 *>(D + (int64_t)r * d)[c];
+    __syncthreads();
+    if (!s_ok) {
+        if (tid == 0) st->ready[i] = 0;
+        return;
+    }
+    const int total = s_pre[i], nteam = blockDim.x / 8, nch = d / 4;
+    for (int base = 0; base < total; base += nteam) {
+        const int t = base + team;
+        int j = 0, x = -1;
+        if (t < total) {
+            int lo = 0, hi = i - 1;  // last j with s_pre[j] <= t
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_pre[mid] <= t) lo = mid;
+                else hi = mid - 1;
+            }
+            j = lo;
+            x = comp[(size_t)j * CX_C + (t - s_pre[j])];
+        }
+        const bool cand = x >= 0 && deg[x] < R;
+        if (!__any_sync(0xffffffffu, cand || x == r)) continue;
+        const float s = team8_dist(reinterpret_cast<const float4 *>(px_rv),
+                                   reinterpret_cast<const float4 *>(D + (int64_t)(x >= 0 ? x : r) * d),
+                                   nch, li, metric);
+        if (li != 0 || x < 0) continue;
+        if (x == r) atomicOr(&s_bits[j >> 5], 1u << (j & 31));
+        if (cand) atomicMin(&s_m[j], pack_sid(s, x));
+    }
+    __syncthreads();
+    for (int j = tid; j < i; j += blockDim.x) st->M[i][j] = s_m[j];
+    if (tid < CB_B / 32) st->in_comp[i][tid] = s_bits[tid];
+    if (tid == 0) st->ready[i] = 1;
+}
+
+// the rounds of the batch in order (warp 0), then the edges, the reached
+// marks and, after an overflowed closure, the BFS from its round
+constexpr int CXD = 256;  // threads of the decide CTA
+
+__global__ void __launch_bounds__(CXD)
+k_cx_decide(int32_t *nbr, int32_t *deg, int R, int64_t n, int *reached, int *queue, ConnX *st,
+            const int *comp, int *err) {
+    extern __shared__ __align__(16) unsigned long long sM[];  // [b][CB_B], row i uses j < i
+    __shared__ unsigned s_in[CB_B][CB_B / 32];
+    __shared__ unsigned long long s_best[CB_B];
+    __shared__ int s_r[CB_B], s_cn[CB_B], s_ready[CB_B];
+    __shared__ int s_cp[CB_B], s_cr[CB_B], s_crank[CB_B], s_ci[CB_B];
+    __shared__ int s_nc, s_stop, s_stop_i, s_full, s_tail;
+    const int b = st->b;
+    if (b == 0) return;
+    const int tid = threadIdx.x, lane = tid & 31;
+    for (int t = tid; t < b * CB_B; t += CXD) {
+        const int i = t / CB_B, j = t % CB_B;
+        if (j < i) sM[t] = st->M[i][j];
+    }
+    for (int t = tid; t < b * (CB_B / 32); t += CXD)
+        s_in[t / (CB_B / 32)][t % (CB_B / 32)] = st->in_comp[t / (CB_B / 32)][t % (CB_B / 32)];
+    for (int i = tid; i < b; i += CXD) {
+        s_best[i] = st->best[i];
+        s_r[i] = st->r[i];
+        s_cn[i] = st->comp_n[i];
+        s_ready[i] = st->ready[i];
+    }
+    __syncthreads();
+    if (tid < 32) {
+        unsigned cm0 = 0, cm1 = 0, cm2 = 0, cm3 = 0;
+        int nc = 0, stop = 0, stop_i = b, full = 0;
+        for (int i = 0; i < b; ++i) {
+            if (!s_ready[i]) {
+                stop = 4;
+                stop_i = i;
+                break;
+            }
+            if ((s_in[i][0] & cm0) | (s_in[i][1] & cm1) | (s_in[i][2] & cm2) | (s_in[i][3] & cm3))
+                continue;  // r_i was reached by a committed round
+            unsigned long long c = ~0ull;
+            for (int j = lane; j < i; j += 32) {
+                const unsigned w = j < 32 ? cm0 : j < 64 ? cm1 : j < 96 ? cm2 : cm3;
+                if ((w >> (j & 31)) & 1u) {
+                    const unsigned long long m = sM[i * CB_B + j];
+                    if (m < c) c = m;
+                }
+            }
+            for (int o = 16; o; o >>= 1) {
+                const unsigned long long y = __shfl_xor_sync(0xffffffffu, c, o);
+                if (y < c) c = y;
+            }
+            const bool from_scan = s_best[i] <= c;
+            if (from_scan) c = s_best[i];
+            if (c == ~0ull) {
+                stop = 2;
+                stop_i = i;
+                break;
+            }
+            const int p = (int)(c & 0xffffffffu);
+            int cnt = 0;
+            for (int k = lane; k < nc; k += 32) cnt += s_cp[k] == p;
+            for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+            if (cnt > 0) {  // p took edges earlier in this batch: is a slot left?
+                int dd = 0;
+                if (lane == 0) dd = deg[p];
+                dd = __shfl_sync(0xffffffffu, dd, 0);
+                if (dd + cnt >= R) {
+                    stop = 1;
+                    stop_i = i;
+                    break;
+                }
+            }
+            if (lane == 0) {
+                s_cp[nc] = p;
+                s_cr[nc] = s_r[i];
+                s_crank[nc] = cnt;
+                s_ci[nc] = i;
+            }
+            __syncwarp();
+            ++nc;
+            if (i < 32) cm0 |= 1u << i;
+            else if (i < 64) cm1 |= 1u << (i - 32);
+            else if (i < 96) cm2 |= 1u << (i - 64);
+            else cm3 |= 1u << (i - 96);
+            full += from_scan ? 1 : 0;
+            if (s_cn[i] > CX_C) {  // committed; its closure overflowed
+                stop = 3;
+                stop_i = i;
+                break;
+            }
+        }
+        if (lane == 0) {
+            s_nc = nc;
+            s_stop = stop;
+            s_stop_i = stop_i;
+            s_full = full;
+            s_tail = 0;
+        }
+    }
+    __syncthreads();
+    const int nc = s_nc, stop = s_stop, stop_i = s_stop_i;
+    // edges: the k-th commit to p goes to slot deg0(p) + rank
+    int d0 = 0;
+    if (tid < nc) d0 = deg[s_cp[tid]];
+    __syncthreads();
+    if (tid < nc) {
+        const int p = s_cp[tid];
+        nbr[(int64_t)p * R + d0 + s_crank[tid]] = s_cr[tid];
+        bool last = true;
+        for (int k = tid + 1; k < nc; ++k) last = last && s_cp[k] != p;
+        if (last) deg[p] = d0 + s_crank[tid] + 1;
+    }
+    // reached marks of the committed closures (an overflowed one is left to the BFS)
+    for (int k = 0; k < nc; ++k) {
+        const int i = s_ci[k];
+        const int cn = s_cn[i];
+        if (cn > CX_C) continue;
+        for (int t = tid; t < cn; t += CXD) reached[comp[(size_t)i * CX_C + t]] = 1;
+    }
+    __syncthreads();
+    if (stop == 3) block_bfs_append(nbr, deg, R, n, reached, queue, s_r[stop_i], &s_tail);
+    if (tid == 0) {
+        st->added += nc;
+        st->full_rounds += s_full;
+        st->fast_rounds += nc - s_full;
+        if (stop == 1) st->conflicts += 1;
+        if (stop == 3) st->big_rounds += 1;
+        if (stop == 2) {
+            record_error(err, DERR_NO_SLOT, s_r[stop_i]);
+            st->cursor = (int)n;
+        } else if (stop == 1 || stop == 4) {
+            st->cursor = s_r[stop_i];
+        } else if (stop == 3 && stop_i + 1 < b) {
+            st->cursor = s_r[stop_i + 1];
+        } else {
+            st->cursor = s_r[b - 1] + 1 < n ? s_r[b - 1] + 1 : (int)n;
+        }
+    }
+}
+
 }  // namespace
 
 pg_status pg_medoid_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
@@ -585,6 +912,68 @@ pg_status pg_medoid_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d, 
     PG_TRY(pg_sync_check(ctx, "medoid"));
     *host_ep = h;
     return PG_OK;
+}
+
+// Batches of the exact-data connect (see ConnX); the state starts from the
+// reached set and cursor of `init`.
+static pg_status connect_exact(pg_ctx *ctx, const float *D, int64_t n, int32_t d, int32_t *nbr,
+                               int32_t *deg, int32_t R, int *reached, int *queue,
+                               const ConnState *init, int64_t *host_added) {
+    TcArgmin tc;
+    PG_TRY(pg_tc_argmin_init(ctx, D, n, d, tc));
+    Scratch<ConnX> st;
+    Scratch<int> comp;
+    PG_TRY(st.alloc(ctx, 1));
+    PG_TRY(comp.alloc(ctx, (size_t)CB_B * CX_C));
+    PG_TRY_CUDA(ctx, cudaMemsetAsync(st.p, 0, sizeof(ConnX), ctx->stream));
+    // cursor and free-list length from the common set-up
+    PG_TRY_CUDA(ctx, cudaMemcpyAsync(&st.p->cursor, &init->cursor, sizeof(int),
+                                     cudaMemcpyDeviceToDevice, ctx->stream));
+    PG_TRY_CUDA(ctx, cudaMemcpyAsync(&st.p->nfree, &init->nfree, sizeof(int),
+                                     cudaMemcpyDeviceToDevice, ctx->stream));
+    const size_t smem_pair = (size_t)d * 4;
+    const size_t smem_dec = (size_t)CB_B * CB_B * 8;
+    PG_TRY_CUDA(ctx, cudaFuncSetAttribute(k_cx_decide, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem_dec));
+    const int64_t max_groups = n / 8 + 2;
+    for (int64_t group = 0;; ++group) {
+        if (group > max_groups)
+            return pg_fail(ctx, PG_ERR_INTERNAL, "connect: no progress after %lld batches",
+                           (long long)(group * 8));
+        for (int g = 0; g < 8; ++g) {
+            pg_timer_begin(ctx, TM_CSELECT);
+            k_cx_select<<<1, CT, 0, ctx->stream>>>(reached, n, st.p);
+            PG_LAUNCHED(ctx);
+            pg_timer_end(ctx, TM_CSELECT);
+            pg_timer_begin(ctx, TM_CSCAN);
+            PG_TRY(pg_tc_argmin(ctx, tc, D, st.p->r, &st.p->b, reached, deg, R, st.p->best));
+            pg_timer_end(ctx, TM_CSCAN);
+            pg_timer_begin(ctx, TM_CFAST);
+            k_cx_comp<<<CB_B, 256, 0, ctx->stream>>>(nbr, deg, R, n, reached, st.p, comp.p);
+            PG_LAUNCHED(ctx);
+            k_cx_pair<<<CB_B, 256, smem_pair, ctx->stream>>>(D, d, 0, deg, R, st.p, comp.p);
+            PG_LAUNCHED(ctx);
+            pg_timer_end(ctx, TM_CFAST);
+            pg_timer_begin(ctx, TM_CCOMMIT);
+            k_cx_decide<<<1, CXD, smem_dec, ctx->stream>>>(nbr, deg, R, n, reached, queue, st.p,
+                                                          comp.p, ctx->d_err);
+            PG_LAUNCHED(ctx);
+            pg_timer_end(ctx, TM_CCOMMIT);
+        }
+        int h[8];
+        PG_TRY_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned, st.p, sizeof h, cudaMemcpyDeviceToHost,
+                                         ctx->stream));
+        PG_TRY(pg_sync_check(ctx, "connect"));
+        memcpy(h, ctx->h_pinned, sizeof h);
+        if (h[0] >= n) {
+            if (host_added) *host_added = h[1];
+            ctx->connect_edges += h[1];
+            ctx->connect_full_rounds += h[2];
+            ctx->connect_why_full += h[4];
+            ctx->connect_free += h[7];
+            return PG_OK;
+        }
+    }
 }
 
 pg_status pg_connect_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
@@ -625,6 +1014,11 @@ pg_status pg_connect_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
     }
     k_connect_init<<<1, CT, 0, ctx->stream>>>(n, reached.p, st.p);
     PG_LAUNCHED(ctx);
+    if (metric == PG_METRIC_L2SQ && facts.exact && facts.bf16_exact && pg_tc_argmin_supported(d)) {
+        PG_TRY(connect_exact(ctx, D, n, d, nbr, deg, R, reached.p, queue.p, st.p, host_added));
+        pg_timer_end(ctx, TM_CONNECT);
+        return PG_OK;
+    }
     const ErrModel em = pg_err_model(metric, d, facts, false);
     const int m = metric == PG_METRIC_L2SQ ? 0 : 1;
     const bool exact = facts.exact != 0;
@@ -675,6 +1069,7 @@ pg_status pg_connect_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
             ctx->connect_edges += h[1];
             ctx->connect_full_rounds += h[2];
             ctx->connect_why_full += h[4];
+            ctx->connect_free += h[7];
             break;
         }
     }

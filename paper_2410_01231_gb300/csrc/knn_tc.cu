@@ -467,6 +467,217 @@ k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUten
 }
 
 // FP32 rows -> BF16 rows padded with zeros to dp columns
+
+// ---------------------------------------------------------------------------
+// Split-column argmin on the tensor cores (the free-node scan of the
+// connectivity step).  Every CTA takes the same <= 128 query rows and a
+// contiguous range of candidate tiles; a column c takes part only while
+// reached[c] != 0 and deg[c] < R (a masked column's norm is staged as +inf).
+// Each row's smallest (s, c) of the range goes to best[row] by atomicMin on
+// the key (FP32 bits << 32 | c): s >= 0, so the key order is the (s, id)
+// order.  Same roles, barriers and deadlines as k_knn_tc.
+struct ArgLayout {
+    uint32_t a, b, nbuf, bars, misc, total;
+};
+
+__host__ __device__ inline ArgLayout arg_layout(int dp) {
+    ArgLayout L;
+    uint32_t o = 0;
+    L.a = o;
+    o += (uint32_t)TM * dp * 2;
+    L.b = o;
+    o += (uint32_t)STAGES * TN * dp * 2;
+    L.nbuf = o;
+    o += 2 * TN * 4;
+    L.bars = o;
+    o += 16 * 8;
+    L.misc = o;
+    o += 16;
+    L.total = o;
+    return L;
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+k_argmin_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUtensorMap mapX,
+            const int *__restrict__ nrows_p, int64_t n, int dp, const float *__restrict__ qnorm,
+            const float *__restrict__ xnorm, const int *__restrict__ reached,
+            const int32_t *__restrict__ deg, int R, int tiles_per_cta,
+            unsigned long long *__restrict__ best, int *err) {
+    const int ntiles_all = (int)((n + TN - 1) / TN);
+    const int t0 = blockIdx.x * tiles_per_cta;
+    const int ntiles = min(ntiles_all - t0, tiles_per_cta);
+    const int nrows = *nrows_p;
+    if (ntiles <= 0 || nrows <= 0) return;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *sm = reinterpret_cast<uint8_t *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const ArgLayout Ly = arg_layout(dp);
+    uint8_t *A = sm + Ly.a;
+    uint8_t *B = sm + Ly.b;
+    float *nbuf = reinterpret_cast<float *>(sm + Ly.nbuf);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + Ly.bars);
+    uint64_t *a_full = bars, *b_full = bars + 1, *b_empty = bars + 1 + STAGES;
+    uint64_t *acc_full = bars + 1 + 2 * STAGES, *acc_empty = bars + 3 + 2 * STAGES;
+    uint64_t *drain = bars + 5 + 2 * STAGES;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + Ly.misc);
+    volatile int *abort = reinterpret_cast<volatile int *>(sm + Ly.misc + 4);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nkb = dp / 64;
+    const uint32_t a_bytes = (uint32_t)TM * dp * 2, b_bytes = (uint32_t)TN * dp * 2;
+
+    if (threadIdx.x == 0) {
+        mbar_init(a_full, 1);
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(b_full + s, 1);
+            mbar_init(b_empty + s, 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(acc_full + a, 1);
+            mbar_init(acc_empty + a, 128);
+        }
+        mbar_init(drain, 1);
+        *abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         saddr(tmem_slot)),
+                     "r"(ACC_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {  // ---------------- TMA producer
+            mbar_expect_tx(a_full, a_bytes);
+            for (int kb = 0; kb < nkb; ++kb) tma_load_2d(A + kb * TM * 128, &mapQ, a_full, kb * 64, 0);
+            int issued = 0;
+            for (int t = 0; t < ntiles; ++t) {
+                const int s = t % STAGES;
+                if (!mbar_wait(b_empty + s, ((t / STAGES) & 1) ^ 1, abort, err, true)) break;
+                mbar_expect_tx(b_full + s, b_bytes);
+                for (int kb = 0; kb < nkb; ++kb)
+                    tma_load_2d(B + (size_t)s * TN * dp * 2 + kb * TN * 128, &mapX, b_full + s,
+                                kb * 64, (t0 + t) * TN);
+                issued = t + 1;
+            }
+            if (*abort) {
+                for (int t = max(0, issued - STAGES); t < issued; ++t) {
+                    uint64_t w0 = gtimer();
+                    while (!mbar_try_wait(b_full + t % STAGES, (t / STAGES) & 1) &&
+                           gtimer() - w0 < 1000000000ull) {
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {  // ---------------- MMA issuer
+            bool ok = mbar_wait(a_full, 0, abort, err, true);
+            for (int t = 0; ok && t < ntiles; ++t) {
+                const int s = t % STAGES, a = t & 1;
+                if (!mbar_wait(b_full + s, (t / STAGES) & 1, abort, err, true)) break;
+                if (!mbar_wait(acc_empty + a, ((t >> 1) & 1) ^ 1, abort, err, true)) break;
+                tc_fence_after();
+                const uint32_t a0 = saddr(A), b0 = saddr(B + (size_t)s * TN * dp * 2);
+                for (int k = 0; k < dp / 16; ++k) {
+                    const int kb = k >> 2, koff = (k & 3) * 32;
+                    umma_bf16(tmem + a * TN, sw128_desc(a0 + kb * TM * 128 + koff),
+                              sw128_desc(b0 + kb * TN * 128 + koff), k > 0 ? 1u : 0u);
+                }
+                umma_commit(b_empty + s);
+                umma_commit(acc_full + a);
+            }
+            umma_commit(drain);
+            uint64_t w0 = gtimer();
+            while (!mbar_try_wait(drain, 0) && gtimer() - w0 < 1000000000ull) {
+            }
+        }
+    } else {  // ---------------------------------------- epilogue
+        const int q = warp & 3;
+        const int row = q * 32 + lane;
+        const bool live = row < nrows;
+        const float nqr = live ? qnorm[row] : 0.f;
+        float bs = INFINITY;
+        int bid = INT_MAX;
+        for (int t = 0; t < ntiles; ++t) {
+            const int a = t & 1;
+            const int64_t colbase = (int64_t)(t0 + t) * TN;
+            {
+                const int64_t c = colbase + row;
+                nbuf[a * TN + row] = (c < n && reached[c] && deg[c] < R) ? xnorm[c] : INFINITY;
+            }
+            mbar_wait(acc_full + a, (t >> 1) & 1, abort, err);
+            epi_barrier();
+            if (*abort) break;
+            tc_fence_after();
+#pragma unroll 1
+            for (int c = 0; c < TN / 32; ++c) {
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * TN + c * 32), v);
+                float m = INFINITY;
+#pragma unroll
+                for (int j = 0; j < 32; ++j) m = fminf(m, fmaf(-2.f, v[j], nbuf[a * TN + c * 32 + j]));
+                // columns rise through the range, so a strictly smaller value
+                // is the only way to a new (s, id) minimum
+                if (live && nqr + m < bs) {
+                    int jm = 0;
+#pragma unroll
+                    for (int j = 31; j >= 0; --j)
+                        if (fmaf(-2.f, v[j], nbuf[a * TN + c * 32 + j]) == m) jm = j;
+                    bs = nqr + m;
+                    bid = (int)(colbase + c * 32 + jm);
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(acc_empty + a);
+        }
+        if (live && bid != INT_MAX && !*abort)
+            atomicMin(best + row, ((unsigned long long)__float_as_uint(fmaxf(bs, 0.f)) << 32) |
+                                      (unsigned)bid);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(ACC_COLS)
+                     : "memory");
+    }
+}
+
+// <= 128 rows ids[0..*count) of D to BF16 [128][dp] (zero rows past the
+// count) with their FP32 squared norms; one warp per row
+__global__ void k_tc_gather_rows(const float *__restrict__ D, int d, int dp, const int *ids,
+                                 const int *count, __nv_bfloat16 *__restrict__ out,
+                                 float *__restrict__ norms) {
+    const int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x & 31;
+    if (row >= TM) return;
+    const bool live = row < *count;
+    const float *src = live ? D + (int64_t)ids[row] * d : nullptr;
+    float acc = 0.f;
+    for (int c = lane; c < dp; c += 32) {
+        const float x = live && c < d ? src[c] : 0.f;
+        acc = fmaf(x, x, acc);
+        out[(int64_t)row * dp + c] = __float2bfloat16_rn(x);
+    }
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) norms[row] = acc;
+}
+
+__global__ void k_tc_norms(const float *__restrict__ D, int64_t n, int d, float *__restrict__ out) {
+    const int64_t r = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x & 31;
+    if (r >= n) return;
+    float acc = 0.f;
+    for (int c = lane; c < d; c += 32) acc = fmaf(D[r * d + c], D[r * d + c], acc);
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) out[r] = acc;
+}
+
 __global__ void k_to_bf16(const float *__restrict__ X, int64_t n, int d, int dp,
                           __nv_bfloat16 *__restrict__ out) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -639,5 +850,47 @@ pg_status pg_knn_tc(pg_ctx *ctx, const float *D, int64_t n, int32_t d, const flo
                                                      dist, ctx->d_err, permp, permp ? 1 : 0);
     PG_LAUNCHED(ctx);
     pg_timer_end(ctx, TM_KNN, 2.0 * (double)nq * (double)n * (double)d);
+    return PG_OK;
+}
+
+// ------------------------------------------------ split-column argmin (host)
+bool pg_tc_argmin_supported(int d) {
+    const int dp = (d + 63) / 64 * 64;
+    return dp <= 256 && arg_layout(dp).total + 1024 <= 227 * 1024;
+}
+
+pg_status pg_tc_argmin_init(pg_ctx *ctx, const float *D, int64_t n, int32_t d, TcArgmin &t) {
+    t.n = n;
+    t.d = d;
+    t.dp = (d + 63) / 64 * 64;
+    PG_TRY(t.xb.alloc(ctx, (size_t)(n * t.dp)));
+    PG_TRY(t.xn.alloc(ctx, (size_t)n));
+    PG_TRY(t.qb.alloc(ctx, (size_t)TM * t.dp));
+    PG_TRY(t.qn.alloc(ctx, (size_t)TM));
+    k_to_bf16<<<(unsigned)((n * t.dp + 255) / 256), 256, 0, ctx->stream>>>(D, n, d, t.dp, t.xb.p);
+    PG_LAUNCHED(ctx);
+    k_tc_norms<<<(unsigned)((n + 7) / 8), 256, 0, ctx->stream>>>(D, n, d, t.xn.p);
+    PG_LAUNCHED(ctx);
+    static_assert(sizeof(t.mapx) >= sizeof(CUtensorMap), "tensor map storage");
+    PG_TRY(make_map(ctx, reinterpret_cast<CUtensorMap *>(t.mapx), t.xb.p, n, t.dp));
+    PG_TRY(make_map(ctx, reinterpret_cast<CUtensorMap *>(t.mapq), t.qb.p, TM, t.dp));
+    const size_t smem = arg_layout(t.dp).total + 1024;
+    PG_TRY_CUDA(ctx, cudaFuncSetAttribute(k_argmin_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem));
+    return PG_OK;
+}
+
+pg_status pg_tc_argmin(pg_ctx *ctx, TcArgmin &t, const float *D, const int *ids, const int *count,
+                       const int *reached, const int32_t *deg, int R, unsigned long long *best) {
+    k_tc_gather_rows<<<TM / 8, 256, 0, ctx->stream>>>(D, t.d, t.dp, ids, count, t.qb.p, t.qn.p);
+    PG_LAUNCHED(ctx);
+    const int ntiles = (int)((t.n + TN - 1) / TN);
+    const int grid = std::max(1, std::min(ctx->num_sms, ntiles));
+    const int per = (ntiles + grid - 1) / grid;
+    const size_t smem = arg_layout(t.dp).total + 1024;
+    k_argmin_tc<<<(unsigned)grid, NTHREADS, smem, ctx->stream>>>(
+        *reinterpret_cast<const CUtensorMap *>(t.mapq), *reinterpret_cast<const CUtensorMap *>(t.mapx),
+        count, t.n, t.dp, t.qn.p, t.xn.p, reached, deg, R, per, best, ctx->d_err);
+    PG_LAUNCHED(ctx);
     return PG_OK;
 }

@@ -27,7 +27,8 @@ struct pg_ctx {
     int64_t launches = 0;
     int64_t connect_edges = 0;        // edges added by the connectivity step
     int64_t connect_full_rounds = 0;  // of those, rounds decided by a full scan
-    int64_t connect_why_full = 0;     // full rounds whose reached list members were all full
+    int64_t connect_why_full = 0;     // batches cut short by a candidate that filled up
+    int64_t connect_free = 0;         // nodes with a free slot when connectivity steps began
     // optional CUDA-event timing of named kernels
     int timing = 0;
     struct TimedPair {
@@ -146,6 +147,25 @@ pg_status pg_data_facts(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_me
 // Leaves `out` empty (p == nullptr) when the data do not qualify.
 bool pg_u8_usable(const DataFacts &f, pg_metric metric, int d, pg_precision precision);
 pg_status pg_make_u8(pg_ctx *ctx, const float *D, int64_t n, int32_t d, Scratch<uint8_t> &out);
+
+// Split-column argmin on the tensor cores over the rows of D (BF16-exact
+// integer data): best[i] = min over columns c with reached[c] != 0 and
+// deg[c] < R of key(s(D[ids[i]], D[c]), c) for i < *count (device), where
+// key = FP32 bits << 32 | c; best[] must hold ~0 beforehand.
+struct TcArgmin {
+    Scratch<__nv_bfloat16> xb;  // BF16 copy of D, rows padded to dp
+    Scratch<float> xn;          // squared row norms
+    Scratch<__nv_bfloat16> qb;  // the <= 128 query rows
+    Scratch<float> qn;
+    alignas(64) unsigned char mapx[128];  // CUtensorMap of xb
+    alignas(64) unsigned char mapq[128];  // CUtensorMap of qb
+    int64_t n = 0;
+    int d = 0, dp = 0;
+};
+bool pg_tc_argmin_supported(int d);
+pg_status pg_tc_argmin_init(pg_ctx *ctx, const float *D, int64_t n, int32_t d, TcArgmin &t);
+pg_status pg_tc_argmin(pg_ctx *ctx, TcArgmin &t, const float *D, const int *ids, const int *count,
+                       const int *reached, const int32_t *deg, int R, unsigned long long *best);
 
 // Error model of an FP32 distance s computed by the kernels (difference form
 // sum of squares for L2, dot product for the chord).  Bounds the distance

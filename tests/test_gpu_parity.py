@@ -201,6 +201,45 @@ def test_connect_matches_oracle(ctx, pg, kind):
     assert (host(gn) == on).all() and (host(gdg) == od).all()
 
 
+def _connect_both(ctx, pg, D, nbr, deg, ep):
+    on, od, oadded = oracle.connect(D, nbr, deg, ep)
+    gn, gdg = dev(nbr), dev(deg)
+    gadded = pg.connect(ctx, dev(D), gn, gdg, ep)
+    assert gadded == oadded
+    assert (host(gdg) == od).all() and (host(gn) == on).all()
+    return oadded
+
+
+def test_connect_closure_larger_than_a_batch_buffer(ctx, pg):
+    """One unreached strongly connected half of 3,000 nodes: its round's
+    BFS closure overflows the per-round buffer and is reached by a full BFS."""
+    D = int_points(6000)
+    R = 8
+    nbr = np.full((6000, R), -1, np.int32)
+    deg = np.zeros(6000, np.int32)
+    for u in range(6000):
+        base, m = (0, 3000) if u < 3000 else (3000, 3000)
+        k = u - base
+        nbr[u, :3] = [base + (k + 1) % m, base + (k + 7) % m, base + (k * 13 + 5) % m]
+        deg[u] = 3
+    added = _connect_both(ctx, pg, D, nbr, deg, 0)
+    assert added == 1
+
+
+@pytest.mark.parametrize("R", [2, 4])
+def test_connect_isolated_nodes_fill_their_targets(ctx, pg, R):
+    """2,000 isolated nodes linked one by one: earlier links become targets
+    of later rounds and targets fill up inside a batch."""
+    D = int_points(2100)
+    nbr = np.full((2100, R), -1, np.int32)
+    deg = np.zeros(2100, np.int32)
+    for u in range(100):
+        nbr[u, 0] = (u + 1) % 100
+        deg[u] = 1
+    added = _connect_both(ctx, pg, D, nbr, deg, 0)
+    assert added == 2000
+
+
 # -------------------------------------------------- search / acquisition
 def _graph(D, metric, R=16, alpha=66.0):
     n = D.shape[0]
