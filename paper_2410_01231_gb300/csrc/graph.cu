@@ -565,16 +565,19 @@ k_cb_commit(const float *__restrict__ D, int64_t n, int d, int metric, int32_t *
 //  * the closure of every round: the nodes BFS from r_i reaches through
 //    nodes unreached at the batch start.  Edges added during the batch start
 //    at reached nodes, so round i's BFS reaches exactly its closure minus
-//    what earlier rounds reached, and the nodes reached after round i are
-//    the batch-start set plus the closures of the committed rounds;
-//  * M[i][j]: the argmin over closure j (free at the batch start) for r_i.
-// One warp then walks the rounds in order: a round whose r lies in a
-// committed closure is skipped; otherwise its candidate is the smaller of
-// the batch-start argmin and M[i][j] over committed j < i.  Only the chosen
-// node's free slot needs checking (every other source is a superset of the
-// current free nodes); when it filled up during the batch, the batch ends
-// there.  A closure longer than CX_C nodes ends the batch after its round,
-// which is then reached by a full BFS.
+//    what earlier rounds reached, and the nodes reached before round i are
+//    the batch-start set plus the closures of the committed rounds j < i.
+//    A round j < i that was skipped had r_j inside an earlier committed
+//    closure, which then contains all of closure j; so "committed j < i"
+//    may be read as "every j < i" in both uses below;
+//  * for every round, the argmin over the closures of all earlier rounds
+//    (free at the batch start) and whether r_i lies in one of them.
+// A single thread then walks the rounds in order: a round whose r lies in
+// an earlier closure is skipped; otherwise its node is the smaller of the
+// two argmins.  Only the chosen node's free slot needs checking (both
+// sources cover a superset of the nodes free now); when it filled up during
+// the batch, the batch ends there.  A closure longer than CX_C nodes ends
+// the batch after its round, which is then reached by a full BFS.
 constexpr int CX_C = 2048;       // closure capacity per round
 constexpr int CX_H = 4096;       // hash slots of one closure BFS (> CX_C + threads)
 constexpr int CX_PAIRS = 32768;  // closure nodes one round compares against
@@ -583,10 +586,10 @@ struct ConnX {
     int cursor, added, full_rounds, fast_rounds, conflicts, b, big_rounds, nfree;
     int r[CB_B];
     int comp_n[CB_B];  // closure sizes; CX_C + 1: overflowed
-    int ready[CB_B];   // the pairwise pass covered this round
-    unsigned long long best[CB_B];
-    unsigned long long M[CB_B][CB_B];
-    unsigned in_comp[CB_B][CB_B / 32];  // bit j of row i: r_i lies in closure j
+    int ready[CB_B];   // the closure pass covered this round
+    int skip[CB_B];    // r_i lies in an earlier round's closure
+    unsigned long long best[CB_B];  // argmin over the batch-start reached free nodes
+    unsigned long long cmin[CB_B];  // argmin over the earlier closures' free nodes
 };
 
 __global__ void __launch_bounds__(CT) k_cx_select(const int *reached, int64_t n, ConnX *st) {
@@ -597,7 +600,9 @@ __global__ void __launch_bounds__(CT) k_cx_select(const int *reached, int64_t n,
     if (tid == 0) s_b = 0;
     for (int i = tid; i < CB_B; i += CT) {
         st->best[i] = ~0ull;
+        st->cmin[i] = ~0ull;
         st->ready[i] = 0;
+        st->skip[i] = 0;
         st->comp_n[i] = 0;
     }
     __syncthreads();
@@ -680,194 +685,181 @@ __global__ void __launch_bounds__(256) k_cx_comp(const int32_t *nbr, const int32
     if (tid == 0) st->comp_n[i] = (s_big || s_tail > CX_C) ? CX_C + 1 : s_tail;
 }
 
-// M[i][j] and the membership bits of round blockIdx.x
+// Every (round i, node x of an earlier round's closure) pair, spread over
+// the grid: r_i in a closure marks i skipped; a free x competes for cmin[i].
+// Rounds behind an overflowed closure or past CX_PAIRS nodes are left out
+// (the walk stops before them).
 __global__ void __launch_bounds__(256) k_cx_pair(const float *__restrict__ D, int d, int metric,
                                                  const int32_t *deg, int R, ConnX *st,
                                                  const int *comp) {
-    extern __shared__ __align__(16) float px_rv[];  // r_i's vector [d]
-    __shared__ int s_pre[CB_B + 1];
-    __shared__ unsigned long long s_m[CB_B];
-    __shared__ unsigned s_bits[CB_B / 32];
-    __shared__ int s_ok;
-    const int i = blockIdx.x, tid = threadIdx.x, lane = tid & 31, team = tid >> 3, li = lane & 7;
-    if (i >= st->b) return;
+    __shared__ int s_pre[CB_B + 1];        // closure nodes of rounds < i
+    __shared__ long long s_acc[CB_B + 1];  // pairs of rounds < i
+    __shared__ int s_last;                 // rounds [0, s_last) take part
+    const int tid = threadIdx.x, lane = tid & 31, li = lane & 7;
+    const int b = st->b;
     if (tid == 0) {
-        int acc = 0, ok = 1;
-        for (int j = 0; j < i; ++j) {
-            s_pre[j] = acc;
-            const int c = st->comp_n[j];
-            if (c > CX_C) ok = 0;
-            acc += min(c, CX_C);
+        int pre = 0, last = b;
+        long long acc = 0;
+        for (int i = 0; i < b; ++i) {
+            s_pre[i] = pre;
+            s_acc[i] = acc;
+            if (pre > CX_PAIRS) {
+                last = i;
+                break;
+            }
+            acc += pre;
+            const int c = st->comp_n[i];
+            if (c > CX_C) {  // the walk ends at round i
+                last = i + 1;
+                s_pre[i + 1] = pre;
+                s_acc[i + 1] = acc;
+                break;
+            }
+            pre += c;
         }
-        s_pre[i] = acc;
-        if (acc > CX_PAIRS) ok = 0;
-        s_ok = ok;
+        if (last == b) {
+            s_pre[b] = pre;
+            s_acc[b] = acc;
+        }
+        s_last = last;
     }
-    for (int j = tid; j < CB_B; j += blockDim.x) s_m[j] = ~0ull;
-    if (tid < CB_B / 32) s_bits[tid] = 0u;
-    const int r = st->r[i];
-    for (int c = tid; c < d / 4; c += blockDim.x)
-        reinterpret_cast<float4 *>(px_rv)[c] = reinterpret_cast<const float4 *>(D + (int64_t)r * d)[c];
     __syncthreads();
-    if (!s_ok) {
-        if (tid == 0) st->ready[i] = 0;
-        return;
-    }
-    const int total = s_pre[i], nteam = blockDim.x / 8, nch = d / 4;
-    for (int base = 0; base < total; base += nteam) {
-        const int t = base + team;
-        int j = 0, x = -1;
-        if (t < total) {
-            int lo = 0, hi = i - 1;  // last j with s_pre[j] <= t
+    const int last = s_last;
+    const long long total = s_acc[last];
+    if (blockIdx.x == 0)
+        for (int i = tid; i < b; i += blockDim.x) st->ready[i] = i < last;
+    const int nch = d / 4;
+    const long long nteam = (long long)gridDim.x * (blockDim.x / 8);
+    for (long long f0 = (long long)blockIdx.x * (blockDim.x / 8); f0 < total; f0 += nteam) {
+        const long long f = f0 + (tid >> 3);
+        int i = 0, x = -1, r = 0;
+        if (f < total) {
+            int lo = 0, hi = last - 1;  // last i with s_acc[i] <= f
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
-                if (s_pre[mid] <= t) lo = mid;
+                if (s_acc[mid] <= f) lo = mid;
                 else hi = mid - 1;
             }
-            j = lo;
-            x = comp[(size_t)j * CX_C + (t - s_pre[j])];
+            i = lo;
+            const int t = (int)(f - s_acc[i]);  // < s_pre[i]
+            int jl = 0, jh = i - 1;             // last j with s_pre[j] <= t
+            while (jl < jh) {
+                const int mid = (jl + jh + 1) >> 1;
+                if (s_pre[mid] <= t) jl = mid;
+                else jh = mid - 1;
+            }
+            x = comp[(size_t)jl * CX_C + (t - s_pre[jl])];
+            r = st->r[i];
         }
-        const bool cand = x >= 0 && deg[x] < R;
-        if (!__any_sync(0xffffffffu, cand || x == r)) continue;
-        const float s = team8_dist(reinterpret_cast<const float4 *>(px_rv),
-                                   reinterpret_cast<const float4 *>(D + (int64_t)(x >= 0 ? x : r) * d),
+        const bool cand = x >= 0 && x != r && deg[x] < R;
+        if (li == 0 && x >= 0 && x == r) st->skip[i] = 1;
+        if (!__any_sync(0xffffffffu, cand)) continue;
+        const float s = team8_dist(reinterpret_cast<const float4 *>(D + (int64_t)r * d),
+                                   reinterpret_cast<const float4 *>(D + (int64_t)(cand ? x : r) * d),
                                    nch, li, metric);
-        if (li != 0 || x < 0) continue;
-        if (x == r) atomicOr(&s_bits[j >> 5], 1u << (j & 31));
-        if (cand) atomicMin(&s_m[j], pack_sid(s, x));
+        if (li == 0 && cand) atomicMin(&st->cmin[i], pack_sid(s, x));
     }
-    __syncthreads();
-    for (int j = tid; j < i; j += blockDim.x) st->M[i][j] = s_m[j];
-    if (tid < CB_B / 32) st->in_comp[i][tid] = s_bits[tid];
-    if (tid == 0) st->ready[i] = 1;
 }
 
-// the rounds of the batch in order (warp 0), then the edges, the reached
-// marks and, after an overflowed closure, the BFS from its round
+// the rounds of the batch in order (one thread), then the edges, the
+// reached marks and, after an overflowed closure, the BFS from its round
 constexpr int CXD = 256;  // threads of the decide CTA
 
 __global__ void __launch_bounds__(CXD)
 k_cx_decide(int32_t *nbr, int32_t *deg, int R, int64_t n, int *reached, int *queue, ConnX *st,
             const int *comp, int *err) {
-    extern __shared__ __align__(16) unsigned long long sM[];  // [b][CB_B], row i uses j < i
-    __shared__ unsigned s_in[CB_B][CB_B / 32];
-    __shared__ unsigned long long s_best[CB_B];
-    __shared__ int s_r[CB_B], s_cn[CB_B], s_ready[CB_B];
-    __shared__ int s_cp[CB_B], s_cr[CB_B], s_crank[CB_B], s_ci[CB_B];
-    __shared__ int s_nc, s_stop, s_stop_i, s_full, s_tail;
+    __shared__ unsigned long long s_c[CB_B];
+    __shared__ int s_r[CB_B], s_cn[CB_B], s_ready[CB_B], s_skip[CB_B], s_scan[CB_B];
+    __shared__ int s_prev[CB_B], s_done[CB_B], s_rank[CB_B], s_d0[CB_B];
+    __shared__ int s_stop, s_stop_i, s_tail;
     const int b = st->b;
     if (b == 0) return;
-    const int tid = threadIdx.x, lane = tid & 31;
-    for (int t = tid; t < b * CB_B; t += CXD) {
-        const int i = t / CB_B, j = t % CB_B;
-        if (j < i) sM[t] = st->M[i][j];
-    }
-    for (int t = tid; t < b * (CB_B / 32); t += CXD)
-        s_in[t / (CB_B / 32)][t % (CB_B / 32)] = st->in_comp[t / (CB_B / 32)][t % (CB_B / 32)];
+    const int tid = threadIdx.x;
     for (int i = tid; i < b; i += CXD) {
-        s_best[i] = st->best[i];
+        const unsigned long long bs = st->best[i], cm = st->cmin[i];
+        s_c[i] = bs <= cm ? bs : cm;
+        s_scan[i] = bs <= cm;
         s_r[i] = st->r[i];
         s_cn[i] = st->comp_n[i];
         s_ready[i] = st->ready[i];
+        s_skip[i] = st->skip[i];
+        s_done[i] = 0;
+        s_rank[i] = 0;
     }
     __syncthreads();
-    if (tid < 32) {
-        unsigned cm0 = 0, cm1 = 0, cm2 = 0, cm3 = 0;
-        int nc = 0, stop = 0, stop_i = b, full = 0;
+    // the previous round with the same candidate node, and that node's degree
+    for (int i = tid; i < b; i += CXD) {
+        int prev = -1;
+        if (s_c[i] != ~0ull)
+            for (int j = i - 1; j >= 0; --j)
+                if (s_c[j] == ~0ull ? false : (unsigned)s_c[j] == (unsigned)s_c[i]) {
+                    prev = j;
+                    break;
+                }
+        s_prev[i] = prev;
+        s_d0[i] = s_c[i] != ~0ull ? deg[(int)(s_c[i] & 0xffffffffu)] : 0;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int stop = 0, stop_i = b;
         for (int i = 0; i < b; ++i) {
             if (!s_ready[i]) {
                 stop = 4;
                 stop_i = i;
                 break;
             }
-            if ((s_in[i][0] & cm0) | (s_in[i][1] & cm1) | (s_in[i][2] & cm2) | (s_in[i][3] & cm3))
-                continue;  // r_i was reached by a committed round
-            unsigned long long c = ~0ull;
-            for (int j = lane; j < i; j += 32) {
-                const unsigned w = j < 32 ? cm0 : j < 64 ? cm1 : j < 96 ? cm2 : cm3;
-                if ((w >> (j & 31)) & 1u) {
-                    const unsigned long long m = sM[i * CB_B + j];
-                    if (m < c) c = m;
-                }
-            }
-            for (int o = 16; o; o >>= 1) {
-                const unsigned long long y = __shfl_xor_sync(0xffffffffu, c, o);
-                if (y < c) c = y;
-            }
-            const bool from_scan = s_best[i] <= c;
-            if (from_scan) c = s_best[i];
-            if (c == ~0ull) {
+            if (s_skip[i]) continue;  // r_i was reached by an earlier round
+            if (s_c[i] == ~0ull) {
                 stop = 2;
                 stop_i = i;
                 break;
             }
-            const int p = (int)(c & 0xffffffffu);
-            int cnt = 0;
-            for (int k = lane; k < nc; k += 32) cnt += s_cp[k] == p;
-            for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-            if (cnt > 0) {  // p took edges earlier in this batch: is a slot left?
-                int dd = 0;
-                if (lane == 0) dd = deg[p];
-                dd = __shfl_sync(0xffffffffu, dd, 0);
-                if (dd + cnt >= R) {
-                    stop = 1;
-                    stop_i = i;
-                    break;
-                }
+            int cnt = 0;  // edges its node took earlier in this batch
+            for (int j = s_prev[i]; j >= 0; j = s_prev[j]) cnt += s_done[j];
+            if (s_d0[i] + cnt >= R) {
+                stop = 1;
+                stop_i = i;
+                break;
             }
-            if (lane == 0) {
-                s_cp[nc] = p;
-                s_cr[nc] = s_r[i];
-                s_crank[nc] = cnt;
-                s_ci[nc] = i;
-            }
-            __syncwarp();
-            ++nc;
-            if (i < 32) cm0 |= 1u << i;
-            else if (i < 64) cm1 |= 1u << (i - 32);
-            else if (i < 96) cm2 |= 1u << (i - 64);
-            else cm3 |= 1u << (i - 96);
-            full += from_scan ? 1 : 0;
+            s_done[i] = 1;
+            s_rank[i] = cnt;
             if (s_cn[i] > CX_C) {  // committed; its closure overflowed
                 stop = 3;
                 stop_i = i;
                 break;
             }
         }
-        if (lane == 0) {
-            s_nc = nc;
-            s_stop = stop;
-            s_stop_i = stop_i;
-            s_full = full;
-            s_tail = 0;
-        }
+        s_stop = stop;
+        s_stop_i = stop_i;
+        s_tail = 0;
     }
     __syncthreads();
-    const int nc = s_nc, stop = s_stop, stop_i = s_stop_i;
-    // edges: the k-th commit to p goes to slot deg0(p) + rank
-    int d0 = 0;
-    if (tid < nc) d0 = deg[s_cp[tid]];
-    __syncthreads();
-    if (tid < nc) {
-        const int p = s_cp[tid];
-        nbr[(int64_t)p * R + d0 + s_crank[tid]] = s_cr[tid];
+    const int stop = s_stop, stop_i = s_stop_i;
+    // edges: the k-th edge of a node goes to slot deg0 + k
+    int added = 0, scanned = 0;
+    for (int i = tid; i < b; i += CXD) {
+        if (!s_done[i]) continue;
+        const int p = (int)(s_c[i] & 0xffffffffu);
+        nbr[(int64_t)p * R + s_d0[i] + s_rank[i]] = s_r[i];
         bool last = true;
-        for (int k = tid + 1; k < nc; ++k) last = last && s_cp[k] != p;
-        if (last) deg[p] = d0 + s_crank[tid] + 1;
+        for (int j = i + 1; j < b; ++j) last = last && !(s_done[j] && (unsigned)s_c[j] == (unsigned)p);
+        if (last) deg[p] = s_d0[i] + s_rank[i] + 1;
+        ++added;
+        scanned += s_scan[i];
     }
     // reached marks of the committed closures (an overflowed one is left to the BFS)
-    for (int k = 0; k < nc; ++k) {
-        const int i = s_ci[k];
-        const int cn = s_cn[i];
-        if (cn > CX_C) continue;
-        for (int t = tid; t < cn; t += CXD) reached[comp[(size_t)i * CX_C + t]] = 1;
+    for (int i = 0; i < b; ++i) {
+        if (!s_done[i] || s_cn[i] > CX_C) continue;
+        for (int t = tid; t < s_cn[i]; t += CXD) reached[comp[(size_t)i * CX_C + t]] = 1;
+    }
+    if (added) {
+        atomicAdd(&st->added, added);
+        atomicAdd(&st->full_rounds, scanned);
+        atomicAdd(&st->fast_rounds, added - scanned);
     }
     __syncthreads();
     if (stop == 3) block_bfs_append(nbr, deg, R, n, reached, queue, s_r[stop_i], &s_tail);
     if (tid == 0) {
-        st->added += nc;
-        st->full_rounds += s_full;
-        st->fast_rounds += nc - s_full;
         if (stop == 1) st->conflicts += 1;
         if (stop == 3) st->big_rounds += 1;
         if (stop == 2) {
@@ -931,10 +923,6 @@ static pg_status connect_exact(pg_ctx *ctx, const float *D, int64_t n, int32_t d
                                      cudaMemcpyDeviceToDevice, ctx->stream));
     PG_TRY_CUDA(ctx, cudaMemcpyAsync(&st.p->nfree, &init->nfree, sizeof(int),
                                      cudaMemcpyDeviceToDevice, ctx->stream));
-    const size_t smem_pair = (size_t)d * 4;
-    const size_t smem_dec = (size_t)CB_B * CB_B * 8;
-    PG_TRY_CUDA(ctx, cudaFuncSetAttribute(k_cx_decide, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem_dec));
     const int64_t max_groups = n / 8 + 2;
     for (int64_t group = 0;; ++group) {
         if (group > max_groups)
@@ -951,12 +939,12 @@ static pg_status connect_exact(pg_ctx *ctx, const float *D, int64_t n, int32_t d
             pg_timer_begin(ctx, TM_CFAST);
             k_cx_comp<<<CB_B, 256, 0, ctx->stream>>>(nbr, deg, R, n, reached, st.p, comp.p);
             PG_LAUNCHED(ctx);
-            k_cx_pair<<<CB_B, 256, smem_pair, ctx->stream>>>(D, d, 0, deg, R, st.p, comp.p);
+            k_cx_pair<<<ctx->num_sms * 2, 256, 0, ctx->stream>>>(D, d, 0, deg, R, st.p, comp.p);
             PG_LAUNCHED(ctx);
             pg_timer_end(ctx, TM_CFAST);
             pg_timer_begin(ctx, TM_CCOMMIT);
-            k_cx_decide<<<1, CXD, smem_dec, ctx->stream>>>(nbr, deg, R, n, reached, queue, st.p,
-                                                          comp.p, ctx->d_err);
+            k_cx_decide<<<1, CXD, 0, ctx->stream>>>(nbr, deg, R, n, reached, queue, st.p, comp.p,
+                                                   ctx->d_err);
             PG_LAUNCHED(ctx);
             pg_timer_end(ctx, TM_CCOMMIT);
         }

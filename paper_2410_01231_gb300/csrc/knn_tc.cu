@@ -386,13 +386,18 @@ k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUten
         int count = 0;
         float thr = INFINITY;  // the heap's K-th pair once full
         int thr_id = INT_MAX;
+        // this thread's column norm of tile t, loaded one tile ahead
+        auto colnorm = [&](int t) -> float {
+            if (t >= ntiles) return INFINITY;
+            const int64_t c = (int64_t)tile_at(t) * TN + row;
+            return c < n ? xnorm[c] : INFINITY;
+        };
+        float next = colnorm(0);
         for (int t = 0; t < ntiles; ++t) {
             const int a = t & 1;
             const int64_t colbase = (int64_t)tile_at(t) * TN;
-            {
-                const int64_t c = colbase + row;
-                nbuf[a * TN + row] = c < n ? xnorm[c] : INFINITY;
-            }
+            nbuf[a * TN + row] = next;
+            next = colnorm(t + 1);
             mbar_wait(acc_full + a, (t >> 1) & 1, abort, err);
             epi_barrier();
             if (*abort) break;
@@ -603,13 +608,22 @@ k_argmin_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CU
         const float nqr = live ? qnorm[row] : 0.f;
         float bs = INFINITY;
         int bid = INT_MAX;
+        // column value of tile t for this thread's column: the norm, or +inf
+        // for a masked column; loaded one tile ahead
+        auto colval = [&](int t) -> float {
+            const int64_t c = (int64_t)(t0 + t) * TN + row;
+            if (t >= ntiles || c >= n) return INFINITY;
+            const int rc = reached[c];
+            const int dc = deg[c];
+            const float xc = xnorm[c];
+            return (rc && dc < R) ? xc : INFINITY;
+        };
+        float next = colval(0);
         for (int t = 0; t < ntiles; ++t) {
             const int a = t & 1;
             const int64_t colbase = (int64_t)(t0 + t) * TN;
-            {
-                const int64_t c = colbase + row;
-                nbuf[a * TN + row] = (c < n && reached[c] && deg[c] < R) ? xnorm[c] : INFINITY;
-            }
+            nbuf[a * TN + row] = next;
+            next = colval(t + 1);
             mbar_wait(acc_full + a, (t >> 1) & 1, abort, err);
             epi_barrier();
             if (*abort) break;
