@@ -308,6 +308,90 @@ def search_nswg(D, layers, ep: int, Q, k: int, ef: int, metric: str = "cosine",
     return search(D, base.nbr, base.deg, Q, w, k, ef, metric)
 
 
+def insert_batch(D_all, layers, ep: int, n_old: int, ef: int, alpha_deg: float = 60.0,
+                 metric: str = "l2", seed: int = 0, M: int = 16, ef_upper: int = 1):
+    """Batched insertion of the points n_old..len(D_all)-1 into a layered
+    index, every new point against the graph as it was before the batch.
+
+    Per new point u (the search and refinement phases of Algorithm 4):
+    its level l(u) is the SplitMix64 draw of the build (Algorithm 7 line 2)
+    capped at the top layer; w <- ep, then w <- first of
+    KANNSearch(G_i, u, 1, ef_upper, w) for the layers above l(u); for
+    i = l(u)..0: W_i <- KANNSearch(G_i, u, ef, ef, w), w <- W_i[0], and
+    N_i(u) <- Prune(u, W_i, R_i, alpha).  Then every old v with new
+    in-edges I_i(v) = {u : v in N_i(u)} gets
+    N_i(v) <- Prune(v, N_i(v) | I_i(v), R_i, alpha) from its list before
+    the batch (the reverse-edge step of Algorithm 4).  New nodes are
+    appended to the layers in id order.  Returns new Layer objects.
+    """
+    D_all = _f32(D_all)
+    N = D_all.shape[0]
+    m = N - n_old
+    top = len(layers) - 1
+    lev = np.minimum(levels(N, seed, M)[n_old:], top)
+    Q = D_all[n_old:]
+    w = np.full(m, ep, np.int32)
+    out = [None] * (top + 1)
+    for i in range(top, -1, -1):
+        lay = layers[i]
+        Ri = lay.R
+        rows = None
+        if i > 0:
+            rows = np.full(N, -1, np.int32)
+            rows[lay.gid] = np.arange(lay.gid.shape[0], dtype=np.int32)
+        S = np.nonzero(lev >= i)[0]
+        B = np.nonzero(lev < i)[0]
+        if i >= 1 and B.shape[0]:
+            ids, _ = search(D_all, lay.nbr, lay.deg, Q[B], w[B], 1, ef_upper, metric, rows=rows)
+            w[B] = ids[:, 0]
+        gid = lay.gid.copy()
+        nbr = lay.nbr.copy()
+        deg = lay.deg.copy()
+        if S.shape[0]:
+            W, _ = search(D_all, lay.nbr, lay.deg, Q[S], w[S], ef, ef, metric, rows=rows)
+            w[S] = W[:, 0]
+            # N_i(u) for the new points: rows of a CSR over all N points
+            cnt = np.zeros(N, np.int64)
+            cnt[n_old + S] = ef
+            off = np.zeros(N + 1, np.int64)
+            off[1:] = np.cumsum(cnt)
+            cand = np.full(int(off[-1]), -1, np.int32)
+            for a, u in enumerate(S):
+                cand[off[n_old + u]:off[n_old + u + 1]] = W[a]
+            pn, pd = prune(D_all, off, cand, Ri, alpha_deg, metric)
+            new_nbr = pn[n_old + S]
+            new_deg = pd[n_old + S]
+            # reverse step for the old nodes that gained in-edges
+            row_of = (lambda v: v) if i == 0 else (lambda v: int(rows[v]))
+            inc = {}
+            for a, u in enumerate(S):
+                for v in new_nbr[a, :new_deg[a]]:
+                    inc.setdefault(int(v), []).append(n_old + int(u))
+            if inc:
+                cnt = np.zeros(N, np.int64)
+                lists = {}
+                for v, us in inc.items():
+                    r = row_of(v)
+                    lst = list(lay.nbr[r, :lay.deg[r]]) + us
+                    lists[v] = lst
+                    cnt[v] = len(lst)
+                off = np.zeros(N + 1, np.int64)
+                off[1:] = np.cumsum(cnt)
+                cand = np.empty(int(off[-1]), np.int32)
+                for v, lst in lists.items():
+                    cand[off[v]:off[v + 1]] = lst
+                pn, pd = prune(D_all, off, cand, Ri, alpha_deg, metric)
+                for v in lists:
+                    r = row_of(v)
+                    nbr[r] = pn[v]
+                    deg[r] = pd[v]
+            gid = np.concatenate([gid, (n_old + S).astype(np.int32)])
+            nbr = np.concatenate([nbr, new_nbr])
+            deg = np.concatenate([deg, new_deg])
+        out[i] = Layer(gid.astype(np.int32), nbr.astype(np.int32), deg.astype(np.int32), Ri)
+    return out
+
+
 # --------------------------------------------------------------------------
 def recall_at_k(found_ids, Q, D, k: int, metric: str = "l2", gt=None):
     """Recall@k = |N*(q) cap N(q)| / k (Section 6, performance indicators).

@@ -23,7 +23,8 @@ pg_status pg_knn_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_
 pg_status pg_prune_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
                             const int64_t *off, const int32_t *cand, int32_t R, double alpha_deg,
                             const DataFacts &facts, int32_t *nbr, int32_t *deg,
-                            const uint8_t *D8 = nullptr);
+                            const uint8_t *D8 = nullptr, int64_t rows = 0,
+                            const int32_t *self_ids = nullptr);
 pg_status pg_reverse_union_internal(pg_ctx *ctx, const int32_t *nbr, const int32_t *deg, int64_t n,
                                     int32_t R, int64_t *off, int32_t *ids);
 pg_status pg_medoid_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,

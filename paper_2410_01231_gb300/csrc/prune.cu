@@ -26,7 +26,9 @@ constexpr int RMAX = 64;
 struct PruneParams {
     const float *D;
     const uint8_t *D8;  // byte shadow of D (exact byte data) or nullptr
-    int64_t n;
+    int64_t n;          // points (ids must lie below n)
+    int64_t rows;       // candidate rows (== n unless self_ids is given)
+    const int32_t *self_ids;  // point id of each row, or nullptr (row = point)
     int d;
     int metric;
     const int64_t *off;
@@ -73,8 +75,9 @@ struct RowStats {
     unsigned long long cands = 0, scanned = 0, tests = 0, rechecks = 0, flips = 0, edges = 0;
 };
 
-__device__ void prune_row(const PruneParams &P, int64_t u, const int32_t *cand, int64_t cnt,
+__device__ void prune_row(const PruneParams &P, int64_t row, const int32_t *cand, int64_t cnt,
                           unsigned char *wsmem, RowStats &st) {
+    const int64_t u = P.self_ids ? (int64_t)P.self_ids[row] : row;  // the point being pruned
     const int lane = threadIdx.x & 31, team = lane >> 3, li = lane & 7;
     const int cap = P.cap;
     double *c64 = reinterpret_cast<double *>(wsmem);
@@ -290,8 +293,8 @@ __device__ void prune_row(const PruneParams &P, int64_t u, const int32_t *cand, 
     }
     st.scanned += j;
     st.edges += kept;
-    for (int t = lane; t < P.R; t += 32) P.nbr[u * P.R + t] = t < kept ? kid[t] : -1;
-    if (lane == 0) P.deg[u] = kept;
+    for (int t = lane; t < P.R; t += 32) P.nbr[row * P.R + t] = t < kept ? kid[t] : -1;
+    if (lane == 0) P.deg[row] = kept;
     __syncwarp();
 }
 
@@ -327,7 +330,7 @@ __global__ void __launch_bounds__(PW * 32) k_prune(PruneParams P) {
         int64_t u = 0;
         if (lane == 0) u = atomicAdd(P.row_counter, 1);
         u = __shfl_sync(0xffffffffu, u, 0);
-        if (u >= P.n) break;
+        if (u >= P.rows) break;
         int64_t a = P.off[u], b = P.off[u + 1];
         if (b < a) {
             if (lane == 0) {
@@ -496,11 +499,13 @@ pg_status pg_reverse_union_internal(pg_ctx *ctx, const int32_t *nbr, const int32
 pg_status pg_prune_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
                             const int64_t *off, const int32_t *cand, int32_t R, double alpha_deg,
                             const DataFacts &facts, int32_t *nbr, int32_t *deg,
-                            const uint8_t *D8) {
+                            const uint8_t *D8, int64_t rows, const int32_t *self_ids) {
     PruneParams P;
     P.D = D;
     P.D8 = D8;
     P.n = n;
+    P.rows = rows > 0 ? rows : n;
+    P.self_ids = self_ids;
     P.d = d;
     P.metric = metric == PG_METRIC_L2SQ ? 0 : 1;
     P.off = off;
@@ -516,7 +521,7 @@ pg_status pg_prune_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d, p
     P.err = ctx->d_err;
     P.counters = ctx->d_counters;
     Scratch<int> ints;
-    PG_TRY(ints.alloc(ctx, (size_t)n + 4));
+    PG_TRY(ints.alloc(ctx, (size_t)P.rows + 4));
     PG_TRY_CUDA(ctx, cudaMemsetAsync(ints.p, 0, 4 * sizeof(int), ctx->stream));
     P.row_counter = ints.p;
     P.long_count = ints.p + 1;
@@ -557,6 +562,8 @@ cudaError_t pg_prune_launch_on(cudaStream_t stream, int num_sms, const float *D,
     P.D = D;
     P.D8 = nullptr;
     P.n = n;
+    P.rows = n;
+    P.self_ids = nullptr;
     P.d = d;
     P.metric = metric == PG_METRIC_L2SQ ? 0 : 1;
     P.off = off;
@@ -621,7 +628,7 @@ extern "C" pg_status pg_prune(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
     if (pg_u8_usable(facts, metric, d, precision)) PG_TRY(pg_make_u8(ctx, D, n, d, d8));
     if (host_stats) PG_TRY(pg_reset_counters(ctx));
     PG_TRY(pg_prune_internal(ctx, D, n, d, metric, cand_off, cand_ids, R, alpha_deg, facts, nbr,
-                             deg, d8.p));
+                             deg, d8.p, 0, nullptr));
     if (host_stats) {
         unsigned long long c[PG_CNT_SLOTS];
         PG_TRY(pg_read_counters(ctx, c));

@@ -449,3 +449,55 @@ def test_recall_helper_on_hand_made_lists():
     assert oracle.recall_at_k(np.array([[0, 1, 3]]), Q, D, 3, gt=gt) == 1.0
     assert oracle.recall_at_k(np.array([[0, 0, 4]]), Q, D, 3, gt=gt) == pytest.approx(1 / 3)
     assert oracle.recall_at_k(np.array([[-1, 2, 1]]), Q, D, 3, gt=gt) == pytest.approx(2 / 3)
+
+
+# ------------------------------------------------------------- insertion
+def _rng_set(P, u, others):
+    """RNG pruning of u's candidates `others` written out in exact integers:
+    scan by (s(u, v), v) and keep v unless a kept w is strictly closer to u
+    and strictly closer to v than u is to v (Algorithm 3 at alpha = 60)."""
+    def s(a, b):
+        return int(((P[a].astype(np.int64) - P[b].astype(np.int64)) ** 2).sum())
+    kept = []
+    for v in sorted(others, key=lambda v: (s(u, v), v)):
+        if not any(s(u, w) < s(u, v) and s(v, w) < s(u, v) for w in kept):
+            kept.append(v)
+    return set(kept)
+
+
+def test_insert_into_complete_layer_links_the_rng_neighbours():
+    """An exhaustive search (ef >= n on a complete layer) makes N(u) the RNG
+    set of u over all points, and every linked v's list the RNG set of v
+    over its old list plus u."""
+    rng = np.random.default_rng(11)
+    P = rng.integers(0, 60, size=(31, 2)).astype(np.float32)
+    P = np.concatenate([P, np.zeros((31, 2), np.float32)], axis=1)  # d = 4
+    n_old = 30
+    layers, ep, _ = oracle.build_nswg(P[:n_old], 8, 40, 16, 32, 60.0, 60.0, 1, "l2", 3,
+                                      lev=np.zeros(n_old, np.int32))
+    assert len(layers) == 1 and (layers[0].deg == n_old - 1).all()  # complete
+    new = oracle.insert_batch(P, layers, ep, n_old, 40, 60.0, "l2", 3, 16)
+    L0 = new[0]
+    u = n_old
+    got = set(L0.nbr[u, :L0.deg[u]].tolist())
+    assert got == _rng_set(P, u, list(range(n_old)))
+    for v in range(n_old):
+        lst = set(L0.nbr[v, :L0.deg[v]].tolist())
+        if v in got:
+            assert lst == _rng_set(P, v, [w for w in range(n_old + 1) if w != v])
+        else:
+            assert lst == set(layers[0].nbr[v, :layers[0].deg[v]].tolist())
+
+
+def test_insert_levels_follow_the_build_draw_capped_at_the_top():
+    D, _, _ = synthetic.workload(1, n=900, nq=1)
+    layers, ep, lev = oracle.build_nswg(D[:800], 16, 32, 16, 32, 70.0, 60.0, 1, "l2", 9)
+    new = oracle.insert_batch(D, layers, ep, 800, 32, 60.0, "l2", 9, 16)
+    top = len(layers) - 1
+    want = np.minimum(oracle.levels(900, 9, 16)[800:], top)
+    for i, L in enumerate(new):
+        members = set(L.gid.tolist())
+        assert set(layers[i].gid.tolist()) <= members
+        assert {800 + k for k in np.nonzero(want >= i)[0]} == members - set(layers[i].gid.tolist())
+        assert (L.deg <= L.R).all() and (np.diff(L.gid) > 0).all()
+    assert (new[0].deg[800:] > 0).all()
