@@ -306,6 +306,32 @@ pg_status pg_index_layer(const pg_index *index, int32_t layer, int64_t *count, i
 pg_status pg_index_export_layer(pg_ctx *ctx, const pg_index *index, int32_t layer, int32_t *gid,
                                 int32_t *nbr, int32_t *deg);
 
+/* ------------------------------------------------------------ insertion */
+
+/* Make `index` growable (serving): the index takes a private DEVICE copy of
+ * its points in a buffer of `capacity` rows (the caller's D is no longer
+ * read afterwards) and grows every layer to hold the points inserted up to
+ * that capacity.  n <= capacity < 2^31.  Synchronous.  Errors:
+ * PG_ERR_INVALID_ARG, PG_ERR_CUDA (allocation). */
+pg_status pg_index_reserve(pg_ctx *ctx, pg_index *index, int64_t capacity);
+
+/* Batched insertion of m points X (DEVICE, [m][d] row-major, caller-owned;
+ * copied into the index) with ids n .. n+m-1: the search and refinement
+ * phases of Algorithm 4 for every new point, all against the graph as it
+ * was before the batch (one batch = one snapshot).  Each new point u takes
+ * the level of the build's SplitMix64 draw (Algorithm 7 line 2), capped at
+ * the top layer; w = the top entry, w <- best of a pool-`upper_beam`
+ * search in each layer above l(u) (1 = the paper's greedy routing); for
+ * i = l(u)..0: W_i <- KANNSearch(G_i, u, ef, ef, w), w <- W_i[0],
+ * N_i(u) <- Prune(u, W_i, R_i) at the build's final angle (Algorithm 3 with
+ * the Section 4.1 rule).  Every old node v that gained in-edges I_i(v)
+ * re-prunes N_i(v) | I_i(v) (the reverse-edge step of Algorithm 4); new
+ * nodes are appended to the layers in id order.  Needs pg_index_reserve
+ * with capacity >= n + m (else PG_ERR_CAPACITY); 1 <= ef, upper_beam <= 256.
+ * Synchronous. */
+pg_status pg_index_insert(pg_ctx *ctx, pg_index *index, const float *X, int64_t m, int32_t ef,
+                          int32_t upper_beam);
+
 /* Seconds spent per build phase by the last build on this index:
  * knn, prune, union, connect, acquire, layers (host array of 6). */
 pg_status pg_index_phase_seconds(const pg_index *index, double *host_seconds6);

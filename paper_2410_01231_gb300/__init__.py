@@ -84,6 +84,8 @@ _sig("pg_ctx_kernel_time", C.c_int, [P, C.c_char_p, P, P])
 _sig("pg_ctx_counter", C.c_int, [P, C.c_char_p, P])
 _sig("pg_ctx_kernel_work", C.c_int, [P, C.c_char_p, P])
 _sig("pg_prune_noalloc", C.c_int, [P, P, i64, i32, C.c_int, P, P, i32, dbl, P, P])
+_sig("pg_index_reserve", C.c_int, [P, P, i64])
+_sig("pg_index_insert", C.c_int, [P, P, P, i64, i32, i32])
 
 EXPORTS = ["pg_default_params", "pg_ctx_create", "pg_ctx_destroy", "pg_last_error", "pg_ctx_sync",
            "pg_ctx_launches", "pg_build_knn", "pg_knn_query", "pg_prune", "pg_reverse_union",
@@ -91,7 +93,7 @@ EXPORTS = ["pg_default_params", "pg_ctx_create", "pg_ctx_destroy", "pg_last_erro
            "pg_build_nswg", "pg_search", "pg_search_host", "pg_index_destroy", "pg_index_info",
            "pg_index_layer", "pg_index_phase_seconds", "pg_index_export_layer",
            "pg_ctx_set_timing", "pg_ctx_kernel_time", "pg_ctx_counter",
-           "pg_ctx_kernel_work", "pg_prune_noalloc"]
+           "pg_ctx_kernel_work", "pg_prune_noalloc", "pg_index_reserve", "pg_index_insert"]
 
 
 class PGError(RuntimeError):
@@ -355,6 +357,17 @@ class Index:
         self.ctx._check(_lib.pg_index_export_layer(self.ctx.handle, self._h, i, _ptr(gid),
                                                    _ptr(nbr), _ptr(deg)), "pg_index_export_layer")
         return gid, nbr, deg
+
+    def reserve(self, capacity: int):
+        """Private copy of the points with room for `capacity` rows (pg_index_reserve)."""
+        self.ctx._check(_lib.pg_index_reserve(self.ctx.handle, self._h, int(capacity)),
+                        "pg_index_reserve")
+
+    def insert(self, X: torch.Tensor, ef: int, upper_beam: int = 1):
+        """Batched insertion of the rows of X (pg_index_insert); new ids follow n."""
+        X = _dev(X, torch.float32, "X")
+        self.ctx._check(_lib.pg_index_insert(self.ctx.handle, self._h, _ptr(X), X.shape[0], ef,
+                                             upper_beam), "pg_index_insert")
 
     def phase_seconds(self):
         arr = (C.c_double * 6)()

@@ -41,6 +41,7 @@ pg_status pg_search_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d, 
 
 struct pg_layer {
     int64_t count = 0;
+    int64_t cap = 0;  // rows allocated
     int R = 0;
     int32_t *gid = nullptr;   // [count] ascending point ids (null: identity)
     int32_t *nbr = nullptr;   // [count][R] point ids
@@ -56,7 +57,11 @@ struct pg_index {
     std::vector<pg_layer> layers;
     int64_t ep_top = 0, ep_base = 0;
     double phase[6] = {0, 0, 0, 0, 0, 0};
+    pg_build_params params{};  // of the build: levels, degrees, pruning angle
+    float *owned = nullptr;    // private copy of the points once reserved
+    int64_t capacity = 0;      // rows of `owned`
     ~pg_index() {
+        cudaFree(owned);
         for (auto &l : layers) {
             cudaFree(l.gid);
             cudaFree(l.nbr);
@@ -158,17 +163,18 @@ uint64_t splitmix64(uint64_t x) {
     return z ^ (z >> 31);
 }
 
-// Level of every point: floor(-ln U / ln M), U = ((z >> 11) + 1) 2^-53 with
+// Level of a point: floor(-ln U / ln M), U = ((z >> 11) + 1) 2^-53 with
 // z = SplitMix64(seed XOR id) -- the exponentially decaying level draw of
 // Algorithm 4 line 4 / Algorithm 7 line 2.
+int level_of(int64_t id, uint64_t seed, int M) {
+    const uint64_t z = splitmix64(seed ^ (uint64_t)id);
+    const double U = (double)((z >> 11) + 1) * (1.0 / 9007199254740992.0);
+    return (int)std::floor(-std::log(U) / std::log((double)M));
+}
+
 std::vector<int> draw_levels(int64_t n, uint64_t seed, int M) {
     std::vector<int> lev((size_t)n);
-    const double lnM = std::log((double)M);
-    for (int64_t i = 0; i < n; ++i) {
-        uint64_t z = splitmix64(seed ^ (uint64_t)i);
-        double U = (double)((z >> 11) + 1) * (1.0 / 9007199254740992.0);
-        lev[(size_t)i] = (int)std::floor(-std::log(U) / lnM);
-    }
+    for (int64_t i = 0; i < n; ++i) lev[(size_t)i] = level_of(i, seed, M);
     return lev;
 }
 
@@ -257,6 +263,7 @@ pg_status iter_nsg(pg_ctx *ctx, const float *X, int64_t m, int32_t d, const pg_b
 
 pg_status alloc_layer(pg_ctx *ctx, pg_layer &l, int64_t count, int R, int64_t n, bool ident) {
     l.count = count;
+    l.cap = count;
     l.R = R;
     PG_TRY_CUDA(ctx, cudaMalloc(&l.nbr, (size_t)(count * R) * sizeof(int32_t)));
     PG_TRY_CUDA(ctx, cudaMalloc(&l.deg, (size_t)count * sizeof(int32_t)));
@@ -323,6 +330,7 @@ pg_status build_common(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
     idx->d = d;
     idx->metric = p->metric;
     idx->D = D;
+    idx->params = *p;
     idx->layers.resize(1);
     pg_status st = alloc_layer(ctx, idx->layers[0], n, p->R, n, true);
     int64_t ep = 0;
@@ -482,4 +490,309 @@ extern "C" pg_status pg_search_host(pg_ctx *ctx, const pg_index *idx, const floa
     PG_TRY_CUDA(ctx, cudaMemcpyAsync(out_dist, ds.p, (size_t)(nq * k) * 4, cudaMemcpyDeviceToHost,
                                      ctx->stream));
     return pg_sync_check(ctx, "pg_search_host");
+}
+
+// ---------------------------------------------------------------- insertion
+namespace {
+
+__global__ void k_gather_i32(const int32_t *src, const int32_t *idx, int64_t m, int32_t *dst) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < m) dst[t] = src[idx[t]];
+}
+
+// dst[idx[k]] = W[k * stride]
+__global__ void k_scatter_first(int32_t *dst, const int32_t *idx, int64_t m, const int32_t *W,
+                                int stride) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < m) dst[idx[t]] = W[t * stride];
+}
+
+// in-edge counts per layer row from the new nodes' lists
+__global__ void k_in_count(const int32_t *nb, const int32_t *dg, int64_t ns, int R,
+                           const int32_t *rows, int32_t *cnt) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ns * R) return;
+    const int64_t k = t / R;
+    if ((int)(t % R) >= dg[k]) return;
+    const int v = nb[t];
+    atomicAdd(&cnt[rows ? rows[v] : v], 1);
+}
+
+__global__ void k_in_fill(const int32_t *nb, const int32_t *dg, int64_t ns, int R,
+                          const int32_t *rows, const int32_t *sglob, unsigned long long *cursor,
+                          int32_t *inlist) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ns * R) return;
+    const int64_t k = t / R;
+    if ((int)(t % R) >= dg[k]) return;
+    const int v = nb[t];
+    inlist[atomicAdd(&cursor[rows ? rows[v] : v], 1ull)] = sglob[k];
+}
+
+__global__ void k_flag_pos(const int32_t *cnt, int64_t m, int32_t *flag) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < m) flag[t] = cnt[t] > 0;
+}
+
+__global__ void k_compact(const int32_t *cnt, int64_t m, const int64_t *pos, int32_t *A) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < m && cnt[t] > 0) A[pos[t]] = (int32_t)t;
+}
+
+__global__ void k_union_sizes(const int32_t *A, int64_t na, const int32_t *deg, int R,
+                              const int32_t *cnt, int32_t *sz) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < na) sz[t] = min(deg[A[t]], R) + cnt[A[t]];
+}
+
+// row a of the union CSR: the old list of layer row A[a], then its in-edges
+__global__ void k_union_fill(const int32_t *A, int64_t na, const int32_t *nbr, const int32_t *deg,
+                             int R, const int64_t *in_off, const int32_t *inlist,
+                             const int64_t *uoff, int32_t *ucand) {
+    const int64_t a = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x & 31;
+    if (a >= na) return;
+    const int r = A[a];
+    const int dr = min(deg[r], R);
+    int32_t *out = ucand + uoff[a];
+    for (int j = lane; j < dr; j += 32) out[j] = nbr[(int64_t)r * R + j];
+    const int64_t b0 = in_off[r], b1 = in_off[r + 1];
+    for (int64_t j = b0 + lane; j < b1; j += 32) out[dr + (j - b0)] = inlist[j];
+}
+
+__global__ void k_scatter_rows(const int32_t *A, int64_t na, const int32_t *tn, const int32_t *td,
+                               int R, int32_t *nbr, int32_t *deg) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= na * R) return;
+    const int64_t a = t / R;
+    const int j = (int)(t % R);
+    nbr[(int64_t)A[a] * R + j] = tn[t];
+    if (j == 0) deg[A[a]] = td[a];
+}
+
+// new members of an upper layer: gid entries and the point -> row map
+__global__ void k_append_members(const int32_t *sglob, int64_t ns, int64_t base, int32_t *gid,
+                                 int32_t *rows) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ns) return;
+    gid[base + t] = sglob[t];
+    rows[sglob[t]] = (int32_t)(base + t);
+}
+
+unsigned blocks(int64_t n) { return (unsigned)((n + 255) / 256); }
+
+template <typename T>
+pg_status grow(pg_ctx *ctx, T *&p, int64_t keep, int64_t cap) {
+    T *q = nullptr;
+    PG_TRY_CUDA(ctx, cudaMalloc(&q, (size_t)std::max<int64_t>(cap, 1) * sizeof(T)));
+    if (p && keep > 0)
+        PG_TRY_CUDA(ctx, cudaMemcpyAsync(q, p, (size_t)keep * sizeof(T), cudaMemcpyDeviceToDevice,
+                                         ctx->stream));
+    PG_TRY_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    cudaFree(p);
+    p = q;
+    return PG_OK;
+}
+
+}  // namespace
+
+extern "C" pg_status pg_index_reserve(pg_ctx *ctx, pg_index *idx, int64_t capacity) {
+    if (!ctx) return PG_ERR_INVALID_ARG;
+    if (!idx) return pg_fail(ctx, PG_ERR_INVALID_ARG, "null index");
+    if (capacity < idx->n || capacity >= INT_MAX)
+        return pg_fail(ctx, PG_ERR_INVALID_ARG, "need n <= capacity < 2^31");
+    if (capacity <= idx->capacity) return PG_OK;
+    const int64_t n = idx->n, d = idx->d;
+    float *pts = nullptr;
+    PG_TRY_CUDA(ctx, cudaMalloc(&pts, (size_t)(capacity * d) * 4));
+    cudaError_t e = cudaMemcpyAsync(pts, idx->D, (size_t)(n * d) * 4, cudaMemcpyDeviceToDevice,
+                                    ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        cudaFree(pts);
+        return pg_cuda_fail(ctx, e, "pg_index_reserve copy");
+    }
+    cudaFree(idx->owned);
+    idx->owned = pts;
+    idx->D = pts;
+    for (size_t i = 0; i < idx->layers.size(); ++i) {
+        pg_layer &l = idx->layers[i];
+        const int64_t cap = i == 0 ? capacity : l.count + (capacity - n);
+        PG_TRY(grow(ctx, l.nbr, l.count * l.R, cap * l.R));
+        PG_TRY(grow(ctx, l.deg, l.count, cap));
+        if (l.gid) {
+            PG_TRY(grow(ctx, l.gid, l.count, cap));
+            PG_TRY(grow(ctx, l.rows, n, capacity));
+            k_fill_i32<<<blocks(capacity - n), 256, 0, ctx->stream>>>(l.rows + n, capacity - n, -1);
+            PG_LAUNCHED(ctx);
+        }
+        l.cap = cap;
+    }
+    idx->capacity = capacity;
+    return pg_sync_check(ctx, "pg_index_reserve");
+}
+
+extern "C" pg_status pg_index_insert(pg_ctx *ctx, pg_index *idx, const float *X, int64_t m,
+                                     int32_t ef, int32_t upper_beam) {
+    if (!ctx) return PG_ERR_INVALID_ARG;
+    if (!idx || (!X && m > 0)) return pg_fail(ctx, PG_ERR_INVALID_ARG, "null pointer");
+    if (m < 0 || ef < 1 || ef > 256 || upper_beam < 1 || upper_beam > 256)
+        return pg_fail(ctx, PG_ERR_INVALID_ARG, "need m >= 0, 1 <= ef, upper_beam <= 256");
+    if (m == 0) return PG_OK;
+    if (!idx->owned || idx->n + m > idx->capacity)
+        return pg_fail(ctx, PG_ERR_CAPACITY, "insert: %lld points exceed the reserved capacity",
+                       (long long)m);
+    const int64_t n0 = idx->n, N = n0 + m, d = idx->d;
+    const pg_build_params &p = idx->params;
+    float *Dall = idx->owned;
+    PG_TRY_CUDA(ctx, cudaMemcpyAsync(Dall + n0 * d, X, (size_t)(m * d) * 4,
+                                     cudaMemcpyDeviceToDevice, ctx->stream));
+    DataFacts facts;
+    PG_TRY(pg_data_facts(ctx, Dall, N, (int32_t)d, idx->metric, &facts));
+    const int top = (int)idx->layers.size() - 1;
+    std::vector<int> lev((size_t)m);
+    for (int64_t k = 0; k < m; ++k)
+        lev[(size_t)k] = std::min(level_of(n0 + k, p.seed, p.M), top);
+    Scratch<int32_t> w, sel, sglob, starts, out1, W, nnb, ndg, cnt, flag, A, sz, ucand, self, tn, td,
+        inl;
+    Scratch<float> Q, out1s, Ws;
+    Scratch<int64_t> off, in_off, pos, uoff;
+    Scratch<unsigned long long> cur;
+    PG_TRY(w.alloc(ctx, (size_t)m));
+    k_fill_i32<<<blocks(m), 256, 0, ctx->stream>>>(w.p, m, (int32_t)idx->ep_top);
+    PG_LAUNCHED(ctx);
+    std::vector<int32_t> hs, hb, hg;
+    for (int i = top; i >= 0; --i) {
+        pg_layer &l = idx->layers[(size_t)i];
+        const int Ri = l.R;
+        hs.clear();
+        hb.clear();
+        for (int64_t k = 0; k < m; ++k) (lev[(size_t)k] >= i ? hs : hb).push_back((int32_t)k);
+        // routing through a layer above the point's level: pool upper_beam, keep the best
+        if (i >= 1 && !hb.empty()) {
+            const int64_t nb = (int64_t)hb.size();
+            PG_TRY(sel.alloc(ctx, (size_t)nb));
+            PG_TRY(sglob.alloc(ctx, (size_t)nb));
+            hg.resize(hb.size());
+            for (size_t a = 0; a < hb.size(); ++a) hg[a] = (int32_t)(n0 + hb[a]);
+            PG_TRY_CUDA(ctx, cudaMemcpyAsync(sel.p, hb.data(), (size_t)nb * 4,
+                                             cudaMemcpyHostToDevice, ctx->stream));
+            PG_TRY_CUDA(ctx, cudaMemcpyAsync(sglob.p, hg.data(), (size_t)nb * 4,
+                                             cudaMemcpyHostToDevice, ctx->stream));
+            PG_TRY(Q.alloc(ctx, (size_t)(nb * d)));
+            PG_TRY(starts.alloc(ctx, (size_t)nb));
+            PG_TRY(out1.alloc(ctx, (size_t)nb));
+            PG_TRY(out1s.alloc(ctx, (size_t)nb));
+            k_gather_rows<<<blocks(nb * (d / 4)), 256, 0, ctx->stream>>>(Dall, (int)d, sglob.p, nb,
+                                                                         Q.p);
+            PG_LAUNCHED(ctx);
+            k_gather_i32<<<blocks(nb), 256, 0, ctx->stream>>>(w.p, sel.p, nb, starts.p);
+            PG_LAUNCHED(ctx);
+            PG_TRY(pg_search_internal(ctx, Dall, n0, (int32_t)d, idx->metric, l.nbr, l.deg, Ri,
+                                      l.rows, Q.p, nb, starts.p, 1, upper_beam, 0, out1.p,
+                                      out1s.p));
+            k_scatter_first<<<blocks(nb), 256, 0, ctx->stream>>>(w.p, sel.p, nb, out1.p, 1);
+            PG_LAUNCHED(ctx);
+        }
+        if (hs.empty()) continue;
+        const int64_t ns = (int64_t)hs.size();
+        PG_TRY(sel.alloc(ctx, (size_t)ns));
+        PG_TRY(sglob.alloc(ctx, (size_t)ns));
+        hg.resize(hs.size());
+        for (size_t a = 0; a < hs.size(); ++a) hg[a] = (int32_t)(n0 + hs[a]);
+        PG_TRY_CUDA(ctx, cudaMemcpyAsync(sel.p, hs.data(), (size_t)ns * 4, cudaMemcpyHostToDevice,
+                                         ctx->stream));
+        PG_TRY_CUDA(ctx, cudaMemcpyAsync(sglob.p, hg.data(), (size_t)ns * 4,
+                                         cudaMemcpyHostToDevice, ctx->stream));
+        // W_i: pool ef on this layer, from the entry found above
+        PG_TRY(Q.alloc(ctx, (size_t)(ns * d)));
+        PG_TRY(starts.alloc(ctx, (size_t)ns));
+        PG_TRY(W.alloc(ctx, (size_t)(ns * ef)));
+        PG_TRY(Ws.alloc(ctx, (size_t)(ns * ef)));
+        k_gather_rows<<<blocks(ns * (d / 4)), 256, 0, ctx->stream>>>(Dall, (int)d, sglob.p, ns,
+                                                                     Q.p);
+        PG_LAUNCHED(ctx);
+        k_gather_i32<<<blocks(ns), 256, 0, ctx->stream>>>(w.p, sel.p, ns, starts.p);
+        PG_LAUNCHED(ctx);
+        PG_TRY(pg_search_internal(ctx, Dall, n0, (int32_t)d, idx->metric, l.nbr, l.deg, Ri, l.rows,
+                                  Q.p, ns, starts.p, ef, ef, 0, W.p, Ws.p));
+        k_scatter_first<<<blocks(ns), 256, 0, ctx->stream>>>(w.p, sel.p, ns, W.p, ef);
+        PG_LAUNCHED(ctx);
+        // N_i(u) = Prune(u, W_i)
+        PG_TRY(off.alloc(ctx, (size_t)ns + 1));
+        PG_TRY(nnb.alloc(ctx, (size_t)(ns * Ri)));
+        PG_TRY(ndg.alloc(ctx, (size_t)ns));
+        k_fill_off<<<blocks(ns + 1), 256, 0, ctx->stream>>>(off.p, ns, ef);
+        PG_LAUNCHED(ctx);
+        PG_TRY(pg_prune_internal(ctx, Dall, N, (int32_t)d, idx->metric, off.p, W.p, Ri,
+                                 p.alpha_final_deg, facts, nnb.p, ndg.p, nullptr, ns, sglob.p));
+        // reverse step: old rows that gained in-edges re-prune their list plus the in-edges
+        const int64_t cnt_rows = l.count;
+        PG_TRY(cnt.alloc(ctx, (size_t)cnt_rows));
+        PG_TRY(in_off.alloc(ctx, (size_t)cnt_rows + 1));
+        PG_TRY(cur.alloc(ctx, (size_t)cnt_rows + 1));
+        PG_TRY(inl.alloc(ctx, (size_t)(ns * Ri)));
+        PG_TRY_CUDA(ctx, cudaMemsetAsync(cnt.p, 0, (size_t)cnt_rows * 4, ctx->stream));
+        k_in_count<<<blocks(ns * Ri), 256, 0, ctx->stream>>>(nnb.p, ndg.p, ns, Ri, l.rows, cnt.p);
+        PG_LAUNCHED(ctx);
+        PG_TRY(pg_scan_counts(ctx, cnt.p, cnt_rows, in_off.p));
+        PG_TRY_CUDA(ctx, cudaMemcpyAsync(cur.p, in_off.p, (size_t)(cnt_rows + 1) * 8,
+                                         cudaMemcpyDeviceToDevice, ctx->stream));
+        k_in_fill<<<blocks(ns * Ri), 256, 0, ctx->stream>>>(nnb.p, ndg.p, ns, Ri, l.rows, sglob.p,
+                                                            cur.p, inl.p);
+        PG_LAUNCHED(ctx);
+        PG_TRY(flag.alloc(ctx, (size_t)cnt_rows));
+        PG_TRY(pos.alloc(ctx, (size_t)cnt_rows + 1));
+        k_flag_pos<<<blocks(cnt_rows), 256, 0, ctx->stream>>>(cnt.p, cnt_rows, flag.p);
+        PG_LAUNCHED(ctx);
+        PG_TRY(pg_scan_counts(ctx, flag.p, cnt_rows, pos.p));
+        int64_t na = 0;
+        PG_TRY_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned, pos.p + cnt_rows, 8, cudaMemcpyDeviceToHost,
+                                         ctx->stream));
+        PG_TRY(pg_sync_check(ctx, "insert"));
+        memcpy(&na, ctx->h_pinned, 8);
+        if (na > 0) {
+            PG_TRY(A.alloc(ctx, (size_t)na));
+            PG_TRY(sz.alloc(ctx, (size_t)na));
+            PG_TRY(uoff.alloc(ctx, (size_t)na + 1));
+            k_compact<<<blocks(cnt_rows), 256, 0, ctx->stream>>>(cnt.p, cnt_rows, pos.p, A.p);
+            PG_LAUNCHED(ctx);
+            k_union_sizes<<<blocks(na), 256, 0, ctx->stream>>>(A.p, na, l.deg, Ri, cnt.p, sz.p);
+            PG_LAUNCHED(ctx);
+            PG_TRY(pg_scan_counts(ctx, sz.p, na, uoff.p));
+            PG_TRY(ucand.alloc(ctx, (size_t)(na * Ri + ns * Ri)));
+            k_union_fill<<<(unsigned)((na + 7) / 8), 256, 0, ctx->stream>>>(
+                A.p, na, l.nbr, l.deg, Ri, in_off.p, inl.p, uoff.p, ucand.p);
+            PG_LAUNCHED(ctx);
+            const int32_t *selfp = A.p;
+            if (l.gid) {
+                PG_TRY(self.alloc(ctx, (size_t)na));
+                k_gather_i32<<<blocks(na), 256, 0, ctx->stream>>>(l.gid, A.p, na, self.p);
+                PG_LAUNCHED(ctx);
+                selfp = self.p;
+            }
+            PG_TRY(tn.alloc(ctx, (size_t)(na * Ri)));
+            PG_TRY(td.alloc(ctx, (size_t)na));
+            PG_TRY(pg_prune_internal(ctx, Dall, N, (int32_t)d, idx->metric, uoff.p, ucand.p, Ri,
+                                     p.alpha_final_deg, facts, tn.p, td.p, nullptr, na, selfp));
+            k_scatter_rows<<<blocks(na * Ri), 256, 0, ctx->stream>>>(A.p, na, tn.p, td.p, Ri,
+                                                                    l.nbr, l.deg);
+            PG_LAUNCHED(ctx);
+        }
+        // append the new members
+        if (l.count + ns > l.cap) return pg_fail(ctx, PG_ERR_INTERNAL, "insert: layer capacity");
+        PG_TRY_CUDA(ctx, cudaMemcpyAsync(l.nbr + l.count * Ri, nnb.p, (size_t)(ns * Ri) * 4,
+                                         cudaMemcpyDeviceToDevice, ctx->stream));
+        PG_TRY_CUDA(ctx, cudaMemcpyAsync(l.deg + l.count, ndg.p, (size_t)ns * 4,
+                                         cudaMemcpyDeviceToDevice, ctx->stream));
+        if (l.gid) {
+            k_append_members<<<blocks(ns), 256, 0, ctx->stream>>>(sglob.p, ns, l.count, l.gid,
+                                                                  l.rows);
+            PG_LAUNCHED(ctx);
+        }
+        l.count += ns;
+        PG_TRY(pg_sync_check(ctx, "insert"));
+    }
+    idx->n = N;
+    return pg_sync_check(ctx, "pg_index_insert");
 }

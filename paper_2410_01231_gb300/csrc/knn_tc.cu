@@ -740,7 +740,6 @@ bool pg_knn_tc_supported(int d, int K) {
     return dp <= 256 && K >= 1 && K <= KTC && tc_layout(dp).total + 1024 <= 227 * 1024;
 }
 
-pg_status pg_scan_counts(pg_ctx *ctx, const int32_t *cnt, int64_t n, int64_t *off);
 
 namespace {
 

@@ -121,6 +121,9 @@ struct Scratch {
     ~Scratch() { release(); }
 };
 
+// Exclusive prefix sum of n int32 counts into n + 1 int64 offsets (async).
+pg_status pg_scan_counts(pg_ctx *ctx, const int32_t *cnt, int64_t n, int64_t *off);
+
 // Synchronise and translate the device error word.
 pg_status pg_sync_check(pg_ctx *ctx, const char *where);
 // Reset statistics counters (async).

@@ -332,6 +332,45 @@ def test_build_nswg_integer_matches_oracle(ctx, pg):
         assert (gid == lay.gid).all() and (dg == lay.deg).all() and (nb == lay.nbr).all(), i
 
 
+@pytest.mark.parametrize("upper_beam", [1, 8])
+def test_insert_batches_match_oracle(ctx, pg, upper_beam):
+    """Two insertion batches into an NSWG index (Algorithm 4 on a snapshot)
+    give the oracle's layers, and queries on the grown index agree."""
+    D, Q, _ = synthetic.workload(1, n=3600, nq=50)
+    n0 = 2800
+    p = dict(K=24, L=48, R=32, M=16, alpha_deg=70.0, iters=1, seed=5)
+    idx = pg.Index.build_nswg(ctx, dev(D[:n0]), metric="l2", **p)
+    layers, ep, _ = oracle.build_nswg(D[:n0], 24, 48, 16, 32, 70.0, 60.0, 1, "l2", 5)
+    idx.reserve(3600)
+    for a, b in ((n0, 3300), (3300, 3600)):
+        idx.insert(dev(D[a:b]), 40, upper_beam)
+        layers = oracle.insert_batch(D[:b], layers, ep, a, 40, 60.0, "l2", 5, 16, upper_beam)
+    info = idx.info()
+    assert info["n"] == 3600 and info["n_layers"] == len(layers)
+    for i, L in enumerate(layers):
+        gid, nb, dg = _export(idx, i)
+        assert (gid == L.gid).all(), i
+        assert (dg == L.deg).all(), i
+        assert (nb == L.nbr).all(), i
+    oi, _ = oracle.search_nswg(D, layers, ep, Q, 10, 64, "l2", ef_upper=upper_beam)
+    gi, _ = idx.search(dev(Q), 10, 64, upper_beam=upper_beam)
+    assert (host(gi) == oi).all()
+
+
+def test_insert_needs_reserved_capacity(ctx, pg):
+    D = int_points(600)
+    idx = pg.Index.build_nswg(ctx, dev(D[:500]), metric="l2", K=16, L=32, R=16, M=16,
+                              alpha_deg=70.0, iters=1, seed=1)
+    with pytest.raises(pg.PGError) as e:
+        idx.insert(dev(D[500:]), 32)
+    assert e.value.status == 5
+    idx.reserve(550)
+    with pytest.raises(pg.PGError):
+        idx.insert(dev(D[500:]), 32)
+    idx.insert(dev(D[500:550]), 32)
+    assert idx.info()["n"] == 550
+
+
 def test_connect_without_free_slot_is_reported_by_both_sides(ctx, pg):
     """R=16 after alpha=70 pruning leaves every reached node full while some
     node is still unreached: the oracle and the library both refuse."""
