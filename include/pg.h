@@ -332,6 +332,42 @@ pg_status pg_index_reserve(pg_ctx *ctx, pg_index *index, int64_t capacity);
 pg_status pg_index_insert(pg_ctx *ctx, pg_index *index, const float *X, int64_t m, int32_t ef,
                           int32_t upper_beam);
 
+/* -------------------------------------------------------------- serving */
+
+/* A serving loop over a growable index: one host worker thread drains a
+ * FIFO of query batches and insertion batches on the context's stream.
+ * While the server runs, ctx and index belong to it (the caller issues no
+ * other call on them until pg_serve_stop).  Requests complete in
+ * submission order.  Consecutive query requests with equal
+ * (k, beam, upper_beam) are merged into one search launch of at most
+ * max_batch queries; an insertion (pg_index_insert) runs alone, so a query
+ * sees exactly the points inserted before it was submitted.  Host buffers
+ * of a request must stay valid until it completes. */
+typedef struct pg_server pg_server;
+
+/* Start the worker (1 <= max_batch <= 65536). */
+pg_status pg_serve_start(pg_ctx *ctx, pg_index *index, int32_t max_batch, pg_server **out);
+
+/* Enqueue nq HOST query rows Q [nq][d]; results go to HOST out_ids [nq][k]
+ * and out_dist [nq][k] (pg_search semantics).  *ticket identifies it. */
+pg_status pg_serve_submit_query(pg_server *server, const float *Q, int64_t nq, int32_t k,
+                                int32_t beam, int32_t upper_beam, int32_t *out_ids,
+                                float *out_dist, int64_t *ticket);
+
+/* Enqueue the insertion of m HOST rows X [m][d] (pg_index_insert). */
+pg_status pg_serve_submit_insert(pg_server *server, const float *X, int64_t m, int32_t ef,
+                                 int32_t upper_beam, int64_t *ticket);
+
+/* Wait up to timeout_s seconds (0: poll) for `ticket`; *done = 1 once it has
+ * completed, and the return value is then that request's status. */
+pg_status pg_serve_wait(pg_server *server, int64_t ticket, double timeout_s, int32_t *done);
+
+/* host_stats4 = {launch batches, requests, queries, inserted points} so far. */
+pg_status pg_serve_stats(pg_server *server, int64_t *host_stats4);
+
+/* Finish every queued request, join the worker and free the server. */
+pg_status pg_serve_stop(pg_server *server);
+
 /* Seconds spent per build phase by the last build on this index:
  * knn, prune, union, connect, acquire, layers (host array of 6). */
 pg_status pg_index_phase_seconds(const pg_index *index, double *host_seconds6);

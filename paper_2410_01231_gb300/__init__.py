@@ -86,6 +86,12 @@ _sig("pg_ctx_kernel_work", C.c_int, [P, C.c_char_p, P])
 _sig("pg_prune_noalloc", C.c_int, [P, P, i64, i32, C.c_int, P, P, i32, dbl, P, P])
 _sig("pg_index_reserve", C.c_int, [P, P, i64])
 _sig("pg_index_insert", C.c_int, [P, P, P, i64, i32, i32])
+_sig("pg_serve_start", C.c_int, [P, P, i32, P])
+_sig("pg_serve_submit_query", C.c_int, [P, P, i64, i32, i32, i32, P, P, P])
+_sig("pg_serve_submit_insert", C.c_int, [P, P, i64, i32, i32, P])
+_sig("pg_serve_wait", C.c_int, [P, i64, dbl, P])
+_sig("pg_serve_stats", C.c_int, [P, P])
+_sig("pg_serve_stop", C.c_int, [P])
 
 EXPORTS = ["pg_default_params", "pg_ctx_create", "pg_ctx_destroy", "pg_last_error", "pg_ctx_sync",
            "pg_ctx_launches", "pg_build_knn", "pg_knn_query", "pg_prune", "pg_reverse_union",
@@ -93,7 +99,9 @@ EXPORTS = ["pg_default_params", "pg_ctx_create", "pg_ctx_destroy", "pg_last_erro
            "pg_build_nswg", "pg_search", "pg_search_host", "pg_index_destroy", "pg_index_info",
            "pg_index_layer", "pg_index_phase_seconds", "pg_index_export_layer",
            "pg_ctx_set_timing", "pg_ctx_kernel_time", "pg_ctx_counter",
-           "pg_ctx_kernel_work", "pg_prune_noalloc", "pg_index_reserve", "pg_index_insert"]
+           "pg_ctx_kernel_work", "pg_prune_noalloc", "pg_index_reserve", "pg_index_insert",
+           "pg_serve_start", "pg_serve_submit_query", "pg_serve_submit_insert", "pg_serve_wait",
+           "pg_serve_stats", "pg_serve_stop"]
 
 
 class PGError(RuntimeError):
@@ -417,5 +425,65 @@ class Index:
     def __del__(self):
         try:
             self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------- serving
+class Server:
+    """Serving loop over a growable index (pg_serve_*): query and insertion
+    requests with host buffers, completed in submission order."""
+
+    def __init__(self, index: Index, max_batch: int = 1024):
+        self.index, self.ctx = index, index.ctx
+        self._h = C.c_void_p()
+        self.ctx._check(_lib.pg_serve_start(self.ctx.handle, index._h, max_batch,
+                                            C.byref(self._h)), "pg_serve_start")
+        self._keep = {}
+
+    def submit_query(self, Q: np.ndarray, k: int, beam: int, upper_beam: int = UPPER_BEAM):
+        """Returns (ticket, ids, dist); ids/dist are filled once the ticket completes."""
+        Q = np.ascontiguousarray(Q, np.float32)
+        ids = np.empty((Q.shape[0], k), np.int32)
+        dist = np.empty((Q.shape[0], k), np.float32)
+        t = C.c_int64()
+        self.ctx._check(_lib.pg_serve_submit_query(
+            self._h, Q.ctypes.data_as(C.c_void_p), Q.shape[0], k, beam, upper_beam,
+            ids.ctypes.data_as(C.c_void_p), dist.ctypes.data_as(C.c_void_p), C.byref(t)),
+            "pg_serve_submit_query")
+        self._keep[t.value] = (Q, ids, dist)
+        return t.value, ids, dist
+
+    def submit_insert(self, X: np.ndarray, ef: int, upper_beam: int = 1) -> int:
+        X = np.ascontiguousarray(X, np.float32)
+        t = C.c_int64()
+        self.ctx._check(_lib.pg_serve_submit_insert(self._h, X.ctypes.data_as(C.c_void_p),
+                                                    X.shape[0], ef, upper_beam, C.byref(t)),
+                        "pg_serve_submit_insert")
+        self._keep[t.value] = (X,)
+        return t.value
+
+    def wait(self, ticket: int, timeout_s: float = 60.0) -> bool:
+        done = C.c_int32()
+        self.ctx._check(_lib.pg_serve_wait(self._h, ticket, timeout_s, C.byref(done)),
+                        "pg_serve_wait")
+        if done.value:
+            self._keep.pop(ticket, None)
+        return bool(done.value)
+
+    def stats(self):
+        a = (C.c_int64 * 4)()
+        _lib.pg_serve_stats(self._h, a)
+        return dict(zip(["batches", "requests", "queries", "inserted"], list(a)))
+
+    def stop(self):
+        if getattr(self, "_h", None):
+            _lib.pg_serve_stop(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.stop()
         except Exception:
             pass

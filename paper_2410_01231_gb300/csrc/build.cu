@@ -367,6 +367,8 @@ extern "C" pg_status pg_build_nswg(pg_ctx *ctx, const float *D, int64_t n, int32
 
 extern "C" void pg_index_destroy(pg_index *index) { delete index; }
 
+int pg_index_dim(const pg_index *index) { return index->d; }
+
 extern "C" pg_status pg_index_info(const pg_index *idx, int32_t *n_layers, int64_t *n,
                                    int64_t *ep_top, int64_t *ep_base) {
     if (!idx) return PG_ERR_INVALID_ARG;

@@ -121,6 +121,9 @@ struct Scratch {
     ~Scratch() { release(); }
 };
 
+// Dimension of the points of an index.
+int pg_index_dim(const pg_index *index);
+
 // Exclusive prefix sum of n int32 counts into n + 1 int64 offsets (async).
 pg_status pg_scan_counts(pg_ctx *ctx, const int32_t *cnt, int64_t n, int64_t *off);
 

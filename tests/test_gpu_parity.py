@@ -412,3 +412,41 @@ def test_build_rejects_bad_params(ctx, pg):
     with pytest.raises(pg.PGError) as e:
         pg.Index.build_rng(ctx, dev(D), R=100)
     assert e.value.status == 1
+
+
+# ------------------------------------------------------------- serving
+def test_serving_loop_equals_the_same_calls_in_order(ctx, pg):
+    """Interleaved query and insertion requests through the serving loop
+    give what the same calls made one after another give; consecutive
+    queries are merged into shared launches."""
+    D, Q, _ = synthetic.workload(1, n=3600, nq=120)
+    n0 = 3000
+    p = dict(K=24, L=48, R=32, M=16, alpha_deg=70.0, iters=1, seed=2)
+    a = pg.Index.build_nswg(ctx, dev(D[:n0]), metric="l2", **p)
+    ctx2 = pg.Context()
+    b = pg.Index.build_nswg(ctx2, dev(D[:n0]), metric="l2", **p)
+    a.reserve(3600)
+    b.reserve(3600)
+    plan = [("q", 0, 7), ("q", 7, 40), ("q", 40, 41), ("i", 3000, 3300), ("q", 41, 90),
+            ("q", 90, 120), ("i", 3300, 3600), ("q", 0, 60)]
+    srv = pg.Server(b, max_batch=64)
+    tickets = []
+    for kind, s0, s1 in plan:
+        if kind == "q":
+            tickets.append(srv.submit_query(Q[s0:s1], 10, 48, 4))
+        else:
+            tickets.append((srv.submit_insert(D[s0:s1], 40, 4), None, None))
+    for t, _, _ in tickets:
+        assert srv.wait(t, 120.0)
+    st = srv.stats()
+    srv.stop()
+    assert st["requests"] == len(plan) and st["batches"] < len(plan)
+    assert st["inserted"] == 600 and st["queries"] == 7 + 33 + 1 + 49 + 30 + 60
+    for (kind, s0, s1), (t, ids, dist) in zip(plan, tickets):
+        if kind == "i":
+            a.insert(dev(D[s0:s1]), 40, 4)
+            continue
+        gi, gd = a.search(dev(Q[s0:s1]), 10, 48, upper_beam=4)
+        assert (host(gi) == ids).all() and np.allclose(host(gd), dist)
+    ia, ib = a.info(), b.info()
+    assert ia == ib and ia["n"] == 3600
