@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-queries", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
     return ap.parse_args()
 
 
@@ -315,6 +316,52 @@ def run_ours(args):
                 "latency": "single-query requests, host wall time per call incl. launch + sync"}
         idx.close()
 
+    # ---------------------------------------------------------- serving
+    # A mixed request stream through the serving loop on the index just
+    # measured: 300 query requests of 1-128 queries (k = 10, beam 48,
+    # upper_beam 16) with two insertion batches of 1% of n each after
+    # requests 100 and 200, all queued at once (merged launches), then
+    # single-query requests one at a time for the request latency.
+    serve = {}
+    if not args.no_serve:
+        ins = max(100, n // 100)
+        X = synthetic.inserts(WORKLOAD, 2 * ins)
+        Qh = Q if isinstance(Q, np.ndarray) else np.asarray(Q)
+        idx = pg.Index.build_rng(ctx, Dd, **params)
+        idx.reserve(n + 2 * ins)
+        srv = pg.Server(idx, max_batch=1024)
+        rs = np.random.default_rng(7)
+        sizes = rs.choice([1, 8, 32, 128], size=300)
+        barrier()
+        t0 = time.perf_counter()
+        last, at, nqs = 0, 0, 0
+        for r, sz in enumerate(sizes):
+            if r in (100, 200):
+                j = 0 if r == 100 else 1
+                last = srv.submit_insert(X[j * ins:(j + 1) * ins], 64, 16)
+            rows = [(at + i) % nq for i in range(int(sz))]
+            at += int(sz)
+            nqs += int(sz)
+            last, _, _ = srv.submit_query(Qh[rows], w["k"], 48, 16)
+        srv.wait(last, 600.0)
+        t_mix = time.perf_counter() - t0
+        st = srv.stats()
+        lat = []
+        for i in range(200):
+            t1 = time.perf_counter()
+            tk, _, _ = srv.submit_query(Qh[i:i + 1], w["k"], 48, 16)
+            srv.wait(tk, 60.0)
+            lat.append((time.perf_counter() - t1) * 1e3)
+        srv.stop()
+        idx.close()
+        serve = {"requests": int(st["requests"]), "launch_batches": int(st["batches"]),
+                 "queries": nqs, "inserted": int(st["inserted"]), "seconds": t_mix,
+                 "requests_per_s": len(sizes) / t_mix, "queries_per_s": nqs / t_mix,
+                 "single_query_p50_ms": float(np.percentile(lat, 50)),
+                 "single_query_p99_ms": float(np.percentile(lat, 99)),
+                 "stream": "300 query requests of 1/8/32/128 queries (k=10, beam 48) with two "
+                           f"insertion batches of {ins} points, host buffers, queued at once"}
+
     # ------------------------------------------------ the other precision form
     forms = {args.precision: {"ms_per_build": ms, "points_per_s": value}}
     identical = None
@@ -427,7 +474,7 @@ def run_ours(args):
                    "l2": (f"inputs larger than L2 ({D.nbytes >> 20} MB points)" if D.nbytes > 129e6
                           else f"inputs smaller than L2 ({D.nbytes >> 20} MB points; test size)"), "parallelism": "replicas"},
         "forms": forms, "forms_identical_graph": identical,
-        "queries": qres, "phase_s": ph,
+        "queries": qres, "serving": serve, "phase_s": ph,
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
         "kernel_launches_per_step": {k: v[1] / args.steps for k, v in kt.items()},
         "connect_edges_per_step": conn_edges / max(1, args.steps + args.warmup),

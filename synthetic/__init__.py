@@ -136,6 +136,20 @@ def make(kind: str, n: int, d: int, clusters: int, seed: int, nq: int, qseed: in
     return D, Q
 
 
+def inserts(c: int, m: int) -> np.ndarray:
+    """m further points of workload ``c`` for insertion (same cluster centres
+    as its points, seed 9012 + c)."""
+    w = WORKLOADS[c]
+    kind, d, k, seed = w["kind"], w["d"], w["clusters"], 9012 + c
+    if kind == "int":
+        return mixture_int(m, d, k, seed, centres=mixture_int(1, d, k, 1234 + c)[1])[0]
+    if kind == "float":
+        return mixture_float(m, d, k, seed, centres=mixture_float(1, d, k, 1234 + c)[1])[0]
+    if kind == "unit":
+        return unit_gaussian(m, d, seed)
+    return sphere_mixture(m, d, k, seed, centres=sphere_mixture(1, d, k, 1234 + c)[1])[0]
+
+
 def workload(c: int, n: int | None = None, nq: int | None = None):
     """(D, Q, params) of workload ``c``; ``n``/``nq`` shrink it for tests."""
     w = dict(WORKLOADS[c])
