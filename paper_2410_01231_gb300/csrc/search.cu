@@ -4,7 +4,7 @@
 // queries.
 //
 // Per warp, in shared memory: the pool (<= L entries sorted by (s, id), the
-// expanded flag in bit 31 of the id; double-buffered for the merge), a lossy
+// expanded flag in bit 31 of the id), a lossy
 // visited table (a node id per slot, last writer wins: it never reports an
 // unvisited node as visited, it may forget a visited one), the query vector
 // and a 32-entry staging area.  One expansion: find the first unexpanded
@@ -13,7 +13,9 @@
 // lanes, drop those that cannot enter the pool (worse than the last entry
 // of a full pool, or already present -- found by an exact (s, id) binary
 // search, which covers what the table forgot), sort the rest in registers
-// and merge them into the pool by rank, truncating at L.
+// and merge them into the pool in place: only the entries behind the first
+// insertion point move (read into registers chunk by chunk from the back,
+// then written to their shifted slots), truncating at L.
 //
 // Because the pool is always the L best of everything inserted so far, a
 // node that was evaluated and left the pool can never re-enter it; the
@@ -52,8 +54,12 @@ struct SearchParams {
     int *qcounter;
 };
 
+// the pool arrays hold an even number of slots, so that the query row that
+// follows the table and the staging area starts on a 16-byte boundary
+__host__ __device__ inline int pool_slots(int L) { return (L + 1) & ~1; }
+
 __host__ __device__ inline size_t search_warp_smem(int L, int hbits, int d) {
-    size_t b = (size_t)L * 8 * 2 + ((size_t)4 << hbits) + 32 * 8 + (size_t)d * 4;
+    size_t b = (size_t)pool_slots(L) * 8 + ((size_t)4 << hbits) + 32 * 8 + (size_t)d * 4;
     return (b + 15) & ~(size_t)15;
 }
 
@@ -76,11 +82,10 @@ __device__ void search_one(const SearchParams &P, int64_t qi, unsigned char *ws,
                            unsigned long long &n_exp, unsigned long long &n_eval) {
     const int lane = threadIdx.x & 31, team = lane >> 3, li = lane & 7;
     const int L = P.L, d = P.d, nch = d / 4;
+    const int Lp = pool_slots(L);
     float *pdA = reinterpret_cast<float *>(ws);
-    int *piA = reinterpret_cast<int *>(pdA + L);
-    float *pdB = reinterpret_cast<float *>(piA + L);
-    int *piB = reinterpret_cast<int *>(pdB + L);
-    int *htab = piB + L;
+    int *piA = reinterpret_cast<int *>(pdA + Lp);
+    int *htab = piA + Lp;
     const int H = 1 << P.hbits;
     float *nd = reinterpret_cast<float *>(htab + H);
     int *ni = reinterpret_cast<int *>(nd + 32);
@@ -196,45 +201,62 @@ __device__ void search_one(const SearchParams &P, int64_t qi, unsigned char *ws,
                 }
                 if (id == INT_MAX) s = INFINITY;
             }
-            warp_sort32(s, id);
-            unsigned nb = __ballot_sync(0xffffffffu, id != INT_MAX);
-            int m2 = __popc(nb);
+            const unsigned live = __ballot_sync(0xffffffffu, id != INT_MAX);
+            const int m2 = __popc(live);
             if (m2 == 0) continue;
+            if (m2 > 1) {
+                warp_sort32(s, id);  // survivors first, ascending
+            } else {
+                const int src = __ffs(live) - 1;
+                s = __shfl_sync(0xffffffffu, s, src);
+                id = __shfl_sync(0xffffffffu, id, src);
+                if (lane != 0) {
+                    s = INFINITY;
+                    id = INT_MAX;
+                }
+            }
             __syncwarp();
             if (lane < m2) {
                 nd[lane] = s;
                 ni[lane] = id;
             }
-            __syncwarp();
-            // merge by rank into the other buffer
-            for (int i = lane; i < size; i += 32) {
-                float es = pdA[i];
-                int eid = piA[i];
-                int key = eid & ID_MASK;
-                int lo = 0, hi = m2;
-                while (lo < hi) {
-                    int mid = (lo + hi) >> 1;
-                    if (pair_less(nd[mid], ni[mid], es, key)) lo = mid + 1;
-                    else hi = mid;
-                }
-                int dst = i + lo;
-                if (dst < L) {
-                    pdB[dst] = es;
-                    piB[dst] = eid;
-                }
-            }
+            // final slots of the new entries, against the pool before the merge
             int mydst = L;
-            if (lane < m2) {
-                mydst = lane + pool_lower_bound(pdA, piA, size, s, id);
-                if (mydst < L) {
-                    pdB[mydst] = s;
-                    piB[mydst] = id;
+            if (lane < m2) mydst = lane + pool_lower_bound(pdA, piA, size, s, id);
+            const int first = __shfl_sync(0xffffffffu, mydst, 0);
+            __syncwarp();
+            // entries at or after `first` move right by the number of new
+            // entries below them; chunks from the back, so every slot is read
+            // before it is overwritten
+            const int moved = size - first;
+            for (int c0 = first + ((moved - 1) & ~31); moved > 0 && c0 >= first; c0 -= 32) {
+                const int i = c0 + lane;
+                float es = 0.f;
+                int eid = 0, dst = L;
+                if (i < size) {
+                    es = pdA[i];
+                    eid = piA[i];
+                    const int key = eid & ID_MASK;
+                    int lo = 0, hi = m2;
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        if (pair_less(nd[mid], ni[mid], es, key)) lo = mid + 1;
+                        else hi = mid;
+                    }
+                    dst = i + lo;
                 }
+                __syncwarp();
+                if (dst < L) {
+                    pdA[dst] = es;
+                    piA[dst] = eid;
+                }
+                __syncwarp();
             }
-            int first = __shfl_sync(0xffffffffu, mydst, 0);
+            if (mydst < L) {
+                pdA[mydst] = s;
+                piA[mydst] = id;
+            }
             size = min(L, size + m2);
-            float *tf = pdA; pdA = pdB; pdB = tf;
-            int *ti = piA; piA = piB; piB = ti;
             if (first < cursor) cursor = first;
             __syncwarp();
         }
