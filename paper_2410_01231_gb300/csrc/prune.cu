@@ -75,6 +75,10 @@ struct RowStats {
     unsigned long long cands = 0, scanned = 0, tests = 0, rechecks = 0, flips = 0, edges = 0;
 };
 
+// REG: byte rows of at most 128 bytes and R <= 32; lane l keeps the row of
+// the l-th kept point in registers, so a candidate is tested against every
+// kept point at once.
+template <bool REG>
 __device__ void prune_row(const PruneParams &P, int64_t row, const int32_t *cand, int64_t cnt,
                           unsigned char *wsmem, RowStats &st) {
     const int64_t u = P.self_ids ? (int64_t)P.self_ids[row] : row;  // the point being pruned
@@ -216,6 +220,60 @@ __device__ void prune_row(const PruneParams &P, int64_t row, const int32_t *cand
     // 4. the scan
     int kept = 0;
     int j = 0;
+    if constexpr (REG) {
+        const int nch16 = d >> 4;  // <= 8
+        uint4 *vrow = reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(uq) + d);
+        uint4 kr[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) kr[c] = make_uint4(0u, 0u, 0u, 0u);
+        float ksl = 0.f;  // s(u, w) of this lane's kept point
+        for (; j < m && kept < P.R; ++j) {
+            const int v = ci[j];
+            const float suv = cs[j];
+            if (lane < nch16)
+                vrow[lane] = __ldg(reinterpret_cast<const uint4 *>(D8 + (int64_t)v * d) + lane);
+            __syncwarp();
+            bool occ = false;
+            if (lane < kept && ksl < suv) {  // exact data: the comparisons are exact
+                unsigned acc = 0;
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+                    if (c < nch16) acc = sq_diff_u8(vrow[c], kr[c], acc);
+                const float svw = (float)acc;
+                st.tests++;
+                if (svw < suv) {
+                    int c3 = 1;
+                    if (!P.alpha60) {
+                        c3 = angle_certain(ksl, P.em.err(ksl), svw, P.em.err(svw), suv,
+                                           P.em.err(suv), P.cos_af);
+                        if (c3 < 0) {
+                            c3 = angle_exceeds64((double)ksl, (double)svw, (double)suv, P.cos_a);
+                            st.rechecks++;
+                            const bool naive =
+                                ((ksl + svw) - suv) < 2.f * P.cos_af * sqrtf(ksl * svw);
+                            if ((c3 != 0) != naive) st.flips++;
+                        }
+                    }
+                    occ = c3 != 0;
+                }
+            }
+            if (!__any_sync(0xffffffffu, occ)) {
+                if (lane == kept) {
+#pragma unroll
+                    for (int c = 0; c < 8; ++c)
+                        if (c < nch16) kr[c] = vrow[c];
+                    ksl = suv;
+                }
+                if (lane == 0) {
+                    kid[kept] = v;
+                    ks[kept] = suv;
+                    kpos[kept] = j;
+                }
+                ++kept;
+            }
+            __syncwarp();
+        }
+    } else {
     for (; j < m && kept < P.R; ++j) {
         const int v = ci[j];
         const float suv = cs[j];
@@ -291,6 +349,7 @@ __device__ void prune_row(const PruneParams &P, int64_t row, const int32_t *cand
             __syncwarp();
         }
     }
+    }
     st.scanned += j;
     st.edges += kept;
     for (int t = lane; t < P.R; t += 32) P.nbr[row * P.R + t] = t < kept ? kid[t] : -1;
@@ -320,6 +379,7 @@ __device__ void flush_stats(const PruneParams &P, RowStats &st, unsigned long lo
     }
 }
 
+template <bool REG>
 __global__ void __launch_bounds__(PW * 32) k_prune(PruneParams P) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -347,7 +407,7 @@ __global__ void __launch_bounds__(PW * 32) k_prune(PruneParams P) {
             }
             continue;
         }
-        prune_row(P, u, P.cand + a, b - a, ws, st);
+        prune_row<REG>(P, u, P.cand + a, b - a, ws, st);
         ++rows;
     }
     flush_stats(P, st, rows, false);
@@ -370,7 +430,7 @@ __global__ void __launch_bounds__(32) k_prune_long(PruneParams P) {
             for (int t = lane; t < P.R; t += 32) P.nbr[u * P.R + t] = -1;
             continue;
         }
-        prune_row(P, u, P.cand + a, b - a, smem, st);
+        prune_row<false>(P, u, P.cand + a, b - a, smem, st);
         ++rows;
     }
     flush_stats(P, st, rows, true);
@@ -528,14 +588,17 @@ pg_status pg_prune_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d, p
     P.long_list = ints.p + 4;
     P.cap = CMAX;
     size_t smem = warp_smem_bytes(CMAX, d) * PW;
-    PG_TRY_CUDA(ctx, cudaFuncSetAttribute(k_prune, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    // byte rows of <= 128 bytes and R <= 32: kept rows held in registers
+    const bool reg = D8 && R <= 32 && d <= 128;
+    auto kern = reg ? k_prune<true> : k_prune<false>;
+    PG_TRY_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)smem));
     int blocks_per_sm = 0;
-    PG_TRY_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_prune, PW * 32,
+    PG_TRY_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, PW * 32,
                                                                    smem));
     if (blocks_per_sm < 1) blocks_per_sm = 1;
     pg_timer_begin(ctx, TM_PRUNE);
-    k_prune<<<ctx->num_sms * blocks_per_sm, PW * 32, smem, ctx->stream>>>(P);
+    kern<<<ctx->num_sms * blocks_per_sm, PW * 32, smem, ctx->stream>>>(P);
     PG_LAUNCHED(ctx);
     pg_timer_end(ctx, TM_PRUNE);
     P.cap = CMAX_LONG;
@@ -585,13 +648,13 @@ cudaError_t pg_prune_launch_on(cudaStream_t stream, int num_sms, const float *D,
     cudaError_t e = cudaMemsetAsync(ints, 0, 4 * sizeof(int), stream);
     if (e != cudaSuccess) return e;
     const size_t smem = warp_smem_bytes(CMAX, d) * PW;
-    e = cudaFuncSetAttribute(k_prune, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(k_prune<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int bps = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_prune, PW * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_prune<false>, PW * 32, smem);
     if (e != cudaSuccess) return e;
     if (bps < 1) bps = 1;
-    k_prune<<<num_sms * bps, PW * 32, smem, stream>>>(P);
+    k_prune<false><<<num_sms * bps, PW * 32, smem, stream>>>(P);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     P.cap = CMAX_LONG;
