@@ -156,8 +156,21 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-__device__ __forceinline__ void epi_barrier() {
-    asm volatile("bar.sync 1, 128;" ::: "memory");
+__device__ __forceinline__ void epi_barrier(int nthreads = 128) {
+    asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+}
+
+// Named barrier of the epilogue threads that also ORs a flag over them, so
+// that every epilogue thread takes the same abort decision.
+__device__ __forceinline__ bool epi_barrier_or(int nthreads, bool flag) {
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred pi, po;\n setp.ne.u32 pi, %1, 0;\n"
+        " bar.red.or.pred po, 1, %2, pi;\n selp.u32 %0, 1, 0, po;\n}"
+        : "=r"(r)
+        : "r"((uint32_t)flag), "r"(nthreads)
+        : "memory");
+    return r != 0;
 }
 
 // Per-row max-heap of the K best (s, id) pairs in shared memory, layout
@@ -241,22 +254,31 @@ __device__ __forceinline__ void heap_sort(float *Hs, int *Hi, int row, int cnt) 
 }
 
 struct TcLayout {
-    uint32_t a, b, ls, li, nbuf, bars, misc, total;
+    uint32_t a, b, ls, li, nbuf, cnt, bars, misc, total;
 };
 
-__host__ __device__ inline TcLayout tc_layout(int dp) {
+// H = 1: four epilogue warps, one per TMEM lane quarter, each thread one
+// row and all 128 columns of a tile; 3 candidate stages.  H = 2: eight
+// epilogue warps, two per lane quarter taking 64 columns each, so two
+// threads and two heaps per row (merged at the end); 2 candidate stages.
+__host__ __device__ constexpr int tc_threads(int H) { return 64 + 128 * H; }
+__host__ __device__ constexpr int tc_stages(int H) { return H == 1 ? 3 : 2; }
+
+__host__ __device__ inline TcLayout tc_layout(int dp, int H) {
     TcLayout L;
     uint32_t o = 0;
     L.a = o;
     o += (uint32_t)TM * dp * 2;
     L.b = o;
-    o += (uint32_t)STAGES * TN * dp * 2;
-    L.ls = o;  // [KTC][TM] per-row heaps: distances
-    o += (uint32_t)KTC * TM * 4;
-    L.li = o;  // [KTC][TM] ids
-    o += (uint32_t)KTC * TM * 4;
+    o += (uint32_t)tc_stages(H) * TN * dp * 2;
+    L.ls = o;  // H x [KTC][TM] per-row heaps: distances
+    o += (uint32_t)H * KTC * TM * 4;
+    L.li = o;  // H x [KTC][TM] ids
+    o += (uint32_t)H * KTC * TM * 4;
     L.nbuf = o;
     o += 2 * TN * 4;
+    L.cnt = o;  // entries of the second heap of every row
+    o += TM * 4;
     L.bars = o;
     o += 16 * 8;
     L.misc = o;
@@ -268,23 +290,26 @@ __host__ __device__ inline TcLayout tc_layout(int dp) {
 // perm (nullable): position -> original id of spatially ordered points (Q
 // is D itself); lists hold original ids, rows are written back in original
 // order.  rotate: scan the tiles around the CTA's rows first.
-__global__ void __launch_bounds__(NTHREADS, 1)
+template <int H>
+__global__ void __launch_bounds__(tc_threads(H), 1)
 k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUtensorMap mapX,
          int64_t nq, int64_t n, int dp, const float *__restrict__ qnorm,
          const float *__restrict__ xnorm, int K, int self_exclude, int32_t *__restrict__ out_i,
          float *__restrict__ out_s, int *err, const int32_t *__restrict__ perm, int rotate) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = reinterpret_cast<uint8_t *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const TcLayout Ly = tc_layout(dp);
+    constexpr int STG = tc_stages(H), NEPI = 128 * H;
+    const TcLayout Ly = tc_layout(dp, H);
     uint8_t *A = sm + Ly.a;
     uint8_t *B = sm + Ly.b;
-    float *Ls = reinterpret_cast<float *>(sm + Ly.ls);
-    int *Li = reinterpret_cast<int *>(sm + Ly.li);
+    float *Ls0 = reinterpret_cast<float *>(sm + Ly.ls);
+    int *Li0 = reinterpret_cast<int *>(sm + Ly.li);
     float *nbuf = reinterpret_cast<float *>(sm + Ly.nbuf);
+    int *cntbuf = reinterpret_cast<int *>(sm + Ly.cnt);
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + Ly.bars);
-    uint64_t *a_full = bars, *b_full = bars + 1, *b_empty = bars + 1 + STAGES;
-    uint64_t *acc_full = bars + 1 + 2 * STAGES, *acc_empty = bars + 3 + 2 * STAGES;
-    uint64_t *drain = bars + 5 + 2 * STAGES;
+    uint64_t *a_full = bars, *b_full = bars + 1, *b_empty = bars + 1 + STG;
+    uint64_t *acc_full = bars + 1 + 2 * STG, *acc_empty = bars + 3 + 2 * STG;
+    uint64_t *drain = bars + 5 + 2 * STG;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + Ly.misc);
     volatile int *abort = reinterpret_cast<volatile int *>(sm + Ly.misc + 4);
 
@@ -305,13 +330,13 @@ k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUten
 
     if (threadIdx.x == 0) {
         mbar_init(a_full, 1);
-        for (int s = 0; s < STAGES; ++s) {
+        for (int s = 0; s < STG; ++s) {
             mbar_init(b_full + s, 1);
             mbar_init(b_empty + s, 1);
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(acc_full + a, 1);
-            mbar_init(acc_empty + a, 128);
+            mbar_init(acc_empty + a, NEPI);
         }
         mbar_init(drain, 1);
         *abort = 0;
@@ -336,8 +361,8 @@ k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUten
                 tma_load_2d(A + kb * TM * 128, &mapQ, a_full, kb * 64, (int)row0);
             int issued = 0;
             for (int t = 0; t < ntiles; ++t) {
-                const int s = t % STAGES;
-                if (!mbar_wait(b_empty + s, ((t / STAGES) & 1) ^ 1, abort, err, true)) break;
+                const int s = t % STG;
+                if (!mbar_wait(b_empty + s, ((t / STG) & 1) ^ 1, abort, err, true)) break;
                 mbar_expect_tx(b_full + s, b_bytes);
                 for (int kb = 0; kb < nkb; ++kb)
                     tma_load_2d(B + (size_t)s * TN * dp * 2 + kb * TN * 128, &mapX, b_full + s,
@@ -345,9 +370,9 @@ k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUten
                 issued = t + 1;
             }
             if (*abort) {  // let the copies already issued land before TMEM is freed
-                for (int t = max(0, issued - STAGES); t < issued; ++t) {
+                for (int t = max(0, issued - STG); t < issued; ++t) {
                     uint64_t t0 = gtimer();
-                    while (!mbar_try_wait(b_full + t % STAGES, (t / STAGES) & 1) &&
+                    while (!mbar_try_wait(b_full + t % STG, (t / STG) & 1) &&
                            gtimer() - t0 < 1000000000ull) {
                     }
                 }
@@ -358,8 +383,8 @@ k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUten
             bool ok = mbar_wait(a_full, 0, abort, err, true);
             int t = 0;
             for (; ok && t < ntiles; ++t) {
-                const int s = t % STAGES, a = t & 1;
-                if (!mbar_wait(b_full + s, (t / STAGES) & 1, abort, err, true)) break;
+                const int s = t % STG, a = t & 1;
+                if (!mbar_wait(b_full + s, (t / STG) & 1, abort, err, true)) break;
                 if (!mbar_wait(acc_empty + a, ((t >> 1) & 1) ^ 1, abort, err, true)) break;
                 tc_fence_after();
                 const uint32_t a0 = saddr(A), b0 = saddr(B + (size_t)s * TN * dp * 2);
@@ -378,7 +403,11 @@ k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUten
             }
         }
     } else {  // ---------------------------------------- epilogue
-        const int q = warp & 3;
+        const int q = warp & 3;               // TMEM lane quarter
+        const int half = (warp - 2) >> 2;     // column half (H = 2)
+        const int c_lo = half * (4 / H), c_hi = c_lo + 4 / H;
+        float *Ls = Ls0 + half * KTC * TM;
+        int *Li = Li0 + half * KTC * TM;
         const int row = q * 32 + lane;
         const int64_t g = row0 + row;
         const bool live = g < nq;
@@ -386,9 +415,10 @@ k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUten
         int count = 0;
         float thr = INFINITY;  // the heap's K-th pair once full
         int thr_id = INT_MAX;
-        // this thread's column norm of tile t, loaded one tile ahead
+        // this thread's column norm of tile t, loaded one tile ahead (the
+        // first half's threads stage all 128 norms of a tile)
         auto colnorm = [&](int t) -> float {
-            if (t >= ntiles) return INFINITY;
+            if (t >= ntiles || half != 0) return INFINITY;
             const int64_t c = (int64_t)tile_at(t) * TN + row;
             return c < n ? xnorm[c] : INFINITY;
         };
@@ -396,15 +426,14 @@ k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUten
         for (int t = 0; t < ntiles; ++t) {
             const int a = t & 1;
             const int64_t colbase = (int64_t)tile_at(t) * TN;
-            nbuf[a * TN + row] = next;
+            if (half == 0) nbuf[a * TN + row] = next;
             next = colnorm(t + 1);
             mbar_wait(acc_full + a, (t >> 1) & 1, abort, err);
-            epi_barrier();
-            if (*abort) break;
+            if (epi_barrier_or(NEPI, *abort != 0)) break;
             tc_fence_after();
             const float4 *nb4 = reinterpret_cast<const float4 *>(nbuf + a * TN);
 #pragma unroll 1
-            for (int c = 0; c < TN / 32; ++c) {
+            for (int c = c_lo; c < c_hi; ++c) {
                 float v[32];
                 tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * TN + c * 32), v);
                 float nbv[32];
@@ -421,7 +450,7 @@ k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUten
                 for (int j = 0; j < 32; ++j) m = fminf(m, fmaf(-2.f, v[j], nbv[j]));
                 // rare: this row may accept a column of the chunk (ties with
                 // the K-th distance are decided by id); each thread pushes
-                // into its own row's heap, independently of the other lanes
+                // into its own heap, independently of the other lanes
                 if (!(live && nqr + m <= thr)) continue;
                 float sv[32];
                 unsigned mask = 0;
@@ -446,18 +475,55 @@ k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUten
             mbar_arrive(acc_empty + a);
         }
         heap_sort(Ls, Li, row, count);
+        if (H == 2) {
+            // the row's two sorted lists (disjoint columns) -> its K best,
+            // merged backwards into the first half's list
+            if (half == 1) cntbuf[row] = count;
+            epi_barrier(NEPI);
+            if (half == 0) {
+                const float *Bs = Ls0 + KTC * TM;
+                const int *Bi = Li0 + KTC * TM;
+                const int na0 = count, nb0 = cntbuf[row];
+                const int total = min(K, na0 + nb0);
+                int i = 0, j = 0;
+                for (int t = 0; t < total; ++t) {
+                    if (j >= nb0 || (i < na0 && pair_less(Ls[i * TM + row], Li[i * TM + row],
+                                                          Bs[j * TM + row], Bi[j * TM + row])))
+                        ++i;
+                    else
+                        ++j;
+                }
+                for (int p = total - 1; p >= 0; --p) {
+                    const bool takeA =
+                        j == 0 || (i > 0 && pair_less(Bs[(j - 1) * TM + row], Bi[(j - 1) * TM + row],
+                                                      Ls[(i - 1) * TM + row], Li[(i - 1) * TM + row]));
+                    if (takeA) {
+                        --i;
+                        Ls[p * TM + row] = Ls[i * TM + row];
+                        Li[p * TM + row] = Li[i * TM + row];
+                    } else {
+                        --j;
+                        Ls[p * TM + row] = Bs[j * TM + row];
+                        Li[p * TM + row] = Bi[j * TM + row];
+                    }
+                }
+                count = total;
+            }
+        }
         __syncwarp();
-        // the warp writes its 32 rows (coalesced along each row); a permuted
-        // point's row goes back to its original position
-        for (int rr = 0; rr < 32; ++rr) {
-            const int r2 = q * 32 + rr;
-            const int64_t gp = row0 + r2;
-            const int cnt2 = __shfl_sync(0xffffffffu, count, rr);
-            if (gp >= nq) continue;
-            const int64_t g2 = perm ? (int64_t)perm[gp] : gp;
-            for (int j = lane; j < K; j += 32) {
-                out_i[g2 * K + j] = j < cnt2 ? Li[j * TM + r2] : -1;
-                out_s[g2 * K + j] = j < cnt2 ? Ls[j * TM + r2] : INFINITY;
+        // the first half's warps write their 32 rows (coalesced along each
+        // row); a permuted point's row goes back to its original position
+        if (half == 0) {
+            for (int rr = 0; rr < 32; ++rr) {
+                const int r2 = q * 32 + rr;
+                const int64_t gp = row0 + r2;
+                const int cnt2 = __shfl_sync(0xffffffffu, count, rr);
+                if (gp >= nq) continue;
+                const int64_t g2 = perm ? (int64_t)perm[gp] : gp;
+                for (int j = lane; j < K; j += 32) {
+                    out_i[g2 * K + j] = j < cnt2 ? Li[j * TM + r2] : -1;
+                    out_s[g2 * K + j] = j < cnt2 ? Ls[j * TM + r2] : INFINITY;
+                }
             }
         }
     }
@@ -625,8 +691,7 @@ k_argmin_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CU
             nbuf[a * TN + row] = next;
             next = colval(t + 1);
             mbar_wait(acc_full + a, (t >> 1) & 1, abort, err);
-            epi_barrier();
-            if (*abort) break;
+            if (epi_barrier_or(128, *abort != 0)) break;
             tc_fence_after();
 #pragma unroll 1
             for (int c = 0; c < TN / 32; ++c) {
@@ -735,9 +800,12 @@ pg_status make_map(pg_ctx *ctx, CUtensorMap *map, const __nv_bfloat16 *base, int
 
 }  // namespace
 
+// two heaps per row (eight epilogue warps) where they fit in shared memory
+static int tc_halves(int dp) { return tc_layout(dp, 2).total + 1024 <= 227 * 1024 ? 2 : 1; }
+
 bool pg_knn_tc_supported(int d, int K) {
     int dp = (d + 63) / 64 * 64;
-    return dp <= 256 && K >= 1 && K <= KTC && tc_layout(dp).total + 1024 <= 227 * 1024;
+    return dp <= 256 && K >= 1 && K <= KTC && tc_layout(dp, 1).total + 1024 <= 227 * 1024;
 }
 
 
@@ -802,9 +870,21 @@ pg_status pg_knn_tc(pg_ctx *ctx, const float *D, int64_t n, int32_t d, const flo
         PG_LAUNCHED(ctx);
         qp = qb.p;
     }
-    const size_t smem = tc_layout(dp).total + 1024;
-    PG_TRY_CUDA(ctx, cudaFuncSetAttribute(k_knn_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem));
+    const int H = tc_halves(dp);
+    const size_t smem = tc_layout(dp, H).total + 1024;
+    PG_TRY_CUDA(ctx, cudaFuncSetAttribute(H == 2 ? k_knn_tc<2> : k_knn_tc<1>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // one launch of the H-variant
+    auto launch = [&](unsigned grid, const CUtensorMap &mq_, const CUtensorMap &mx_, int64_t nq_,
+                      int64_t n_, const float *qn_, const float *xn_, int K_, int self_,
+                      int32_t *oi, float *os, const int32_t *perm_, int rot) {
+        if (H == 2)
+            k_knn_tc<2><<<grid, tc_threads(2), smem, ctx->stream>>>(
+                mq_, mx_, nq_, n_, dp, qn_, xn_, K_, self_, oi, os, ctx->d_err, perm_, rot);
+        else
+            k_knn_tc<1><<<grid, tc_threads(1), smem, ctx->stream>>>(
+                mq_, mx_, nq_, n_, dp, qn_, xn_, K_, self_, oi, os, ctx->d_err, perm_, rot);
+    };
     const int32_t *permp = nullptr;
     const __nv_bfloat16 *xp = xb.p;
     const float *xnp = xnorm, *qnp = qnorm;
@@ -826,8 +906,8 @@ pg_status pg_knn_tc(pg_ctx *ctx, const float *D, int64_t n, int32_t d, const flo
         CUtensorMap mqa, mpa;
         PG_TRY(make_map(ctx, &mqa, xb.p, n, dp));
         PG_TRY(make_map(ctx, &mpa, pb.p, P, dp));
-        k_knn_tc<<<(unsigned)((n + TM - 1) / TM), NTHREADS, smem, ctx->stream>>>(
-            mqa, mpa, n, P, dp, xnorm, pn.p, 1, 0, asg.p, adist.p, ctx->d_err, nullptr, 0);
+        launch((unsigned)((n + TM - 1) / TM), mqa, mpa, n, P, xnorm, pn.p, 1, 0, asg.p, adist.p,
+               nullptr, 0);
         PG_LAUNCHED(ctx);
         PG_TRY(cnt.alloc(ctx, (size_t)P));
         PG_TRY(boff.alloc(ctx, (size_t)P + 1));
@@ -859,8 +939,7 @@ pg_status pg_knn_tc(pg_ctx *ctx, const float *D, int64_t n, int32_t d, const flo
     PG_TRY(make_map(ctx, &mq, qp, self ? n : nq, dp));
     const unsigned grid = (unsigned)((nq + TM - 1) / TM);
     pg_timer_begin(ctx, TM_KNN);
-    k_knn_tc<<<grid, NTHREADS, smem, ctx->stream>>>(mq, mx, nq, n, dp, qnp, xnp, K, self, ids,
-                                                     dist, ctx->d_err, permp, permp ? 1 : 0);
+    launch(grid, mq, mx, nq, n, qnp, xnp, K, self, ids, dist, permp, permp ? 1 : 0);
     PG_LAUNCHED(ctx);
     pg_timer_end(ctx, TM_KNN, 2.0 * (double)nq * (double)n * (double)d);
     return PG_OK;
