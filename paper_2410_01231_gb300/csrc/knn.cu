@@ -333,9 +333,46 @@ __global__ void k_knn_fix(const float *__restrict__ Q, const float *__restrict__
     }
 }
 
+// Screened form on non-integer data: the Kx BF16-nearest candidates of a
+// row re-measured in FP32 (difference form / chord, the same arithmetic as
+// the FP32 gathers) and the K best by (s, id) kept.  One warp per row.
+__global__ void k_knn_rerank(const float *__restrict__ Q, const float *__restrict__ X, int64_t nq,
+                             int d, int metric, int Kx, int K, const int32_t *__restrict__ ci,
+                             int32_t *__restrict__ out_i, float *__restrict__ out_s) {
+    __shared__ float ks[8][128];
+    __shared__ int kid[8][128];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, team = lane >> 3, li = lane & 7;
+    const int64_t row = (int64_t)blockIdx.x * 8 + w;
+    if (row >= nq) return;
+    for (int j = lane; j < 128; j += 32) {
+        ks[w][j] = INFINITY;
+        kid[w][j] = INT_MAX;
+    }
+    __syncwarp();
+    const float4 *q4 = reinterpret_cast<const float4 *>(Q + row * d);
+    for (int b0 = 0; b0 < Kx; b0 += 4) {
+        const int j = b0 + team;
+        const int id = j < Kx ? ci[row * Kx + j] : -1;
+        const float sv = team8_dist(q4, reinterpret_cast<const float4 *>(X + (int64_t)(id >= 0 ? id : 0) * d),
+                                    d / 4, li, metric);
+        if (li == 0 && id >= 0) {
+            ks[w][j] = sv;
+            kid[w][j] = id;
+        }
+    }
+    __syncwarp();
+    warp_bitonic_sort(ks[w], kid[w], 128);
+    for (int t = lane; t < K; t += 32) {
+        const bool ok = kid[w][t] != INT_MAX;
+        out_i[row * K + t] = ok ? kid[w][t] : -1;
+        out_s[row * K + t] = ok ? ks[w][t] : INFINITY;
+    }
+}
+
 }  // namespace
 
 bool pg_knn_tc_supported(int d, int K);
+int pg_knn_tc_max_k();
 pg_status pg_knn_tc(pg_ctx *ctx, const float *D, int64_t n, int32_t d, const float *Q, int64_t nq,
                     int self, int32_t K, const float *xnorm, const float *qnorm, int32_t *ids,
                     float *dist);
@@ -375,6 +412,24 @@ pg_status knn_core(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric 
     if (precision == PG_PREC_BF16_SCREEN && metric == PG_METRIC_L2SQ && facts.exact &&
         facts.bf16_exact && pg_knn_tc_supported(d, K))
         return pg_knn_tc(ctx, D, n, d, self ? nullptr : Q, nq, self, K, xn.p, qnp, ids, dist);
+    // Other data in the screened form: the Ks = min(128, max(2K, K + 8))
+    // nearest by BF16 tiles (the BF16 rounding moves distances by up to
+    // ~2^-8 (|x| + |y|) sqrt(s)), re-measured in FP32 and cut to K.
+    // Membership at the K-th place can differ from the exact kNN; the
+    // candidate order and distances are FP32.
+    const int Ks = std::min(pg_knn_tc_max_k(), std::max(2 * K, K + 8));
+    if (precision == PG_PREC_BF16_SCREEN && !(facts.exact && facts.bf16_exact) && Ks >= K + 8 &&
+        pg_knn_tc_supported(d, Ks)) {
+        Scratch<int32_t> wi;
+        Scratch<float> ws;
+        PG_TRY(wi.alloc(ctx, (size_t)nq * Ks));
+        PG_TRY(ws.alloc(ctx, (size_t)nq * Ks));
+        PG_TRY(pg_knn_tc(ctx, D, n, d, self ? nullptr : Q, nq, self, Ks, xn.p, qnp, wi.p, ws.p));
+        k_knn_rerank<<<(unsigned)((nq + 7) / 8), 256, 0, ctx->stream>>>(
+            Qp, D, nq, d, metric == PG_METRIC_L2SQ ? 0 : 1, Ks, K, wi.p, ids, dist);
+        PG_LAUNCHED(ctx);
+        return PG_OK;
+    }
     // rows hold Kx entries when ties must be resolved in FP64 afterwards
     int64_t avail = self ? n - 1 : n;
     int Kx = facts.exact ? K : (int)std::min<int64_t>((int64_t)K + 8, KMAX);

@@ -30,7 +30,8 @@ namespace {
 constexpr int TM = 128;       // query rows per CTA = TMEM lanes
 constexpr int TN = 128;       // candidate columns per tile
 constexpr int STAGES = 3;     // candidate-tile ring
-constexpr int KTC = 64;       // largest K of this kernel
+constexpr int KTC = 64;       // largest K of the resident-query kernel
+constexpr int KTCK = 128;     // largest K of the k-blocked kernel
 constexpr int NTHREADS = 192;
 constexpr int ACC_COLS = 256;  // two accumulator buffers of TN columns
 
@@ -261,20 +262,27 @@ struct TcLayout {
 // row and all 128 columns of a tile; 3 candidate stages.  H = 2: eight
 // epilogue warps, two per lane quarter taking 64 columns each, so two
 // threads and two heaps per row (merged at the end); 2 candidate stages.
+// KB (k-blocked, any dp): the query tile is not resident; every stage holds
+// one 64-column block of the query tile and of the candidate tile, and the
+// MMAs of a tile accumulate over the blocks; H = 1, 3 stages, K <= KTCK.
 __host__ __device__ constexpr int tc_threads(int H) { return 64 + 128 * H; }
-__host__ __device__ constexpr int tc_stages(int H) { return H == 1 ? 3 : 2; }
+__host__ __device__ constexpr int tc_stages(int H, bool KB = false) {
+    return KB ? 3 : (H == 1 ? 3 : 2);
+}
+__host__ __device__ constexpr int tc_kcap(bool KB) { return KB ? KTCK : KTC; }
+constexpr uint32_t KB_STAGE = (uint32_t)(TM + TN) * 64 * 2;  // bytes of one k-blocked stage
 
-__host__ __device__ inline TcLayout tc_layout(int dp, int H) {
+__host__ __device__ inline TcLayout tc_layout(int dp, int H, bool KB = false) {
     TcLayout L;
     uint32_t o = 0;
     L.a = o;
-    o += (uint32_t)TM * dp * 2;
+    if (!KB) o += (uint32_t)TM * dp * 2;
     L.b = o;
-    o += (uint32_t)tc_stages(H) * TN * dp * 2;
-    L.ls = o;  // H x [KTC][TM] per-row heaps: distances
-    o += (uint32_t)H * KTC * TM * 4;
-    L.li = o;  // H x [KTC][TM] ids
-    o += (uint32_t)H * KTC * TM * 4;
+    o += KB ? tc_stages(H, KB) * KB_STAGE : (uint32_t)tc_stages(H) * TN * dp * 2;
+    L.ls = o;  // H x [kcap][TM] per-row heaps: distances
+    o += (uint32_t)H * tc_kcap(KB) * TM * 4;
+    L.li = o;  // H x [kcap][TM] ids
+    o += (uint32_t)H * tc_kcap(KB) * TM * 4;
     L.nbuf = o;
     o += 2 * TN * 4;
     L.cnt = o;  // entries of the second heap of every row
@@ -290,7 +298,7 @@ __host__ __device__ inline TcLayout tc_layout(int dp, int H) {
 // perm (nullable): position -> original id of spatially ordered points (Q
 // is D itself); lists hold original ids, rows are written back in original
 // order.  rotate: scan the tiles around the CTA's rows first.
-template <int H>
+template <int H, bool KB>
 __global__ void __launch_bounds__(tc_threads(H), 1)
 k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUtensorMap mapX,
          int64_t nq, int64_t n, int dp, const float *__restrict__ qnorm,
@@ -298,8 +306,8 @@ k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUten
          float *__restrict__ out_s, int *err, const int32_t *__restrict__ perm, int rotate) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = reinterpret_cast<uint8_t *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    constexpr int STG = tc_stages(H), NEPI = 128 * H;
-    const TcLayout Ly = tc_layout(dp, H);
+    constexpr int STG = tc_stages(H, KB), NEPI = 128 * H, KCAP = tc_kcap(KB);
+    const TcLayout Ly = tc_layout(dp, H, KB);
     uint8_t *A = sm + Ly.a;
     uint8_t *B = sm + Ly.b;
     float *Ls0 = reinterpret_cast<float *>(sm + Ly.ls);
@@ -355,7 +363,32 @@ k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUten
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 0) {
-        if (lane == 0) {  // ---------------- TMA producer
+        if (lane == 0 && KB) {  // ---------------- TMA producer, k-blocked
+            int issued = 0;
+            bool ok = true;
+            for (int t = 0; ok && t < ntiles; ++t) {
+                for (int kb = 0; kb < nkb; ++kb) {
+                    const int it = t * nkb + kb, s = it % STG;
+                    if (!mbar_wait(b_empty + s, ((it / STG) & 1) ^ 1, abort, err, true)) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t *st = B + (size_t)s * KB_STAGE;
+                    mbar_expect_tx(b_full + s, KB_STAGE);
+                    tma_load_2d(st, &mapQ, b_full + s, kb * 64, (int)row0);
+                    tma_load_2d(st + TM * 128, &mapX, b_full + s, kb * 64, tile_at(t) * TN);
+                    issued = it + 1;
+                }
+            }
+            if (*abort) {  // let the copies already issued land before TMEM is freed
+                for (int it = max(0, issued - STG); it < issued; ++it) {
+                    uint64_t t0 = gtimer();
+                    while (!mbar_try_wait(b_full + it % STG, (it / STG) & 1) &&
+                           gtimer() - t0 < 1000000000ull) {
+                    }
+                }
+            }
+        } else if (lane == 0) {  // ---------------- TMA producer
             mbar_expect_tx(a_full, a_bytes);
             for (int kb = 0; kb < nkb; ++kb)
                 tma_load_2d(A + kb * TM * 128, &mapQ, a_full, kb * 64, (int)row0);
@@ -379,7 +412,31 @@ k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUten
             }
         }
     } else if (warp == 1) {
-        if (lane == 0) {  // ---------------- MMA issuer
+        if (lane == 0 && KB) {  // ---------------- MMA issuer, k-blocked
+            bool ok = true;
+            for (int t = 0; ok && t < ntiles; ++t) {
+                const int a = t & 1;
+                if (!mbar_wait(acc_empty + a, ((t >> 1) & 1) ^ 1, abort, err, true)) break;
+                for (int kb = 0; kb < nkb; ++kb) {
+                    const int it = t * nkb + kb, s = it % STG;
+                    if (!mbar_wait(b_full + s, (it / STG) & 1, abort, err, true)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a0 = saddr(B + (size_t)s * KB_STAGE), b0 = a0 + TM * 128;
+                    for (int k = 0; k < 4; ++k)
+                        umma_bf16(tmem + a * TN, sw128_desc(a0 + k * 32), sw128_desc(b0 + k * 32),
+                                  (kb > 0 || k > 0) ? 1u : 0u);
+                    umma_commit(b_empty + s);
+                }
+                if (ok) umma_commit(acc_full + a);
+            }
+            umma_commit(drain);
+            uint64_t t0 = gtimer();
+            while (!mbar_try_wait(drain, 0) && gtimer() - t0 < 1000000000ull) {
+            }
+        } else if (lane == 0) {  // ---------------- MMA issuer
             bool ok = mbar_wait(a_full, 0, abort, err, true);
             int t = 0;
             for (; ok && t < ntiles; ++t) {
@@ -406,8 +463,8 @@ k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUten
         const int q = warp & 3;               // TMEM lane quarter
         const int half = (warp - 2) >> 2;     // column half (H = 2)
         const int c_lo = half * (4 / H), c_hi = c_lo + 4 / H;
-        float *Ls = Ls0 + half * KTC * TM;
-        int *Li = Li0 + half * KTC * TM;
+        float *Ls = Ls0 + half * KCAP * TM;
+        int *Li = Li0 + half * KCAP * TM;
         const int row = q * 32 + lane;
         const int64_t g = row0 + row;
         const bool live = g < nq;
@@ -481,8 +538,8 @@ k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUten
             if (half == 1) cntbuf[row] = count;
             epi_barrier(NEPI);
             if (half == 0) {
-                const float *Bs = Ls0 + KTC * TM;
-                const int *Bi = Li0 + KTC * TM;
+                const float *Bs = Ls0 + KCAP * TM;
+                const int *Bi = Li0 + KCAP * TM;
                 const int na0 = count, nb0 = cntbuf[row];
                 const int total = min(K, na0 + nb0);
                 int i = 0, j = 0;
@@ -800,13 +857,26 @@ pg_status make_map(pg_ctx *ctx, CUtensorMap *map, const __nv_bfloat16 *base, int
 
 }  // namespace
 
-// two heaps per row (eight epilogue warps) where they fit in shared memory
-static int tc_halves(int dp) { return tc_layout(dp, 2).total + 1024 <= 227 * 1024 ? 2 : 1; }
+// Kernel variant for dp columns and K neighbours: the resident-query kernel
+// with two heaps per row, else with one, else the k-blocked kernel.
+struct TcVariant {
+    int H;
+    bool KB;
+};
+
+static TcVariant tc_variant(int dp, int K) {
+    const uint32_t cap = 227 * 1024 - 1024;
+    if (K <= KTC && tc_layout(dp, 2).total <= cap) return {2, false};
+    if (K <= KTC && tc_layout(dp, 1).total <= cap) return {1, false};
+    return {1, true};
+}
 
 bool pg_knn_tc_supported(int d, int K) {
-    int dp = (d + 63) / 64 * 64;
-    return dp <= 256 && K >= 1 && K <= KTC && tc_layout(dp, 1).total + 1024 <= 227 * 1024;
+    const int dp = (d + 63) / 64 * 64;
+    return K >= 1 && K <= KTCK && d <= 8192 && tc_layout(dp, 1, true).total + 1024 <= 227 * 1024;
 }
+
+int pg_knn_tc_max_k() { return KTCK; }
 
 
 namespace {
@@ -870,19 +940,23 @@ pg_status pg_knn_tc(pg_ctx *ctx, const float *D, int64_t n, int32_t d, const flo
         PG_LAUNCHED(ctx);
         qp = qb.p;
     }
-    const int H = tc_halves(dp);
-    const size_t smem = tc_layout(dp, H).total + 1024;
-    PG_TRY_CUDA(ctx, cudaFuncSetAttribute(H == 2 ? k_knn_tc<2> : k_knn_tc<1>,
+    const TcVariant V = tc_variant(dp, K);
+    const size_t smem = tc_layout(dp, V.H, V.KB).total + 1024;
+    PG_TRY_CUDA(ctx, cudaFuncSetAttribute(V.KB ? k_knn_tc<1, true>
+                                               : (V.H == 2 ? k_knn_tc<2, false> : k_knn_tc<1, false>),
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    // one launch of the H-variant
+    // one launch of the chosen variant
     auto launch = [&](unsigned grid, const CUtensorMap &mq_, const CUtensorMap &mx_, int64_t nq_,
                       int64_t n_, const float *qn_, const float *xn_, int K_, int self_,
                       int32_t *oi, float *os, const int32_t *perm_, int rot) {
-        if (H == 2)
-            k_knn_tc<2><<<grid, tc_threads(2), smem, ctx->stream>>>(
+        if (V.KB)
+            k_knn_tc<1, true><<<grid, tc_threads(1), smem, ctx->stream>>>(
+                mq_, mx_, nq_, n_, dp, qn_, xn_, K_, self_, oi, os, ctx->d_err, perm_, rot);
+        else if (V.H == 2)
+            k_knn_tc<2, false><<<grid, tc_threads(2), smem, ctx->stream>>>(
                 mq_, mx_, nq_, n_, dp, qn_, xn_, K_, self_, oi, os, ctx->d_err, perm_, rot);
         else
-            k_knn_tc<1><<<grid, tc_threads(1), smem, ctx->stream>>>(
+            k_knn_tc<1, false><<<grid, tc_threads(1), smem, ctx->stream>>>(
                 mq_, mx_, nq_, n_, dp, qn_, xn_, K_, self_, oi, os, ctx->d_err, perm_, rot);
     };
     const int32_t *permp = nullptr;

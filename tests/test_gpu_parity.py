@@ -85,6 +85,41 @@ def test_knn_bf16_tensor_cores_match_oracle(ctx, pg, n, K):
     assert (host(qi) == oqi).all()
 
 
+@pytest.mark.parametrize("d,K", [(256, 32), (320, 64), (192, 70)])
+def test_knn_bf16_k_blocked_tiles_match_oracle(ctx, pg, d, K):
+    """Rows wider than 128 dims (and K > 64) take the k-blocked tensor-core
+    kernel; small integers keep it exact, so it equals the oracle."""
+    rng = np.random.default_rng(d)
+    D = rng.integers(0, 16, size=(3000, d)).astype(np.float32)
+    gi, gd = pg.build_knn(ctx, dev(D), K, precision="bf16")
+    oi, od = oracle.knn(D, K)
+    assert (host(gi) == oi).all()
+    assert (host(gd) == od.astype(np.float32)).all()
+
+
+@pytest.mark.parametrize("n,d,metric", [(3000, 960, "l2"), (20000, 128, "l2"),
+                                        (3000, 96, "cosine")])
+def test_knn_bf16_screen_on_real_data_recall(ctx, pg, n, d, metric):
+    """Non-integer rows: the 2K BF16-nearest re-measured in FP32.  Lists
+    are sorted, distances are FP32 values of the returned pairs, and the
+    lists hold the exact K nearest up to rare swaps at the K-th place."""
+    if metric == "l2":
+        D, _ = synthetic.mixture_float(n, d, max(4, n // 1000), 17)
+    else:
+        D = synthetic.unit_gaussian(n, d, 17)
+    K = 32
+    gi, gd = pg.build_knn(ctx, dev(D), K, metric, precision="bf16")
+    gi, gd = host(gi), host(gd)
+    oi, od = oracle.knn(D, K, metric)
+    rows = np.arange(n)
+    for u in rows[:200]:
+        ref = np.array([oracle.dist(D[u], D[v], metric) for v in gi[u]])
+        assert np.allclose(gd[u], ref, rtol=2e-5, atol=1e-6)
+        assert (np.diff(gd[u]) >= 0).all()
+    hits = np.mean([len(set(gi[u]) & set(oi[u])) / K for u in rows])
+    assert hits >= 0.995
+
+
 def test_knn_queries_and_padding(ctx, pg):
     D = int_points(300)
     Q, _ = synthetic.mixture_int(37, 128, 32, 99)
