@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-queries", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-screen", action="store_true")
     return ap.parse_args()
 
 
@@ -362,6 +363,39 @@ def run_ours(args):
                  "stream": "300 query requests of 1/8/32/128 queries (k=10, beam 48) with two "
                            f"insertion batches of {ins} points, host buffers, queued at once"}
 
+    # ------------------------------------------- screened kNN, real-valued rows
+    # The 1M x 960 real-valued workload's recipe (512 centres U[0,1]^960,
+    # sigma 0.1) sampled at 100,000 points: kNN graph (K = 64) in the FP32
+    # form and in the screened form (BF16 tiles, 2K candidates re-measured
+    # in FP32); list recall of the screened form against the FP32 form.
+    screen = {}
+    if not args.no_screen:
+        w3 = synthetic.WORKLOADS[3]
+        ns = min(100_000, max(20_000, n // 10))
+        X3, _ = synthetic.mixture_float(ns, w3["d"], max(8, w3["clusters"] * ns // w3["n"]), 1234 + 3)
+        X3d = torch.from_numpy(X3).cuda()
+        times = {}
+        lists = {}
+        for prec in ("fp32", "bf16"):
+            pg.build_knn(ctx, X3d, w3["K"], precision=prec)  # warm-up
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ids3, _ = pg.build_knn(ctx, X3d, w3["K"], precision=prec)
+            e1.record(stream)
+            barrier()
+            times[prec] = e0.elapsed_time(e1)
+            lists[prec] = ids3.cpu().numpy()
+        a, b = lists["fp32"], lists["bf16"]
+        hit = float(np.mean([len(np.intersect1d(a[i], b[i])) for i in range(0, ns, 97)]) / w3["K"])
+        flops = 2.0 * ns * ns * w3["d"]
+        screen = {"workload": f"{w3['name']} recipe at n={ns}", "K": w3["K"],
+                  "knn_fp32_ms": times["fp32"], "knn_bf16_screen_ms": times["bf16"],
+                  "speedup": times["fp32"] / times["bf16"],
+                  "bf16_tflops_algorithmic": flops / (times["bf16"] / 1e3) / 1e12,
+                  "list_recall_vs_fp32": hit}
+        del X3d
+
     # ------------------------------------------------ the other precision form
     forms = {args.precision: {"ms_per_build": ms, "points_per_s": value}}
     identical = None
@@ -474,7 +508,7 @@ def run_ours(args):
                    "l2": (f"inputs larger than L2 ({D.nbytes >> 20} MB points)" if D.nbytes > 129e6
                           else f"inputs smaller than L2 ({D.nbytes >> 20} MB points; test size)"), "parallelism": "replicas"},
         "forms": forms, "forms_identical_graph": identical,
-        "queries": qres, "serving": serve, "phase_s": ph,
+        "queries": qres, "serving": serve, "screened_knn_d960": screen, "phase_s": ph,
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
         "kernel_launches_per_step": {k: v[1] / args.steps for k, v in kt.items()},
         "connect_edges_per_step": conn_edges / max(1, args.steps + args.warmup),
