@@ -174,6 +174,7 @@ __device__ __forceinline__ bool epi_barrier_or(int nthreads, bool flag) {
     return r != 0;
 }
 
+
 // Per-row max-heap of the K best (s, id) pairs in shared memory, layout
 // [pos][TM]: element pos of row r at pos * TM + r, so a thread's accesses
 // always fall in its own bank.  The root is the K-th best once the heap is
@@ -462,7 +463,7 @@ k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUten
     } else {  // ---------------------------------------- epilogue
         const int q = warp & 3;               // TMEM lane quarter
         const int half = (warp - 2) >> 2;     // column half (H = 2)
-        const int c_lo = half * (4 / H), c_hi = c_lo + 4 / H;
+        const int c_lo = half * (4 / H);
         float *Ls = Ls0 + half * KCAP * TM;
         int *Li = Li0 + half * KCAP * TM;
         const int row = q * 32 + lane;
@@ -472,31 +473,47 @@ k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUten
         int count = 0;
         float thr = INFINITY;  // the heap's K-th pair once full
         int thr_id = INT_MAX;
-        // this thread's column norm of tile t, loaded one tile ahead (the
-        // first half's threads stage all 128 norms of a tile)
-        auto colnorm = [&](int t) -> float {
-            if (t >= ntiles || half != 0) return INFINITY;
-            const int64_t c = (int64_t)tile_at(t) * TN + row;
-            return c < n ? xnorm[c] : INFINITY;
+        // Column norms: lane j of a warp loads the norm of column j of each
+        // 32-column chunk it processes, one tile ahead, and stages it in the
+        // warp's own 32-float slot right before the chunk: no barrier across
+        // warps inside the tile loop.
+        constexpr int NCH = 4 / H;  // chunks of one thread per tile
+        float *wn = nbuf + (warp - 2) * 32;
+        auto colnorm = [&](int t, int c) -> float {
+            if (t >= ntiles) return INFINITY;
+            const int64_t col = (int64_t)tile_at(t) * TN + c * 32 + lane;
+            return col < n ? xnorm[col] : INFINITY;
         };
-        float next = colnorm(0);
+        float nxt[NCH];
+#pragma unroll
+        for (int ci = 0; ci < NCH; ++ci) nxt[ci] = colnorm(0, c_lo + ci);
         for (int t = 0; t < ntiles; ++t) {
             const int a = t & 1;
             const int64_t colbase = (int64_t)tile_at(t) * TN;
-            if (half == 0) nbuf[a * TN + row] = next;
-            next = colnorm(t + 1);
+            float cur[NCH];
+#pragma unroll
+            for (int ci = 0; ci < NCH; ++ci) {
+                cur[ci] = nxt[ci];
+                nxt[ci] = colnorm(t + 1, c_lo + ci);
+            }
             mbar_wait(acc_full + a, (t >> 1) & 1, abort, err);
-            if (epi_barrier_or(NEPI, *abort != 0)) break;
+            // a warp that sees the abort leaves; the others leave at their
+            // next check (no epilogue barrier inside this loop)
+            if (__any_sync(0xffffffffu, *abort != 0)) break;
             tc_fence_after();
-            const float4 *nb4 = reinterpret_cast<const float4 *>(nbuf + a * TN);
-#pragma unroll 1
-            for (int c = c_lo; c < c_hi; ++c) {
+#pragma unroll
+            for (int ci = 0; ci < NCH; ++ci) {
+                const int c = c_lo + ci;
+                __syncwarp();
+                wn[lane] = cur[ci];
+                __syncwarp();
                 float v[32];
                 tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * TN + c * 32), v);
                 float nbv[32];
+                const float4 *nb4 = reinterpret_cast<const float4 *>(wn);
 #pragma unroll
                 for (int j4 = 0; j4 < 8; ++j4) {
-                    const float4 t4 = nb4[c * 8 + j4];
+                    const float4 t4 = nb4[j4];
                     nbv[j4 * 4 + 0] = t4.x;
                     nbv[j4 * 4 + 1] = t4.y;
                     nbv[j4 * 4 + 2] = t4.z;
