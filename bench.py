@@ -169,6 +169,21 @@ def cpu_model():
 
 
 # ------------------------------------------------------------------ arms
+def job_rate(ms_local: float, n_per_rank: int, world: int, device: str = "cpu"):
+    """Whole-job rate of independent replicas (weak scaling): every rank builds
+    its own n-point index; the step time is the slowest rank's (max over
+    ranks), and the job processes world * n points per step.  Returns
+    (ms_max, points_per_s).  Needs an initialised process group when world > 1."""
+    ms = ms_local
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * n_per_rank / (ms / 1e3)
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -274,11 +289,7 @@ def run_ours(args):
     work = {c: ctx.counter(c) for c in ("search_expansions", "search_evaluations", "search_bytes",
                                         "prune_rows", "prune_candidates", "prune_bytes")}
     ctx.set_timing(False)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * n / (ms / 1e3)
+    ms, value = job_rate(ms, n, world, "cuda")
 
     # ---------------------------------------------------------- queries
     qres = {}
