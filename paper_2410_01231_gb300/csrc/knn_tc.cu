@@ -304,7 +304,8 @@ __global__ void __launch_bounds__(tc_threads(H), 1)
 k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUtensorMap mapX,
          int64_t nq, int64_t n, int dp, const float *__restrict__ qnorm,
          const float *__restrict__ xnorm, int K, int self_exclude, int32_t *__restrict__ out_i,
-         float *__restrict__ out_s, int *err, const int32_t *__restrict__ perm, int rotate) {
+         float *__restrict__ out_s, int *err, const int32_t *__restrict__ perm, int rotate,
+         unsigned long long *progress, int resident) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = reinterpret_cast<uint8_t *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     constexpr int STG = tc_stages(H, KB), NEPI = 128 * H, KCAP = tc_kcap(KB);
@@ -329,13 +330,17 @@ k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUten
     const uint32_t a_bytes = (uint32_t)TM * dp * 2, b_bytes = (uint32_t)TN * dp * 2;
     // With `rotate` (spatially sorted points) the scan first covers a window
     // of `pre` tiles around the CTA's own rows, where its nearest candidates
-    // are, so the thresholds tighten early; then every other tile in the
-    // common global order, so that concurrent CTAs read the same candidate
+    // are, so the thresholds tighten early; then every other tile in a
+    // common cyclic order.  A CTA starts that cycle where the CTAs already
+    // running are: `progress` counts the tiles issued by all CTAs, so
+    // progress / resident is the position every resident CTA has reached if
+    // each started the same way, and concurrent CTAs read the same candidate
     // tiles at about the same time and share them in L2.  Every role walks
-    // the same order.
+    // the same order (the start is read once and shared).
     const int pre = rotate ? min(16, ntiles) : 0;
     const int w0 = rotate ? max(0, min((int)(row0 / TN) - pre / 2, ntiles - pre)) : 0;
-    auto tile_at = [&](int t) { return t < pre ? w0 + t : (t - pre < w0 ? t - pre : t); };
+    const int nrest = max(1, ntiles - pre);
+    int *start_slot = reinterpret_cast<int *>(sm + Ly.misc + 8);
 
     if (threadIdx.x == 0) {
         mbar_init(a_full, 1);
@@ -349,6 +354,9 @@ k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUten
         }
         mbar_init(drain, 1);
         *abort = 0;
+        *start_slot = progress ? (int)((atomicAdd(progress, 0ull) / (unsigned long long)resident) %
+                                       (unsigned long long)nrest)
+                               : 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -362,6 +370,13 @@ k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUten
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    const int start = *start_slot;
+    auto tile_at = [&](int t) {
+        if (t < pre) return w0 + t;
+        int k = t - pre + start;
+        if (k >= nrest) k -= nrest;
+        return k < w0 ? k : k + pre;
+    };
 
     if (warp == 0) {
         if (lane == 0 && KB) {  // ---------------- TMA producer, k-blocked
@@ -378,6 +393,7 @@ k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUten
                     mbar_expect_tx(b_full + s, KB_STAGE);
                     tma_load_2d(st, &mapQ, b_full + s, kb * 64, (int)row0);
                     tma_load_2d(st + TM * 128, &mapX, b_full + s, kb * 64, tile_at(t) * TN);
+                    if (kb == 0 && progress) atomicAdd(progress, 1ull);
                     issued = it + 1;
                 }
             }
@@ -401,6 +417,7 @@ k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUten
                 for (int kb = 0; kb < nkb; ++kb)
                     tma_load_2d(B + (size_t)s * TN * dp * 2 + kb * TN * 128, &mapX, b_full + s,
                                 kb * 64, tile_at(t) * TN);
+                if (progress) atomicAdd(progress, 1ull);
                 issued = t + 1;
             }
             if (*abort) {  // let the copies already issued land before TMEM is freed
@@ -883,8 +900,8 @@ struct TcVariant {
 
 static TcVariant tc_variant(int dp, int K) {
     const uint32_t cap = 227 * 1024 - 1024;
-    if (K <= KTC && tc_layout(dp, 2).total <= cap) return {2, false};
     if (K <= KTC && tc_layout(dp, 1).total <= cap) return {1, false};
+    if (K <= KTC && tc_layout(dp, 2).total <= cap) return {2, false};
     return {1, true};
 }
 
@@ -963,18 +980,27 @@ pg_status pg_knn_tc(pg_ctx *ctx, const float *D, int64_t n, int32_t d, const flo
                                                : (V.H == 2 ? k_knn_tc<2, false> : k_knn_tc<1, false>),
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     // one launch of the chosen variant
+    // tiles issued by all CTAs of a launch (the common start of each cycle)
+    Scratch<unsigned long long> prog;
+    PG_TRY(prog.alloc(ctx, 2));
     auto launch = [&](unsigned grid, const CUtensorMap &mq_, const CUtensorMap &mx_, int64_t nq_,
                       int64_t n_, const float *qn_, const float *xn_, int K_, int self_,
-                      int32_t *oi, float *os, const int32_t *perm_, int rot) {
+                      int32_t *oi, float *os, const int32_t *perm_, int rot) -> pg_status {
+        PG_TRY_CUDA(ctx, cudaMemsetAsync(prog.p, 0, 8, ctx->stream));
+        const int res = ctx->num_sms;  // one CTA per SM (shared memory)
         if (V.KB)
             k_knn_tc<1, true><<<grid, tc_threads(1), smem, ctx->stream>>>(
-                mq_, mx_, nq_, n_, dp, qn_, xn_, K_, self_, oi, os, ctx->d_err, perm_, rot);
+                mq_, mx_, nq_, n_, dp, qn_, xn_, K_, self_, oi, os, ctx->d_err, perm_, rot, prog.p,
+                res);
         else if (V.H == 2)
             k_knn_tc<2, false><<<grid, tc_threads(2), smem, ctx->stream>>>(
-                mq_, mx_, nq_, n_, dp, qn_, xn_, K_, self_, oi, os, ctx->d_err, perm_, rot);
+                mq_, mx_, nq_, n_, dp, qn_, xn_, K_, self_, oi, os, ctx->d_err, perm_, rot, prog.p,
+                res);
         else
             k_knn_tc<1, false><<<grid, tc_threads(1), smem, ctx->stream>>>(
-                mq_, mx_, nq_, n_, dp, qn_, xn_, K_, self_, oi, os, ctx->d_err, perm_, rot);
+                mq_, mx_, nq_, n_, dp, qn_, xn_, K_, self_, oi, os, ctx->d_err, perm_, rot, prog.p,
+                res);
+        return PG_OK;
     };
     const int32_t *permp = nullptr;
     const __nv_bfloat16 *xp = xb.p;
@@ -997,8 +1023,8 @@ pg_status pg_knn_tc(pg_ctx *ctx, const float *D, int64_t n, int32_t d, const flo
         CUtensorMap mqa, mpa;
         PG_TRY(make_map(ctx, &mqa, xb.p, n, dp));
         PG_TRY(make_map(ctx, &mpa, pb.p, P, dp));
-        launch((unsigned)((n + TM - 1) / TM), mqa, mpa, n, P, xnorm, pn.p, 1, 0, asg.p, adist.p,
-               nullptr, 0);
+        PG_TRY(launch((unsigned)((n + TM - 1) / TM), mqa, mpa, n, P, xnorm, pn.p, 1, 0, asg.p,
+                      adist.p, nullptr, 0));
         PG_LAUNCHED(ctx);
         PG_TRY(cnt.alloc(ctx, (size_t)P));
         PG_TRY(boff.alloc(ctx, (size_t)P + 1));
@@ -1030,7 +1056,7 @@ pg_status pg_knn_tc(pg_ctx *ctx, const float *D, int64_t n, int32_t d, const flo
     PG_TRY(make_map(ctx, &mq, qp, self ? n : nq, dp));
     const unsigned grid = (unsigned)((nq + TM - 1) / TM);
     pg_timer_begin(ctx, TM_KNN);
-    launch(grid, mq, mx, nq, n, qnp, xnp, K, self, ids, dist, permp, permp ? 1 : 0);
+    PG_TRY(launch(grid, mq, mx, nq, n, qnp, xnp, K, self, ids, dist, permp, permp ? 1 : 0));
     PG_LAUNCHED(ctx);
     pg_timer_end(ctx, TM_KNN, 2.0 * (double)nq * (double)n * (double)d);
     return PG_OK;
