@@ -493,6 +493,23 @@ def run_ours(args):
             "kernel": "k_prune", "bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s",
             "frac": a / hbm, "traffic": None, "algorithmic_bytes_per_step": b / args.steps,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    # DRAM traffic of a kernel's main launch from an ncu capture recorded in
+    # profiles/roofline_traffic.json, valid only while the kernel's source
+    # file is byte-identical to the one captured (else null)
+    try:
+        import hashlib
+        with open(os.path.join(ROOT, "profiles", "roofline_traffic.json")) as f:
+            rec = json.load(f)
+        for name, r in rooflines.items():
+            ent = rec.get(r["kernel"])
+            if not ent or ent.get("n") != n:
+                continue
+            with open(os.path.join(ROOT, ent["source"]), "rb") as f:
+                if hashlib.sha256(f.read()).hexdigest() == ent["source_sha256"]:
+                    r["traffic"] = ent["dram_bytes_per_launch"]
+                    r["traffic_note"] = ent["note"]
+    except (OSError, ValueError, KeyError):
+        pass
     # the dominant single kernel of the step (connect is a chain of kernels)
     top = max(rooflines, key=lambda k: kt[k][0]) if rooflines else None
     roof = dict(rooflines[top], share_of_step=kt[top][0] / args.steps / ms) if top else None
