@@ -362,11 +362,25 @@ pg_status pg_serve_submit_insert(pg_server *server, const float *X, int64_t m, i
  * completed, and the return value is then that request's status. */
 pg_status pg_serve_wait(pg_server *server, int64_t ticket, double timeout_s, int32_t *done);
 
+/* Admission control: a submit is refused with PG_ERR_CAPACITY (nothing
+ * enqueued, no ticket) while `limit` requests are pending (queued or
+ * running); 0 = no limit (the default). */
+pg_status pg_serve_set_queue_limit(pg_server *server, int64_t limit);
+
 /* host_stats4 = {launch batches, requests, queries, inserted points} so far. */
 pg_status pg_serve_stats(pg_server *server, int64_t *host_stats4);
 
 /* Finish every queued request, join the worker and free the server. */
 pg_status pg_serve_stop(pg_server *server);
+
+/* ------------------------------------------------------------ self test */
+
+/* Failure path of the bounded device waits, without a fault: one thread
+ * waits on an mbarrier that nothing completes, gives up after `seconds`
+ * (0 < seconds <= 5), records a timeout in the context's error word and
+ * returns; the call then returns PG_ERR_TIMEOUT, like a kernel whose
+ * pipeline wait expired, and the context stays usable. */
+pg_status pg_selftest_wait_timeout(pg_ctx *ctx, double seconds);
 
 /* Seconds spent per build phase by the last build on this index:
  * knn, prune, union, connect, acquire, layers (host array of 6). */

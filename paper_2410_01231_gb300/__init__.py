@@ -92,6 +92,8 @@ _sig("pg_serve_submit_insert", C.c_int, [P, P, i64, i32, i32, P])
 _sig("pg_serve_wait", C.c_int, [P, i64, dbl, P])
 _sig("pg_serve_stats", C.c_int, [P, P])
 _sig("pg_serve_stop", C.c_int, [P])
+_sig("pg_serve_set_queue_limit", C.c_int, [P, i64])
+_sig("pg_selftest_wait_timeout", C.c_int, [P, dbl])
 
 EXPORTS = ["pg_default_params", "pg_ctx_create", "pg_ctx_destroy", "pg_last_error", "pg_ctx_sync",
            "pg_ctx_launches", "pg_build_knn", "pg_knn_query", "pg_prune", "pg_reverse_union",
@@ -101,7 +103,8 @@ EXPORTS = ["pg_default_params", "pg_ctx_create", "pg_ctx_destroy", "pg_last_erro
            "pg_ctx_set_timing", "pg_ctx_kernel_time", "pg_ctx_counter",
            "pg_ctx_kernel_work", "pg_prune_noalloc", "pg_index_reserve", "pg_index_insert",
            "pg_serve_start", "pg_serve_submit_query", "pg_serve_submit_insert", "pg_serve_wait",
-           "pg_serve_stats", "pg_serve_stop"]
+           "pg_serve_stats", "pg_serve_stop", "pg_serve_set_queue_limit",
+           "pg_selftest_wait_timeout"]
 
 
 class PGError(RuntimeError):
@@ -163,6 +166,11 @@ class Context:
         self._check(_lib.pg_ctx_kernel_work(self._h, name.encode(), C.byref(v)),
                     "pg_ctx_kernel_work")
         return v.value
+
+    def selftest_wait_timeout(self, seconds: float = 0.2):
+        """Bounded-wait failure path (pg_selftest_wait_timeout): raises PGError TIMEOUT."""
+        self._check(_lib.pg_selftest_wait_timeout(self._h, float(seconds)),
+                    "pg_selftest_wait_timeout")
 
     def counter(self, name: str) -> int:
         """Cumulative counter (pg_ctx_counter): "connect_edges", "connect_full_rounds",
@@ -470,6 +478,11 @@ class Server:
         if done.value:
             self._keep.pop(ticket, None)
         return bool(done.value)
+
+    def set_queue_limit(self, limit: int):
+        """Refuse submissions (PGError CAPACITY) while `limit` requests are pending."""
+        self.ctx._check(_lib.pg_serve_set_queue_limit(self._h, int(limit)),
+                        "pg_serve_set_queue_limit")
 
     def stats(self):
         a = (C.c_int64 * 4)()

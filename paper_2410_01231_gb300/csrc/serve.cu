@@ -37,6 +37,7 @@ struct pg_server {
     int device = 0;
     int d = 0;
     int max_batch = 1024;
+    int64_t queue_limit = 0;  // pending requests admitted at most (0: no limit)
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<Req> queue;
@@ -131,6 +132,8 @@ pg_status submit(pg_server *s, Req r, int64_t *ticket) {
     {
         std::lock_guard<std::mutex> lk(s->mu);
         if (s->stopping) return pg_fail(s->ctx, PG_ERR_INVALID_ARG, "server is stopping");
+        if (s->queue_limit > 0 && s->next_ticket - 1 - s->last_done >= s->queue_limit)
+            return PG_ERR_CAPACITY;  // admission refused: the queue is full
         r.ticket = s->next_ticket++;
         s->queue.push_back(r);
     }
@@ -206,6 +209,13 @@ extern "C" pg_status pg_serve_wait(pg_server *s, int64_t ticket, double timeout_
     if (!*done) return PG_OK;
     auto it = s->failed.find(ticket);
     return it == s->failed.end() ? PG_OK : (pg_status)it->second;
+}
+
+extern "C" pg_status pg_serve_set_queue_limit(pg_server *s, int64_t limit) {
+    if (!s || limit < 0) return PG_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->queue_limit = limit;
+    return PG_OK;
 }
 
 extern "C" pg_status pg_serve_stats(pg_server *s, int64_t *host_stats4) {
