@@ -28,7 +28,7 @@ def _points(n):
 def test_budget_refuses_scratch_and_context_stays_usable(pg):
     D = _points(3000)
     Dd = torch.from_numpy(D).cuda()
-    small = pg.Context(hbm_budget_bytes=1 << 20)
+    small = pg.Context(hbm_budget_bytes=4096)
     with pytest.raises(pg.PGError) as e:
         pg.build_knn(small, Dd, 16)
     assert e.value.status == 6  # PG_ERR_BUDGET
@@ -58,8 +58,8 @@ def test_full_serving_queue_refuses_admission(pg):
     ctx = pg.Context()
     D = _points(3000)
     X = synthetic.inserts(1, 12000)
-    idx = pg.Index.build_nswg(ctx, torch.from_numpy(D).cuda(), metric="l2", K=16, L=32, R=16,
-                              M=16, alpha_deg=70.0, iters=1, seed=3)
+    idx = pg.Index.build_nswg(ctx, torch.from_numpy(D).cuda(), metric="l2", K=24, L=48, R=32,
+                              M=16, alpha_deg=70.0, iters=1, seed=5)
     idx.reserve(3000 + 12000)
     srv = pg.Server(idx)
     srv.set_queue_limit(1)
