@@ -84,8 +84,8 @@ typedef struct {
 typedef struct {
     pg_metric metric;
     pg_precision precision;
-    int32_t K;               /* k0: degree of the exact initial KNNG (Alg. 6 l.1)   */
-    int32_t L;               /* pool width of the k-CNA search (Alg. 5 l.8); ef    */
+    int32_t K;               /* k0: degree of the exact initial KNNG (Alg. 6)   */
+    int32_t L;               /* pool width of the k-CNA search (Alg. 5); ef    */
     int32_t R;               /* degree bound M of the RNG graph / NSWG layer 0     */
     int32_t M;               /* NSWG upper-layer degree bound and level base       */
     double alpha_deg;        /* alpha of the OptKCNA refinements (Section 4.1)     */
@@ -146,7 +146,7 @@ pg_status pg_ctx_counter(pg_ctx *ctx, const char *name, int64_t *value);
 /* ------------------------------------------------------------------ steps */
 
 /* Exact K nearest neighbours of every point (the KNNG G_k0 of the
- * initialization phase, Section 3.1 and Algorithm 6 line 1, computed by
+ * initialization phase, Section 3.1 and Algorithm 6, computed by
  * brute force).  For every u the K smallest (s(u,v), v) with v != u.
  * ids [n][K], dist [n][K] (FP32 value of s); rows with fewer than K other
  * points are padded with -1 / +inf.  1 <= K <= 256, d % 4 == 0.
@@ -206,7 +206,7 @@ pg_status pg_prune_noalloc(void *cuda_stream, const float *D, int64_t n, int32_t
                            pg_metric metric, const int64_t *cand_off, const int32_t *cand_ids,
                            int32_t R, double alpha_deg, int32_t *nbr, int32_t *deg);
 
-/* Reverse-edge union (Algorithm 2 lines 7-8, Algorithm 5 lines 3-4): row
+/* Reverse-edge union (Algorithm 2, Algorithm 5): row
  * u = N(u) together with every v that has u in N(v).  nbr [n][R], deg [n]
  * in; off [n+1] and ids out (ids needs capacity >= 2 * sum(deg); entries
  * within a row are in no particular order).  *host_total (host, may be
@@ -222,7 +222,7 @@ pg_status pg_reverse_union(pg_ctx *ctx, const int32_t *nbr, const int32_t *deg, 
 pg_status pg_medoid(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
                     int64_t *host_ep);
 
-/* Connectivity step (Algorithm 2 lines 10-11, Algorithm 5 lines 5-6),
+/* Connectivity step (Algorithm 2, Algorithm 5),
  * in place on nbr/deg: S = nodes reachable from ep; while S != V the
  * smallest unreached id r is linked from p = argmin over x in S with
  * deg(x) < R of (s(x,r), x), and everything reachable from r joins S.
@@ -272,7 +272,7 @@ pg_status pg_build_nswg(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
 
 /* k-ANN queries on an index: from the top layer down to layer 1,
  * w <- first of KANNSearch(G_i, q, 1, upper_beam, w); then
- * KANNSearch(G_0, q, k, beam, w) (pattern of Algorithm 4 lines 8-12, where
+ * KANNSearch(G_0, q, k, beam, w) (pattern of Algorithm 4, where
  * upper_beam = 1 is the greedy routing of the paper); an index without
  * upper layers (or with PG_SEARCH_FLAT) starts at its medoid.
  * Q [nq][d] device; out [nq][k].  1 <= k <= beam <= 256,
@@ -319,7 +319,7 @@ pg_status pg_index_reserve(pg_ctx *ctx, pg_index *index, int64_t capacity);
  * copied into the index) with ids n .. n+m-1: the search and refinement
  * phases of Algorithm 4 for every new point, all against the graph as it
  * was before the batch (one batch = one snapshot).  Each new point u takes
- * the level of the build's SplitMix64 draw (Algorithm 7 line 2), capped at
+ * the level of the build's SplitMix64 draw (Algorithm 7), capped at
  * the top layer; w = the top entry, w <- best of a pool-`upper_beam`
  * search in each layer above l(u) (1 = the paper's greedy routing); for
  * i = l(u)..0: W_i <- KANNSearch(G_i, u, ef, ef, w), w <- W_i[0],

@@ -137,7 +137,7 @@ def prune(D, off, cand, R: int, alpha_deg: float, metric: str = "l2"):
 
 
 def reverse_union(nbr, deg):
-    """Row u = N(u) then {v : u in N(v)} (Algorithm 2 lines 7-8)."""
+    """Row u = N(u) then {v : u in N(v)} (Algorithm 2)."""
     nbr = np.ascontiguousarray(nbr, np.int32)
     deg = np.ascontiguousarray(deg, np.int32)
     n, R = nbr.shape
@@ -155,7 +155,7 @@ def medoid(D, metric: str = "l2") -> int:
 
 
 def connect(D, nbr, deg, ep: int, metric: str = "l2"):
-    """Link unreachable components (Algorithm 2 lines 10-11); returns copies."""
+    """Link unreachable components (Algorithm 2); returns copies."""
     D = _f32(D)
     nbr = np.array(nbr, np.int32, copy=True)
     deg = np.array(deg, np.int32, copy=True)
@@ -197,7 +197,7 @@ def search(D, nbr, deg, Q, starts, k: int, L: int, metric: str = "l2", rows=None
 
 
 def acquire(D, nbr, deg, L: int, metric: str = "l2"):
-    """C(u) <- KANNSearch(G, u, L, L, u) minus u (Algorithm 5 lines 7-8)."""
+    """C(u) <- KANNSearch(G, u, L, L, u) minus u (Algorithm 5)."""
     D = _f32(D)
     nbr = np.ascontiguousarray(nbr, np.int32)
     deg = np.ascontiguousarray(deg, np.int32)
@@ -231,7 +231,7 @@ def splitmix64(x: int) -> int:
 
 
 def levels(n: int, seed: int, M: int) -> np.ndarray:
-    """HNSW levels floor(-ln U / ln M), U from SplitMix64 (Algorithm 7 line 2)."""
+    """HNSW levels floor(-ln U / ln M), U from SplitMix64 (Algorithm 7)."""
     out = np.empty(n, np.int32)
     _get().or_levels(n, seed, M, _p(out))
     return out
@@ -292,7 +292,7 @@ def search_nswg(D, layers, ep: int, Q, k: int, ef: int, metric: str = "cosine",
                 ef_upper: int = 1):
     """Layered query: w <- first of KANNSearch(G_i, q, 1, ef_upper, w) from
     the top layer down to layer 1, then KANNSearch(G_0, q, k, ef, w)
-    (pattern of Algorithm 4 lines 8-12; ef_upper = 1 is greedy routing)."""
+    (pattern of Algorithm 4; ef_upper = 1 is greedy routing)."""
     D = _f32(D)
     Q = _f32(Q)
     n = D.shape[0]
@@ -314,7 +314,7 @@ def insert_batch(D_all, layers, ep: int, n_old: int, ef: int, alpha_deg: float =
     index, every new point against the graph as it was before the batch.
 
     Per new point u (the search and refinement phases of Algorithm 4):
-    its level l(u) is the SplitMix64 draw of the build (Algorithm 7 line 2)
+    its level l(u) is the SplitMix64 draw of the build (Algorithm 7)
     capped at the top layer; w <- ep, then w <- first of
     KANNSearch(G_i, u, 1, ef_upper, w) for the layers above l(u); for
     i = l(u)..0: W_i <- KANNSearch(G_i, u, ef, ef, w), w <- W_i[0], and

@@ -102,7 +102,7 @@ static int topk_push(item_t *top, int cnt, int cap, item_t it)
 
 /* ---------------------------------------------------------------------- */
 /* Exact k-nearest neighbours (the KNNG of the initialization phase,      */
-/* Section 3.1 / Algorithm 6 line 1, computed exactly by brute force).    */
+/* Section 3.1 / Algorithm 6, computed exactly by brute force).    */
 /* For query row q the K smallest (s(q,v), v) over all v != exclude[q].    */
 /* Q may be D itself (exclude[q] = q) or external queries (exclude NULL). */
 /* Rows shorter than K (n-1 < K) are padded with id -1, dist +inf.        */
@@ -152,7 +152,7 @@ int or_knn(const float *D, int64_t n, int d, int metric, const float *Q, int64_t
 /* alpha = 60 degrees is RNG pruning exactly (Section 4.2): when uv is the */
 /* strictly longest side of the triangle its opposite angle exceeds 60,   */
 /* so with alpha60 set the angle clause is skipped.                        */
-/* The scan stops once R candidates are kept (Algorithm 3 line 9).         */
+/* The scan stops once R candidates are kept (Algorithm 3).         */
 /* Returns the number kept; out[] receives them in scan order.            */
 /* ---------------------------------------------------------------------- */
 static int angle_exceeds(double suw, double svw, double suv, double cos_alpha)
@@ -230,7 +230,7 @@ int or_prune(const float *D, int64_t n, int d, int metric, const int64_t *off,
 }
 
 /* ---------------------------------------------------------------------- */
-/* Reverse-edge union (Algorithm 2 lines 7-8; Algorithm 5 lines 3-4):     */
+/* Reverse-edge union (Algorithm 2; Algorithm 5):     */
 /* row u of the result is N(u) followed by every v with u in N(v), v in   */
 /* increasing order.  Every row reads the same input graph (the pass-1    */
 /* lists), which is the reading of "for each u in parallel".  Prune then  */
@@ -302,7 +302,7 @@ int64_t or_medoid(const float *D, int64_t n, int d, int metric, double *centroid
 }
 
 /* ---------------------------------------------------------------------- */
-/* Connectivity (Algorithm 2 lines 10-11; Algorithm 5 lines 5-6): "find   */
+/* Connectivity (Algorithm 2; Algorithm 5): "find   */
 /* connected components via DFS; add extra edges between them".  Reading, */
 /* deterministic: S = nodes reachable from ep along directed edges.  While */
 /* S != V: r = smallest unreached id; p = argmin over x in S with          */
@@ -484,7 +484,7 @@ int or_search(const float *D, int64_t n, int d, int metric, const int32_t *nbr,
 }
 
 /* ---------------------------------------------------------------------- */
-/* k-CNA by search on the refined graph (Algorithm 5 lines 7-8):          */
+/* k-CNA by search on the refined graph (Algorithm 5):          */
 /* C(u) <- KANNSearch(G^, u, L, L, u): every point searches for itself,    */
 /* starting at itself, with pool width L.  The row keeps the pool minus u */
 /* itself, in pool order, padded with -1 to L entries.                     */
@@ -528,7 +528,7 @@ int or_acquire(const float *D, int64_t n, int d, int metric, const int32_t *nbr,
 /*   repeat I times:                                                       */
 /*     N <- Prune(C, R, alpha);  N <- Prune(N u reverse(N), R, alpha);     */
 /*     connect(N, ep);  C(u) <- KANNSearch(N, u, L, L, u)                  */
-/*   final Refine (Algorithm 2 lines 5-11): the same two prunes with        */
+/*   final Refine (Algorithm 2): the same two prunes with        */
 /*   alpha = alpha_final (60 degrees: RNG pruning), then connect unless    */
 /*   connect_final is 0 (NSWG layers, Section 5.3).                        */
 /* ep is the medoid (or_medoid).  Outputs nbr [n][R], deg [n]; returns ep, */
@@ -601,7 +601,7 @@ int64_t or_build_rng(const float *D, int64_t n, int d, int metric, int K, int L,
 }
 
 /* ---------------------------------------------------------------------- */
-/* HNSW level draw (Algorithm 4 line 4, Algorithm 7 line 2): an           */
+/* HNSW level draw (Algorithm 4, Algorithm 7): an           */
 /* exponentially decaying level l = floor(-ln(U) / ln(M)).  The uniform   */
 /* U of point i comes from SplitMix64 (Steele, Lea and Flood, OOPSLA      */
 /* 2014) seeded with seed XOR i: U = ((z >> 11) + 1) * 2^-53, in (0, 1].   */

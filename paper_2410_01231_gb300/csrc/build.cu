@@ -165,7 +165,7 @@ uint64_t splitmix64(uint64_t x) {
 
 // Level of a point: floor(-ln U / ln M), U = ((z >> 11) + 1) 2^-53 with
 // z = SplitMix64(seed XOR id) -- the exponentially decaying level draw of
-// Algorithm 4 line 4 / Algorithm 7 line 2.
+// Algorithm 4 / Algorithm 7.
 int level_of(int64_t id, uint64_t seed, int M) {
     const uint64_t z = splitmix64(seed ^ (uint64_t)id);
     const double U = (double)((z >> 11) + 1) * (1.0 / 9007199254740992.0);

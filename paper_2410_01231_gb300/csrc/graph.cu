@@ -6,7 +6,7 @@
 // inside the block), the block sums are added in block order and divided
 // by n; ep is the exact FP64 argmin of s(x, centroid), ties by id.
 //
-// Connectivity (Algorithm 2 lines 10-11, Algorithm 5 lines 5-6): nodes
+// Connectivity (Algorithm 2, Algorithm 5): nodes
 // reachable from ep are marked by a breadth-first pass; then, one round per
 // unreached component, the smallest unreached id r is linked from the
 // nearest reached node with a free adjacency slot (FP32 argmin, re-decided

@@ -1,5 +1,5 @@
 // knn.cu -- exact K-nearest-neighbour graph (the KNNG G_k0 of the
-// initialization phase, Section 3.1 / Algorithm 6 line 1) by brute-force
+// initialization phase, Section 3.1 / Algorithm 6) by brute-force
 // distance tiles with a fused top-K.
 //
 // FP32 form: a CTA owns 64 query rows and streams every candidate column in

@@ -1,6 +1,6 @@
 // prune.cu -- alpha-pruning (Section 4.1 rule in the scan of Prune,
-// Algorithm 3) and the reverse-edge union (Algorithm 2 lines 7-8,
-// Algorithm 5 lines 3-4).
+// Algorithm 3) and the reverse-edge union (Algorithm 2,
+// Algorithm 5).
 //
 // One warp prunes one point u.  Candidate distances s(u,v) are computed by
 // four teams of eight lanes (128-bit loads), the row is sorted by (s, id)

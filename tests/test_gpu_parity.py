@@ -158,8 +158,8 @@ def test_prune_bit_exact_given_identical_candidates(ctx, pg, kind, alpha):
     assert (host(gdg) == odg).all()
     assert (host(gn) == on).all()
     assert st["rows"] == D.shape[0] and st["edges"] == int(odg.sum())
-    # near-margin decisions are rare (spec budget: < 0.01% of edges
-    # may be decided by a margin below 1e-5; here they are all rechecked)
+    # near-margin decisions are rare (a tolerance of < 0.01% of edges decided
+    # by a margin below 1e-5 would be acceptable; here they are all rechecked)
     assert st["fp64_flips"] <= st["fp64_rechecks"]
 
 
