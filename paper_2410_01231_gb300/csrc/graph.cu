@@ -923,30 +923,74 @@ static pg_status connect_exact(pg_ctx *ctx, const float *D, int64_t n, int32_t d
                                      cudaMemcpyDeviceToDevice, ctx->stream));
     PG_TRY_CUDA(ctx, cudaMemcpyAsync(&st.p->nfree, &init->nfree, sizeof(int),
                                      cudaMemcpyDeviceToDevice, ctx->stream));
+    // One group = 8 batches of 6 launches each, the same launches every time
+    // (all state lives in ConnX): the loop is launch-bound, so the group is
+    // captured once as a CUDA graph and replayed (direct launches if the
+    // capture is refused).  Per-kernel timers only on the direct path.
+    auto issue_group = [&](bool timed) -> pg_status {
+        for (int g = 0; g < 8; ++g) {
+            if (timed) pg_timer_begin(ctx, TM_CSELECT);
+            k_cx_select<<<1, CT, 0, ctx->stream>>>(reached, n, st.p);
+            PG_LAUNCHED(ctx);
+            if (timed) pg_timer_end(ctx, TM_CSELECT);
+            if (timed) pg_timer_begin(ctx, TM_CSCAN);
+            PG_TRY(pg_tc_argmin(ctx, tc, D, st.p->r, &st.p->b, reached, deg, R, st.p->best));
+            if (timed) pg_timer_end(ctx, TM_CSCAN);
+            if (timed) pg_timer_begin(ctx, TM_CFAST);
+            k_cx_comp<<<CB_B, 256, 0, ctx->stream>>>(nbr, deg, R, n, reached, st.p, comp.p);
+            PG_LAUNCHED(ctx);
+            k_cx_pair<<<ctx->num_sms * 2, 256, 0, ctx->stream>>>(D, d, 0, deg, R, st.p, comp.p);
+            PG_LAUNCHED(ctx);
+            if (timed) pg_timer_end(ctx, TM_CFAST);
+            if (timed) pg_timer_begin(ctx, TM_CCOMMIT);
+            k_cx_decide<<<1, CXD, 0, ctx->stream>>>(nbr, deg, R, n, reached, queue, st.p, comp.p,
+                                                   ctx->d_err);
+            PG_LAUNCHED(ctx);
+            if (timed) pg_timer_end(ctx, TM_CCOMMIT);
+        }
+        return PG_OK;
+    };
+    struct GraphExec {
+        cudaGraphExec_t e = nullptr;
+        ~GraphExec() {
+            if (e) cudaGraphExecDestroy(e);
+        }
+    } exec;
+    int64_t per_group = 0;
+    {
+        // captured on a private stream (the context's stream may be the legacy
+        // default stream, which cannot capture); replayed on the context's
+        const int64_t l0 = ctx->launches;
+        cudaStream_t cap = nullptr;
+        if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) == cudaSuccess) {
+            cudaStream_t saved = ctx->stream;
+            ctx->stream = cap;
+            cudaGraph_t graph = nullptr;
+            if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                const pg_status cs = issue_group(false);
+                const cudaError_t e = cudaStreamEndCapture(cap, &graph);
+                if (cs == PG_OK && e == cudaSuccess && graph &&
+                    cudaGraphInstantiate(&exec.e, graph, 0) != cudaSuccess)
+                    exec.e = nullptr;
+                if (graph) cudaGraphDestroy(graph);
+            }
+            ctx->stream = saved;
+            cudaStreamDestroy(cap);
+        }
+        cudaGetLastError();  // a refused capture leaves no sticky error
+        per_group = ctx->launches - l0;
+        ctx->launches = l0;
+    }
     const int64_t max_groups = n / 8 + 2;
     for (int64_t group = 0;; ++group) {
         if (group > max_groups)
             return pg_fail(ctx, PG_ERR_INTERNAL, "connect: no progress after %lld batches",
                            (long long)(group * 8));
-        for (int g = 0; g < 8; ++g) {
-            pg_timer_begin(ctx, TM_CSELECT);
-            k_cx_select<<<1, CT, 0, ctx->stream>>>(reached, n, st.p);
-            PG_LAUNCHED(ctx);
-            pg_timer_end(ctx, TM_CSELECT);
-            pg_timer_begin(ctx, TM_CSCAN);
-            PG_TRY(pg_tc_argmin(ctx, tc, D, st.p->r, &st.p->b, reached, deg, R, st.p->best));
-            pg_timer_end(ctx, TM_CSCAN);
-            pg_timer_begin(ctx, TM_CFAST);
-            k_cx_comp<<<CB_B, 256, 0, ctx->stream>>>(nbr, deg, R, n, reached, st.p, comp.p);
-            PG_LAUNCHED(ctx);
-            k_cx_pair<<<ctx->num_sms * 2, 256, 0, ctx->stream>>>(D, d, 0, deg, R, st.p, comp.p);
-            PG_LAUNCHED(ctx);
-            pg_timer_end(ctx, TM_CFAST);
-            pg_timer_begin(ctx, TM_CCOMMIT);
-            k_cx_decide<<<1, CXD, 0, ctx->stream>>>(nbr, deg, R, n, reached, queue, st.p, comp.p,
-                                                   ctx->d_err);
-            PG_LAUNCHED(ctx);
-            pg_timer_end(ctx, TM_CCOMMIT);
+        if (exec.e) {
+            PG_TRY_CUDA(ctx, cudaGraphLaunch(exec.e, ctx->stream));
+            ctx->launches += per_group;
+        } else {
+            PG_TRY(issue_group(true));
         }
         int h[8];
         PG_TRY_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned, st.p, sizeof h, cudaMemcpyDeviceToHost,
