@@ -380,7 +380,7 @@ __device__ void flush_stats(const PruneParams &P, RowStats &st, unsigned long lo
 }
 
 template <bool REG>
-__global__ void __launch_bounds__(PW * 32) k_prune(PruneParams P) {
+__global__ void __launch_bounds__(PW * 32, REG ? 3 : 2) k_prune(PruneParams P) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     unsigned char *ws = smem + (size_t)wid * warp_smem_bytes(CMAX, P.d);
