@@ -293,7 +293,7 @@ __device__ void search_one(const SearchParams &P, int64_t qi, unsigned char *ws,
     __syncwarp();
 }
 
-__global__ void __launch_bounds__(SW * 32) k_search(SearchParams P) {
+__global__ void __launch_bounds__(SW * 32, 8) k_search(SearchParams P) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     unsigned char *ws = smem + (size_t)wid * search_warp_smem(P.L, P.hbits, P.d);
