@@ -349,6 +349,21 @@ def test_search_on_complete_graph_is_exact_knn():
         assert ids[q].tolist() == [v for _, v in pairs]
 
 
+def test_search_recall_grows_with_the_pool_width():
+    """A wider pool explores a superset of the routes of a narrower one, so
+    recall@10 on a pruned graph rises with L (soft: a small dip is allowed,
+    the trend is not)."""
+    D, Q, _ = synthetic.workload(1, n=3000, nq=60)
+    nbr, deg, ep = oracle.build_rng(D, 16, 48, 12, 66.0, 60.0, 1)  # connected
+    gt = oracle.knn(D, 10, Q=Q)
+    rec = []
+    for L in (10, 20, 40, 80, 160):
+        found, _ = oracle.search(D, nbr, deg, Q, ep, 10, L)
+        rec.append(oracle.recall_at_k(found, Q, D, 10, gt=gt))
+    assert all(b >= a - 0.02 for a, b in zip(rec, rec[1:]))
+    assert rec[-1] > rec[0]
+
+
 def test_search_on_path_graph_walks_to_the_target():
     n = 60
     D = np.arange(n, dtype=np.float32).reshape(n, 1)
