@@ -349,7 +349,9 @@ typedef struct pg_server pg_server;
 pg_status pg_serve_start(pg_ctx *ctx, pg_index *index, int32_t max_batch, pg_server **out);
 
 /* Enqueue nq HOST query rows Q [nq][d]; results go to HOST out_ids [nq][k]
- * and out_dist [nq][k] (pg_search semantics).  *ticket identifies it. */
+ * and out_dist [nq][k] (pg_search semantics).  *ticket identifies it.  A
+ * refused submission (bad arguments, stopping: PG_ERR_INVALID_ARG; full:
+ * PG_ERR_CAPACITY) returns its status and records no message. */
 pg_status pg_serve_submit_query(pg_server *server, const float *Q, int64_t nq, int32_t k,
                                 int32_t beam, int32_t upper_beam, int32_t *out_ids,
                                 float *out_dist, int64_t *ticket);

@@ -449,13 +449,19 @@ class Server:
                                             C.byref(self._h)), "pg_serve_start")
         self._keep = {}
 
+    @staticmethod
+    def _chk(st, what):
+        # the context's error message belongs to the worker while serving
+        if st != 0:
+            raise PGError(st, what)
+
     def submit_query(self, Q: np.ndarray, k: int, beam: int, upper_beam: int = UPPER_BEAM):
         """Returns (ticket, ids, dist); ids/dist are filled once the ticket completes."""
         Q = np.ascontiguousarray(Q, np.float32)
         ids = np.empty((Q.shape[0], k), np.int32)
         dist = np.empty((Q.shape[0], k), np.float32)
         t = C.c_int64()
-        self.ctx._check(_lib.pg_serve_submit_query(
+        self._chk(_lib.pg_serve_submit_query(
             self._h, Q.ctypes.data_as(C.c_void_p), Q.shape[0], k, beam, upper_beam,
             ids.ctypes.data_as(C.c_void_p), dist.ctypes.data_as(C.c_void_p), C.byref(t)),
             "pg_serve_submit_query")
@@ -465,7 +471,7 @@ class Server:
     def submit_insert(self, X: np.ndarray, ef: int, upper_beam: int = 1) -> int:
         X = np.ascontiguousarray(X, np.float32)
         t = C.c_int64()
-        self.ctx._check(_lib.pg_serve_submit_insert(self._h, X.ctypes.data_as(C.c_void_p),
+        self._chk(_lib.pg_serve_submit_insert(self._h, X.ctypes.data_as(C.c_void_p),
                                                     X.shape[0], ef, upper_beam, C.byref(t)),
                         "pg_serve_submit_insert")
         self._keep[t.value] = (X,)
@@ -473,7 +479,7 @@ class Server:
 
     def wait(self, ticket: int, timeout_s: float = 60.0) -> bool:
         done = C.c_int32()
-        self.ctx._check(_lib.pg_serve_wait(self._h, ticket, timeout_s, C.byref(done)),
+        self._chk(_lib.pg_serve_wait(self._h, ticket, timeout_s, C.byref(done)),
                         "pg_serve_wait")
         if done.value:
             self._keep.pop(ticket, None)
@@ -481,7 +487,7 @@ class Server:
 
     def set_queue_limit(self, limit: int):
         """Refuse submissions (PGError CAPACITY) while `limit` requests are pending."""
-        self.ctx._check(_lib.pg_serve_set_queue_limit(self._h, int(limit)),
+        self._chk(_lib.pg_serve_set_queue_limit(self._h, int(limit)),
                         "pg_serve_set_queue_limit")
 
     def stats(self):

@@ -9,6 +9,11 @@
 // insertion batch (Algorithm 4 on a snapshot, pg_index_insert) runs alone,
 // after every earlier query and before every later one, so a query always
 // sees exactly the points inserted before it was submitted.
+//
+// While the server runs, the context belongs to the worker thread: the
+// submit functions, called from other threads, only validate and enqueue;
+// a refused submission returns its status without touching the context's
+// error message (which the worker may be writing).
 #include <condition_variable>
 #include <deque>
 #include <mutex>
@@ -131,7 +136,7 @@ void worker_main(pg_server *s) {
 pg_status submit(pg_server *s, Req r, int64_t *ticket) {
     {
         std::lock_guard<std::mutex> lk(s->mu);
-        if (s->stopping) return pg_fail(s->ctx, PG_ERR_INVALID_ARG, "server is stopping");
+        if (s->stopping) return PG_ERR_INVALID_ARG;  // the server is stopping
         if (s->queue_limit > 0 && s->next_ticket - 1 - s->last_done >= s->queue_limit)
             return PG_ERR_CAPACITY;  // admission refused: the queue is full
         r.ticket = s->next_ticket++;
@@ -166,11 +171,9 @@ extern "C" pg_status pg_serve_submit_query(pg_server *s, const float *Q, int64_t
                                            int32_t beam, int32_t upper_beam, int32_t *out_ids,
                                            float *out_dist, int64_t *ticket) {
     if (!s) return PG_ERR_INVALID_ARG;
-    if (!Q || !out_ids || !out_dist || !ticket)
-        return pg_fail(s->ctx, PG_ERR_INVALID_ARG, "null pointer");
+    if (!Q || !out_ids || !out_dist || !ticket) return PG_ERR_INVALID_ARG;
     if (nq < 1 || k < 1 || beam < k || beam > 256 || upper_beam < 1 || upper_beam > 256)
-        return pg_fail(s->ctx, PG_ERR_INVALID_ARG,
-                       "need nq >= 1, 1 <= k <= beam <= 256, 1 <= upper_beam <= 256");
+        return PG_ERR_INVALID_ARG;
     Req r;
     r.kind = 0;
     r.host = Q;
@@ -186,9 +189,9 @@ extern "C" pg_status pg_serve_submit_query(pg_server *s, const float *Q, int64_t
 extern "C" pg_status pg_serve_submit_insert(pg_server *s, const float *X, int64_t m, int32_t ef,
                                             int32_t upper_beam, int64_t *ticket) {
     if (!s) return PG_ERR_INVALID_ARG;
-    if (!X || !ticket) return pg_fail(s->ctx, PG_ERR_INVALID_ARG, "null pointer");
+    if (!X || !ticket) return PG_ERR_INVALID_ARG;
     if (m < 1 || ef < 1 || ef > 256 || upper_beam < 1 || upper_beam > 256)
-        return pg_fail(s->ctx, PG_ERR_INVALID_ARG, "need m >= 1, 1 <= ef, upper_beam <= 256");
+        return PG_ERR_INVALID_ARG;
     Req r;
     r.kind = 1;
     r.host = X;
