@@ -222,6 +222,44 @@ def test_prune_output_is_the_defined_set(alpha):
     assert ambiguous < 20
 
 
+def test_prune_definition_on_random_shapes():
+    """The same definition check over random sizes, dimensions, value ranges,
+    degree bounds and angles (property test; skipped without hypothesis)."""
+    pytest.importorskip("hypothesis")
+    from hypothesis import given, settings, strategies as st
+
+    @settings(max_examples=40, deadline=None)
+    @given(n=st.integers(3, 50), d=st.sampled_from([4, 8, 12]), hi=st.integers(2, 9),
+           R=st.integers(1, 12), alpha=st.sampled_from([60.0, 66.0, 90.0, 120.0, 180.0]),
+           seed=st.integers(0, 2**31 - 1))
+    def run(n, d, hi, R, alpha, seed):
+        rng = np.random.default_rng(seed)
+        D = rng.integers(0, hi, size=(n, d)).astype(np.float32)
+        m = int(rng.integers(1, 3 * n))
+        cand = rng.integers(-1, n, size=(n, m)).astype(np.int32)
+        off = np.arange(n + 1, dtype=np.int64) * m
+        nbr, deg = oracle.prune(D, off, cand.ravel(), R, alpha)
+        cos_a = oracle.cos_alpha(alpha)
+        for u in range(n):
+            kept = nbr[u, :deg[u]].tolist()
+            assert deg[u] <= R and len(set(kept)) == len(kept) and u not in kept
+            order = sorted({(exact_s(D[u], D[v]), v) for v in cand[u] if v >= 0 and v != u})
+            rebuilt = []
+            for _, v in order:
+                if len(rebuilt) == R:
+                    break
+                res = [_exact_occludes(D, u, w, v, cos_a) for w in rebuilt]
+                if any(0 < mg < 1e-12 for _, mg in res):  # FP64 may round either way
+                    if v in kept:
+                        rebuilt.append(v)
+                    continue
+                if not any(o for o, _ in res):
+                    rebuilt.append(v)
+            assert rebuilt == kept
+
+    run()
+
+
 def test_prune_drops_self_negative_and_repeats():
     D = int_data(10, 3, 11)
     off = np.array([0, 8] + [8] * 9, np.int64)
