@@ -176,6 +176,30 @@ def test_prune_screened_form_byte_rows_match_oracle(ctx, pg, alpha):
     assert st["edges"] == int(odg.sum())
 
 
+@pytest.mark.parametrize("seed", range(12))
+def test_prune_random_shapes_match_oracle(ctx, pg, seed):
+    """Random sizes, widths (byte rows, wide rows, widths off the 16-byte
+    grid), value kinds, degree bounds and angles, both precision forms."""
+    rng = np.random.default_rng(1000 + seed)
+    n = int(rng.integers(3, 400))
+    d = int(rng.choice([4, 8, 20, 32, 128, 136]))
+    R = int(rng.integers(1, 65))
+    alpha = float(rng.choice([60.0, 66.0, 90.0, 120.0, 180.0]))
+    if seed % 2:
+        D = rng.integers(0, 256, size=(n, d)).astype(np.float32)
+    else:
+        D = rng.normal(size=(n, d)).astype(np.float32)
+    m = int(rng.integers(1, 300))
+    cand = rng.integers(-1, n, size=(n, m)).astype(np.int32)
+    off = np.arange(n + 1, dtype=np.int64) * m
+    on, odg = oracle.prune(D, off, cand.ravel(), R, alpha)
+    for precision in ("fp32", "bf16"):
+        gn, gdg = pg.prune(ctx, dev(D), dev(off), dev(cand.ravel()), R, alpha,
+                           precision=precision)
+        assert (host(gdg) == odg).all(), precision
+        assert (host(gn) == on).all(), precision
+
+
 @pytest.mark.parametrize("precision", ["fp32", "bf16"])
 def test_prune_long_rows_and_empty_rows(ctx, pg, precision):
     D = int_points(3000)
