@@ -257,8 +257,8 @@ def build_nswg(D, K: int, L: int, M: int, R0: int, alpha_deg: float = 66.0,
     complete graph (every other member, by (s, id)); any other layer is the
     IterNSG build of D_i with pool width ef = L, whose final refinement
     skips the connectivity step (Section 5.3).  M_0 = R0 and M_i = M for
-    i >= 1.  ep is the smallest id on the top layer (reading of "randomly
-    select ep"; deterministic).  Layer adjacency holds global ids.
+    i >= 1.  ep is the smallest id on the top layer (a deterministic reading
+    of the paper's random choice of the entry).  Layer adjacency holds global ids.
     """
     D = _f32(D)
     n = D.shape[0]

@@ -102,7 +102,7 @@ static int topk_push(item_t *top, int cnt, int cap, item_t it)
 
 /* ---------------------------------------------------------------------- */
 /* Exact k-nearest neighbours (the KNNG of the initialization phase,      */
-/* Section 3.1 / Algorithm 6, computed exactly by brute force).    */
+/* Section 3.1 / Algorithm 6, computed exactly by brute force).           */
 /* For query row q the K smallest (s(q,v), v) over all v != exclude[q].    */
 /* Q may be D itself (exclude[q] = q) or external queries (exclude NULL). */
 /* Rows shorter than K (n-1 < K) are padded with id -1, dist +inf.        */
@@ -152,7 +152,7 @@ int or_knn(const float *D, int64_t n, int d, int metric, const float *Q, int64_t
 /* alpha = 60 degrees is RNG pruning exactly (Section 4.2): when uv is the */
 /* strictly longest side of the triangle its opposite angle exceeds 60,   */
 /* so with alpha60 set the angle clause is skipped.                        */
-/* The scan stops once R candidates are kept (Algorithm 3).         */
+/* The scan stops once R candidates are kept (Algorithm 3).               */
 /* Returns the number kept; out[] receives them in scan order.            */
 /* ---------------------------------------------------------------------- */
 static int angle_exceeds(double suw, double svw, double suv, double cos_alpha)
@@ -230,12 +230,12 @@ int or_prune(const float *D, int64_t n, int d, int metric, const int64_t *off,
 }
 
 /* ---------------------------------------------------------------------- */
-/* Reverse-edge union (Algorithm 2; Algorithm 5):     */
+/* Reverse-edge union (Algorithm 2; Algorithm 5):                         */
 /* row u of the result is N(u) followed by every v with u in N(v), v in   */
 /* increasing order.  Every row reads the same input graph (the pass-1    */
-/* lists), which is the reading of "for each u in parallel".  Prune then  */
-/* sorts and de-duplicates.  off has n+1 entries; ids needs off[n] slots: */
-/* call with ids == NULL to get the total.                                */
+/* lists), our reading of a step the paper runs for all u at once.  Then */
+/* Prune sorts and de-duplicates.  off has n+1 entries; ids needs off[n] */
+/* slots: call with ids == NULL to get the total.                         */
 /* ---------------------------------------------------------------------- */
 int64_t or_reverse_union(const int32_t *nbr, const int32_t *deg, int64_t n, int R,
                          int64_t *off, int32_t *ids)
@@ -265,8 +265,8 @@ int64_t or_reverse_union(const int32_t *nbr, const int32_t *deg, int64_t n, int 
 }
 
 /* ---------------------------------------------------------------------- */
-/* Entry point: the point closest to the centroid (Section 3.1, search    */
-/* phase: "ep is the closest point in D to the centroid of D").  Reading: */
+/* Entry point: the point closest to the centroid of D (Section 3.1,     */
+/* search phase, which names this point as the entry).  Reading:          */
 /* the exact argmin over all points, ties by id.  The centroid is summed  */
 /* in double per coordinate in blocks of 1024 consecutive points (each    */
 /* block summed in index order, then the block sums added in block order) */
@@ -302,8 +302,9 @@ int64_t or_medoid(const float *D, int64_t n, int d, int metric, double *centroid
 }
 
 /* ---------------------------------------------------------------------- */
-/* Connectivity (Algorithm 2; Algorithm 5): "find   */
-/* connected components via DFS; add extra edges between them".  Reading, */
+/* Connectivity (Algorithm 2; Algorithm 5).  The paper finds connected  */
+/* components by depth-first search and links them with extra edges.     */
+/* Reading,                                                               */
 /* deterministic: S = nodes reachable from ep along directed edges.  While */
 /* S != V: r = smallest unreached id; p = argmin over x in S with          */
 /* deg(x) < R of (s(x,r), x); append r to N(p); add everything reachable  */
@@ -484,7 +485,7 @@ int or_search(const float *D, int64_t n, int d, int metric, const int32_t *nbr,
 }
 
 /* ---------------------------------------------------------------------- */
-/* k-CNA by search on the refined graph (Algorithm 5):          */
+/* k-CNA by search on the refined graph (Algorithm 5):                    */
 /* C(u) <- KANNSearch(G^, u, L, L, u): every point searches for itself,    */
 /* starting at itself, with pool width L.  The row keeps the pool minus u */
 /* itself, in pool order, padded with -1 to L entries.                     */
@@ -528,7 +529,7 @@ int or_acquire(const float *D, int64_t n, int d, int metric, const int32_t *nbr,
 /*   repeat I times:                                                       */
 /*     N <- Prune(C, R, alpha);  N <- Prune(N u reverse(N), R, alpha);     */
 /*     connect(N, ep);  C(u) <- KANNSearch(N, u, L, L, u)                  */
-/*   final Refine (Algorithm 2): the same two prunes with        */
+/*   final Refine (Algorithm 2): the same two prunes with                 */
 /*   alpha = alpha_final (60 degrees: RNG pruning), then connect unless    */
 /*   connect_final is 0 (NSWG layers, Section 5.3).                        */
 /* ep is the medoid (or_medoid).  Outputs nbr [n][R], deg [n]; returns ep, */
@@ -601,7 +602,7 @@ int64_t or_build_rng(const float *D, int64_t n, int d, int metric, int K, int L,
 }
 
 /* ---------------------------------------------------------------------- */
-/* HNSW level draw (Algorithm 4, Algorithm 7): an           */
+/* HNSW level draw (Algorithm 4, Algorithm 7): an                         */
 /* exponentially decaying level l = floor(-ln(U) / ln(M)).  The uniform   */
 /* U of point i comes from SplitMix64 (Steele, Lea and Flood, OOPSLA      */
 /* 2014) seeded with seed XOR i: U = ((z >> 11) + 1) * 2^-53, in (0, 1].   */
