@@ -159,13 +159,26 @@ def oracle_build_rate(D, w, ns: int, threads: int | None = None):
 
 
 def cpu_model():
+    """CPU model from /proc/cpuinfo; on Arm (no model name) the implementer and
+    part codes, e.g. 0x41 / 0xd4f for an Arm Neoverse V2 (NVIDIA Grace)."""
+    import platform
+    impl = part = None
     try:
         for line in open("/proc/cpuinfo"):
-            if line.lower().startswith(("model name", "cpu model")):
+            key = line.lower()
+            if key.startswith(("model name", "cpu model")):
                 return line.split(":", 1)[1].strip()
-    except Exception:
+            if key.startswith("cpu implementer") and impl is None:
+                impl = line.split(":", 1)[1].strip()
+            if key.startswith("cpu part") and part is None:
+                part = line.split(":", 1)[1].strip()
+    except OSError:
         pass
-    return "unknown"
+    if impl or part:
+        names = {("0x41", "0xd4f"): "Arm Neoverse V2"}
+        return f"{platform.machine()} implementer {impl} part {part}" + (
+            f" ({names[(impl, part)]})" if (impl, part) in names else "")
+    return platform.machine() or "unknown"
 
 
 # ------------------------------------------------------------------ arms
