@@ -54,7 +54,8 @@ typedef enum {
     PG_ERR_CAPACITY = 5,    /* input larger than a documented capacity    */
     PG_ERR_BUDGET = 6,      /* scratch would exceed the context HBM budget */
     PG_ERR_INTERNAL = 7,    /* invariant broken inside the library         */
-    PG_ERR_DEVICE_CHECK = 8 /* a kernel met an invalid id (skipped)        */
+    PG_ERR_DEVICE_CHECK = 8, /* a kernel met an invalid id (skipped)       */
+    PG_ERR_IO = 9            /* a file could not be opened, read or written */
 } pg_status;
 
 typedef enum { PG_METRIC_L2SQ = 0, PG_METRIC_COSINE = 1, PG_METRIC_IP = 2 } pg_metric;
@@ -331,6 +332,50 @@ pg_status pg_index_reserve(pg_ctx *ctx, pg_index *index, int64_t capacity);
  * Synchronous. */
 pg_status pg_index_insert(pg_ctx *ctx, pg_index *index, const float *X, int64_t m, int32_t ef,
                           int32_t upper_beam);
+
+/* Build parameters and dimension of an index (host outs, each nullable). */
+pg_status pg_index_params(const pg_index *index, pg_build_params *params, int32_t *d);
+
+/* ---------------------------------------------------------- index files */
+
+/* Write `index` to the file `path`: its build parameters, entry points,
+ * every layer (members, degrees, neighbour lists) and its n points, then a
+ * checksum.  The layout, little-endian, version 1:
+ *   "PGINDEX\0", u32 version, u32 byte-order mark 0x01020304,
+ *   i64 n, i32 d, i32 metric, i64 ep_top, i64 ep_base,
+ *   i32 metric, precision, K, L, R, M; f64 alpha_deg, alpha_final_deg;
+ *   i32 iters, connect_final, route_layers, 0; u64 seed;
+ *   i32 layers, i32 0; per layer i64 count, i32 R, i32 has_gid;
+ *   per layer: gid i32[count] (upper layers only), deg i32[count],
+ *   nbr i32[count][R] (point ids);
+ *   points f32[n][d];
+ *   u64 checksum: FNV-1a (offset basis 0xcbf29ce484222325, prime
+ *   0x100000001b3) over the preceding bytes read as little-endian 64-bit
+ *   words, the last partial word zero-padded.
+ * The file is written under a temporary name and renamed when complete,
+ * so `path` never holds a partial index.  Synchronous (device -> host
+ * copies on the context stream).  Errors: PG_ERR_INVALID_ARG (null
+ * argument), PG_ERR_CUDA, PG_ERR_IO (the message names the failing step). */
+pg_status pg_index_save(pg_ctx *ctx, const pg_index *index, const char *path);
+
+/* Read an index written by pg_index_save.  The whole file is checked on
+ * the host before the index is returned: magic, version, byte order,
+ * parameter ranges (those of pg_build_rng), layer 0 holding every point,
+ * upper layers holding strictly ascending ids, each a subset of the layer
+ * below, degrees within [0, R], every listed neighbour a member of its
+ * layer, the entry points (ep_top in the top layer), no trailing bytes and
+ * the checksum.  The index owns a private DEVICE copy of its points
+ * (pg_index_reserve grows it for insertion).  Synchronous.  Errors:
+ * PG_ERR_IO (open / short read), PG_ERR_INVALID_ARG (a failed check; the
+ * message says which), PG_ERR_CUDA (allocation or copy); *out is NULL on
+ * error. */
+pg_status pg_index_load(pg_ctx *ctx, const char *path, pg_index **out);
+
+/* The checks of pg_index_load without a context or a device: n, d and the
+ * number of layers of a valid file go to the host outs (each nullable);
+ * on error a one-line reason is written to msg (msg_len bytes, nullable). */
+pg_status pg_index_file_check(const char *path, int64_t *n, int32_t *d, int32_t *n_layers,
+                              char *msg, size_t msg_len);
 
 /* -------------------------------------------------------------- serving */
 

@@ -31,7 +31,7 @@ METRIC = {"l2": 0, "cosine": 1, "ip": 2}
 UPPER_BEAM = 16
 PRECISION = {"fp32": 0, "bf16": 1}
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "TIMEOUT", 5: "CAPACITY", 6: "BUDGET",
-          7: "INTERNAL", 8: "DEVICE_CHECK"}
+          7: "INTERNAL", 8: "DEVICE_CHECK", 9: "IO"}
 
 P = C.c_void_p
 i32, i64, dbl, u64 = C.c_int32, C.c_int64, C.c_double, C.c_uint64
@@ -94,6 +94,10 @@ _sig("pg_serve_stats", C.c_int, [P, P])
 _sig("pg_serve_stop", C.c_int, [P])
 _sig("pg_serve_set_queue_limit", C.c_int, [P, i64])
 _sig("pg_selftest_wait_timeout", C.c_int, [P, dbl])
+_sig("pg_index_params", C.c_int, [P, P, P])
+_sig("pg_index_save", C.c_int, [P, P, C.c_char_p])
+_sig("pg_index_load", C.c_int, [P, C.c_char_p, P])
+_sig("pg_index_file_check", C.c_int, [C.c_char_p, P, P, P, C.c_char_p, C.c_size_t])
 
 EXPORTS = ["pg_default_params", "pg_ctx_create", "pg_ctx_destroy", "pg_last_error", "pg_ctx_sync",
            "pg_ctx_launches", "pg_build_knn", "pg_knn_query", "pg_prune", "pg_reverse_union",
@@ -104,7 +108,8 @@ EXPORTS = ["pg_default_params", "pg_ctx_create", "pg_ctx_destroy", "pg_last_erro
            "pg_ctx_kernel_work", "pg_prune_noalloc", "pg_index_reserve", "pg_index_insert",
            "pg_serve_start", "pg_serve_submit_query", "pg_serve_submit_insert", "pg_serve_wait",
            "pg_serve_stats", "pg_serve_stop", "pg_serve_set_queue_limit",
-           "pg_selftest_wait_timeout"]
+           "pg_selftest_wait_timeout", "pg_index_params", "pg_index_save", "pg_index_load",
+           "pg_index_file_check"]
 
 
 class PGError(RuntimeError):
@@ -132,6 +137,7 @@ class Context:
         if not torch.cuda.is_available():
             raise RuntimeError("libpg needs a CUDA device")
         self.stream = stream or torch.cuda.current_stream()
+        self.device = torch.device("cuda", torch.cuda.current_device())
         h = C.c_void_p()
         st = _lib.pg_ctx_create(C.c_void_p(self.stream.cuda_stream), hbm_budget_bytes, C.byref(h))
         if st != 0:
@@ -209,6 +215,18 @@ def default_params(**kw) -> BuildParams:
 
 
 # --------------------------------------------------------------- steps
+def index_file_check(path: str) -> dict:
+    """Host-only check of an index file (pg_index_file_check, no GPU needed):
+    {"n", "d", "n_layers"} of a valid file, else PGError with the reason."""
+    n, d, nl = C.c_int64(), C.c_int32(), C.c_int32()
+    msg = C.create_string_buffer(256)
+    st = _lib.pg_index_file_check(os.fsencode(path), C.byref(n), C.byref(d), C.byref(nl), msg,
+                                  len(msg))
+    if st != 0:
+        raise PGError(st, f"pg_index_file_check: {msg.value.decode()}")
+    return dict(n=n.value, d=d.value, n_layers=nl.value)
+
+
 def build_knn(ctx: Context, D: torch.Tensor, K: int, metric="l2", precision="fp32"):
     """Exact K-NN graph: (ids int32 [n][K], dist float32 [n][K])."""
     D = _dev(D, torch.float32, "D")
@@ -331,10 +349,38 @@ def search_graph(ctx: Context, D, nbr, deg, Q, starts, k: int, L: int, metric="l
 
 # --------------------------------------------------------------- index
 class Index:
-    """A built graph index (owned by libpg; D must stay alive)."""
+    """A built graph index (owned by libpg; D must stay alive unless the index
+    holds its own copy of the points: after reserve() or load())."""
 
-    def __init__(self, ctx: Context, handle, D: torch.Tensor, metric: str):
+    def __init__(self, ctx: Context, handle, D: torch.Tensor | None, metric: str,
+                 device: torch.device | None = None):
         self.ctx, self._h, self.D, self.metric = ctx, handle, D, metric
+        self.device = D.device if D is not None else device
+
+    @classmethod
+    def load(cls, ctx: Context, path: str):
+        """Read an index file written by save() (pg_index_load): checked in full on
+        the host, then copied to the context's device, points included."""
+        h = C.c_void_p()
+        ctx._check(_lib.pg_index_load(ctx.handle, os.fsencode(path), C.byref(h)),
+                   "pg_index_load")
+        p, d = BuildParams(), C.c_int32()
+        _lib.pg_index_params(h, C.byref(p), C.byref(d))
+        metric = {v: k for k, v in METRIC.items()}[p.metric]
+        return cls(ctx, h, None, metric, ctx.device)
+
+    def save(self, path: str):
+        """Write the index, its build parameters and its points to `path` (pg_index_save)."""
+        self.ctx._check(_lib.pg_index_save(self.ctx.handle, self._h, os.fsencode(path)),
+                        "pg_index_save")
+
+    def params(self):
+        """Build parameters (a BuildParams structure) and dimension of the index."""
+        p, d = BuildParams(), C.c_int32()
+        st = _lib.pg_index_params(self._h, C.byref(p), C.byref(d))
+        if st != 0:
+            raise PGError(st, "pg_index_params")
+        return p, d.value
 
     @classmethod
     def build_rng(cls, ctx: Context, D: torch.Tensor, **params):
@@ -366,7 +412,7 @@ class Index:
         if st != 0:
             raise PGError(st, "pg_index_layer")
         m, R = cnt.value, R.value
-        dev = self.D.device
+        dev = self.device
         gid = torch.empty(m, dtype=torch.int32, device=dev)
         nbr = torch.empty((m, R), dtype=torch.int32, device=dev)
         deg = torch.empty(m, dtype=torch.int32, device=dev)

@@ -39,38 +39,6 @@ pg_status pg_search_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d, 
                              const int32_t *starts, int32_t k, int32_t L, int self,
                              int32_t *out_i, float *out_s, const uint8_t *D8 = nullptr);
 
-struct pg_layer {
-    int64_t count = 0;
-    int64_t cap = 0;  // rows allocated
-    int R = 0;
-    int32_t *gid = nullptr;   // [count] ascending point ids (null: identity)
-    int32_t *nbr = nullptr;   // [count][R] point ids
-    int32_t *deg = nullptr;   // [count]
-    int32_t *rows = nullptr;  // [n] point id -> row, -1 if absent (null: identity)
-};
-
-struct pg_index {
-    int64_t n = 0;
-    int d = 0;
-    pg_metric metric = PG_METRIC_L2SQ;
-    const float *D = nullptr;
-    std::vector<pg_layer> layers;
-    int64_t ep_top = 0, ep_base = 0;
-    double phase[6] = {0, 0, 0, 0, 0, 0};
-    pg_build_params params{};  // of the build: levels, degrees, pruning angle
-    float *owned = nullptr;    // private copy of the points once reserved
-    int64_t capacity = 0;      // rows of `owned`
-    ~pg_index() {
-        cudaFree(owned);
-        for (auto &l : layers) {
-            cudaFree(l.gid);
-            cudaFree(l.nbr);
-            cudaFree(l.deg);
-            cudaFree(l.rows);
-        }
-    }
-};
-
 namespace {
 
 enum { PH_KNN = 0, PH_PRUNE, PH_UNION, PH_CONNECT, PH_ACQUIRE, PH_LAYERS };

@@ -42,6 +42,41 @@ struct pg_ctx {
     double timer_work[16] = {0};  // algorithmic flops or bytes of the timed launches
 };
 
+// ------------------------------------------------------------------ index
+// One layer of an index and the index itself (built in build.cu, written
+// and read by index_io.cu).
+struct pg_layer {
+    int64_t count = 0;
+    int64_t cap = 0;  // rows allocated
+    int R = 0;
+    int32_t *gid = nullptr;   // [count] ascending point ids (null: identity)
+    int32_t *nbr = nullptr;   // [count][R] point ids
+    int32_t *deg = nullptr;   // [count]
+    int32_t *rows = nullptr;  // [n] point id -> row, -1 if absent (null: identity)
+};
+
+struct pg_index {
+    int64_t n = 0;
+    int d = 0;
+    pg_metric metric = PG_METRIC_L2SQ;
+    const float *D = nullptr;
+    std::vector<pg_layer> layers;
+    int64_t ep_top = 0, ep_base = 0;
+    double phase[6] = {0, 0, 0, 0, 0, 0};
+    pg_build_params params{};  // of the build: levels, degrees, pruning angle
+    float *owned = nullptr;    // private copy of the points once reserved
+    int64_t capacity = 0;      // rows of `owned`
+    ~pg_index() {
+        cudaFree(owned);
+        for (auto &l : layers) {
+            cudaFree(l.gid);
+            cudaFree(l.nbr);
+            cudaFree(l.deg);
+            cudaFree(l.rows);
+        }
+    }
+};
+
 // named kernel timers
 enum {
     TM_KNN = 0, TM_PRUNE, TM_UNION, TM_CONNECT, TM_SEARCH, TM_MEDOID, TM_CSELECT, TM_CFAST,
