@@ -29,6 +29,7 @@ sys.path.insert(0, ROOT)
 
 import synthetic  # noqa: E402
 
+SERVE_SLOTS = 4  # concurrent query groups of the serving loop
 WORKLOAD = 2
 
 
@@ -342,50 +343,89 @@ def run_ours(args):
         idx.close()
 
     # ---------------------------------------------------------- serving
-    # A mixed request stream through the serving loop on the index just
-    # measured: 300 query requests of 1-128 queries (k = 10, beam 48,
-    # upper_beam 16) with two insertion batches of 1% of n each after
-    # requests 100 and 200, all queued at once (merged launches), then
-    # single-query requests one at a time for the request latency.
+    # The serving loop on the index just measured (groups of up to 1,024
+    # queries on four workers, host buffers), request sizes drawn from
+    # {1, 8, 32, 128, 1024} queries (k = 10, beam 48, upper_beam 16), two
+    # insertion batches of 1% of n after requests 100 and 200 of 300:
+    #   saturated: all 300 requests queued at once, with four workers and
+    #   with one (same mix), for requests/s and queries/s;
+    #   poisson: the same mix arriving as a Poisson process at 70% of the
+    #   four-worker saturated request rate, for the latency of each request
+    #   from submission to completion (p50 / p99, host clock);
+    # then 200 single-query requests one at a time.
     serve = {}
     if not args.no_serve:
         ins = max(100, n // 100)
-        X = synthetic.inserts(WORKLOAD, 2 * ins)
+        X = synthetic.inserts(WORKLOAD, 6 * ins)
         Qh = Q if isinstance(Q, np.ndarray) else np.asarray(Q)
         idx = pg.Index.build_rng(ctx, Dd, **params)
-        idx.reserve(n + 2 * ins)
-        srv = pg.Server(idx, max_batch=1024)
+        idx.reserve(n + 6 * ins)
         rs = np.random.default_rng(7)
-        sizes = rs.choice([1, 8, 32, 128], size=300)
+        sizes = rs.choice([1, 8, 32, 128, 1024], size=300)
+        cursor = {"q": 0, "x": 0}
+
+        def run_stream(srv, gaps=None):
+            tickets, queries, nqs = [], [], 0
+            t0 = time.perf_counter()
+            for r, sz in enumerate(sizes):
+                if gaps is not None:
+                    due = t0 + gaps[r]
+                    while True:
+                        left = due - time.perf_counter()
+                        if left <= 0:
+                            break
+                        time.sleep(left if left > 1e-3 else 0)
+                if r in (100, 200):
+                    j = cursor["x"]
+                    cursor["x"] += 1
+                    tickets.append(srv.submit_insert(X[j * ins:(j + 1) * ins], 64, 16))
+                rows = (cursor["q"] + np.arange(int(sz))) % nq
+                cursor["q"] += int(sz)
+                nqs += int(sz)
+                t, _, _ = srv.submit_query(Qh[rows], w["k"], 48, 16)
+                tickets.append(t)
+                queries.append(t)
+            assert srv.wait_all(tickets, 600.0)
+            secs = time.perf_counter() - t0
+            lat = [srv.latency(t) * 1e3 for t in queries]
+            return secs, nqs, lat
+
         barrier()
-        t0 = time.perf_counter()
-        last, at, nqs = 0, 0, 0
-        for r, sz in enumerate(sizes):
-            if r in (100, 200):
-                j = 0 if r == 100 else 1
-                last = srv.submit_insert(X[j * ins:(j + 1) * ins], 64, 16)
-            rows = [(at + i) % nq for i in range(int(sz))]
-            at += int(sz)
-            nqs += int(sz)
-            last, _, _ = srv.submit_query(Qh[rows], w["k"], 48, 16)
-        srv.wait(last, 600.0)
-        t_mix = time.perf_counter() - t0
+        sat = {}
+        for slots in (SERVE_SLOTS, 1):
+            srv = pg.Server(idx, max_batch=1024, slots=slots)
+            secs, nqs, _ = run_stream(srv)
+            st = srv.stats()
+            srv.stop()
+            sat[slots] = {"seconds": secs, "requests_per_s": len(sizes) / secs,
+                          "queries_per_s": nqs / secs, "groups": int(st["batches"]),
+                          "max_in_flight": int(st["max_in_flight"])}
+        rate = 0.7 * sat[SERVE_SLOTS]["requests_per_s"]
+        gaps = np.cumsum(rs.exponential(1.0 / rate, size=len(sizes)))
+        srv = pg.Server(idx, max_batch=1024, slots=SERVE_SLOTS)
+        secs, nqs, lat = run_stream(srv, gaps)
         st = srv.stats()
-        lat = []
+        single = []
         for i in range(200):
             t1 = time.perf_counter()
             tk, _, _ = srv.submit_query(Qh[i:i + 1], w["k"], 48, 16)
             srv.wait(tk, 60.0)
-            lat.append((time.perf_counter() - t1) * 1e3)
+            single.append((time.perf_counter() - t1) * 1e3)
         srv.stop()
         idx.close()
-        serve = {"requests": int(st["requests"]), "launch_batches": int(st["batches"]),
-                 "queries": nqs, "inserted": int(st["inserted"]), "seconds": t_mix,
-                 "requests_per_s": len(sizes) / t_mix, "queries_per_s": nqs / t_mix,
-                 "single_query_p50_ms": float(np.percentile(lat, 50)),
-                 "single_query_p99_ms": float(np.percentile(lat, 99)),
-                 "stream": "300 query requests of 1/8/32/128 queries (k=10, beam 48) with two "
-                           f"insertion batches of {ins} points, host buffers, queued at once"}
+        serve = {"slots": SERVE_SLOTS, "requests": len(sizes), "queries": int(sizes.sum()),
+                 "inserted_per_stream": 2 * ins,
+                 "saturated": sat[SERVE_SLOTS], "saturated_one_worker": sat[1],
+                 "poisson": {"rate_requests_per_s": rate, "seconds": secs,
+                             "queries_per_s": nqs / secs, "groups": int(st["batches"]),
+                             "max_in_flight": int(st["max_in_flight"]),
+                             "admission_waits": int(st["admission_waits"]),
+                             "p50_ms": float(np.percentile(lat, 50)),
+                             "p99_ms": float(np.percentile(lat, 99))},
+                 "single_query_p50_ms": float(np.percentile(single, 50)),
+                 "single_query_p99_ms": float(np.percentile(single, 99)),
+                 "stream": "300 query requests of 1/8/32/128/1024 queries (k=10, beam 48) with "
+                           f"two insertion batches of {ins} points, host buffers"}
 
     # ------------------------------------------- screened kNN, real-valued rows
     # The 1M x 960 real-valued workload's recipe (512 centres U[0,1]^960,

@@ -379,19 +379,28 @@ pg_status pg_index_file_check(const char *path, int64_t *n, int32_t *d, int32_t 
 
 /* -------------------------------------------------------------- serving */
 
-/* A serving loop over a growable index: one host worker thread drains a
- * FIFO of query batches and insertion batches on the context's stream.
- * While the server runs, ctx and index belong to it (the caller issues no
- * other call on them until pg_serve_stop).  Requests complete in
- * submission order.  Consecutive query requests with equal
- * (k, beam, upper_beam) are merged into one search launch of at most
- * max_batch queries; an insertion (pg_index_insert) runs alone, so a query
- * sees exactly the points inserted before it was submitted.  Host buffers
- * of a request must stay valid until it completes. */
+/* A serving loop over a growable index: a dispatcher thread takes query
+ * and insertion requests in submission order and hands query groups to
+ * `slots` worker threads, each with its own context on its own CUDA stream,
+ * so that groups of different requests run concurrently on the device.
+ * Consecutive query requests with equal (k, beam, upper_beam) are merged
+ * into one group of at most max_batch queries.  A group is admitted when a
+ * worker is free and the device scratch of the groups in flight plus its
+ * own (queries, results and search state: rows x (4 d + 8 k + 12) bytes)
+ * fits the HBM budget of ctx (0 = no limit); a group larger than the budget
+ * fails with PG_ERR_BUDGET.  An insertion (pg_index_insert on ctx) waits for
+ * every group dispatched before it and runs alone, so a query sees exactly
+ * the points inserted before it was submitted.  Tickets complete out of
+ * order.  While the server runs, ctx and index belong to it (the caller
+ * issues no other call on them until pg_serve_stop).  Host buffers of a
+ * request must stay valid until it completes. */
 typedef struct pg_server pg_server;
 
-/* Start the worker (1 <= max_batch <= 65536). */
-pg_status pg_serve_start(pg_ctx *ctx, pg_index *index, int32_t max_batch, pg_server **out);
+/* Start the dispatcher and the workers on ctx's device (1 <= max_batch <=
+ * 65536, 1 <= slots <= 16; the workers' streams and contexts are created
+ * here and freed by pg_serve_stop). */
+pg_status pg_serve_start(pg_ctx *ctx, pg_index *index, int32_t max_batch, int32_t slots,
+                         pg_server **out);
 
 /* Enqueue nq HOST query rows Q [nq][d]; results go to HOST out_ids [nq][k]
  * and out_dist [nq][k] (pg_search semantics).  *ticket identifies it.  A
@@ -406,19 +415,50 @@ pg_status pg_serve_submit_insert(pg_server *server, const float *X, int64_t m, i
                                  int32_t upper_beam, int64_t *ticket);
 
 /* Wait up to timeout_s seconds (0: poll) for `ticket`; *done = 1 once it has
- * completed, and the return value is then that request's status. */
+ * completed, and the return value is then that request's status.
+ * PG_ERR_INVALID_ARG for a ticket that was never issued. */
 pg_status pg_serve_wait(pg_server *server, int64_t ticket, double timeout_s, int32_t *done);
+
+/* Seconds from the submission of `ticket` to its completion (host clock),
+ * for a completed ticket among the last 65,536 issued; else
+ * PG_ERR_INVALID_ARG. */
+pg_status pg_serve_latency(pg_server *server, int64_t ticket, double *seconds);
 
 /* Admission control: a submit is refused with PG_ERR_CAPACITY (nothing
  * enqueued, no ticket) while `limit` requests are pending (queued or
  * running); 0 = no limit (the default). */
 pg_status pg_serve_set_queue_limit(pg_server *server, int64_t limit);
 
-/* host_stats4 = {launch batches, requests, queries, inserted points} so far. */
-pg_status pg_serve_stats(pg_server *server, int64_t *host_stats4);
+/* Admission budget: bytes of device scratch the groups in flight may hold
+ * together (0 = no limit; the default is ctx's HBM budget).  A group larger
+ * than the budget fails with PG_ERR_BUDGET when it is dispatched. */
+pg_status pg_serve_set_budget(pg_server *server, int64_t bytes);
 
-/* Finish every queued request, join the worker and free the server. */
+/* The first `count` (<= 6) of {groups run (query groups and insertions),
+ * requests completed, queries, inserted points, most groups in flight at
+ * once, dispatches that waited for a worker, for memory or for the groups
+ * before an insertion} go to host_stats. */
+pg_status pg_serve_stats(pg_server *server, int64_t *host_stats, int32_t count);
+
+/* Finish every queued request, join the threads and free the server. */
 pg_status pg_serve_stop(pg_server *server);
+
+/* The scheduler of the serving loop with simulated work, host only (no
+ * context, no device): `count` requests submitted at once, request i a
+ * query of rows[i] queries with merge key shape[i] (kind[i] = 0) or an
+ * insertion of rows[i] points (kind[i] = 1).  Running a group sleeps
+ * work_us x (1 + rows / 64) microseconds; its scratch is rows x
+ * bytes_per_row against budget_bytes.  Per request (caller arrays of
+ * `count`, left untouched for requests refused with PG_ERR_BUDGET):
+ * start_seq / end_seq, the positions of the start and the end of its group
+ * in one sequence of events shared by all threads; slot_of, the worker
+ * that ran it (-1: insertion); group_of, its group.  host_stats6 as
+ * pg_serve_stats (nullable).  Returns once every request has completed. */
+pg_status pg_serve_simulate(int32_t slots, int32_t max_batch, int64_t budget_bytes,
+                            int32_t count, const int32_t *kind, const int32_t *rows,
+                            const int32_t *shape, int32_t work_us, int64_t bytes_per_row,
+                            int64_t *start_seq, int64_t *end_seq, int32_t *slot_of,
+                            int64_t *group_of, int64_t *host_stats6);
 
 /* ------------------------------------------------------------ self test */
 

@@ -86,18 +86,21 @@ _sig("pg_ctx_kernel_work", C.c_int, [P, C.c_char_p, P])
 _sig("pg_prune_noalloc", C.c_int, [P, P, i64, i32, C.c_int, P, P, i32, dbl, P, P])
 _sig("pg_index_reserve", C.c_int, [P, P, i64])
 _sig("pg_index_insert", C.c_int, [P, P, P, i64, i32, i32])
-_sig("pg_serve_start", C.c_int, [P, P, i32, P])
+_sig("pg_serve_start", C.c_int, [P, P, i32, i32, P])
 _sig("pg_serve_submit_query", C.c_int, [P, P, i64, i32, i32, i32, P, P, P])
 _sig("pg_serve_submit_insert", C.c_int, [P, P, i64, i32, i32, P])
 _sig("pg_serve_wait", C.c_int, [P, i64, dbl, P])
-_sig("pg_serve_stats", C.c_int, [P, P])
+_sig("pg_serve_stats", C.c_int, [P, P, i32])
 _sig("pg_serve_stop", C.c_int, [P])
 _sig("pg_serve_set_queue_limit", C.c_int, [P, i64])
+_sig("pg_serve_set_budget", C.c_int, [P, i64])
+_sig("pg_serve_latency", C.c_int, [P, i64, P])
 _sig("pg_selftest_wait_timeout", C.c_int, [P, dbl])
 _sig("pg_index_params", C.c_int, [P, P, P])
 _sig("pg_index_save", C.c_int, [P, P, C.c_char_p])
 _sig("pg_index_load", C.c_int, [P, C.c_char_p, P])
 _sig("pg_index_file_check", C.c_int, [C.c_char_p, P, P, P, C.c_char_p, C.c_size_t])
+_sig("pg_serve_simulate", C.c_int, [i32, i32, i64, i32, P, P, P, i32, i64, P, P, P, P, P])
 
 EXPORTS = ["pg_default_params", "pg_ctx_create", "pg_ctx_destroy", "pg_last_error", "pg_ctx_sync",
            "pg_ctx_launches", "pg_build_knn", "pg_knn_query", "pg_prune", "pg_reverse_union",
@@ -109,7 +112,8 @@ EXPORTS = ["pg_default_params", "pg_ctx_create", "pg_ctx_destroy", "pg_last_erro
            "pg_serve_start", "pg_serve_submit_query", "pg_serve_submit_insert", "pg_serve_wait",
            "pg_serve_stats", "pg_serve_stop", "pg_serve_set_queue_limit",
            "pg_selftest_wait_timeout", "pg_index_params", "pg_index_save", "pg_index_load",
-           "pg_index_file_check"]
+           "pg_index_file_check", "pg_serve_simulate",
+           "pg_serve_set_budget", "pg_serve_latency"]
 
 
 class PGError(RuntimeError):
@@ -484,14 +488,44 @@ class Index:
 
 
 # ------------------------------------------------------------- serving
+def serve_simulate(kind, rows, shape, slots: int = 4, max_batch: int = 1024,
+                   budget_bytes: int = 0, work_us: int = 200, bytes_per_row: int = 0):
+    """The serving scheduler with simulated work on the host (pg_serve_simulate):
+    per-request event positions, worker and group, and the stats."""
+    kind = np.ascontiguousarray(kind, np.int32)
+    rows = np.ascontiguousarray(rows, np.int32)
+    shape = np.ascontiguousarray(shape, np.int32)
+    n = len(kind)
+    start = np.full(n, -1, np.int64)
+    end = np.full(n, -1, np.int64)
+    slot = np.full(n, -2, np.int32)
+    group = np.full(n, -1, np.int64)
+    st = (C.c_int64 * len(SERVE_STATS))()
+
+    def p(a):
+        return a.ctypes.data_as(C.c_void_p)
+
+    rc = _lib.pg_serve_simulate(slots, max_batch, budget_bytes, n, p(kind), p(rows), p(shape),
+                                work_us, bytes_per_row, p(start), p(end), p(slot), p(group), st)
+    if rc != 0:
+        raise PGError(rc, "pg_serve_simulate")
+    return dict(start=start, end=end, slot=slot, group=group,
+                stats=dict(zip(SERVE_STATS, list(st))))
+
+
+SERVE_STATS = ["batches", "requests", "queries", "inserted", "max_in_flight",
+               "admission_waits"]
+
+
 class Server:
     """Serving loop over a growable index (pg_serve_*): query and insertion
-    requests with host buffers, completed in submission order."""
+    requests with host buffers; query groups run on `slots` concurrent
+    workers, insertions alone; tickets complete out of order."""
 
-    def __init__(self, index: Index, max_batch: int = 1024):
+    def __init__(self, index: Index, max_batch: int = 1024, slots: int = 4):
         self.index, self.ctx = index, index.ctx
         self._h = C.c_void_p()
-        self.ctx._check(_lib.pg_serve_start(self.ctx.handle, index._h, max_batch,
+        self.ctx._check(_lib.pg_serve_start(self.ctx.handle, index._h, max_batch, slots,
                                             C.byref(self._h)), "pg_serve_start")
         self._keep = {}
 
@@ -536,10 +570,24 @@ class Server:
         self._chk(_lib.pg_serve_set_queue_limit(self._h, int(limit)),
                         "pg_serve_set_queue_limit")
 
+    def latency(self, ticket: int) -> float:
+        """Seconds from submission to completion of a completed ticket."""
+        v = C.c_double()
+        self._chk(_lib.pg_serve_latency(self._h, ticket, C.byref(v)), "pg_serve_latency")
+        return v.value
+
+    def set_budget(self, nbytes: int):
+        """Device scratch the groups in flight may hold together (0: no limit)."""
+        self._chk(_lib.pg_serve_set_budget(self._h, int(nbytes)), "pg_serve_set_budget")
+
     def stats(self):
-        a = (C.c_int64 * 4)()
-        _lib.pg_serve_stats(self._h, a)
-        return dict(zip(["batches", "requests", "queries", "inserted"], list(a)))
+        a = (C.c_int64 * len(SERVE_STATS))()
+        _lib.pg_serve_stats(self._h, a, len(SERVE_STATS))
+        return dict(zip(SERVE_STATS, list(a)))
+
+    def wait_all(self, tickets, timeout_s: float = 60.0) -> bool:
+        """Wait for every ticket (they complete out of order)."""
+        return all(self.wait(t, timeout_s) for t in tickets)
 
     def stop(self):
         if getattr(self, "_h", None):

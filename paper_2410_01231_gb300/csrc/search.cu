@@ -21,6 +21,7 @@
 // node that was evaluated and left the pool can never re-enter it; the
 // lossy table therefore changes the work done, never the result.
 #include <climits>
+#include <mutex>
 
 #include "pg_internal.cuh"
 
@@ -314,6 +315,8 @@ __global__ void __launch_bounds__(SW * 32, 8) k_search(SearchParams P) {
     }
 }
 
+std::mutex search_launch_mu;
+
 }  // namespace
 
 pg_status pg_search_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
@@ -355,6 +358,10 @@ pg_status pg_search_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d, 
     size_t smem = search_warp_smem(L, hb, d) * SW;
     if (smem > 227 * 1024)
         return pg_fail(ctx, PG_ERR_CAPACITY, "search: pool/table do not fit shared memory");
+    // the shared-memory attribute is per kernel, not per launch: searches
+    // of other contexts on other threads (the serving workers) may set a
+    // different size, so setting it and launching are one critical section
+    std::lock_guard<std::mutex> lk(search_launch_mu);
     PG_TRY_CUDA(ctx, cudaFuncSetAttribute(k_search, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)smem));
     int bps = 0;

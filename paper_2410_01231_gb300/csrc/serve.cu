@@ -1,22 +1,36 @@
 // serve.cu -- serving loop over a growable index: a request queue of query
-// batches and insertion batches drained by one host worker thread that owns
-// the context and the index while the server runs.
+// batches and insertion batches, a dispatcher thread and `slots` worker
+// threads, each worker with its own context (own CUDA stream, scratch and
+// error word), so that query launches of different requests overlap on the
+// device.
 //
-// Requests run in submission order, so completion is monotone: ticket t is
-// done once the worker has finished every request up to t.  Consecutive
-// query requests with the same (k, beam, upper_beam) are merged into one
-// search launch of up to max_batch queries (continuous batching); an
-// insertion batch (Algorithm 4 on a snapshot, pg_index_insert) runs alone,
-// after every earlier query and before every later one, so a query always
-// sees exactly the points inserted before it was submitted.
+// Dispatch is in submission order.  Consecutive query requests with the
+// same (k, beam, upper_beam) are merged into one group of at most max_batch
+// queries (continuous batching); a group is admitted to a worker once a
+// worker is free and the device scratch of the groups in flight plus its
+// own fits the HBM budget of the server's context (a group that could never
+// fit fails with PG_ERR_BUDGET).  An insertion batch (Algorithm 4 on a
+// snapshot, pg_index_insert) waits until every group dispatched before it
+// has finished, then runs alone on the server's context, and nothing after
+// it is dispatched before it finishes: a query sees exactly the points
+// inserted before it was submitted, however the groups overlap.  Tickets
+// complete out of order; pg_serve_wait waits for one ticket.
 //
-// While the server runs, the context belongs to the worker thread: the
-// submit functions, called from other threads, only validate and enqueue;
-// a refused submission returns its status without touching the context's
-// error message (which the worker may be writing).
+// The scheduler below is host-only and takes its work as callbacks, so the
+// same code runs with simulated work on a machine without a GPU
+// (pg_serve_simulate).  While the server runs, the context and the index
+// belong to it: the submit functions, called from other threads, only
+// validate and enqueue; a refused submission returns its status without
+// touching the context's error message (which the dispatcher may be
+// writing).
+#include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <condition_variable>
 #include <deque>
+#include <functional>
 #include <mutex>
+#include <set>
 #include <thread>
 #include <unordered_map>
 
@@ -32,6 +46,230 @@ struct Req {
     int k = 0, beam = 0, upper_beam = 1, ef = 0;
     int32_t *out_ids = nullptr;
     float *out_dist = nullptr;
+    int64_t shape = 0;  // simulated requests: merge key
+    std::chrono::steady_clock::time_point submitted;
+};
+
+struct Group {
+    std::vector<Req> reqs;
+    int64_t rows = 0;
+    size_t bytes = 0;
+};
+
+enum { SLOT_IDLE = 0, SLOT_ASSIGNED, SLOT_RUNNING };
+
+struct Sched {
+    // configuration and work
+    int nslots = 1;
+    int64_t max_batch = 1024;
+    size_t budget = 0;  // bytes of device scratch in flight at most (0: no limit)
+    std::function<bool(const Req &, const Req &)> mergeable;
+    std::function<size_t(const Group &)> group_bytes;
+    std::function<pg_status(int, const Group &)> run_group;
+    std::function<pg_status(const Req &)> run_insert;
+
+    // state, under mu
+    std::mutex mu;
+    std::condition_variable cv_work, cv_free, cv_slot, cv_done;
+    std::deque<Req> queue;
+    bool stopping = false, slots_exit = false;
+    int64_t next_ticket = 1, completed = 0, queue_limit = 0;
+    int64_t done_below = 1;          // every ticket below it is done
+    std::set<int64_t> done_above;    // done tickets at or above done_below
+    std::unordered_map<int64_t, int> failed;  // ticket -> status
+    std::vector<int> slot_state;
+    std::vector<Group> slot_job;
+    int busy = 0;
+    size_t bytes_in_flight = 0;
+    int64_t n_groups = 0, n_requests = 0, n_queries = 0, n_inserted = 0, max_in_flight = 0,
+            admission_waits = 0;
+    // seconds from submission to completion of the last kLatRing tickets
+    static constexpr int64_t kLatRing = int64_t(1) << 16;
+    std::vector<double> latency = std::vector<double>((size_t)kLatRing, 0.0);
+    std::thread dispatcher;
+    std::vector<std::thread> workers;
+    std::function<void()> thread_init;  // run first on every thread (device binding)
+
+    bool is_done(int64_t t) const { return t < done_below || done_above.count(t) != 0; }
+
+    // with mu held
+    void complete(const std::vector<Req> &reqs, pg_status st) {
+        const auto now = std::chrono::steady_clock::now();
+        for (const Req &r : reqs) {
+            latency[(size_t)(r.ticket % kLatRing)] =
+                std::chrono::duration<double>(now - r.submitted).count();
+            if (st != PG_OK) failed[r.ticket] = (int)st;
+            done_above.insert(r.ticket);
+            ++completed;
+            ++n_requests;
+            (r.kind == 0 ? n_queries : n_inserted) += r.rows;
+        }
+        ++n_groups;
+        while (!done_above.empty() && *done_above.begin() == done_below) {
+            done_above.erase(done_above.begin());
+            ++done_below;
+        }
+        cv_done.notify_all();
+    }
+
+    void worker_main(int s) {
+        if (thread_init) thread_init();
+        for (;;) {
+            Group g;
+            {
+                std::unique_lock<std::mutex> lk(mu);
+                cv_slot.wait(lk, [&] {
+                    return slots_exit || slot_state[(size_t)s] == SLOT_ASSIGNED;
+                });
+                if (slot_state[(size_t)s] != SLOT_ASSIGNED) return;  // exit with nothing assigned
+                slot_state[(size_t)s] = SLOT_RUNNING;
+                g = std::move(slot_job[(size_t)s]);
+            }
+            const pg_status st = run_group(s, g);
+            {
+                std::lock_guard<std::mutex> lk(mu);
+                complete(g.reqs, st);
+                slot_state[(size_t)s] = SLOT_IDLE;
+                --busy;
+                bytes_in_flight -= g.bytes;
+            }
+            cv_free.notify_all();
+        }
+    }
+
+    void dispatcher_main() {
+        if (thread_init) thread_init();
+        for (;;) {
+            Group g;
+            {
+                std::unique_lock<std::mutex> lk(mu);
+                cv_work.wait(lk, [&] { return stopping || !queue.empty(); });
+                if (queue.empty()) break;  // stopping and drained
+                g.reqs.push_back(queue.front());
+                g.rows = queue.front().rows;
+                queue.pop_front();
+                if (g.reqs[0].kind == 0) {
+                    while (!queue.empty() && mergeable(g.reqs[0], queue.front()) &&
+                           g.rows + queue.front().rows <= max_batch) {
+                        g.rows += queue.front().rows;
+                        g.reqs.push_back(queue.front());
+                        queue.pop_front();
+                    }
+                }
+            }
+            if (g.reqs[0].kind == 1) {
+                {
+                    std::unique_lock<std::mutex> lk(mu);
+                    if (busy) ++admission_waits;
+                    cv_free.wait(lk, [&] { return busy == 0; });
+                }
+                const pg_status st = run_insert(g.reqs[0]);
+                std::lock_guard<std::mutex> lk(mu);
+                complete(g.reqs, st);
+                continue;
+            }
+            g.bytes = group_bytes(g);
+            std::unique_lock<std::mutex> lk(mu);
+            if (budget && g.bytes > budget) {
+                complete(g.reqs, PG_ERR_BUDGET);
+                continue;
+            }
+            auto admissible = [&] {
+                return busy < nslots && (!budget || bytes_in_flight + g.bytes <= budget);
+            };
+            if (!admissible()) {
+                ++admission_waits;
+                cv_free.wait(lk, admissible);
+            }
+            int s = 0;
+            while (slot_state[(size_t)s] != SLOT_IDLE) ++s;
+            slot_state[(size_t)s] = SLOT_ASSIGNED;
+            bytes_in_flight += g.bytes;
+            slot_job[(size_t)s] = std::move(g);
+            ++busy;
+            max_in_flight = std::max<int64_t>(max_in_flight, busy);
+            cv_slot.notify_all();
+        }
+        std::unique_lock<std::mutex> lk(mu);
+        cv_free.wait(lk, [&] { return busy == 0; });
+        slots_exit = true;
+        cv_slot.notify_all();
+    }
+
+    // false if a thread could not be started (the others are joined again)
+    bool start() {
+        slot_state.assign((size_t)nslots, SLOT_IDLE);
+        slot_job.resize((size_t)nslots);
+        try {
+            for (int s = 0; s < nslots; ++s) workers.emplace_back(&Sched::worker_main, this, s);
+            dispatcher = std::thread(&Sched::dispatcher_main, this);
+        } catch (const std::exception &) {
+            {
+                std::lock_guard<std::mutex> lk(mu);
+                stopping = slots_exit = true;
+            }
+            cv_slot.notify_all();
+            cv_work.notify_all();
+            for (auto &t : workers)
+                if (t.joinable()) t.join();
+            if (dispatcher.joinable()) dispatcher.join();
+            return false;
+        }
+        return true;
+    }
+
+    void stop() {
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            stopping = true;
+        }
+        cv_work.notify_all();
+        if (dispatcher.joinable()) dispatcher.join();
+        for (auto &t : workers)
+            if (t.joinable()) t.join();
+    }
+
+    pg_status submit(Req r, int64_t *ticket) {
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            if (stopping) return PG_ERR_INVALID_ARG;  // the server is stopping
+            if (queue_limit > 0 && next_ticket - 1 - completed >= queue_limit)
+                return PG_ERR_CAPACITY;  // admission refused: the queue is full
+            r.ticket = next_ticket++;
+            r.submitted = std::chrono::steady_clock::now();
+            queue.push_back(r);
+        }
+        cv_work.notify_one();
+        *ticket = r.ticket;
+        return PG_OK;
+    }
+
+    pg_status wait(int64_t ticket, double timeout_s, int32_t *done) {
+        std::unique_lock<std::mutex> lk(mu);
+        if (ticket < 1 || ticket >= next_ticket) return PG_ERR_INVALID_ARG;
+        auto ready = [&] { return is_done(ticket); };
+        if (timeout_s > 0) cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), ready);
+        *done = ready() ? 1 : 0;
+        if (!*done) return PG_OK;
+        auto it = failed.find(ticket);
+        return it == failed.end() ? PG_OK : (pg_status)it->second;
+    }
+
+    pg_status latency_of(int64_t ticket, double *seconds) {
+        std::lock_guard<std::mutex> lk(mu);
+        if (ticket < 1 || ticket >= next_ticket || ticket <= next_ticket - 1 - kLatRing ||
+            !is_done(ticket))
+            return PG_ERR_INVALID_ARG;
+        *seconds = latency[(size_t)(ticket % kLatRing)];
+        return PG_OK;
+    }
+
+    void stats(int64_t *out, int count) {
+        std::lock_guard<std::mutex> lk(mu);
+        const int64_t v[6] = {n_groups, n_requests, n_queries, n_inserted, max_in_flight,
+                              admission_waits};
+        for (int i = 0; i < count && i < 6; ++i) out[i] = v[i];
+    }
 };
 
 }  // namespace
@@ -41,41 +279,38 @@ struct pg_server {
     pg_index *index = nullptr;
     int device = 0;
     int d = 0;
-    int max_batch = 1024;
-    int64_t queue_limit = 0;  // pending requests admitted at most (0: no limit)
-    std::mutex mu;
-    std::condition_variable cv_work, cv_done;
-    std::deque<Req> queue;
-    bool stopping = false;
-    int64_t next_ticket = 1;
-    int64_t last_done = 0;
-    std::unordered_map<int64_t, int> failed;  // ticket -> status
-    int64_t n_batches = 0, n_requests = 0, n_queries = 0, n_inserted = 0;
-    std::thread worker;
+    std::vector<cudaStream_t> streams;
+    std::vector<pg_ctx *> slot_ctx;
+    Sched sched;
 };
 
 namespace {
 
-pg_status run_queries(pg_server *s, const std::vector<Req> &batch) {
-    pg_ctx *ctx = s->ctx;
-    int64_t total = 0;
-    for (const Req &r : batch) total += r.rows;
-    const int k = batch[0].k, d = s->d;
+size_t query_group_bytes(int d, const Group &g) {
+    // queries, results and the search's own scratch (entry, next entry and
+    // its distance per query)
+    const int64_t k = g.reqs[0].k;
+    return (size_t)g.rows * ((size_t)d * 4 + (size_t)k * 8 + 12);
+}
+
+pg_status run_queries(pg_ctx *ctx, pg_index *index, int d, const Group &g) {
+    const int64_t total = g.rows;
+    const int k = g.reqs[0].k;
     Scratch<float> Q, dist;
     Scratch<int32_t> ids;
     PG_TRY(Q.alloc(ctx, (size_t)(total * d)));
     PG_TRY(ids.alloc(ctx, (size_t)(total * k)));
     PG_TRY(dist.alloc(ctx, (size_t)(total * k)));
     int64_t at = 0;
-    for (const Req &r : batch) {
+    for (const Req &r : g.reqs) {
         PG_TRY_CUDA(ctx, cudaMemcpyAsync(Q.p + at * d, r.host, (size_t)(r.rows * d) * 4,
                                          cudaMemcpyHostToDevice, ctx->stream));
         at += r.rows;
     }
-    PG_TRY(pg_search(ctx, s->index, Q.p, total, k, batch[0].beam, batch[0].upper_beam, 0,
+    PG_TRY(pg_search(ctx, index, Q.p, total, k, g.reqs[0].beam, g.reqs[0].upper_beam, 0,
                      PG_PREC_FP32, ids.p, dist.p));
     at = 0;
-    for (const Req &r : batch) {
+    for (const Req &r : g.reqs) {
         PG_TRY_CUDA(ctx, cudaMemcpyAsync(r.out_ids, ids.p + at * k, (size_t)(r.rows * k) * 4,
                                          cudaMemcpyDeviceToHost, ctx->stream));
         PG_TRY_CUDA(ctx, cudaMemcpyAsync(r.out_dist, dist.p + at * k, (size_t)(r.rows * k) * 4,
@@ -99,70 +334,74 @@ bool same_query_shape(const Req &a, const Req &b) {
            a.upper_beam == b.upper_beam;
 }
 
-void worker_main(pg_server *s) {
-    cudaSetDevice(s->device);
-    for (;;) {
-        std::vector<Req> batch;
-        {
-            std::unique_lock<std::mutex> lk(s->mu);
-            s->cv_work.wait(lk, [s] { return s->stopping || !s->queue.empty(); });
-            if (s->queue.empty()) break;  // stopping and drained
-            batch.push_back(s->queue.front());
-            s->queue.pop_front();
-            if (batch[0].kind == 0) {
-                int64_t total = batch[0].rows;
-                while (!s->queue.empty() && same_query_shape(batch[0], s->queue.front()) &&
-                       total + s->queue.front().rows <= s->max_batch) {
-                    total += s->queue.front().rows;
-                    batch.push_back(s->queue.front());
-                    s->queue.pop_front();
-                }
-            }
-        }
-        const pg_status st = batch[0].kind == 0 ? run_queries(s, batch) : run_insert(s, batch[0]);
-        {
-            std::lock_guard<std::mutex> lk(s->mu);
-            s->last_done = batch.back().ticket;
-            if (st != PG_OK)
-                for (const Req &r : batch) s->failed[r.ticket] = (int)st;
-            s->n_batches += 1;
-            s->n_requests += (int64_t)batch.size();
-            for (const Req &r : batch) (r.kind == 0 ? s->n_queries : s->n_inserted) += r.rows;
-        }
-        s->cv_done.notify_all();
-    }
-}
-
-pg_status submit(pg_server *s, Req r, int64_t *ticket) {
-    {
-        std::lock_guard<std::mutex> lk(s->mu);
-        if (s->stopping) return PG_ERR_INVALID_ARG;  // the server is stopping
-        if (s->queue_limit > 0 && s->next_ticket - 1 - s->last_done >= s->queue_limit)
-            return PG_ERR_CAPACITY;  // admission refused: the queue is full
-        r.ticket = s->next_ticket++;
-        s->queue.push_back(r);
-    }
-    s->cv_work.notify_one();
-    *ticket = r.ticket;
-    return PG_OK;
+void release_slots(pg_server *s) {
+    for (pg_ctx *c : s->slot_ctx) pg_ctx_destroy(c);
+    for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
+    s->slot_ctx.clear();
+    s->streams.clear();
 }
 
 }  // namespace
 
 extern "C" pg_status pg_serve_start(pg_ctx *ctx, pg_index *index, int32_t max_batch,
-                                    pg_server **out) {
+                                    int32_t slots, pg_server **out) {
     if (!ctx) return PG_ERR_INVALID_ARG;
     if (!index || !out) return pg_fail(ctx, PG_ERR_INVALID_ARG, "null pointer");
     if (max_batch < 1 || max_batch > 65536)
         return pg_fail(ctx, PG_ERR_INVALID_ARG, "need 1 <= max_batch <= 65536");
+    if (slots < 1 || slots > 16) return pg_fail(ctx, PG_ERR_INVALID_ARG, "need 1 <= slots <= 16");
     pg_server *s = new (std::nothrow) pg_server();
     if (!s) return pg_fail(ctx, PG_ERR_OOM, "host allocation");
     s->ctx = ctx;
     s->index = index;
     s->device = ctx->device;
     s->d = pg_index_dim(index);
-    s->max_batch = max_batch;
-    s->worker = std::thread(worker_main, s);
+    // one context per worker, each on its own non-blocking stream, created
+    // on the server's device (the caller's current device is restored)
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(s->device);
+    pg_status st = PG_OK;
+    for (int i = 0; i < slots && st == PG_OK; ++i) {
+        cudaStream_t stream = nullptr;
+        cudaError_t e = cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            st = pg_cuda_fail(ctx, e, "pg_serve_start stream");
+            break;
+        }
+        s->streams.push_back(stream);
+        pg_ctx *c = nullptr;
+        st = pg_ctx_create(stream, 0, &c);
+        if (st != PG_OK) {
+            pg_fail(ctx, st, "pg_serve_start: worker context");
+            break;
+        }
+        s->slot_ctx.push_back(c);
+    }
+    cudaSetDevice(prev);
+    if (st != PG_OK) {
+        release_slots(s);
+        delete s;
+        return st;
+    }
+    Sched &q = s->sched;
+    q.nslots = slots;
+    q.max_batch = max_batch;
+    q.budget = ctx->budget;
+    q.mergeable = same_query_shape;
+    const int d = s->d;
+    q.group_bytes = [d](const Group &g) { return query_group_bytes(d, g); };
+    q.run_group = [s](int slot, const Group &g) {
+        return run_queries(s->slot_ctx[(size_t)slot], s->index, s->d, g);
+    };
+    q.run_insert = [s](const Req &r) { return run_insert(s, r); };
+    const int dev = s->device;
+    q.thread_init = [dev] { cudaSetDevice(dev); };
+    if (!q.start()) {
+        release_slots(s);
+        delete s;
+        return pg_fail(ctx, PG_ERR_INTERNAL, "pg_serve_start: cannot start the worker threads");
+    }
     *out = s;
     return PG_OK;
 }
@@ -183,7 +422,7 @@ extern "C" pg_status pg_serve_submit_query(pg_server *s, const float *Q, int64_t
     r.upper_beam = upper_beam;
     r.out_ids = out_ids;
     r.out_dist = out_dist;
-    return submit(s, r, ticket);
+    return s->sched.submit(r, ticket);
 }
 
 extern "C" pg_status pg_serve_submit_insert(pg_server *s, const float *X, int64_t m, int32_t ef,
@@ -198,47 +437,108 @@ extern "C" pg_status pg_serve_submit_insert(pg_server *s, const float *X, int64_
     r.rows = m;
     r.ef = ef;
     r.upper_beam = upper_beam;
-    return submit(s, r, ticket);
+    return s->sched.submit(r, ticket);
 }
 
 extern "C" pg_status pg_serve_wait(pg_server *s, int64_t ticket, double timeout_s,
                                    int32_t *done) {
     if (!s || !done) return PG_ERR_INVALID_ARG;
-    std::unique_lock<std::mutex> lk(s->mu);
-    auto ready = [s, ticket] { return s->last_done >= ticket; };
-    if (timeout_s > 0)
-        s->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), ready);
-    *done = ready() ? 1 : 0;
-    if (!*done) return PG_OK;
-    auto it = s->failed.find(ticket);
-    return it == s->failed.end() ? PG_OK : (pg_status)it->second;
+    return s->sched.wait(ticket, timeout_s, done);
+}
+
+extern "C" pg_status pg_serve_latency(pg_server *s, int64_t ticket, double *seconds) {
+    if (!s || !seconds) return PG_ERR_INVALID_ARG;
+    return s->sched.latency_of(ticket, seconds);
 }
 
 extern "C" pg_status pg_serve_set_queue_limit(pg_server *s, int64_t limit) {
     if (!s || limit < 0) return PG_ERR_INVALID_ARG;
-    std::lock_guard<std::mutex> lk(s->mu);
-    s->queue_limit = limit;
+    std::lock_guard<std::mutex> lk(s->sched.mu);
+    s->sched.queue_limit = limit;
     return PG_OK;
 }
 
-extern "C" pg_status pg_serve_stats(pg_server *s, int64_t *host_stats4) {
-    if (!s || !host_stats4) return PG_ERR_INVALID_ARG;
-    std::lock_guard<std::mutex> lk(s->mu);
-    host_stats4[0] = s->n_batches;
-    host_stats4[1] = s->n_requests;
-    host_stats4[2] = s->n_queries;
-    host_stats4[3] = s->n_inserted;
+extern "C" pg_status pg_serve_set_budget(pg_server *s, int64_t bytes) {
+    if (!s || bytes < 0) return PG_ERR_INVALID_ARG;
+    {
+        std::lock_guard<std::mutex> lk(s->sched.mu);
+        s->sched.budget = (size_t)bytes;
+    }
+    s->sched.cv_free.notify_all();
+    return PG_OK;
+}
+
+extern "C" pg_status pg_serve_stats(pg_server *s, int64_t *host_stats, int32_t count) {
+    if (!s || !host_stats || count < 0) return PG_ERR_INVALID_ARG;
+    s->sched.stats(host_stats, count);
     return PG_OK;
 }
 
 extern "C" pg_status pg_serve_stop(pg_server *s) {
     if (!s) return PG_ERR_INVALID_ARG;
-    {
-        std::lock_guard<std::mutex> lk(s->mu);
-        s->stopping = true;
-    }
-    s->cv_work.notify_all();
-    if (s->worker.joinable()) s->worker.join();
+    s->sched.stop();
+    release_slots(s);
     delete s;
     return PG_OK;
+}
+
+// ------------------------------------------------------------- simulation
+
+extern "C" pg_status pg_serve_simulate(int32_t slots, int32_t max_batch, int64_t budget_bytes,
+                                       int32_t count, const int32_t *kind, const int32_t *rows,
+                                       const int32_t *shape, int32_t work_us,
+                                       int64_t bytes_per_row, int64_t *start_seq,
+                                       int64_t *end_seq, int32_t *slot_of, int64_t *group_of,
+                                       int64_t *host_stats6) {
+    if (slots < 1 || slots > 16 || max_batch < 1 || budget_bytes < 0 || count < 0 ||
+        work_us < 0 || work_us > 100000 || bytes_per_row < 0)
+        return PG_ERR_INVALID_ARG;
+    if (count && (!kind || !rows || !shape || !start_seq || !end_seq || !slot_of || !group_of))
+        return PG_ERR_INVALID_ARG;
+    for (int32_t i = 0; i < count; ++i)
+        if ((kind[i] != 0 && kind[i] != 1) || rows[i] < 1) return PG_ERR_INVALID_ARG;
+    std::atomic<int64_t> seq{0}, group_id{0};
+    Sched q;
+    q.nslots = slots;
+    q.max_batch = max_batch;
+    q.budget = (size_t)budget_bytes;
+    q.mergeable = [](const Req &a, const Req &b) {
+        return a.kind == 0 && b.kind == 0 && a.shape == b.shape;
+    };
+    q.group_bytes = [bytes_per_row](const Group &g) { return (size_t)(g.rows * bytes_per_row); };
+    auto simulate = [&](int s, const std::vector<Req> &reqs, int64_t units) {
+        const int64_t g = group_id++;
+        const int64_t t0 = seq++;
+        std::this_thread::sleep_for(std::chrono::microseconds((int64_t)work_us * (1 + units / 64)));
+        const int64_t t1 = seq++;
+        for (const Req &r : reqs) {
+            const size_t i = (size_t)(r.ticket - 1);
+            start_seq[i] = t0;
+            end_seq[i] = t1;
+            slot_of[i] = s;
+            group_of[i] = g;
+        }
+        return PG_OK;
+    };
+    q.run_group = [&](int s, const Group &g) { return simulate(s, g.reqs, g.rows); };
+    q.run_insert = [&](const Req &r) { return simulate(-1, std::vector<Req>{r}, r.rows); };
+    if (!q.start()) return PG_ERR_INTERNAL;
+    pg_status st = PG_OK;
+    for (int32_t i = 0; i < count && st == PG_OK; ++i) {
+        Req r;
+        r.kind = kind[i];
+        r.rows = rows[i];
+        r.shape = shape[i];
+        int64_t t = 0;
+        st = q.submit(r, &t);
+    }
+    for (int64_t t = 1; t <= count && st == PG_OK; ++t) {
+        int32_t done = 0;
+        const pg_status w = q.wait(t, 60.0, &done);
+        if (!done) st = PG_ERR_TIMEOUT;
+        else if (w != PG_OK && w != PG_ERR_BUDGET) st = w;
+    }
+    q.stop();
+    if (host_stats6) q.stats(host_stats6, 6);
+    return st;
 }

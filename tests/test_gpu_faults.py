@@ -1,6 +1,7 @@
 """Failure paths exercised without a GPU fault: an HBM budget that refuses a
 scratch allocation, a bounded device wait that runs out (a barrier nothing
-completes) and a full serving queue.  Each returns an error status and leaves
+completes), a full serving queue and a serving group larger than the
+serving budget.  Each returns an error status and leaves
 the context usable."""
 from __future__ import annotations
 
@@ -73,3 +74,25 @@ def test_full_serving_queue_refuses_admission(pg):
     assert srv.wait(t2, 60.0)
     srv.stop()
     assert ids.shape == (4, 5) and (ids[:, 0] >= 0).all()
+
+
+def test_serving_budget_refuses_a_group_that_never_fits(pg):
+    ctx = pg.Context()
+    D = _points(2000)
+    idx = pg.Index.build_nswg(ctx, torch.from_numpy(D).cuda(), metric="l2", K=16, L=32, R=16,
+                              M=16, alpha_deg=70.0, iters=1, seed=4)
+    srv = pg.Server(idx, max_batch=65536, slots=2)
+    # a query row costs 4 d + 8 k + 12 bytes (604 for d = 128, k = 10):
+    # 4,000 rows need 2,416,000 bytes, more than 1 MiB; 64 rows need 38,656
+    srv.set_budget(1 << 20)
+    big = np.ascontiguousarray(np.resize(D, (4000, D.shape[1])))
+    t1, _, _ = srv.submit_query(big, 10, 32, 1)
+    t2, ids, _ = srv.submit_query(D[:64], 10, 16, 1)
+    with pytest.raises(pg.PGError) as e:
+        srv.wait(t1, 60.0)
+    assert e.value.status == 6  # PG_ERR_BUDGET
+    assert srv.wait(t2, 60.0) and (ids[:, 0] >= 0).all()
+    srv.set_budget(0)
+    t3, ids3, _ = srv.submit_query(big, 10, 32, 1)
+    assert srv.wait(t3, 120.0) and (ids3[:, 0] >= 0).all()
+    srv.stop()

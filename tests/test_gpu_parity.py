@@ -509,3 +509,31 @@ def test_serving_loop_equals_the_same_calls_in_order(ctx, pg):
         assert (host(gi) == ids).all() and np.allclose(host(gd), dist)
     ia, ib = a.info(), b.info()
     assert ia == ib and ia["n"] == 3600
+
+
+def test_serving_overlapped_groups_equal_single_searches(ctx, pg):
+    """Requests of four shapes never merge, so every request is its own
+    group on one of four workers (own streams, concurrent on the device);
+    each result equals the same search made alone afterwards."""
+    D, Q, _ = synthetic.workload(1, n=3000, nq=200)
+    ctx2 = pg.Context()
+    b = pg.Index.build_nswg(ctx2, dev(D), metric="l2", K=24, L=48, R=32, M=16, alpha_deg=70.0,
+                            iters=1, seed=3)
+    shapes = [(10, 32, 1), (10, 48, 4), (5, 64, 16), (1, 16, 1)]
+    srv = pg.Server(b, max_batch=256, slots=4)
+    reqs, at = [], 0
+    for i in range(40):
+        k, beam, ub = shapes[i % 4]
+        m = 1 + (i * 7) % 9
+        rows = np.arange(at, at + m) % 200
+        at += m
+        t, ids, dist = srv.submit_query(Q[rows], k, beam, ub)
+        reqs.append((rows, k, beam, ub, t, ids, dist))
+    assert srv.wait_all([r[4] for r in reqs], 120.0)
+    st = srv.stats()
+    assert all(0.0 < srv.latency(r[4]) < 120.0 for r in reqs)
+    srv.stop()
+    assert st["requests"] == 40 and st["batches"] == 40 and st["max_in_flight"] >= 2
+    for rows, k, beam, ub, t, ids, dist in reqs:
+        gi, gd = b.search(dev(Q[rows]), k, beam, upper_beam=ub)
+        assert (host(gi) == ids).all() and (host(gd) == dist).all()
