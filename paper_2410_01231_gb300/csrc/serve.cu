@@ -141,45 +141,43 @@ struct Sched {
         if (thread_init) thread_init();
         for (;;) {
             Group g;
-            {
-                std::unique_lock<std::mutex> lk(mu);
-                cv_work.wait(lk, [&] { return stopping || !queue.empty(); });
-                if (queue.empty()) break;  // stopping and drained
-                g.reqs.push_back(queue.front());
-                g.rows = queue.front().rows;
-                queue.pop_front();
-                if (g.reqs[0].kind == 0) {
-                    while (!queue.empty() && mergeable(g.reqs[0], queue.front()) &&
-                           g.rows + queue.front().rows <= max_batch) {
-                        g.rows += queue.front().rows;
-                        g.reqs.push_back(queue.front());
-                        queue.pop_front();
-                    }
-                }
+            std::unique_lock<std::mutex> lk(mu);
+            cv_work.wait(lk, [&] { return stopping || !queue.empty(); });
+            if (queue.empty()) break;  // stopping and drained
+            // A group is formed only once it can start (a free worker; for an
+            // insertion, no group in flight), so requests that arrive while
+            // the workers are busy join it: batching follows the load.
+            const bool insertion = queue.front().kind == 1;
+            auto can_start = [&] { return insertion ? busy == 0 : busy < nslots; };
+            if (!can_start()) {
+                ++admission_waits;
+                cv_free.wait(lk, can_start);
             }
-            if (g.reqs[0].kind == 1) {
-                {
-                    std::unique_lock<std::mutex> lk(mu);
-                    if (busy) ++admission_waits;
-                    cv_free.wait(lk, [&] { return busy == 0; });
-                }
+            g.reqs.push_back(queue.front());
+            g.rows = queue.front().rows;
+            queue.pop_front();
+            if (insertion) {
+                lk.unlock();
                 const pg_status st = run_insert(g.reqs[0]);
-                std::lock_guard<std::mutex> lk(mu);
+                lk.lock();
                 complete(g.reqs, st);
                 continue;
             }
+            while (!queue.empty() && mergeable(g.reqs[0], queue.front()) &&
+                   g.rows + queue.front().rows <= max_batch) {
+                g.rows += queue.front().rows;
+                g.reqs.push_back(queue.front());
+                queue.pop_front();
+            }
             g.bytes = group_bytes(g);
-            std::unique_lock<std::mutex> lk(mu);
             if (budget && g.bytes > budget) {
                 complete(g.reqs, PG_ERR_BUDGET);
                 continue;
             }
-            auto admissible = [&] {
-                return busy < nslots && (!budget || bytes_in_flight + g.bytes <= budget);
-            };
-            if (!admissible()) {
+            auto fits = [&] { return !budget || bytes_in_flight + g.bytes <= budget; };
+            if (!fits()) {
                 ++admission_waits;
-                cv_free.wait(lk, admissible);
+                cv_free.wait(lk, fits);
             }
             int s = 0;
             while (slot_state[(size_t)s] != SLOT_IDLE) ++s;
@@ -241,6 +239,21 @@ struct Sched {
         }
         cv_work.notify_one();
         *ticket = r.ticket;
+        return PG_OK;
+    }
+
+    // enqueue several requests at once (the dispatcher sees all of them)
+    pg_status submit_all(std::vector<Req> &rs) {
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            if (stopping) return PG_ERR_INVALID_ARG;
+            for (Req &r : rs) {
+                r.ticket = next_ticket++;
+                r.submitted = std::chrono::steady_clock::now();
+                queue.push_back(r);
+            }
+        }
+        cv_work.notify_one();
         return PG_OK;
     }
 
@@ -523,15 +536,13 @@ extern "C" pg_status pg_serve_simulate(int32_t slots, int32_t max_batch, int64_t
     q.run_group = [&](int s, const Group &g) { return simulate(s, g.reqs, g.rows); };
     q.run_insert = [&](const Req &r) { return simulate(-1, std::vector<Req>{r}, r.rows); };
     if (!q.start()) return PG_ERR_INTERNAL;
-    pg_status st = PG_OK;
-    for (int32_t i = 0; i < count && st == PG_OK; ++i) {
-        Req r;
-        r.kind = kind[i];
-        r.rows = rows[i];
-        r.shape = shape[i];
-        int64_t t = 0;
-        st = q.submit(r, &t);
+    std::vector<Req> reqs((size_t)count);
+    for (int32_t i = 0; i < count; ++i) {
+        reqs[(size_t)i].kind = kind[i];
+        reqs[(size_t)i].rows = rows[i];
+        reqs[(size_t)i].shape = shape[i];
     }
+    pg_status st = q.submit_all(reqs);
     for (int64_t t = 1; t <= count && st == PG_OK; ++t) {
         int32_t done = 0;
         const pg_status w = q.wait(t, 60.0, &done);

@@ -476,8 +476,8 @@ def test_build_rejects_bad_params(ctx, pg):
 # ------------------------------------------------------------- serving
 def test_serving_loop_equals_the_same_calls_in_order(ctx, pg):
     """Interleaved query and insertion requests through the serving loop
-    give what the same calls made one after another give; consecutive
-    queries are merged into shared launches."""
+    give what the same calls made one after another give; with one worker,
+    queries that arrive while a group runs are merged into shared launches."""
     D, Q, _ = synthetic.workload(1, n=3600, nq=120)
     n0 = 3000
     p = dict(K=24, L=48, R=32, M=16, alpha_deg=70.0, iters=1, seed=2)
@@ -488,7 +488,7 @@ def test_serving_loop_equals_the_same_calls_in_order(ctx, pg):
     b.reserve(3600)
     plan = [("q", 0, 7), ("q", 7, 40), ("q", 40, 41), ("i", 3000, 3300), ("q", 41, 90),
             ("q", 90, 120), ("i", 3300, 3600), ("q", 0, 60)]
-    srv = pg.Server(b, max_batch=64)
+    srv = pg.Server(b, max_batch=64, slots=1)
     tickets = []
     for kind, s0, s1 in plan:
         if kind == "q":
