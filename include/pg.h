@@ -63,8 +63,19 @@ typedef enum { PG_METRIC_L2SQ = 0, PG_METRIC_COSINE = 1, PG_METRIC_IP = 2 } pg_m
 /* PG_PREC_FP32: distances in FP32 (FP64 recheck near margins).
  * PG_PREC_BF16_SCREEN: distance tiles / gathers from a BF16 copy of D with
  * FP32 accumulation; decisions inside the BF16 error bound are redone in
- * FP32 and then FP64, so results equal the FP32 form's. */
-typedef enum { PG_PREC_FP32 = 0, PG_PREC_BF16_SCREEN = 1 } pg_precision;
+ * FP32 and then FP64, so results equal the FP32 form's.
+ * PG_PREC_FP8_SCREEN: queries only (pg_search, pg_search_host, serving):
+ * the base-layer beam search ranks by distances from an FP8 E4M3 copy of
+ * the index's points (one FP32 scale per row, the row's largest magnitude
+ * mapped to 448; the cross term from the FP8 row, exact FP32 norms for
+ * L2), then the final pool is re-measured in FP32 and its k best returned:
+ * returned distances are FP32, membership is approximate (recall).  Every
+ * other entry point refuses it with PG_ERR_INVALID_ARG. */
+typedef enum {
+    PG_PREC_FP32 = 0,
+    PG_PREC_BF16_SCREEN = 1,
+    PG_PREC_FP8_SCREEN = 2
+} pg_precision;
 
 typedef struct pg_ctx pg_ctx;
 typedef struct pg_index pg_index;
@@ -377,14 +388,23 @@ pg_status pg_index_load(pg_ctx *ctx, const char *path, pg_index **out);
 pg_status pg_index_file_check(const char *path, int64_t *n, int32_t *d, int32_t *n_layers,
                               char *msg, size_t msg_len);
 
+/* The FP8 rows that PG_PREC_FP8_SCREEN searches use, for n DEVICE rows
+ * D [n][d]: scale[i] = max_j |D[i][j]| / 448 in FP32 (1 for a zero row),
+ * codes[i][j] = E4M3 (OCP FP8, 1-4-3 bits, bias 7, no infinities) of
+ * D[i][j] * (1 / scale[i]) rounded to nearest even and saturated at +-448,
+ * norm[i] = sum_j D[i][j]^2 in FP32.  Caller DEVICE buffers codes [n][d],
+ * scale [n], norm [n].  Synchronous. */
+pg_status pg_encode_fp8(pg_ctx *ctx, const float *D, int64_t n, int32_t d, uint8_t *codes,
+                        float *scale, float *norm);
+
 /* -------------------------------------------------------------- serving */
 
 /* A serving loop over a growable index: a dispatcher thread takes query
  * and insertion requests in submission order and hands query groups to
  * `slots` worker threads, each with its own context on its own CUDA stream,
  * so that groups of different requests run concurrently on the device.
- * Consecutive query requests with equal (k, beam, upper_beam) are merged
- * into one group of at most max_batch queries.  A group is admitted when a
+ * Consecutive query requests with equal (k, beam, upper_beam, precision)
+ * are merged into one group of at most max_batch queries.  A group is admitted when a
  * worker is free and the device scratch of the groups in flight plus its
  * own (queries, results and search state: rows x (4 d + 8 k + 12) bytes)
  * fits the HBM budget of ctx (0 = no limit); a group larger than the budget
@@ -428,6 +448,11 @@ pg_status pg_serve_latency(pg_server *server, int64_t ticket, double *seconds);
  * enqueued, no ticket) while `limit` requests are pending (queued or
  * running); 0 = no limit (the default). */
 pg_status pg_serve_set_queue_limit(pg_server *server, int64_t limit);
+
+/* Distance form of the query requests submitted from now on (PG_PREC_FP32,
+ * the default, PG_PREC_BF16_SCREEN or PG_PREC_FP8_SCREEN, as pg_search);
+ * requests of different forms are not merged. */
+pg_status pg_serve_set_precision(pg_server *server, pg_precision precision);
 
 /* Admission budget: bytes of device scratch the groups in flight may hold
  * together (0 = no limit; the default is ctx's HBM budget).  A group larger

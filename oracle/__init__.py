@@ -4,9 +4,12 @@ Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  The CUDA library never calls it and
 shares no code with it.  The arithmetic lives in ``oracle.c``; this module
 compiles it (gcc, ``-ffp-contract=off``), marshals numpy arrays and composes
-the hierarchical build of Algorithm 7 from the C pieces.
+the hierarchical build of Algorithm 7 from the C pieces.  The FP8 row format
+of the screened queries (not a subject of the paper) is written out here in
+Python from the definition of the number format.
 
-Every function names the passage of arXiv 2410.01231 it restates.
+Every function of the method names the passage of arXiv 2410.01231 it
+restates.
 """
 from __future__ import annotations
 
@@ -419,3 +422,79 @@ def recall_at_k(found_ids, Q, D, k: int, metric: str = "l2", gt=None):
                 hit += 1
         total += min(hit, k) / k
     return total / Q.shape[0]
+
+
+# --------------------------------------------------------------- FP8 rows
+# The number format of the FP8-screened queries (a precision form added on
+# top of the paper's search, which does not discuss number formats): OCP
+# 8-bit floating point E4M3 -- 1 sign bit, 4 exponent bits with bias 7,
+# 3 mantissa bits, subnormals, no infinities, S.1111.111 = NaN, largest
+# finite value 448.
+def fp8_e4m3_decode(codes) -> np.ndarray:
+    """Values (float64) of E4M3 codes, from the bit fields; NaN codes give nan."""
+    c = np.asarray(codes, np.uint8)
+    out = np.empty(c.shape, np.float64)
+    for i, b in np.ndenumerate(c):
+        b = int(b)
+        sign = -1.0 if b & 0x80 else 1.0
+        e, m = (b >> 3) & 0xF, b & 0x7
+        if e == 0xF and m == 0x7:
+            out[i] = math.nan
+        elif e == 0:
+            out[i] = sign * m * 2.0 ** -9
+        else:
+            out[i] = sign * (1.0 + m / 8.0) * 2.0 ** (e - 7)
+    return out
+
+
+def _round_half_even(x: float) -> int:
+    f = math.floor(x)
+    r = x - f
+    if r > 0.5 or (r == 0.5 and f % 2 == 1):
+        return int(f) + 1
+    return int(f)
+
+
+def fp8_e4m3_encode(values) -> np.ndarray:
+    """E4M3 codes of float32 values: nearest representable value, ties to the
+    even mantissa, magnitudes of 448 and above saturated to 448; the sign of
+    a value that rounds to zero is kept."""
+    v = np.asarray(values, np.float32)
+    out = np.empty(v.shape, np.uint8)
+    for i, x in np.ndenumerate(v):
+        x = float(x)
+        sign = 0x80 if math.copysign(1.0, x) < 0 else 0
+        a = abs(x)
+        if a >= 448.0:
+            code = 0x7E
+        elif a < 2.0 ** -6:
+            # subnormals are the multiples of 2^-9; 8 * 2^-9 is the smallest
+            # normal, whose code is 0b0001000 = 8 as well
+            code = _round_half_even(a * 2.0 ** 9)
+        else:
+            e = math.frexp(a)[1] - 1  # 2^e <= a < 2^(e + 1)
+            q = _round_half_even(a / 2.0 ** (e - 3))  # 8 <= q <= 16
+            if q == 16:
+                e, q = e + 1, 8
+            code = ((e + 7) << 3) | (q - 8)
+        out[i] = sign | code
+    return out
+
+
+def fp8_rows(D):
+    """FP8 rows of the screened queries: per row scale = max|x| / 448 in
+    float32 (1 for a zero row), codes of x * float32(1 / scale) (both steps
+    in float32), and the squared norm in FP64."""
+    D = np.asarray(D, np.float32)
+    n, d = D.shape
+    codes = np.empty((n, d), np.uint8)
+    scale = np.empty(n, np.float32)
+    norm = np.empty(n, np.float64)
+    for r in range(n):
+        mx = np.float32(np.max(np.abs(D[r]))) if d else np.float32(0)
+        sc = np.float32(mx / np.float32(448.0)) if mx > 0 else np.float32(1.0)
+        inv = np.float32(np.float32(1.0) / sc)
+        codes[r] = fp8_e4m3_encode((D[r] * inv).astype(np.float32))
+        scale[r] = sc
+        norm[r] = float(np.sum(D[r].astype(np.float64) ** 2))
+    return codes, scale, norm

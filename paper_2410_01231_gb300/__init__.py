@@ -29,7 +29,7 @@ METRIC = {"l2": 0, "cosine": 1, "ip": 2}
 # (1 is the paper's greedy routing; 16 enters the query's cluster far more
 # reliably on well-separated data)
 UPPER_BEAM = 16
-PRECISION = {"fp32": 0, "bf16": 1}
+PRECISION = {"fp32": 0, "bf16": 1, "fp8": 2}
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "TIMEOUT", 5: "CAPACITY", 6: "BUDGET",
           7: "INTERNAL", 8: "DEVICE_CHECK", 9: "IO"}
 
@@ -95,6 +95,8 @@ _sig("pg_serve_stop", C.c_int, [P])
 _sig("pg_serve_set_queue_limit", C.c_int, [P, i64])
 _sig("pg_serve_set_budget", C.c_int, [P, i64])
 _sig("pg_serve_latency", C.c_int, [P, i64, P])
+_sig("pg_serve_set_precision", C.c_int, [P, C.c_int])
+_sig("pg_encode_fp8", C.c_int, [P, P, i64, i32, P, P, P])
 _sig("pg_selftest_wait_timeout", C.c_int, [P, dbl])
 _sig("pg_index_params", C.c_int, [P, P, P])
 _sig("pg_index_save", C.c_int, [P, P, C.c_char_p])
@@ -113,7 +115,8 @@ EXPORTS = ["pg_default_params", "pg_ctx_create", "pg_ctx_destroy", "pg_last_erro
            "pg_serve_stats", "pg_serve_stop", "pg_serve_set_queue_limit",
            "pg_selftest_wait_timeout", "pg_index_params", "pg_index_save", "pg_index_load",
            "pg_index_file_check", "pg_serve_simulate",
-           "pg_serve_set_budget", "pg_serve_latency"]
+           "pg_serve_set_budget", "pg_serve_latency", "pg_serve_set_precision",
+           "pg_encode_fp8"]
 
 
 class PGError(RuntimeError):
@@ -229,6 +232,19 @@ def index_file_check(path: str) -> dict:
     if st != 0:
         raise PGError(st, f"pg_index_file_check: {msg.value.decode()}")
     return dict(n=n.value, d=d.value, n_layers=nl.value)
+
+
+def encode_fp8(ctx: Context, D: torch.Tensor):
+    """FP8 E4M3 rows of D as the screened search uses them (pg_encode_fp8):
+    (codes uint8 [n][d], scale float32 [n], norm float32 [n])."""
+    D = _dev(D, torch.float32, "D")
+    n, d = D.shape
+    codes = torch.empty((n, d), dtype=torch.uint8, device=D.device)
+    scale = torch.empty(n, dtype=torch.float32, device=D.device)
+    norm = torch.empty(n, dtype=torch.float32, device=D.device)
+    ctx._check(_lib.pg_encode_fp8(ctx.handle, _ptr(D), n, d, _ptr(codes), _ptr(scale),
+                                  _ptr(norm)), "pg_encode_fp8")
+    return codes, scale, norm
 
 
 def build_knn(ctx: Context, D: torch.Tensor, K: int, metric="l2", precision="fp32"):
@@ -454,7 +470,7 @@ class Index:
 
     def search_host(self, Q: np.ndarray, k: int, beam: int, upper_beam: int = UPPER_BEAM,
                     flat: bool = False, out_ids: np.ndarray | None = None,
-                    out_dist: np.ndarray | None = None):
+                    out_dist: np.ndarray | None = None, precision="fp32"):
         """Host buffers in and out (copies inside the call)."""
         if not (isinstance(Q, np.ndarray) or isinstance(Q, torch.Tensor)):
             raise TypeError("Q must be a host array")
@@ -470,8 +486,8 @@ class Index:
             return a.ctypes.data_as(C.c_void_p)
 
         self.ctx._check(_lib.pg_search_host(self.ctx.handle, self._h, hp(Q), nq, k, beam,
-                                            upper_beam, 1 if flat else 0, 0, hp(out_ids),
-                                            hp(out_dist)),
+                                            upper_beam, 1 if flat else 0, PRECISION[precision],
+                                            hp(out_ids), hp(out_dist)),
                         "pg_search_host")
         return out_ids, out_dist
 
@@ -575,6 +591,11 @@ class Server:
         v = C.c_double()
         self._chk(_lib.pg_serve_latency(self._h, ticket, C.byref(v)), "pg_serve_latency")
         return v.value
+
+    def set_precision(self, precision: str):
+        """Distance form ("fp32", "bf16", "fp8") of query requests submitted from now on."""
+        self._chk(_lib.pg_serve_set_precision(self._h, PRECISION[precision]),
+                  "pg_serve_set_precision")
 
     def set_budget(self, nbytes: int):
         """Device scratch the groups in flight may hold together (0: no limit)."""

@@ -33,11 +33,6 @@ pg_status pg_connect_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
                               int32_t *nbr, int32_t *deg, int32_t R, int64_t ep,
                               const DataFacts &facts, const int32_t *knn, int32_t K,
                               int64_t *host_added);
-pg_status pg_search_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
-                             const int32_t *nbr, const int32_t *deg, int32_t R,
-                             const int32_t *rows, const float *Q, int64_t nq,
-                             const int32_t *starts, int32_t k, int32_t L, int self,
-                             int32_t *out_i, float *out_s, const uint8_t *D8 = nullptr);
 
 namespace {
 
@@ -163,6 +158,8 @@ pg_status check_params(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
         return pg_fail(ctx, PG_ERR_INVALID_ARG, "need 0 <= alpha <= 180");
     if (p->metric < PG_METRIC_L2SQ || p->metric > PG_METRIC_IP)
         return pg_fail(ctx, PG_ERR_INVALID_ARG, "bad metric");
+    if (!pg_build_precision(p->precision))
+        return pg_fail(ctx, PG_ERR_INVALID_ARG, "builds take FP32 or BF16 screening");
     return PG_OK;
 }
 
@@ -395,10 +392,41 @@ extern "C" pg_status pg_index_phase_seconds(const pg_index *idx, double *host_se
     return PG_OK;
 }
 
+// The FP8 rows of the index for screened queries, made or extended on this
+// context's stream (rows added by insertions are encoded on first use).
+// Serialised per index: concurrent searches of a serving loop wait for one
+// encoding, which completes before the lock is released.
+static pg_status index_f8(pg_ctx *ctx, const pg_index *idx, F8Rows *out) {
+    std::lock_guard<std::mutex> lk(idx->f8_mu);
+    const int64_t cap = std::max(idx->n, idx->capacity);
+    if (idx->f8_cap < cap) {
+        cudaFree(idx->f8);
+        cudaFree(idx->f8_scale);
+        cudaFree(idx->f8_norm);
+        idx->f8 = nullptr;
+        idx->f8_scale = idx->f8_norm = nullptr;
+        idx->f8_rows = idx->f8_cap = 0;
+        PG_TRY_CUDA(ctx, cudaMalloc(&idx->f8, (size_t)(cap * idx->d)));
+        PG_TRY_CUDA(ctx, cudaMalloc(&idx->f8_scale, (size_t)cap * 4));
+        PG_TRY_CUDA(ctx, cudaMalloc(&idx->f8_norm, (size_t)cap * 4));
+        idx->f8_cap = cap;
+    }
+    if (idx->f8_rows < idx->n) {
+        PG_TRY(pg_make_f8(ctx, idx->D, idx->f8_rows, idx->n, idx->d, idx->f8, idx->f8_scale,
+                          idx->f8_norm));
+        PG_TRY_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        idx->f8_rows = idx->n;
+    }
+    *out = F8Rows{idx->f8, idx->f8_scale, idx->f8_norm};
+    return PG_OK;
+}
+
 static pg_status search_index(pg_ctx *ctx, const pg_index *idx, const float *Q, int64_t nq,
                               int32_t k, int32_t beam, int32_t upper_beam, int32_t flags,
-                              int32_t *out_ids, float *out_dist) {
+                              pg_precision precision, int32_t *out_ids, float *out_dist) {
     if (nq == 0) return PG_OK;
+    F8Rows f8{};
+    if (precision == PG_PREC_FP8_SCREEN) PG_TRY(index_f8(ctx, idx, &f8));
     Scratch<int32_t> w, w2;
     Scratch<float> s2;
     PG_TRY(w.alloc(ctx, (size_t)nq));
@@ -418,34 +446,37 @@ static pg_status search_index(pg_ctx *ctx, const pg_index *idx, const float *Q, 
     }
     const pg_layer &b = idx->layers[0];
     return pg_search_internal(ctx, idx->D, idx->n, idx->d, idx->metric, b.nbr, b.deg, b.R, nullptr,
-                              Q, nq, w.p, k, beam, 0, out_ids, out_dist);
+                              Q, nq, w.p, k, beam, 0, out_ids, out_dist, nullptr,
+                              precision == PG_PREC_FP8_SCREEN ? &f8 : nullptr);
 }
 
 static pg_status check_search(pg_ctx *ctx, const pg_index *idx, const float *Q, int64_t nq,
-                              int32_t k, int32_t beam, int32_t upper_beam, const void *a,
-                              const void *b) {
+                              int32_t k, int32_t beam, int32_t upper_beam, pg_precision precision,
+                              const void *a, const void *b) {
     if (!ctx) return PG_ERR_INVALID_ARG;
     if (!idx || !Q || !a || !b) return pg_fail(ctx, PG_ERR_INVALID_ARG, "null pointer");
     if (nq < 0 || k < 1 || beam < k || beam > 256 || upper_beam < 1 || upper_beam > 256)
         return pg_fail(ctx, PG_ERR_INVALID_ARG,
                        "need 1 <= k <= beam <= 256 and 1 <= upper_beam <= 256");
+    if (precision != PG_PREC_FP32 && precision != PG_PREC_BF16_SCREEN &&
+        precision != PG_PREC_FP8_SCREEN)
+        return pg_fail(ctx, PG_ERR_INVALID_ARG, "bad precision");
     return PG_OK;
 }
 
 extern "C" pg_status pg_search(pg_ctx *ctx, const pg_index *idx, const float *Q, int64_t nq,
                                int32_t k, int32_t beam, int32_t upper_beam, int32_t flags,
                                pg_precision precision, int32_t *out_ids, float *out_dist) {
-    (void)precision;
-    PG_TRY(check_search(ctx, idx, Q, nq, k, beam, upper_beam, out_ids, out_dist));
-    PG_TRY(search_index(ctx, idx, Q, nq, k, beam, upper_beam, flags, out_ids, out_dist));
+    PG_TRY(check_search(ctx, idx, Q, nq, k, beam, upper_beam, precision, out_ids, out_dist));
+    PG_TRY(search_index(ctx, idx, Q, nq, k, beam, upper_beam, flags, precision, out_ids,
+                        out_dist));
     return pg_sync_check(ctx, "pg_search");
 }
 
 extern "C" pg_status pg_search_host(pg_ctx *ctx, const pg_index *idx, const float *Q, int64_t nq,
                                     int32_t k, int32_t beam, int32_t upper_beam, int32_t flags,
                                     pg_precision precision, int32_t *out_ids, float *out_dist) {
-    (void)precision;
-    PG_TRY(check_search(ctx, idx, Q, nq, k, beam, upper_beam, out_ids, out_dist));
+    PG_TRY(check_search(ctx, idx, Q, nq, k, beam, upper_beam, precision, out_ids, out_dist));
     if (nq == 0) return PG_OK;
     Scratch<float> dq, ds;
     Scratch<int32_t> di;
@@ -454,7 +485,7 @@ extern "C" pg_status pg_search_host(pg_ctx *ctx, const pg_index *idx, const floa
     PG_TRY(di.alloc(ctx, (size_t)(nq * k)));
     PG_TRY_CUDA(ctx, cudaMemcpyAsync(dq.p, Q, (size_t)(nq * idx->d) * 4, cudaMemcpyHostToDevice,
                                      ctx->stream));
-    PG_TRY(search_index(ctx, idx, dq.p, nq, k, beam, upper_beam, flags, di.p, ds.p));
+    PG_TRY(search_index(ctx, idx, dq.p, nq, k, beam, upper_beam, flags, precision, di.p, ds.p));
     PG_TRY_CUDA(ctx, cudaMemcpyAsync(out_ids, di.p, (size_t)(nq * k) * 4, cudaMemcpyDeviceToHost,
                                      ctx->stream));
     PG_TRY_CUDA(ctx, cudaMemcpyAsync(out_dist, ds.p, (size_t)(nq * k) * 4, cudaMemcpyDeviceToHost,

@@ -386,6 +386,8 @@ pg_status knn_core(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric 
     if (n < 1 || nq < 0 || d < 4 || d % 4 || d > 8192)
         return pg_fail(ctx, PG_ERR_INVALID_ARG, "knn: need n >= 1, d % 4 == 0, 4 <= d <= 8192");
     if (K < 1 || K > KMAX) return pg_fail(ctx, PG_ERR_INVALID_ARG, "knn: need 1 <= K <= %d", KMAX);
+    if (!pg_build_precision(precision))
+        return pg_fail(ctx, PG_ERR_INVALID_ARG, "knn takes FP32 or BF16 screening");
     if (nq == 0) return PG_OK;
     const float *Qp = self ? D : Q;
     DataFacts facts;

@@ -7,6 +7,7 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -66,8 +67,18 @@ struct pg_index {
     pg_build_params params{};  // of the build: levels, degrees, pruning angle
     float *owned = nullptr;    // private copy of the points once reserved
     int64_t capacity = 0;      // rows of `owned`
+    // FP8 E4M3 copy of the points for screened queries: made on first use,
+    // extended after insertions (rows [0, f8_rows) valid, f8_cap allocated)
+    mutable std::mutex f8_mu;
+    mutable uint8_t *f8 = nullptr;      // [f8_cap][d]
+    mutable float *f8_scale = nullptr;  // [f8_cap] value of 1.0 in the FP8 row
+    mutable float *f8_norm = nullptr;   // [f8_cap] squared FP32 norms
+    mutable int64_t f8_rows = 0, f8_cap = 0;
     ~pg_index() {
         cudaFree(owned);
+        cudaFree(f8);
+        cudaFree(f8_scale);
+        cudaFree(f8_norm);
         for (auto &l : layers) {
             cudaFree(l.gid);
             cudaFree(l.nbr);
@@ -76,6 +87,23 @@ struct pg_index {
         }
     }
 };
+
+// FP8 rows of an index for screened queries (device pointers)
+struct F8Rows {
+    const uint8_t *q8;    // [n][d] E4M3 codes of x / scale
+    const float *scale;   // [n]
+    const float *norm;    // [n] squared FP32 norms
+};
+
+// Batched beam search (Algorithm 1), one warp per query: self mode (Q null,
+// query i is row i from start i) or queries Q from starts; D8 the byte rows
+// (self mode, exact data), f8 the FP8 rows (screened queries).
+pg_status pg_search_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
+                             const int32_t *nbr, const int32_t *deg, int32_t R,
+                             const int32_t *rows, const float *Q, int64_t nq,
+                             const int32_t *starts, int32_t k, int32_t L, int self,
+                             int32_t *out_i, float *out_s, const uint8_t *D8 = nullptr,
+                             const F8Rows *f8 = nullptr);
 
 // named kernel timers
 enum {
@@ -188,6 +216,14 @@ pg_status pg_data_facts(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_me
 // Leaves `out` empty (p == nullptr) when the data do not qualify.
 bool pg_u8_usable(const DataFacts &f, pg_metric metric, int d, pg_precision precision);
 pg_status pg_make_u8(pg_ctx *ctx, const float *D, int64_t n, int32_t d, Scratch<uint8_t> &out);
+// FP8 E4M3 rows r0..r1-1 of D: codes of x / scale (scale = max|x| / 448,
+// 1 for a zero row) and the squared FP32 norm of x (queued on ctx's stream)
+pg_status pg_make_f8(pg_ctx *ctx, const float *D, int64_t r0, int64_t r1, int32_t d, uint8_t *q8,
+                     float *scale, float *norm);
+// build-like entry points take FP32 or BF16 screening only
+inline bool pg_build_precision(pg_precision p) {
+    return p == PG_PREC_FP32 || p == PG_PREC_BF16_SCREEN;
+}
 
 // Split-column argmin on the tensor cores over the rows of D (BF16-exact
 // integer data): best[i] = min over columns c with reached[c] != 0 and

@@ -685,6 +685,8 @@ extern "C" pg_status pg_prune(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
     if (R < 1 || R > RMAX) return pg_fail(ctx, PG_ERR_INVALID_ARG, "need 1 <= R <= %d", RMAX);
     if (!(alpha_deg >= 0.0 && alpha_deg <= 180.0))
         return pg_fail(ctx, PG_ERR_INVALID_ARG, "need 0 <= alpha <= 180");
+    if (!pg_build_precision(precision))
+        return pg_fail(ctx, PG_ERR_INVALID_ARG, "pruning takes FP32 or BF16 screening");
     DataFacts facts;
     PG_TRY(pg_data_facts(ctx, D, n, d, metric, &facts));
     Scratch<uint8_t> d8;

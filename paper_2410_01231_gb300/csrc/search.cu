@@ -20,6 +20,13 @@
 // Because the pool is always the L best of everything inserted so far, a
 // node that was evaluated and left the pool can never re-enter it; the
 // lossy table therefore changes the work done, never the result.
+//
+// FP8-screened queries rank the expansion candidates by distances from the
+// index's FP8 E4M3 rows (cross term scale * sum e_i q_i in FP32, exact FP32
+// norms for L2); at the end the whole pool is re-measured in FP32 and the
+// k best by (s, id) are returned.
+#include <cuda_fp8.h>
+
 #include <climits>
 #include <mutex>
 
@@ -34,6 +41,8 @@ constexpr int SW = 4;  // warps per CTA
 struct SearchParams {
     const float *D;
     const uint8_t *D8;  // byte shadow of D (exact data, self mode) or nullptr
+    const uint8_t *F8;  // FP8 E4M3 rows of D (screened queries) or nullptr
+    const float *f8scale, *f8norm;
     int64_t n;
     int d;
     int metric;
@@ -79,8 +88,69 @@ __device__ __forceinline__ unsigned hslot(int v, int hbits) {
     return ((unsigned)v * 2654435761u) >> (32 - hbits);
 }
 
+// sum of e_i q_i over one FP8 row (codes of 16 elements per 16-byte chunk),
+// by a team of eight lanes
+__device__ __forceinline__ float team8_dot_f8_16(const float4 *__restrict__ q,
+                                                 const uint4 *__restrict__ x, int nch16, int li) {
+    float acc = 0.f;
+    for (int c = li; c < nch16; c += 8) {
+        const uint4 w = __ldg(x + c);
+        const unsigned words[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const float4 qa = q[c * 4 + h];
+            const __half2 lo(__nv_cvt_fp8x2_to_halfraw2(
+                (__nv_fp8x2_storage_t)(words[h] & 0xffffu), __NV_E4M3));
+            const __half2 hi(__nv_cvt_fp8x2_to_halfraw2(
+                (__nv_fp8x2_storage_t)(words[h] >> 16), __NV_E4M3));
+            const float2 a = __half22float2(lo), b = __half22float2(hi);
+            acc = fmaf(a.x, qa.x, acc);
+            acc = fmaf(a.y, qa.y, acc);
+            acc = fmaf(b.x, qa.z, acc);
+            acc = fmaf(b.y, qa.w, acc);
+        }
+    }
+    return warp_sum8(acc);
+}
+
+// the same for rows whose width is not a multiple of 16 (4 elements a load)
+__device__ __forceinline__ float team8_dot_f8_4(const float4 *__restrict__ q,
+                                                const unsigned *__restrict__ x, int nch4, int li) {
+    float acc = 0.f;
+    for (int c = li; c < nch4; c += 8) {
+        const unsigned w = __ldg(x + c);
+        const float4 qa = q[c];
+        const __half2 lo(__nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w & 0xffffu),
+                                                     __NV_E4M3));
+        const __half2 hi(__nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w >> 16),
+                                                     __NV_E4M3));
+        const float2 a = __half22float2(lo), b = __half22float2(hi);
+        acc = fmaf(a.x, qa.x, acc);
+        acc = fmaf(a.y, qa.y, acc);
+        acc = fmaf(b.x, qa.z, acc);
+        acc = fmaf(b.y, qa.w, acc);
+    }
+    return warp_sum8(acc);
+}
+
+// screened distance of FP8 row v to the query (squared L2 from the norms
+// and the cross term, or the chord 2 - 2<x, q> of unit rows)
+__device__ __forceinline__ float team8_dist_f8(const SearchParams &P, const float4 *q, float qn,
+                                               int v, int li) {
+    const int d = P.d;
+    const uint8_t *row = P.F8 + (int64_t)v * d;
+    const float dot = (d & 15) == 0
+                          ? team8_dot_f8_16(q, reinterpret_cast<const uint4 *>(row), d >> 4, li)
+                          : team8_dot_f8_4(q, reinterpret_cast<const unsigned *>(row), d >> 2, li);
+    const float cross = __ldg(P.f8scale + v) * dot;
+    if (P.metric == 0) return fmaxf(__ldg(P.f8norm + v) + qn - 2.f * cross, 0.f);
+    return fmaxf(2.f - 2.f * cross, 0.f);
+}
+
+template <bool kF8>
 __device__ void search_one(const SearchParams &P, int64_t qi, unsigned char *ws,
-                           unsigned long long &n_exp, unsigned long long &n_eval) {
+                           unsigned long long &n_exp, unsigned long long &n_eval,
+                           unsigned long long &n_rerank) {
     const int lane = threadIdx.x & 31, team = lane >> 3, li = lane & 7;
     const int L = P.L, d = P.d, nch = d / 4;
     const int Lp = pool_slots(L);
@@ -104,6 +174,13 @@ __device__ void search_one(const SearchParams &P, int64_t qi, unsigned char *ws,
             reinterpret_cast<float4 *>(q)[c] = __ldg(reinterpret_cast<const float4 *>(qsrc) + c);
     }
     for (int h = lane; h < H; h += 32) htab[h] = -1;
+    constexpr bool f8 = kF8;  // FP8 rows (P.F8) in use
+    float qn = 0.f;
+    if (f8) {
+        __syncwarp();
+        for (int c = lane; c < d; c += 32) qn = fmaf(q[c], q[c], qn);
+        for (int o = 16; o; o >>= 1) qn += __shfl_xor_sync(0xffffffffu, qn, o);
+    }
     int start = P.self ? (int)qi : P.starts[qi];
     bool bad = start < 0 || start >= P.n;
     if (bad) {
@@ -114,6 +191,8 @@ __device__ void search_one(const SearchParams &P, int64_t qi, unsigned char *ws,
     float s0;
     if (D8) {
         s0 = team8_dist_u8(q16, reinterpret_cast<const uint4 *>(D8 + (int64_t)start * d), d >> 4, li);
+    } else if (f8) {
+        s0 = team8_dist_f8(P, q4, qn, start, li);
     } else {
         s0 = team8_dist(q4, reinterpret_cast<const float4 *>(P.D + (int64_t)start * d), nch, li,
                         P.metric);
@@ -178,6 +257,12 @@ __device__ void search_one(const SearchParams &P, int64_t qi, unsigned char *ws,
             __syncwarp();
             if (D8) {
                 batch_dist_u8(D8, d, q16, ni, cnt, nd);
+            } else if (f8) {
+                for (int b0 = 0; b0 < cnt; b0 += 4) {
+                    int i = b0 + team;
+                    float s = team8_dist_f8(P, q4, qn, ni[i < cnt ? i : 0], li);
+                    if (li == 0 && i < cnt) nd[i] = s;
+                }
             } else {
                 for (int b0 = 0; b0 < cnt; b0 += 4) {
                     int i = b0 + team;
@@ -284,6 +369,50 @@ __device__ void search_one(const SearchParams &P, int64_t qi, unsigned char *ws,
             P.out_i[qi * L + t] = -1;
             if (P.out_s) P.out_s[qi * L + t] = INFINITY;
         }
+    } else if (f8 && !bad) {
+        // re-measure the pool in FP32 (bit 31 now marks "returned")
+        for (int b0 = 0; b0 < size; b0 += 4) {
+            const int i = b0 + team;
+            const int id = piA[i < size ? i : 0] & ID_MASK;
+            const float s = team8_dist(q4, reinterpret_cast<const float4 *>(P.D + (int64_t)id * d),
+                                       nch, li, P.metric);
+            __syncwarp();
+            if (li == 0 && i < size) {
+                pdA[i] = s;
+                piA[i] = id;
+            }
+        }
+        n_rerank += (unsigned long long)size;
+        __syncwarp();
+        // the k best by (s, id): one warp-wide minimum per output slot
+        for (int t = 0; t < P.k; ++t) {
+            float bs = INFINITY;
+            int bid = INT_MAX, bpos = -1;
+            for (int i = lane; i < size; i += 32) {
+                const int e = piA[i];
+                if (!(e & EXP_BIT) && pair_less(pdA[i], e, bs, bid)) {
+                    bs = pdA[i];
+                    bid = e;
+                    bpos = i;
+                }
+            }
+            for (int o = 16; o; o >>= 1) {
+                const float os = __shfl_xor_sync(0xffffffffu, bs, o);
+                const int oid = __shfl_xor_sync(0xffffffffu, bid, o);
+                const int opos = __shfl_xor_sync(0xffffffffu, bpos, o);
+                if (pair_less(os, oid, bs, bid)) {
+                    bs = os;
+                    bid = oid;
+                    bpos = opos;
+                }
+            }
+            if (lane == 0) {
+                P.out_i[qi * P.k + t] = bpos >= 0 ? bid : -1;
+                P.out_s[qi * P.k + t] = bpos >= 0 ? bs : INFINITY;
+                if (bpos >= 0) piA[bpos] |= EXP_BIT;
+            }
+            __syncwarp();
+        }
     } else {
         for (int t = lane; t < P.k; t += 32) {
             bool ok = t < size && !bad;
@@ -294,24 +423,28 @@ __device__ void search_one(const SearchParams &P, int64_t qi, unsigned char *ws,
     __syncwarp();
 }
 
+template <bool kF8>
 __global__ void __launch_bounds__(SW * 32, 8) k_search(SearchParams P) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     unsigned char *ws = smem + (size_t)wid * search_warp_smem(P.L, P.hbits, P.d);
-    unsigned long long n_exp = 0, n_eval = 0;
+    unsigned long long n_exp = 0, n_eval = 0, n_rerank = 0;
     for (;;) {
         int64_t qi = 0;
         if (lane == 0) qi = atomicAdd(P.qcounter, 1);
         qi = __shfl_sync(0xffffffffu, qi, 0);
         if (qi >= P.nq) break;
-        search_one(P, qi, ws, n_exp, n_eval);
+        search_one<kF8>(P, qi, ws, n_exp, n_eval, n_rerank);
     }
     if (lane == 0) {
-        // algorithmic bytes: one row per evaluation, one adjacency row per expansion
-        const unsigned long long row = P.D8 ? (unsigned long long)P.d : 4ull * P.d;
+        // algorithmic bytes: one row per evaluation (FP8 rows also their scale
+        // and norm), one adjacency row per expansion, one FP32 row per re-measure
+        const unsigned long long row =
+            P.D8 ? (unsigned long long)P.d : P.F8 ? (unsigned long long)P.d + 8ull : 4ull * P.d;
         atomicAdd(P.counters + CNT_SEARCH_EXP, n_exp);
         atomicAdd(P.counters + CNT_SEARCH_EVAL, n_eval);
-        atomicAdd(P.counters + CNT_SEARCH_BYTES, n_eval * row + n_exp * 4ull * P.R);
+        atomicAdd(P.counters + CNT_SEARCH_BYTES,
+                  n_eval * row + n_exp * 4ull * P.R + n_rerank * 4ull * P.d);
     }
 }
 
@@ -323,11 +456,14 @@ pg_status pg_search_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d, 
                              const int32_t *nbr, const int32_t *deg, int32_t R,
                              const int32_t *rows, const float *Q, int64_t nq,
                              const int32_t *starts, int32_t k, int32_t L, int self,
-                             int32_t *out_i, float *out_s, const uint8_t *D8) {
+                             int32_t *out_i, float *out_s, const uint8_t *D8, const F8Rows *f8) {
     if (nq == 0) return PG_OK;
     SearchParams P;
     P.D = D;
     P.D8 = self ? D8 : nullptr;
+    P.F8 = !self && f8 ? f8->q8 : nullptr;
+    P.f8scale = P.F8 ? f8->scale : nullptr;
+    P.f8norm = P.F8 ? f8->norm : nullptr;
     P.n = n;
     P.d = d;
     P.metric = metric == PG_METRIC_L2SQ ? 0 : 1;
@@ -362,18 +498,67 @@ pg_status pg_search_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d, 
     // of other contexts on other threads (the serving workers) may set a
     // different size, so setting it and launching are one critical section
     std::lock_guard<std::mutex> lk(search_launch_mu);
-    PG_TRY_CUDA(ctx, cudaFuncSetAttribute(k_search, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    void (*kern)(SearchParams) = P.F8 ? k_search<true> : k_search<false>;
+    PG_TRY_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)smem));
     int bps = 0;
-    PG_TRY_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_search, SW * 32, smem));
+    PG_TRY_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, SW * 32, smem));
     if (bps < 1) bps = 1;
     int64_t want = (nq + SW - 1) / SW;
     int64_t grid = std::min<int64_t>((int64_t)ctx->num_sms * bps, want);
     pg_timer_begin(ctx, TM_SEARCH);
-    k_search<<<(unsigned)grid, SW * 32, smem, ctx->stream>>>(P);
+    kern<<<(unsigned)grid, SW * 32, smem, ctx->stream>>>(P);
     PG_LAUNCHED(ctx);
     pg_timer_end(ctx, TM_SEARCH);
     return PG_OK;
+}
+
+// One warp per row: scale = max|x| / 448 (1 for a zero row), codes of
+// x / scale rounded to nearest E4M3 (saturating), squared FP32 norm.
+__global__ void k_make_f8(const float *D, int64_t r0, int64_t r1, int d, uint8_t *q8,
+                          float *scale, float *norm) {
+    const int lane = threadIdx.x & 31;
+    const int64_t r = r0 + ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    if (r >= r1) return;
+    const float *x = D + r * d;
+    float mx = 0.f, nn = 0.f;
+    for (int c = lane; c < d; c += 32) {
+        const float v = x[c];
+        mx = fmaxf(mx, fabsf(v));
+        nn = fmaf(v, v, nn);
+    }
+    for (int o = 16; o; o >>= 1) {
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        nn += __shfl_xor_sync(0xffffffffu, nn, o);
+    }
+    const float sc = mx > 0.f ? mx / 448.f : 1.f;
+    const float inv = 1.f / sc;
+    for (int c = lane; c < d; c += 32)
+        q8[r * d + c] = (uint8_t)__nv_cvt_float_to_fp8(x[c] * inv, __NV_SATFINITE, __NV_E4M3);
+    if (lane == 0) {
+        scale[r] = sc;
+        norm[r] = nn;
+    }
+}
+
+pg_status pg_make_f8(pg_ctx *ctx, const float *D, int64_t r0, int64_t r1, int32_t d, uint8_t *q8,
+                     float *scale, float *norm) {
+    if (r1 <= r0) return PG_OK;
+    const int64_t warps = r1 - r0;
+    k_make_f8<<<(unsigned)((warps + 7) / 8), 256, 0, ctx->stream>>>(D, r0, r1, d, q8, scale, norm);
+    PG_LAUNCHED(ctx);
+    return PG_OK;
+}
+
+extern "C" pg_status pg_encode_fp8(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
+                                   uint8_t *codes, float *scale, float *norm) {
+    if (!ctx) return PG_ERR_INVALID_ARG;
+    if (!D || !codes || !scale || !norm) return pg_fail(ctx, PG_ERR_INVALID_ARG, "null pointer");
+    if (n < 0 || n >= INT_MAX) return pg_fail(ctx, PG_ERR_INVALID_ARG, "need 0 <= n < 2^31");
+    if (d < 4 || d % 4 || d > 8192)
+        return pg_fail(ctx, PG_ERR_INVALID_ARG, "need d % 4 == 0 and 4 <= d <= 8192");
+    PG_TRY(pg_make_f8(ctx, D, 0, n, d, codes, scale, norm));
+    return pg_sync_check(ctx, "pg_encode_fp8");
 }
 
 static pg_status check_graph_args(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
@@ -394,6 +579,8 @@ extern "C" pg_status pg_acquire_candidates(pg_ctx *ctx, const float *D, int64_t 
                                            pg_precision precision, int32_t *cand) {
     PG_TRY(check_graph_args(ctx, D, n, d, nbr, deg, R, L));
     if (!cand) return pg_fail(ctx, PG_ERR_INVALID_ARG, "null cand");
+    if (!pg_build_precision(precision))
+        return pg_fail(ctx, PG_ERR_INVALID_ARG, "acquisition takes FP32 or BF16 screening");
     Scratch<uint8_t> d8;
     if (precision == PG_PREC_BF16_SCREEN) {
         DataFacts facts;
@@ -411,7 +598,9 @@ extern "C" pg_status pg_search_graph(pg_ctx *ctx, const float *D, int64_t n, int
                                      const int32_t *starts, int32_t k, int32_t L,
                                      pg_precision precision, int32_t *out_ids, float *out_dist) {
     PG_TRY(check_graph_args(ctx, D, n, d, nbr, deg, R, L));
-    (void)precision;
+    if (!pg_build_precision(precision))
+        return pg_fail(ctx, PG_ERR_INVALID_ARG,
+                       "pg_search_graph takes FP32 (FP8 screening needs an index)");
     if (!Q || !starts || !out_ids || !out_dist)
         return pg_fail(ctx, PG_ERR_INVALID_ARG, "null pointer");
     if (nq < 0 || k < 1 || k > L) return pg_fail(ctx, PG_ERR_INVALID_ARG, "need 1 <= k <= L");

@@ -5,7 +5,7 @@
 // device.
 //
 // Dispatch is in submission order.  Consecutive query requests with the
-// same (k, beam, upper_beam) are merged into one group of at most max_batch
+// same (k, beam, upper_beam, precision) are merged into one group of at most max_batch
 // queries (continuous batching); a group is admitted to a worker once a
 // worker is free and the device scratch of the groups in flight plus its
 // own fits the HBM budget of the server's context (a group that could never
@@ -44,6 +44,7 @@ struct Req {
     const float *host = nullptr;
     int64_t rows = 0;
     int k = 0, beam = 0, upper_beam = 1, ef = 0;
+    pg_precision precision = PG_PREC_FP32;  // queries: distance form of the search
     int32_t *out_ids = nullptr;
     float *out_dist = nullptr;
     int64_t shape = 0;  // simulated requests: merge key
@@ -74,6 +75,7 @@ struct Sched {
     std::deque<Req> queue;
     bool stopping = false, slots_exit = false;
     int64_t next_ticket = 1, completed = 0, queue_limit = 0;
+    pg_precision precision = PG_PREC_FP32;  // taken by query requests when submitted
     int64_t done_below = 1;          // every ticket below it is done
     std::set<int64_t> done_above;    // done tickets at or above done_below
     std::unordered_map<int64_t, int> failed;  // ticket -> status
@@ -235,6 +237,7 @@ struct Sched {
                 return PG_ERR_CAPACITY;  // admission refused: the queue is full
             r.ticket = next_ticket++;
             r.submitted = std::chrono::steady_clock::now();
+            if (r.kind == 0) r.precision = precision;
             queue.push_back(r);
         }
         cv_work.notify_one();
@@ -321,7 +324,7 @@ pg_status run_queries(pg_ctx *ctx, pg_index *index, int d, const Group &g) {
         at += r.rows;
     }
     PG_TRY(pg_search(ctx, index, Q.p, total, k, g.reqs[0].beam, g.reqs[0].upper_beam, 0,
-                     PG_PREC_FP32, ids.p, dist.p));
+                     g.reqs[0].precision, ids.p, dist.p));
     at = 0;
     for (const Req &r : g.reqs) {
         PG_TRY_CUDA(ctx, cudaMemcpyAsync(r.out_ids, ids.p + at * k, (size_t)(r.rows * k) * 4,
@@ -344,7 +347,7 @@ pg_status run_insert(pg_server *s, const Req &r) {
 
 bool same_query_shape(const Req &a, const Req &b) {
     return a.kind == 0 && b.kind == 0 && a.k == b.k && a.beam == b.beam &&
-           a.upper_beam == b.upper_beam;
+           a.upper_beam == b.upper_beam && a.precision == b.precision;
 }
 
 void release_slots(pg_server *s) {
@@ -468,6 +471,16 @@ extern "C" pg_status pg_serve_set_queue_limit(pg_server *s, int64_t limit) {
     if (!s || limit < 0) return PG_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(s->sched.mu);
     s->sched.queue_limit = limit;
+    return PG_OK;
+}
+
+extern "C" pg_status pg_serve_set_precision(pg_server *s, pg_precision precision) {
+    if (!s) return PG_ERR_INVALID_ARG;
+    if (precision != PG_PREC_FP32 && precision != PG_PREC_BF16_SCREEN &&
+        precision != PG_PREC_FP8_SCREEN)
+        return PG_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->sched.mu);
+    s->sched.precision = precision;
     return PG_OK;
 }
 
