@@ -331,12 +331,24 @@ def run_ours(args):
                           "recall_flat_entry": recall(flat)})
         ok = [c for c in curve if c["recall"] >= 0.95]
         best = ok[0] if ok else curve[-1]
+        # FP8-screened queries (E4M3 rows, FP32 re-measure of the final pool)
+        fp8 = []
+        for beam in w["beams"]:
+            idx.search(Qd, w["k"], beam, precision="fp8")
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ids, _ = idx.search(Qd, w["k"], beam, precision="fp8")
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / 1e3
+            fp8.append({"beam": beam, "recall": recall(ids), "qps": nq / t})
         lat = []
         for i in range(min(200, nq)):
             t0 = time.perf_counter()
             idx.search(Qd[i:i + 1], w["k"], best["beam"])
             lat.append((time.perf_counter() - t0) * 1e3)
-        qres = {"curve": curve, "beam_at_0.95": best["beam"] if ok else None,
+        qres = {"curve": curve, "fp8_screen_curve": fp8,
+                "beam_at_0.95": best["beam"] if ok else None,
                 "recall": best["recall"], "qps": best["qps"],
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                 "latency": "single-query requests, host wall time per call incl. launch + sync"}
@@ -347,8 +359,9 @@ def run_ours(args):
     # queries on four workers, host buffers), request sizes drawn from
     # {1, 8, 32, 128, 1024} queries (k = 10, beam 48, upper_beam 16), two
     # insertion batches of 1% of n after requests 100 and 200 of 300:
-    #   saturated: all 300 requests queued at once, with four workers and
-    #   with one (same mix), for requests/s and queries/s;
+    #   saturated: all 300 requests queued at once, with four workers, with
+    #   one, and with four workers and FP8-screened queries, for requests/s
+    #   and queries/s;
     #   poisson: the same mix arriving as a Poisson process at 70% of the
     #   four-worker saturated request rate, for the latency of each request
     #   from submission to completion (p50 / p99, host clock);
@@ -356,10 +369,10 @@ def run_ours(args):
     serve = {}
     if not args.no_serve:
         ins = max(100, n // 100)
-        X = synthetic.inserts(WORKLOAD, 6 * ins)
+        X = synthetic.inserts(WORKLOAD, 8 * ins)
         Qh = Q if isinstance(Q, np.ndarray) else np.asarray(Q)
         idx = pg.Index.build_rng(ctx, Dd, **params)
-        idx.reserve(n + 6 * ins)
+        idx.reserve(n + 8 * ins)
         rs = np.random.default_rng(7)
         sizes = rs.choice([1, 8, 32, 128, 1024], size=300)
         cursor = {"q": 0, "x": 0}
@@ -392,15 +405,16 @@ def run_ours(args):
 
         barrier()
         sat = {}
-        for slots in (SERVE_SLOTS, 1):
+        for slots, prec in ((SERVE_SLOTS, "fp32"), (1, "fp32"), (SERVE_SLOTS, "fp8")):
             srv = pg.Server(idx, max_batch=1024, slots=slots)
+            srv.set_precision(prec)
             secs, nqs, _ = run_stream(srv)
             st = srv.stats()
             srv.stop()
-            sat[slots] = {"seconds": secs, "requests_per_s": len(sizes) / secs,
-                          "queries_per_s": nqs / secs, "groups": int(st["batches"]),
-                          "max_in_flight": int(st["max_in_flight"])}
-        rate = 0.7 * sat[SERVE_SLOTS]["requests_per_s"]
+            sat[(slots, prec)] = {"seconds": secs, "requests_per_s": len(sizes) / secs,
+                                  "queries_per_s": nqs / secs, "groups": int(st["batches"]),
+                                  "max_in_flight": int(st["max_in_flight"])}
+        rate = 0.7 * sat[(SERVE_SLOTS, "fp32")]["requests_per_s"]
         gaps = np.cumsum(rs.exponential(1.0 / rate, size=len(sizes)))
         srv = pg.Server(idx, max_batch=1024, slots=SERVE_SLOTS)
         secs, nqs, lat = run_stream(srv, gaps)
@@ -415,7 +429,9 @@ def run_ours(args):
         idx.close()
         serve = {"slots": SERVE_SLOTS, "requests": len(sizes), "queries": int(sizes.sum()),
                  "inserted_per_stream": 2 * ins,
-                 "saturated": sat[SERVE_SLOTS], "saturated_one_worker": sat[1],
+                 "saturated": sat[(SERVE_SLOTS, "fp32")],
+                 "saturated_one_worker": sat[(1, "fp32")],
+                 "saturated_fp8_screen": sat[(SERVE_SLOTS, "fp8")],
                  "poisson": {"rate_requests_per_s": rate, "seconds": secs,
                              "queries_per_s": nqs / secs, "groups": int(st["batches"]),
                              "max_in_flight": int(st["max_in_flight"]),

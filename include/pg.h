@@ -67,8 +67,9 @@ typedef enum { PG_METRIC_L2SQ = 0, PG_METRIC_COSINE = 1, PG_METRIC_IP = 2 } pg_m
  * PG_PREC_FP8_SCREEN: queries only (pg_search, pg_search_host, serving):
  * the base-layer beam search ranks by distances from an FP8 E4M3 copy of
  * the index's points (one FP32 scale per row, the row's largest magnitude
- * mapped to 448; the cross term from the FP8 row, exact FP32 norms for
- * L2), then the final pool is re-measured in FP32 and its k best returned:
+ * mapped to 448; squared L2 to the decoded row, or the chord from its dot
+ * product with the query), then the final pool is re-measured in FP32 and
+ * its k best returned:
  * returned distances are FP32, membership is approximate (recall).  Every
  * other entry point refuses it with PG_ERR_INVALID_ARG. */
 typedef enum {
@@ -391,11 +392,11 @@ pg_status pg_index_file_check(const char *path, int64_t *n, int32_t *d, int32_t 
 /* The FP8 rows that PG_PREC_FP8_SCREEN searches use, for n DEVICE rows
  * D [n][d]: scale[i] = max_j |D[i][j]| / 448 in FP32 (1 for a zero row),
  * codes[i][j] = E4M3 (OCP FP8, 1-4-3 bits, bias 7, no infinities) of
- * D[i][j] * (1 / scale[i]) rounded to nearest even and saturated at +-448,
- * norm[i] = sum_j D[i][j]^2 in FP32.  Caller DEVICE buffers codes [n][d],
- * scale [n], norm [n].  Synchronous. */
+ * D[i][j] * (1 / scale[i]) (both steps in FP32) rounded to nearest even
+ * and saturated at +-448.  Caller DEVICE buffers codes [n][d], scale [n].
+ * Synchronous. */
 pg_status pg_encode_fp8(pg_ctx *ctx, const float *D, int64_t n, int32_t d, uint8_t *codes,
-                        float *scale, float *norm);
+                        float *scale);
 
 /* -------------------------------------------------------------- serving */
 

@@ -483,18 +483,16 @@ def fp8_e4m3_encode(values) -> np.ndarray:
 
 def fp8_rows(D):
     """FP8 rows of the screened queries: per row scale = max|x| / 448 in
-    float32 (1 for a zero row), codes of x * float32(1 / scale) (both steps
-    in float32), and the squared norm in FP64."""
+    float32 (1 for a zero row) and the codes of x * float32(1 / scale) (both
+    steps in float32)."""
     D = np.asarray(D, np.float32)
     n, d = D.shape
     codes = np.empty((n, d), np.uint8)
     scale = np.empty(n, np.float32)
-    norm = np.empty(n, np.float64)
     for r in range(n):
         mx = np.float32(np.max(np.abs(D[r]))) if d else np.float32(0)
         sc = np.float32(mx / np.float32(448.0)) if mx > 0 else np.float32(1.0)
         inv = np.float32(np.float32(1.0) / sc)
         codes[r] = fp8_e4m3_encode((D[r] * inv).astype(np.float32))
         scale[r] = sc
-        norm[r] = float(np.sum(D[r].astype(np.float64) ** 2))
-    return codes, scale, norm
+    return codes, scale

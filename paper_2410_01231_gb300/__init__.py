@@ -96,7 +96,7 @@ _sig("pg_serve_set_queue_limit", C.c_int, [P, i64])
 _sig("pg_serve_set_budget", C.c_int, [P, i64])
 _sig("pg_serve_latency", C.c_int, [P, i64, P])
 _sig("pg_serve_set_precision", C.c_int, [P, C.c_int])
-_sig("pg_encode_fp8", C.c_int, [P, P, i64, i32, P, P, P])
+_sig("pg_encode_fp8", C.c_int, [P, P, i64, i32, P, P])
 _sig("pg_selftest_wait_timeout", C.c_int, [P, dbl])
 _sig("pg_index_params", C.c_int, [P, P, P])
 _sig("pg_index_save", C.c_int, [P, P, C.c_char_p])
@@ -236,15 +236,14 @@ def index_file_check(path: str) -> dict:
 
 def encode_fp8(ctx: Context, D: torch.Tensor):
     """FP8 E4M3 rows of D as the screened search uses them (pg_encode_fp8):
-    (codes uint8 [n][d], scale float32 [n], norm float32 [n])."""
+    (codes uint8 [n][d], scale float32 [n])."""
     D = _dev(D, torch.float32, "D")
     n, d = D.shape
     codes = torch.empty((n, d), dtype=torch.uint8, device=D.device)
     scale = torch.empty(n, dtype=torch.float32, device=D.device)
-    norm = torch.empty(n, dtype=torch.float32, device=D.device)
-    ctx._check(_lib.pg_encode_fp8(ctx.handle, _ptr(D), n, d, _ptr(codes), _ptr(scale),
-                                  _ptr(norm)), "pg_encode_fp8")
-    return codes, scale, norm
+    ctx._check(_lib.pg_encode_fp8(ctx.handle, _ptr(D), n, d, _ptr(codes), _ptr(scale)),
+               "pg_encode_fp8")
+    return codes, scale
 
 
 def build_knn(ctx: Context, D: torch.Tensor, K: int, metric="l2", precision="fp32"):

@@ -402,22 +402,19 @@ static pg_status index_f8(pg_ctx *ctx, const pg_index *idx, F8Rows *out) {
     if (idx->f8_cap < cap) {
         cudaFree(idx->f8);
         cudaFree(idx->f8_scale);
-        cudaFree(idx->f8_norm);
         idx->f8 = nullptr;
-        idx->f8_scale = idx->f8_norm = nullptr;
+        idx->f8_scale = nullptr;
         idx->f8_rows = idx->f8_cap = 0;
         PG_TRY_CUDA(ctx, cudaMalloc(&idx->f8, (size_t)(cap * idx->d)));
         PG_TRY_CUDA(ctx, cudaMalloc(&idx->f8_scale, (size_t)cap * 4));
-        PG_TRY_CUDA(ctx, cudaMalloc(&idx->f8_norm, (size_t)cap * 4));
         idx->f8_cap = cap;
     }
     if (idx->f8_rows < idx->n) {
-        PG_TRY(pg_make_f8(ctx, idx->D, idx->f8_rows, idx->n, idx->d, idx->f8, idx->f8_scale,
-                          idx->f8_norm));
+        PG_TRY(pg_make_f8(ctx, idx->D, idx->f8_rows, idx->n, idx->d, idx->f8, idx->f8_scale));
         PG_TRY_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
         idx->f8_rows = idx->n;
     }
-    *out = F8Rows{idx->f8, idx->f8_scale, idx->f8_norm};
+    *out = F8Rows{idx->f8, idx->f8_scale};
     return PG_OK;
 }
 

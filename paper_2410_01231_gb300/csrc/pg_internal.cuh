@@ -72,13 +72,11 @@ struct pg_index {
     mutable std::mutex f8_mu;
     mutable uint8_t *f8 = nullptr;      // [f8_cap][d]
     mutable float *f8_scale = nullptr;  // [f8_cap] value of 1.0 in the FP8 row
-    mutable float *f8_norm = nullptr;   // [f8_cap] squared FP32 norms
     mutable int64_t f8_rows = 0, f8_cap = 0;
     ~pg_index() {
         cudaFree(owned);
         cudaFree(f8);
         cudaFree(f8_scale);
-        cudaFree(f8_norm);
         for (auto &l : layers) {
             cudaFree(l.gid);
             cudaFree(l.nbr);
@@ -92,7 +90,6 @@ struct pg_index {
 struct F8Rows {
     const uint8_t *q8;    // [n][d] E4M3 codes of x / scale
     const float *scale;   // [n]
-    const float *norm;    // [n] squared FP32 norms
 };
 
 // Batched beam search (Algorithm 1), one warp per query: self mode (Q null,
@@ -217,9 +214,9 @@ pg_status pg_data_facts(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_me
 bool pg_u8_usable(const DataFacts &f, pg_metric metric, int d, pg_precision precision);
 pg_status pg_make_u8(pg_ctx *ctx, const float *D, int64_t n, int32_t d, Scratch<uint8_t> &out);
 // FP8 E4M3 rows r0..r1-1 of D: codes of x / scale (scale = max|x| / 448,
-// 1 for a zero row) and the squared FP32 norm of x (queued on ctx's stream)
+// 1 for a zero row), queued on ctx's stream
 pg_status pg_make_f8(pg_ctx *ctx, const float *D, int64_t r0, int64_t r1, int32_t d, uint8_t *q8,
-                     float *scale, float *norm);
+                     float *scale);
 // build-like entry points take FP32 or BF16 screening only
 inline bool pg_build_precision(pg_precision p) {
     return p == PG_PREC_FP32 || p == PG_PREC_BF16_SCREEN;

@@ -22,9 +22,9 @@
 // lossy table therefore changes the work done, never the result.
 //
 // FP8-screened queries rank the expansion candidates by distances from the
-// index's FP8 E4M3 rows (cross term scale * sum e_i q_i in FP32, exact FP32
-// norms for L2); at the end the whole pool is re-measured in FP32 and the
-// k best by (s, id) are returned.
+// index's FP8 E4M3 rows (decoded row scale * e against the FP32 query: the
+// squared L2 distance, or the chord from the dot product); at the end the
+// whole pool is re-measured in FP32 and the k best by (s, id) are returned.
 #include <cuda_fp8.h>
 
 #include <climits>
@@ -42,7 +42,7 @@ struct SearchParams {
     const float *D;
     const uint8_t *D8;  // byte shadow of D (exact data, self mode) or nullptr
     const uint8_t *F8;  // FP8 E4M3 rows of D (screened queries) or nullptr
-    const float *f8scale, *f8norm;
+    const float *f8scale;
     int64_t n;
     int d;
     int metric;
@@ -88,63 +88,61 @@ __device__ __forceinline__ unsigned hslot(int v, int hbits) {
     return ((unsigned)v * 2654435761u) >> (32 - hbits);
 }
 
-// sum of e_i q_i over one FP8 row (codes of 16 elements per 16-byte chunk),
-// by a team of eight lanes
-__device__ __forceinline__ float team8_dot_f8_16(const float4 *__restrict__ q,
-                                                 const uint4 *__restrict__ x, int nch16, int li) {
+// Two E4M3 codes (the low and high byte of a 16-bit word) as floats.
+__device__ __forceinline__ float2 f8x2_to_float2(unsigned w16) {
+    const __half2 h(__nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)w16, __NV_E4M3));
+    return __half22float2(h);
+}
+
+// One FP8 row against the query, by a team of eight lanes: kL2 sums
+// (sc e_i - q_i)^2 -- the squared distance to the decoded row, whose error
+// grows with |x - q| and not with |x| --, otherwise sums e_i q_i.  Rows whose
+// width is a multiple of 16 are read 16 codes a load, others 4 codes a load.
+template <bool kL2>
+__device__ __forceinline__ float team8_f8(const float4 *__restrict__ q,
+                                          const uint8_t *__restrict__ row, int d, int li,
+                                          float sc) {
     float acc = 0.f;
-    for (int c = li; c < nch16; c += 8) {
-        const uint4 w = __ldg(x + c);
-        const unsigned words[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {
-            const float4 qa = q[c * 4 + h];
-            const __half2 lo(__nv_cvt_fp8x2_to_halfraw2(
-                (__nv_fp8x2_storage_t)(words[h] & 0xffffu), __NV_E4M3));
-            const __half2 hi(__nv_cvt_fp8x2_to_halfraw2(
-                (__nv_fp8x2_storage_t)(words[h] >> 16), __NV_E4M3));
-            const float2 a = __half22float2(lo), b = __half22float2(hi);
+    auto four = [&](unsigned w, const float4 qa) {
+        const float2 a = f8x2_to_float2(w & 0xffffu), b = f8x2_to_float2(w >> 16);
+        if (kL2) {
+            const float t0 = fmaf(a.x, sc, -qa.x), t1 = fmaf(a.y, sc, -qa.y);
+            const float t2 = fmaf(b.x, sc, -qa.z), t3 = fmaf(b.y, sc, -qa.w);
+            acc = fmaf(t0, t0, acc);
+            acc = fmaf(t1, t1, acc);
+            acc = fmaf(t2, t2, acc);
+            acc = fmaf(t3, t3, acc);
+        } else {
             acc = fmaf(a.x, qa.x, acc);
             acc = fmaf(a.y, qa.y, acc);
             acc = fmaf(b.x, qa.z, acc);
             acc = fmaf(b.y, qa.w, acc);
         }
+    };
+    if ((d & 15) == 0) {
+        const uint4 *x = reinterpret_cast<const uint4 *>(row);
+        for (int c = li; c < (d >> 4); c += 8) {
+            const uint4 w = __ldg(x + c);
+            four(w.x, q[c * 4 + 0]);
+            four(w.y, q[c * 4 + 1]);
+            four(w.z, q[c * 4 + 2]);
+            four(w.w, q[c * 4 + 3]);
+        }
+    } else {
+        const unsigned *x = reinterpret_cast<const unsigned *>(row);
+        for (int c = li; c < (d >> 2); c += 8) four(__ldg(x + c), q[c]);
     }
     return warp_sum8(acc);
 }
 
-// the same for rows whose width is not a multiple of 16 (4 elements a load)
-__device__ __forceinline__ float team8_dot_f8_4(const float4 *__restrict__ q,
-                                                const unsigned *__restrict__ x, int nch4, int li) {
-    float acc = 0.f;
-    for (int c = li; c < nch4; c += 8) {
-        const unsigned w = __ldg(x + c);
-        const float4 qa = q[c];
-        const __half2 lo(__nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w & 0xffffu),
-                                                     __NV_E4M3));
-        const __half2 hi(__nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w >> 16),
-                                                     __NV_E4M3));
-        const float2 a = __half22float2(lo), b = __half22float2(hi);
-        acc = fmaf(a.x, qa.x, acc);
-        acc = fmaf(a.y, qa.y, acc);
-        acc = fmaf(b.x, qa.z, acc);
-        acc = fmaf(b.y, qa.w, acc);
-    }
-    return warp_sum8(acc);
-}
-
-// screened distance of FP8 row v to the query (squared L2 from the norms
-// and the cross term, or the chord 2 - 2<x, q> of unit rows)
-__device__ __forceinline__ float team8_dist_f8(const SearchParams &P, const float4 *q, float qn,
-                                               int v, int li) {
-    const int d = P.d;
-    const uint8_t *row = P.F8 + (int64_t)v * d;
-    const float dot = (d & 15) == 0
-                          ? team8_dot_f8_16(q, reinterpret_cast<const uint4 *>(row), d >> 4, li)
-                          : team8_dot_f8_4(q, reinterpret_cast<const unsigned *>(row), d >> 2, li);
-    const float cross = __ldg(P.f8scale + v) * dot;
-    if (P.metric == 0) return fmaxf(__ldg(P.f8norm + v) + qn - 2.f * cross, 0.f);
-    return fmaxf(2.f - 2.f * cross, 0.f);
+// screened distance of FP8 row v to the query: squared L2 to the decoded
+// row, or the chord 2 - 2 sc <e, q> of unit rows
+__device__ __forceinline__ float team8_dist_f8(const SearchParams &P, const float4 *q, int v,
+                                               int li) {
+    const uint8_t *row = P.F8 + (int64_t)v * P.d;
+    const float sc = __ldg(P.f8scale + v);
+    if (P.metric == 0) return team8_f8<true>(q, row, P.d, li, sc);
+    return fmaxf(2.f - 2.f * sc * team8_f8<false>(q, row, P.d, li, sc), 0.f);
 }
 
 template <bool kF8>
@@ -175,12 +173,6 @@ __device__ void search_one(const SearchParams &P, int64_t qi, unsigned char *ws,
     }
     for (int h = lane; h < H; h += 32) htab[h] = -1;
     constexpr bool f8 = kF8;  // FP8 rows (P.F8) in use
-    float qn = 0.f;
-    if (f8) {
-        __syncwarp();
-        for (int c = lane; c < d; c += 32) qn = fmaf(q[c], q[c], qn);
-        for (int o = 16; o; o >>= 1) qn += __shfl_xor_sync(0xffffffffu, qn, o);
-    }
     int start = P.self ? (int)qi : P.starts[qi];
     bool bad = start < 0 || start >= P.n;
     if (bad) {
@@ -192,7 +184,7 @@ __device__ void search_one(const SearchParams &P, int64_t qi, unsigned char *ws,
     if (D8) {
         s0 = team8_dist_u8(q16, reinterpret_cast<const uint4 *>(D8 + (int64_t)start * d), d >> 4, li);
     } else if (f8) {
-        s0 = team8_dist_f8(P, q4, qn, start, li);
+        s0 = team8_dist_f8(P, q4, start, li);
     } else {
         s0 = team8_dist(q4, reinterpret_cast<const float4 *>(P.D + (int64_t)start * d), nch, li,
                         P.metric);
@@ -260,7 +252,7 @@ __device__ void search_one(const SearchParams &P, int64_t qi, unsigned char *ws,
             } else if (f8) {
                 for (int b0 = 0; b0 < cnt; b0 += 4) {
                     int i = b0 + team;
-                    float s = team8_dist_f8(P, q4, qn, ni[i < cnt ? i : 0], li);
+                    float s = team8_dist_f8(P, q4, ni[i < cnt ? i : 0], li);
                     if (li == 0 && i < cnt) nd[i] = s;
                 }
             } else {
@@ -437,10 +429,10 @@ __global__ void __launch_bounds__(SW * 32, 8) k_search(SearchParams P) {
         search_one<kF8>(P, qi, ws, n_exp, n_eval, n_rerank);
     }
     if (lane == 0) {
-        // algorithmic bytes: one row per evaluation (FP8 rows also their scale
-        // and norm), one adjacency row per expansion, one FP32 row per re-measure
+        // algorithmic bytes: one row per evaluation (FP8 rows also their
+        // scale), one adjacency row per expansion, one FP32 row per re-measure
         const unsigned long long row =
-            P.D8 ? (unsigned long long)P.d : P.F8 ? (unsigned long long)P.d + 8ull : 4ull * P.d;
+            P.D8 ? (unsigned long long)P.d : P.F8 ? (unsigned long long)P.d + 4ull : 4ull * P.d;
         atomicAdd(P.counters + CNT_SEARCH_EXP, n_exp);
         atomicAdd(P.counters + CNT_SEARCH_EVAL, n_eval);
         atomicAdd(P.counters + CNT_SEARCH_BYTES,
@@ -463,7 +455,6 @@ pg_status pg_search_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d, 
     P.D8 = self ? D8 : nullptr;
     P.F8 = !self && f8 ? f8->q8 : nullptr;
     P.f8scale = P.F8 ? f8->scale : nullptr;
-    P.f8norm = P.F8 ? f8->norm : nullptr;
     P.n = n;
     P.d = d;
     P.metric = metric == PG_METRIC_L2SQ ? 0 : 1;
@@ -514,50 +505,40 @@ pg_status pg_search_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d, 
 }
 
 // One warp per row: scale = max|x| / 448 (1 for a zero row), codes of
-// x / scale rounded to nearest E4M3 (saturating), squared FP32 norm.
+// x * (1 / scale) rounded to nearest E4M3 (saturating).
 __global__ void k_make_f8(const float *D, int64_t r0, int64_t r1, int d, uint8_t *q8,
-                          float *scale, float *norm) {
+                          float *scale) {
     const int lane = threadIdx.x & 31;
     const int64_t r = r0 + ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
     if (r >= r1) return;
     const float *x = D + r * d;
-    float mx = 0.f, nn = 0.f;
-    for (int c = lane; c < d; c += 32) {
-        const float v = x[c];
-        mx = fmaxf(mx, fabsf(v));
-        nn = fmaf(v, v, nn);
-    }
-    for (int o = 16; o; o >>= 1) {
-        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        nn += __shfl_xor_sync(0xffffffffu, nn, o);
-    }
+    float mx = 0.f;
+    for (int c = lane; c < d; c += 32) mx = fmaxf(mx, fabsf(x[c]));
+    for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     const float sc = mx > 0.f ? mx / 448.f : 1.f;
     const float inv = 1.f / sc;
     for (int c = lane; c < d; c += 32)
         q8[r * d + c] = (uint8_t)__nv_cvt_float_to_fp8(x[c] * inv, __NV_SATFINITE, __NV_E4M3);
-    if (lane == 0) {
-        scale[r] = sc;
-        norm[r] = nn;
-    }
+    if (lane == 0) scale[r] = sc;
 }
 
 pg_status pg_make_f8(pg_ctx *ctx, const float *D, int64_t r0, int64_t r1, int32_t d, uint8_t *q8,
-                     float *scale, float *norm) {
+                     float *scale) {
     if (r1 <= r0) return PG_OK;
     const int64_t warps = r1 - r0;
-    k_make_f8<<<(unsigned)((warps + 7) / 8), 256, 0, ctx->stream>>>(D, r0, r1, d, q8, scale, norm);
+    k_make_f8<<<(unsigned)((warps + 7) / 8), 256, 0, ctx->stream>>>(D, r0, r1, d, q8, scale);
     PG_LAUNCHED(ctx);
     return PG_OK;
 }
 
 extern "C" pg_status pg_encode_fp8(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
-                                   uint8_t *codes, float *scale, float *norm) {
+                                   uint8_t *codes, float *scale) {
     if (!ctx) return PG_ERR_INVALID_ARG;
-    if (!D || !codes || !scale || !norm) return pg_fail(ctx, PG_ERR_INVALID_ARG, "null pointer");
+    if (!D || !codes || !scale) return pg_fail(ctx, PG_ERR_INVALID_ARG, "null pointer");
     if (n < 0 || n >= INT_MAX) return pg_fail(ctx, PG_ERR_INVALID_ARG, "need 0 <= n < 2^31");
     if (d < 4 || d % 4 || d > 8192)
         return pg_fail(ctx, PG_ERR_INVALID_ARG, "need d % 4 == 0 and 4 <= d <= 8192");
-    PG_TRY(pg_make_f8(ctx, D, 0, n, d, codes, scale, norm));
+    PG_TRY(pg_make_f8(ctx, D, 0, n, d, codes, scale));
     return pg_sync_check(ctx, "pg_encode_fp8");
 }
 

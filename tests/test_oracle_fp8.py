@@ -69,8 +69,8 @@ def test_rows_scale_maps_the_largest_magnitude_to_448():
     rs = np.random.default_rng(4)
     D = rs.normal(0, 1, (20, 48)).astype(np.float32)
     D[3] = 0.0
-    codes, scale, norm = oracle.fp8_rows(D)
-    assert scale[3] == 1.0 and (codes[3] == 0).all() and norm[3] == 0.0
+    codes, scale = oracle.fp8_rows(D)
+    assert scale[3] == 1.0 and (codes[3] == 0).all()
     for r in range(20):
         if r == 3:
             continue
@@ -82,4 +82,3 @@ def test_rows_scale_maps_the_largest_magnitude_to_448():
         rec = oracle.fp8_e4m3_decode(codes[r]) * scale[r]
         tol = np.maximum(np.abs(D[r]) * 2.0 ** -4, 2.0 ** -10 * scale[r])
         assert (np.abs(rec - D[r]) <= tol * (1 + 1e-6)).all()
-        assert norm[r] == pytest.approx(float(np.sum(D[r].astype(np.float64) ** 2)), rel=1e-15)
