@@ -264,7 +264,10 @@ struct Sched {
         std::unique_lock<std::mutex> lk(mu);
         if (ticket < 1 || ticket >= next_ticket) return PG_ERR_INVALID_ARG;
         auto ready = [&] { return is_done(ticket); };
-        if (timeout_s > 0) cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), ready);
+        // at most a day per call: longer durations would overflow the clock
+        if (timeout_s > 0)
+            cv_done.wait_for(lk, std::chrono::duration<double>(std::min(timeout_s, 86400.0)),
+                             ready);
         *done = ready() ? 1 : 0;
         if (!*done) return PG_OK;
         auto it = failed.find(ticket);
