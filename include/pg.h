@@ -34,6 +34,14 @@
  * which the next synchronising call (or pg_ctx_sync) turns into
  * PG_ERR_DEVICE_CHECK.  pg_last_error() gives a one-line message.  No
  * exception crosses this boundary.
+ *
+ * Threads.  A context is used by one thread at a time.  Searches of one
+ * index (pg_search, pg_search_host) may run concurrently from several
+ * threads on different contexts, as the serving loop's workers do; builds,
+ * pruning and insertion set per-kernel launch attributes and are not made
+ * safe against each other across threads.  An index is not modified while
+ * it is searched: insertion and growth need exclusive use (the serving
+ * loop orders them).
  */
 #ifndef PG_H
 #define PG_H
