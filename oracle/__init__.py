@@ -424,6 +424,52 @@ def recall_at_k(found_ids, Q, D, k: int, metric: str = "l2", gt=None):
     return total / Q.shape[0]
 
 
+# ---------------------------------------------------- quality examination
+def quality_sample_size(n: int, eps: float, l: float = 1.0) -> int:
+    """Smallest n_s meeting the bound of Theorem 3 (Section 5.2, quality
+    examination): n_s >= (8 + 2 eps) l log n / eps^2, log the natural
+    logarithm (the Chernoff bound of the proof is an exponential), so that
+    the sample mean of r(u) is within eps / 2 of r(G) / n with probability at
+    least 1 - n^-l."""
+    if n < 2 or not eps > 0 or not l > 0:
+        raise ValueError("need n >= 2, eps > 0, l > 0")
+    return int(math.ceil((8.0 + 2.0 * eps) * l * math.log(n) / (eps * eps)))
+
+
+def kcna_recall(D, cand, k: int, metric: str = "l2", rows=None) -> np.ndarray:
+    """r(u) of Section 5.2 for the points ``rows`` (all by default): the
+    recall of the first k entries of the k-CNA list C(u) (row u of ``cand``,
+    ordered by (s, id), -1 for empty) against the exact k nearest
+    neighbours of u other than u.  Reading for ties, as in recall_at_k: an
+    entry counts when its FP64 distance to u is at most the exact k-th
+    distance; repeated or negative ids count once / never."""
+    D = _f32(D)
+    cand = np.asarray(cand)
+    rows = np.arange(D.shape[0]) if rows is None else np.asarray(rows, np.int64)
+    _, gt_d = knn(D, k, metric, rows=rows)
+    out = np.empty(rows.shape[0], np.float64)
+    for i, u in enumerate(rows):
+        kth = gt_d[i, k - 1]
+        seen, hit = set(), 0
+        for v in cand[u, :k]:
+            v = int(v)
+            if v < 0 or v == int(u) or v in seen:
+                continue
+            seen.add(v)
+            if dist(D[u], D[v], metric) <= kth:
+                hit += 1
+        out[i] = min(hit, k) / k
+    return out
+
+
+def estimate_quality(D, cand, k: int, n_s: int, seed: int, metric: str = "l2") -> float:
+    """The estimator of Section 5.2: the mean of r(u) over n_s points drawn
+    uniformly without replacement (numpy default_rng(seed))."""
+    n = np.asarray(D).shape[0]
+    sample = np.random.default_rng(seed).choice(n, size=min(n_s, n), replace=False)
+    return float(kcna_recall(D, cand, k, metric, rows=np.sort(sample)).mean())
+
+
 # --------------------------------------------------------------- FP8 rows
 # The number format of the FP8-screened queries (a precision form added on
 # top of the paper's search, which does not discuss number formats): OCP
