@@ -424,6 +424,66 @@ def recall_at_k(found_ids, Q, D, k: int, metric: str = "l2", gt=None):
     return total / Q.shape[0]
 
 
+# ------------------------------------------------------------------- K2P
+def _prune_scan(D, u: int, cand_row, R: int, ca: float, a60: bool, metric: str, reuse=None):
+    """One row of alpha-pruning in plain Python (the Algorithm 3 scan with
+    the Section 4.1 rule), optionally with the K2P reuse of Section 5.4:
+    ``reuse`` = (C_prev(u), N_prev(u)) as sets.  Returns (kept ids, number
+    of occlusion checks that needed s(v, w))."""
+    items = sorted({(dist(D[u], D[int(v)], metric), int(v)) for v in cand_row
+                    if int(v) >= 0 and int(v) != u})
+    out, out_s, checks = [], [], 0
+    for suv, v in items:
+        if len(out) >= R:
+            break
+        # K2P: v was a candidate and was kept last time, so no member kept
+        # then occluded it; only members new to the kept list are checked
+        skip_old = reuse is not None and v in reuse[0] and v in reuse[1]
+        occluded = False
+        for w, suw in zip(out, out_s):
+            if not suw < suv:
+                continue
+            if skip_old and w in reuse[1]:
+                continue
+            checks += 1
+            svw = dist(D[v], D[w], metric)
+            if not svw < suv:
+                continue
+            if a60 or (suw + svw) - suv < (2.0 * ca) * math.sqrt(suw * svw):
+                occluded = True
+                break
+        if not occluded:
+            out.append(v)
+            out_s.append(suv)
+    return out, checks
+
+
+def prune_k2p(D, cand_prev, kept_prev, cand, R: int, alpha_deg: float, metric: str = "l2"):
+    """K2P of Section 5.4: alpha-pruning of the k-CNA lists ``cand`` (rows of
+    C_i(u), -1 padded) that reuses the previous iteration's pruning of the
+    same points: for a candidate b that was in C_{i-1}(u) and was kept in
+    N_{i-1}(u) (``kept_prev``, the result of pruning C_{i-1}(u) with the same
+    rule), the members of N_{i-1}(u) are not checked again.  The pairwise
+    occlusion test depends only on u, b and the member, and the list order
+    only on s(u, .), so the kept lists are those of plain pruning.  Returns
+    (nbr [n][R], deg [n], checks with reuse, checks of the plain scan)."""
+    D = _f32(D)
+    n = D.shape[0]
+    ca, a60 = cos_alpha(alpha_deg), alpha_deg == 60.0
+    nbr = np.full((n, R), -1, np.int32)
+    deg = np.zeros(n, np.int32)
+    reused = plain = 0
+    for u in range(n):
+        prev = ({int(v) for v in cand_prev[u] if v >= 0}, {int(v) for v in kept_prev[u] if v >= 0})
+        out, c = _prune_scan(D, u, cand[u], R, ca, a60, metric, reuse=prev)
+        _, c0 = _prune_scan(D, u, cand[u], R, ca, a60, metric)
+        nbr[u, :len(out)] = out
+        deg[u] = len(out)
+        reused += c
+        plain += c0
+    return nbr, deg, reused, plain
+
+
 # ---------------------------------------------------- quality examination
 def quality_sample_size(n: int, eps: float, l: float = 1.0) -> int:
     """Smallest n_s meeting the bound of Theorem 3 (Section 5.2, quality
