@@ -311,6 +311,12 @@ pg_status pg_search_host(pg_ctx *ctx, const pg_index *index, const float *Q, int
 
 void pg_index_destroy(pg_index *index);
 
+/* The layer of each point id 0..n-1 that pg_build_nswg (and insertion)
+ * assign, host only (no context, no device): l(u) = floor(-ln U / ln M)
+ * with U = ((z >> 11) + 1) 2^-53, z = SplitMix64(seed XOR u) (the
+ * exponentially decaying level draw of Algorithm 7).  host_levels [n]. */
+pg_status pg_levels(int64_t n, uint64_t seed, int32_t M, int32_t *host_levels);
+
 /* Shape of an index: number of layers, points, entry points (host outs). */
 pg_status pg_index_info(const pg_index *index, int32_t *n_layers, int64_t *n, int64_t *ep_top,
                         int64_t *ep_base);

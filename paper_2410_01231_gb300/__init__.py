@@ -97,6 +97,7 @@ _sig("pg_serve_set_budget", C.c_int, [P, i64])
 _sig("pg_serve_latency", C.c_int, [P, i64, P])
 _sig("pg_serve_set_precision", C.c_int, [P, C.c_int])
 _sig("pg_encode_fp8", C.c_int, [P, P, i64, i32, P, P])
+_sig("pg_levels", C.c_int, [i64, u64, i32, P])
 _sig("pg_selftest_wait_timeout", C.c_int, [P, dbl])
 _sig("pg_index_params", C.c_int, [P, P, P])
 _sig("pg_index_save", C.c_int, [P, P, C.c_char_p])
@@ -116,7 +117,7 @@ EXPORTS = ["pg_default_params", "pg_ctx_create", "pg_ctx_destroy", "pg_last_erro
            "pg_selftest_wait_timeout", "pg_index_params", "pg_index_save", "pg_index_load",
            "pg_index_file_check", "pg_serve_simulate",
            "pg_serve_set_budget", "pg_serve_latency", "pg_serve_set_precision",
-           "pg_encode_fp8"]
+           "pg_encode_fp8", "pg_levels"]
 
 
 class PGError(RuntimeError):
@@ -232,6 +233,15 @@ def index_file_check(path: str) -> dict:
     if st != 0:
         raise PGError(st, f"pg_index_file_check: {msg.value.decode()}")
     return dict(n=n.value, d=d.value, n_layers=nl.value)
+
+
+def levels(n: int, seed: int, M: int) -> np.ndarray:
+    """Layer of every point id as the NSWG build draws it (pg_levels, host only)."""
+    out = np.empty(n, np.int32)
+    st = _lib.pg_levels(n, seed, M, out.ctypes.data_as(C.c_void_p))
+    if st != 0:
+        raise PGError(st, "pg_levels")
+    return out
 
 
 def encode_fp8(ctx: Context, D: torch.Tensor):

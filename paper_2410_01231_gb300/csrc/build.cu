@@ -330,6 +330,12 @@ extern "C" pg_status pg_build_nswg(pg_ctx *ctx, const float *D, int64_t n, int32
     return build_common(ctx, D, n, d, params, false, out);
 }
 
+extern "C" pg_status pg_levels(int64_t n, uint64_t seed, int32_t M, int32_t *host_levels) {
+    if (n < 0 || M < 2 || (n > 0 && !host_levels)) return PG_ERR_INVALID_ARG;
+    for (int64_t i = 0; i < n; ++i) host_levels[i] = level_of(i, seed, M);
+    return PG_OK;
+}
+
 extern "C" void pg_index_destroy(pg_index *index) { delete index; }
 
 int pg_index_dim(const pg_index *index) { return index->d; }
