@@ -172,10 +172,15 @@ pg_status pg_ctx_counter(pg_ctx *ctx, const char *name, int64_t *value);
  * ids [n][K], dist [n][K] (FP32 value of s); rows with fewer than K other
  * points are padded with -1 / +inf.  1 <= K <= 256, d % 4 == 0.
  * PG_PREC_BF16_SCREEN runs the distance tiles on the tensor cores
- * (tcgen05, BF16 inputs, FP32 accumulation) when the BF16 copy of D and all
- * partial sums are exact (integer data with |x| <= 256 and d*(2^8)^2
- * sums below 2^24, L2, d <= 128, K <= 64); otherwise it runs the FP32
- * tiles, so the result never depends on the precision argument. */
+ * (tcgen05, BF16 inputs, FP32 accumulation).  When the BF16 copy of D and
+ * every partial sum are exact (integer rows with |x| <= 256 whose squared
+ * distances stay below 2^24, L2) the result equals the FP32 form's.  For
+ * other rows the tiles select the min(128, max(2K, K + 8)) BF16-nearest
+ * candidates of each row, which are re-measured in FP32 and cut to K:
+ * distances and order are FP32, membership at the K-th place can differ
+ * from the exact lists (measured by list recall).  K beyond the tile
+ * kernels' limit, or PG_PREC_FP32, runs the FP32 tiles (exact lists, FP64
+ * fix-up of near ties). */
 pg_status pg_build_knn(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
                        int32_t K, pg_precision precision, int32_t *ids, float *dist);
 
@@ -252,8 +257,8 @@ pg_status pg_medoid(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric
 pg_status pg_connect(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
                      int32_t *nbr, int32_t *deg, int32_t R, int64_t ep, int64_t *host_added);
 
-/* k-CNA acquisition by search on the refined graph (Algorithm 5 lines
- * 7-8): for every u, KANNSearch(G, u, L, L, u) of Algorithm 1; row u of
+/* k-CNA acquisition by search on the refined graph (the search step of
+ * Algorithm 5): for every u, KANNSearch(G, u, L, L, u) of Algorithm 1; row u of
  * cand [n][L] receives the final pool minus u, in (s, id) order, padded
  * with -1.  nbr [n][R] / deg [n] is the graph.  1 <= L <= 256, R <= 64. */
 pg_status pg_acquire_candidates(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
@@ -274,8 +279,8 @@ pg_status pg_search_graph(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_
 /* ----------------------------------------------------------------- builds */
 
 /* IterNSG with a fixed number of iterations (Algorithm 6 with the
- * OptKCNA iterations of Algorithm 5; final refinement as Algorithm 2 lines
- * 5-11).  With route_layers set, NSWG upper layers (Algorithm 7, i >= 1)
+ * OptKCNA iterations of Algorithm 5; final refinement with the refinement
+ * steps of Algorithm 2: pruning, reverse-edge union, connectivity).  With route_layers set, NSWG upper layers (Algorithm 7, i >= 1)
  * are added so that queries enter the graph near their target.  D stays
  * owned by the caller and must outlive the index.  Synchronous. */
 pg_status pg_build_rng(pg_ctx *ctx, const float *D, int64_t n, int32_t d,

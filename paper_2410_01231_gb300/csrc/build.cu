@@ -3,7 +3,7 @@
 // pg_build_rng: IterNSG with a fixed number of iterations (Algorithm 6),
 // each iteration one OptKCNA (Algorithm 5): alpha-prune C -> reverse-edge
 // union -> alpha-prune -> connect -> self-search for new C; then the final
-// refinement of Algorithm 2 (lines 5-11) at alpha_final.  The graph,
+// refinement steps of Algorithm 2 at alpha_final.  The graph,
 // vectors and candidate lists stay on the device for the whole build; the
 // host only reads scalars (the medoid id, connectivity progress).
 //
