@@ -280,9 +280,10 @@ pg_status pg_search_graph(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_
 
 /* IterNSG with a fixed number of iterations (Algorithm 6 with the
  * OptKCNA iterations of Algorithm 5; final refinement with the refinement
- * steps of Algorithm 2: pruning, reverse-edge union, connectivity).  With route_layers set, NSWG upper layers (Algorithm 7, i >= 1)
- * are added so that queries enter the graph near their target.  D stays
- * owned by the caller and must outlive the index.  Synchronous. */
+ * steps of Algorithm 2: pruning, reverse-edge union, connectivity).  With
+ * route_layers set, NSWG upper layers (Algorithm 7, i >= 1) are added so
+ * that queries enter the graph near their target.  D stays owned by the
+ * caller and must outlive the index.  Synchronous. */
 pg_status pg_build_rng(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
                        const pg_build_params *params, pg_index **out);
 
