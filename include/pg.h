@@ -199,7 +199,9 @@ pg_status pg_knn_query(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_met
  * s(v,w) < s(u,v) and angle(u,w,v) > alpha; the scan stops at R kept.
  * alpha_deg = 60 is RNG pruning (the angle clause is then implied).
  * Output nbr [n][R] in keep order (-1 padded), deg [n].  R in [1, 64];
- * rows longer than 16384 candidates return PG_ERR_CAPACITY.  host_stats
+ * rows longer than 16384 candidates return PG_ERR_CAPACITY.
+ * PG_PREC_BF16_SCREEN gathers byte rows when the rows are exact bytes (same
+ * lists as FP32); PG_PREC_FP8_SCREEN is refused.  host_stats
  * (host pointer, may be NULL) receives counters and makes the call
  * synchronous. */
 pg_status pg_prune(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
@@ -258,9 +260,11 @@ pg_status pg_connect(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metri
                      int32_t *nbr, int32_t *deg, int32_t R, int64_t ep, int64_t *host_added);
 
 /* k-CNA acquisition by search on the refined graph (the search step of
- * Algorithm 5): for every u, KANNSearch(G, u, L, L, u) of Algorithm 1; row u of
- * cand [n][L] receives the final pool minus u, in (s, id) order, padded
- * with -1.  nbr [n][R] / deg [n] is the graph.  1 <= L <= 256, R <= 64. */
+ * Algorithm 5): for every u, KANNSearch(G, u, L, L, u) of Algorithm 1; row
+ * u of cand [n][L] receives the final pool minus u, in (s, id) order, padded
+ * with -1.  nbr [n][R] / deg [n] is the graph.  1 <= L <= 256, R <= 64.
+ * PG_PREC_BF16_SCREEN gathers byte rows (a u8 copy of D) when the rows are
+ * exact bytes (same result as FP32); PG_PREC_FP8_SCREEN is refused. */
 pg_status pg_acquire_candidates(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
                                 pg_metric metric, const int32_t *nbr, const int32_t *deg,
                                 int32_t R, int32_t L, pg_precision precision, int32_t *cand);
@@ -269,7 +273,8 @@ pg_status pg_acquire_candidates(pg_ctx *ctx, const float *D, int64_t n, int32_t 
  * graph: query i starts at starts[i] (device, nq entries).  rows (device,
  * may be NULL) maps a point id to its adjacency row when the graph covers
  * a subset of D (a layer of a hierarchical index); NULL = row id.  Output
- * out_ids / out_dist [nq][k], padded with -1 / +inf.  1 <= k <= L <= 256. */
+ * out_ids / out_dist [nq][k], padded with -1 / +inf.  1 <= k <= L <= 256.
+ * precision: PG_PREC_FP32 or PG_PREC_BF16_SCREEN (both FP32 rows here). */
 pg_status pg_search_graph(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
                           const int32_t *nbr, const int32_t *deg, int32_t R,
                           const int32_t *rows, const float *Q, int64_t nq,
@@ -303,7 +308,9 @@ pg_status pg_build_nswg(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
  * upper_beam = 1 is the greedy routing of the paper); an index without
  * upper layers (or with PG_SEARCH_FLAT) starts at its medoid.
  * Q [nq][d] device; out [nq][k].  1 <= k <= beam <= 256,
- * 1 <= upper_beam <= 256. */
+ * 1 <= upper_beam <= 256.  precision: PG_PREC_FP8_SCREEN screens the
+ * base-layer search (see pg_precision); PG_PREC_FP32 and
+ * PG_PREC_BF16_SCREEN search FP32 rows. */
 pg_status pg_search(pg_ctx *ctx, const pg_index *index, const float *Q, int64_t nq, int32_t k,
                     int32_t beam, int32_t upper_beam, int32_t flags, pg_precision precision,
                     int32_t *out_ids, float *out_dist);
