@@ -428,6 +428,57 @@ def test_search_visited_policy_does_not_change_the_pool():
         assert (a[0] == b[0]).all() and (a[1] == b[1]).all()
 
 
+def _kann_search_literal(D, nbr, deg, q, starts, k, L):
+    """Algorithm 1 written out with Python containers and exact integer
+    distances: the pool holds (s, id) pairs sorted ascending and cut to L;
+    the first entry not yet expanded is expanded next; a node is evaluated
+    once (visited set) and an evicted node never comes back."""
+    pool = sorted((exact_s(q, D[e]), int(e)) for e in starts)[:L]
+    visited = {int(e) for e in starts}
+    expanded = set()
+    while True:
+        nxt = next((v for _, v in pool if v not in expanded), None)
+        if nxt is None:
+            break
+        expanded.add(nxt)
+        for w in nbr[nxt][:deg[nxt]]:
+            w = int(w)
+            if w < 0 or w in visited:
+                continue
+            visited.add(w)
+            pool.append((exact_s(q, D[w]), w))
+        pool = sorted(pool)[:L]
+    out = [v for _, v in pool[:k]]
+    return out + [-1] * (k - len(out))
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_search_equals_a_literal_algorithm1_on_random_graphs(seed):
+    """Tiny random directed graphs (uneven degrees, -1 padding, many exact
+    ties from small integer values), one or several entry points, random
+    k <= L: the C oracle's search returns the literal restatement's lists."""
+    rs = np.random.default_rng(100 + seed)
+    n, d, R = int(rs.integers(5, 60)), int(rs.integers(1, 5)), int(rs.integers(1, 7))
+    D = int_data(n, d, 200 + seed, hi=5)
+    nq = 12
+    Q = int_data(nq, d, 300 + seed, hi=5)
+    nbr = np.full((n, R), -1, np.int32)
+    deg = rs.integers(0, R + 1, size=n).astype(np.int32)
+    for u in range(n):
+        nbr[u, :deg[u]] = rs.choice(n, size=deg[u], replace=True)
+    width = int(rs.integers(1, 4))
+    starts = np.array([rs.choice(n, size=min(width, n), replace=False) for _ in range(nq)],
+                      np.int32)
+    L = int(rs.integers(1, 12))
+    k = int(rs.integers(1, L + 1))
+    ids, ds = oracle.search(D, nbr, deg, Q, starts, k, L)
+    for i in range(nq):
+        want = _kann_search_literal(D, nbr, deg, Q[i], starts[i], k, L)
+        assert ids[i].tolist() == want, (seed, i)
+        got = [exact_s(Q[i], D[v]) for v in want if v >= 0]
+        assert ds[i][:len(got)].tolist() == got
+
+
 def test_acquire_on_complete_graph_is_exact_knn_minus_self():
     D = int_data(30, 3, 19, hi=7)
     n = 30
