@@ -372,6 +372,65 @@ def test_connect_reaches_everything_on_a_real_build():
     assert (out_deg <= 16).all()
 
 
+def _connect_literal(D, nbr, deg, ep, R):
+    """The connectivity reading written out with Python sets and exact
+    integer distances: S = reachable from ep; while some node is unreached,
+    r = the smallest unreached id, p = argmin over reached x with a free
+    slot of (s(x, r), x), append r to p's list, add what r reaches to S.
+    Returns (adjacency lists, added) or None when no reached node is free."""
+    n = len(D)
+    adj = [list(map(int, nbr[u][:deg[u]])) for u in range(n)]
+
+    def grow(S, start):
+        stack = [start]
+        S.add(start)
+        while stack:
+            v = stack.pop()
+            for w in adj[v]:
+                if w >= 0 and w not in S:
+                    S.add(w)
+                    stack.append(w)
+
+    S = set()
+    grow(S, ep)
+    added = 0
+    while len(S) < n:
+        r = min(set(range(n)) - S)
+        free = [x for x in S if len(adj[x]) < R]
+        if not free:
+            return None
+        p = min(free, key=lambda x: (exact_s(D[x], D[r]), x))
+        adj[p].append(r)
+        added += 1
+        grow(S, r)
+    return adj, added
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_connect_equals_its_literal_reading_on_random_graphs(seed):
+    """Random sparse directed graphs (many components, small integer rows
+    with ties): the C oracle's connectivity step adds exactly the literal
+    reading's edges, or refuses exactly when it does."""
+    rs = np.random.default_rng(500 + seed)
+    n, R = int(rs.integers(4, 70)), int(rs.integers(1, 5))
+    D = int_data(n, 3, 600 + seed, hi=6)
+    nbr = np.full((n, R), -1, np.int32)
+    deg = rs.integers(0, R + 1, size=n).astype(np.int32)
+    deg[rs.random(n) < 0.5] = 0  # many isolated nodes
+    for u in range(n):
+        nbr[u, :deg[u]] = rs.choice(n, size=deg[u], replace=True)
+    ep = int(rs.integers(0, n))
+    want = _connect_literal(D, nbr, deg, ep, R)
+    if want is None:
+        assert oracle.connect(D, nbr, deg, ep)[2] < 0  # refused
+        return
+    adj, added = want
+    out_nbr, out_deg, got_added = oracle.connect(D, nbr, deg, ep)
+    assert got_added == added
+    for u in range(n):
+        assert out_nbr[u, :out_deg[u]].tolist() == adj[u], (seed, u)
+
+
 # --------------------------------------------------------------------------
 # beam search
 # --------------------------------------------------------------------------
