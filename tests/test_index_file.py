@@ -4,7 +4,8 @@ layout that include/pg.h documents.  A valid file is accepted; each kind of
 damage (checksum, truncation, trailing bytes, foreign magic, version or byte
 order, an out-of-range or non-member neighbour, a degree above R, upper
 layers that are not ascending subsets of the layer below, a top entry point
-outside the top layer) is refused with the documented status."""
+outside the top layer) is refused with the documented status, and so is
+every one of 2,000 random corruptions."""
 import struct
 
 import numpy as np
@@ -174,3 +175,35 @@ def test_layer_shapes(tmp_path):
     ix = tiny_index()
     refused(tmp_path, encode(ix, counts=[11, 6]), INVALID, "shape of layer 0")
     refused(tmp_path, encode(ix, counts=[12, 13]), INVALID, "shape of layer 1")
+
+
+def test_random_damage_is_always_refused(tmp_path):
+    """2,000 random corruptions of a valid file (bit flips, byte runs,
+    truncation, extension, spliced headers): each is refused with a status,
+    never accepted and never a crash or a huge allocation (the size check
+    comes before any array is read)."""
+    good = encode(tiny_index())
+    rs = np.random.default_rng(77)
+    p = tmp_path / "fz.pgi"
+    for i in range(2000):
+        b = bytearray(good)
+        kind = i % 5
+        if kind == 0:  # one bit
+            j = int(rs.integers(0, len(b)))
+            b[j] ^= 1 << int(rs.integers(0, 8))
+        elif kind == 1:  # a run of random bytes
+            j = int(rs.integers(0, len(b) - 8))
+            b[j:j + 8] = rs.integers(0, 256, 8, dtype=np.uint8).tobytes()
+        elif kind == 2:  # truncation
+            b = b[:int(rs.integers(0, len(b)))]
+        elif kind == 3:  # extension
+            b += rs.integers(0, 256, int(rs.integers(1, 64)), dtype=np.uint8).tobytes()
+        else:  # a huge count or width in the header region
+            j = int(rs.integers(16, 200))
+            b[j:j + 8] = struct.pack("<q", int(rs.integers(1, 2**62)))
+        if bytes(b) == good:
+            continue
+        p.write_bytes(bytes(b))
+        with pytest.raises(pg.PGError) as e:
+            pg.index_file_check(str(p))
+        assert e.value.status in (IO, INVALID), (i, e.value.status)
