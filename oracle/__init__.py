@@ -59,6 +59,8 @@ def _get():
         lib.or_medoid.argtypes = [P, i64, i32, i32, P]
         lib.or_connect.restype = i64
         lib.or_connect.argtypes = [P, i64, i32, i32, P, P, i32, i64]
+        lib.or_connect_replace.restype = i64
+        lib.or_connect_replace.argtypes = [P, i64, i32, i32, P, P, i32, i64, P]
         lib.or_search.restype = i32
         lib.or_search.argtypes = [P, i64, i32, i32, P, P, i32, P, P, i64, P, i32, i32, i32,
                                   i32, P, P, P]
@@ -165,6 +167,23 @@ def connect(D, nbr, deg, ep: int, metric: str = "l2"):
     n, R = nbr.shape
     added = _get().or_connect(_p(D), n, D.shape[1], METRICS[metric], _p(nbr), _p(deg), R, ep)
     return nbr, deg, int(added)
+
+
+def connect_replace(D, nbr, deg, ep: int, metric: str = "l2"):
+    """The connectivity step with edge replacement (a reading for graphs whose
+    reached nodes are all full; the builds use ``connect``): when no reached
+    node has a free slot, the nearest reached node with an original edge
+    gives up its last one for the unreached node, and reachability is
+    recomputed.  Returns copies and (edges added, of which replacements);
+    edges added is negative when nothing can be linked."""
+    D = _f32(D)
+    nbr = np.array(nbr, np.int32, copy=True)
+    deg = np.array(deg, np.int32, copy=True)
+    n, R = nbr.shape
+    rep = np.zeros(1, np.int64)
+    added = _get().or_connect_replace(_p(D), n, D.shape[1], METRICS[metric], _p(nbr), _p(deg),
+                                      R, ep, _p(rep))
+    return nbr, deg, int(added), int(rep[0])
 
 
 def search(D, nbr, deg, Q, starts, k: int, L: int, metric: str = "l2", rows=None,

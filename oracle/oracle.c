@@ -371,6 +371,80 @@ int64_t or_connect(const float *D, int64_t n, int d, int metric, int32_t *nbr, i
 }
 
 /* ---------------------------------------------------------------------- */
+/* The connectivity step with edge replacement (a reading for graphs whose */
+/* reached nodes are all full, not used by the builds): as or_connect, but */
+/* when no reached node has a free slot, the reached node p nearest to r   */
+/* that still holds an edge not added by this step gives up the last such */
+/* edge in its list (its farthest original neighbour) for r, and the      */
+/* reached set is recomputed from ep, since the dropped edge may have been */
+/* the only route to some nodes (p itself stays reached: a route to p     */
+/* never needs p's own out-edges).  Every replacement removes one original */
+/* edge and every free-slot link grows the reached set, so the loop ends. */
+/* Returns the edges added (replacements included; *replaced counts them), */
+/* -1 when no reached node has a free slot or an original edge.           */
+/* ---------------------------------------------------------------------- */
+int64_t or_connect_replace(const float *D, int64_t n, int d, int metric, int32_t *nbr,
+                           int32_t *deg, int R, int64_t ep, int64_t *replaced)
+{
+    uint8_t *inS = (uint8_t *)calloc((size_t)n, 1);
+    uint8_t *added_here = (uint8_t *)calloc((size_t)(n * R), 1);
+    int64_t *queue = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    if (!inS || !added_here || !queue) {
+        free(inS);
+        free(added_here);
+        free(queue);
+        return -2;
+    }
+    int64_t reached = reach_from(nbr, deg, R, ep, inS, queue);
+    int64_t edges = 0, rep = 0, r = 0;
+    while (reached < n) {
+        while (inS[r]) ++r;
+        const float *xr = D + (size_t)r * d;
+        item_t best = { INFINITY, -1 };
+        for (int64_t x = 0; x < n; ++x) {
+            if (!inS[x] || deg[x] >= R) continue;
+            item_t it = { or_dist(D + (size_t)x * d, xr, d, metric), (int32_t)x };
+            if (best.id < 0 || item_less(it, best)) best = it;
+        }
+        if (best.id >= 0) {
+            added_here[(int64_t)best.id * R + deg[best.id]] = 1;
+            nbr[(int64_t)best.id * R + deg[best.id]] = (int32_t)r;
+            deg[best.id] += 1;
+            ++edges;
+            reached += reach_from(nbr, deg, R, r, inS, queue);
+            continue;
+        }
+        for (int64_t x = 0; x < n; ++x) {
+            if (!inS[x]) continue;
+            int has = 0;
+            for (int j = 0; j < deg[x] && !has; ++j) has = !added_here[x * R + j];
+            if (!has) continue;
+            item_t it = { or_dist(D + (size_t)x * d, xr, d, metric), (int32_t)x };
+            if (best.id < 0 || item_less(it, best)) best = it;
+        }
+        if (best.id < 0) {
+            edges = -1;
+            break;
+        }
+        const int64_t p = best.id;
+        int slot = deg[p] - 1;
+        while (added_here[p * R + slot]) --slot;
+        nbr[p * R + slot] = (int32_t)r;
+        added_here[p * R + slot] = 1;
+        ++edges;
+        ++rep;
+        memset(inS, 0, (size_t)n);
+        reached = reach_from(nbr, deg, R, ep, inS, queue);
+        r = 0;
+    }
+    if (replaced) *replaced = rep;
+    free(inS);
+    free(added_here);
+    free(queue);
+    return edges;
+}
+
+/* ---------------------------------------------------------------------- */
 /* Beam search, KANNSearch(G, q, k, L, ep) of Algorithm 1.                 */
 /*                                                                        */
 /* pool: at most L (s, id, expanded) entries sorted by (s, id).  It starts */

@@ -431,6 +431,93 @@ def test_connect_equals_its_literal_reading_on_random_graphs(seed):
         assert out_nbr[u, :out_deg[u]].tolist() == adj[u], (seed, u)
 
 
+def _connect_replace_literal(D, nbr, deg, ep, R):
+    """The replacement reading written out: as _connect_literal, and when no
+    reached node is free, the reached p nearest to r (by (s, id)) among
+    those with an edge not added here gives its last such edge to r, then
+    the reached set is recomputed from ep and r restarts from 0."""
+    n = len(D)
+    adj = [list(map(int, nbr[u][:deg[u]])) for u in range(n)]
+    new = [[False] * len(a) for a in adj]
+
+    def reach():
+        S, stack = {ep}, [ep]
+        while stack:
+            v = stack.pop()
+            for w in adj[v]:
+                if w not in S:
+                    S.add(w)
+                    stack.append(w)
+        return S
+
+    S, added, rep = reach(), 0, 0
+    while len(S) < n:
+        r = min(set(range(n)) - S)
+        key = lambda x: (exact_s(D[x], D[r]), x)
+        free = [x for x in S if len(adj[x]) < R]
+        if free:
+            p = min(free, key=key)
+            adj[p].append(r)
+            new[p].append(True)
+        else:
+            own = [x for x in S if not all(new[x])]
+            if not own:
+                return None
+            p = min(own, key=key)
+            j = max(i for i, f in enumerate(new[p]) if not f)
+            adj[p][j], new[p][j] = r, True
+            rep += 1
+        added += 1
+        S = reach()
+    return adj, added, rep
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_connect_replacement_equals_its_literal_reading(seed):
+    """The edge-replacement reading (for graphs whose reached nodes are all
+    full) equals its literal restatement, reaches every node and keeps every
+    degree within R, on random graphs where the plain step often refuses."""
+    rs = np.random.default_rng(700 + seed)
+    n, R = int(rs.integers(4, 50)), int(rs.integers(1, 4))
+    D = int_data(n, 3, 800 + seed, hi=6)
+    nbr = np.full((n, R), -1, np.int32)
+    deg = np.full(n, R, np.int32)  # full rows: the plain step mostly refuses
+    deg[rs.random(n) < 0.2] = 0
+    for u in range(n):
+        nbr[u, :deg[u]] = rs.choice(n, size=deg[u], replace=True)
+    ep = int(rs.integers(0, n))
+    want = _connect_replace_literal(D, nbr, deg, ep, R)
+    out_nbr, out_deg, added, rep = oracle.connect_replace(D, nbr, deg, ep)
+    if want is None:
+        assert added < 0
+        return
+    adj, w_added, w_rep = want
+    assert (added, rep) == (w_added, w_rep)
+    for u in range(n):
+        assert out_nbr[u, :out_deg[u]].tolist() == adj[u], (seed, u)
+    assert (out_deg <= R).all()
+    assert _reach(out_nbr, out_deg, ep) == set(range(n))
+
+
+def test_connect_replacement_links_full_tight_clusters():
+    """Tight clusters whose pruned rows are all full (the situation of the
+    4,096-cluster 384-d recipe at alpha 66): the plain step refuses, the
+    replacement reading connects everything within R."""
+    rs = np.random.default_rng(41)
+    centres = rs.normal(0, 10, (12, 64))
+    D = np.vstack([c + rs.normal(0, 0.05, (16, 64)) for c in centres]).astype(np.float32)
+    n, K, R = D.shape[0], 8, 4
+    ids, _ = oracle.knn(D, K)
+    nbr, deg = oracle.prune(D, np.arange(n + 1, dtype=np.int64) * K, ids.ravel(), R, 66.0)
+    ep = oracle.medoid(D)
+    reach0 = _reach(nbr, deg, ep)
+    assert len(reach0) < n and all(deg[x] == R for x in reach0)
+    assert oracle.connect(D, nbr, deg, ep)[2] < 0
+    out_nbr, out_deg, added, rep = oracle.connect_replace(D, nbr, deg, ep)
+    assert added > 0 and rep > 0
+    assert _reach(out_nbr, out_deg, ep) == set(range(n)) and (out_deg <= R).all()
+
+
 # --------------------------------------------------------------------------
 # beam search
 # --------------------------------------------------------------------------
