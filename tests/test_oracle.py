@@ -751,3 +751,39 @@ def test_insert_levels_follow_the_build_draw_capped_at_the_top():
         assert {800 + k for k in np.nonzero(want >= i)[0]} == members - set(layers[i].gid.tolist())
         assert (L.deg <= L.R).all() and (np.diff(L.gid) > 0).all()
     assert (new[0].deg[800:] > 0).all()
+
+
+# --------------------------------------------------------------------------
+# qualitative claims of the paper (soft trends)
+# --------------------------------------------------------------------------
+def test_more_iterations_do_not_lower_recall():
+    """Exp. 1-a: further OptKCNA iterations improve the graph, with little
+    change after the second (soft: non-decreasing recall at a fixed beam)."""
+    D, Q, _ = synthetic.workload(1, n=2000, nq=80)
+    gt = oracle.knn(D, 10, Q=Q)
+    rec = []
+    for it in (0, 1, 2):
+        nbr, deg, ep = oracle.build_rng(D, 16, 48, 16, 66.0, 60.0, it)
+        ids, _ = oracle.search(D, nbr, deg, Q, ep, 10, 24)
+        rec.append(oracle.recall_at_k(ids, Q, D, 10, gt=gt))
+    assert rec[1] >= rec[0] and rec[2] >= rec[1] - 0.01, rec
+
+
+def test_wider_alpha_loses_less_kcna_quality():
+    """Section 4.2 (Lemma 1, Theorem 2): pruning with a larger alpha loses
+    less k-CNA quality; alpha = 60 (RNG pruning) keeps the fewest edges."""
+    D, _, _ = synthetic.workload(1, n=2000, nq=1)
+    ids, _ = oracle.knn(D, 16)
+    off = np.arange(2001, dtype=np.int64) * 16
+    ep = oracle.medoid(D)
+    quality, degree = [], []
+    for a in (60.0, 66.0, 90.0):
+        N, dg = oracle.prune(D, off, ids.ravel(), 16, a)
+        uoff, uids = oracle.reverse_union(N, dg)
+        G, gd = oracle.prune(D, uoff, uids, 16, a)
+        G, gd, _ = oracle.connect(D, G, gd, ep)
+        C = oracle.acquire(D, G, gd, 32)
+        quality.append(oracle.kcna_recall(D, C, 10).mean())
+        degree.append(gd.mean())
+    assert quality[0] <= quality[1] <= quality[2], quality
+    assert degree[0] < degree[1] <= degree[2], degree
