@@ -433,9 +433,7 @@ pg_status knn_core(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric 
         return PG_OK;
     }
     // rows hold Kx entries when ties must be resolved in FP64 afterwards
-    int64_t avail = self ? n - 1 : n;
     int Kx = facts.exact ? K : (int)std::min<int64_t>((int64_t)K + 8, KMAX);
-    (void)avail;
     Scratch<int32_t> wi;
     Scratch<float> ws;
     int32_t *ti = ids;
