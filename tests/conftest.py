@@ -1,5 +1,7 @@
+import importlib.util
 import os
 import sys
+import warnings
 
 import pytest
 
@@ -8,6 +10,23 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
+def _ensure_library():
+    """Build libpg.so in-tree when it is missing or older than its sources:
+    several CPU tests exercise the library's host code (index-file checks,
+    the serving scheduler, the level draw), and the package refuses to
+    import without the library."""
+    path = os.path.join(ROOT, "paper_2410_01231_gb300", "_build.py")
+    spec = importlib.util.spec_from_file_location("pg_build_step", path)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    if mod.stale():
+        try:
+            mod.build()
+        except Exception as e:  # the tests that need it then fail on import
+            warnings.warn(f"libpg.so could not be built: {e}")
+
+
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
     config.addinivalue_line("markers", "slow: larger CPU case")
+    _ensure_library()
