@@ -215,19 +215,20 @@ pg_status pg_prune(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric 
 /* pg_prune for callers that cannot allocate device memory.  The paper has
  * no counterpart: this is a deployment variant of the same pruning step
  * (same rule, same output as pg_prune), for code that may not call
- * cudaMalloc or anything that allocates -- for instance while a CUDA graph
- * is being built around it, under an allocator or runtime that owns every
- * device allocation, or in a process whose memory footprint must stay fixed
- * after start-up.  It needs no context: it takes the stream (a
- * cudaStream_t; NULL = the legacy default stream) and uses the current
- * device.  All scratch comes from one fixed device array inside the library
- * (about 4.2 MB; every GPU that loads the library holds it until the
- * process exits), so n may not exceed PG_PRUNE_NOALLOC_MAX_N (larger n:
- * PG_ERR_CAPACITY, before any work).  The first call on a device looks up
- * that array's device address with the device current; make that first call
- * before any stream capture.  Every call shares the one array, so calls
- * whose work overlaps on the GPU (other streams, other host threads) race
- * and must be serialised by the caller.  The call is synchronous.  Errors:
+ * cudaMalloc or anything that allocates -- for instance under an allocator
+ * or runtime that owns every device allocation, or in a process whose
+ * memory footprint must stay fixed after start-up.  It needs no context: it
+ * takes the stream (a cudaStream_t; NULL = the legacy default stream) and
+ * uses the current device.  All scratch comes from one fixed device array
+ * inside the library (about 4.2 MB; every GPU that loads the library holds
+ * it until the process exits), so n may not exceed PG_PRUNE_NOALLOC_MAX_N
+ * (larger n: PG_ERR_CAPACITY, before any work).  The first call on a device
+ * looks up that array's device address with the device current.  Every call
+ * shares the one array, so calls whose work overlaps on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller.
+ * The call is synchronous: it synchronises the stream twice and copies the
+ * data facts and the error word to host memory, so it must not be made on a
+ * stream that is being captured into a CUDA graph.  Errors:
  * PG_ERR_INVALID_ARG / PG_ERR_CAPACITY for bad arguments, PG_ERR_CUDA for a
  * failed CUDA call, PG_ERR_DEVICE_CHECK for a candidate id outside [-1, n). */
 pg_status pg_prune_noalloc(void *cuda_stream, const float *D, int64_t n, int32_t d,

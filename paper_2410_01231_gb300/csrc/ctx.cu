@@ -319,6 +319,30 @@ __global__ void k_data_facts(const float *__restrict__ D, int64_t n, int d, floa
     }
 }
 
+DataFacts pg_reduce_facts(const float *blk, int blocks, int64_t n, int32_t d, pg_metric metric) {
+    int integral = 1;
+    float mn = INFINITY, mx = -INFINITY, nrm = 0.f;
+    for (int b = 0; b < blocks; ++b) {
+        integral &= blk[b * 4] != 0.f;
+        mn = fminf(mn, blk[b * 4 + 1]);
+        mx = fmaxf(mx, blk[b * 4 + 2]);
+        nrm = fmaxf(nrm, blk[b * 4 + 3]);
+    }
+    DataFacts f;
+    f.max_norm2 = nrm;
+    f.max_abs = fmaxf(fabsf(mn), fabsf(mx));
+    // Exact FP32 distances need integer rows whose every partial sum stays
+    // below 2^24: d*(max-min)^2 for the difference form, 2*d*max|x|^2 for
+    // the norm form |x|^2 + |y|^2 - 2<x,y>.
+    const double range = (double)mx - (double)mn;
+    const double lim = 16777216.0;
+    f.bf16_exact = integral && f.max_abs <= 256.f;
+    f.u8_exact = integral && n > 0 && mn >= 0.f && mx <= 255.f;
+    f.exact = metric == PG_METRIC_L2SQ && integral && n > 0 && (double)d * range * range < lim &&
+              2.0 * (double)d * (double)f.max_abs * (double)f.max_abs < lim;
+    return f;
+}
+
 pg_status pg_data_facts(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
                         DataFacts *out) {
     int blocks = ctx->num_sms * 4;
@@ -330,26 +354,7 @@ pg_status pg_data_facts(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_me
     PG_TRY_CUDA(ctx, cudaMemcpyAsync(h.data(), blk.p, h.size() * sizeof(float),
                                      cudaMemcpyDeviceToHost, ctx->stream));
     PG_TRY(pg_sync_check(ctx, "data facts"));
-    int integral = 1;
-    float mn = INFINITY, mx = -INFINITY, nrm = 0.f;
-    for (int b = 0; b < blocks; ++b) {
-        integral &= h[b * 4] != 0.f;
-        mn = fminf(mn, h[b * 4 + 1]);
-        mx = fmaxf(mx, h[b * 4 + 2]);
-        nrm = fmaxf(nrm, h[b * 4 + 3]);
-    }
-    out->max_norm2 = nrm;
-    out->max_abs = fmaxf(fabsf(mn), fabsf(mx));
-    // Exact FP32 distances need integer rows whose every partial sum stays
-    // below 2^24: d*(max-min)^2 for the difference form, 2*d*max|x|^2 for
-    // the norm form |x|^2 + |y|^2 - 2<x,y>.
-    double range = (double)mx - (double)mn;
-    double lim = 16777216.0;
-    out->bf16_exact = integral && out->max_abs <= 256.f;
-    out->u8_exact = integral && n > 0 && mn >= 0.f && mx <= 255.f;
-    out->exact = metric == PG_METRIC_L2SQ && integral && n > 0 &&
-                 (double)d * range * range < lim &&
-                 2.0 * (double)d * (double)out->max_abs * (double)out->max_abs < lim;
+    *out = pg_reduce_facts(h.data(), blocks, n, d, metric);
     return PG_OK;
 }
 

@@ -2,13 +2,15 @@
 // memory.
 //
 // Some callers may not call cudaMalloc (or anything that allocates) at the
-// point where they prune: code running while a CUDA graph is being built
-// around it, allocators and runtimes that own every device allocation
-// themselves, or processes that must keep their footprint fixed after
-// start-up.  pg_prune_noalloc does the same work as pg_prune but takes all
-// of its scratch from one file-scope device array of fixed size, so it
+// point where they prune: allocators and runtimes that own every device
+// allocation themselves, or processes that must keep their footprint fixed
+// after start-up.  pg_prune_noalloc does the same work as pg_prune but takes
+// all of its scratch from one file-scope device array of fixed size, so it
 // allocates nothing at all: no device memory, no host heap, no library
-// context.
+// context.  The call is synchronous: it waits on the caller's stream twice
+// (for the data facts and for the device error word) and copies both to
+// host stack buffers, so it may not be made on a stream that is being
+// captured into a CUDA graph.
 #include <climits>
 #include <cstring>
 #include <mutex>
@@ -97,21 +99,7 @@ extern "C" pg_status pg_prune_noalloc(void *cuda_stream, const float *D, int64_t
                             cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) return from_cuda(e);
-    int integral = 1;
-    float mn = INFINITY, mx = -INFINITY, nrm = 0.f;
-    for (int b = 0; b < blocks; ++b) {
-        integral &= h[b * 4] != 0.f;
-        mn = fminf(mn, h[b * 4 + 1]);
-        mx = fmaxf(mx, h[b * 4 + 2]);
-        nrm = fmaxf(nrm, h[b * 4 + 3]);
-    }
-    DataFacts f;
-    f.max_norm2 = nrm;
-    f.max_abs = fmaxf(fabsf(mn), fabsf(mx));
-    f.bf16_exact = integral && f.max_abs <= 256.f;
-    const double range = (double)mx - (double)mn, lim = 16777216.0;
-    f.exact = metric == PG_METRIC_L2SQ && integral && (double)d * range * range < lim &&
-              2.0 * (double)d * (double)f.max_abs * (double)f.max_abs < lim;
+    const DataFacts f = pg_reduce_facts(h, blocks, n, d, metric);
 
     e = pg_prune_launch_on(stream, sms, D, n, d, metric, cand_off, cand_ids, R, alpha_deg, f, nbr,
                            deg, ints, err, cnt);

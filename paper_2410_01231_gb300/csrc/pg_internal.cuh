@@ -206,6 +206,10 @@ struct DataFacts {
 };
 pg_status pg_data_facts(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
                         DataFacts *out);
+// The facts from the per-block results of k_data_facts (host copy, `blocks`
+// groups of {integral, min, max, max squared norm}); shared by every entry
+// point so that all of them take the same exactness decisions.
+DataFacts pg_reduce_facts(const float *blk, int blocks, int64_t n, int32_t d, pg_metric metric);
 
 // Byte shadow of D for the screened (BF16) form: when every FP32 distance is
 // exact and the rows are bytes, the gathers of prune / search read 16-byte

@@ -110,7 +110,7 @@ __device__ void prune_row(const PruneParams &P, int64_t row, const int32_t *cand
         for (int64_t base = 0; base < cnt; base += 32) {
             const int64_t j = base + lane;
             int v = j < cnt ? cand[j] : -1;
-            if (j < cnt && v >= P.n) record_error(P.err, DERR_BAD_ID, u);
+            if (j < cnt && (v >= P.n || v < -1)) record_error(P.err, DERR_BAD_ID, u);
             const bool ok = v >= 0 && v != u && v < P.n;
             if (j < cnt) ci[j] = ok ? v : -1;
             __syncwarp();
@@ -124,7 +124,7 @@ __device__ void prune_row(const PruneParams &P, int64_t row, const int32_t *cand
             int64_t j = base + team;
             int v = j < cnt ? cand[j] : -1;
             bool ok = v >= 0 && v != u && v < P.n;
-            if (j < cnt && v >= P.n) record_error(P.err, DERR_BAD_ID, u);
+            if (j < cnt && (v >= P.n || v < -1)) record_error(P.err, DERR_BAD_ID, u);
             int row = ok ? v : (int)u;
             float s = team8_dist(reinterpret_cast<const float4 *>(uq),
                                  reinterpret_cast<const float4 *>(D + (int64_t)row * d), nch, li,

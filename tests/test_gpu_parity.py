@@ -217,12 +217,15 @@ def test_prune_long_rows_and_empty_rows(ctx, pg, precision):
     assert st["long_rows"] == 4
 
 
-def test_prune_rejects_out_of_range_ids(ctx, pg):
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("bad", [100, -5])
+def test_prune_rejects_out_of_range_ids(ctx, pg, precision, bad):
+    """An id at or above n, or below the padding value -1, is reported."""
     D = int_points(100)
-    off = np.array([0, 2] + [2] * 99, np.int64)
-    cand = np.array([5, 100], np.int32)
+    off = np.array([0, 3] + [3] * 99, np.int64)
+    cand = np.array([5, bad, -1], np.int32)
     with pytest.raises(pg.PGError) as e:
-        pg.prune(ctx, dev(D), dev(off), dev(cand), 4, 60.0)
+        pg.prune(ctx, dev(D), dev(off), dev(cand), 4, 60.0, precision=precision)
     assert e.value.status == 8
 
 

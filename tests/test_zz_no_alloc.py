@@ -1,10 +1,11 @@
 """The allocation-free pruning entry point (pg_prune_noalloc).
 
-Callers that may not allocate device memory -- code running while a CUDA
-graph is being built around it, or under an allocator that owns every
-allocation -- prune through pg_prune_noalloc, which keeps its scratch in a
-fixed array inside the library.  It must give exactly what pg_prune gives,
-call after call (the shared scratch keeps the previous call's contents).
+Callers that may not allocate device memory -- under an allocator or
+runtime that owns every device allocation, or with a footprint fixed after
+start-up -- prune through pg_prune_noalloc, which keeps its scratch in a
+fixed array inside the library.  It must give exactly what pg_prune and the
+FP64 oracle give, call after call (the shared scratch keeps the previous
+call's contents).
 This file is collected last so that a run stopping at the first failure has
 already run every other test.
 """
@@ -14,6 +15,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import synthetic
 
 pytestmark = pytest.mark.gpu
@@ -50,6 +52,9 @@ def test_prune_noalloc_equals_pg_prune_on_two_calls_in_a_row():
         torch.cuda.synchronize()
         assert torch.equal(deg, ref_deg), k
         assert torch.equal(nbr, ref_nbr), k
+        on, odg = oracle.prune(D, off, cand, R, alpha, metric)
+        assert (deg.cpu().numpy() == odg).all(), k
+        assert (nbr.cpu().numpy() == on).all(), k
 
 
 def test_prune_noalloc_rejects_sizes_beyond_its_scratch():
