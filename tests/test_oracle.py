@@ -625,6 +625,107 @@ def test_search_equals_a_literal_algorithm1_on_random_graphs(seed):
         assert ds[i][:len(got)].tolist() == got
 
 
+def _path_layer(members, edges, R):
+    """An oracle.Layer over the ascending ids `members` with the undirected
+    `edges` (pairs of point ids), adjacency rows in member order."""
+    members = sorted(members)
+    row = {v: i for i, v in enumerate(members)}
+    nbr = np.full((len(members), R), -1, np.int32)
+    deg = np.zeros(len(members), np.int32)
+    for a, b in edges:
+        for x, y in ((a, b), (b, a)):
+            nbr[row[x], deg[row[x]]] = y
+            deg[row[x]] += 1
+    return oracle.Layer(np.array(members, np.int32), nbr, deg, R)
+
+
+def test_search_nswg_hand_built_descent():
+    """Points 0..39 on a line.  Layer 0 is two paths, 0-...-19 and
+    20-...-39, so a search that starts on the wrong side can never cross;
+    layer 1 holds {0, 10, 30} linked 0-10-30; layer 2 holds {0}.  Greedy
+    routing from ep 0 for the query 33.2 goes 0 -> 10 -> 30 on layer 1, and
+    the width-4 search of layer 0 from 30 returns 33, 34, 32.  For 7.4 it
+    stops at 10 and returns 7, 8, 6.  Skipping layer 1, or reading layer 1's
+    rows through the wrong map, starts layer 0 at 0 and cannot reach 33."""
+    n = 40
+    D = np.arange(n, dtype=np.float32).reshape(n, 1)
+    base_edges = [(u, u + 1) for u in range(19)] + [(u, u + 1) for u in range(20, 39)]
+    base = _path_layer(range(n), base_edges, 2)
+    base.gid = None
+    lay1 = _path_layer([0, 10, 30], [(0, 10), (10, 30)], 2)
+    lay2 = _path_layer([0], [], 1)
+    Q = np.array([[33.2], [7.4]], np.float32)
+    ids, _ = oracle.search_nswg(D, [base, lay1, lay2], 0, Q, 3, 4, "l2")
+    assert ids.tolist() == [[33, 34, 32], [7, 8, 6]]
+    # without the routing layer the base search from 0 stays on 0..19
+    ids, _ = oracle.search_nswg(D, [base, lay2], 0, Q, 3, 4, "l2")
+    assert ids.tolist() == [[19, 18, 17], [7, 8, 6]]
+
+
+def _layered_search_literal(D, layers, ep, q, k, ef, ef_upper):
+    """The layered query written out: w <- ep; for each layer from the top
+    down to layer 1, w <- the nearest result of Algorithm 1 on that layer
+    (pool ef_upper, from w); then Algorithm 1 on layer 0 (pool ef, from w).
+    Adjacency is looked up by point id in a dictionary per layer."""
+    w = ep
+    for i in range(len(layers) - 1, -1, -1):
+        lay = layers[i]
+        gid = range(lay.nbr.shape[0]) if lay.gid is None else lay.gid.tolist()
+        adj = {int(v): [int(x) for x in lay.nbr[r][:lay.deg[r]]] for r, v in enumerate(gid)}
+        L = ef if i == 0 else ef_upper
+        pool = [(exact_s(q, D[w]), w)]
+        visited, expanded = {w}, set()
+        while True:
+            nxt = next((v for _, v in pool if v not in expanded), None)
+            if nxt is None:
+                break
+            expanded.add(nxt)
+            for x in adj[nxt]:
+                if x not in visited:
+                    visited.add(x)
+                    pool.append((exact_s(q, D[x]), x))
+            pool = sorted(pool)[:L]
+        if i > 0:
+            w = pool[0][1]
+        else:
+            out = [v for _, v in pool[:k]]
+            return out + [-1] * (k - len(out))
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_search_nswg_equals_a_literal_layered_descent(seed):
+    """Random nested layers (each a subset of the one below, uneven random
+    adjacency among its members, exact integer distances with many ties),
+    random ef_upper: oracle.search_nswg returns the literal descent's lists."""
+    rs = np.random.default_rng(700 + seed)
+    n, d = int(rs.integers(20, 80)), int(rs.integers(1, 4))
+    D = int_data(n, d, 710 + seed, hi=6)
+    nq = 10
+    Q = int_data(nq, d, 720 + seed, hi=6)
+    members = list(range(n))
+    layers = []
+    for i in range(int(rs.integers(2, 5))):
+        if i > 0:
+            keep = max(1, len(members) // int(rs.integers(2, 5)))
+            members = sorted(rs.choice(members, size=keep, replace=False).tolist())
+        R = int(rs.integers(1, 6))
+        m = len(members)
+        nbr = np.full((m, R), -1, np.int32)
+        deg = rs.integers(0, R + 1, size=m).astype(np.int32)
+        for r in range(m):
+            nbr[r, :deg[r]] = rs.choice(members, size=deg[r], replace=True)
+        gid = None if i == 0 else np.array(members, np.int32)
+        layers.append(oracle.Layer(gid, nbr, deg, R))
+    ep = members[0]
+    ef = int(rs.integers(1, 10))
+    k = int(rs.integers(1, ef + 1))
+    ef_upper = int(rs.integers(1, 4))
+    ids, _ = oracle.search_nswg(D, layers, ep, Q, k, ef, "l2", ef_upper=ef_upper)
+    for i in range(nq):
+        want = _layered_search_literal(D, layers, ep, Q[i], k, ef, ef_upper)
+        assert ids[i].tolist() == want, (seed, i)
+
+
 def test_acquire_on_complete_graph_is_exact_knn_minus_self():
     D = int_data(30, 3, 19, hi=7)
     n = 30
