@@ -99,6 +99,8 @@ typedef struct {
     int64_t fp64_flips;         /* ... whose FP64 outcome differed from FP32's */
     int64_t edges;              /* kept edges (sum of out-degrees)            */
     int64_t long_rows;          /* rows handled by the long-row kernel        */
+    int64_t near_ties;          /* decisions with relative margin < 1e-5 (counted
+                                   only when pg_ctx_set_tie_count is on)        */
 } pg_prune_stats;
 
 /* Parameters of the graph builds (pg_default_params fills the defaults). */
@@ -161,8 +163,21 @@ pg_status pg_ctx_kernel_work(pg_ctx *ctx, const char *name, double *work);
  * "search_bytes" (one data row per evaluation + one adjacency row per
  * expansion) and "prune_bytes" (one data row + 8 bytes per examined
  * candidate + the point's own row); a data row is 4d bytes, or d bytes
- * when the screened form gathers byte rows. */
+ * when the screened form gathers byte rows; "prune_edges" (kept edges),
+ * "prune_fp64_rechecks" and "prune_fp64_flips" (decisions re-made in FP64,
+ * and those whose FP64 outcome differed from the plain FP32 one), and
+ * "prune_near_ties" (see pg_ctx_set_tie_count). */
 pg_status pg_ctx_counter(pg_ctx *ctx, const char *name, int64_t *value);
+
+/* Tie accounting of the pruning kernels (off by default): when on, every
+ * decision of the occlusion test (Section 4.1: s(u,w) < s(u,v),
+ * s(v,w) < s(u,v) and the angle clause) whose relative margin is below
+ * 1e-5 is counted in "prune_near_ties".  Margins: |a - b| / max(a, b) for a
+ * distance comparison, |(s_uw + s_vw - s_uv) - 2 cos(alpha) sqrt(s_uw s_vw)|
+ * / (s_uw + s_vw + s_uv) for the angle clause, from the FP32 distances.
+ * Such decisions are still decided exactly (integer arithmetic or the FP64
+ * recheck); the count states how many of them the tie budget covers. */
+pg_status pg_ctx_set_tie_count(pg_ctx *ctx, int enable);
 
 /* ------------------------------------------------------------------ steps */
 

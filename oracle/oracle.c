@@ -335,6 +335,30 @@ static int64_t reach_from(const int32_t *nbr, const int32_t *deg, int R, int64_t
     return added;
 }
 
+/* The nearest reached node with a free slot to the row xr: argmin over  */
+/* x with inS[x] and deg[x] < R of the pair (s(x, r), x).  The minimum of  */
+/* a total order does not depend on how the scan is split among threads.   */
+static item_t nearest_reached_free(const float *D, int64_t n, int d, int metric,
+                                   const uint8_t *inS, const int32_t *deg, int R, const float *xr)
+{
+    item_t best = { INFINITY, -1 };
+#pragma omp parallel
+    {
+        item_t loc = { INFINITY, -1 };
+#pragma omp for schedule(static)
+        for (int64_t x = 0; x < n; ++x) {
+            if (!inS[x] || deg[x] >= R) continue;
+            item_t it = { or_dist(D + (size_t)x * d, xr, d, metric), (int32_t)x };
+            if (loc.id < 0 || item_less(it, loc)) loc = it;
+        }
+#pragma omp critical
+        {
+            if (loc.id >= 0 && (best.id < 0 || item_less(loc, best))) best = loc;
+        }
+    }
+    return best;
+}
+
 int64_t or_connect(const float *D, int64_t n, int d, int metric, int32_t *nbr, int32_t *deg,
                    int R, int64_t ep)
 {
@@ -350,12 +374,7 @@ int64_t or_connect(const float *D, int64_t n, int d, int metric, int32_t *nbr, i
     while (reached < n) {
         while (inS[r]) ++r;
         const float *xr = D + (size_t)r * d;
-        item_t best = { INFINITY, -1 };
-        for (int64_t x = 0; x < n; ++x) {
-            if (!inS[x] || deg[x] >= R) continue;
-            item_t it = { or_dist(D + (size_t)x * d, xr, d, metric), (int32_t)x };
-            if (best.id < 0 || item_less(it, best)) best = it;
-        }
+        item_t best = nearest_reached_free(D, n, d, metric, inS, deg, R, xr);
         if (best.id < 0) {
             edges = -1;
             break;
@@ -400,12 +419,7 @@ int64_t or_connect_replace(const float *D, int64_t n, int d, int metric, int32_t
     while (reached < n) {
         while (inS[r]) ++r;
         const float *xr = D + (size_t)r * d;
-        item_t best = { INFINITY, -1 };
-        for (int64_t x = 0; x < n; ++x) {
-            if (!inS[x] || deg[x] >= R) continue;
-            item_t it = { or_dist(D + (size_t)x * d, xr, d, metric), (int32_t)x };
-            if (best.id < 0 || item_less(it, best)) best = it;
-        }
+        item_t best = nearest_reached_free(D, n, d, metric, inS, deg, R, xr);
         if (best.id >= 0) {
             added_here[(int64_t)best.id * R + deg[best.id]] = 1;
             nbr[(int64_t)best.id * R + deg[best.id]] = (int32_t)r;

@@ -45,7 +45,8 @@ class BuildParams(C.Structure):
 
 class PruneStats(C.Structure):
     _fields_ = [(name, i64) for name in ("rows", "candidates", "scanned", "occlusion_tests",
-                                         "fp64_rechecks", "fp64_flips", "edges", "long_rows")]
+                                         "fp64_rechecks", "fp64_flips", "edges", "long_rows",
+                                         "near_ties")]
 
 
 def _sig(name, res, args):
@@ -80,6 +81,7 @@ _sig("pg_index_layer", C.c_int, [P, i32, P, P, P, P, P])
 _sig("pg_index_phase_seconds", C.c_int, [P, P])
 _sig("pg_index_export_layer", C.c_int, [P, P, i32, P, P, P])
 _sig("pg_ctx_set_timing", C.c_int, [P, C.c_int])
+_sig("pg_ctx_set_tie_count", C.c_int, [P, C.c_int])
 _sig("pg_ctx_kernel_time", C.c_int, [P, C.c_char_p, P, P])
 _sig("pg_ctx_counter", C.c_int, [P, C.c_char_p, P])
 _sig("pg_ctx_kernel_work", C.c_int, [P, C.c_char_p, P])
@@ -110,7 +112,7 @@ EXPORTS = ["pg_default_params", "pg_ctx_create", "pg_ctx_destroy", "pg_last_erro
            "pg_medoid", "pg_connect", "pg_acquire_candidates", "pg_search_graph", "pg_build_rng",
            "pg_build_nswg", "pg_search", "pg_search_host", "pg_index_destroy", "pg_index_info",
            "pg_index_layer", "pg_index_phase_seconds", "pg_index_export_layer",
-           "pg_ctx_set_timing", "pg_ctx_kernel_time", "pg_ctx_counter",
+           "pg_ctx_set_timing", "pg_ctx_set_tie_count", "pg_ctx_kernel_time", "pg_ctx_counter",
            "pg_ctx_kernel_work", "pg_prune_noalloc", "pg_index_reserve", "pg_index_insert",
            "pg_serve_start", "pg_serve_submit_query", "pg_serve_submit_insert", "pg_serve_wait",
            "pg_serve_stats", "pg_serve_stop", "pg_serve_set_queue_limit",
@@ -167,6 +169,11 @@ class Context:
         """Enable CUDA-event timing of the main kernels (resets totals)."""
         self._check(_lib.pg_ctx_set_timing(self._h, 1 if enable else 0), "pg_ctx_set_timing")
 
+    def set_tie_count(self, enable: bool = True):
+        """Count pruning decisions with relative margin below 1e-5 (pg_ctx_set_tie_count)."""
+        self._check(_lib.pg_ctx_set_tie_count(self._h, 1 if enable else 0),
+                    "pg_ctx_set_tie_count")
+
     def kernel_time(self, name: str):
         """(total device ms, launches) of a timed kernel since the last reset."""
         ms, cnt = C.c_double(), C.c_int64()
@@ -189,7 +196,9 @@ class Context:
     def counter(self, name: str) -> int:
         """Cumulative counter (pg_ctx_counter): "connect_edges", "connect_full_rounds",
         "connect_conflicts", "search_expansions", "search_evaluations", "prune_rows",
-        "prune_candidates", "prune_scanned", "prune_occlusion_tests"."""
+        "prune_candidates", "prune_scanned", "prune_occlusion_tests", "prune_edges",
+        "prune_fp64_rechecks", "prune_fp64_flips", "prune_near_ties", "search_bytes",
+        "prune_bytes"."""
         v = C.c_int64()
         self._check(_lib.pg_ctx_counter(self._h, name.encode(), C.byref(v)), "pg_ctx_counter")
         return v.value

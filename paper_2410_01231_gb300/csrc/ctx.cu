@@ -129,6 +129,12 @@ extern "C" pg_status pg_ctx_set_timing(pg_ctx *ctx, int enable) {
     return pg_reset_counters(ctx);
 }
 
+extern "C" pg_status pg_ctx_set_tie_count(pg_ctx *ctx, int enable) {
+    if (!ctx) return PG_ERR_INVALID_ARG;
+    ctx->count_ties = enable ? 1 : 0;
+    return PG_OK;
+}
+
 extern "C" pg_status pg_ctx_kernel_work(pg_ctx *ctx, const char *name, double *work) {
     if (!ctx || !name || !work) return PG_ERR_INVALID_ARG;
     pg_timer_resolve(ctx);
@@ -168,7 +174,9 @@ extern "C" pg_status pg_ctx_counter(pg_ctx *ctx, const char *name, int64_t *valu
         } dev[] = {{"search_expansions", CNT_SEARCH_EXP}, {"search_evaluations", CNT_SEARCH_EVAL},
                    {"prune_rows", CNT_ROWS},           {"prune_candidates", CNT_CANDS},
                    {"prune_scanned", CNT_SCANNED},     {"prune_occlusion_tests", CNT_OCCL},
-                   {"search_bytes", CNT_SEARCH_BYTES}, {"prune_bytes", CNT_PRUNE_BYTES}};
+                   {"search_bytes", CNT_SEARCH_BYTES}, {"prune_bytes", CNT_PRUNE_BYTES},
+                   {"prune_fp64_rechecks", CNT_RECHECK}, {"prune_fp64_flips", CNT_FLIP},
+                   {"prune_near_ties", CNT_NEAR_TIE},  {"prune_edges", CNT_EDGES}};
         for (const auto &e : dev) {
             if (strcmp(name, e.name) == 0) {
                 unsigned long long c[PG_CNT_SLOTS];

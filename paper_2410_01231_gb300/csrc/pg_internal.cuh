@@ -30,6 +30,7 @@ struct pg_ctx {
     int64_t connect_full_rounds = 0;  // of those, rounds decided by a full scan
     int64_t connect_why_full = 0;     // batches cut short by a candidate that filled up
     int64_t connect_free = 0;         // nodes with a free slot when connectivity steps began
+    int count_ties = 0;               // pruning counts near-tie decisions (pg_ctx_set_tie_count)
     // optional CUDA-event timing of named kernels
     int timing = 0;
     struct TimedPair {
@@ -118,7 +119,7 @@ enum { PG_CNT_SLOTS = 32 };
 enum {
     CNT_ROWS = 0, CNT_CANDS, CNT_SCANNED, CNT_OCCL, CNT_RECHECK, CNT_FLIP, CNT_EDGES, CNT_LONG,
     CNT_LONG_LIST = 16, CNT_KNN_RECHECK = 17, CNT_KNN_UNRESOLVED = 18, CNT_SEARCH_EXP = 19,
-    CNT_SEARCH_EVAL = 20, CNT_SEARCH_BYTES = 21, CNT_PRUNE_BYTES = 22
+    CNT_SEARCH_EVAL = 20, CNT_SEARCH_BYTES = 21, CNT_PRUNE_BYTES = 22, CNT_NEAR_TIE = 23
 };
 
 // device error codes (first one recorded wins)

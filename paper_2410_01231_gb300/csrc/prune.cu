@@ -38,6 +38,7 @@ struct PruneParams {
     float cos_af;
     int alpha60;
     int exact;
+    int count_ties;      // count decisions with relative margin below 1e-5
     ErrModel em;
     int32_t *nbr;
     int32_t *deg;
@@ -73,7 +74,21 @@ __device__ __forceinline__ float kept_dist_u8(const uint8_t *__restrict__ xv8, u
 
 struct RowStats {
     unsigned long long cands = 0, scanned = 0, tests = 0, rechecks = 0, flips = 0, edges = 0;
+    unsigned long long ties = 0;  // decisions with relative margin below 1e-5
 };
+
+// Relative margin of a distance comparison a < b below 1e-5 (the tie
+// budget's definition: |a - b| / max(a, b)).
+__device__ __forceinline__ bool near_tie(float a, float b) {
+    return fabsf(a - b) < 1e-5f * fmaxf(a, b);
+}
+
+// Relative margin of the angle clause below 1e-5:
+// |(s_uw + s_vw - s_uv) - 2 cos(alpha) sqrt(s_uw s_vw)| / (s_uw + s_vw + s_uv).
+__device__ __forceinline__ bool near_tie_angle(float suw, float svw, float suv, float ca) {
+    const float lhs = (suw + svw) - suv, rhs = 2.f * ca * sqrtf(suw * svw);
+    return fabsf(lhs - rhs) < 1e-5f * (suw + svw + suv);
+}
 
 // REG: byte rows of at most 128 bytes and R <= 32; lane l keeps the row of
 // the l-th kept point in registers, so a candidate is tested against every
@@ -234,6 +249,7 @@ __device__ void prune_row(const PruneParams &P, int64_t row, const int32_t *cand
                 vrow[lane] = __ldg(reinterpret_cast<const uint4 *>(D8 + (int64_t)v * d) + lane);
             __syncwarp();
             bool occ = false;
+            if (lane < kept && P.count_ties && near_tie(ksl, suv)) st.ties++;
             if (lane < kept && ksl < suv) {  // exact data: the comparisons are exact
                 unsigned acc = 0;
 #pragma unroll
@@ -241,9 +257,11 @@ __device__ void prune_row(const PruneParams &P, int64_t row, const int32_t *cand
                     if (c < nch16) acc = sq_diff_u8(vrow[c], kr[c], acc);
                 const float svw = (float)acc;
                 st.tests++;
+                if (P.count_ties && near_tie(svw, suv)) st.ties++;
                 if (svw < suv) {
                     int c3 = 1;
                     if (!P.alpha60) {
+                        if (P.count_ties && near_tie_angle(ksl, svw, suv, P.cos_af)) st.ties++;
                         c3 = angle_certain(ksl, P.em.err(ksl), svw, P.em.err(svw), suv,
                                            P.em.err(suv), P.cos_af);
                         if (c3 < 0) {
@@ -297,12 +315,14 @@ __device__ void prune_row(const PruneParams &P, int64_t row, const int32_t *cand
             if (active && li == 0) {
                 const int wpos = kpos[t];
                 const float suw = ks[t];
+                if (P.count_ties && near_tie(suw, suv)) st.ties++;
                 bool c1;
                 if (P.exact) c1 = suw < suv;
                 else if (runid[wpos] != runid[j]) c1 = true;  // separated by a certain gap
                 else c1 = c64[wpos] < c64[j];
                 if (c1) {
                     st.tests++;
+                    if (P.count_ties && near_tie(svw, suv)) st.ties++;
                     const float evw = P.em.err(svw);
                     int c2 = P.exact ? (svw < suv) : less_certain(svw, evw, suv, euv);
                     double s64vw = -1.0, s64uv = c64[j], s64uw = c64[wpos];
@@ -316,6 +336,7 @@ __device__ void prune_row(const PruneParams &P, int64_t row, const int32_t *cand
                     if (c2) {
                         int c3 = 1;
                         if (!P.alpha60) {
+                            if (P.count_ties && near_tie_angle(suw, svw, suv, P.cos_af)) st.ties++;
                             c3 = angle_certain(suw, P.em.err(suw), svw, evw, suv, euv, P.cos_af);
                             if (c3 < 0) {
                                 if (P.exact) {  // the FP32 distances are the exact values
@@ -360,8 +381,8 @@ __device__ void prune_row(const PruneParams &P, int64_t row, const int32_t *cand
 __device__ void flush_stats(const PruneParams &P, RowStats &st, unsigned long long rows, bool lng) {
     const int lane = threadIdx.x & 31;
     // per-lane counters (tests/rechecks/flips live on team leaders)
-    unsigned long long v[5] = {st.tests, st.rechecks, st.flips, 0, 0};
-    for (int k = 0; k < 3; ++k)
+    unsigned long long v[5] = {st.tests, st.rechecks, st.flips, st.ties, 0};
+    for (int k = 0; k < 4; ++k)
         for (int o = 16; o; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
     if (lane == 0) {
         atomicAdd(P.counters + CNT_ROWS, rows);
@@ -371,6 +392,7 @@ __device__ void flush_stats(const PruneParams &P, RowStats &st, unsigned long lo
         atomicAdd(P.counters + CNT_RECHECK, v[1]);
         atomicAdd(P.counters + CNT_FLIP, v[2]);
         atomicAdd(P.counters + CNT_EDGES, st.edges);
+        if (v[3]) atomicAdd(P.counters + CNT_NEAR_TIE, v[3]);
         if (lng) atomicAdd(P.counters + CNT_LONG, rows);
         // algorithmic bytes: each examined candidate's row plus (id, distance),
         // and the point's own row
@@ -575,6 +597,7 @@ pg_status pg_prune_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d, p
     P.cos_af = (float)P.cos_a;
     P.alpha60 = alpha_deg == 60.0;
     P.exact = facts.exact;
+    P.count_ties = ctx->count_ties;
     P.em = pg_err_model(metric, d, facts, false);
     P.nbr = nbr;
     P.deg = deg;
@@ -636,6 +659,7 @@ cudaError_t pg_prune_launch_on(cudaStream_t stream, int num_sms, const float *D,
     P.cos_af = (float)P.cos_a;
     P.alpha60 = alpha_deg == 60.0;
     P.exact = facts.exact;
+    P.count_ties = 0;
     P.em = pg_err_model(metric, d, facts, false);
     P.nbr = nbr;
     P.deg = deg;
@@ -705,6 +729,7 @@ extern "C" pg_status pg_prune(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
         host_stats->fp64_flips = (int64_t)c[CNT_FLIP];
         host_stats->edges = (int64_t)c[CNT_EDGES];
         host_stats->long_rows = (int64_t)c[CNT_LONG];
+        host_stats->near_ties = (int64_t)c[CNT_NEAR_TIE];
         return PG_OK;
     }
     return pg_sync_check(ctx, "pg_prune");
