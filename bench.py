@@ -116,11 +116,6 @@ def peaks():
         return {}
 
 
-def fp32_simt_peak_tflops(sm_mhz: float) -> float:
-    # 152 SMs x 128 FP32 lanes x 2 flop (FMA) x clock
-    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-
-
 def oracle_build_rate(D, w, ns: int, threads: int | None = None):
     """Oracle stages on the first ns points of the workload, extrapolated
     to the full n: exact kNN scaled by (n/ns)^2, every other stage by n/ns."""
@@ -264,10 +259,6 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    for _ in range(args.warmup):
-        idx = pg.Index.build_rng(ctx, Dd, **params)
-        idx.close()
-
     gpu_id = local
     vis = os.environ.get("CUDA_VISIBLE_DEVICES")
     if vis:
@@ -275,40 +266,56 @@ def run_ours(args):
             gpu_id = int(vis.split(",")[local])
         except ValueError:
             pass
-    clocks = Clocks(gpu_id)
-    ctx.set_timing(True)
-    launches0 = ctx.launches
-    barrier()
-    clocks.start()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    nvtx = getattr(torch.cuda, "nvtx", None)
-    try:  # names the timed region for profilers (ncu --nvtx-include timed/)
-        nvtx.range_push("timed")
-    except Exception:
-        nvtx = None
-    ev0.record(stream)
-    phases = []
-    for _ in range(args.steps):
-        idx = pg.Index.build_rng(ctx, Dd, **params)
-        phases.append(idx.phase_seconds())
-        idx.close()
-    ev1.record(stream)
-    if nvtx is not None:
-        nvtx.range_pop()
-    barrier()
-    clk = clocks.stop()
-    launches = ctx.launches - launches0
-    ms = ev0.elapsed_time(ev1) / args.steps
-    knn_ms, knn_launches = ctx.kernel_time("knn")
-    knn_work = ctx.kernel_work("knn")
-    kt = {k: ctx.kernel_time(k) for k in ("knn", "prune", "union", "connect", "search", "medoid")}
-    conn_edges = ctx.counter("connect_edges")
-    conn_full = ctx.counter("connect_full_rounds")
-    work = {c: ctx.counter(c) for c in ("search_expansions", "search_evaluations", "search_bytes",
-                                        "prune_rows", "prune_candidates", "prune_bytes")}
-    ctx.set_timing(False)
-    ms, value = job_rate(ms, n, world, "cuda")
+
+    def timed_builds(prm, warmup, steps, clocks=None):
+        """warmup untimed builds, then `steps` builds bracketed by a barrier and
+        a synchronize on both sides and timed with CUDA events on the
+        context's stream; per-kernel CUDA-event times and the kernels' own
+        work counters over the timed builds."""
+        for _ in range(warmup):
+            pg.Index.build_rng(ctx, Dd, **prm).close()
+        ctx.set_timing(True)
+        launches0 = ctx.launches
+        barrier()
+        if clocks:
+            clocks.start()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        nvtx = getattr(torch.cuda, "nvtx", None)
+        try:  # names the timed region for profilers (ncu --nvtx-include timed/)
+            nvtx.range_push("timed")
+        except Exception:
+            nvtx = None
+        ev0.record(stream)
+        phases = []
+        for _ in range(steps):
+            idx = pg.Index.build_rng(ctx, Dd, **prm)
+            phases.append(idx.phase_seconds())
+            idx.close()
+        ev1.record(stream)
+        if nvtx is not None:
+            nvtx.range_pop()
+        barrier()
+        clk = clocks.stop() if clocks else None
+        r = {"ms": ev0.elapsed_time(ev1) / steps, "launches": ctx.launches - launches0,
+             "clocks": clk, "steps": steps, "warmup": warmup,
+             "kt": {k: ctx.kernel_time(k) for k in ("knn", "prune", "union", "connect", "search",
+                                                    "medoid")},
+             "knn_work": ctx.kernel_work("knn"),
+             "work": {c: ctx.counter(c) for c in ("search_expansions", "search_evaluations",
+                                                  "search_bytes", "prune_rows",
+                                                  "prune_candidates", "prune_bytes")},
+             "conn_edges": ctx.counter("connect_edges"),
+             "conn_full": ctx.counter("connect_full_rounds"),
+             "phases": ({k: statistics.mean(p[k] for p in phases) for k in phases[0]}
+                        if phases else {})}
+        ctx.set_timing(False)
+        return r
+
+    main_run = timed_builds(params, args.warmup, args.steps, Clocks(gpu_id))
+    ms, value = job_rate(main_run["ms"], n, world, "cuda")
+    kt, work = main_run["kt"], main_run["work"]
+    launches, clk, phases_mean = main_run["launches"], main_run["clocks"], main_run["phases"]
 
     # ---------------------------------------------------------- queries
     qres = {}
@@ -482,46 +489,70 @@ def run_ours(args):
         del X3d
 
     # ------------------------------------------------ the other precision form
-    forms = {args.precision: {"ms_per_build": ms, "points_per_s": value}}
+    # Timed like the main form (CUDA events on the context's stream, barrier
+    # and synchronize on both sides) over min(steps, 3) builds after one
+    # warm-up: the FP32 form takes several seconds per build.
+    forms = {args.precision: {"ms_per_build": ms, "points_per_s": value, "steps": args.steps,
+                              "kernel_ms_per_build": {k: v[0] / args.steps
+                                                      for k, v in kt.items()}}}
     identical = None
+    other_run = None
+    fp32_peak = ctx.measure_fp32_peak()
     if not args.no_other_form:
         other = "fp32" if args.precision == "bf16" else "bf16"
         p2 = dict(params, precision=other)
+        other_run = timed_builds(p2, 1, min(args.steps, 3))
+        forms[other] = {"ms_per_build": other_run["ms"],
+                        "points_per_s": n / (other_run["ms"] / 1e3),
+                        "steps": other_run["steps"], "warmup": other_run["warmup"],
+                        "kernel_ms_per_build": {k: v[0] / other_run["steps"]
+                                                for k, v in other_run["kt"].items()},
+                        "phase_s": other_run["phases"]}
         a = pg.Index.build_rng(ctx, Dd, **params)
-        barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
         b = pg.Index.build_rng(ctx, Dd, **p2)
-        e1.record(stream)
-        barrier()
-        t = e0.elapsed_time(e1)
-        forms[other] = {"ms_per_build": t, "points_per_s": n / (t / 1e3)}
         _, na, da = a.layer(0)
         _, nb_, db = b.layer(0)
         identical = bool(torch.equal(na, nb_) and torch.equal(da, db))
         a.close()
         b.close()
 
+    # --------------------------------------------------------- tie budget
+    # One more (untimed) build of the main form with the pruning kernels'
+    # tie accounting on: decisions of the occlusion test whose relative
+    # margin is below 1e-5, the FP64 rechecks and the rechecks whose FP64
+    # outcome differed from plain FP32, over all six pruning calls.
+    ctx.set_timing(True)  # resets the device counters
+    ctx.set_tie_count(True)
+    pg.Index.build_rng(ctx, Dd, **params).close()
+    tie = {k: ctx.counter("prune_" + k) for k in ("edges", "near_ties", "fp64_rechecks",
+                                                   "fp64_flips")}
+    ctx.set_tie_count(False)
+    ctx.set_timing(False)
+    tie["near_tie_share_of_edges"] = tie["near_ties"] / max(1, tie["edges"])
+    tie["note"] = ("counts over the six pruning calls of one build (base layer); every near-tie "
+                   "decision is decided exactly (integer distances or the FP64 recheck), so the "
+                   "allowed mismatches are 0; mismatches against the oracle: oracle_check")
+
     # ------------------------------------------------------------- e2e
+    # The same build through the C ABI with HOST buffers (pg_build_rng_host):
+    # the pinned host points are uploaded, the graph is built and the base
+    # graph (nbr [n][R], deg [n]) is read back inside the call; wall time of
+    # the call, averaged over min(steps, 3) calls after one warm-up.
     e2e = None
     if not args.no_e2e:
         Dh = torch.from_numpy(D).pin_memory()
         nbr_h = torch.empty((n, w["R"]), dtype=torch.int32).pin_memory()
         deg_h = torch.empty(n, dtype=torch.int32).pin_memory()
+        pg.Index.build_rng_host(ctx, Dh, nbr_h, deg_h, **params)
+        reps = min(args.steps, 3)
         barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        Dx = torch.empty_like(Dd)
-        Dx.copy_(Dh, non_blocking=True)
-        idx = pg.Index.build_rng(ctx, Dx, **params)
-        _, nb, dg = idx.layer(0)
-        nbr_h.copy_(nb, non_blocking=True)
-        deg_h.copy_(dg, non_blocking=True)
-        e1.record(stream)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            pg.Index.build_rng_host(ctx, Dh, nbr_h, deg_h, **params)
         barrier()
-        idx.close()
-        t = e0.elapsed_time(e1) / 1e3
-        e2e = {"value": world * n / t, "unit": "points/s",
+        t = (time.perf_counter() - t0) / reps
+        e2e = {"value": world * n / t, "unit": "points/s", "seconds_per_build": t,
+               "calls": reps, "api": "pg_build_rng_host (host buffers, pinned)",
                "h2d_bytes_per_step": int(D.nbytes),
                "d2h_bytes_per_step": int(nbr_h.numel() * 4 + deg_h.numel() * 4)}
 
@@ -533,62 +564,70 @@ def run_ours(args):
     # expansion.  Prune: one data row plus (id, distance) per examined
     # candidate, plus the point's own row.  A data row is 4d bytes, d bytes
     # where the screened form gathers byte rows (counted by the kernels).
+    # Kernels timed inside a seconds-long build take the sustained peaks.
     pk = peaks()
     hbm = pk.get("hbm_gbs", 6800.0)
-    d = w["d"]
-    rooflines = {}
-    if knn_ms > 0:
-        a = knn_work / (knn_ms / 1e3) / 1e12
-        if args.precision == "fp32":
-            peak = fp32_simt_peak_tflops(pk.get("sm_max_mhz", 2070.0))
-            rooflines["knn"] = {
-                "kernel": "k_knn_fp32", "bound": "alu", "achieved": a, "peak": peak,
-                "unit": "TFLOP/s", "frac": a / peak, "traffic": None,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (derived)"}
-        else:
-            peak = pk.get("bf16_tflops", 1900.0)
-            rooflines["knn"] = {
-                "kernel": "k_knn_tc", "bound": "tensor", "achieved": a, "peak": peak,
-                "unit": "TFLOP/s", "frac": a / peak, "traffic": None,
-                "peak_source": "MEASURED_PEAKS.json bf16_tflops (of measured)"}
-    s_ms = kt["search"][0]
-    if s_ms > 0:
-        b = work["search_bytes"]
-        a = b / (s_ms / 1e3) / 1e9
-        rooflines["search"] = {
-            "kernel": "k_search", "bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s",
-            "frac": a / hbm, "traffic": None, "algorithmic_bytes_per_step": b / args.steps,
-            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
-    p_ms = kt["prune"][0]
-    if p_ms > 0:
-        b = work["prune_bytes"]
-        a = b / (p_ms / 1e3) / 1e9
-        rooflines["prune"] = {
-            "kernel": "k_prune", "bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s",
-            "frac": a / hbm, "traffic": None, "algorithmic_bytes_per_step": b / args.steps,
-            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
-    # DRAM traffic of a kernel's main launch from an ncu capture recorded in
-    # profiles/roofline_traffic.json, valid only while the kernel's source
-    # file is byte-identical to the one captured (else null)
-    try:
-        import hashlib
-        with open(os.path.join(ROOT, "profiles", "roofline_traffic.json")) as f:
-            rec = json.load(f)
-        for name, r in rooflines.items():
-            ent = rec.get(r["kernel"])
-            if not ent or ent.get("n") != n:
-                continue
-            with open(os.path.join(ROOT, ent["source"]), "rb") as f:
-                if hashlib.sha256(f.read()).hexdigest() == ent["source_sha256"]:
-                    r["traffic"] = ent["dram_bytes_per_launch"]
-                    r["traffic_note"] = ent["note"]
-    except (OSError, ValueError, KeyError):
-        pass
+
+    def rooflines_of(run, form):
+        out = {}
+        steps = run["steps"]
+        knn_ms = run["kt"]["knn"][0]
+        if knn_ms > 0:
+            a = run["knn_work"] / (knn_ms / 1e3) / 1e12
+            if form == "fp32":
+                out["knn"] = {
+                    "kernel": "k_knn_fp32", "bound": "alu", "achieved": a, "peak": fp32_peak,
+                    "unit": "TFLOP/s", "frac": a / fp32_peak if fp32_peak else None,
+                    "traffic": None,
+                    "peak_source": "measured FP32 FMA throughput (pg_measure_fp32_peak, this run)"}
+            else:
+                peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1700.0))
+                out["knn"] = {
+                    "kernel": "k_knn_tc", "bound": "tensor", "achieved": a, "peak": peak,
+                    "unit": "TFLOP/s", "frac": a / peak, "traffic": None,
+                    "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)",
+                    "frac_of_burst": a / pk.get("bf16_tflops", peak)}
+        for name, kern, key in (("search", "k_search", "search_bytes"),
+                                ("prune", "k_prune", "prune_bytes")):
+            t_ms = run["kt"][name][0]
+            if t_ms > 0:
+                b = run["work"][key]
+                a = b / (t_ms / 1e3) / 1e9
+                out[name] = {
+                    "kernel": kern, "bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s",
+                    "frac": a / hbm, "traffic": None, "algorithmic_bytes_per_step": b / steps,
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+        if "search" in out:
+            out["search"]["evaluations_per_step"] = run["work"]["search_evaluations"] / steps
+        # DRAM traffic of a kernel's main launch from an ncu capture recorded
+        # in profiles/roofline_traffic.json, valid only while the kernel's
+        # source file is byte-identical to the one captured (else null)
+        try:
+            import hashlib
+            with open(os.path.join(ROOT, "profiles", "roofline_traffic.json")) as f:
+                rec = json.load(f)
+            for r in out.values():
+                ent = rec.get(r["kernel"])
+                if not ent or ent.get("n") != n:
+                    continue
+                with open(os.path.join(ROOT, ent["source"]), "rb") as f:
+                    if hashlib.sha256(f.read()).hexdigest() == ent["source_sha256"]:
+                        r["traffic"] = ent["dram_bytes_per_launch"]
+                        r["traffic_note"] = ent["note"]
+        except (OSError, ValueError, KeyError):
+            pass
+        return out
+
+    rooflines = rooflines_of(main_run, args.precision)
+    if other_run is not None:
+        forms[other]["rooflines"] = rooflines_of(other_run, other)
+    forms[args.precision]["rooflines"] = rooflines
     # the dominant single kernel of the step (connect is a chain of kernels)
     top = max(rooflines, key=lambda k: kt[k][0]) if rooflines else None
     roof = dict(rooflines[top], share_of_step=kt[top][0] / args.steps / ms) if top else None
 
     cpu = None
+    oracle_check = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         ns = min(n, 40000)
@@ -597,8 +636,26 @@ def run_ours(args):
                "sample": (f"oracle stages on the first {ns} points ({sampled:.1f} s of CPU work); "
                           f"kNN scaled by (n/ns)^2, other stages by n/ns"),
                "cpu": cpu_model()}
+        # Full-size exactness of one pruning pass (untimed): the first
+        # iteration's pass over the GPU's own kNN rows (alpha 66, all n rows),
+        # every row against the oracle given the same candidates.
+        K = w["K"]
+        gi, _ = pg.build_knn(ctx, Dd, K, precision=args.precision)
+        off = torch.arange(n + 1, dtype=torch.int64, device="cuda") * K
+        gn, gdg = pg.prune(ctx, Dd, off, gi.reshape(-1), w["R"], 66.0, precision=args.precision)
+        t0 = time.perf_counter()
+        on, odg = oracle.prune(D, off.cpu().numpy(), gi.cpu().numpy().ravel(), w["R"], 66.0)
+        secs = time.perf_counter() - t0
+        gnh, gdh = gn.cpu().numpy(), gdg.cpu().numpy()
+        bad = int(((gnh != on).any(1) | (gdh != odg)).sum())
+        oracle_check = {"step": "pruning pass 1 of iteration 1 (alpha 66) on the GPU's kNN rows",
+                        "rows": n, "mismatched_rows": bad,
+                        "mismatched_edges": int(np.abs(gdh.astype(np.int64) - odg).sum()
+                                                + (gnh != on).sum()),
+                        "oracle_seconds": secs, "cores": oracle.num_threads()}
+        del gi, gn, gdg
+    tie["oracle_check"] = oracle_check
 
-    ph = {k: statistics.mean(p[k] for p in phases) for k in phases[0]} if phases else {}
     line = {
         "metric": "build_points_per_s", "value": value, "unit": "points/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -607,16 +664,22 @@ def run_ours(args):
         "config": {"workload": w["name"], "n": n, "d": w["d"], "K": w["K"], "L": w["L"],
                    "R": w["R"], "alpha": [66.0, 60.0], "iters": 2, "route_layers_M": 16,
                    "nq": nq, "k": w["k"], "precision": args.precision,
+                   "index": ("RNG base graph (Algorithm 6) + NSWG routing layers (M 16) for query "
+                             "entry, upper_beam 16; recall_flat_entry = medoid entry only"),
+                   "query_index_form": (f"{args.precision} form (its graph equals the other "
+                                        "form's: forms_identical_graph)"),
                    "l2": (f"inputs larger than L2 ({D.nbytes >> 20} MB points)" if D.nbytes > 129e6
-                          else f"inputs smaller than L2 ({D.nbytes >> 20} MB points; test size)"), "parallelism": "replicas"},
-        "forms": forms, "forms_identical_graph": identical,
-        "queries": qres, "serving": serve, "screened_knn_d960": screen, "phase_s": ph,
+                          else f"inputs smaller than L2 ({D.nbytes >> 20} MB points; test size)"),
+                   "parallelism": "replicas"},
+        "forms": forms, "forms_identical_graph": identical, "tie_budget": tie,
+        "queries": qres, "serving": serve, "screened_knn_d960": screen, "phase_s": phases_mean,
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
         "kernel_launches_per_step": {k: v[1] / args.steps for k, v in kt.items()},
-        "connect_edges_per_step": conn_edges / max(1, args.steps + args.warmup),
-        "connect_full_rounds_per_step": conn_full / max(1, args.steps + args.warmup),
-        "roofline": roof, "rooflines": rooflines, "clocks": clk, "gpu_launches": launches, "e2e": e2e,
-        "cpu_baseline": cpu,
+        "connect_edges_per_step": main_run["conn_edges"] / args.steps,
+        "connect_full_rounds_per_step": main_run["conn_full"] / args.steps,
+        "fp32_simt_peak_tflops_measured": fp32_peak,
+        "roofline": roof, "rooflines": rooflines, "clocks": clk, "gpu_launches": launches,
+        "e2e": e2e, "cpu_baseline": cpu,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -117,10 +117,14 @@ typedef struct {
     int32_t connect_final;   /* RNG build: connectivity step after the final prune  */
     int32_t route_layers;    /* RNG build: add NSWG upper layers for query routing  */
     uint64_t seed;           /* level draw (SplitMix64, seed XOR id)                */
+    int32_t reuse_pruning;   /* K2P (Section 5.4): a refinement whose angle is >= the
+                                previous one's tests a candidate the previous pass kept
+                                only against new members (same lists, fewer tests) */
 } pg_build_params;
 
 /* Defaults: L2SQ, FP32, K=64, L=200, R=32, M=16, alpha 66/60, I=2,
- * connect_final=1, route_layers=1, seed=0.  params must not be NULL. */
+ * connect_final=1, route_layers=1, seed=0, reuse_pruning=1.  params must
+ * not be NULL. */
 void pg_default_params(pg_build_params *params);
 
 /* ---------------------------------------------------------------- context */
@@ -224,6 +228,23 @@ pg_status pg_prune(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric 
                    double alpha_deg, pg_precision precision, int32_t *nbr, int32_t *deg,
                    pg_prune_stats *host_stats);
 
+/* pg_prune with the K2P reuse of Section 5.4: prev_nbr [n][prev_R] /
+ * prev_deg [n] (DEVICE) are the lists that an earlier pruning of the same
+ * points kept, with an angle no larger than alpha_deg (the build passes the
+ * previous refinement's lists).  A candidate v found in prev_nbr's row of u
+ * was then tested against every member of that row that precedes it and was
+ * not occluded; the occlusion test of a pair depends only on u, v and w (a
+ * larger angle occludes less) and the scan order only on s(u, .), so v is
+ * tested only against kept members that are not in the previous row.  The
+ * lists equal pg_prune's; only "occlusion_tests" drops.  The caller
+ * guarantees the premise: lists that are not such an earlier pruning give
+ * other lists.  Other arguments and errors as pg_prune. */
+pg_status pg_prune_k2p(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
+                       const int64_t *cand_off, const int32_t *cand_ids, const int32_t *prev_nbr,
+                       const int32_t *prev_deg, int32_t prev_R, int32_t R, double alpha_deg,
+                       pg_precision precision, int32_t *nbr, int32_t *deg,
+                       pg_prune_stats *host_stats);
+
 /* Largest n accepted by pg_prune_noalloc. */
 #define PG_PRUNE_NOALLOC_MAX_N (1 << 20)
 
@@ -307,6 +328,16 @@ pg_status pg_search_graph(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_
  * caller and must outlive the index.  Synchronous. */
 pg_status pg_build_rng(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
                        const pg_build_params *params, pg_index **out);
+
+/* pg_build_rng from HOST memory: D_host [n][d] (host, pinned or pageable)
+ * is copied to a device buffer that the index owns, the build runs as
+ * pg_build_rng, and the base graph (layer 0) is copied back to the host
+ * arrays nbr_host [n][R] and deg_host [n].  Synchronous.  out may be NULL
+ * (the index is then destroyed before returning); otherwise *out is an
+ * index that owns its points. */
+pg_status pg_build_rng_host(pg_ctx *ctx, const float *D_host, int64_t n, int32_t d,
+                            const pg_build_params *params, int32_t *nbr_host, int32_t *deg_host,
+                            pg_index **out);
 
 /* Global NSWG construction, OptHNSW (Algorithm 7): levels drawn up front
  * (l(u) = floor(-ln U / ln M), U from SplitMix64(seed XOR u)); layer i
@@ -537,6 +568,13 @@ pg_status pg_serve_simulate(int32_t slots, int32_t max_batch, int64_t budget_byt
  * returns; the call then returns PG_ERR_TIMEOUT, like a kernel whose
  * pipeline wait expired, and the context stays usable. */
 pg_status pg_selftest_wait_timeout(pg_ctx *ctx, double seconds);
+
+/* Measured FP32 FMA throughput of the context's device (not from the paper:
+ * the SIMT roofline of the FP32 form's distance tiles): eight independent
+ * fused multiply-add chains per thread, 2048 threads per SM, timed with CUDA
+ * events on the context's stream; *host_tflops receives the best of three
+ * timed launches (2 flop per FMA).  Synchronous. */
+pg_status pg_measure_fp32_peak(pg_ctx *ctx, double *host_tflops);
 
 /* Seconds spent per build phase by the last build on this index:
  * knn, prune, union, connect, acquire, layers (host array of 6). */

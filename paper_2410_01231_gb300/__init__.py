@@ -40,7 +40,8 @@ i32, i64, dbl, u64 = C.c_int32, C.c_int64, C.c_double, C.c_uint64
 class BuildParams(C.Structure):
     _fields_ = [("metric", C.c_int), ("precision", C.c_int), ("K", i32), ("L", i32), ("R", i32),
                 ("M", i32), ("alpha_deg", dbl), ("alpha_final_deg", dbl), ("iters", i32),
-                ("connect_final", i32), ("route_layers", i32), ("seed", u64)]
+                ("connect_final", i32), ("route_layers", i32), ("seed", u64),
+                ("reuse_pruning", i32)]
 
 
 class PruneStats(C.Structure):
@@ -65,6 +66,8 @@ _sig("pg_ctx_launches", i64, [P])
 _sig("pg_build_knn", C.c_int, [P, P, i64, i32, C.c_int, i32, C.c_int, P, P])
 _sig("pg_knn_query", C.c_int, [P, P, i64, i32, C.c_int, P, i64, i32, C.c_int, P, P])
 _sig("pg_prune", C.c_int, [P, P, i64, i32, C.c_int, P, P, i32, dbl, C.c_int, P, P, P])
+_sig("pg_prune_k2p", C.c_int, [P, P, i64, i32, C.c_int, P, P, P, P, i32, i32, dbl, C.c_int, P, P,
+                               P])
 _sig("pg_reverse_union", C.c_int, [P, P, P, i64, i32, P, P, i64, P])
 _sig("pg_medoid", C.c_int, [P, P, i64, i32, C.c_int, P])
 _sig("pg_connect", C.c_int, [P, P, i64, i32, C.c_int, P, P, i32, i64, P])
@@ -73,6 +76,8 @@ _sig("pg_search_graph", C.c_int, [P, P, i64, i32, C.c_int, P, P, i32, P, P, i64,
                                   C.c_int, P, P])
 _sig("pg_build_rng", C.c_int, [P, P, i64, i32, P, P])
 _sig("pg_build_nswg", C.c_int, [P, P, i64, i32, P, P])
+_sig("pg_build_rng_host", C.c_int, [P, P, i64, i32, P, P, P, P])
+_sig("pg_measure_fp32_peak", C.c_int, [P, P])
 _sig("pg_search", C.c_int, [P, P, P, i64, i32, i32, i32, i32, C.c_int, P, P])
 _sig("pg_search_host", C.c_int, [P, P, P, i64, i32, i32, i32, i32, C.c_int, P, P])
 _sig("pg_index_destroy", None, [P])
@@ -110,6 +115,7 @@ _sig("pg_serve_simulate", C.c_int, [i32, i32, i64, i32, P, P, P, i32, i64, P, P,
 EXPORTS = ["pg_default_params", "pg_ctx_create", "pg_ctx_destroy", "pg_last_error", "pg_ctx_sync",
            "pg_ctx_launches", "pg_build_knn", "pg_knn_query", "pg_prune", "pg_reverse_union",
            "pg_medoid", "pg_connect", "pg_acquire_candidates", "pg_search_graph", "pg_build_rng",
+           "pg_build_rng_host", "pg_measure_fp32_peak", "pg_prune_k2p",
            "pg_build_nswg", "pg_search", "pg_search_host", "pg_index_destroy", "pg_index_info",
            "pg_index_layer", "pg_index_phase_seconds", "pg_index_export_layer",
            "pg_ctx_set_timing", "pg_ctx_set_tie_count", "pg_ctx_kernel_time", "pg_ctx_counter",
@@ -188,6 +194,12 @@ class Context:
                     "pg_ctx_kernel_work")
         return v.value
 
+    def measure_fp32_peak(self) -> float:
+        """Measured FP32 FMA throughput of the device in TFLOP/s (pg_measure_fp32_peak)."""
+        v = C.c_double()
+        self._check(_lib.pg_measure_fp32_peak(self._h, C.byref(v)), "pg_measure_fp32_peak")
+        return v.value
+
     def selftest_wait_timeout(self, seconds: float = 0.2):
         """Bounded-wait failure path (pg_selftest_wait_timeout): raises PGError TIMEOUT."""
         self._check(_lib.pg_selftest_wait_timeout(self._h, float(seconds)),
@@ -222,7 +234,10 @@ class Context:
 def default_params(**kw) -> BuildParams:
     p = BuildParams()
     _lib.pg_default_params(C.byref(p))
+    names = {f for f, _ in BuildParams._fields_}
     for k, v in kw.items():
+        if k not in names:
+            raise TypeError(f"unknown build parameter {k!r}")
         if k == "metric":
             v = METRIC[v] if isinstance(v, str) else v
         if k == "precision":
@@ -301,6 +316,28 @@ def prune(ctx: Context, D, off, cand, R: int, alpha_deg: float, metric="l2", pre
     ctx._check(_lib.pg_prune(ctx.handle, _ptr(D), n, d, METRIC[metric], _ptr(off), _ptr(cand), R,
                              float(alpha_deg), PRECISION[precision], _ptr(nbr), _ptr(deg),
                              C.byref(ps) if stats else None), "pg_prune")
+    if stats:
+        return nbr, deg, {k: int(getattr(ps, k)) for k, _ in PruneStats._fields_}
+    return nbr, deg
+
+
+def prune_k2p(ctx: Context, D, off, cand, prev_nbr, prev_deg, R: int, alpha_deg: float,
+              metric="l2", precision="fp32", stats: bool = False):
+    """pg_prune_k2p: alpha-pruning that reuses an earlier pruning of the same
+    points (prev_nbr [n][prev_R], prev_deg [n]) as Section 5.4's K2P."""
+    D = _dev(D, torch.float32, "D")
+    off = _dev(off, torch.int64, "off")
+    cand = _dev(cand, torch.int32, "cand")
+    prev_nbr = _dev(prev_nbr, torch.int32, "prev_nbr")
+    prev_deg = _dev(prev_deg, torch.int32, "prev_deg")
+    n, d = D.shape
+    nbr = torch.empty((n, R), dtype=torch.int32, device=D.device)
+    deg = torch.empty(n, dtype=torch.int32, device=D.device)
+    ps = PruneStats()
+    ctx._check(_lib.pg_prune_k2p(ctx.handle, _ptr(D), n, d, METRIC[metric], _ptr(off), _ptr(cand),
+                                 _ptr(prev_nbr), _ptr(prev_deg), prev_nbr.shape[1], R,
+                                 float(alpha_deg), PRECISION[precision], _ptr(nbr), _ptr(deg),
+                                 C.byref(ps) if stats else None), "pg_prune_k2p")
     if stats:
         return nbr, deg, {k: int(getattr(ps, k)) for k, _ in PruneStats._fields_}
     return nbr, deg
@@ -423,6 +460,32 @@ class Index:
     @classmethod
     def build_rng(cls, ctx: Context, D: torch.Tensor, **params):
         return cls._build(ctx, D, "pg_build_rng", params)
+
+    @classmethod
+    def build_rng_host(cls, ctx: Context, D: torch.Tensor, nbr: torch.Tensor, deg: torch.Tensor,
+                       keep: bool = False, **params):
+        """pg_build_rng_host: D [n][d] float32 in HOST memory (pinned or not) is
+        uploaded, built and the base graph written to the HOST tensors nbr
+        [n][R] and deg [n] (int32).  Returns an Index owning its points when
+        keep, else None."""
+        if D.is_cuda or nbr.is_cuda or deg.is_cuda:
+            raise ValueError("build_rng_host takes host tensors")
+        if D.dtype != torch.float32 or not D.is_contiguous() or D.dim() != 2:
+            raise ValueError("D must be a contiguous float32 [n][d] host tensor")
+        p = default_params(**params)
+        n = D.shape[0]
+        if (nbr.dtype != torch.int32 or deg.dtype != torch.int32 or tuple(nbr.shape) != (n, p.R)
+                or tuple(deg.shape) != (n,) or not nbr.is_contiguous()):
+            raise ValueError("nbr must be int32 [n][R] and deg int32 [n], contiguous")
+        h = C.c_void_p()
+        ctx._check(_lib.pg_build_rng_host(ctx.handle, C.c_void_p(D.data_ptr()), n, D.shape[1],
+                                          C.byref(p), C.c_void_p(nbr.data_ptr()),
+                                          C.c_void_p(deg.data_ptr()),
+                                          C.byref(h) if keep else None), "pg_build_rng_host")
+        if not keep:
+            return None
+        metric = {v: k for k, v in METRIC.items()}[p.metric]
+        return cls(ctx, h, None, metric, ctx.device)
 
     @classmethod
     def build_nswg(cls, ctx: Context, D: torch.Tensor, **params):

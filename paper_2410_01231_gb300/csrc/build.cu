@@ -24,7 +24,8 @@ pg_status pg_prune_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d, p
                             const int64_t *off, const int32_t *cand, int32_t R, double alpha_deg,
                             const DataFacts &facts, int32_t *nbr, int32_t *deg,
                             const uint8_t *D8 = nullptr, int64_t rows = 0,
-                            const int32_t *self_ids = nullptr);
+                            const int32_t *self_ids = nullptr, const int32_t *prev_nbr = nullptr,
+                            const int32_t *prev_deg = nullptr, int32_t prev_R = 0);
 pg_status pg_reverse_union_internal(pg_ctx *ctx, const int32_t *nbr, const int32_t *deg, int64_t n,
                                     int32_t R, int64_t *off, int32_t *ids);
 pg_status pg_medoid_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
@@ -175,7 +176,7 @@ pg_status iter_nsg(pg_ctx *ctx, const float *X, int64_t m, int32_t d, const pg_b
     *ep_out = ep;
     const int K = (int)std::min<int64_t>(p->K, m - 1);
     const int L = p->L;
-    Scratch<int32_t> knn_i, cand, nbr1, deg1, uids;
+    Scratch<int32_t> knn_i, cand, nbr1, deg1, uids, pv1n, pv1d, pv2n, pv2d;
     Scratch<float> knn_s;
     Scratch<int64_t> off, uoff;
     PG_TRY(knn_i.alloc(ctx, (size_t)(m * K)));
@@ -195,15 +196,45 @@ pg_status iter_nsg(pg_ctx *ctx, const float *X, int64_t m, int32_t d, const pg_b
     // the screened form gathers byte rows when the data are exact bytes
     Scratch<uint8_t> x8;
     if (pg_u8_usable(facts, p->metric, d, p->precision)) PG_TRY(pg_make_u8(ctx, X, m, d, x8));
-    auto refine = [&](double alpha, int do_connect) -> pg_status {
+    // K2P (Section 5.4): each pass may reuse the previous refinement's
+    // pass of the same kind (pass 1 on C(u), pass 2 on the union rows before
+    // connectivity) when its angle is at least the previous one
+    const bool k2p = p->reuse_pruning &&
+                     (p->iters >= 2 || (p->iters >= 1 && p->alpha_final_deg >= p->alpha_deg));
+    if (k2p) {
+        PG_TRY(pv1n.alloc(ctx, (size_t)(m * R)));
+        PG_TRY(pv1d.alloc(ctx, (size_t)m));
+        PG_TRY(pv2n.alloc(ctx, (size_t)(m * R)));
+        PG_TRY(pv2d.alloc(ctx, (size_t)m));
+    }
+    int refines = 0;
+    double prev_alpha = 0.0;
+    auto refine = [&](double alpha, int do_connect, bool last) -> pg_status {
+        const bool reuse = k2p && refines > 0 && alpha >= prev_alpha;
         clk.start(PH_PRUNE);
+        if (reuse) {
+            PG_TRY_CUDA(ctx, cudaMemcpyAsync(pv1n.p, nbr1.p, (size_t)(m * R) * 4,
+                                             cudaMemcpyDeviceToDevice, ctx->stream));
+            PG_TRY_CUDA(ctx, cudaMemcpyAsync(pv1d.p, deg1.p, (size_t)m * 4,
+                                             cudaMemcpyDeviceToDevice, ctx->stream));
+        }
         PG_TRY(pg_prune_internal(ctx, X, m, d, p->metric, off.p, cur, R, alpha, facts, nbr1.p,
-                                 deg1.p, x8.p));
+                                 deg1.p, x8.p, 0, nullptr, reuse ? pv1n.p : nullptr,
+                                 reuse ? pv1d.p : nullptr, R));
         clk.start(PH_UNION);
         PG_TRY(pg_reverse_union_internal(ctx, nbr1.p, deg1.p, m, R, uoff.p, uids.p));
         clk.start(PH_PRUNE);
         PG_TRY(pg_prune_internal(ctx, X, m, d, p->metric, uoff.p, uids.p, R, alpha, facts, nbr,
-                                 deg, x8.p));
+                                 deg, x8.p, 0, nullptr, reuse ? pv2n.p : nullptr,
+                                 reuse ? pv2d.p : nullptr, R));
+        if (k2p && !last) {  // pass-2 lists before connectivity, for the next refinement
+            PG_TRY_CUDA(ctx, cudaMemcpyAsync(pv2n.p, nbr, (size_t)(m * R) * 4,
+                                             cudaMemcpyDeviceToDevice, ctx->stream));
+            PG_TRY_CUDA(ctx, cudaMemcpyAsync(pv2d.p, deg, (size_t)m * 4,
+                                             cudaMemcpyDeviceToDevice, ctx->stream));
+        }
+        ++refines;
+        prev_alpha = alpha;
         if (do_connect) {
             clk.start(PH_CONNECT);
             PG_TRY(pg_connect_internal(ctx, X, m, d, p->metric, nbr, deg, R, ep, facts, knn_i.p, K,
@@ -212,7 +243,7 @@ pg_status iter_nsg(pg_ctx *ctx, const float *X, int64_t m, int32_t d, const pg_b
         return PG_OK;
     };
     for (int it = 0; it < p->iters; ++it) {
-        PG_TRY(refine(p->alpha_deg, 1));
+        PG_TRY(refine(p->alpha_deg, 1, false));
         if (!cand.p) PG_TRY(cand.alloc(ctx, (size_t)(m * L)));
         clk.start(PH_ACQUIRE);
         PG_TRY(pg_search_internal(ctx, X, m, d, p->metric, nbr, deg, R, nullptr, nullptr, m,
@@ -221,7 +252,7 @@ pg_status iter_nsg(pg_ctx *ctx, const float *X, int64_t m, int32_t d, const pg_b
         PG_LAUNCHED(ctx);
         cur = cand.p;
     }
-    PG_TRY(refine(p->alpha_final_deg, connect_final));
+    PG_TRY(refine(p->alpha_final_deg, connect_final, true));
     clk.stop();
     return pg_sync_check(ctx, "build");
 }
@@ -323,6 +354,48 @@ pg_status build_common(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
 extern "C" pg_status pg_build_rng(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
                                   const pg_build_params *params, pg_index **out) {
     return build_common(ctx, D, n, d, params, true, out);
+}
+
+extern "C" pg_status pg_build_rng_host(pg_ctx *ctx, const float *D_host, int64_t n, int32_t d,
+                                       const pg_build_params *params, int32_t *nbr_host,
+                                       int32_t *deg_host, pg_index **out) {
+    PG_TRY(check_params(ctx, D_host, n, d, params));
+    if (!nbr_host || !deg_host) return pg_fail(ctx, PG_ERR_INVALID_ARG, "null pointer");
+    if (out) *out = nullptr;
+    float *Dd = nullptr;
+    PG_TRY_CUDA(ctx, cudaMalloc(&Dd, (size_t)(n * d) * sizeof(float)));
+    cudaError_t e = cudaMemcpyAsync(Dd, D_host, (size_t)(n * d) * sizeof(float),
+                                    cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess) {
+        cudaFree(Dd);
+        return pg_cuda_fail(ctx, e, "pg_build_rng_host upload");
+    }
+    pg_index *idx = nullptr;
+    pg_status st = build_common(ctx, Dd, n, d, params, true, &idx);
+    if (st != PG_OK) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(Dd);
+        return st;
+    }
+    idx->owned = Dd;  // the index owns the uploaded points from here on
+    idx->capacity = n;
+    const pg_layer &b = idx->layers[0];
+    e = cudaMemcpyAsync(nbr_host, b.nbr, (size_t)(n * b.R) * sizeof(int32_t),
+                        cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(deg_host, b.deg, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                            ctx->stream);
+    if (e != cudaSuccess) {
+        delete idx;
+        return pg_cuda_fail(ctx, e, "pg_build_rng_host download");
+    }
+    st = pg_sync_check(ctx, "pg_build_rng_host");
+    if (st != PG_OK || !out) {
+        delete idx;
+        return st;
+    }
+    *out = idx;
+    return PG_OK;
 }
 
 extern "C" pg_status pg_build_nswg(pg_ctx *ctx, const float *D, int64_t n, int32_t d,

@@ -37,6 +37,7 @@ extern "C" void pg_default_params(pg_build_params *p) {
     p->connect_final = 1;
     p->route_layers = 1;
     p->seed = 0;
+    p->reuse_pruning = 1;
 }
 
 extern "C" pg_status pg_ctx_create(void *cuda_stream, size_t hbm_budget_bytes, pg_ctx **out) {

@@ -48,12 +48,18 @@ struct PruneParams {
     int *long_count;
     int *row_counter;    // dynamic row fetch
     int cap;             // capacity of this kernel
+    // K2P reuse (Section 5.4): the previous pruning of the same points with
+    // an angle <= this one, N_prev [rows][prev_R] / deg, or nullptr
+    const int32_t *prev_nbr;
+    const int32_t *prev_deg;
+    int prev_R;
 };
 
 // shared layout of one warp: c64[cap], cs[cap], ci[cap], runid[cap],
-// kid[RMAX], ks[RMAX], kpos[RMAX], uq[d] (FP32 row, or the byte row)
+// kid[RMAX], ks[RMAX], kpos[RMAX], kchk[RMAX], uq[d] (FP32 row, or the byte
+// row and the scanned candidate's byte row), cold[cap]
 __host__ __device__ inline size_t warp_smem_bytes(int cap, int d) {
-    return (size_t)cap * (4 + 4 + 4 + 8) + RMAX * (4 + 4 + 4) + (size_t)d * 4 + 64;
+    return (size_t)cap * (4 + 4 + 4 + 8 + 1) + RMAX * (4 + 4 + 4 + 4) + (size_t)d * 4 + 64;
 }
 
 // s(v, w) of two byte rows (lane li's chunk of v already in vreg when
@@ -106,8 +112,10 @@ __device__ void prune_row(const PruneParams &P, int64_t row, const int32_t *cand
     int *kid = runid + cap;
     float *ks = reinterpret_cast<float *>(kid + RMAX);
     int *kpos = reinterpret_cast<int *>(ks + RMAX);
-    float *uq = reinterpret_cast<float *>(kpos + RMAX);
+    int *kchk = kpos + RMAX;
+    float *uq = reinterpret_cast<float *>(kchk + RMAX);
     const int d = P.d, nch = d / 4;
+    unsigned char *cold = reinterpret_cast<unsigned char *>(uq + d);
     const float *D = P.D;
     const uint8_t *D8 = P.D8;
 
@@ -232,6 +240,32 @@ __device__ void prune_row(const PruneParams &P, int64_t row, const int32_t *cand
         }
     }
 
+    // 3b. K2P (Section 5.4): cold[j] marks a candidate that the previous
+    // pruning of u kept.  It was then tested against every member of
+    // N_prev(u) that precedes it and none occluded it; the test of a pair
+    // depends only on u, v and w (and a larger angle occludes less), and the
+    // scan order only on s(u, .), so such a candidate is tested only against
+    // kept members that are not in N_prev(u).
+    const bool reuse = P.prev_nbr != nullptr;
+    if (reuse) {
+        int pd = P.prev_deg[row];
+        pd = pd < 0 ? 0 : (pd > P.prev_R ? P.prev_R : pd);
+        const int32_t *pr = P.prev_nbr + row * P.prev_R;
+        const int p0 = lane < pd ? pr[lane] : -2;
+        const int p1 = lane + 32 < pd ? pr[lane + 32] : -2;
+        for (int base = 0; base < m; base += 32) {
+            const int jj = base + lane;
+            const int v = jj < m ? ci[jj] : -3;
+            bool hit = false;
+            for (int t = 0; t < pd; ++t) {
+                const int pv = __shfl_sync(0xffffffffu, t < 32 ? p0 : p1, t & 31);
+                hit |= pv == v;
+            }
+            if (jj < m) cold[jj] = hit ? 1 : 0;
+        }
+        __syncwarp();
+    }
+
     // 4. the scan
     int kept = 0;
     int j = 0;
@@ -242,15 +276,22 @@ __device__ void prune_row(const PruneParams &P, int64_t row, const int32_t *cand
 #pragma unroll
         for (int c = 0; c < 8; ++c) kr[c] = make_uint4(0u, 0u, 0u, 0u);
         float ksl = 0.f;  // s(u, w) of this lane's kept point
+        bool kold = false;  // this lane's kept point is in N_prev(u) (K2P)
         for (; j < m && kept < P.R; ++j) {
             const int v = ci[j];
             const float suv = cs[j];
-            if (lane < nch16)
-                vrow[lane] = __ldg(reinterpret_cast<const uint4 *>(D8 + (int64_t)v * d) + lane);
-            __syncwarp();
+            const bool vold = reuse && cold[j];
+            const bool mine = lane < kept && !(vold && kold);
+            if (P.count_ties && mine && near_tie(ksl, suv)) st.ties++;
+            const bool work = mine && ksl < suv;
             bool occ = false;
-            if (lane < kept && P.count_ties && near_tie(ksl, suv)) st.ties++;
-            if (lane < kept && ksl < suv) {  // exact data: the comparisons are exact
+            const bool loaded = __any_sync(0xffffffffu, work);
+            if (loaded) {
+                if (lane < nch16)
+                    vrow[lane] = __ldg(reinterpret_cast<const uint4 *>(D8 + (int64_t)v * d) + lane);
+                __syncwarp();
+            }
+            if (work) {  // exact data: the comparisons are exact
                 unsigned acc = 0;
 #pragma unroll
                 for (int c = 0; c < 8; ++c)
@@ -277,10 +318,18 @@ __device__ void prune_row(const PruneParams &P, int64_t row, const int32_t *cand
             }
             if (!__any_sync(0xffffffffu, occ)) {
                 if (lane == kept) {
+                    if (loaded) {
 #pragma unroll
-                    for (int c = 0; c < 8; ++c)
-                        if (c < nch16) kr[c] = vrow[c];
+                        for (int c = 0; c < 8; ++c)
+                            if (c < nch16) kr[c] = vrow[c];
+                    } else {
+                        const uint4 *xv = reinterpret_cast<const uint4 *>(D8 + (int64_t)v * d);
+#pragma unroll
+                        for (int c = 0; c < 8; ++c)
+                            if (c < nch16) kr[c] = __ldg(xv + c);
+                    }
                     ksl = suv;
+                    kold = vold;
                 }
                 if (lane == 0) {
                     kid[kept] = v;
@@ -298,13 +347,28 @@ __device__ void prune_row(const PruneParams &P, int64_t row, const int32_t *cand
         const float euv = P.em.err(suv);
         const float *xv = D + (int64_t)v * d;
         const uint8_t *xv8 = D8 ? D8 + (int64_t)v * d : nullptr;
+        // K2P: a candidate kept last time is tested only against new members
+        const bool vold = reuse && cold[j];
+        int nchk = kept;
+        if (vold) {
+            nchk = 0;
+            for (int base = 0; base < kept; base += 32) {
+                const int t = base + lane;
+                const bool need = t < kept && !cold[kpos[t]];
+                const unsigned bal = __ballot_sync(0xffffffffu, need);
+                if (need) kchk[nchk + __popc(bal & ((1u << lane) - 1))] = t;
+                nchk += __popc(bal);
+            }
+            __syncwarp();
+        }
         uint4 vreg = make_uint4(0u, 0u, 0u, 0u);
-        if (D8 && li < (d >> 4) && (d >> 4) <= 8)
+        if (D8 && li < (d >> 4) && (d >> 4) <= 8 && nchk > 0)
             vreg = __ldg(reinterpret_cast<const uint4 *>(xv8) + li);
         bool occluded = false;
-        for (int kb = 0; kb < kept && !occluded; kb += 4) {
-            const int t = kb + team;
-            const bool active = t < kept;
+        for (int kb = 0; kb < nchk && !occluded; kb += 4) {
+            const int ti = kb + team;
+            const bool active = ti < nchk;
+            const int t = active ? (vold ? kchk[ti] : ti) : 0;
             const int w = active ? kid[t] : v;
             const float svw =
                 D8 ? kept_dist_u8(xv8, vreg, D8 + (int64_t)w * d, d, li)
@@ -581,8 +645,12 @@ pg_status pg_reverse_union_internal(pg_ctx *ctx, const int32_t *nbr, const int32
 pg_status pg_prune_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
                             const int64_t *off, const int32_t *cand, int32_t R, double alpha_deg,
                             const DataFacts &facts, int32_t *nbr, int32_t *deg,
-                            const uint8_t *D8, int64_t rows, const int32_t *self_ids) {
+                            const uint8_t *D8, int64_t rows, const int32_t *self_ids,
+                            const int32_t *prev_nbr, const int32_t *prev_deg, int32_t prev_R) {
     PruneParams P;
+    P.prev_nbr = prev_nbr;
+    P.prev_deg = prev_deg;
+    P.prev_R = prev_R;
     P.D = D;
     P.D8 = D8;
     P.n = n;
@@ -645,6 +713,9 @@ cudaError_t pg_prune_launch_on(cudaStream_t stream, int num_sms, const float *D,
                                const DataFacts &facts, int32_t *nbr, int32_t *deg, int *ints,
                                int *err, unsigned long long *counters) {
     PruneParams P;
+    P.prev_nbr = nullptr;
+    P.prev_deg = nullptr;
+    P.prev_R = 0;
     P.D = D;
     P.D8 = nullptr;
     P.n = n;
@@ -699,10 +770,11 @@ static pg_status check_common(pg_ctx *ctx, const float *D, int64_t n, int32_t d)
     return PG_OK;
 }
 
-extern "C" pg_status pg_prune(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
-                              const int64_t *cand_off, const int32_t *cand_ids, int32_t R,
-                              double alpha_deg, pg_precision precision, int32_t *nbr,
-                              int32_t *deg, pg_prune_stats *host_stats) {
+static pg_status prune_entry(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
+                             const int64_t *cand_off, const int32_t *cand_ids,
+                             const int32_t *prev_nbr, const int32_t *prev_deg, int32_t prev_R,
+                             int32_t R, double alpha_deg, pg_precision precision, int32_t *nbr,
+                             int32_t *deg, pg_prune_stats *host_stats, const char *what) {
     PG_TRY(check_common(ctx, D, n, d));
     if (!cand_off || !cand_ids || !nbr || !deg)
         return pg_fail(ctx, PG_ERR_INVALID_ARG, "null pointer");
@@ -717,7 +789,7 @@ extern "C" pg_status pg_prune(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
     if (pg_u8_usable(facts, metric, d, precision)) PG_TRY(pg_make_u8(ctx, D, n, d, d8));
     if (host_stats) PG_TRY(pg_reset_counters(ctx));
     PG_TRY(pg_prune_internal(ctx, D, n, d, metric, cand_off, cand_ids, R, alpha_deg, facts, nbr,
-                             deg, d8.p, 0, nullptr));
+                             deg, d8.p, 0, nullptr, prev_nbr, prev_deg, prev_R));
     if (host_stats) {
         unsigned long long c[PG_CNT_SLOTS];
         PG_TRY(pg_read_counters(ctx, c));
@@ -732,7 +804,29 @@ extern "C" pg_status pg_prune(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
         host_stats->near_ties = (int64_t)c[CNT_NEAR_TIE];
         return PG_OK;
     }
-    return pg_sync_check(ctx, "pg_prune");
+    return pg_sync_check(ctx, what);
+}
+
+extern "C" pg_status pg_prune(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
+                              const int64_t *cand_off, const int32_t *cand_ids, int32_t R,
+                              double alpha_deg, pg_precision precision, int32_t *nbr,
+                              int32_t *deg, pg_prune_stats *host_stats) {
+    return prune_entry(ctx, D, n, d, metric, cand_off, cand_ids, nullptr, nullptr, 0, R,
+                       alpha_deg, precision, nbr, deg, host_stats, "pg_prune");
+}
+
+extern "C" pg_status pg_prune_k2p(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
+                                  pg_metric metric, const int64_t *cand_off,
+                                  const int32_t *cand_ids, const int32_t *prev_nbr,
+                                  const int32_t *prev_deg, int32_t prev_R, int32_t R,
+                                  double alpha_deg, pg_precision precision, int32_t *nbr,
+                                  int32_t *deg, pg_prune_stats *host_stats) {
+    if (!ctx) return PG_ERR_INVALID_ARG;
+    if (!prev_nbr || !prev_deg) return pg_fail(ctx, PG_ERR_INVALID_ARG, "null previous lists");
+    if (prev_R < 1 || prev_R > RMAX)
+        return pg_fail(ctx, PG_ERR_INVALID_ARG, "need 1 <= prev_R <= %d", RMAX);
+    return prune_entry(ctx, D, n, d, metric, cand_off, cand_ids, prev_nbr, prev_deg, prev_R, R,
+                       alpha_deg, precision, nbr, deg, host_stats, "pg_prune_k2p");
 }
 
 extern "C" pg_status pg_reverse_union(pg_ctx *ctx, const int32_t *nbr, const int32_t *deg,

@@ -155,6 +155,32 @@ def test_full_size_build_steps_equal_the_oracle_on_every_row(ctx, pg, full):
     assert report["mismatched_rows"] == 0
 
 
+def test_connectivity_equals_the_oracle_on_a_262k_prefix(ctx, pg, full):
+    """The connectivity step (Algorithm 2 with the reading: link the smallest
+    unreached id from the nearest reached node with a free slot, then add
+    everything reachable from it) on the first 262,144 points of the bench
+    workload, given the GPU's own pruned graph (kNN K 64, pass 1, reverse
+    union, pass 2 at alpha 66): pg_connect adds exactly the oracle's edges.
+    At 1M points the oracle's scan of every reached node per round is too
+    slow, so the full-size test checks reachability there."""
+    D, _, w = full
+    m, K, R = 262_144, w["K"], w["R"]
+    X = np.ascontiguousarray(D[:m])
+    Xd = torch.from_numpy(X).cuda()
+    gi, _ = pg.build_knn(ctx, Xd, K, precision="bf16")
+    off = torch.arange(m + 1, dtype=torch.int64, device="cuda") * K
+    n1, d1 = pg.prune(ctx, Xd, off, gi.reshape(-1), R, 66.0, precision="bf16")
+    uo, ui = pg.reverse_union(ctx, n1, d1)
+    n2, d2 = pg.prune(ctx, Xd, uo, ui, R, 66.0, precision="bf16")
+    ep = pg.medoid(ctx, Xd)
+    pre_n, pre_d = n2.cpu().numpy(), d2.cpu().numpy()
+    added = pg.connect(ctx, Xd, n2, d2, ep)
+    assert added > 100  # the prefix is far from connected: many rounds are compared
+    on, od, oadded = oracle.connect(X, pre_n, pre_d, ep)
+    assert oadded == added
+    assert np.array_equal(d2.cpu().numpy(), od) and np.array_equal(n2.cpu().numpy(), on)
+
+
 def test_full_size_build_recall(ctx, pg, full):
     D, Q, w = full
     Dd = torch.from_numpy(D).cuda()
