@@ -120,10 +120,18 @@ typedef struct {
     int32_t reuse_pruning;   /* K2P (Section 5.4): a refinement whose angle is >= the
                                 previous one's tests a candidate the previous pass kept
                                 only against new members (same lists, fewer tests) */
+    double quality_target;   /* > 0: quality examination (Section 5.2) ends the OptKCNA
+                                loop of Algorithm 6 once the sampled k-CNA recall
+                                reaches it; `iters` is then the most iterations run.
+                                0: exactly `iters` iterations                        */
+    double quality_eps;      /* epsilon of Theorem 3 (sample size n_s), default 0.6   */
+    int32_t quality_k;       /* k of the recall r(u) (first k entries of C(u));
+                                0 = K                                                */
 } pg_build_params;
 
 /* Defaults: L2SQ, FP32, K=64, L=200, R=32, M=16, alpha 66/60, I=2,
- * connect_final=1, route_layers=1, seed=0, reuse_pruning=1.  params must
+ * connect_final=1, route_layers=1, seed=0, reuse_pruning=1,
+ * quality_target=0 (fixed I), quality_eps=0.6, quality_k=0 (K).  params must
  * not be NULL. */
 void pg_default_params(pg_build_params *params);
 
@@ -328,6 +336,39 @@ pg_status pg_search_graph(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_
  * caller and must outlive the index.  Synchronous. */
 pg_status pg_build_rng(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
                        const pg_build_params *params, pg_index **out);
+
+/* Quality examination of the k-CNA lists (Section 5.2): for each sampled
+ * point u = sample[i] (DEVICE, ns ids in [0, n)), recall[i] (DEVICE,
+ * double) = r(u), the share of the first k entries of row u of cand
+ * (DEVICE [n][L], -1 padded, the k-CNA lists C(u)) that are among the exact
+ * k nearest points of u other than u: an entry counts once when its id is
+ * valid, not u and not repeated, and its FP64 distance to u is at most the
+ * exact k-th distance (ties count).  *host_mean (host, may be NULL) receives
+ * the mean over the sample, the estimator r^(S) / n_s.  1 <= k <= min(L,
+ * 255), k < n.  Synchronous.  An id outside [0, n) in sample gives
+ * PG_ERR_DEVICE_CHECK. */
+pg_status pg_kcna_recall(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
+                         const int32_t *cand, int32_t L, int32_t k, const int32_t *sample,
+                         int64_t ns, double *recall, double *host_mean);
+
+/* Sample size of Theorem 3 (host only): the smallest n_s with
+ * n_s >= (8 + 2 eps) l ln(n) / eps^2, so that the sampled mean of r(u) is
+ * within eps / 2 of the exact mean with probability >= 1 - n^-l.  -1 for
+ * n < 2, eps <= 0 or l <= 0. */
+int64_t pg_quality_sample_size(int64_t n, double eps, double l);
+
+/* The sample the builds draw (host only): ns distinct ids of [0, n),
+ * ascending, from SplitMix64 outputs of seed XOR (0x51a3c0ffee000000 + c),
+ * c = 0, 1, ..., each mapped to the high 64 bits of z * n, repeats
+ * skipped.  host_ids [ns].  PG_ERR_INVALID_ARG unless 0 <= ns <= n < 2^31. */
+pg_status pg_quality_sample(int64_t n, int64_t ns, uint64_t seed, int32_t *host_ids);
+
+/* Quality examination record of the last build of this index (layer 0):
+ * *iters_run (host) = OptKCNA iterations run, *sample_size (host) = n_s
+ * (0 when the examination was off), host_estimates [iters_run] (host, may
+ * be NULL; at most 16) = the estimate after each iteration. */
+pg_status pg_index_quality(const pg_index *index, int32_t *iters_run, int64_t *sample_size,
+                           double *host_estimates);
 
 /* pg_build_rng from HOST memory: D_host [n][d] (host, pinned or pageable)
  * is copied to a device buffer that the index owns, the build runs as

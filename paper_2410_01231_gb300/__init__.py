@@ -41,7 +41,8 @@ class BuildParams(C.Structure):
     _fields_ = [("metric", C.c_int), ("precision", C.c_int), ("K", i32), ("L", i32), ("R", i32),
                 ("M", i32), ("alpha_deg", dbl), ("alpha_final_deg", dbl), ("iters", i32),
                 ("connect_final", i32), ("route_layers", i32), ("seed", u64),
-                ("reuse_pruning", i32)]
+                ("reuse_pruning", i32), ("quality_target", dbl), ("quality_eps", dbl),
+                ("quality_k", i32)]
 
 
 class PruneStats(C.Structure):
@@ -66,6 +67,10 @@ _sig("pg_ctx_launches", i64, [P])
 _sig("pg_build_knn", C.c_int, [P, P, i64, i32, C.c_int, i32, C.c_int, P, P])
 _sig("pg_knn_query", C.c_int, [P, P, i64, i32, C.c_int, P, i64, i32, C.c_int, P, P])
 _sig("pg_prune", C.c_int, [P, P, i64, i32, C.c_int, P, P, i32, dbl, C.c_int, P, P, P])
+_sig("pg_kcna_recall", C.c_int, [P, P, i64, i32, C.c_int, P, i32, i32, P, i64, P, P])
+_sig("pg_quality_sample_size", i64, [i64, dbl, dbl])
+_sig("pg_quality_sample", C.c_int, [i64, i64, u64, P])
+_sig("pg_index_quality", C.c_int, [P, P, P, P])
 _sig("pg_prune_k2p", C.c_int, [P, P, i64, i32, C.c_int, P, P, P, P, i32, i32, dbl, C.c_int, P, P,
                                P])
 _sig("pg_reverse_union", C.c_int, [P, P, P, i64, i32, P, P, i64, P])
@@ -116,6 +121,7 @@ EXPORTS = ["pg_default_params", "pg_ctx_create", "pg_ctx_destroy", "pg_last_erro
            "pg_ctx_launches", "pg_build_knn", "pg_knn_query", "pg_prune", "pg_reverse_union",
            "pg_medoid", "pg_connect", "pg_acquire_candidates", "pg_search_graph", "pg_build_rng",
            "pg_build_rng_host", "pg_measure_fp32_peak", "pg_prune_k2p",
+           "pg_kcna_recall", "pg_quality_sample_size", "pg_quality_sample", "pg_index_quality",
            "pg_build_nswg", "pg_search", "pg_search_host", "pg_index_destroy", "pg_index_info",
            "pg_index_layer", "pg_index_phase_seconds", "pg_index_export_layer",
            "pg_ctx_set_timing", "pg_ctx_set_tie_count", "pg_ctx_kernel_time", "pg_ctx_counter",
@@ -319,6 +325,36 @@ def prune(ctx: Context, D, off, cand, R: int, alpha_deg: float, metric="l2", pre
     if stats:
         return nbr, deg, {k: int(getattr(ps, k)) for k, _ in PruneStats._fields_}
     return nbr, deg
+
+
+def kcna_recall(ctx: Context, D, cand, k: int, sample, metric="l2"):
+    """pg_kcna_recall: (r(u) for each sampled u as a float64 device tensor,
+    their mean) for the k-CNA rows cand [n][L] (Section 5.2)."""
+    D = _dev(D, torch.float32, "D")
+    cand = _dev(cand, torch.int32, "cand")
+    sample = _dev(sample, torch.int32, "sample")
+    n, d = D.shape
+    ns = sample.shape[0]
+    rec = torch.empty(ns, dtype=torch.float64, device=D.device)
+    mean = C.c_double()
+    ctx._check(_lib.pg_kcna_recall(ctx.handle, _ptr(D), n, d, METRIC[metric], _ptr(cand),
+                                   cand.shape[1], k, _ptr(sample), ns, _ptr(rec), C.byref(mean)),
+               "pg_kcna_recall")
+    return rec, mean.value
+
+
+def quality_sample_size(n: int, eps: float, l: float = 1.0) -> int:
+    """Theorem 3's sample size (pg_quality_sample_size, host only)."""
+    return int(_lib.pg_quality_sample_size(int(n), float(eps), float(l)))
+
+
+def quality_sample(n: int, ns: int, seed: int) -> np.ndarray:
+    """The builds' sample of ns distinct ids of [0, n) (pg_quality_sample, host only)."""
+    out = np.empty(max(ns, 1), np.int32)
+    st = _lib.pg_quality_sample(int(n), int(ns), int(seed), out.ctypes.data)
+    if st != 0:
+        raise PGError(st, "pg_quality_sample")
+    return out[:ns]
 
 
 def prune_k2p(ctx: Context, D, off, cand, prev_nbr, prev_deg, R: int, alpha_deg: float,
@@ -531,6 +567,14 @@ class Index:
         X = _dev(X, torch.float32, "X")
         self.ctx._check(_lib.pg_index_insert(self.ctx.handle, self._h, _ptr(X), X.shape[0], ef,
                                              upper_beam), "pg_index_insert")
+
+    def quality(self):
+        """(OptKCNA iterations run, sample size n_s, estimates per iteration) of
+        the last build's quality examination (pg_index_quality)."""
+        it, ns = C.c_int32(), C.c_int64()
+        est = (C.c_double * 16)()
+        _lib.pg_index_quality(self._h, C.byref(it), C.byref(ns), est)
+        return it.value, ns.value, [est[i] for i in range(min(it.value, 16))]
 
     def phase_seconds(self):
         arr = (C.c_double * 6)()

@@ -34,6 +34,9 @@ pg_status pg_connect_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
                               int32_t *nbr, int32_t *deg, int32_t R, int64_t ep,
                               const DataFacts &facts, const int32_t *knn, int32_t K,
                               int64_t *host_added);
+pg_status pg_quality_estimate(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
+                              const int32_t *cand, int32_t L, int32_t k, double eps, uint64_t seed,
+                              double *est, int64_t *ns_out);
 
 namespace {
 
@@ -161,13 +164,25 @@ pg_status check_params(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
         return pg_fail(ctx, PG_ERR_INVALID_ARG, "bad metric");
     if (!pg_build_precision(p->precision))
         return pg_fail(ctx, PG_ERR_INVALID_ARG, "builds take FP32 or BF16 screening");
+    if (!(p->quality_target >= 0.0 && p->quality_target <= 1.0) ||
+        (p->quality_target > 0.0 && !(p->quality_eps > 0.0)) || p->quality_k < 0 ||
+        p->quality_k > 255)
+        return pg_fail(ctx, PG_ERR_INVALID_ARG,
+                       "need 0 <= quality_target <= 1, quality_eps > 0, 0 <= quality_k <= 255");
     return PG_OK;
 }
 
 // IterNSG on a dense dataset X [m][d]: writes nbr [m][R] / deg [m] (local ids)
+// Quality examination record of one IterNSG run.
+struct QualityRecord {
+    int32_t iters = 0;
+    int64_t ns = 0;
+    double est[16] = {0};
+};
+
 pg_status iter_nsg(pg_ctx *ctx, const float *X, int64_t m, int32_t d, const pg_build_params *p,
                    int R, int connect_final, int32_t *nbr, int32_t *deg, int64_t *ep_out,
-                   double *phase) {
+                   double *phase, QualityRecord *qrec = nullptr) {
     PhaseClock clk{ctx, phase};
     DataFacts facts;
     PG_TRY(pg_data_facts(ctx, X, m, d, p->metric, &facts));
@@ -242,6 +257,12 @@ pg_status iter_nsg(pg_ctx *ctx, const float *X, int64_t m, int32_t d, const pg_b
         }
         return PG_OK;
     };
+    // Algorithm 6: OptKCNA iterations until the quality examination
+    // (Section 5.2) accepts the k-CNA lists, at most `iters` of them; with
+    // the examination off, exactly `iters`
+    const bool qexam = p->quality_target > 0.0;
+    const int qk = std::min(p->quality_k > 0 ? p->quality_k : K, std::min(L, 255));
+    QualityRecord q;
     for (int it = 0; it < p->iters; ++it) {
         PG_TRY(refine(p->alpha_deg, 1, false));
         if (!cand.p) PG_TRY(cand.alloc(ctx, (size_t)(m * L)));
@@ -251,7 +272,17 @@ pg_status iter_nsg(pg_ctx *ctx, const float *X, int64_t m, int32_t d, const pg_b
         k_fill_off<<<g1, 256, 0, ctx->stream>>>(off.p, m, L);
         PG_LAUNCHED(ctx);
         cur = cand.p;
+        q.iters = it + 1;
+        if (qexam && qk < m) {
+            clk.stop();
+            double est = 0.0;
+            PG_TRY(pg_quality_estimate(ctx, X, m, d, p->metric, cand.p, L, qk, p->quality_eps,
+                                       p->seed + (uint64_t)it, &est, &q.ns));
+            if (it < 16) q.est[it] = est;
+            if (est >= p->quality_target) break;
+        }
     }
+    if (qrec) *qrec = q;
     PG_TRY(refine(p->alpha_final_deg, connect_final, true));
     clk.stop();
     return pg_sync_check(ctx, "build");
@@ -330,9 +361,13 @@ pg_status build_common(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
     idx->layers.resize(1);
     pg_status st = alloc_layer(ctx, idx->layers[0], n, p->R, n, true);
     int64_t ep = 0;
+    QualityRecord q;
     if (st == PG_OK)
         st = iter_nsg(ctx, D, n, d, p, p->R, rng ? p->connect_final : 0, idx->layers[0].nbr,
-                      idx->layers[0].deg, &ep, idx->phase);
+                      idx->layers[0].deg, &ep, idx->phase, &q);
+    idx->iters_run = q.iters;
+    idx->quality_ns = q.ns;
+    memcpy(idx->quality_est, q.est, sizeof q.est);
     idx->ep_base = ep;
     idx->ep_top = ep;
     if (st == PG_OK && (!rng || p->route_layers)) {
@@ -463,6 +498,16 @@ extern "C" pg_status pg_index_export_layer(pg_ctx *ctx, const pg_index *idx, int
         }
     }
     return pg_sync_check(ctx, "pg_index_export_layer");
+}
+
+extern "C" pg_status pg_index_quality(const pg_index *idx, int32_t *iters_run,
+                                      int64_t *sample_size, double *host_estimates) {
+    if (!idx) return PG_ERR_INVALID_ARG;
+    if (iters_run) *iters_run = idx->iters_run;
+    if (sample_size) *sample_size = idx->quality_ns;
+    if (host_estimates)
+        for (int i = 0; i < std::min(idx->iters_run, 16); ++i) host_estimates[i] = idx->quality_est[i];
+    return PG_OK;
 }
 
 extern "C" pg_status pg_index_phase_seconds(const pg_index *idx, double *host_seconds6) {

@@ -38,6 +38,9 @@ extern "C" void pg_default_params(pg_build_params *p) {
     p->route_layers = 1;
     p->seed = 0;
     p->reuse_pruning = 1;
+    p->quality_target = 0.0;
+    p->quality_eps = 0.6;
+    p->quality_k = 0;
 }
 
 extern "C" pg_status pg_ctx_create(void *cuda_stream, size_t hbm_budget_bytes, pg_ctx **out) {

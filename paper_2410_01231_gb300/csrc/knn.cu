@@ -471,6 +471,12 @@ pg_status pg_knn_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_
     return knn_core(ctx, D, n, d, metric, nullptr, n, 1, K, precision, ids, dist);
 }
 
+pg_status pg_knn_query_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
+                                pg_metric metric, const float *Q, int64_t nq, int32_t k,
+                                pg_precision precision, int32_t *ids, float *dist) {
+    return knn_core(ctx, D, n, d, metric, Q, nq, 0, k, precision, ids, dist);
+}
+
 extern "C" pg_status pg_build_knn(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
                                   pg_metric metric, int32_t K, pg_precision precision,
                                   int32_t *ids, float *dist) {

@@ -65,6 +65,9 @@ struct pg_index {
     std::vector<pg_layer> layers;
     int64_t ep_top = 0, ep_base = 0;
     double phase[6] = {0, 0, 0, 0, 0, 0};
+    int32_t iters_run = 0;     // OptKCNA iterations of the last build (layer 0)
+    int64_t quality_ns = 0;    // quality examination sample size (0: off)
+    double quality_est[16] = {0};
     pg_build_params params{};  // of the build: levels, degrees, pruning angle
     float *owned = nullptr;    // private copy of the points once reserved
     int64_t capacity = 0;      // rows of `owned`
