@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-queries", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-screen", action="store_true")
+    ap.add_argument("--sweep", action="store_true",
+                    help="alpha / I sweep on the workload instead of the benchmark line")
     return ap.parse_args()
 
 
@@ -687,10 +689,98 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_sweep(args):
+    """alpha and I sweeps on the 1M x 128 workload (analogues of Exp. 1-b and
+    Exp. 1-a), printed as one JSON line.
+
+    alpha (Exp. 1-b, k-CNA quality and efficiency): from the exact kNN graph,
+    one OptKCNA iteration at alpha (prune, reverse union, prune, connect, then
+    the k-CNA self-search of every point); the searches' throughput (points/s,
+    CUDA events), the mean out-degree of the pruned graph, and the recall of
+    the first 10 and K entries of C(u) on a 10,000-point sample (r(u) of
+    Section 5.2, pg_kcna_recall).
+    I (Exp. 1-a): full builds with I = 0..4 (alpha 66 / 60), build time and
+    query recall@10 / queries/s at beams 32, 48, 64 (routing layers on)."""
+    import torch
+    import paper_2410_01231_gb300 as pg
+
+    torch.cuda.set_device(0)
+    n = args.n or synthetic.WORKLOADS[WORKLOAD]["n"]
+    nq = args.nq or synthetic.WORKLOADS[WORKLOAD]["nq"]
+    D, Q, w = synthetic.workload(WORKLOAD, n=n, nq=nq)
+    K, L, R = w["K"], w["L"], w["R"]
+    Dd, Qd = torch.from_numpy(D).cuda(), torch.from_numpy(Q).cuda()
+    stream = torch.cuda.current_stream()
+    ctx = pg.Context(stream)
+    prec = args.precision
+
+    def events():
+        return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    knn, _ = pg.build_knn(ctx, Dd, K, precision=prec)
+    ep = pg.medoid(ctx, Dd)
+    off = torch.arange(n + 1, dtype=torch.int64, device="cuda") * K
+    sample = torch.from_numpy(pg.quality_sample(n, min(n, 10_000), 3)).cuda()
+    alphas = []
+    for alpha in (60.0, 62.0, 64.0, 66.0, 68.0, 70.0, 75.0):
+        n1, d1 = pg.prune(ctx, Dd, off, knn.reshape(-1), R, alpha, precision=prec)
+        uo, ui = pg.reverse_union(ctx, n1, d1)
+        n2, d2 = pg.prune(ctx, Dd, uo, ui, R, alpha, precision=prec)
+        pg.connect(ctx, Dd, n2, d2, ep)
+        pg.acquire_candidates(ctx, Dd, n2, d2, L, precision=prec)  # warm-up
+        e0, e1 = events()
+        e0.record(stream)
+        cand = pg.acquire_candidates(ctx, Dd, n2, d2, L, precision=prec)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        secs = e0.elapsed_time(e1) / 1e3
+        _, r10 = pg.kcna_recall(ctx, Dd, cand, 10, sample)
+        _, rK = pg.kcna_recall(ctx, Dd, cand, K, sample)
+        alphas.append({"alpha": alpha, "kcna_points_per_s": n / secs,
+                       "mean_out_degree": float(d2.float().mean()),
+                       "kcna_recall_at_10": r10, f"kcna_recall_at_{K}": rK})
+    iters = []
+    for it in range(5):
+        prm = dict(K=K, L=L, R=R, M=16, alpha_deg=66.0, alpha_final_deg=60.0, iters=it,
+                   precision=prec, route_layers=1, seed=0)
+        pg.Index.build_rng(ctx, Dd, **prm).close()
+        e0, e1 = events()
+        e0.record(stream)
+        idx = pg.Index.build_rng(ctx, Dd, **prm)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        build_s = e0.elapsed_time(e1) / 1e3
+        gt_i, gt_d = pg.knn_query(ctx, Dd, Qd, w["k"])
+        kth = gt_d[:, w["k"] - 1].clone()
+        curve = []
+        for beam in (32, 48, 64):
+            idx.search(Qd, w["k"], beam)
+            e0, e1 = events()
+            e0.record(stream)
+            ids, _ = idx.search(Qd, w["k"], beam)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            dq = ((Qd[:, None, :] - Dd[ids.long().clamp(min=0)]) ** 2).sum(-1)
+            ok = (dq <= kth[:, None]) & (ids >= 0)
+            rec = float(ok.sum(1).clamp(max=w["k"]).float().mean() / w["k"])
+            curve.append({"beam": beam, "recall_at_10": rec,
+                          "qps": nq / (e0.elapsed_time(e1) / 1e3)})
+        _, nb, dg = idx.layer(0)
+        iters.append({"iters": it, "build_s": build_s, "points_per_s": n / build_s,
+                      "mean_out_degree": float(dg.float().mean()), "queries": curve})
+        idx.close()
+    print(json.dumps({"sweep": "alpha (one OptKCNA iteration from the kNN graph) and I (full "
+                               "builds)", "workload": w["name"], "n": n, "d": w["d"], "K": K,
+                      "L": L, "R": R, "precision": prec, "alpha": alphas, "iters": iters}),
+          flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.sweep:
+        run_sweep(args)
     else:
         run_ours(args)
 

@@ -268,7 +268,7 @@ pg_status iter_nsg(pg_ctx *ctx, const float *X, int64_t m, int32_t d, const pg_b
         if (!cand.p) PG_TRY(cand.alloc(ctx, (size_t)(m * L)));
         clk.start(PH_ACQUIRE);
         PG_TRY(pg_search_internal(ctx, X, m, d, p->metric, nbr, deg, R, nullptr, nullptr, m,
-                                  nullptr, L, L, 1, cand.p, nullptr, x8.p));
+                                  nullptr, L, L, 1, cand.p, nullptr, x8.p, nullptr, &facts));
         k_fill_off<<<g1, 256, 0, ctx->stream>>>(off.p, m, L);
         PG_LAUNCHED(ctx);
         cur = cand.p;
@@ -365,6 +365,10 @@ pg_status build_common(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
     if (st == PG_OK)
         st = iter_nsg(ctx, D, n, d, p, p->R, rng ? p->connect_final : 0, idx->layers[0].nbr,
                       idx->layers[0].deg, &ep, idx->phase, &q);
+    if (st == PG_OK) {
+        st = pg_data_facts(ctx, D, n, d, p->metric, &idx->facts);
+        idx->has_facts = st == PG_OK;
+    }
     idx->iters_run = q.iters;
     idx->quality_ns = q.ns;
     memcpy(idx->quality_est, q.est, sizeof q.est);
@@ -548,6 +552,11 @@ static pg_status search_index(pg_ctx *ctx, const pg_index *idx, const float *Q, 
     if (nq == 0) return PG_OK;
     F8Rows f8{};
     if (precision == PG_PREC_FP8_SCREEN) PG_TRY(index_f8(ctx, idx, &f8));
+    // exactness of every (query, point) distance, for the search's comparator
+    DataFacts facts;
+    if (idx->has_facts) facts = idx->facts;
+    else PG_TRY(pg_data_facts(ctx, idx->D, idx->n, idx->d, idx->metric, &facts));
+    PG_TRY(pg_query_facts(ctx, Q, nq, idx->d, idx->metric, &facts));
     Scratch<int32_t> w, w2;
     Scratch<float> s2;
     PG_TRY(w.alloc(ctx, (size_t)nq));
@@ -561,14 +570,15 @@ static pg_status search_index(pg_ctx *ctx, const pg_index *idx, const float *Q, 
         for (int i = (int)idx->layers.size() - 1; i >= 1; --i) {
             const pg_layer &l = idx->layers[(size_t)i];
             PG_TRY(pg_search_internal(ctx, idx->D, idx->n, idx->d, idx->metric, l.nbr, l.deg, l.R,
-                                      l.rows, Q, nq, w.p, 1, upper_beam, 0, w2.p, s2.p));
+                                      l.rows, Q, nq, w.p, 1, upper_beam, 0, w2.p, s2.p, nullptr,
+                                      nullptr, &facts));
             std::swap(w.p, w2.p);
         }
     }
     const pg_layer &b = idx->layers[0];
     return pg_search_internal(ctx, idx->D, idx->n, idx->d, idx->metric, b.nbr, b.deg, b.R, nullptr,
                               Q, nq, w.p, k, beam, 0, out_ids, out_dist, nullptr,
-                              precision == PG_PREC_FP8_SCREEN ? &f8 : nullptr);
+                              precision == PG_PREC_FP8_SCREEN ? &f8 : nullptr, &facts);
 }
 
 static pg_status check_search(pg_ctx *ctx, const pg_index *idx, const float *Q, int64_t nq,
@@ -812,7 +822,7 @@ extern "C" pg_status pg_index_insert(pg_ctx *ctx, pg_index *idx, const float *X,
             PG_LAUNCHED(ctx);
             PG_TRY(pg_search_internal(ctx, Dall, n0, (int32_t)d, idx->metric, l.nbr, l.deg, Ri,
                                       l.rows, Q.p, nb, starts.p, 1, upper_beam, 0, out1.p,
-                                      out1s.p));
+                                      out1s.p, nullptr, nullptr, &facts));
             k_scatter_first<<<blocks(nb), 256, 0, ctx->stream>>>(w.p, sel.p, nb, out1.p, 1);
             PG_LAUNCHED(ctx);
         }
@@ -837,7 +847,8 @@ extern "C" pg_status pg_index_insert(pg_ctx *ctx, pg_index *idx, const float *X,
         k_gather_i32<<<blocks(ns), 256, 0, ctx->stream>>>(w.p, sel.p, ns, starts.p);
         PG_LAUNCHED(ctx);
         PG_TRY(pg_search_internal(ctx, Dall, n0, (int32_t)d, idx->metric, l.nbr, l.deg, Ri, l.rows,
-                                  Q.p, ns, starts.p, ef, ef, 0, W.p, Ws.p));
+                                  Q.p, ns, starts.p, ef, ef, 0, W.p, Ws.p, nullptr, nullptr,
+                                  &facts));
         k_scatter_first<<<blocks(ns), 256, 0, ctx->stream>>>(w.p, sel.p, ns, W.p, ef);
         PG_LAUNCHED(ctx);
         // N_i(u) = Prune(u, W_i)
@@ -916,5 +927,7 @@ extern "C" pg_status pg_index_insert(pg_ctx *ctx, pg_index *idx, const float *X,
         PG_TRY(pg_sync_check(ctx, "insert"));
     }
     idx->n = N;
+    idx->facts = facts;
+    idx->has_facts = 1;
     return pg_sync_check(ctx, "pg_index_insert");
 }

@@ -4,6 +4,8 @@
 #include <cstring>
 #include <cmath>
 
+#include <algorithm>
+
 #include "pg_internal.cuh"
 
 pg_status pg_fail(pg_ctx *ctx, pg_status st, const char *fmt, ...) {
@@ -343,6 +345,8 @@ DataFacts pg_reduce_facts(const float *blk, int blocks, int64_t n, int32_t d, pg
     DataFacts f;
     f.max_norm2 = nrm;
     f.max_abs = fmaxf(fabsf(mn), fabsf(mx));
+    f.min_v = mn;
+    f.max_v = mx;
     // Exact FP32 distances need integer rows whose every partial sum stays
     // below 2^24: d*(max-min)^2 for the difference form, 2*d*max|x|^2 for
     // the norm form |x|^2 + |y|^2 - 2<x,y>.
@@ -367,6 +371,24 @@ pg_status pg_data_facts(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_me
                                      cudaMemcpyDeviceToHost, ctx->stream));
     PG_TRY(pg_sync_check(ctx, "data facts"));
     *out = pg_reduce_facts(h.data(), blocks, n, d, metric);
+    return PG_OK;
+}
+
+pg_status pg_query_facts(pg_ctx *ctx, const float *Q, int64_t nq, int32_t d, pg_metric metric,
+                         DataFacts *f) {
+    if (nq <= 0) return PG_OK;
+    DataFacts fq;
+    PG_TRY(pg_data_facts(ctx, Q, nq, d, metric, &fq));
+    const double lo = std::min(f->min_v, fq.min_v), hi = std::max(f->max_v, fq.max_v);
+    const double mab = std::max(f->max_abs, fq.max_abs);
+    f->exact = f->exact && fq.exact && (double)d * (hi - lo) * (hi - lo) < 16777216.0 &&
+               2.0 * (double)d * mab * mab < 16777216.0;
+    f->bf16_exact = f->bf16_exact && fq.bf16_exact;
+    f->u8_exact = f->u8_exact && fq.u8_exact;
+    f->max_norm2 = std::max(f->max_norm2, fq.max_norm2);
+    f->max_abs = (float)mab;
+    f->min_v = (float)lo;
+    f->max_v = (float)hi;
     return PG_OK;
 }
 

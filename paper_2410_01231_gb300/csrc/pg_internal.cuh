@@ -44,6 +44,18 @@ struct pg_ctx {
     double timer_work[16] = {0};  // algorithmic flops or bytes of the timed launches
 };
 
+// Data facts computed once per dataset: whether every FP32 distance the
+// kernels form is exact (integer-valued rows small enough that all partial
+// sums stay below 2^24), and the largest squared row norm.
+struct DataFacts {
+    int exact = 0;
+    int bf16_exact = 0;  // integer rows with |x| <= 256: the BF16 copy is exact
+    int u8_exact = 0;    // integer rows in [0, 255]: a byte copy is exact
+    float max_norm2 = 0.f;
+    float max_abs = 0.f;
+    float min_v = 0.f, max_v = 0.f;  // value range of the rows
+};
+
 // ------------------------------------------------------------------ index
 // One layer of an index and the index itself (built in build.cu, written
 // and read by index_io.cu).
@@ -68,6 +80,8 @@ struct pg_index {
     int32_t iters_run = 0;     // OptKCNA iterations of the last build (layer 0)
     int64_t quality_ns = 0;    // quality examination sample size (0: off)
     double quality_est[16] = {0};
+    DataFacts facts{};         // of the points (kept up to date by insertion)
+    int has_facts = 0;
     pg_build_params params{};  // of the build: levels, degrees, pruning angle
     float *owned = nullptr;    // private copy of the points once reserved
     int64_t capacity = 0;      // rows of `owned`
@@ -98,13 +112,14 @@ struct F8Rows {
 
 // Batched beam search (Algorithm 1), one warp per query: self mode (Q null,
 // query i is row i from start i) or queries Q from starts; D8 the byte rows
-// (self mode, exact data), f8 the FP8 rows (screened queries).
+// (self mode, exact data), f8 the FP8 rows (screened queries); facts the
+// data facts of D (nullptr: computed here, which synchronises the stream).
 pg_status pg_search_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
                              const int32_t *nbr, const int32_t *deg, int32_t R,
                              const int32_t *rows, const float *Q, int64_t nq,
                              const int32_t *starts, int32_t k, int32_t L, int self,
                              int32_t *out_i, float *out_s, const uint8_t *D8 = nullptr,
-                             const F8Rows *f8 = nullptr);
+                             const F8Rows *f8 = nullptr, const DataFacts *facts = nullptr);
 
 // named kernel timers
 enum {
@@ -198,18 +213,14 @@ pg_status pg_reset_counters(pg_ctx *ctx);
 pg_status pg_read_counters(pg_ctx *ctx, unsigned long long *host32);
 
 // ---------------------------------------------------------- arithmetic facts
-// Data facts computed once per dataset: whether every FP32 distance the
-// kernels form is exact (integer-valued rows small enough that all partial
-// sums stay below 2^24), and the largest squared row norm.
-struct DataFacts {
-    int exact = 0;
-    int bf16_exact = 0;  // integer rows with |x| <= 256: the BF16 copy is exact
-    int u8_exact = 0;    // integer rows in [0, 255]: a byte copy is exact
-    float max_norm2 = 0.f;
-    float max_abs = 0.f;
-};
+// The facts of D [n][d] (one kernel pass; synchronises the stream).
 pg_status pg_data_facts(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
                         DataFacts *out);
+// Extend the facts of D to the pairs (query row, row of D) of Q [nq][d]:
+// exact only if both sides are and the combined range keeps every partial
+// sum below 2^24; the norm and value bounds cover both.
+pg_status pg_query_facts(pg_ctx *ctx, const float *Q, int64_t nq, int32_t d, pg_metric metric,
+                         DataFacts *f);
 // The facts from the per-block results of k_data_facts (host copy, `blocks`
 // groups of {integral, min, max, max squared norm}); shared by every entry
 // point so that all of them take the same exactness decisions.

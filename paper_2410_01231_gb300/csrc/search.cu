@@ -21,12 +21,22 @@
 // node that was evaluated and left the pool can never re-enter it; the
 // lossy table therefore changes the work done, never the result.
 //
+// Exactness.  On integer rows whose partial sums stay below 2^24 (and
+// queries inside the rows' value range) every FP32 distance is exact.  On
+// other rows the pool order is decided by an exact comparator: two FP32
+// distances further apart than their rigorous rounding bounds are ordered
+// by FP32; nearer ones by their FP64 distances with the CPU reference's
+// sequential order, computed on first need and kept beside the pool entry.
+// The pool, its truncation at L, the expansion order and the output are
+// therefore those of Algorithm 1 on FP64 distances.
+//
 // FP8-screened queries rank the expansion candidates by distances from the
 // index's FP8 E4M3 rows (decoded row scale * e against the FP32 query: the
 // squared L2 distance, or the chord from the dot product); at the end the
 // whole pool is re-measured in FP32 and the k best by (s, id) are returned.
 #include <cuda_fp8.h>
 
+#include <algorithm>
 #include <climits>
 #include <mutex>
 
@@ -62,15 +72,91 @@ struct SearchParams {
     int *err;
     unsigned long long *counters;
     int *qcounter;
+    int cert;   // near ties decided in FP64 (else every FP32 distance is exact)
+    float rel;  // L2: |s32 - s64| <= rel * s32
+    float nm;   // largest squared row norm of D (chord bound)
 };
 
 // the pool arrays hold an even number of slots, so that the query row that
 // follows the table and the staging area starts on a 16-byte boundary
 __host__ __device__ inline int pool_slots(int L) { return (L + 1) & ~1; }
 
-__host__ __device__ inline size_t search_warp_smem(int L, int hbits, int d) {
+// certified mode adds the FP64 distance of every pool entry and of the 32
+// staged candidates (NaN until computed) in front of the rest
+__host__ __device__ inline size_t search_warp_smem(int L, int hbits, int d, bool cert) {
     size_t b = (size_t)pool_slots(L) * 8 + ((size_t)4 << hbits) + 32 * 8 + (size_t)d * 4;
+    if (cert) b += (size_t)pool_slots(L) * 8 + 32 * 8;
     return (b + 15) & ~(size_t)15;
+}
+
+// Exact comparator of the certified mode: distances further apart than the
+// sum of their bounds are ordered by FP32, others by (FP64, id).
+struct ExactCmp {
+    int metric;
+    float rel;   // L2 bound relative to the FP32 value
+    float abs2;  // chord: twice the absolute bound
+    const float *q;
+    const float *D;
+    int d;
+    __device__ __forceinline__ bool near(float a, float b) const {
+        const float diff = fabsf(a - b);
+        return metric == 0 ? diff <= 2.02f * rel * fmaxf(a, b) : diff <= abs2;
+    }
+    __device__ __forceinline__ double s64(int id) const {
+        return dist64_rows(q, D + (int64_t)id * d, d, metric);
+    }
+    // FP64 distance of a pool or staging slot, computed on first need
+    __device__ __forceinline__ double cached(double *slot, int id) const {
+        double v = *slot;
+        if (v != v) {
+            v = s64(id);
+            *slot = v;
+        }
+        return v;
+    }
+};
+
+// (s, id) order of a candidate (s, *a64, aid) against slot (t, *b64, bid)
+__device__ __forceinline__ bool xless(const ExactCmp &X, float a, double *a64, int aid, float b,
+                                      double *b64, int bid) {
+    if (!X.near(a, b)) return a < b;
+    const double x = X.cached(a64, aid), y = X.cached(b64, bid);
+    return x < y || (x == y && aid < bid);
+}
+
+// Exact lower bound of (s, id) in the pool [0, size) (sorted in exact order):
+// a bracket on the FP32 keys widened by twice the bound (keys may be out of
+// FP32 order only inside a near-tie run), then exact comparisons inside.
+// *dup = the id is present.
+__device__ __forceinline__ int pool_lower_bound_exact(const ExactCmp &X, const float *pd,
+                                                      const int *pi, double *pd64, int size,
+                                                      float s, double *s64, int id, bool *dup) {
+    const float w = X.metric == 0 ? 4.2f * X.rel * s : 2.1f * X.abs2;
+    const float lo_key = s - w, hi_key = s + w;
+    int a = 0, hi = size;
+    while (a < hi) {
+        const int mid = (a + hi) >> 1;
+        if (pd[mid] < lo_key) a = mid + 1;
+        else hi = mid;
+    }
+    int b = a;
+    hi = size;
+    while (b < hi) {
+        const int mid = (b + hi) >> 1;
+        if (pd[mid] <= hi_key) b = mid + 1;
+        else hi = mid;
+    }
+    int pos = a;
+    *dup = false;
+    for (int i = a; i < b; ++i) {
+        const int eid = pi[i] & ID_MASK;
+        if (eid == id) {
+            *dup = true;
+            return i;
+        }
+        if (xless(X, pd[i], pd64 + i, eid, s, s64, id)) pos = i + 1;
+    }
+    return pos;
 }
 
 __device__ __forceinline__ int pool_lower_bound(const float *pd, const int *pi, int size, float s,
@@ -145,14 +231,50 @@ __device__ __forceinline__ float team8_dist_f8(const SearchParams &P, const floa
     return fmaxf(2.f - 2.f * sc * team8_f8<false>(q, row, P.d, li, sc), 0.f);
 }
 
-template <bool kF8>
+// Register bitonic sort of one (s, s64, id, pos) per lane across the warp
+// by the exact comparator; a lane that needs the partner's FP64 distance
+// computes it from the partner's id (the same value the partner computes).
+__device__ __forceinline__ void warp_sort32_exact(const ExactCmp &X, float &key, double &k64,
+                                                  int &id, int &pos) {
+    const int lane = threadIdx.x & 31;
+    for (int k = 2; k <= 32; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            float ok = __shfl_xor_sync(0xffffffffu, key, j);
+            double o64 = __shfl_xor_sync(0xffffffffu, k64, j);
+            int oi = __shfl_xor_sync(0xffffffffu, id, j);
+            int op = __shfl_xor_sync(0xffffffffu, pos, j);
+            const bool lower = (lane & j) == 0;
+            const bool up = (lane & k) == 0;
+            bool other_less, mine_less;
+            if (id == INT_MAX || oi == INT_MAX) {  // empty slots sort last
+                other_less = pair_less(ok, oi, key, id);
+                mine_less = pair_less(key, id, ok, oi);
+            } else {
+                other_less = xless(X, ok, &o64, oi, key, &k64, id);
+                mine_less = xless(X, key, &k64, id, ok, &o64, oi);
+            }
+            const bool take_other = (lower == up) ? other_less : mine_less;
+            if (take_other) {
+                key = ok;
+                k64 = o64;
+                id = oi;
+                pos = op;
+            }
+        }
+    }
+}
+
+template <bool kF8, bool kCert>
 __device__ void search_one(const SearchParams &P, int64_t qi, unsigned char *ws,
                            unsigned long long &n_exp, unsigned long long &n_eval,
                            unsigned long long &n_rerank) {
     const int lane = threadIdx.x & 31, team = lane >> 3, li = lane & 7;
     const int L = P.L, d = P.d, nch = d / 4;
     const int Lp = pool_slots(L);
-    float *pdA = reinterpret_cast<float *>(ws);
+    constexpr bool cert = kCert;
+    double *pd64 = reinterpret_cast<double *>(ws);  // certified mode only
+    double *nd64 = pd64 + Lp;
+    float *pdA = reinterpret_cast<float *>(cert ? reinterpret_cast<unsigned char *>(nd64 + 32) : ws);
     int *piA = reinterpret_cast<int *>(pdA + Lp);
     int *htab = piA + Lp;
     const int H = 1 << P.hbits;
@@ -173,6 +295,16 @@ __device__ void search_one(const SearchParams &P, int64_t qi, unsigned char *ws,
     }
     for (int h = lane; h < H; h += 32) htab[h] = -1;
     constexpr bool f8 = kF8;  // FP8 rows (P.F8) in use
+    ExactCmp X{P.metric, P.rel, 0.f, q, P.D, d};
+    if (cert && P.metric != 0) {
+        // chord bound with the larger of the rows' and the query's norms
+        __syncwarp();
+        float qq = 0.f;
+        for (int c = lane; c < d; c += 32) qq = fmaf(q[c], q[c], qq);
+        for (int o = 16; o; o >>= 1) qq += __shfl_xor_sync(0xffffffffu, qq, o);
+        const double u = 5.9604644775390625e-08, nm = fmax((double)P.nm, (double)qq * 1.001);
+        X.abs2 = (float)(2.0 * ((2.0 * (d + 2) * u * nm + u * (2.0 + 2.0 * nm)) * 1.01 + 1e-12));
+    }
     int start = P.self ? (int)qi : P.starts[qi];
     bool bad = start < 0 || start >= P.n;
     if (bad) {
@@ -190,9 +322,11 @@ __device__ void search_one(const SearchParams &P, int64_t qi, unsigned char *ws,
                         P.metric);
     }
     int size = 1, cursor = 0;
+    const double nan64 = __longlong_as_double(0x7ff8000000000000ll);
     if (lane == 0) {
         pdA[0] = s0;
         piA[0] = start;
+        if (cert) pd64[0] = nan64;
         htab[hslot(start, P.hbits)] = start;
     }
     __syncwarp();
@@ -268,10 +402,16 @@ __device__ void search_one(const SearchParams &P, int64_t qi, unsigned char *ws,
             __syncwarp();
             float s = INFINITY;
             int id = INT_MAX;
+            double s64 = nan64;  // certified mode: FP64 distance once computed
+            int cpos = L;        // certified mode: exact slot against the pool
             if (lane < cnt) {
                 s = nd[lane];
                 id = ni[lane];
-                if (size == L && !pair_less(s, id, pdA[L - 1], piA[L - 1] & ID_MASK)) {
+                if (cert) {
+                    bool dup = false;
+                    cpos = pool_lower_bound_exact(X, pdA, piA, pd64, size, s, &s64, id, &dup);
+                    if (dup || cpos >= L) id = INT_MAX;
+                } else if (size == L && !pair_less(s, id, pdA[L - 1], piA[L - 1] & ID_MASK)) {
                     id = INT_MAX;
                 } else {
                     int pos = pool_lower_bound(pdA, piA, size, s, id);
@@ -283,11 +423,14 @@ __device__ void search_one(const SearchParams &P, int64_t qi, unsigned char *ws,
             const int m2 = __popc(live);
             if (m2 == 0) continue;
             if (m2 > 1) {
-                warp_sort32(s, id);  // survivors first, ascending
+                if (cert) warp_sort32_exact(X, s, s64, id, cpos);
+                else warp_sort32(s, id);  // survivors first, ascending
             } else {
                 const int src = __ffs(live) - 1;
                 s = __shfl_sync(0xffffffffu, s, src);
                 id = __shfl_sync(0xffffffffu, id, src);
+                s64 = __shfl_sync(0xffffffffu, s64, src);
+                cpos = __shfl_sync(0xffffffffu, cpos, src);
                 if (lane != 0) {
                     s = INFINITY;
                     id = INT_MAX;
@@ -297,10 +440,12 @@ __device__ void search_one(const SearchParams &P, int64_t qi, unsigned char *ws,
             if (lane < m2) {
                 nd[lane] = s;
                 ni[lane] = id;
+                if (cert) nd64[lane] = s64;
             }
             // final slots of the new entries, against the pool before the merge
             int mydst = L;
-            if (lane < m2) mydst = lane + pool_lower_bound(pdA, piA, size, s, id);
+            if (lane < m2)
+                mydst = lane + (cert ? cpos : pool_lower_bound(pdA, piA, size, s, id));
             const int first = __shfl_sync(0xffffffffu, mydst, 0);
             __syncwarp();
             // entries at or after `first` move right by the number of new
@@ -311,14 +456,18 @@ __device__ void search_one(const SearchParams &P, int64_t qi, unsigned char *ws,
                 const int i = c0 + lane;
                 float es = 0.f;
                 int eid = 0, dst = L;
+                double e64 = nan64;
                 if (i < size) {
                     es = pdA[i];
                     eid = piA[i];
                     const int key = eid & ID_MASK;
+                    if (cert) e64 = pd64[i];
                     int lo = 0, hi = m2;
                     while (lo < hi) {
                         const int mid = (lo + hi) >> 1;
-                        if (pair_less(nd[mid], ni[mid], es, key)) lo = mid + 1;
+                        const bool less = cert ? xless(X, nd[mid], nd64 + mid, ni[mid], es, &e64, key)
+                                               : pair_less(nd[mid], ni[mid], es, key);
+                        if (less) lo = mid + 1;
                         else hi = mid;
                     }
                     dst = i + lo;
@@ -327,12 +476,14 @@ __device__ void search_one(const SearchParams &P, int64_t qi, unsigned char *ws,
                 if (dst < L) {
                     pdA[dst] = es;
                     piA[dst] = eid;
+                    if (cert) pd64[dst] = e64;
                 }
                 __syncwarp();
             }
             if (mydst < L) {
                 pdA[mydst] = s;
                 piA[mydst] = id;
+                if (cert) pd64[mydst] = s64;
             }
             size = min(L, size + m2);
             if (first < cursor) cursor = first;
@@ -415,18 +566,18 @@ __device__ void search_one(const SearchParams &P, int64_t qi, unsigned char *ws,
     __syncwarp();
 }
 
-template <bool kF8>
+template <bool kF8, bool kCert>
 __global__ void __launch_bounds__(SW * 32, 8) k_search(SearchParams P) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    unsigned char *ws = smem + (size_t)wid * search_warp_smem(P.L, P.hbits, P.d);
+    unsigned char *ws = smem + (size_t)wid * search_warp_smem(P.L, P.hbits, P.d, P.cert);
     unsigned long long n_exp = 0, n_eval = 0, n_rerank = 0;
     for (;;) {
         int64_t qi = 0;
         if (lane == 0) qi = atomicAdd(P.qcounter, 1);
         qi = __shfl_sync(0xffffffffu, qi, 0);
         if (qi >= P.nq) break;
-        search_one<kF8>(P, qi, ws, n_exp, n_eval, n_rerank);
+        search_one<kF8, kCert>(P, qi, ws, n_exp, n_eval, n_rerank);
     }
     if (lane == 0) {
         // algorithmic bytes: one row per evaluation (FP8 rows also their
@@ -448,9 +599,24 @@ pg_status pg_search_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d, 
                              const int32_t *nbr, const int32_t *deg, int32_t R,
                              const int32_t *rows, const float *Q, int64_t nq,
                              const int32_t *starts, int32_t k, int32_t L, int self,
-                             int32_t *out_i, float *out_s, const uint8_t *D8, const F8Rows *f8) {
+                             int32_t *out_i, float *out_s, const uint8_t *D8, const F8Rows *f8,
+                             const DataFacts *facts) {
     if (nq == 0) return PG_OK;
     SearchParams P;
+    // exactness: rows (and query rows) whose FP32 distances are exact need
+    // no FP64 decisions; facts given by the caller cover the queries too
+    DataFacts fd;
+    if (facts) {
+        fd = *facts;
+    } else {
+        PG_TRY(pg_data_facts(ctx, D, n, d, metric, &fd));
+        if (!self) PG_TRY(pg_query_facts(ctx, Q, nq, d, metric, &fd));
+    }
+    const bool exact = fd.exact != 0;
+    const ErrModel em = pg_err_model(metric, d, fd, false);
+    P.cert = !exact && !(self && D8) && !(!self && f8 && f8->q8);
+    P.rel = em.rel;
+    P.nm = fd.max_norm2;
     P.D = D;
     P.D8 = self ? D8 : nullptr;
     P.F8 = !self && f8 ? f8->q8 : nullptr;
@@ -482,14 +648,15 @@ pg_status pg_search_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d, 
     PG_TRY(qc.alloc(ctx, 1));
     PG_TRY_CUDA(ctx, cudaMemsetAsync(qc.p, 0, sizeof(int), ctx->stream));
     P.qcounter = qc.p;
-    size_t smem = search_warp_smem(L, hb, d) * SW;
+    size_t smem = search_warp_smem(L, hb, d, P.cert) * SW;
     if (smem > 227 * 1024)
         return pg_fail(ctx, PG_ERR_CAPACITY, "search: pool/table do not fit shared memory");
     // the shared-memory attribute is per kernel, not per launch: searches
     // of other contexts on other threads (the serving workers) may set a
     // different size, so setting it and launching are one critical section
     std::lock_guard<std::mutex> lk(search_launch_mu);
-    void (*kern)(SearchParams) = P.F8 ? k_search<true> : k_search<false>;
+    void (*kern)(SearchParams) =
+        P.F8 ? k_search<true, false> : (P.cert ? k_search<false, true> : k_search<false, false>);
     PG_TRY_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)smem));
     int bps = 0;

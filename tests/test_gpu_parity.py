@@ -320,14 +320,42 @@ def test_acquire_matches_oracle_integer(ctx, pg, L, precision):
     assert (host(cand) == ocand).all()
 
 
-def test_acquire_float_overlap(ctx, pg):
-    D = unit_points(2000, 96, 7)
-    nbr, deg = _graph(D, "cosine")
-    cand = host(pg.acquire_candidates(ctx, dev(D), dev(nbr), dev(deg), 64, "cosine"))
-    ocand = oracle.acquire(D, nbr, deg, 64, "cosine")
-    same = np.mean([len(set(cand[u]) & set(ocand[u])) / max(1, (ocand[u] >= 0).sum())
-                    for u in range(2000)])
-    assert same > 0.999
+@pytest.mark.parametrize("kind", ["float", "cosine"])
+@pytest.mark.parametrize("L", [1, 17, 64, 200])
+def test_acquire_real_rows_equal_the_oracle(ctx, pg, kind, L):
+    """Real-valued rows: near ties of the pool are decided by FP64 distances
+    (rigorous FP32 bounds elsewhere), so the k-CNA rows equal the FP64
+    oracle's element by element."""
+    D, metric = DATA[kind][0](), DATA[kind][1]
+    nbr, deg = _graph(D, metric)
+    cand = host(pg.acquire_candidates(ctx, dev(D), dev(nbr), dev(deg), L, metric))
+    ocand = oracle.acquire(D, nbr, deg, L, metric)
+    assert (cand == ocand).all()
+
+
+def _close(got, want):
+    """FP32 distances against FP64 values: within 1e-5 relative (1e-6
+    absolute near 0, where the chord 2 - 2<x,y> cancels)."""
+    return bool((np.abs(got - want) <= 1e-5 * np.maximum(np.abs(want), 0.1)).all())
+
+
+@pytest.mark.parametrize("kind", ["float", "cosine"])
+@pytest.mark.parametrize("L", [1, 10, 64, 256])
+def test_search_graph_real_rows_equal_the_oracle(ctx, pg, kind, L):
+    D, metric = DATA[kind][0](), DATA[kind][1]
+    nq = 300
+    if kind == "float":
+        Q, _ = synthetic.mixture_float(nq, D.shape[1], 16, 91)
+    else:
+        Q = unit_points(nq, D.shape[1], 92)
+    nbr, deg = _graph(D, metric)
+    starts = np.random.default_rng(9).integers(0, D.shape[0], size=nq).astype(np.int32)
+    k = min(10, L)
+    gi, gd = pg.search_graph(ctx, dev(D), dev(nbr), dev(deg), dev(Q), dev(starts), k, L, metric)
+    oi, od = oracle.search(D, nbr, deg, Q, starts, k, L, metric)
+    assert (host(gi) == oi).all()
+    m = oi >= 0
+    assert _close(host(gd)[m], od[m])
 
 
 @pytest.mark.parametrize("L", [1, 10, 64, 256])
@@ -394,6 +422,34 @@ def test_build_nswg_integer_matches_oracle(ctx, pg):
         assert (gid == lay.gid).all() and (dg == lay.deg).all() and (nb == lay.nbr).all(), i
 
 
+def test_build_nswg_cosine_equals_the_oracle(ctx, pg):
+    """Unit rows, cosine, FP32 form: kNN tiles with FP64 near-tie fixes,
+    pruning with FP64 rechecks and the beam search's exact comparator make
+    every layer equal the FP64 oracle's Algorithm 7 layers."""
+    D = unit_points(3000, 48, 13)
+    p = dict(K=20, L=40, R=24, M=12, alpha_deg=68.0, iters=2, seed=3)
+    idx = pg.Index.build_nswg(ctx, dev(D), metric="cosine", **p)
+    layers, ep, _ = oracle.build_nswg(D, 20, 40, 12, 24, 68.0, 60.0, 2, "cosine", seed=3)
+    info = idx.info()
+    assert info["n_layers"] == len(layers) and info["ep_top"] == ep
+    for i, lay in enumerate(layers):
+        gid, nb, dg = _export(idx, i)
+        assert (gid == lay.gid).all() and (dg == lay.deg).all() and (nb == lay.nbr).all(), i
+
+
+def test_build_rng_real_rows_equals_the_oracle(ctx, pg):
+    """Real-valued L2 rows (Gaussian mixture), FP32 form: the whole IterNSG
+    build (two OptKCNA iterations with K2P, final RNG refinement,
+    connectivity, medoid) equals the FP64 oracle's graph."""
+    D = float_points(3000, 64, 14)
+    idx = pg.Index.build_rng(ctx, dev(D), K=20, L=48, R=24, M=16, alpha_deg=66.0,
+                             alpha_final_deg=60.0, iters=2, route_layers=0)
+    onbr, odeg, oep = oracle.build_rng(D, 20, 48, 24, 66.0, 60.0, 2)
+    assert idx.info()["ep_base"] == oep
+    _, gnbr, gdeg = _export(idx, 0)
+    assert (gdeg == odeg).all() and (gnbr == onbr).all()
+
+
 @pytest.mark.parametrize("upper_beam", [1, 8])
 def test_insert_batches_match_oracle(ctx, pg, upper_beam):
     """Two insertion batches into an NSWG index (Algorithm 4 on a snapshot)
@@ -457,8 +513,18 @@ def test_build_nswg_cosine_properties_and_recall(ctx, pg):
         if gid.shape[0] <= R:
             for a in range(gid.shape[0]):
                 assert sorted(nb[a, : dg[a]]) == sorted(x for x in gid if x != gid[a])
-    ids, _ = idx.search(dev(Q), 10, 128)
+    ids, dist = idx.search(dev(Q), 10, 128)
     assert oracle.recall_at_k(host(ids), Q, D, 10, "cosine") >= 0.9
+    # the layered query on real rows equals the oracle's on the same layers
+    layers = []
+    for i in range(info["n_layers"]):
+        gid, nb, dg = _export(idx, i)
+        layers.append(oracle.Layer(None if i == 0 else gid, nb, dg, nb.shape[1]))
+    for ub in (1, 4):
+        ids, dist = idx.search(dev(Q), 10, 64, upper_beam=ub)
+        oi, od = oracle.search_nswg(D, layers, info["ep_top"], Q, 10, 64, "cosine", ef_upper=ub)
+        assert (host(ids) == oi).all(), ub
+        assert _close(host(dist)[oi >= 0], od[oi >= 0])
 
 
 def test_search_host_buffers_equal_device_path(ctx, pg):
