@@ -178,7 +178,10 @@ pg_status pg_ctx_kernel_work(pg_ctx *ctx, const char *name, double *work);
  * when the screened form gathers byte rows; "prune_edges" (kept edges),
  * "prune_fp64_rechecks" and "prune_fp64_flips" (decisions re-made in FP64,
  * and those whose FP64 outcome differed from the plain FP32 one), and
- * "prune_near_ties" (see pg_ctx_set_tie_count). */
+ * "prune_near_ties" (see pg_ctx_set_tie_count); "knn_fp64_rechecks" (kNN
+ * entries re-ordered by FP64 distance) and "knn_fallback_rows" (rows of
+ * the screened kNN that the certificate could not accept and the FP32
+ * tiles computed). */
 pg_status pg_ctx_counter(pg_ctx *ctx, const char *name, int64_t *value);
 
 /* Tie accounting of the pruning kernels (off by default): when on, every

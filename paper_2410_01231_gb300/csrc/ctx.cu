@@ -182,7 +182,8 @@ extern "C" pg_status pg_ctx_counter(pg_ctx *ctx, const char *name, int64_t *valu
                    {"prune_scanned", CNT_SCANNED},     {"prune_occlusion_tests", CNT_OCCL},
                    {"search_bytes", CNT_SEARCH_BYTES}, {"prune_bytes", CNT_PRUNE_BYTES},
                    {"prune_fp64_rechecks", CNT_RECHECK}, {"prune_fp64_flips", CNT_FLIP},
-                   {"prune_near_ties", CNT_NEAR_TIE},  {"prune_edges", CNT_EDGES}};
+                   {"prune_near_ties", CNT_NEAR_TIE},  {"prune_edges", CNT_EDGES},
+                   {"knn_fallback_rows", CNT_KNN_FALLBACK}, {"knn_fp64_rechecks", CNT_KNN_RECHECK}};
         for (const auto &e : dev) {
             if (strcmp(name, e.name) == 0) {
                 unsigned long long c[PG_CNT_SLOTS];

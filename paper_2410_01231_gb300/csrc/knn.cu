@@ -333,26 +333,128 @@ __global__ void k_knn_fix(const float *__restrict__ Q, const float *__restrict__
     }
 }
 
-// Screened form on non-integer data: the Kx BF16-nearest candidates of a
-// row re-measured in FP32 (difference form / chord, the same arithmetic as
-// the FP32 gathers) and the K best by (s, id) kept.  One warp per row.
-__global__ void k_knn_rerank(const float *__restrict__ Q, const float *__restrict__ X, int64_t nq,
-                             int d, int metric, int Kx, int K, const int32_t *__restrict__ ci,
-                             int32_t *__restrict__ out_i, float *__restrict__ out_s) {
+// ------------------------------------------------------ certified screen
+// The screened form on rows that are not BF16-exact.  Rows are centred on
+// the column means (L2 only: distances do not change) and split into BF16
+// hi + lo parts; the tile kernel contracts [hi | hi | lo] with [hi | lo | hi]
+// (hi.hi + hi.lo + lo.hi) and keeps each row's Ks nearest by that screened
+// distance.  k_knn_certify re-measures those Ks in FP32, re-orders near-tie
+// runs by FP64 distance, and accepts the row only if a rigorous bound shows
+// that no point outside the shortlist can come nearer than the K-th; other
+// rows take the FP32 tiles.  The result equals the FP32 form's.
+
+// Column sums of X (FP32 atomics; the mean only has to be some vector
+// close to the centre: any shift leaves the distances unchanged).
+__global__ void k_col_sums(const float *__restrict__ X, int64_t n, int d, int64_t rows_per_block,
+                           float *sums) {
+    const int c = blockIdx.y * blockDim.x + threadIdx.x;
+    if (c >= d) return;
+    const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
+    const int64_t r1 = min(n, r0 + rows_per_block);
+    float acc = 0.f;
+    for (int64_t r = r0; r < r1; ++r) acc += X[r * d + c];
+    atomicAdd(sums + c, acc);
+}
+
+// One warp per row: xh = x - mean (L2) or x (chord); hi = bf16(xh),
+// lo = bf16(xh - hi) (xh - hi is exact in FP32); xq row [hi | hi | lo],
+// xc row [hi | lo | hi], zero columns up to dp3; norms[r] = |xh|^2 in FP32
+// (L2) or 1 (chord: the tiles then give 2 - 2<x, y>); *maxn = the largest
+// |xh|^2 (float bits, non-negative, so integer order).
+__global__ void k_split_rows(const float *__restrict__ X, int64_t n, int d, int dp3,
+                             const float *__restrict__ colsum, float inv_n, int center,
+                             __nv_bfloat16 *__restrict__ xq, __nv_bfloat16 *__restrict__ xc,
+                             float *__restrict__ norms, unsigned *maxn) {
+    const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (r >= n) return;
+    const float *x = X + r * d;
+    __nv_bfloat16 *q = xq + r * dp3, *c = xc + r * dp3;
+    float acc = 0.f;
+    for (int i = lane; i < d; i += 32) {
+        const float v = center ? x[i] - colsum[i] * inv_n : x[i];
+        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+        const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+        q[i] = hi;
+        q[d + i] = hi;
+        q[2 * d + i] = lo;
+        c[i] = hi;
+        c[d + i] = lo;
+        c[2 * d + i] = hi;
+        acc = fmaf(v, v, acc);
+    }
+    const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
+    for (int i = 3 * d + lane; i < dp3; i += 32) {
+        q[i] = z;
+        c[i] = z;
+    }
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+        norms[r] = center ? acc : 1.f;
+        atomicMax(maxn, __float_as_uint(acc));
+    }
+}
+
+// Rigorous bound on |s_screen - s| for a row of squared norm na against any
+// point of squared norm <= nb (norms of the centred rows for L2, of the rows
+// for the chord); d the width, dp3 the contraction length.  Terms: the
+// dropped lo.lo and the hi/lo residuals (3 2^-16 |x||y|, twice for -2<x,y>),
+// the FP32 accumulation of dp3 exact products (dp3 2^-23 / (1 - dp3 2^-23)
+// of their magnitudes, allowing truncating adders), the FP32 row norms
+// (d 2^-23 relative), the final additions (2^-22 relative), and for L2 the
+// rounding of the centring (2^-24 |xh| per row moves sqrt(s) by at most
+// delta = 2^-24 (|x| + |y|)).
+__device__ __forceinline__ float screen_bound(float na, float nb, int d, int dp3, int center) {
+    const double a = sqrt((double)na) * 1.0001, b = sqrt((double)nb) * 1.0001;
+    const double u16 = 1.52587890625e-05, u23 = 1.1920928955078125e-07;
+    const double g = dp3 * u23 / (1.0 - dp3 * u23);
+    double e = 2.0 * (3.001 * u16 + 1.02 * g) * a * b;
+    if (center) {
+        const double dl = 5.9604644775390625e-08 * 1.001 * (a + b);
+        e += d * u23 * (a * a + b * b) + 2.3841857910156250e-07 * 1.01 * (a + b) * (a + b) +
+             2.0 * (a + b) * dl + dl * dl;
+    } else {
+        e += 2.3841857910156250e-07 * 1.01 * (2.0 + 2.0 * a * b);
+    }
+    return (float)(e * 1.01 + 1e-12);
+}
+
+// One warp per row r: the Ks screened candidates (sid / ssc [n][Ks], sorted
+// by screened distance) re-measured in FP32 (difference form / chord, the
+// arithmetic of the FP32 gathers, error rel * s or abs_err), sorted by
+// (s, id), near-tie runs that reach the first K re-ordered by FP64
+// distance.  The row is certified when the exact K-th distance (FP64 if
+// resolved, else FP32 plus its bound) is below the last screened distance
+// minus screen_bound: every point outside the shortlist is then strictly
+// farther.  Certified rows are written (FP64 distances rounded to FP32, as
+// the FP32 form writes them); others go to fail[] for the FP32 tiles.
+__global__ void __launch_bounds__(256) k_knn_certify(
+    const float *__restrict__ X, int64_t n, int d, int metric, const int32_t *__restrict__ sid,
+    const float *__restrict__ ssc, int Ks, int K, float rel, float abs_err,
+    const float *__restrict__ norms, const unsigned *__restrict__ maxn, int dp3, int center,
+    int32_t *__restrict__ out_i, float *__restrict__ out_s, int *fail, int *nfail,
+    unsigned long long *counters) {
     __shared__ float ks[8][128];
     __shared__ int kid[8][128];
+    __shared__ double k64[8];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, team = lane >> 3, li = lane & 7;
-    const int64_t row = (int64_t)blockIdx.x * 8 + w;
-    if (row >= nq) return;
+    const int64_t r = (int64_t)blockIdx.x * 8 + w;
+    if (r >= n) return;
+    const float *xr = X + r * d;
+    const float4 *q4 = reinterpret_cast<const float4 *>(xr);
     for (int j = lane; j < 128; j += 32) {
         ks[w][j] = INFINITY;
         kid[w][j] = INT_MAX;
     }
     __syncwarp();
-    const float4 *q4 = reinterpret_cast<const float4 *>(Q + row * d);
-    for (int b0 = 0; b0 < Kx; b0 += 4) {
+    int m = 0;
+    for (int b0 = 0; b0 < Ks; b0 += 32) {
+        const int j = b0 + lane;
+        m += __popc(__ballot_sync(0xffffffffu, j < Ks && sid[r * Ks + j] >= 0));
+    }
+    for (int b0 = 0; b0 < Ks; b0 += 4) {
         const int j = b0 + team;
-        const int id = j < Kx ? ci[row * Kx + j] : -1;
+        const int id = j < Ks ? sid[r * Ks + j] : -1;
         const float sv = team8_dist(q4, reinterpret_cast<const float4 *>(X + (int64_t)(id >= 0 ? id : 0) * d),
                                     d / 4, li, metric);
         if (li == 0 && id >= 0) {
@@ -362,22 +464,186 @@ __global__ void k_knn_rerank(const float *__restrict__ Q, const float *__restric
     }
     __syncwarp();
     warp_bitonic_sort(ks[w], kid[w], 128);
-    for (int t = lane; t < K; t += 32) {
-        const bool ok = kid[w][t] != INT_MAX;
-        out_i[row * K + t] = ok ? kid[w][t] : -1;
-        out_s[row * K + t] = ok ? ks[w][t] : INFINITY;
+    float na = center ? norms[r] : 0.f;
+    if (!center) {
+        for (int c = lane; c < d; c += 32) na = fmaf(xr[c], xr[c], na);
+        for (int o = 16; o; o >>= 1) na += __shfl_xor_sync(0xffffffffu, na, o);
     }
+    int ok = 1;
+    if (lane == 0) {
+        auto err = [&](int j) -> float { return metric == 0 ? rel * ks[w][j] : abs_err; };
+        unsigned long long rechecked = 0;
+        double kth = -1.0;  // exact K-th distance when resolved in FP64
+        int j = 0;
+        while (ok && j < m && j < K) {
+            int e = j;
+            while (e + 1 < m && ks[w][e + 1] - ks[w][e] <= err(e) + err(e + 1)) ++e;
+            if (e > j) {
+                if ((e == m - 1 && m == Ks) || e - j + 1 > 64) {
+                    ok = 0;  // the run may continue outside the shortlist
+                    break;
+                }
+                double td[64];
+                int ti[64];
+                const int cnt = e - j + 1;
+                for (int t = 0; t < cnt; ++t) {
+                    ti[t] = kid[w][j + t];
+                    td[t] = dist64_rows(xr, X + (int64_t)ti[t] * d, d, metric);
+                }
+                for (int a = 1; a < cnt; ++a) {
+                    const double kd = td[a];
+                    const int ki = ti[a];
+                    int b = a - 1;
+                    while (b >= 0 && (td[b] > kd || (td[b] == kd && ti[b] > ki))) {
+                        td[b + 1] = td[b];
+                        ti[b + 1] = ti[b];
+                        --b;
+                    }
+                    td[b + 1] = kd;
+                    ti[b + 1] = ki;
+                }
+                for (int t = 0; t < cnt; ++t) kid[w][j + t] = ti[t];
+                if (j <= K - 1 && e >= K - 1) kth = td[K - 1 - j];
+                rechecked += cnt;
+            }
+            j = e + 1;
+        }
+        if (ok) {
+            if (m < Ks) {
+                ok = m == n - 1;  // the shortlist holds every other point
+            } else {
+                const double up = kth >= 0.0 ? kth : (double)ks[w][K - 1] + (double)err(K - 1);
+                const float nb = __uint_as_float(*maxn);
+                const double lower =
+                    (double)ssc[r * Ks + Ks - 1] - (double)screen_bound(na, nb, d, dp3, center);
+                ok = up < lower;
+            }
+        }
+        if (rechecked) atomicAdd(counters + CNT_KNN_RECHECK, rechecked);
+        if (!ok) {
+            fail[atomicAdd(nfail, 1)] = (int)r;
+            atomicAdd(counters + CNT_KNN_FALLBACK, 1ull);
+        }
+        k64[w] = ok ? 1.0 : 0.0;
+    }
+    __syncwarp();
+    if (k64[w] == 0.0) return;
+    for (int t = lane; t < K; t += 32) {
+        const int id = t < m ? kid[w][t] : -1;
+        out_i[r * K + t] = id;
+        out_s[r * K + t] = id >= 0 ? (float)dist64_rows(xr, X + (int64_t)id * d, d, metric) : INFINITY;
+    }
+}
+
+// Rows the screen could not certify: their K + 1 nearest by the FP32 tiles
+// (the row itself among them unless K + 1 duplicates of it come first),
+// written without the row itself.
+__global__ void k_knn_fallback_scatter(const int *__restrict__ fail, int nf,
+                                       const int32_t *__restrict__ gi, const float *__restrict__ gs,
+                                       int K, int32_t *__restrict__ out_i, float *__restrict__ out_s) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nf) return;
+    const int64_t u = fail[t];
+    int w = 0;
+    for (int j = 0; j <= K && w < K; ++j) {
+        const int id = gi[(int64_t)t * (K + 1) + j];
+        if (id == (int)u) continue;
+        out_i[u * K + w] = id;
+        out_s[u * K + w] = gs[(int64_t)t * (K + 1) + j];
+        ++w;
+    }
+    for (; w < K; ++w) {
+        out_i[u * K + w] = -1;
+        out_s[u * K + w] = INFINITY;
+    }
+}
+
+__global__ void k_gather_fail_rows(const float *__restrict__ X, int d, const int *__restrict__ fail,
+                                   int nf, float *__restrict__ out) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nch = d / 4;
+    if (t >= (int64_t)nf * nch) return;
+    const int64_t r = t / nch, c = t % nch;
+    reinterpret_cast<float4 *>(out)[r * nch + c] =
+        reinterpret_cast<const float4 *>(X + (int64_t)fail[r] * d)[c];
 }
 
 }  // namespace
 
 bool pg_knn_tc_supported(int d, int K);
 int pg_knn_tc_max_k();
+pg_status pg_knn_tc_split(pg_ctx *ctx, Scratch<__nv_bfloat16> &xc, Scratch<__nv_bfloat16> &xq,
+                          int64_t n, int dp3, const float *norms, int32_t K, int32_t *ids,
+                          float *dist, double work);
 pg_status pg_knn_tc(pg_ctx *ctx, const float *D, int64_t n, int32_t d, const float *Q, int64_t nq,
                     int self, int32_t K, const float *xnorm, const float *qnorm, int32_t *ids,
                     float *dist);
 
 namespace {
+
+pg_status knn_core(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
+                   const float *Q, int64_t nq, int self, int32_t K, pg_precision precision,
+                   int32_t *ids, float *dist);
+
+pg_status knn_screened(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
+                       int32_t K, int Ks, int dp3, const DataFacts &facts, int32_t *ids,
+                       float *dist) {
+    const int center = metric == PG_METRIC_L2SQ;
+    Scratch<float> csum, nrm, ss;
+    Scratch<unsigned> mx;
+    Scratch<__nv_bfloat16> xq, xc;
+    Scratch<int32_t> si;
+    Scratch<int> fail;
+    PG_TRY(csum.alloc(ctx, (size_t)d));
+    PG_TRY_CUDA(ctx, cudaMemsetAsync(csum.p, 0, (size_t)d * 4, ctx->stream));
+    if (center) {
+        const int64_t rpb = std::max<int64_t>(64, (n + ctx->num_sms * 4 - 1) / (ctx->num_sms * 4));
+        const dim3 g((unsigned)((n + rpb - 1) / rpb), (unsigned)((d + 255) / 256));
+        k_col_sums<<<g, 256, 0, ctx->stream>>>(D, n, d, rpb, csum.p);
+        PG_LAUNCHED(ctx);
+    }
+    PG_TRY(xq.alloc(ctx, (size_t)(n * dp3)));
+    PG_TRY(xc.alloc(ctx, (size_t)(n * dp3)));
+    PG_TRY(nrm.alloc(ctx, (size_t)n));
+    PG_TRY(mx.alloc(ctx, 1));
+    PG_TRY_CUDA(ctx, cudaMemsetAsync(mx.p, 0, sizeof(unsigned), ctx->stream));
+    k_split_rows<<<(unsigned)((n * 32 + 255) / 256), 256, 0, ctx->stream>>>(
+        D, n, d, dp3, csum.p, (float)(1.0 / (double)n), center, xq.p, xc.p, nrm.p, mx.p);
+    PG_LAUNCHED(ctx);
+    PG_TRY(si.alloc(ctx, (size_t)(n * Ks)));
+    PG_TRY(ss.alloc(ctx, (size_t)(n * Ks)));
+    // the contraction the tensor cores run: 3d (padded) columns per pair
+    PG_TRY(pg_knn_tc_split(ctx, xc, xq, n, dp3, nrm.p, Ks, si.p, ss.p,
+                           2.0 * (double)n * (double)n * (double)dp3));
+    PG_TRY(fail.alloc(ctx, (size_t)n + 1));
+    PG_TRY_CUDA(ctx, cudaMemsetAsync(fail.p + n, 0, sizeof(int), ctx->stream));
+    const ErrModel em = pg_err_model(metric, d, facts, false);
+    k_knn_certify<<<(unsigned)((n + 7) / 8), 256, 0, ctx->stream>>>(
+        D, n, d, metric == PG_METRIC_L2SQ ? 0 : 1, si.p, ss.p, Ks, K, em.rel, em.abs_, nrm.p,
+        mx.p, dp3, center, ids, dist, fail.p, fail.p + n, ctx->d_counters);
+    PG_LAUNCHED(ctx);
+    int nf = 0;
+    PG_TRY_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned, fail.p + n, sizeof(int),
+                                     cudaMemcpyDeviceToHost, ctx->stream));
+    PG_TRY(pg_sync_check(ctx, "screened knn"));
+    memcpy(&nf, ctx->h_pinned, sizeof(int));
+    if (nf > 0) {
+        Scratch<float> Qf, gs;
+        Scratch<int32_t> gi;
+        PG_TRY(Qf.alloc(ctx, (size_t)nf * d));
+        PG_TRY(gi.alloc(ctx, (size_t)nf * (K + 1)));
+        PG_TRY(gs.alloc(ctx, (size_t)nf * (K + 1)));
+        const int64_t tot = (int64_t)nf * (d / 4);
+        k_gather_fail_rows<<<(unsigned)((tot + 255) / 256), 256, 0, ctx->stream>>>(D, d, fail.p,
+                                                                                 nf, Qf.p);
+        PG_LAUNCHED(ctx);
+        PG_TRY(knn_core(ctx, D, n, d, metric, Qf.p, nf, 0, K + 1, PG_PREC_FP32, gi.p, gs.p));
+        k_knn_fallback_scatter<<<(unsigned)((nf + 255) / 256), 256, 0, ctx->stream>>>(
+            fail.p, nf, gi.p, gs.p, K, ids, dist);
+        PG_LAUNCHED(ctx);
+    }
+    return PG_OK;
+}
 
 pg_status knn_core(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
                    const float *Q, int64_t nq, int self, int32_t K, pg_precision precision,
@@ -414,24 +680,14 @@ pg_status knn_core(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric 
     if (precision == PG_PREC_BF16_SCREEN && metric == PG_METRIC_L2SQ && facts.exact &&
         facts.bf16_exact && pg_knn_tc_supported(d, K))
         return pg_knn_tc(ctx, D, n, d, self ? nullptr : Q, nq, self, K, xn.p, qnp, ids, dist);
-    // Other data in the screened form: the Ks = min(128, max(2K, K + 8))
-    // nearest by BF16 tiles (the BF16 rounding moves distances by up to
-    // ~2^-8 (|x| + |y|) sqrt(s)), re-measured in FP32 and cut to K.
-    // Membership at the K-th place can differ from the exact kNN; the
-    // candidate order and distances are FP32.
+    // Other data in the screened form (self kNN): the certified hi/lo
+    // screen for the Ks = min(128, max(2K, K + 8)) nearest, then FP32 tiles
+    // for the rows it cannot certify.  The result equals the FP32 form's.
     const int Ks = std::min(pg_knn_tc_max_k(), std::max(2 * K, K + 8));
-    if (precision == PG_PREC_BF16_SCREEN && !(facts.exact && facts.bf16_exact) && Ks >= K + 8 &&
-        pg_knn_tc_supported(d, Ks)) {
-        Scratch<int32_t> wi;
-        Scratch<float> ws;
-        PG_TRY(wi.alloc(ctx, (size_t)nq * Ks));
-        PG_TRY(ws.alloc(ctx, (size_t)nq * Ks));
-        PG_TRY(pg_knn_tc(ctx, D, n, d, self ? nullptr : Q, nq, self, Ks, xn.p, qnp, wi.p, ws.p));
-        k_knn_rerank<<<(unsigned)((nq + 7) / 8), 256, 0, ctx->stream>>>(
-            Qp, D, nq, d, metric == PG_METRIC_L2SQ ? 0 : 1, Ks, K, wi.p, ids, dist);
-        PG_LAUNCHED(ctx);
-        return PG_OK;
-    }
+    const int dp3 = (3 * d + 63) / 64 * 64;
+    if (self && precision == PG_PREC_BF16_SCREEN && !(facts.exact && facts.bf16_exact) &&
+        Ks >= K + 8 && n > Ks && pg_knn_tc_supported(dp3, Ks))
+        return knn_screened(ctx, D, n, d, metric, K, Ks, dp3, facts, ids, dist);
     // rows hold Kx entries when ties must be resolved in FP64 afterwards
     int Kx = facts.exact ? K : (int)std::min<int64_t>((int64_t)K + 8, KMAX);
     Scratch<int32_t> wi;

@@ -949,31 +949,20 @@ __global__ void k_bucket_scatter(const int32_t *__restrict__ bucket, int64_t n,
 
 }  // namespace
 
-// Exact kNN of Q (or of D itself when self) on the tensor cores; the caller
-// guarantees BF16-exact integer data.  xnorm/qnorm are FP32 squared norms.
-// For the graph (self) the points are first ordered by their nearest of
-// ~n/1024 pivots (a kNN with K = 1 on the same kernel), so that every CTA
-// meets its rows' neighbours in its first tiles; lists hold original ids and
-// rows are written back in original order, so the result does not depend
-// on the order.
-pg_status pg_knn_tc(pg_ctx *ctx, const float *D, int64_t n, int32_t d, const float *Q, int64_t nq,
-                    int self, int32_t K, const float *xnorm, const float *qnorm, int32_t *ids,
-                    float *dist) {
-    const int dp = (d + 63) / 64 * 64;
-    Scratch<__nv_bfloat16> xb, qb, pb, xs;
+// The tile launch on prepared BF16 copies [rows][dp]: xc the candidate
+// rows; for self mode the query rows are xc itself or, when xq_sep is
+// given, the same points in another layout (the hi/lo split of the
+// screened form); otherwise qext holds nq external query rows.  The copies
+// are released once the spatially ordered ones are made.
+static pg_status tc_knn_run(pg_ctx *ctx, Scratch<__nv_bfloat16> &xc,
+                            Scratch<__nv_bfloat16> *xq_sep, const __nv_bfloat16 *qext, int64_t n,
+                            int64_t nq, int dp, int self, int32_t K, const float *xnorm,
+                            const float *qnorm, int32_t *ids, float *dist, double work) {
+    Scratch<__nv_bfloat16> pb, xs, xqs;
     Scratch<int32_t> pid, asg, perm, cnt;
     Scratch<float> adist, pn, xsn;
     Scratch<int64_t> boff;
-    PG_TRY(xb.alloc(ctx, (size_t)(n * dp)));
-    k_to_bf16<<<(unsigned)((n * dp + 255) / 256), 256, 0, ctx->stream>>>(D, n, d, dp, xb.p);
-    PG_LAUNCHED(ctx);
-    const __nv_bfloat16 *qp = xb.p;
-    if (!self) {
-        PG_TRY(qb.alloc(ctx, (size_t)(nq * dp)));
-        k_to_bf16<<<(unsigned)((nq * dp + 255) / 256), 256, 0, ctx->stream>>>(Q, nq, d, dp, qb.p);
-        PG_LAUNCHED(ctx);
-        qp = qb.p;
-    }
+    const __nv_bfloat16 *qp = self ? (xq_sep ? xq_sep->p : xc.p) : qext;
     const TcVariant V = tc_variant(dp, K);
     const size_t smem = tc_layout(dp, V.H, V.KB).total + 1024;
     PG_TRY_CUDA(ctx, cudaFuncSetAttribute(V.KB ? k_knn_tc<1, true>
@@ -1003,7 +992,7 @@ pg_status pg_knn_tc(pg_ctx *ctx, const float *D, int64_t n, int32_t d, const flo
         return PG_OK;
     };
     const int32_t *permp = nullptr;
-    const __nv_bfloat16 *xp = xb.p;
+    const __nv_bfloat16 *xp = xc.p;
     const float *xnp = xnorm, *qnp = qnorm;
     if (self && n >= 16384) {
         // ---- spatial order: nearest pivot, then a counting sort by pivot
@@ -1016,12 +1005,12 @@ pg_status pg_knn_tc(pg_ctx *ctx, const float *D, int64_t n, int32_t d, const flo
         k_pivot_ids<<<(P + 255) / 256, 256, 0, ctx->stream>>>(pid.p, P, n);
         PG_LAUNCHED(ctx);
         k_gather_bf16<<<(unsigned)(((int64_t)P * dp / 8 + 255) / 256), 256, 0, ctx->stream>>>(
-            xb.p, pid.p, P, dp, pb.p);
+            xc.p, pid.p, P, dp, pb.p);
         PG_LAUNCHED(ctx);
         k_gather_f32<<<(P + 255) / 256, 256, 0, ctx->stream>>>(xnorm, pid.p, P, pn.p);
         PG_LAUNCHED(ctx);
         CUtensorMap mqa, mpa;
-        PG_TRY(make_map(ctx, &mqa, xb.p, n, dp));
+        PG_TRY(make_map(ctx, &mqa, qp, n, dp));
         PG_TRY(make_map(ctx, &mpa, pb.p, P, dp));
         PG_TRY(launch((unsigned)((n + TM - 1) / TM), mqa, mpa, n, P, xnorm, pn.p, 1, 0, asg.p,
                       adist.p, nullptr, 0));
@@ -1040,14 +1029,22 @@ pg_status pg_knn_tc(pg_ctx *ctx, const float *D, int64_t n, int32_t d, const flo
         PG_TRY(xs.alloc(ctx, (size_t)(n * dp)));
         PG_TRY(xsn.alloc(ctx, (size_t)n));
         k_gather_bf16<<<(unsigned)((n * dp / 8 + 255) / 256), 256, 0, ctx->stream>>>(
-            xb.p, perm.p, n, dp, xs.p);
+            xc.p, perm.p, n, dp, xs.p);
         PG_LAUNCHED(ctx);
         k_gather_f32<<<gn, 256, 0, ctx->stream>>>(xnorm, perm.p, n, xsn.p);
         PG_LAUNCHED(ctx);
-        xb.release();
+        xc.release();
         permp = perm.p;
         xp = xs.p;
         qp = xs.p;
+        if (xq_sep) {
+            PG_TRY(xqs.alloc(ctx, (size_t)(n * dp)));
+            k_gather_bf16<<<(unsigned)((n * dp / 8 + 255) / 256), 256, 0, ctx->stream>>>(
+                xq_sep->p, perm.p, n, dp, xqs.p);
+            PG_LAUNCHED(ctx);
+            xq_sep->release();
+            qp = xqs.p;
+        }
         xnp = xsn.p;
         qnp = xsn.p;
     }
@@ -1058,8 +1055,42 @@ pg_status pg_knn_tc(pg_ctx *ctx, const float *D, int64_t n, int32_t d, const flo
     pg_timer_begin(ctx, TM_KNN);
     PG_TRY(launch(grid, mq, mx, nq, n, qnp, xnp, K, self, ids, dist, permp, permp ? 1 : 0));
     PG_LAUNCHED(ctx);
-    pg_timer_end(ctx, TM_KNN, 2.0 * (double)nq * (double)n * (double)d);
+    pg_timer_end(ctx, TM_KNN, work);
     return PG_OK;
+}
+
+// Exact kNN of Q (or of D itself when self) on the tensor cores; the caller
+// guarantees BF16-exact integer data.  xnorm/qnorm are FP32 squared norms.
+// For the graph (self) the points are first ordered by their nearest of
+// ~n/1024 pivots (a kNN with K = 1 on the same kernel), so that every CTA
+// meets its rows' neighbours in its first tiles; lists hold original ids and
+// rows are written back in original order, so the result does not depend
+// on the order.
+pg_status pg_knn_tc(pg_ctx *ctx, const float *D, int64_t n, int32_t d, const float *Q, int64_t nq,
+                    int self, int32_t K, const float *xnorm, const float *qnorm, int32_t *ids,
+                    float *dist) {
+    const int dp = (d + 63) / 64 * 64;
+    Scratch<__nv_bfloat16> xb, qb;
+    PG_TRY(xb.alloc(ctx, (size_t)(n * dp)));
+    k_to_bf16<<<(unsigned)((n * dp + 255) / 256), 256, 0, ctx->stream>>>(D, n, d, dp, xb.p);
+    PG_LAUNCHED(ctx);
+    if (!self) {
+        PG_TRY(qb.alloc(ctx, (size_t)(nq * dp)));
+        k_to_bf16<<<(unsigned)((nq * dp + 255) / 256), 256, 0, ctx->stream>>>(Q, nq, d, dp, qb.p);
+        PG_LAUNCHED(ctx);
+    }
+    return tc_knn_run(ctx, xb, nullptr, qb.p, n, nq, dp, self, K, xnorm, qnorm, ids, dist,
+                      2.0 * (double)nq * (double)n * (double)d);
+}
+
+// Self kNN on the hi/lo split copies of the screened form: xq rows
+// [hi | hi | lo] and xc rows [hi | lo | hi] (dp3 columns), so that one
+// contraction gives hi.hi + hi.lo + lo.hi; norms are the rows' FP32 squared
+// norms (1 for the chord).  work: the algorithmic flops to report.
+pg_status pg_knn_tc_split(pg_ctx *ctx, Scratch<__nv_bfloat16> &xc, Scratch<__nv_bfloat16> &xq,
+                          int64_t n, int dp3, const float *norms, int32_t K, int32_t *ids,
+                          float *dist, double work) {
+    return tc_knn_run(ctx, xc, &xq, nullptr, n, n, dp3, 1, K, norms, norms, ids, dist, work);
 }
 
 // ------------------------------------------------ split-column argmin (host)

@@ -137,7 +137,8 @@ enum { PG_CNT_SLOTS = 32 };
 enum {
     CNT_ROWS = 0, CNT_CANDS, CNT_SCANNED, CNT_OCCL, CNT_RECHECK, CNT_FLIP, CNT_EDGES, CNT_LONG,
     CNT_LONG_LIST = 16, CNT_KNN_RECHECK = 17, CNT_KNN_UNRESOLVED = 18, CNT_SEARCH_EXP = 19,
-    CNT_SEARCH_EVAL = 20, CNT_SEARCH_BYTES = 21, CNT_PRUNE_BYTES = 22, CNT_NEAR_TIE = 23
+    CNT_SEARCH_EVAL = 20, CNT_SEARCH_BYTES = 21, CNT_PRUNE_BYTES = 22, CNT_NEAR_TIE = 23,
+    CNT_KNN_FALLBACK = 24
 };
 
 // device error codes (first one recorded wins)

@@ -57,6 +57,12 @@ DATA = {
 }
 
 
+def _close(got, want):
+    """FP32 distances against FP64 values: within 1e-5 relative (1e-6
+    absolute near 0, where the chord 2 - 2<x,y> cancels)."""
+    return bool((np.abs(got - want) <= 1e-5 * np.maximum(np.abs(want), 0.1)).all())
+
+
 # ----------------------------------------------------------------- kNN
 @pytest.mark.parametrize("kind", ["int", "float", "cosine"])
 def test_knn_matches_oracle(ctx, pg, kind):
@@ -97,27 +103,58 @@ def test_knn_bf16_k_blocked_tiles_match_oracle(ctx, pg, d, K):
     assert (host(gd) == od.astype(np.float32)).all()
 
 
-@pytest.mark.parametrize("n,d,metric", [(3000, 960, "l2"), (20000, 128, "l2"),
-                                        (3000, 96, "cosine")])
-def test_knn_bf16_screen_on_real_data_recall(ctx, pg, n, d, metric):
-    """Non-integer rows: the 2K BF16-nearest re-measured in FP32.  Lists
-    are sorted, distances are FP32 values of the returned pairs, and the
-    lists hold the exact K nearest up to rare swaps at the K-th place."""
+@pytest.mark.parametrize("n,d,metric,K", [(3000, 960, "l2", 32), (20000, 128, "l2", 64),
+                                          (3000, 96, "cosine", 32), (5000, 64, "l2", 10),
+                                          (2500, 384, "ip", 16)])
+def test_knn_bf16_screen_on_real_data_equals_the_oracle(ctx, pg, n, d, metric, K):
+    """Non-integer rows, screened form: the hi/lo BF16 tiles shortlist each
+    row, the shortlist is re-measured in FP32 with FP64 near-tie fixes and
+    certified by a rigorous bound (or the row is redone by the FP32 tiles),
+    so the lists equal the exact kNN of the FP64 oracle and the FP32
+    form's lists and distances bit for bit."""
     if metric == "l2":
         D, _ = synthetic.mixture_float(n, d, max(4, n // 1000), 17)
     else:
         D = synthetic.unit_gaussian(n, d, 17)
-    K = 32
+    ctx.set_timing(True)  # resets the device counters
     gi, gd = pg.build_knn(ctx, dev(D), K, metric, precision="bf16")
-    gi, gd = host(gi), host(gd)
+    fallback = ctx.counter("knn_fallback_rows")
+    ctx.set_timing(False)
+    fi, fd = pg.build_knn(ctx, dev(D), K, metric, precision="fp32")
+    assert torch.equal(gi, fi) and torch.equal(gd, fd)
     oi, od = oracle.knn(D, K, metric)
-    rows = np.arange(n)
-    for u in rows[:200]:
-        ref = np.array([oracle.dist(D[u], D[v], metric) for v in gi[u]])
-        assert np.allclose(gd[u], ref, rtol=2e-5, atol=1e-6)
-        assert (np.diff(gd[u]) >= 0).all()
-    hits = np.mean([len(set(gi[u]) & set(oi[u])) / K for u in rows])
-    assert hits >= 0.995
+    assert (host(gi) == oi).all()
+    assert _close(host(gd), od.astype(np.float64))
+    assert fallback < n  # the certificate accepts rows (the screen is used)
+
+
+def test_knn_bf16_screen_certificate_forces_the_fallback(ctx, pg):
+    """Stars of 2d arms at +-0.5 along every axis around centres 50 apart
+    (halves: not integers, so the screened path runs; every distance is
+    exact all the same): a centre has 64 equidistant arms and an arm 62
+    equidistant siblings, more than the 40-entry shortlist holds, so no row
+    can be certified at the K-th place.  Every row takes the FP32 tiles and
+    the lists equal the oracle's."""
+    d, stars = 32, 40
+    rows = []
+    for k in range(stars):
+        c = np.zeros(d, np.float32)
+        c[0] = 50.0 * k
+        rows.append(c)
+        for i in range(d):
+            for sgn in (0.5, -0.5):
+                x = c.copy()
+                x[i] += sgn
+                rows.append(x)
+    D = np.stack(rows).astype(np.float32)
+    ctx.set_timing(True)
+    gi, gd = pg.build_knn(ctx, dev(D), 20, precision="bf16")
+    fallback = ctx.counter("knn_fallback_rows")
+    ctx.set_timing(False)
+    oi, od = oracle.knn(D, 20)
+    assert (host(gi) == oi).all()
+    assert (host(gd) == od.astype(np.float32)).all()
+    assert fallback == D.shape[0]
 
 
 def test_knn_queries_and_padding(ctx, pg):
@@ -331,12 +368,6 @@ def test_acquire_real_rows_equal_the_oracle(ctx, pg, kind, L):
     cand = host(pg.acquire_candidates(ctx, dev(D), dev(nbr), dev(deg), L, metric))
     ocand = oracle.acquire(D, nbr, deg, L, metric)
     assert (cand == ocand).all()
-
-
-def _close(got, want):
-    """FP32 distances against FP64 values: within 1e-5 relative (1e-6
-    absolute near 0, where the chord 2 - 2<x,y> cancels)."""
-    return bool((np.abs(got - want) <= 1e-5 * np.maximum(np.abs(want), 0.1)).all())
 
 
 @pytest.mark.parametrize("kind", ["float", "cosine"])
