@@ -727,10 +727,9 @@ def run_sweep(args):
         uo, ui = pg.reverse_union(ctx, n1, d1)
         n2, d2 = pg.prune(ctx, Dd, uo, ui, R, alpha, precision=prec)
         deg_pruned = float(d2.float().mean())
-        try:
-            added = pg.connect(ctx, Dd, n2, d2, ep)
-        except pg.PGError as e:  # every reached node full: no free slot to link from
-            added = f"refused ({e.status})"
+        # connectivity with edge replacement: at large alpha every reached
+        # node is full and the plain step has no free slot to link from
+        added, replaced = pg.connect_replace(ctx, Dd, n2, d2, ep)
         pg.acquire_candidates(ctx, Dd, n2, d2, L, precision=prec)  # warm-up
         e0, e1 = events()
         e0.record(stream)
@@ -742,6 +741,7 @@ def run_sweep(args):
         _, rK = pg.kcna_recall(ctx, Dd, cand, K, sample)
         alphas.append({"alpha": alpha, "kcna_points_per_s": n / secs,
                        "mean_out_degree": deg_pruned, "connect_edges": added,
+                       "connect_replaced_edges": replaced,
                        "kcna_recall_at_10": r10, f"kcna_recall_at_{K}": rK})
     iters = []
     for it in range(5):

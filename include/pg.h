@@ -127,12 +127,15 @@ typedef struct {
     double quality_eps;      /* epsilon of Theorem 3 (sample size n_s), default 0.6   */
     int32_t quality_k;       /* k of the recall r(u) (first k entries of C(u));
                                 0 = K                                                */
+    int32_t connect_replace; /* connectivity steps use edge replacement when every
+                                reached node is full (pg_connect_replace); 0: such a
+                                build fails with PG_ERR_CAPACITY                    */
 } pg_build_params;
 
 /* Defaults: L2SQ, FP32, K=64, L=200, R=32, M=16, alpha 66/60, I=2,
  * connect_final=1, route_layers=1, seed=0, reuse_pruning=1,
- * quality_target=0 (fixed I), quality_eps=0.6, quality_k=0 (K).  params must
- * not be NULL. */
+ * quality_target=0 (fixed I), quality_eps=0.6, quality_k=0 (K),
+ * connect_replace=1.  params must not be NULL. */
 void pg_default_params(pg_build_params *params);
 
 /* ---------------------------------------------------------------- context */
@@ -306,6 +309,21 @@ pg_status pg_medoid(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric
  * PG_ERR_CAPACITY if no reached node has a free slot.  Synchronous. */
 pg_status pg_connect(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
                      int32_t *nbr, int32_t *deg, int32_t R, int64_t ep, int64_t *host_added);
+
+/* The connectivity step with edge replacement (a reading for graphs whose
+ * reached nodes are all full; the paper only says that extra edges join the
+ * components).  As pg_connect while some reached node has a free slot;
+ * when none has one for the smallest unreached id r, the reached node p
+ * nearest to r by (s, id) that still holds an edge not added by this call
+ * gives up the last such edge in its list (its farthest original
+ * neighbour) for r, and the reached set is recomputed from ep.  Equal to
+ * pg_connect whenever pg_connect succeeds.  *host_added / *host_replaced
+ * (host, may be NULL): edges added (replacements included) and
+ * replacements.  PG_ERR_CAPACITY when no reached node has a free slot or
+ * an original edge. */
+pg_status pg_connect_replace(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
+                             int32_t *nbr, int32_t *deg, int32_t R, int64_t ep,
+                             int64_t *host_added, int64_t *host_replaced);
 
 /* k-CNA acquisition by search on the refined graph (the search step of
  * Algorithm 5): for every u, KANNSearch(G, u, L, L, u) of Algorithm 1; row

@@ -42,7 +42,7 @@ class BuildParams(C.Structure):
                 ("M", i32), ("alpha_deg", dbl), ("alpha_final_deg", dbl), ("iters", i32),
                 ("connect_final", i32), ("route_layers", i32), ("seed", u64),
                 ("reuse_pruning", i32), ("quality_target", dbl), ("quality_eps", dbl),
-                ("quality_k", i32)]
+                ("quality_k", i32), ("connect_replace", i32)]
 
 
 class PruneStats(C.Structure):
@@ -71,6 +71,7 @@ _sig("pg_kcna_recall", C.c_int, [P, P, i64, i32, C.c_int, P, i32, i32, P, i64, P
 _sig("pg_quality_sample_size", i64, [i64, dbl, dbl])
 _sig("pg_quality_sample", C.c_int, [i64, i64, u64, P])
 _sig("pg_index_quality", C.c_int, [P, P, P, P])
+_sig("pg_connect_replace", C.c_int, [P, P, i64, i32, C.c_int, P, P, i32, i64, P, P])
 _sig("pg_prune_k2p", C.c_int, [P, P, i64, i32, C.c_int, P, P, P, P, i32, i32, dbl, C.c_int, P, P,
                                P])
 _sig("pg_reverse_union", C.c_int, [P, P, P, i64, i32, P, P, i64, P])
@@ -121,7 +122,7 @@ EXPORTS = ["pg_default_params", "pg_ctx_create", "pg_ctx_destroy", "pg_last_erro
            "pg_ctx_launches", "pg_build_knn", "pg_knn_query", "pg_prune", "pg_reverse_union",
            "pg_medoid", "pg_connect", "pg_acquire_candidates", "pg_search_graph", "pg_build_rng",
            "pg_build_rng_host", "pg_measure_fp32_peak", "pg_prune_k2p",
-           "pg_kcna_recall", "pg_quality_sample_size", "pg_quality_sample", "pg_index_quality",
+           "pg_kcna_recall", "pg_connect_replace", "pg_quality_sample_size", "pg_quality_sample", "pg_index_quality",
            "pg_build_nswg", "pg_search", "pg_search_host", "pg_index_destroy", "pg_index_info",
            "pg_index_layer", "pg_index_phase_seconds", "pg_index_export_layer",
            "pg_ctx_set_timing", "pg_ctx_set_tie_count", "pg_ctx_kernel_time", "pg_ctx_counter",
@@ -426,6 +427,19 @@ def connect(ctx: Context, D, nbr, deg, ep: int, metric="l2") -> int:
     ctx._check(_lib.pg_connect(ctx.handle, _ptr(D), n, D.shape[1], METRIC[metric], _ptr(nbr),
                                _ptr(deg), R, ep, C.byref(added)), "pg_connect")
     return int(added.value)
+
+
+def connect_replace(ctx: Context, D, nbr, deg, ep: int, metric="l2"):
+    """pg_connect_replace, in place on nbr/deg: (edges added, replacements)."""
+    D = _dev(D, torch.float32, "D")
+    if not (nbr.is_contiguous() and deg.is_contiguous()):
+        raise ValueError("nbr/deg must be contiguous (updated in place)")
+    n, R = nbr.shape
+    added, rep = C.c_int64(), C.c_int64()
+    ctx._check(_lib.pg_connect_replace(ctx.handle, _ptr(D), n, D.shape[1], METRIC[metric],
+                                       _ptr(nbr), _ptr(deg), R, ep, C.byref(added),
+                                       C.byref(rep)), "pg_connect_replace")
+    return int(added.value), int(rep.value)
 
 
 def acquire_candidates(ctx: Context, D, nbr, deg, L: int, metric="l2", precision="fp32"):

@@ -34,6 +34,10 @@ pg_status pg_connect_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
                               int32_t *nbr, int32_t *deg, int32_t R, int64_t ep,
                               const DataFacts &facts, const int32_t *knn, int32_t K,
                               int64_t *host_added);
+pg_status pg_connect_replace_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
+                                      pg_metric metric, int32_t *nbr, int32_t *deg, int32_t R,
+                                      int64_t ep, const DataFacts &facts, const int32_t *knn,
+                                      int32_t K, int64_t *host_added, int64_t *host_replaced);
 pg_status pg_quality_estimate(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
                               const int32_t *cand, int32_t L, int32_t k, double eps, uint64_t seed,
                               double *est, int64_t *ns_out);
@@ -252,8 +256,12 @@ pg_status iter_nsg(pg_ctx *ctx, const float *X, int64_t m, int32_t d, const pg_b
         prev_alpha = alpha;
         if (do_connect) {
             clk.start(PH_CONNECT);
-            PG_TRY(pg_connect_internal(ctx, X, m, d, p->metric, nbr, deg, R, ep, facts, knn_i.p, K,
-                                       nullptr));
+            if (p->connect_replace)
+                PG_TRY(pg_connect_replace_internal(ctx, X, m, d, p->metric, nbr, deg, R, ep, facts,
+                                                   knn_i.p, K, nullptr, nullptr));
+            else
+                PG_TRY(pg_connect_internal(ctx, X, m, d, p->metric, nbr, deg, R, ep, facts,
+                                           knn_i.p, K, nullptr));
         }
         return PG_OK;
     };

@@ -43,6 +43,7 @@ extern "C" void pg_default_params(pg_build_params *p) {
     p->quality_target = 0.0;
     p->quality_eps = 0.6;
     p->quality_k = 0;
+    p->connect_replace = 1;
 }
 
 extern "C" pg_status pg_ctx_create(void *cuda_stream, size_t hbm_budget_bytes, pg_ctx **out) {
@@ -241,8 +242,10 @@ pg_status pg_sync_check(pg_ctx *ctx, const char *where) {
     PG_TRY_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     int err[4];
     memcpy(err, ctx->h_err, sizeof err);
+    ctx->last_derr = err[0];
     if (err[0] != DERR_NONE) {
         long long info = (long long)(unsigned)err[2] | ((long long)err[3] << 32);
+        ctx->last_err_info = info;
         PG_TRY_CUDA(ctx, cudaMemsetAsync(ctx->d_err, 0, 4 * sizeof(int), ctx->stream));
         PG_TRY_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
         switch (err[0]) {

@@ -1131,3 +1131,199 @@ extern "C" pg_status pg_connect(pg_ctx *ctx, const float *D, int64_t n, int32_t 
     return pg_connect_internal(ctx, D, n, d, metric, nbr, deg, R, ep, facts, nullptr, 0,
                                host_added);
 }
+
+// ---------------------------------------- connectivity with edge replacement
+// A reading for graphs whose reached nodes are all full (the paper's
+// connectivity step only says that extra edges link the components): when
+// no reached node has a free slot for the smallest unreached id r, the
+// reached node p nearest to r that still holds an edge not added by this
+// step gives up the last such edge in its list (its farthest original
+// neighbour) for r, and the reached set is recomputed from ep.  Until the
+// first such round the step equals the plain one, which therefore runs
+// batched as above; each refusal is followed by one replacement and a new
+// plain pass from the changed graph.  Every replacement removes an original
+// edge and every plain link grows the reached set, so the loop ends.
+namespace {
+
+struct RepState {
+    unsigned long long key32;  // exact data: FP32 bits << 32 | id; else min FP32 bits
+    unsigned long long key64;  // min FP64 bits among the candidates inside the bound
+    int id64;                  // smallest id at that FP64 minimum
+};
+
+// Argmin over reached nodes x with orig[x] > 0 (an original edge left) of
+// (s(x, r), x); one warp per node.  Exact data: one pass on packed keys.
+// Otherwise pass 0 takes the FP32 minimum, pass 1 the FP64 minimum among
+// nodes whose FP32 distance lies within the error bounds of it, pass 2 the
+// smallest id at that FP64 value.
+__global__ void k_rep_scan(const float *__restrict__ D, int64_t n, int d, int metric, int64_t r,
+                           const int *__restrict__ reached, const int32_t *__restrict__ orig,
+                           ErrModel em, int exact, int pass, RepState *st) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const float *xr = D + r * d;
+    const float smin = __uint_as_float((unsigned)(exact ? 0u : st->key32));
+    for (int64_t x = w0; x < n; x += nw) {
+        if (!reached[x] || orig[x] <= 0) continue;
+        const float *xx = D + x * d;
+        float acc = 0.f;
+        if (metric == 0) {
+            for (int c = lane; c < d; c += 32) {
+                const float t = xx[c] - xr[c];
+                acc = fmaf(t, t, acc);
+            }
+        } else {
+            for (int c = lane; c < d; c += 32) acc = fmaf(xx[c], xr[c], acc);
+        }
+        for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        const float s = metric == 0 ? acc : fmaxf(2.f - 2.f * acc, 0.f);
+        if (lane != 0) continue;
+        if (exact) {
+            atomicMin(&st->key32, ((unsigned long long)__float_as_uint(s) << 32) | (unsigned)x);
+        } else if (pass == 0) {
+            atomicMin(&st->key32, (unsigned long long)__float_as_uint(s));
+        } else if (s - em.err(s) <= smin + em.err(smin)) {
+            const double s64 = dist64_rows(xx, xr, d, metric);
+            const unsigned long long b = (unsigned long long)__double_as_longlong(s64);
+            if (pass == 1) atomicMin(&st->key64, b);
+            else if (b == st->key64) atomicMin(&st->id64, (int)x);
+        }
+    }
+}
+
+// node p gives up its last original edge for r
+__global__ void k_rep_replace(int32_t *nbr, int R, int32_t *orig, int p, int r) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        const int slot = orig[p] - 1;
+        nbr[(int64_t)p * R + slot] = r;
+        orig[p] = slot;
+    }
+}
+
+__global__ void k_rep_mark(int *reached, int64_t ep, int *queue) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        reached[ep] = 1;
+        queue[0] = (int)ep;
+    }
+}
+
+__global__ void k_deg_sum(const int32_t *deg, const int32_t *deg0, int64_t n,
+                          unsigned long long *out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    long long v = i < n ? (long long)deg[i] - (long long)deg0[i] : 0;
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(out, (unsigned long long)v);
+}
+
+}  // namespace
+
+// The connectivity step with edge replacement (see above).  *host_added
+// (may be NULL) = edges added, replacements included; *host_replaced (may be
+// NULL) = replacements.  PG_ERR_CAPACITY when a refused round finds no
+// reached node with an original edge either.
+pg_status pg_connect_replace_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
+                                      pg_metric metric, int32_t *nbr, int32_t *deg, int32_t R,
+                                      int64_t ep, const DataFacts &facts, const int32_t *knn,
+                                      int32_t K, int64_t *host_added, int64_t *host_replaced) {
+    Scratch<int32_t> deg0, orig;
+    Scratch<int> reached, queue, fcnt;
+    Scratch<RepState> st;
+    Scratch<unsigned long long> sum;
+    PG_TRY(deg0.alloc(ctx, (size_t)n));
+    PG_TRY(orig.alloc(ctx, (size_t)n));
+    PG_TRY_CUDA(ctx, cudaMemcpyAsync(deg0.p, deg, (size_t)n * 4, cudaMemcpyDeviceToDevice,
+                                     ctx->stream));
+    PG_TRY_CUDA(ctx, cudaMemcpyAsync(orig.p, deg, (size_t)n * 4, cudaMemcpyDeviceToDevice,
+                                     ctx->stream));
+    const ErrModel em = pg_err_model(metric, d, facts, false);
+    const int m = metric == PG_METRIC_L2SQ ? 0 : 1;
+    const int exact = facts.exact ? 1 : 0;
+    int64_t replaced = 0;
+    for (int64_t round = 0;; ++round) {
+        if (round > n + 1)
+            return pg_fail(ctx, PG_ERR_INTERNAL, "connect: no progress after %lld replacements",
+                           (long long)round);
+        pg_status s = pg_connect_internal(ctx, D, n, d, metric, nbr, deg, R, ep, facts, knn, K,
+                                          nullptr);
+        if (s == PG_OK) break;
+        if (ctx->last_derr != DERR_NO_SLOT) return s;
+        const int64_t r = ctx->last_err_info;
+        if (r < 0 || r >= n) return pg_fail(ctx, PG_ERR_INTERNAL, "connect: refused node %lld",
+                                            (long long)r);
+        // the reached set from ep on the graph as the plain pass left it
+        if (!reached.p) {
+            PG_TRY(reached.alloc(ctx, (size_t)n));
+            PG_TRY(queue.alloc(ctx, (size_t)n * 2));
+            PG_TRY(fcnt.alloc(ctx, 1));
+            PG_TRY(st.alloc(ctx, 1));
+        }
+        PG_TRY_CUDA(ctx, cudaMemsetAsync(reached.p, 0, (size_t)n * 4, ctx->stream));
+        k_rep_mark<<<1, 32, 0, ctx->stream>>>(reached.p, ep, queue.p);
+        PG_LAUNCHED(ctx);
+        int *fa = queue.p, *fb = queue.p + n;
+        int fcount = 1;
+        while (fcount > 0) {
+            PG_TRY_CUDA(ctx, cudaMemsetAsync(fcnt.p, 0, sizeof(int), ctx->stream));
+            k_bfs_level<<<(fcount + 255) / 256, 256, 0, ctx->stream>>>(nbr, deg, R, n, reached.p,
+                                                                       fa, fcount, fb, fcnt.p);
+            PG_LAUNCHED(ctx);
+            PG_TRY_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned, fcnt.p, sizeof(int),
+                                             cudaMemcpyDeviceToHost, ctx->stream));
+            PG_TRY_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+            memcpy(&fcount, ctx->h_pinned, sizeof(int));
+            std::swap(fa, fb);
+        }
+        // the reached node nearest to r that still holds an original edge
+        RepState init{~0ull, ~0ull, INT_MAX};
+        PG_TRY_CUDA(ctx, cudaMemcpyAsync(st.p, &init, sizeof init, cudaMemcpyHostToDevice,
+                                         ctx->stream));
+        const unsigned grid = (unsigned)ctx->num_sms * 8;
+        for (int pass = 0; pass < (exact ? 1 : 3); ++pass) {
+            k_rep_scan<<<grid, 256, 0, ctx->stream>>>(D, n, d, m, r, reached.p, orig.p, em, exact,
+                                                      pass, st.p);
+            PG_LAUNCHED(ctx);
+        }
+        RepState h;
+        PG_TRY_CUDA(ctx, cudaMemcpyAsync(&h, st.p, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+        PG_TRY(pg_sync_check(ctx, "connect replacement"));
+        const int p = exact ? (h.key32 == ~0ull ? -1 : (int)(h.key32 & 0xffffffffu))
+                            : (h.id64 == INT_MAX ? -1 : h.id64);
+        if (p < 0)
+            return pg_fail(ctx, PG_ERR_CAPACITY,
+                           "connect: no reached node has a free slot or an original edge "
+                           "(unreached node %lld)", (long long)r);
+        k_rep_replace<<<1, 32, 0, ctx->stream>>>(nbr, R, orig.p, p, (int)r);
+        PG_LAUNCHED(ctx);
+        ++replaced;
+    }
+    if (host_added) {
+        PG_TRY(sum.alloc(ctx, 1));
+        PG_TRY_CUDA(ctx, cudaMemsetAsync(sum.p, 0, 8, ctx->stream));
+        k_deg_sum<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(deg, deg0.p, n, sum.p);
+        PG_LAUNCHED(ctx);
+        unsigned long long v = 0;
+        PG_TRY_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned, sum.p, 8, cudaMemcpyDeviceToHost,
+                                         ctx->stream));
+        PG_TRY(pg_sync_check(ctx, "connect"));
+        memcpy(&v, ctx->h_pinned, 8);
+        *host_added = (int64_t)v + replaced;
+    }
+    if (host_replaced) *host_replaced = replaced;
+    return PG_OK;
+}
+
+extern "C" pg_status pg_connect_replace(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
+                                        pg_metric metric, int32_t *nbr, int32_t *deg, int32_t R,
+                                        int64_t ep, int64_t *host_added,
+                                        int64_t *host_replaced) {
+    if (!ctx) return PG_ERR_INVALID_ARG;
+    if (!D || !nbr || !deg) return pg_fail(ctx, PG_ERR_INVALID_ARG, "null pointer");
+    if (n < 1 || n >= INT_MAX || d < 4 || d % 4 || d > 8192 || R < 1 || R > 64)
+        return pg_fail(ctx, PG_ERR_INVALID_ARG, "bad n / d / R");
+    if (ep < 0 || ep >= n) return pg_fail(ctx, PG_ERR_INVALID_ARG, "ep out of range");
+    DataFacts facts;
+    PG_TRY(pg_data_facts(ctx, D, n, d, metric, &facts));
+    return pg_connect_replace_internal(ctx, D, n, d, metric, nbr, deg, R, ep, facts, nullptr, 0,
+                                       host_added, host_replaced);
+}

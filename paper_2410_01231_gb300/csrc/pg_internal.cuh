@@ -31,6 +31,8 @@ struct pg_ctx {
     int64_t connect_why_full = 0;     // batches cut short by a candidate that filled up
     int64_t connect_free = 0;         // nodes with a free slot when connectivity steps began
     int count_ties = 0;               // pruning counts near-tie decisions (pg_ctx_set_tie_count)
+    int last_derr = 0;                // device error code of the last failed synchronisation
+    int64_t last_err_info = 0;        // ... and its info word (e.g. the refused node)
     // optional CUDA-event timing of named kernels
     int timing = 0;
     struct TimedPair {
