@@ -51,7 +51,8 @@ def _tight(seed, clusters=12, per=16, d=64, scale=1.0):
 
 @pytest.mark.parametrize("kind", ["real", "int"])
 def test_replacement_links_full_tight_clusters_like_the_oracle(ctx, pg, kind):
-    D = _tight(41) if kind == "real" else np.rint(_tight(41, scale=4.0) + 64).astype(np.float32)
+    # integer rows: exact FP32 distances (partial sums below 2^24), one pass
+    D = _tight(41) if kind == "real" else np.rint(_tight(41, scale=6.0)).astype(np.float32)
     n, K, R = D.shape[0], 8, 4
     ids, _ = oracle.knn(D, K)
     nbr, deg = oracle.prune(D, np.arange(n + 1, dtype=np.int64) * K, ids.ravel(), R, 66.0)

@@ -522,14 +522,21 @@ def test_insert_needs_reserved_capacity(ctx, pg):
 
 def test_connect_without_free_slot_is_reported_by_both_sides(ctx, pg):
     """R=16 after alpha=70 pruning leaves every reached node full while some
-    node is still unreached: the oracle and the library both refuse."""
+    node is still unreached: the oracle's plain step and the library's (with
+    edge replacement switched off) both refuse; with replacement (the
+    default) the build completes with every degree within its bound."""
     D = int_points(4000)
     with pytest.raises(RuntimeError):
         oracle.build_nswg(D, 16, 40, 16, 16, 70.0, 60.0, 1, "l2", seed=5)
+    prm = dict(metric="l2", K=16, L=40, R=16, M=16, alpha_deg=70.0, iters=1, seed=5)
     with pytest.raises(pg.PGError) as e:
-        pg.Index.build_nswg(ctx, dev(D), metric="l2", K=16, L=40, R=16, M=16, alpha_deg=70.0,
-                            iters=1, seed=5)
+        pg.Index.build_nswg(ctx, dev(D), connect_replace=0, **prm)
     assert e.value.status == 5
+    idx = pg.Index.build_nswg(ctx, dev(D), **prm)
+    for i in range(idx.info()["n_layers"]):
+        gid, nb, dg = _export(idx, i)
+        assert (dg >= 0).all() and (dg <= nb.shape[1]).all()
+    idx.close()
 
 
 def test_build_nswg_cosine_properties_and_recall(ctx, pg):
