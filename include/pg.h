@@ -208,12 +208,16 @@ pg_status pg_ctx_set_tie_count(pg_ctx *ctx, int enable);
  * (tcgen05, BF16 inputs, FP32 accumulation).  When the BF16 copy of D and
  * every partial sum are exact (integer rows with |x| <= 256 whose squared
  * distances stay below 2^24, L2) the result equals the FP32 form's.  For
- * other rows the tiles select the min(128, max(2K, K + 8)) BF16-nearest
- * candidates of each row, which are re-measured in FP32 and cut to K:
- * distances and order are FP32, membership at the K-th place can differ
- * from the exact lists (measured by list recall).  K beyond the tile
- * kernels' limit, or PG_PREC_FP32, runs the FP32 tiles (exact lists, FP64
- * fix-up of near ties). */
+ * other rows the rows are centred (L2) and split into BF16 hi + lo parts;
+ * the tiles contract [hi|hi|lo] with [hi|lo|hi] and keep each row's
+ * Ks = min(120, max(2K, K + 8)) nearest, which are re-measured in FP32 with
+ * FP64 re-ordering of near ties; a row is accepted only when a rigorous
+ * bound on the screen's error shows that no point outside its shortlist can
+ * come nearer than its K-th, and every other row is recomputed by the FP32
+ * tiles ("knn_fallback_rows"), so the lists and distances equal the FP32
+ * form's.  K beyond the tile kernels' limit, or PG_PREC_FP32, runs the
+ * FP32 tiles (exact lists, FP64 fix-up of near ties).  Distances are the
+ * FP64 values rounded to FP32 where a row was re-measured. */
 pg_status pg_build_knn(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
                        int32_t K, pg_precision precision, int32_t *ids, float *dist);
 

@@ -681,7 +681,7 @@ pg_status knn_core(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric 
         facts.bf16_exact && pg_knn_tc_supported(d, K))
         return pg_knn_tc(ctx, D, n, d, self ? nullptr : Q, nq, self, K, xn.p, qnp, ids, dist);
     // Other data in the screened form (self kNN): the certified hi/lo
-    // screen for the Ks = min(128, max(2K, K + 8)) nearest, then FP32 tiles
+    // screen for the Ks = min(120, max(2K, K + 8)) nearest, then FP32 tiles
     // for the rows it cannot certify.  The result equals the FP32 form's.
     const int Ks = std::min(pg_knn_tc_max_k(), std::max(2 * K, K + 8));
     const int dp3 = (3 * d + 63) / 64 * 64;

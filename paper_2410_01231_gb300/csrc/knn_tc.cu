@@ -31,7 +31,7 @@ constexpr int TM = 128;       // query rows per CTA = TMEM lanes
 constexpr int TN = 128;       // candidate columns per tile
 constexpr int STAGES = 3;     // candidate-tile ring
 constexpr int KTC = 64;       // largest K of the resident-query kernel
-constexpr int KTCK = 128;     // largest K of the k-blocked kernel
+constexpr int KTCK = 120;     // largest K of the k-blocked kernel (shared-memory fit)
 constexpr int NTHREADS = 192;
 constexpr int ACC_COLS = 256;  // two accumulator buffers of TN columns
 
@@ -155,6 +155,49 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// Asynchronous form: issue the load of 32 columns into r ...
+__device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+        "%28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+
+// ... and wait for it; r is an operand of the wait so that no use of the
+// loaded values can be scheduled before it.
+__device__ __forceinline__ void tmem_ld_wait(uint32_t (&r)[32]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                   "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
+                   "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]),
+                   "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]),
+                   "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]),
+                   "+r"(r[30]), "+r"(r[31])
+                 :
+                 : "memory");
+}
+
+// r[j] as a float for a run-time j, by a tree of selects over registers
+// (no local-memory copy of the array)
+__device__ __forceinline__ float pick32(const uint32_t (&r)[32], int j) {
+    uint32_t l1[16], l2[8], l3[4], l4[2];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) l1[i] = (j & 1) ? r[2 * i + 1] : r[2 * i];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) l2[i] = (j & 2) ? l1[2 * i + 1] : l1[2 * i];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) l3[i] = (j & 4) ? l2[2 * i + 1] : l2[2 * i];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) l4[i] = (j & 8) ? l3[2 * i + 1] : l3[2 * i];
+    return __uint_as_float((j & 16) ? l4[1] : l4[0]);
 }
 
 __device__ __forceinline__ void epi_barrier(int nthreads = 128) {
@@ -284,10 +327,10 @@ __host__ __device__ inline TcLayout tc_layout(int dp, int H, bool KB = false) {
     o += (uint32_t)H * tc_kcap(KB) * TM * 4;
     L.li = o;  // H x [kcap][TM] ids
     o += (uint32_t)H * tc_kcap(KB) * TM * 4;
-    L.nbuf = o;
-    o += 2 * TN * 4;
-    L.cnt = o;  // entries of the second heap of every row
-    o += TM * 4;
+    L.nbuf = o;  // per epilogue warp: the norms and ids of its columns of the tile
+    o += 8 * TN * 4;
+    L.cnt = o;  // entries of the second heap of every row (H = 2)
+    o += H == 2 ? TM * 4 : 0;
     L.bars = o;
     o += 16 * 8;
     L.misc = o;
@@ -490,74 +533,101 @@ k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUten
         int count = 0;
         float thr = INFINITY;  // the heap's K-th pair once full
         int thr_id = INT_MAX;
-        // Column norms: lane j of a warp loads the norm of column j of each
-        // 32-column chunk it processes, one tile ahead, and stages it in the
-        // warp's own 32-float slot right before the chunk: no barrier across
-        // warps inside the tile loop.
+        // Column norms and ids: lane j of a warp loads, one tile ahead, the
+        // norm and the original id of column j of each 32-column chunk it
+        // screens, and stages them in the warp's own slot once per tile (no
+        // barrier across warps inside the tile loop).
         constexpr int NCH = 4 / H;  // chunks of one thread per tile
-        float *wn = nbuf + (warp - 2) * 32;
+        constexpr int WC = 32 * NCH;
+        float *wn = nbuf + (warp - 2) * WC;
+        int *wp = reinterpret_cast<int *>(nbuf + 4 * TN) + (warp - 2) * WC;
         auto colnorm = [&](int t, int c) -> float {
             if (t >= ntiles) return INFINITY;
             const int64_t col = (int64_t)tile_at(t) * TN + c * 32 + lane;
             return col < n ? xnorm[col] : INFINITY;
         };
+        auto colid = [&](int t, int c) -> int {
+            if (t >= ntiles) return INT_MAX;
+            const int64_t col = (int64_t)tile_at(t) * TN + c * 32 + lane;
+            return col < n ? (perm ? perm[col] : (int)col) : INT_MAX;
+        };
         float nxt[NCH];
+        int nxi[NCH];
 #pragma unroll
-        for (int ci = 0; ci < NCH; ++ci) nxt[ci] = colnorm(0, c_lo + ci);
+        for (int ci = 0; ci < NCH; ++ci) {
+            nxt[ci] = colnorm(0, c_lo + ci);
+            nxi[ci] = colid(0, c_lo + ci);
+        }
         for (int t = 0; t < ntiles; ++t) {
             const int a = t & 1;
             const int64_t colbase = (int64_t)tile_at(t) * TN;
             float cur[NCH];
+            int curi[NCH];
 #pragma unroll
             for (int ci = 0; ci < NCH; ++ci) {
                 cur[ci] = nxt[ci];
+                curi[ci] = nxi[ci];
                 nxt[ci] = colnorm(t + 1, c_lo + ci);
+                nxi[ci] = colid(t + 1, c_lo + ci);
             }
             mbar_wait(acc_full + a, (t >> 1) & 1, abort, err);
             // a warp that sees the abort leaves; the others leave at their
             // next check (no epilogue barrier inside this loop)
             if (__any_sync(0xffffffffu, *abort != 0)) break;
             tc_fence_after();
+            // every chunk's TMEM load in flight at once, then one wait
+            const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * TN);
+            uint32_t rb[NCH][32];
+#pragma unroll
+            for (int ci = 0; ci < NCH; ++ci)
+                tmem_ld32_issue(trow + (uint32_t)((c_lo + ci) * 32), rb[ci]);
+            __syncwarp();
 #pragma unroll
             for (int ci = 0; ci < NCH; ++ci) {
-                const int c = c_lo + ci;
-                __syncwarp();
-                wn[lane] = cur[ci];
-                __syncwarp();
-                float v[32];
-                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * TN + c * 32), v);
-                float nbv[32];
-                const float4 *nb4 = reinterpret_cast<const float4 *>(wn);
+                wn[ci * 32 + lane] = cur[ci];
+                wp[ci * 32 + lane] = curi[ci];
+            }
+            __syncwarp();
+#pragma unroll
+            for (int ci = 0; ci < NCH; ++ci) tmem_ld_wait(rb[ci]);
+            // screen: the chunk minimum of |x|^2 - 2<q, x> by independent
+            // chains (the minimum is exact in any order)
+            float mc[NCH];
+#pragma unroll
+            for (int ci = 0; ci < NCH; ++ci) {
+                const float4 *nb4 = reinterpret_cast<const float4 *>(wn + ci * 32);
+                float m4[4] = {INFINITY, INFINITY, INFINITY, INFINITY};
 #pragma unroll
                 for (int j4 = 0; j4 < 8; ++j4) {
-                    const float4 t4 = nb4[j4];
-                    nbv[j4 * 4 + 0] = t4.x;
-                    nbv[j4 * 4 + 1] = t4.y;
-                    nbv[j4 * 4 + 2] = t4.z;
-                    nbv[j4 * 4 + 3] = t4.w;
+                    const float4 nb = nb4[j4];
+                    m4[0] = fminf(m4[0], fmaf(-2.f, __uint_as_float(rb[ci][4 * j4 + 0]), nb.x));
+                    m4[1] = fminf(m4[1], fmaf(-2.f, __uint_as_float(rb[ci][4 * j4 + 1]), nb.y));
+                    m4[2] = fminf(m4[2], fmaf(-2.f, __uint_as_float(rb[ci][4 * j4 + 2]), nb.z));
+                    m4[3] = fminf(m4[3], fmaf(-2.f, __uint_as_float(rb[ci][4 * j4 + 3]), nb.w));
                 }
-                float m = INFINITY;
+                mc[ci] = fminf(fminf(m4[0], m4[1]), fminf(m4[2], m4[3]));
+            }
+            // rare: a row may accept a column of a chunk (ties with the K-th
+            // distance are decided by id); each thread pushes into its own
+            // heap, independently of the other lanes
 #pragma unroll
-                for (int j = 0; j < 32; ++j) m = fminf(m, fmaf(-2.f, v[j], nbv[j]));
-                // rare: this row may accept a column of the chunk (ties with
-                // the K-th distance are decided by id); each thread pushes
-                // into its own heap, independently of the other lanes
-                if (!(live && nqr + m <= thr)) continue;
-                float sv[32];
+            for (int ci = 0; ci < NCH; ++ci) {
+                if (!(live && nqr + mc[ci] <= thr)) continue;
+                const float *nb = wn + ci * 32;
                 unsigned mask = 0;
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
-                    sv[j] = fmaxf(nqr + fmaf(-2.f, v[j], nbv[j]), 0.f);
-                    if (sv[j] <= thr) mask |= 1u << j;
+                    const float sv = fmaxf(nqr + fmaf(-2.f, __uint_as_float(rb[ci][j]), nb[j]), 0.f);
+                    if (sv <= thr) mask |= 1u << j;
                 }
                 while (mask) {
                     const int j = __ffs(mask) - 1;
                     mask &= mask - 1;
-                    const float s = sv[j];
+                    const float s = fmaxf(nqr + fmaf(-2.f, pick32(rb[ci], j), nb[j]), 0.f);
                     if (!(s <= thr)) continue;
-                    const int64_t col = colbase + c * 32 + j;
+                    const int64_t col = colbase + (c_lo + ci) * 32 + j;
                     if (col >= n || (self_exclude && col == g)) continue;
-                    const int id = perm ? perm[col] : (int)col;
+                    const int id = wp[ci * 32 + j];
                     if (!pair_less(s, id, thr, thr_id)) continue;
                     heap_push(Ls, Li, row, K, count, s, id, thr, thr_id);
                 }
