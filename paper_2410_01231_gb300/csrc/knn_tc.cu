@@ -7,11 +7,13 @@
 // 2^24: then the BF16 copy is exact and the tensor-core sums are exact
 // integers, so the result equals the FP32 and FP64 definitions bit for bit.
 //
-// CTA = 6 warps.  Warp 0 issues TMA loads (128B-swizzled K-major tiles):
-// the 128-row query tile once, then 128-row candidate tiles through a
+// CTA = 6 warps.  The epilogue threads first write the 128-row query tile
+// into TMEM (one row per lane, two BF16 per 32-bit column), so the MMAs
+// read only the candidate tiles from shared memory.  Warp 0 issues TMA loads
+// (128B-swizzled K-major tiles) of 128-row candidate tiles through a
 // 3-stage ring.  Warp 1 owns the TMEM allocation and issues the MMAs
-// (M128 N128 K16 steps) into a double-buffered FP32 accumulator (2 x 128
-// columns).  Warps 2-5 are the epilogue: thread t of the four owns query
+// (M128 N128 K16 steps, A from TMEM) into a double-buffered FP32
+// accumulator (2 x 128 columns).  Warps 2-5 are the epilogue: thread t of the four owns query
 // row t; it reads its accumulator row with tcgen05.ld.32x32b.x32, screens
 // 32 columns at a time by their minimum against its current K-th distance
 // and keeps a private max-heap of its K best in shared memory (sorted once
@@ -126,6 +128,16 @@ __device__ __forceinline__ void umma_bf16(uint32_t dtmem, uint64_t ad, uint64_t 
         "l"(ad), "l"(bd), "r"(IDESC), "r"(acc));
 }
 
+// D (TMEM) [+]= A (TMEM, lane = row, a 32-bit column = two consecutive
+// BF16 of a row) x B (shared memory descriptor)
+__device__ __forceinline__ void umma_bf16_ts(uint32_t dtmem, uint32_t atmem, uint64_t bd,
+                                             uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}" ::"r"(dtmem),
+        "r"(atmem), "l"(bd), "r"(IDESC), "r"(acc));
+}
+
 __device__ __forceinline__ void umma_commit(uint64_t *bar) {
     asm volatile(
         "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -157,47 +169,18 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-// Asynchronous form: issue the load of 32 columns into r ...
-__device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, uint32_t (&r)[32]) {
+// 32 columns of the warp's TMEM lane quarter from 32 registers per thread
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
         "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
-        "%28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-}
-
-// ... and wait for it; r is an operand of the wait so that no use of the
-// loaded values can be scheduled before it.
-__device__ __forceinline__ void tmem_ld_wait(uint32_t (&r)[32]) {
-    asm volatile("tcgen05.wait::ld.sync.aligned;"
-                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
-                   "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
-                   "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]),
-                   "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]),
-                   "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]),
-                   "+r"(r[30]), "+r"(r[31])
-                 :
-                 : "memory");
-}
-
-// r[j] as a float for a run-time j, by a tree of selects over registers
-// (no local-memory copy of the array)
-__device__ __forceinline__ float pick32(const uint32_t (&r)[32], int j) {
-    uint32_t l1[16], l2[8], l3[4], l4[2];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) l1[i] = (j & 1) ? r[2 * i + 1] : r[2 * i];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) l2[i] = (j & 2) ? l1[2 * i + 1] : l1[2 * i];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) l3[i] = (j & 4) ? l2[2 * i + 1] : l2[2 * i];
-#pragma unroll
-    for (int i = 0; i < 2; ++i) l4[i] = (j & 8) ? l3[2 * i + 1] : l3[2 * i];
-    return __uint_as_float((j & 16) ? l4[1] : l4[0]);
+        "%28, %29, %30, %31, %32};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+        "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
+        "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]),
+        "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]),
+        "r"(r[29]), "r"(r[30]), "r"(r[31])
+        : "memory");
 }
 
 __device__ __forceinline__ void epi_barrier(int nthreads = 128) {
@@ -319,16 +302,15 @@ constexpr uint32_t KB_STAGE = (uint32_t)(TM + TN) * 64 * 2;  // bytes of one k-b
 __host__ __device__ inline TcLayout tc_layout(int dp, int H, bool KB = false) {
     TcLayout L;
     uint32_t o = 0;
-    L.a = o;
-    if (!KB) o += (uint32_t)TM * dp * 2;
+    L.a = o;  // unused: the resident query tile lives in TMEM
     L.b = o;
     o += KB ? tc_stages(H, KB) * KB_STAGE : (uint32_t)tc_stages(H) * TN * dp * 2;
     L.ls = o;  // H x [kcap][TM] per-row heaps: distances
     o += (uint32_t)H * tc_kcap(KB) * TM * 4;
     L.li = o;  // H x [kcap][TM] ids
     o += (uint32_t)H * tc_kcap(KB) * TM * 4;
-    L.nbuf = o;  // per epilogue warp: the norms and ids of its columns of the tile
-    o += 8 * TN * 4;
+    L.nbuf = o;
+    o += 2 * TN * 4;
     L.cnt = o;  // entries of the second heap of every row (H = 2)
     o += H == 2 ? TM * 4 : 0;
     L.bars = o;
@@ -345,15 +327,18 @@ __host__ __device__ inline TcLayout tc_layout(int dp, int H, bool KB = false) {
 template <int H, bool KB>
 __global__ void __launch_bounds__(tc_threads(H), 1)
 k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUtensorMap mapX,
-         int64_t nq, int64_t n, int dp, const float *__restrict__ qnorm,
+         const __nv_bfloat16 *__restrict__ qrows, int64_t nq, int64_t n, int dp,
+         const float *__restrict__ qnorm,
          const float *__restrict__ xnorm, int K, int self_exclude, int32_t *__restrict__ out_i,
          float *__restrict__ out_s, int *err, const int32_t *__restrict__ perm, int rotate,
          unsigned long long *progress, int resident) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = reinterpret_cast<uint8_t *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     constexpr int STG = tc_stages(H, KB), NEPI = 128 * H, KCAP = tc_kcap(KB);
+    // resident variants: accumulators in columns [0, 256), the query tile in
+    // [256, 256 + dp / 2) (two BF16 of a row per 32-bit column)
+    constexpr uint32_t TMEM_COLS = KB ? (uint32_t)ACC_COLS : 512u;
     const TcLayout Ly = tc_layout(dp, H, KB);
-    uint8_t *A = sm + Ly.a;
     uint8_t *B = sm + Ly.b;
     float *Ls0 = reinterpret_cast<float *>(sm + Ly.ls);
     int *Li0 = reinterpret_cast<int *>(sm + Ly.li);
@@ -370,7 +355,7 @@ k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUten
     const int64_t row0 = (int64_t)blockIdx.x * TM;
     const int nkb = dp / 64;
     const int ntiles = (int)((n + TN - 1) / TN);
-    const uint32_t a_bytes = (uint32_t)TM * dp * 2, b_bytes = (uint32_t)TN * dp * 2;
+    const uint32_t b_bytes = (uint32_t)TN * dp * 2;
     // With `rotate` (spatially sorted points) the scan first covers a window
     // of `pre` tiles around the CTA's own rows, where its nearest candidates
     // are, so the thresholds tighten early; then every other tile in a
@@ -386,7 +371,7 @@ k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUten
     int *start_slot = reinterpret_cast<int *>(sm + Ly.misc + 8);
 
     if (threadIdx.x == 0) {
-        mbar_init(a_full, 1);
+        mbar_init(a_full, KB ? 1 : NEPI);  // resident: every epilogue thread stages its row
         for (int s = 0; s < STG; ++s) {
             mbar_init(b_full + s, 1);
             mbar_init(b_empty + s, 1);
@@ -405,7 +390,7 @@ k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUten
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          saddr(tmem_slot)),
-                     "r"(ACC_COLS)
+                     "r"(TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -449,9 +434,6 @@ k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUten
                 }
             }
         } else if (lane == 0) {  // ---------------- TMA producer
-            mbar_expect_tx(a_full, a_bytes);
-            for (int kb = 0; kb < nkb; ++kb)
-                tma_load_2d(A + kb * TM * 128, &mapQ, a_full, kb * 64, (int)row0);
             int issued = 0;
             for (int t = 0; t < ntiles; ++t) {
                 const int s = t % STG;
@@ -505,11 +487,11 @@ k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUten
                 if (!mbar_wait(b_full + s, (t / STG) & 1, abort, err, true)) break;
                 if (!mbar_wait(acc_empty + a, ((t >> 1) & 1) ^ 1, abort, err, true)) break;
                 tc_fence_after();
-                const uint32_t a0 = saddr(A), b0 = saddr(B + (size_t)s * TN * dp * 2);
+                const uint32_t b0 = saddr(B + (size_t)s * TN * dp * 2);
                 for (int k = 0; k < dp / 16; ++k) {
                     const int kb = k >> 2, koff = (k & 3) * 32;
-                    umma_bf16(tmem + a * TN, sw128_desc(a0 + kb * TM * 128 + koff),
-                              sw128_desc(b0 + kb * TN * 128 + koff), k > 0 ? 1u : 0u);
+                    umma_bf16_ts(tmem + a * TN, tmem + ACC_COLS + 8 * k,
+                                 sw128_desc(b0 + kb * TN * 128 + koff), k > 0 ? 1u : 0u);
                 }
                 umma_commit(b_empty + s);
                 umma_commit(acc_full + a);
@@ -530,104 +512,99 @@ k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUten
         const int64_t g = row0 + row;
         const bool live = g < nq;
         const float nqr = live ? qnorm[g] : 0.f;
+        if (!KB) {
+            // the query tile into TMEM: thread `row` writes its row (zeros
+            // past nq) to columns [256, 256 + dp / 2) of its lane
+            if (half == 0) {
+                const uint4 *src = reinterpret_cast<const uint4 *>(qrows + (live ? g : 0) * dp);
+                for (int b = 0; b < dp / 64; ++b) {
+                    uint32_t r[32];
+#pragma unroll
+                    for (int c4 = 0; c4 < 8; ++c4) {
+                        const uint4 v = live ? __ldg(src + b * 8 + c4) : make_uint4(0u, 0u, 0u, 0u);
+                        r[4 * c4 + 0] = v.x;
+                        r[4 * c4 + 1] = v.y;
+                        r[4 * c4 + 2] = v.z;
+                        r[4 * c4 + 3] = v.w;
+                    }
+                    tmem_st32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ACC_COLS + 32 * b), r);
+                }
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            }
+            tc_fence_before();
+            mbar_arrive(a_full);
+        }
         int count = 0;
         float thr = INFINITY;  // the heap's K-th pair once full
         int thr_id = INT_MAX;
-        // Column norms and ids: lane j of a warp loads, one tile ahead, the
-        // norm and the original id of column j of each 32-column chunk it
-        // screens, and stages them in the warp's own slot once per tile (no
-        // barrier across warps inside the tile loop).
+        // Column norms: lane j of a warp loads the norm of column j of each
+        // 32-column chunk it processes, one tile ahead, and stages it in the
+        // warp's own 32-float slot right before the chunk: no barrier across
+        // warps inside the tile loop.
         constexpr int NCH = 4 / H;  // chunks of one thread per tile
-        constexpr int WC = 32 * NCH;
-        float *wn = nbuf + (warp - 2) * WC;
-        int *wp = reinterpret_cast<int *>(nbuf + 4 * TN) + (warp - 2) * WC;
+        float *wn = nbuf + (warp - 2) * 32;
         auto colnorm = [&](int t, int c) -> float {
             if (t >= ntiles) return INFINITY;
             const int64_t col = (int64_t)tile_at(t) * TN + c * 32 + lane;
             return col < n ? xnorm[col] : INFINITY;
         };
-        auto colid = [&](int t, int c) -> int {
-            if (t >= ntiles) return INT_MAX;
-            const int64_t col = (int64_t)tile_at(t) * TN + c * 32 + lane;
-            return col < n ? (perm ? perm[col] : (int)col) : INT_MAX;
-        };
         float nxt[NCH];
-        int nxi[NCH];
 #pragma unroll
-        for (int ci = 0; ci < NCH; ++ci) {
-            nxt[ci] = colnorm(0, c_lo + ci);
-            nxi[ci] = colid(0, c_lo + ci);
-        }
+        for (int ci = 0; ci < NCH; ++ci) nxt[ci] = colnorm(0, c_lo + ci);
         for (int t = 0; t < ntiles; ++t) {
             const int a = t & 1;
             const int64_t colbase = (int64_t)tile_at(t) * TN;
             float cur[NCH];
-            int curi[NCH];
 #pragma unroll
             for (int ci = 0; ci < NCH; ++ci) {
                 cur[ci] = nxt[ci];
-                curi[ci] = nxi[ci];
                 nxt[ci] = colnorm(t + 1, c_lo + ci);
-                nxi[ci] = colid(t + 1, c_lo + ci);
             }
             mbar_wait(acc_full + a, (t >> 1) & 1, abort, err);
             // a warp that sees the abort leaves; the others leave at their
             // next check (no epilogue barrier inside this loop)
             if (__any_sync(0xffffffffu, *abort != 0)) break;
             tc_fence_after();
-            // every chunk's TMEM load in flight at once, then one wait
-            const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * TN);
-            uint32_t rb[NCH][32];
-#pragma unroll
-            for (int ci = 0; ci < NCH; ++ci)
-                tmem_ld32_issue(trow + (uint32_t)((c_lo + ci) * 32), rb[ci]);
-            __syncwarp();
 #pragma unroll
             for (int ci = 0; ci < NCH; ++ci) {
-                wn[ci * 32 + lane] = cur[ci];
-                wp[ci * 32 + lane] = curi[ci];
-            }
-            __syncwarp();
-#pragma unroll
-            for (int ci = 0; ci < NCH; ++ci) tmem_ld_wait(rb[ci]);
-            // screen: the chunk minimum of |x|^2 - 2<q, x> by independent
-            // chains (the minimum is exact in any order)
-            float mc[NCH];
-#pragma unroll
-            for (int ci = 0; ci < NCH; ++ci) {
-                const float4 *nb4 = reinterpret_cast<const float4 *>(wn + ci * 32);
-                float m4[4] = {INFINITY, INFINITY, INFINITY, INFINITY};
+                const int c = c_lo + ci;
+                __syncwarp();
+                wn[lane] = cur[ci];
+                __syncwarp();
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * TN + c * 32), v);
+                float nbv[32];
+                const float4 *nb4 = reinterpret_cast<const float4 *>(wn);
 #pragma unroll
                 for (int j4 = 0; j4 < 8; ++j4) {
-                    const float4 nb = nb4[j4];
-                    m4[0] = fminf(m4[0], fmaf(-2.f, __uint_as_float(rb[ci][4 * j4 + 0]), nb.x));
-                    m4[1] = fminf(m4[1], fmaf(-2.f, __uint_as_float(rb[ci][4 * j4 + 1]), nb.y));
-                    m4[2] = fminf(m4[2], fmaf(-2.f, __uint_as_float(rb[ci][4 * j4 + 2]), nb.z));
-                    m4[3] = fminf(m4[3], fmaf(-2.f, __uint_as_float(rb[ci][4 * j4 + 3]), nb.w));
+                    const float4 t4 = nb4[j4];
+                    nbv[j4 * 4 + 0] = t4.x;
+                    nbv[j4 * 4 + 1] = t4.y;
+                    nbv[j4 * 4 + 2] = t4.z;
+                    nbv[j4 * 4 + 3] = t4.w;
                 }
-                mc[ci] = fminf(fminf(m4[0], m4[1]), fminf(m4[2], m4[3]));
-            }
-            // rare: a row may accept a column of a chunk (ties with the K-th
-            // distance are decided by id); each thread pushes into its own
-            // heap, independently of the other lanes
+                float m = INFINITY;
 #pragma unroll
-            for (int ci = 0; ci < NCH; ++ci) {
-                if (!(live && nqr + mc[ci] <= thr)) continue;
-                const float *nb = wn + ci * 32;
+                for (int j = 0; j < 32; ++j) m = fminf(m, fmaf(-2.f, v[j], nbv[j]));
+                // rare: this row may accept a column of the chunk (ties with
+                // the K-th distance are decided by id); each thread pushes
+                // into its own heap, independently of the other lanes
+                if (!(live && nqr + m <= thr)) continue;
+                float sv[32];
                 unsigned mask = 0;
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
-                    const float sv = fmaxf(nqr + fmaf(-2.f, __uint_as_float(rb[ci][j]), nb[j]), 0.f);
-                    if (sv <= thr) mask |= 1u << j;
+                    sv[j] = fmaxf(nqr + fmaf(-2.f, v[j], nbv[j]), 0.f);
+                    if (sv[j] <= thr) mask |= 1u << j;
                 }
                 while (mask) {
                     const int j = __ffs(mask) - 1;
                     mask &= mask - 1;
-                    const float s = fmaxf(nqr + fmaf(-2.f, pick32(rb[ci], j), nb[j]), 0.f);
+                    const float s = sv[j];
                     if (!(s <= thr)) continue;
-                    const int64_t col = colbase + (c_lo + ci) * 32 + j;
+                    const int64_t col = colbase + c * 32 + j;
                     if (col >= n || (self_exclude && col == g)) continue;
-                    const int id = wp[ci * 32 + j];
+                    const int id = perm ? perm[col] : (int)col;
                     if (!pair_less(s, id, thr, thr_id)) continue;
                     heap_push(Ls, Li, row, K, count, s, id, thr, thr_id);
                 }
@@ -693,7 +670,7 @@ k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUten
     if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                     "r"(ACC_COLS)
+                     "r"(TMEM_COLS)
                      : "memory");
     }
 }
@@ -1042,22 +1019,26 @@ static pg_status tc_knn_run(pg_ctx *ctx, Scratch<__nv_bfloat16> &xc,
     // tiles issued by all CTAs of a launch (the common start of each cycle)
     Scratch<unsigned long long> prog;
     PG_TRY(prog.alloc(ctx, 2));
-    auto launch = [&](unsigned grid, const CUtensorMap &mq_, const CUtensorMap &mx_, int64_t nq_,
-                      int64_t n_, const float *qn_, const float *xn_, int K_, int self_,
-                      int32_t *oi, float *os, const int32_t *perm_, int rot) -> pg_status {
+    auto launch = [&](unsigned grid, const CUtensorMap &mq_, const CUtensorMap &mx_,
+                      const __nv_bfloat16 *qrows_, int64_t nq_, int64_t n_, const float *qn_,
+                      const float *xn_, int K_, int self_, int32_t *oi, float *os,
+                      const int32_t *perm_, int rot) -> pg_status {
         PG_TRY_CUDA(ctx, cudaMemsetAsync(prog.p, 0, 8, ctx->stream));
         const int res = ctx->num_sms;  // one CTA per SM (shared memory)
         if (V.KB)
             k_knn_tc<1, true><<<grid, tc_threads(1), smem, ctx->stream>>>(
-                mq_, mx_, nq_, n_, dp, qn_, xn_, K_, self_, oi, os, ctx->d_err, perm_, rot, prog.p,
+                mq_, mx_, qrows_, nq_, n_, dp, qn_, xn_, K_, self_, oi, os, ctx->d_err, perm_, rot,
+                prog.p,
                 res);
         else if (V.H == 2)
             k_knn_tc<2, false><<<grid, tc_threads(2), smem, ctx->stream>>>(
-                mq_, mx_, nq_, n_, dp, qn_, xn_, K_, self_, oi, os, ctx->d_err, perm_, rot, prog.p,
+                mq_, mx_, qrows_, nq_, n_, dp, qn_, xn_, K_, self_, oi, os, ctx->d_err, perm_, rot,
+                prog.p,
                 res);
         else
             k_knn_tc<1, false><<<grid, tc_threads(1), smem, ctx->stream>>>(
-                mq_, mx_, nq_, n_, dp, qn_, xn_, K_, self_, oi, os, ctx->d_err, perm_, rot, prog.p,
+                mq_, mx_, qrows_, nq_, n_, dp, qn_, xn_, K_, self_, oi, os, ctx->d_err, perm_, rot,
+                prog.p,
                 res);
         return PG_OK;
     };
@@ -1082,8 +1063,8 @@ static pg_status tc_knn_run(pg_ctx *ctx, Scratch<__nv_bfloat16> &xc,
         CUtensorMap mqa, mpa;
         PG_TRY(make_map(ctx, &mqa, qp, n, dp));
         PG_TRY(make_map(ctx, &mpa, pb.p, P, dp));
-        PG_TRY(launch((unsigned)((n + TM - 1) / TM), mqa, mpa, n, P, xnorm, pn.p, 1, 0, asg.p,
-                      adist.p, nullptr, 0));
+        PG_TRY(launch((unsigned)((n + TM - 1) / TM), mqa, mpa, qp, n, P, xnorm, pn.p, 1, 0,
+                      asg.p, adist.p, nullptr, 0));
         PG_LAUNCHED(ctx);
         PG_TRY(cnt.alloc(ctx, (size_t)P));
         PG_TRY(boff.alloc(ctx, (size_t)P + 1));
@@ -1123,7 +1104,7 @@ static pg_status tc_knn_run(pg_ctx *ctx, Scratch<__nv_bfloat16> &xc,
     PG_TRY(make_map(ctx, &mq, qp, self ? n : nq, dp));
     const unsigned grid = (unsigned)((nq + TM - 1) / TM);
     pg_timer_begin(ctx, TM_KNN);
-    PG_TRY(launch(grid, mq, mx, nq, n, qnp, xnp, K, self, ids, dist, permp, permp ? 1 : 0));
+    PG_TRY(launch(grid, mq, mx, qp, nq, n, qnp, xnp, K, self, ids, dist, permp, permp ? 1 : 0));
     PG_LAUNCHED(ctx);
     pg_timer_end(ctx, TM_KNN, work);
     return PG_OK;
