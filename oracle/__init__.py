@@ -64,6 +64,8 @@ def _get():
         lib.or_search.restype = i32
         lib.or_search.argtypes = [P, i64, i32, i32, P, P, i32, P, P, i64, P, i32, i32, i32,
                                   i32, P, P, P]
+        lib.or_knn_descent.restype = i32
+        lib.or_knn_descent.argtypes = [P, i64, i32, i32, i32, i32, P, P, P]
         lib.or_acquire.restype = i32
         lib.or_acquire.argtypes = [P, i64, i32, i32, P, P, i32, i32, P, P]
         lib.or_build_rng.restype = i64
@@ -139,6 +141,23 @@ def prune(D, off, cand, R: int, alpha_deg: float, metric: str = "l2"):
                          cos_alpha(alpha_deg), int(alpha_deg == 60.0), _p(nbr), _p(deg))
     assert rc == 0
     return nbr, deg
+
+
+def knn_descent(D, init, iters: int, metric: str = "l2"):
+    """kNN graph refined by 2-hop neighbours (the KGraph iteration as Exp. 12
+    describes it): N_0(u) = the ids of init[u] sorted by (s, id); each
+    iteration N(u) <- the K best by (s, id) of N(u) and the lists of its
+    members, u excluded.  Returns (ids [n][K], dist [n][K] FP64)."""
+    D = _f32(D)
+    n, d = D.shape
+    init = np.ascontiguousarray(init, np.int32)
+    K = init.shape[1]
+    ids = np.empty((n, K), np.int32)
+    dist = np.empty((n, K), np.float64)
+    rc = _get().or_knn_descent(_p(D), n, d, METRICS[metric], K, int(iters), _p(init), _p(ids),
+                               _p(dist))
+    assert rc == 0
+    return ids, dist
 
 
 def reverse_union(nbr, deg):

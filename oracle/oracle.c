@@ -715,6 +715,99 @@ void or_levels(int64_t n, uint64_t seed, int M, int32_t *level)
     }
 }
 
+/* ---------------------------------------------------------------------- */
+/* kNN-graph refinement by 2-hop neighbours, the iteration of KGraph's      */
+/* NN-descent as Exp. 12 describes it: starting from K neighbours per point */
+/* (drawn at random; here an input), every iteration each point u computes  */
+/* the distance to its 2-hop neighbours, and its new list is the K best by  */
+/* (s, id) of its current neighbours and their neighbours, u excluded.      */
+/* Lists are ordered by (s, id), -1 padded, repeated ids counted once.      */
+/* cur [n][K] is read (the iteration's snapshot) and next [n][K] written.   */
+/* ---------------------------------------------------------------------- */
+static void descent_row(const float *D, int64_t n, int d, int metric, const int32_t *cur, int K,
+                        int64_t u, int32_t *out_i, double *out_s, item_t *buf, int64_t *seen,
+                        int64_t stamp)
+{
+    int m = 0;
+    for (int a = 0; a < K; ++a) {
+        const int32_t v = cur[u * K + a];
+        if (v < 0) continue;
+        for (int b = -1; b < K; ++b) {
+            const int32_t w = b < 0 ? v : cur[(int64_t)v * K + b];
+            if (w < 0 || w == u || seen[w] == stamp) continue;
+            seen[w] = stamp;
+            buf[m].s = or_dist(D + (size_t)u * d, D + (size_t)w * d, d, metric);
+            buf[m].id = w;
+            ++m;
+        }
+    }
+    qsort(buf, (size_t)m, sizeof(item_t), item_cmp);
+    for (int j = 0; j < K; ++j) {
+        out_i[j] = j < m ? buf[j].id : -1;
+        if (out_s) out_s[j] = j < m ? buf[j].s : INFINITY;
+    }
+}
+
+int or_knn_descent(const float *D, int64_t n, int d, int metric, int K, int iters,
+                   const int32_t *init, int32_t *ids, double *dist)
+{
+    int32_t *cur = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n * K));
+    int32_t *nxt = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n * K));
+    if (!cur || !nxt) {
+        free(cur);
+        free(nxt);
+        return -2;
+    }
+    /* N_0(u): the initial ids themselves, sorted by (s, id) */
+#pragma omp parallel
+    {
+        item_t *buf = (item_t *)malloc(sizeof(item_t) * (size_t)K);
+#pragma omp for schedule(dynamic, 64)
+        for (int64_t u = 0; u < n; ++u) {
+            int m = 0;
+            for (int a = 0; a < K; ++a) {
+                const int32_t v = init[u * K + a];
+                if (v < 0 || v >= n || v == u) continue;
+                int dup = 0;
+                for (int e = 0; e < m && !dup; ++e) dup = buf[e].id == v;
+                if (dup) continue;
+                buf[m].s = or_dist(D + (size_t)u * d, D + (size_t)v * d, d, metric);
+                buf[m].id = v;
+                ++m;
+            }
+            qsort(buf, (size_t)m, sizeof(item_t), item_cmp);
+            for (int j = 0; j < K; ++j) cur[u * K + j] = j < m ? buf[j].id : -1;
+        }
+        free(buf);
+    }
+    for (int it = 0; it < iters; ++it) {
+#pragma omp parallel
+        {
+            item_t *buf = (item_t *)malloc(sizeof(item_t) * (size_t)(K * (K + 1)));
+            int64_t *seen = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+            for (int64_t i = 0; i < n; ++i) seen[i] = -1;
+#pragma omp for schedule(dynamic, 16)
+            for (int64_t u = 0; u < n; ++u)
+                descent_row(D, n, d, metric, cur, K, u, nxt + u * K, NULL, buf, seen, u);
+            free(buf);
+            free(seen);
+        }
+        int32_t *t = cur;
+        cur = nxt;
+        nxt = t;
+    }
+    for (int64_t u = 0; u < n; ++u)
+        for (int j = 0; j < K; ++j) {
+            const int32_t v = cur[u * K + j];
+            ids[u * K + j] = v;
+            dist[u * K + j] = v >= 0 ? or_dist(D + (size_t)u * d, D + (size_t)v * d, d, metric)
+                                     : INFINITY;
+        }
+    free(cur);
+    free(nxt);
+    return 0;
+}
+
 int or_num_threads(void)
 {
 #ifdef _OPENMP
