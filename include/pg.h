@@ -130,12 +130,15 @@ typedef struct {
     int32_t connect_replace; /* connectivity steps use edge replacement when every
                                 reached node is full (pg_connect_replace); 0: such a
                                 build fails with PG_ERR_CAPACITY                    */
+    int32_t knn_descent_iters; /* initial KNNG: -1 the exact kNN tiles; >= 0 the
+                                approximate graph of pg_knn_descent with that many
+                                iterations from a random draw (seed), K <= 64  */
 } pg_build_params;
 
 /* Defaults: L2SQ, FP32, K=64, L=200, R=32, M=16, alpha 66/60, I=2,
  * connect_final=1, route_layers=1, seed=0, reuse_pruning=1,
  * quality_target=0 (fixed I), quality_eps=0.6, quality_k=0 (K),
- * connect_replace=1.  params must not be NULL. */
+ * connect_replace=1, knn_descent_iters=-1.  params must not be NULL. */
 void pg_default_params(pg_build_params *params);
 
 /* ---------------------------------------------------------------- context */
@@ -220,6 +223,23 @@ pg_status pg_ctx_set_tie_count(pg_ctx *ctx, int enable);
  * FP64 values rounded to FP32 where a row was re-measured. */
 pg_status pg_build_knn(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
                        int32_t K, pg_precision precision, int32_t *ids, float *dist);
+
+/* Approximate KNNG by 2-hop refinement, the KGraph (NN-descent) iteration
+ * of the initialization phase (Section 3.1) as Exp. 12 describes it: each
+ * point starts from K ids (init, DEVICE [n][K]: any order, repeats, -1 and
+ * the point itself allowed and dropped; NULL: drawn by the library, id
+ * j of point u = high 64 bits of SplitMix64(seed XOR (u K + j)) times n);
+ * every iteration every point u takes the K best by (s(u, .), id) of its
+ * neighbours and their neighbours, u excluded (all points read the previous
+ * iteration's lists).  Pairs whose both entries were already there in the
+ * previous iteration are not compared again (they cannot enter), which does
+ * not change the result.  Out: ids / dist [n][K] as pg_build_knn (FP32
+ * distances; orders decided on FP32 values, exact for rows whose FP32
+ * distances are exact).  1 <= K <= 64, 0 <= iters <= 64.  host_updates
+ * (host, may be NULL) [iters]: entries that entered a list per iteration. */
+pg_status pg_knn_descent(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
+                         int32_t K, int32_t iters, const int32_t *init, uint64_t seed,
+                         int32_t *ids, float *dist, int64_t *host_updates);
 
 /* Exact k nearest points of D for external queries Q [nq][d] (ground
  * truth for recall).  Same output layout and precision rules as

@@ -42,7 +42,7 @@ class BuildParams(C.Structure):
                 ("M", i32), ("alpha_deg", dbl), ("alpha_final_deg", dbl), ("iters", i32),
                 ("connect_final", i32), ("route_layers", i32), ("seed", u64),
                 ("reuse_pruning", i32), ("quality_target", dbl), ("quality_eps", dbl),
-                ("quality_k", i32), ("connect_replace", i32)]
+                ("quality_k", i32), ("connect_replace", i32), ("knn_descent_iters", i32)]
 
 
 class PruneStats(C.Structure):
@@ -72,6 +72,7 @@ _sig("pg_quality_sample_size", i64, [i64, dbl, dbl])
 _sig("pg_quality_sample", C.c_int, [i64, i64, u64, P])
 _sig("pg_index_quality", C.c_int, [P, P, P, P])
 _sig("pg_connect_replace", C.c_int, [P, P, i64, i32, C.c_int, P, P, i32, i64, P, P])
+_sig("pg_knn_descent", C.c_int, [P, P, i64, i32, C.c_int, i32, i32, P, u64, P, P, P])
 _sig("pg_prune_k2p", C.c_int, [P, P, i64, i32, C.c_int, P, P, P, P, i32, i32, dbl, C.c_int, P, P,
                                P])
 _sig("pg_reverse_union", C.c_int, [P, P, P, i64, i32, P, P, i64, P])
@@ -122,7 +123,7 @@ EXPORTS = ["pg_default_params", "pg_ctx_create", "pg_ctx_destroy", "pg_last_erro
            "pg_ctx_launches", "pg_build_knn", "pg_knn_query", "pg_prune", "pg_reverse_union",
            "pg_medoid", "pg_connect", "pg_acquire_candidates", "pg_search_graph", "pg_build_rng",
            "pg_build_rng_host", "pg_measure_fp32_peak", "pg_prune_k2p",
-           "pg_kcna_recall", "pg_connect_replace", "pg_quality_sample_size", "pg_quality_sample", "pg_index_quality",
+           "pg_kcna_recall", "pg_connect_replace", "pg_knn_descent", "pg_quality_sample_size", "pg_quality_sample", "pg_index_quality",
            "pg_build_nswg", "pg_search", "pg_search_host", "pg_index_destroy", "pg_index_info",
            "pg_index_layer", "pg_index_phase_seconds", "pg_index_export_layer",
            "pg_ctx_set_timing", "pg_ctx_set_tie_count", "pg_ctx_kernel_time", "pg_ctx_counter",
@@ -296,6 +297,23 @@ def build_knn(ctx: Context, D: torch.Tensor, K: int, metric="l2", precision="fp3
     ctx._check(_lib.pg_build_knn(ctx.handle, _ptr(D), n, d, METRIC[metric], K,
                                  PRECISION[precision], _ptr(ids), _ptr(dist)), "pg_build_knn")
     return ids, dist
+
+
+def knn_descent(ctx: Context, D: torch.Tensor, K: int, iters: int, init=None, seed: int = 0,
+                metric="l2"):
+    """pg_knn_descent: approximate KNNG by 2-hop refinement; returns
+    (ids [n][K], dist [n][K], entries entering the lists per iteration)."""
+    D = _dev(D, torch.float32, "D")
+    n, d = D.shape
+    if init is not None:
+        init = _dev(init, torch.int32, "init")
+    ids = torch.empty((n, K), dtype=torch.int32, device=D.device)
+    dist = torch.empty((n, K), dtype=torch.float32, device=D.device)
+    upd = (C.c_int64 * max(iters, 1))()
+    ctx._check(_lib.pg_knn_descent(ctx.handle, _ptr(D), n, d, METRIC[metric], K, iters,
+                                   _ptr(init), int(seed), _ptr(ids), _ptr(dist), upd),
+               "pg_knn_descent")
+    return ids, dist, [int(upd[i]) for i in range(iters)]
 
 
 def knn_query(ctx: Context, D: torch.Tensor, Q: torch.Tensor, k: int, metric="l2",

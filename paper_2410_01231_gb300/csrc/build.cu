@@ -38,6 +38,10 @@ pg_status pg_connect_replace_internal(pg_ctx *ctx, const float *D, int64_t n, in
                                       pg_metric metric, int32_t *nbr, int32_t *deg, int32_t R,
                                       int64_t ep, const DataFacts &facts, const int32_t *knn,
                                       int32_t K, int64_t *host_added, int64_t *host_replaced);
+pg_status pg_knn_descent_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
+                                  pg_metric metric, int32_t K, int32_t iters,
+                                  const int32_t *init, uint64_t seed, int32_t *ids, float *dist,
+                                  int64_t *host_updates);
 pg_status pg_quality_estimate(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
                               const int32_t *cand, int32_t L, int32_t k, double eps, uint64_t seed,
                               double *est, int64_t *ns_out);
@@ -168,6 +172,8 @@ pg_status check_params(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
         return pg_fail(ctx, PG_ERR_INVALID_ARG, "bad metric");
     if (!pg_build_precision(p->precision))
         return pg_fail(ctx, PG_ERR_INVALID_ARG, "builds take FP32 or BF16 screening");
+    if (p->knn_descent_iters > 64 || (p->knn_descent_iters >= 0 && p->K > 64))
+        return pg_fail(ctx, PG_ERR_INVALID_ARG, "kNN descent: need iterations <= 64 and K <= 64");
     if (!(p->quality_target >= 0.0 && p->quality_target <= 1.0) ||
         (p->quality_target > 0.0 && !(p->quality_eps > 0.0)) || p->quality_k < 0 ||
         p->quality_k > 255)
@@ -206,7 +212,11 @@ pg_status iter_nsg(pg_ctx *ctx, const float *X, int64_t m, int32_t d, const pg_b
     PG_TRY(deg1.alloc(ctx, (size_t)m));
     PG_TRY(uids.alloc(ctx, (size_t)(2 * m * R)));
     clk.start(PH_KNN);
-    PG_TRY(pg_knn_internal(ctx, X, m, d, p->metric, K, p->precision, knn_i.p, knn_s.p));
+    if (p->knn_descent_iters >= 0)  // approximate initial KNNG (Section 3.1, Exp. 12)
+        PG_TRY(pg_knn_descent_internal(ctx, X, m, d, p->metric, K, p->knn_descent_iters, nullptr,
+                                       p->seed, knn_i.p, knn_s.p, nullptr));
+    else
+        PG_TRY(pg_knn_internal(ctx, X, m, d, p->metric, K, p->precision, knn_i.p, knn_s.p));
     knn_s.release();
     const unsigned g1 = (unsigned)((m + 256) / 256);
     k_fill_off<<<g1, 256, 0, ctx->stream>>>(off.p, m, K);

@@ -44,6 +44,7 @@ extern "C" void pg_default_params(pg_build_params *p) {
     p->quality_eps = 0.6;
     p->quality_k = 0;
     p->connect_replace = 1;
+    p->knn_descent_iters = -1;
 }
 
 extern "C" pg_status pg_ctx_create(void *cuda_stream, size_t hbm_budget_bytes, pg_ctx **out) {
