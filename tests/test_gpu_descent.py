@@ -82,14 +82,21 @@ def test_descent_on_real_rows_follows_the_oracle(ctx, pg):
 
 
 def test_build_from_the_descent_graph_keeps_search_quality(ctx, pg):
+    """Exp. 12: the framework's iterations make up for an approximate initial
+    KNNG; the build from a few 2-hop iterations reaches the search quality
+    of the build from the exact kNN graph."""
     D, Q, w = synthetic.workload(1)
     Dd = dev(D)
-    prm = dict(K=w["K"], L=w["L"], R=w["R"], M=16, iters=2, route_layers=0)
-    idx = pg.Index.build_rng(ctx, Dd, knn_descent_iters=3, **prm)
-    ids, _ = idx.search(dev(Q), 10, 64)
+    prm = dict(K=w["K"], L=w["L"], R=w["R"], M=16, iters=2)
     gt = oracle.knn(D, 10, Q=Q)
-    assert oracle.recall_at_k(ids.cpu().numpy(), Q, D, 10, gt=gt) >= 0.95
-    _, nb, dg = idx.layer(0)
-    assert (dg.cpu().numpy() <= w["R"]).all()
+    rec = {}
+    for it in (-1, 4):
+        idx = pg.Index.build_rng(ctx, Dd, knn_descent_iters=it, **prm)
+        ids, _ = idx.search(dev(Q), 10, 64)
+        rec[it] = oracle.recall_at_k(ids.cpu().numpy(), Q, D, 10, gt=gt)
+        _, nb, dg = idx.layer(0)
+        assert (dg.cpu().numpy() <= w["R"]).all()
+        idx.close()
+    assert rec[4] >= rec[-1] - 0.02 and rec[-1] >= 0.95, rec
     with pytest.raises(pg.PGError):
         pg.Index.build_rng(ctx, Dd, knn_descent_iters=3, **dict(prm, K=80))
