@@ -190,6 +190,20 @@ pg_status pg_ctx_kernel_work(pg_ctx *ctx, const char *name, double *work);
  * tiles computed). */
 pg_status pg_ctx_counter(pg_ctx *ctx, const char *name, int64_t *value);
 
+/* Launch-configuration autotuning (off by default; not in the paper).  The
+ * persistent pruning and beam-search kernels give the same results under any
+ * grid; with tuning on, the first pruning or search call for a key (kernel,
+ * width d, degree / pool width, row form) on a device times each candidate
+ * configuration on that call's own input (CUDA events; CTAs per SM, and the
+ * search's visited-table size) and keeps the fastest in a process-wide
+ * table that later calls use.  Search calls of fewer than 4096 queries are
+ * not tuned. */
+pg_status pg_ctx_set_autotune(pg_ctx *ctx, int enable);
+/* The tuning table as text, one line per key ("label -> choice (config:ms
+ * ...)"), written to buf (host, cap bytes, NUL-terminated, may be NULL);
+ * returns the bytes the whole text needs. */
+int64_t pg_autotune_report(char *buf, int64_t cap);
+
 /* Tie accounting of the pruning kernels (off by default): when on, every
  * decision of the occlusion test (Section 4.1: s(u,w) < s(u,v),
  * s(v,w) < s(u,v) and the angle clause) whose relative margin is below

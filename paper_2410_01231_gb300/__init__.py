@@ -94,6 +94,8 @@ _sig("pg_index_phase_seconds", C.c_int, [P, P])
 _sig("pg_index_export_layer", C.c_int, [P, P, i32, P, P, P])
 _sig("pg_ctx_set_timing", C.c_int, [P, C.c_int])
 _sig("pg_ctx_set_tie_count", C.c_int, [P, C.c_int])
+_sig("pg_ctx_set_autotune", C.c_int, [P, C.c_int])
+_sig("pg_autotune_report", i64, [P, i64])
 _sig("pg_ctx_kernel_time", C.c_int, [P, C.c_char_p, P, P])
 _sig("pg_ctx_counter", C.c_int, [P, C.c_char_p, P])
 _sig("pg_ctx_kernel_work", C.c_int, [P, C.c_char_p, P])
@@ -126,7 +128,8 @@ EXPORTS = ["pg_default_params", "pg_ctx_create", "pg_ctx_destroy", "pg_last_erro
            "pg_kcna_recall", "pg_connect_replace", "pg_knn_descent", "pg_quality_sample_size", "pg_quality_sample", "pg_index_quality",
            "pg_build_nswg", "pg_search", "pg_search_host", "pg_index_destroy", "pg_index_info",
            "pg_index_layer", "pg_index_phase_seconds", "pg_index_export_layer",
-           "pg_ctx_set_timing", "pg_ctx_set_tie_count", "pg_ctx_kernel_time", "pg_ctx_counter",
+           "pg_ctx_set_timing", "pg_ctx_set_tie_count", "pg_ctx_set_autotune",
+           "pg_autotune_report", "pg_ctx_kernel_time", "pg_ctx_counter",
            "pg_ctx_kernel_work", "pg_prune_noalloc", "pg_index_reserve", "pg_index_insert",
            "pg_serve_start", "pg_serve_submit_query", "pg_serve_submit_insert", "pg_serve_wait",
            "pg_serve_stats", "pg_serve_stop", "pg_serve_set_queue_limit",
@@ -188,6 +191,11 @@ class Context:
         self._check(_lib.pg_ctx_set_tie_count(self._h, 1 if enable else 0),
                     "pg_ctx_set_tie_count")
 
+    def set_autotune(self, enable: bool = True):
+        """Launch configurations of the prune / search kernels chosen by timing
+        (pg_ctx_set_autotune)."""
+        self._check(_lib.pg_ctx_set_autotune(self._h, 1 if enable else 0), "pg_ctx_set_autotune")
+
     def kernel_time(self, name: str):
         """(total device ms, launches) of a timed kernel since the last reset."""
         ms, cnt = C.c_double(), C.c_int64()
@@ -237,6 +245,14 @@ class Context:
     @property
     def handle(self):
         return self._h
+
+
+def autotune_report() -> str:
+    """The autotuner's table (pg_autotune_report)."""
+    need = int(_lib.pg_autotune_report(None, 0))
+    buf = C.create_string_buffer(max(need, 1))
+    _lib.pg_autotune_report(buf, need)
+    return buf.value.decode()
 
 
 def default_params(**kw) -> BuildParams:

@@ -7,6 +7,7 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <functional>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -31,6 +32,7 @@ struct pg_ctx {
     int64_t connect_why_full = 0;     // batches cut short by a candidate that filled up
     int64_t connect_free = 0;         // nodes with a free slot when connectivity steps began
     int count_ties = 0;               // pruning counts near-tie decisions (pg_ctx_set_tie_count)
+    int autotune = 0;                 // launch configurations chosen by timing (tune.cu)
     int last_derr = 0;                // device error code of the last failed synchronisation
     int64_t last_err_info = 0;        // ... and its info word (e.g. the refused node)
     // optional CUDA-event timing of named kernels
@@ -202,6 +204,20 @@ struct Scratch {
     }
     ~Scratch() { release(); }
 };
+
+// Launch-configuration autotuner (tune.cu): a key names a kernel and the
+// shape it runs on; configs are kernel-specific codes.
+struct TuneKey {
+    int device, kernel, d, p, form;
+};
+enum { TUNE_PRUNE = 1, TUNE_SEARCH = 2 };
+bool pg_tune_lookup(const TuneKey &k, int *config);
+void pg_tune_store(const TuneKey &k, int config, const std::vector<std::pair<int, float>> &tried,
+                   const char *label);
+// Time run(c) for every c (CUDA events on ctx's stream), *best = the fastest.
+pg_status pg_tune_time(pg_ctx *ctx, const std::vector<int> &configs,
+                       const std::function<pg_status(int)> &run, int *best,
+                       std::vector<std::pair<int, float>> *tried);
 
 // Dimension of the points of an index.
 int pg_index_dim(const pg_index *index);

@@ -688,8 +688,39 @@ pg_status pg_prune_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d, p
     PG_TRY_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, PW * 32,
                                                                    smem));
     if (blocks_per_sm < 1) blocks_per_sm = 1;
+    // CTAs per SM: the occupancy limit, or the autotuner's choice
+    int bps = blocks_per_sm;
+    if (ctx->autotune && blocks_per_sm > 1) {
+        const TuneKey key{ctx->device, TUNE_PRUNE, d, R,
+                          (reg ? 2 : (D8 ? 1 : 0)) + 4 * (prev_nbr != nullptr) + 8 * P.metric};
+        int cfg = 0;
+        if (pg_tune_lookup(key, &cfg)) {
+            bps = cfg;
+        } else {
+            Scratch<unsigned long long> junk;
+            PG_TRY(junk.alloc(ctx, PG_CNT_SLOTS));
+            std::vector<int> cands;
+            for (int c = 1; c <= blocks_per_sm; ++c) cands.push_back(c);
+            auto run = [&](int c) -> pg_status {
+                PruneParams Q = P;
+                Q.counters = junk.p;
+                PG_TRY_CUDA(ctx, cudaMemsetAsync(ints.p, 0, 4 * sizeof(int), ctx->stream));
+                kern<<<ctx->num_sms * c, PW * 32, smem, ctx->stream>>>(Q);
+                PG_LAUNCHED(ctx);
+                return PG_OK;
+            };
+            std::vector<std::pair<int, float>> tried;
+            PG_TRY(pg_tune_time(ctx, cands, run, &bps, &tried));
+            char label[128];
+            snprintf(label, sizeof label, "k_prune d=%d R=%d rows=%s%s CTAs/SM", d, R,
+                     reg ? "bytes-in-registers" : (D8 ? "bytes" : "fp32"),
+                     prev_nbr ? " k2p" : "");
+            pg_tune_store(key, bps, tried, label);
+            PG_TRY_CUDA(ctx, cudaMemsetAsync(ints.p, 0, 4 * sizeof(int), ctx->stream));
+        }
+    }
     pg_timer_begin(ctx, TM_PRUNE);
-    kern<<<ctx->num_sms * blocks_per_sm, PW * 32, smem, ctx->stream>>>(P);
+    kern<<<ctx->num_sms * bps, PW * 32, smem, ctx->stream>>>(P);
     PG_LAUNCHED(ctx);
     pg_timer_end(ctx, TM_PRUNE);
     P.cap = CMAX_LONG;

@@ -648,8 +648,7 @@ pg_status pg_search_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d, 
     PG_TRY(qc.alloc(ctx, 1));
     PG_TRY_CUDA(ctx, cudaMemsetAsync(qc.p, 0, sizeof(int), ctx->stream));
     P.qcounter = qc.p;
-    size_t smem = search_warp_smem(L, hb, d, P.cert) * SW;
-    if (smem > 227 * 1024)
+    if (search_warp_smem(L, hb, d, P.cert) * SW > 227 * 1024)
         return pg_fail(ctx, PG_ERR_CAPACITY, "search: pool/table do not fit shared memory");
     // the shared-memory attribute is per kernel, not per launch: searches
     // of other contexts on other threads (the serving workers) may set a
@@ -657,18 +656,56 @@ pg_status pg_search_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d, 
     std::lock_guard<std::mutex> lk(search_launch_mu);
     void (*kern)(SearchParams) =
         P.F8 ? k_search<true, false> : (P.cert ? k_search<false, true> : k_search<false, false>);
-    PG_TRY_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem));
-    int bps = 0;
-    PG_TRY_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, SW * 32, smem));
-    if (bps < 1) bps = 1;
-    int64_t want = (nq + SW - 1) / SW;
-    int64_t grid = std::min<int64_t>((int64_t)ctx->num_sms * bps, want);
-    pg_timer_begin(ctx, TM_SEARCH);
-    kern<<<(unsigned)grid, SW * 32, smem, ctx->stream>>>(P);
-    PG_LAUNCHED(ctx);
-    pg_timer_end(ctx, TM_SEARCH);
-    return PG_OK;
+    // a configuration: visited-table bits * 16 + CTAs per SM (0: the
+    // occupancy limit)
+    auto launch = [&](int cfg, const SearchParams &Q, bool timed) -> pg_status {
+        const int hbits = cfg >> 4;
+        SearchParams R2 = Q;
+        R2.hbits = hbits;
+        const size_t smem = search_warp_smem(L, hbits, d, R2.cert) * SW;
+        PG_TRY_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)smem));
+        int bps = 0;
+        PG_TRY_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, SW * 32, smem));
+        if (bps < 1) bps = 1;
+        if ((cfg & 15) > 0) bps = std::min(bps, cfg & 15);
+        const int64_t want = (nq + SW - 1) / SW;
+        const int64_t grid = std::min<int64_t>((int64_t)ctx->num_sms * bps, want);
+        PG_TRY_CUDA(ctx, cudaMemsetAsync(qc.p, 0, sizeof(int), ctx->stream));
+        if (timed) pg_timer_begin(ctx, TM_SEARCH);
+        kern<<<(unsigned)grid, SW * 32, smem, ctx->stream>>>(R2);
+        PG_LAUNCHED(ctx);
+        if (timed) pg_timer_end(ctx, TM_SEARCH);
+        return PG_OK;
+    };
+    int cfg = hb << 4;
+    if (ctx->autotune && nq >= 4096) {
+        const TuneKey key{ctx->device, TUNE_SEARCH, d, L * 256 + R,
+                          (P.D8 ? 1 : 0) | (P.F8 ? 2 : 0) | (P.cert ? 4 : 0) | (self ? 8 : 0) |
+                              P.metric * 16};
+        if (!pg_tune_lookup(key, &cfg)) {
+            Scratch<unsigned long long> junk;
+            PG_TRY(junk.alloc(ctx, PG_CNT_SLOTS));
+            SearchParams Q = P;
+            Q.counters = junk.p;
+            std::vector<int> cands;
+            for (int hbits = std::max(9, hb - 1); hbits <= std::min(13, hb + 1); ++hbits) {
+                if (search_warp_smem(L, hbits, d, P.cert) * SW > 227 * 1024) continue;
+                cands.push_back(hbits << 4);
+                cands.push_back((hbits << 4) | 4);
+            }
+            std::vector<std::pair<int, float>> tried;
+            PG_TRY(pg_tune_time(ctx, cands, [&](int c) { return launch(c, Q, false); }, &cfg,
+                                &tried));
+            char label[160];
+            snprintf(label, sizeof label,
+                     "k_search d=%d L=%d R=%d rows=%s%s%s (table bits*16 + CTAs/SM cap)", d, L, R,
+                     P.D8 ? "bytes" : (P.F8 ? "fp8" : "fp32"), P.cert ? " certified" : "",
+                     self ? " self" : "");
+            pg_tune_store(key, cfg, tried, label);
+        }
+    }
+    return launch(cfg, P, true);
 }
 
 // One warp per row: scale = max|x| / 448 (1 for a zero row), codes of
