@@ -497,7 +497,7 @@ def run_ours(args):
         del lists
         p3 = dict(K=w3["K"], L=w3["L"], R=w3["R"], M=16, alpha_deg=66.0, alpha_final_deg=60.0,
                   iters=2, route_layers=1, seed=0)
-        builds, graphs = {}, {}
+        builds, graphs, phases3 = {}, {}, {}
         gt_i, gt_d = pg.knn_query(ctx, X3d, Q3d, 10)
         kth3 = gt_d[:, 9].clone()
         for prec in ("fp32", "bf16"):
@@ -508,6 +508,7 @@ def run_ours(args):
             e1.record(stream)
             barrier()
             builds[prec] = e0.elapsed_time(e1)
+            phases3[prec] = idx3.phase_seconds()
             _, nb3, dg3 = idx3.layer(0)
             graphs[prec] = (nb3.clone(), dg3.clone())
             if prec == "bf16":
@@ -531,6 +532,7 @@ def run_ours(args):
                   "screen_tiles_tflops": tiles_flops / (tiles_ms / 1e3) / 1e12 if tiles_ms else None,
                   "screen_tiles_note": "executed contraction: 2 n^2 x 3d (hi.hi + hi.lo + lo.hi)",
                   "build_fp32_ms": builds["fp32"], "build_bf16_screen_ms": builds["bf16"],
+                  "build_phase_s": phases3,
                   "edge_agreement_rows": same_rows / ns, "graphs_identical": same_rows == ns,
                   "queries": curve3}
         del X3d, Q3d, graphs

@@ -431,12 +431,16 @@ ErrModel pg_err_model(pg_metric metric, int d, const DataFacts &f, bool gemm_for
             // callers of the norm form use a per-pair bound instead.
             m.rel = (float)((d + 8) * u * 1.01 + 1e-12);
         } else {
-            m.rel = (float)((d + 4) * u * 1.01 + 1e-12);
+            // the gathers sum in teams of eight lanes (each lane a strided
+            // sequence of at most ceil(d / 8) + 3 terms, then three butterfly
+            // additions) or in 32 strided lanes and five additions: at most
+            // ceil(d / 8) + 8 roundings on any term's path
+            m.rel = (float)((double)((d + 7) / 8 + 8) * u * 1.01 + 1e-12);
         }
     } else {
         m.metric = 1;
         double nm = f.max_norm2 > 0.f ? (double)f.max_norm2 : 1.0;
-        m.abs_ = (float)((2.0 * (d + 2) * u * nm + u * (2.0 + 2.0 * nm)) * 1.01 + 1e-12);
+        m.abs_ = (float)((2.0 * ((d + 7) / 8 + 8) * u * nm + u * (2.0 + 2.0 * nm)) * 1.01 + 1e-12);
     }
     return m;
 }

@@ -261,66 +261,83 @@ k_knn_fp32(const float *__restrict__ Q, int64_t nq, const float *__restrict__ X,
 
 // Re-order near-tie runs of each sorted row by FP64 distance (one warp per
 // row).  Rows hold Kx entries; ties are judged with the per-pair error
-// bound of the norm form.  The first K entries are written to the output.
-// A run that reaches the last stored entry cannot be closed: counted.
-__global__ void k_knn_fix(const float *__restrict__ Q, const float *__restrict__ X, int64_t nq,
-                          int d, int metric, const float *__restrict__ qnorm,
-                          const float *__restrict__ xnorm, float rel, float abs_err, int Kx, int K,
-                          int32_t *__restrict__ ids, float *__restrict__ ds,
-                          int32_t *__restrict__ out_i, float *__restrict__ out_s,
-                          unsigned long long *counters) {
-    int64_t q = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+// bound of the norm form.  Lane 0 finds the runs that reach the first K
+// entries, every lane computes FP64 distances of their members, lane 0
+// re-orders them.  A run that reaches the last stored entry cannot be
+// closed inside the row: the row goes to fail[] (recomputed with more
+// entries) unless fail is null (then it is only counted).  The first K
+// entries are written to the output.
+__global__ void __launch_bounds__(256) k_knn_fix(
+    const float *__restrict__ Q, const float *__restrict__ X, int64_t nq, int d, int metric,
+    const float *__restrict__ qnorm, const float *__restrict__ xnorm, float rel, float abs_err,
+    int Kx, int K, int32_t *__restrict__ ids, float *__restrict__ ds, int32_t *__restrict__ out_i,
+    float *__restrict__ out_s, unsigned long long *counters, int *fail, int *nfail) {
+    __shared__ double c64[8][256];
+    __shared__ int cut[8];
+    const int w = threadIdx.x >> 5;
+    int64_t q = (int64_t)blockIdx.x * (blockDim.x / 32) + w;
     int lane = threadIdx.x & 31;
     if (q >= nq) return;
     int32_t *ri = ids + q * Kx;
     float *rs = ds + q * Kx;
     const float *qrow = Q + q * d;
+    const double nan64 = __longlong_as_double(0x7ff8000000000000ll);
     auto err = [&](int j) -> float {
         int id = ri[j];
         if (id < 0) return 0.f;
         if (metric == 0) return rel * (qnorm[q] + xnorm[id] + fabsf(qnorm[q] + xnorm[id] - rs[j]));
         return abs_err;
     };
-    // lane 0 walks the row; runs are rare
+    for (int j = lane; j < Kx; j += 32) c64[w][j] = nan64;
+    __syncwarp();
+    // lane 0 marks the members of runs that start before K (end: cut)
     if (lane == 0) {
-        int j = 0;
-        unsigned long long rechecked = 0, unresolved = 0;
-        while (j < Kx && ri[j] >= 0) {
+        int j = 0, end = 0;
+        while (j < Kx && ri[j] >= 0 && j < K) {
             int e = j;
             while (e + 1 < Kx && ri[e + 1] >= 0 && rs[e + 1] - rs[e] <= err(e) + err(e + 1)) ++e;
-            if (e > j && j < K) {
-                // FP64 distances and insertion sort of the run
-                double tmp_d[64];
-                int tmp_i[64];
-                int m = e - j + 1;
-                if (m > 64) m = 64;
-                for (int t = 0; t < m; ++t) {
-                    tmp_i[t] = ri[j + t];
-                    tmp_d[t] = dist64_rows(qrow, X + (int64_t)tmp_i[t] * d, d, metric);
-                }
-                for (int a = 1; a < m; ++a) {
-                    double kd = tmp_d[a];
-                    int ki = tmp_i[a];
-                    int b = a - 1;
-                    while (b >= 0 && (tmp_d[b] > kd || (tmp_d[b] == kd && tmp_i[b] > ki))) {
-                        tmp_d[b + 1] = tmp_d[b];
-                        tmp_i[b + 1] = tmp_i[b];
-                        --b;
-                    }
-                    tmp_d[b + 1] = kd;
-                    tmp_i[b + 1] = ki;
-                }
-                for (int t = 0; t < m; ++t) {
-                    ri[j + t] = tmp_i[t];
-                    rs[j + t] = (float)tmp_d[t];
-                }
-                rechecked += m;
-                if (e == Kx - 1 && K < Kx) ++unresolved;
+            if (e > j)
+                for (int t = j; t <= e; ++t) c64[w][t] = 0.0;  // to compute
+            end = e + 1;
+            j = e + 1;
+        }
+        cut[w] = end;
+    }
+    __syncwarp();
+    for (int j = lane; j < cut[w]; j += 32)
+        if (c64[w][j] == 0.0) c64[w][j] = dist64_rows(qrow, X + (int64_t)ri[j] * d, d, metric);
+    __syncwarp();
+    if (lane == 0) {
+        unsigned long long rechecked = 0, unresolved = 0;
+        int j = 0;
+        while (j < cut[w]) {
+            if (c64[w][j] != c64[w][j]) {
+                ++j;
+                continue;
             }
+            int e = j;
+            while (e + 1 < cut[w] && c64[w][e + 1] == c64[w][e + 1]) ++e;
+            for (int a = j + 1; a <= e; ++a) {  // insertion sort by (FP64, id)
+                const double kd = c64[w][a];
+                const int ki = ri[a];
+                int b = a - 1;
+                while (b >= j && (c64[w][b] > kd || (c64[w][b] == kd && ri[b] > ki))) {
+                    c64[w][b + 1] = c64[w][b];
+                    ri[b + 1] = ri[b];
+                    --b;
+                }
+                c64[w][b + 1] = kd;
+                ri[b + 1] = ki;
+            }
+            rechecked += (unsigned long long)(e - j + 1);
+            if (e == Kx - 1 && K < Kx) ++unresolved;
             j = e + 1;
         }
         if (rechecked) atomicAdd(counters + CNT_KNN_RECHECK, rechecked);
-        if (unresolved) atomicAdd(counters + CNT_KNN_UNRESOLVED, unresolved);
+        if (unresolved) {
+            if (fail) fail[atomicAdd(nfail, 1)] = (int)q;
+            else atomicAdd(counters + CNT_KNN_UNRESOLVED, unresolved);
+        }
     }
     __syncwarp();
     // the norm form loses relative accuracy to cancellation: report every
@@ -436,6 +453,7 @@ __global__ void __launch_bounds__(256) k_knn_certify(
     unsigned long long *counters) {
     __shared__ float ks[8][128];
     __shared__ int kid[8][128];
+    __shared__ double c64[8][128];
     __shared__ double k64[8];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, team = lane >> 3, li = lane & 7;
     const int64_t r = (int64_t)blockIdx.x * 8 + w;
@@ -469,43 +487,56 @@ __global__ void __launch_bounds__(256) k_knn_certify(
         for (int c = lane; c < d; c += 32) na = fmaf(xr[c], xr[c], na);
         for (int o = 16; o; o >>= 1) na += __shfl_xor_sync(0xffffffffu, na, o);
     }
-    int ok = 1;
+    auto err = [&](int j) -> float { return metric == 0 ? rel * ks[w][j] : abs_err; };
+    const double nan64 = __longlong_as_double(0x7ff8000000000000ll);
+    for (int j = lane; j < 128; j += 32) c64[w][j] = nan64;
+    __syncwarp();
+    // lane 0 marks the members of the near-tie runs that reach the first K
     if (lane == 0) {
-        auto err = [&](int j) -> float { return metric == 0 ? rel * ks[w][j] : abs_err; };
-        unsigned long long rechecked = 0;
-        double kth = -1.0;  // exact K-th distance when resolved in FP64
-        int j = 0;
+        int j = 0, ok = 1, end = 0;
         while (ok && j < m && j < K) {
             int e = j;
             while (e + 1 < m && ks[w][e + 1] - ks[w][e] <= err(e) + err(e + 1)) ++e;
             if (e > j) {
-                if ((e == m - 1 && m == Ks) || e - j + 1 > 64) {
-                    ok = 0;  // the run may continue outside the shortlist
-                    break;
-                }
-                double td[64];
-                int ti[64];
-                const int cnt = e - j + 1;
-                for (int t = 0; t < cnt; ++t) {
-                    ti[t] = kid[w][j + t];
-                    td[t] = dist64_rows(xr, X + (int64_t)ti[t] * d, d, metric);
-                }
-                for (int a = 1; a < cnt; ++a) {
-                    const double kd = td[a];
-                    const int ki = ti[a];
-                    int b = a - 1;
-                    while (b >= 0 && (td[b] > kd || (td[b] == kd && ti[b] > ki))) {
-                        td[b + 1] = td[b];
-                        ti[b + 1] = ti[b];
-                        --b;
-                    }
-                    td[b + 1] = kd;
-                    ti[b + 1] = ki;
-                }
-                for (int t = 0; t < cnt; ++t) kid[w][j + t] = ti[t];
-                if (j <= K - 1 && e >= K - 1) kth = td[K - 1 - j];
-                rechecked += cnt;
+                if (e == m - 1 && m == Ks) ok = 0;  // the run may continue outside the shortlist
+                for (int t = j; t <= e; ++t) c64[w][t] = 0.0;  // to compute
             }
+            end = e + 1;
+            j = e + 1;
+        }
+        k64[w] = ok ? (double)end : -1.0;
+    }
+    __syncwarp();
+    const int cut = k64[w] < 0.0 ? 0 : (int)k64[w];
+    for (int j = lane; j < cut; j += 32)
+        if (c64[w][j] == 0.0) c64[w][j] = dist64_rows(xr, X + (int64_t)kid[w][j] * d, d, metric);
+    __syncwarp();
+    if (lane == 0) {
+        int ok = k64[w] >= 0.0;
+        unsigned long long rechecked = 0;
+        double kth = -1.0;  // exact K-th distance when resolved in FP64
+        int j = 0;
+        while (ok && j < cut) {
+            if (c64[w][j] != c64[w][j]) {
+                ++j;
+                continue;
+            }
+            int e = j;
+            while (e + 1 < cut && c64[w][e + 1] == c64[w][e + 1]) ++e;
+            for (int a = j + 1; a <= e; ++a) {  // insertion sort by (FP64, id)
+                const double kd = c64[w][a];
+                const int ki = kid[w][a];
+                int b = a - 1;
+                while (b >= j && (c64[w][b] > kd || (c64[w][b] == kd && kid[w][b] > ki))) {
+                    c64[w][b + 1] = c64[w][b];
+                    kid[w][b + 1] = kid[w][b];
+                    --b;
+                }
+                c64[w][b + 1] = kd;
+                kid[w][b + 1] = ki;
+            }
+            if (j <= K - 1 && e >= K - 1) kth = c64[w][K - 1];
+            rechecked += (unsigned long long)(e - j + 1);
             j = e + 1;
         }
         if (ok) {
@@ -540,16 +571,18 @@ __global__ void __launch_bounds__(256) k_knn_certify(
 // written without the row itself.
 __global__ void k_knn_fallback_scatter(const int *__restrict__ fail, int nf,
                                        const int32_t *__restrict__ gi, const float *__restrict__ gs,
-                                       int K, int32_t *__restrict__ out_i, float *__restrict__ out_s) {
+                                       int K, int32_t *__restrict__ out_i, float *__restrict__ out_s,
+                                       int drop_self = 1) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nf) return;
     const int64_t u = fail[t];
+    const int kin = K + drop_self;  // entries of an input row
     int w = 0;
-    for (int j = 0; j <= K && w < K; ++j) {
-        const int id = gi[(int64_t)t * (K + 1) + j];
-        if (id == (int)u) continue;
+    for (int j = 0; j < kin && w < K; ++j) {
+        const int id = gi[(int64_t)t * kin + j];
+        if (drop_self && id == (int)u) continue;
         out_i[u * K + w] = id;
-        out_s[u * K + w] = gs[(int64_t)t * (K + 1) + j];
+        out_s[u * K + w] = gs[(int64_t)t * kin + j];
         ++w;
     }
     for (; w < K; ++w) {
@@ -583,7 +616,7 @@ namespace {
 
 pg_status knn_core(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
                    const float *Q, int64_t nq, int self, int32_t K, pg_precision precision,
-                   int32_t *ids, float *dist);
+                   int32_t *ids, float *dist, int kx_extra = 8);
 
 pg_status knn_screened(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
                        int32_t K, int Ks, int dp3, const DataFacts &facts, int32_t *ids,
@@ -647,7 +680,7 @@ pg_status knn_screened(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_met
 
 pg_status knn_core(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
                    const float *Q, int64_t nq, int self, int32_t K, pg_precision precision,
-                   int32_t *ids, float *dist) {
+                   int32_t *ids, float *dist, int kx_extra) {
     if (!D || !ids || !dist || (!Q && !self)) return pg_fail(ctx, PG_ERR_INVALID_ARG, "null pointer");
     if (n < 1 || nq < 0 || d < 4 || d % 4 || d > 8192)
         return pg_fail(ctx, PG_ERR_INVALID_ARG, "knn: need n >= 1, d % 4 == 0, 4 <= d <= 8192");
@@ -689,7 +722,7 @@ pg_status knn_core(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric 
         Ks >= K + 8 && n > Ks && pg_knn_tc_supported(dp3, Ks))
         return knn_screened(ctx, D, n, d, metric, K, Ks, dp3, facts, ids, dist);
     // rows hold Kx entries when ties must be resolved in FP64 afterwards
-    int Kx = facts.exact ? K : (int)std::min<int64_t>((int64_t)K + 8, KMAX);
+    int Kx = facts.exact ? K : (int)std::min<int64_t>((int64_t)K + kx_extra, KMAX);
     Scratch<int32_t> wi;
     Scratch<float> ws;
     int32_t *ti = ids;
@@ -712,10 +745,42 @@ pg_status knn_core(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric 
     pg_timer_end(ctx, TM_KNN, 2.0 * (double)nq * (double)n * (double)d);
     if (Kx != K) {
         ErrModel em = pg_err_model(metric, d, facts, true);
+        // rows whose near-tie run reaches the last stored entry are redone
+        // with more entries (while the tiles can hold more)
+        const bool redo = Kx < KMAX && K + (self ? 1 : 0) <= KMAX;
+        Scratch<int> fail;
+        if (redo) {
+            PG_TRY(fail.alloc(ctx, (size_t)nq + 1));
+            PG_TRY_CUDA(ctx, cudaMemsetAsync(fail.p + nq, 0, sizeof(int), ctx->stream));
+        }
         k_knn_fix<<<(unsigned)((nq + 7) / 8), 256, 0, ctx->stream>>>(
             Qp, D, nq, d, metric == PG_METRIC_L2SQ ? 0 : 1, qnp, xn.p, em.rel, em.abs_, Kx, K, ti,
-            ts, ids, dist, ctx->d_counters);
+            ts, ids, dist, ctx->d_counters, redo ? fail.p : nullptr, redo ? fail.p + nq : nullptr);
         PG_LAUNCHED(ctx);
+        if (redo) {
+            int nf = 0;
+            PG_TRY_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned, fail.p + nq, sizeof(int),
+                                             cudaMemcpyDeviceToHost, ctx->stream));
+            PG_TRY(pg_sync_check(ctx, "knn fix"));
+            memcpy(&nf, ctx->h_pinned, sizeof(int));
+            if (nf > 0) {
+                const int Kr = K + (self ? 1 : 0);
+                Scratch<float> Qf, gs;
+                Scratch<int32_t> gi;
+                PG_TRY(Qf.alloc(ctx, (size_t)nf * d));
+                PG_TRY(gi.alloc(ctx, (size_t)nf * Kr));
+                PG_TRY(gs.alloc(ctx, (size_t)nf * Kr));
+                const int64_t tot = (int64_t)nf * (d / 4);
+                k_gather_fail_rows<<<(unsigned)((tot + 255) / 256), 256, 0, ctx->stream>>>(
+                    Qp, d, fail.p, nf, Qf.p);
+                PG_LAUNCHED(ctx);
+                PG_TRY(knn_core(ctx, D, n, d, metric, Qf.p, nf, 0, Kr, PG_PREC_FP32, gi.p, gs.p,
+                                std::min(KMAX, 8 * kx_extra)));
+                k_knn_fallback_scatter<<<(unsigned)((nf + 255) / 256), 256, 0, ctx->stream>>>(
+                    fail.p, nf, gi.p, gs.p, K, ids, dist, self ? 1 : 0);
+                PG_LAUNCHED(ctx);
+            }
+        }
     }
     return PG_OK;
 }

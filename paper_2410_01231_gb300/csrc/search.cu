@@ -303,7 +303,8 @@ __device__ void search_one(const SearchParams &P, int64_t qi, unsigned char *ws,
         for (int c = lane; c < d; c += 32) qq = fmaf(q[c], q[c], qq);
         for (int o = 16; o; o >>= 1) qq += __shfl_xor_sync(0xffffffffu, qq, o);
         const double u = 5.9604644775390625e-08, nm = fmax((double)P.nm, (double)qq * 1.001);
-        X.abs2 = (float)(2.0 * ((2.0 * (d + 2) * u * nm + u * (2.0 + 2.0 * nm)) * 1.01 + 1e-12));
+        X.abs2 = (float)(2.0 * ((2.0 * ((d + 7) / 8 + 8) * u * nm + u * (2.0 + 2.0 * nm)) * 1.01 +
+                                1e-12));
     }
     int start = P.self ? (int)qi : P.starts[qi];
     bool bad = start < 0 || start >= P.n;

@@ -1,10 +1,11 @@
 """The FP32 rounding bounds that decide when a kernel re-decides a
-comparison in FP64 (CPU): the squared-L2 difference form is within
-(d + 4) 2^-24 relative of the exact value, and the unit-row chord
-2 - 2<x, y> within 2 (d + 2) 2^-24 |x||y| + 2^-24 (2 + 2 |x||y|) absolute,
-for the kernels' summation orders (sequential, eight strided lanes combined
-by a butterfly, pairwise) with fused multiply-adds, on random and
-cancellation-heavy rows.  Exact values come from Python fractions."""
+comparison in FP64 (CPU): with c = ceil(d / 8) + 8, the squared-L2
+difference form is within c 2^-24 relative of the exact value, and the
+unit-row chord 2 - 2<x, y> within 2 c 2^-24 |x||y| + 2^-24 (2 + 2 |x||y|)
+absolute, for the kernels' summation orders (eight strided lanes of float4
+chunks combined by a butterfly, 32 strided lanes and a butterfly,
+pairwise) with fused multiply-adds, on random and cancellation-heavy rows.
+Exact values come from Python fractions."""
 from fractions import Fraction
 
 import numpy as np
@@ -35,15 +36,18 @@ def sum_orders(terms_a, terms_b, form):
         return fma32(terms_a[i], terms_b[i], acc)
 
     out = []
-    acc = f32(0)
-    for i in range(d):  # sequential
-        acc = term_acc(acc, i)
-    out.append(acc)
-    lanes = [f32(0)] * 8  # eight strided lanes, then a butterfly
-    for i in range(d):
-        lanes[i % 8] = term_acc(lanes[i % 8], i)
+    lanes = [f32(0)] * 8  # eight lanes, lane li takes float4 chunks li, li + 8, ...
+    for c in range(d // 4):
+        for e in range(4):
+            lanes[c % 8] = term_acc(lanes[c % 8], 4 * c + e)
     for o in (4, 2, 1):
         lanes = [f32(lanes[j] + lanes[j ^ o]) for j in range(8)]
+    out.append(lanes[0])
+    lanes = [f32(0)] * 32  # 32 strided lanes, then a butterfly
+    for i in range(d):
+        lanes[i % 32] = term_acc(lanes[i % 32], i)
+    for o in (16, 8, 4, 2, 1):
+        lanes = [f32(lanes[j] + lanes[j ^ o]) for j in range(32)]
     out.append(lanes[0])
     parts = [term_acc(f32(0), i) for i in range(d)]  # pairwise
     while len(parts) > 1:
@@ -59,10 +63,10 @@ def exact_sum(a, b, form):
     return sum(Fraction(float(x)) * Fraction(float(y)) for x, y in zip(a, b))
 
 
-@pytest.mark.parametrize("d", [4, 36, 128, 384])
+@pytest.mark.parametrize("d", [4, 36, 128, 384, 960])
 def test_difference_form_bound(d):
     rs = np.random.default_rng(d)
-    bound = (d + 4) * U * 1.01
+    bound = ((d + 7) // 8 + 8) * U * 1.01
     for trial in range(60):
         scale = 10.0 ** rs.uniform(-3, 3)
         x = (rs.normal(0, 1, d) * scale).astype(np.float32)
@@ -84,8 +88,9 @@ def test_chord_form_bound(d):
         y = x + rs.normal(0, 10.0 ** rs.uniform(-4, 0), d)
         y = (y / np.linalg.norm(y)).astype(np.float32)
         nm = float(np.linalg.norm(x.astype(np.float64)) * np.linalg.norm(y.astype(np.float64)))
-        bound = (2 * (d + 2) * U * nm + U * (2 + 2 * nm)) * 1.01
+        bound = (2 * ((d + 7) // 8 + 8) * U * nm + U * (2 + 2 * nm)) * 1.01
         exact = 2 - 2 * exact_sum(x, y, "dot")
         for dot in sum_orders(x, y, "dot"):
             got = max(float(f32(2) - f32(2) * dot), 0.0)
             assert abs(Fraction(got) - exact) <= Fraction(bound), (d, trial)
+
