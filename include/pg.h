@@ -583,9 +583,13 @@ pg_status pg_encode_fp8(pg_ctx *ctx, const float *D, int64_t n, int32_t d, uint8
  * worker is free and the device scratch of the groups in flight plus its
  * own (queries, results and search state: rows x (4 d + 8 k + 12) bytes)
  * fits the HBM budget of ctx (0 = no limit); a group larger than the budget
- * fails with PG_ERR_BUDGET.  An insertion (pg_index_insert on ctx) waits for
- * every group dispatched before it and runs alone, so a query sees exactly
- * the points inserted before it was submitted.  Tickets complete out of
+ * fails with PG_ERR_BUDGET.  A query group searches the version of the
+ * index pinned when it was dispatched.  An insertion (pg_index_insert on a
+ * free worker's context) runs beside the groups in flight: it builds the
+ * next version in copies of the graph arrays, publishes it when it ends,
+ * and nothing submitted after it is dispatched before then, so a query sees
+ * exactly the points inserted before it was submitted.  The arrays of a
+ * version are freed once no group pins it.  Tickets complete out of
  * order.  While the server runs, ctx and index belong to it (the caller
  * issues no other call on them until pg_serve_stop).  Host buffers of a
  * request must stay valid until it completes. */
@@ -652,13 +656,16 @@ pg_status pg_serve_stop(pg_server *server);
  * `count`, left untouched for requests refused with PG_ERR_BUDGET):
  * start_seq / end_seq, the positions of the start and the end of its group
  * in one sequence of events shared by all threads; slot_of, the worker
- * that ran it (-1: insertion); group_of, its group.  host_stats6 as
- * pg_serve_stats (nullable).  Returns once every request has completed. */
+ * that ran it; group_of, its group; version_of (nullable), for a query the
+ * version of the index its group pinned when dispatched and for an
+ * insertion the version it published (versions count the insertions that
+ * have ended, from 0).  host_stats6 as pg_serve_stats (nullable).  Returns
+ * once every request has completed. */
 pg_status pg_serve_simulate(int32_t slots, int32_t max_batch, int64_t budget_bytes,
                             int32_t count, const int32_t *kind, const int32_t *rows,
                             const int32_t *shape, int32_t work_us, int64_t bytes_per_row,
                             int64_t *start_seq, int64_t *end_seq, int32_t *slot_of,
-                            int64_t *group_of, int64_t *host_stats6);
+                            int64_t *group_of, int64_t *version_of, int64_t *host_stats6);
 
 /* ------------------------------------------------------------ self test */
 

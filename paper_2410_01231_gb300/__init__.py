@@ -119,7 +119,7 @@ _sig("pg_index_params", C.c_int, [P, P, P])
 _sig("pg_index_save", C.c_int, [P, P, C.c_char_p])
 _sig("pg_index_load", C.c_int, [P, C.c_char_p, P])
 _sig("pg_index_file_check", C.c_int, [C.c_char_p, P, P, P, C.c_char_p, C.c_size_t])
-_sig("pg_serve_simulate", C.c_int, [i32, i32, i64, i32, P, P, P, i32, i64, P, P, P, P, P])
+_sig("pg_serve_simulate", C.c_int, [i32, i32, i64, i32, P, P, P, i32, i64, P, P, P, P, P, P])
 
 EXPORTS = ["pg_default_params", "pg_ctx_create", "pg_ctx_destroy", "pg_last_error", "pg_ctx_sync",
            "pg_ctx_launches", "pg_build_knn", "pg_knn_query", "pg_prune", "pg_reverse_union",
@@ -689,16 +689,18 @@ def serve_simulate(kind, rows, shape, slots: int = 4, max_batch: int = 1024,
     end = np.full(n, -1, np.int64)
     slot = np.full(n, -2, np.int32)
     group = np.full(n, -1, np.int64)
+    version = np.full(n, -1, np.int64)
     st = (C.c_int64 * len(SERVE_STATS))()
 
     def p(a):
         return a.ctypes.data_as(C.c_void_p)
 
     rc = _lib.pg_serve_simulate(slots, max_batch, budget_bytes, n, p(kind), p(rows), p(shape),
-                                work_us, bytes_per_row, p(start), p(end), p(slot), p(group), st)
+                                work_us, bytes_per_row, p(start), p(end), p(slot), p(group),
+                                p(version), st)
     if rc != 0:
         raise PGError(rc, "pg_serve_simulate")
-    return dict(start=start, end=end, slot=slot, group=group,
+    return dict(start=start, end=end, slot=slot, group=group, version=version,
                 stats=dict(zip(SERVE_STATS, list(st))))
 
 
@@ -708,8 +710,9 @@ SERVE_STATS = ["batches", "requests", "queries", "inserted", "max_in_flight",
 
 class Server:
     """Serving loop over a growable index (pg_serve_*): query and insertion
-    requests with host buffers; query groups run on `slots` concurrent
-    workers, insertions alone; tickets complete out of order."""
+    requests with host buffers; query groups and insertions run on `slots`
+    concurrent workers, each query group on the index version pinned when it
+    was dispatched; tickets complete out of order."""
 
     def __init__(self, index: Index, max_batch: int = 1024, slots: int = 4):
         self.index, self.ctx = index, index.ctx

@@ -542,9 +542,9 @@ extern "C" pg_status pg_index_phase_seconds(const pg_index *idx, double *host_se
 // context's stream (rows added by insertions are encoded on first use).
 // Serialised per index: concurrent searches of a serving loop wait for one
 // encoding, which completes before the lock is released.
-static pg_status index_f8(pg_ctx *ctx, const pg_index *idx, F8Rows *out) {
+static pg_status index_f8(pg_ctx *ctx, const pg_index *idx, int64_t n, F8Rows *out) {
     std::lock_guard<std::mutex> lk(idx->f8_mu);
-    const int64_t cap = std::max(idx->n, idx->capacity);
+    const int64_t cap = std::max(n, idx->capacity);
     if (idx->f8_cap < cap) {
         cudaFree(idx->f8);
         cudaFree(idx->f8_scale);
@@ -555,46 +555,48 @@ static pg_status index_f8(pg_ctx *ctx, const pg_index *idx, F8Rows *out) {
         PG_TRY_CUDA(ctx, cudaMalloc(&idx->f8_scale, (size_t)cap * 4));
         idx->f8_cap = cap;
     }
-    if (idx->f8_rows < idx->n) {
-        PG_TRY(pg_make_f8(ctx, idx->D, idx->f8_rows, idx->n, idx->d, idx->f8, idx->f8_scale));
+    if (idx->f8_rows < n) {
+        PG_TRY(pg_make_f8(ctx, idx->D, idx->f8_rows, n, idx->d, idx->f8, idx->f8_scale));
         PG_TRY_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-        idx->f8_rows = idx->n;
+        idx->f8_rows = n;
     }
     *out = F8Rows{idx->f8, idx->f8_scale};
     return PG_OK;
 }
 
-static pg_status search_index(pg_ctx *ctx, const pg_index *idx, const float *Q, int64_t nq,
+// Queries on one published version of the index (the snapshot sn).
+static pg_status search_index(pg_ctx *ctx, const IndexSnap &sn, const float *Q, int64_t nq,
                               int32_t k, int32_t beam, int32_t upper_beam, int32_t flags,
                               pg_precision precision, int32_t *out_ids, float *out_dist) {
     if (nq == 0) return PG_OK;
+    const pg_index *idx = sn.idx;
     F8Rows f8{};
-    if (precision == PG_PREC_FP8_SCREEN) PG_TRY(index_f8(ctx, idx, &f8));
+    if (precision == PG_PREC_FP8_SCREEN) PG_TRY(index_f8(ctx, idx, sn.n, &f8));
     // exactness of every (query, point) distance, for the search's comparator
     DataFacts facts;
-    if (idx->has_facts) facts = idx->facts;
-    else PG_TRY(pg_data_facts(ctx, idx->D, idx->n, idx->d, idx->metric, &facts));
+    if (sn.has_facts) facts = sn.facts;
+    else PG_TRY(pg_data_facts(ctx, idx->D, sn.n, idx->d, idx->metric, &facts));
     PG_TRY(pg_query_facts(ctx, Q, nq, idx->d, idx->metric, &facts));
     Scratch<int32_t> w, w2;
     Scratch<float> s2;
     PG_TRY(w.alloc(ctx, (size_t)nq));
-    const bool layered = idx->layers.size() > 1 && !(flags & PG_SEARCH_FLAT);
+    const bool layered = sn.layers.size() > 1 && !(flags & PG_SEARCH_FLAT);
     k_fill_i32<<<(unsigned)((nq + 255) / 256), 256, 0, ctx->stream>>>(
-        w.p, nq, (int32_t)(layered ? idx->ep_top : idx->ep_base));
+        w.p, nq, (int32_t)(layered ? sn.ep_top : sn.ep_base));
     PG_LAUNCHED(ctx);
     if (layered) {
         PG_TRY(w2.alloc(ctx, (size_t)nq));
         PG_TRY(s2.alloc(ctx, (size_t)nq));
-        for (int i = (int)idx->layers.size() - 1; i >= 1; --i) {
-            const pg_layer &l = idx->layers[(size_t)i];
-            PG_TRY(pg_search_internal(ctx, idx->D, idx->n, idx->d, idx->metric, l.nbr, l.deg, l.R,
+        for (int i = (int)sn.layers.size() - 1; i >= 1; --i) {
+            const pg_layer &l = sn.layers[(size_t)i];
+            PG_TRY(pg_search_internal(ctx, idx->D, sn.n, idx->d, idx->metric, l.nbr, l.deg, l.R,
                                       l.rows, Q, nq, w.p, 1, upper_beam, 0, w2.p, s2.p, nullptr,
                                       nullptr, &facts));
             std::swap(w.p, w2.p);
         }
     }
-    const pg_layer &b = idx->layers[0];
-    return pg_search_internal(ctx, idx->D, idx->n, idx->d, idx->metric, b.nbr, b.deg, b.R, nullptr,
+    const pg_layer &b = sn.layers[0];
+    return pg_search_internal(ctx, idx->D, sn.n, idx->d, idx->metric, b.nbr, b.deg, b.R, nullptr,
                               Q, nq, w.p, k, beam, 0, out_ids, out_dist, nullptr,
                               precision == PG_PREC_FP8_SCREEN ? &f8 : nullptr, &facts);
 }
@@ -617,7 +619,17 @@ extern "C" pg_status pg_search(pg_ctx *ctx, const pg_index *idx, const float *Q,
                                int32_t k, int32_t beam, int32_t upper_beam, int32_t flags,
                                pg_precision precision, int32_t *out_ids, float *out_dist) {
     PG_TRY(check_search(ctx, idx, Q, nq, k, beam, upper_beam, precision, out_ids, out_dist));
-    PG_TRY(search_index(ctx, idx, Q, nq, k, beam, upper_beam, flags, precision, out_ids,
+    const IndexSnap sn(idx);  // a reader of this version until the work has synchronised
+    PG_TRY(search_index(ctx, sn, Q, nq, k, beam, upper_beam, flags, precision, out_ids,
+                        out_dist));
+    return pg_sync_check(ctx, "pg_search");
+}
+
+pg_status pg_search_pinned(pg_ctx *ctx, const IndexSnap &sn, const float *Q, int64_t nq,
+                           int32_t k, int32_t beam, int32_t upper_beam, int32_t flags,
+                           pg_precision precision, int32_t *out_ids, float *out_dist) {
+    PG_TRY(check_search(ctx, sn.idx, Q, nq, k, beam, upper_beam, precision, out_ids, out_dist));
+    PG_TRY(search_index(ctx, sn, Q, nq, k, beam, upper_beam, flags, precision, out_ids,
                         out_dist));
     return pg_sync_check(ctx, "pg_search");
 }
@@ -627,6 +639,7 @@ extern "C" pg_status pg_search_host(pg_ctx *ctx, const pg_index *idx, const floa
                                     pg_precision precision, int32_t *out_ids, float *out_dist) {
     PG_TRY(check_search(ctx, idx, Q, nq, k, beam, upper_beam, precision, out_ids, out_dist));
     if (nq == 0) return PG_OK;
+    const IndexSnap sn(idx);  // a reader of this version until the work has synchronised
     Scratch<float> dq, ds;
     Scratch<int32_t> di;
     PG_TRY(dq.alloc(ctx, (size_t)(nq * idx->d)));
@@ -634,7 +647,7 @@ extern "C" pg_status pg_search_host(pg_ctx *ctx, const pg_index *idx, const floa
     PG_TRY(di.alloc(ctx, (size_t)(nq * k)));
     PG_TRY_CUDA(ctx, cudaMemcpyAsync(dq.p, Q, (size_t)(nq * idx->d) * 4, cudaMemcpyHostToDevice,
                                      ctx->stream));
-    PG_TRY(search_index(ctx, idx, dq.p, nq, k, beam, upper_beam, flags, precision, di.p, ds.p));
+    PG_TRY(search_index(ctx, sn, dq.p, nq, k, beam, upper_beam, flags, precision, di.p, ds.p));
     PG_TRY_CUDA(ctx, cudaMemcpyAsync(out_ids, di.p, (size_t)(nq * k) * 4, cudaMemcpyDeviceToHost,
                                      ctx->stream));
     PG_TRY_CUDA(ctx, cudaMemcpyAsync(out_dist, ds.p, (size_t)(nq * k) * 4, cudaMemcpyDeviceToHost,
@@ -782,24 +795,19 @@ extern "C" pg_status pg_index_reserve(pg_ctx *ctx, pg_index *idx, int64_t capaci
     return pg_sync_check(ctx, "pg_index_reserve");
 }
 
-extern "C" pg_status pg_index_insert(pg_ctx *ctx, pg_index *idx, const float *X, int64_t m,
-                                     int32_t ef, int32_t upper_beam) {
-    if (!ctx) return PG_ERR_INVALID_ARG;
-    if (!idx || (!X && m > 0)) return pg_fail(ctx, PG_ERR_INVALID_ARG, "null pointer");
-    if (m < 0 || ef < 1 || ef > 256 || upper_beam < 1 || upper_beam > 256)
-        return pg_fail(ctx, PG_ERR_INVALID_ARG, "need m >= 0, 1 <= ef, upper_beam <= 256");
-    if (m == 0) return PG_OK;
-    if (!idx->owned || idx->n + m > idx->capacity)
-        return pg_fail(ctx, PG_ERR_CAPACITY, "insert: %lld points exceed the reserved capacity",
-                       (long long)m);
-    const int64_t n0 = idx->n, N = n0 + m, d = idx->d;
+// Algorithm 4 on a snapshot, applied to the working copy L of the layers
+// (n0 points before the batch); facts_out receives the facts of all N rows.
+static pg_status insert_into(pg_ctx *ctx, pg_index *idx, std::vector<pg_layer> &L, int64_t n0,
+                             const float *X, int64_t m, int32_t ef, int32_t upper_beam,
+                             DataFacts *facts_out) {
+    const int64_t N = n0 + m, d = idx->d;
     const pg_build_params &p = idx->params;
     float *Dall = idx->owned;
     PG_TRY_CUDA(ctx, cudaMemcpyAsync(Dall + n0 * d, X, (size_t)(m * d) * 4,
                                      cudaMemcpyDeviceToDevice, ctx->stream));
     DataFacts facts;
     PG_TRY(pg_data_facts(ctx, Dall, N, (int32_t)d, idx->metric, &facts));
-    const int top = (int)idx->layers.size() - 1;
+    const int top = (int)L.size() - 1;
     std::vector<int> lev((size_t)m);
     for (int64_t k = 0; k < m; ++k)
         lev[(size_t)k] = std::min(level_of(n0 + k, p.seed, p.M), top);
@@ -813,7 +821,7 @@ extern "C" pg_status pg_index_insert(pg_ctx *ctx, pg_index *idx, const float *X,
     PG_LAUNCHED(ctx);
     std::vector<int32_t> hs, hb, hg;
     for (int i = top; i >= 0; --i) {
-        pg_layer &l = idx->layers[(size_t)i];
+        pg_layer &l = L[(size_t)i];
         const int Ri = l.R;
         hs.clear();
         hb.clear();
@@ -944,8 +952,73 @@ extern "C" pg_status pg_index_insert(pg_ctx *ctx, pg_index *idx, const float *X,
         l.count += ns;
         PG_TRY(pg_sync_check(ctx, "insert"));
     }
-    idx->n = N;
+    *facts_out = facts;
+    return pg_sync_check(ctx, "pg_index_insert");
+}
+
+extern "C" pg_status pg_index_insert(pg_ctx *ctx, pg_index *idx, const float *X, int64_t m,
+                                     int32_t ef, int32_t upper_beam) {
+    if (!ctx) return PG_ERR_INVALID_ARG;
+    if (!idx || (!X && m > 0)) return pg_fail(ctx, PG_ERR_INVALID_ARG, "null pointer");
+    if (m < 0 || ef < 1 || ef > 256 || upper_beam < 1 || upper_beam > 256)
+        return pg_fail(ctx, PG_ERR_INVALID_ARG, "need m >= 0, 1 <= ef, upper_beam <= 256");
+    if (m == 0) return PG_OK;
+    std::vector<pg_layer> L;
+    int64_t n0 = 0;
+    {
+        std::lock_guard<std::mutex> lk(idx->ver_mu);
+        L = idx->layers;
+        n0 = idx->n;
+    }
+    if (!idx->owned || n0 + m > idx->capacity)
+        return pg_fail(ctx, PG_ERR_CAPACITY, "insert: %lld points exceed the reserved capacity",
+                       (long long)m);
+    // the next version in copies of every layer's arrays: searches keep
+    // reading the published version meanwhile
+    std::vector<void *> fresh;
+    auto copy_of = [&](int32_t *&ptr, int64_t count, int64_t keep) -> pg_status {
+        int32_t *q = nullptr;
+        PG_TRY_CUDA(ctx, cudaMalloc(&q, (size_t)std::max<int64_t>(count, 1) * 4));
+        fresh.push_back(q);
+        if (keep > 0)
+            PG_TRY_CUDA(ctx, cudaMemcpyAsync(q, ptr, (size_t)keep * 4, cudaMemcpyDeviceToDevice,
+                                             ctx->stream));
+        ptr = q;
+        return PG_OK;
+    };
+    pg_status st = PG_OK;
+    for (auto &l : L) {
+        if (st == PG_OK) st = copy_of(l.nbr, l.cap * l.R, l.count * l.R);
+        if (st == PG_OK) st = copy_of(l.deg, l.cap, l.count);
+        if (st == PG_OK && l.gid) st = copy_of(l.gid, l.cap, l.count);
+        if (st == PG_OK && l.rows) st = copy_of(l.rows, idx->capacity, idx->capacity);
+    }
+    DataFacts facts;
+    if (st == PG_OK) st = insert_into(ctx, idx, L, n0, X, m, ef, upper_beam, &facts);
+    if (st != PG_OK) {
+        cudaStreamSynchronize(ctx->stream);
+        for (void *q : fresh) cudaFree(q);
+        return st;
+    }
+    // publish; the arrays of versions no search reads any more are freed
+    std::lock_guard<std::mutex> lk(idx->ver_mu);
+    std::vector<void *> old;
+    for (auto &l : idx->layers)
+        for (void *q : {(void *)l.nbr, (void *)l.deg, (void *)l.gid, (void *)l.rows})
+            if (q) old.push_back(q);
+    idx->retired.push_back({idx->version, std::move(old)});
+    idx->layers = L;
+    idx->n = n0 + m;
     idx->facts = facts;
     idx->has_facts = 1;
-    return pg_sync_check(ctx, "pg_index_insert");
+    idx->version += 1;
+    for (auto it = idx->retired.begin(); it != idx->retired.end();) {
+        if (idx->readers.count(it->first) == 0) {
+            for (void *q : it->second) cudaFree(q);
+            it = idx->retired.erase(it);
+        } else {
+            ++it;
+        }
+    }
+    return PG_OK;
 }

@@ -8,6 +8,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <functional>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -95,6 +96,16 @@ struct pg_index {
     mutable uint8_t *f8 = nullptr;      // [f8_cap][d]
     mutable float *f8_scale = nullptr;  // [f8_cap] value of 1.0 in the FP8 row
     mutable int64_t f8_rows = 0, f8_cap = 0;
+    // Published versions of the layers (serving): a search takes a snapshot
+    // of `layers`, `n` and the entry points under ver_mu and counts as a
+    // reader of `version` until it has synchronised; an insertion builds the
+    // next version in copies of the layer arrays and publishes it; arrays of
+    // older versions are freed by a later insertion (or here) once no search
+    // reads them.
+    mutable std::mutex ver_mu;
+    uint64_t version = 0;
+    mutable std::map<uint64_t, int> readers;
+    std::vector<std::pair<uint64_t, std::vector<void *>>> retired;
     ~pg_index() {
         cudaFree(owned);
         cudaFree(f8);
@@ -105,8 +116,44 @@ struct pg_index {
             cudaFree(l.deg);
             cudaFree(l.rows);
         }
+        for (auto &r : retired)
+            for (void *p : r.second) cudaFree(p);
     }
 };
+
+// A search's view of an index: the published layers, point count and entry
+// points of one version, held as a reader of that version while alive.
+struct IndexSnap {
+    const pg_index *idx;
+    std::vector<pg_layer> layers;
+    int64_t n = 0, ep_top = 0, ep_base = 0;
+    uint64_t version = 0;
+    DataFacts facts{};
+    int has_facts = 0;
+    explicit IndexSnap(const pg_index *index) : idx(index) {
+        std::lock_guard<std::mutex> lk(idx->ver_mu);
+        layers = idx->layers;
+        n = idx->n;
+        ep_top = idx->ep_top;
+        ep_base = idx->ep_base;
+        version = idx->version;
+        facts = idx->facts;
+        has_facts = idx->has_facts;
+        idx->readers[version] += 1;
+    }
+    ~IndexSnap() {
+        std::lock_guard<std::mutex> lk(idx->ver_mu);
+        if (--idx->readers[version] == 0) idx->readers.erase(version);
+    }
+    IndexSnap(const IndexSnap &) = delete;
+    IndexSnap &operator=(const IndexSnap &) = delete;
+};
+
+// pg_search on a pinned version of the index (the serving loop pins it when
+// it dispatches a query group); synchronises the context's stream
+pg_status pg_search_pinned(pg_ctx *ctx, const IndexSnap &sn, const float *Q, int64_t nq,
+                           int32_t k, int32_t beam, int32_t upper_beam, int32_t flags,
+                           pg_precision precision, int32_t *out_ids, float *out_dist);
 
 // FP8 rows of an index for screened queries (device pointers)
 struct F8Rows {

@@ -10,11 +10,13 @@
 // worker is free and the device scratch of the groups in flight plus its
 // own fits the HBM budget of the server's context (a group that could never
 // fit fails with PG_ERR_BUDGET).  An insertion batch (Algorithm 4 on a
-// snapshot, pg_index_insert) waits until every group dispatched before it
-// has finished, then runs alone on the server's context, and nothing after
-// it is dispatched before it finishes: a query sees exactly the points
-// inserted before it was submitted, however the groups overlap.  Tickets
-// complete out of order; pg_serve_wait waits for one ticket.
+// snapshot, pg_index_insert) takes a free worker beside the query groups in
+// flight: it builds the next version of the index in copies of the layer
+// arrays while those groups keep searching the version they started on
+// (epoch snapshots), publishes it when it ends, and nothing submitted after
+// it is dispatched before then: a query sees exactly the points inserted
+// before it was submitted, however the work overlaps.  Tickets complete out
+// of order; pg_serve_wait waits for one ticket.
 //
 // The scheduler below is host-only and takes its work as callbacks, so the
 // same code runs with simulated work on a machine without a GPU
@@ -29,6 +31,7 @@
 #include <condition_variable>
 #include <deque>
 #include <functional>
+#include <memory>
 #include <mutex>
 #include <set>
 #include <thread>
@@ -55,6 +58,8 @@ struct Group {
     std::vector<Req> reqs;
     int64_t rows = 0;
     size_t bytes = 0;
+    bool insert = false;
+    std::shared_ptr<void> pinned;  // the index version a query group searches
 };
 
 enum { SLOT_IDLE = 0, SLOT_ASSIGNED, SLOT_RUNNING };
@@ -67,7 +72,11 @@ struct Sched {
     std::function<bool(const Req &, const Req &)> mergeable;
     std::function<size_t(const Group &)> group_bytes;
     std::function<pg_status(int, const Group &)> run_group;
-    std::function<pg_status(const Req &)> run_insert;
+    std::function<pg_status(int, const Req &)> run_insert;
+    // pins the current version of the index for a query group being
+    // dispatched (with mu held): the group searches it wherever its worker
+    // starts, so it sees exactly the insertions submitted before it
+    std::function<std::shared_ptr<void>()> pin;
 
     // state, under mu
     std::mutex mu;
@@ -82,6 +91,7 @@ struct Sched {
     std::vector<int> slot_state;
     std::vector<Group> slot_job;
     int busy = 0;
+    bool insert_running = false;  // an insertion is on a worker: nothing after it starts
     size_t bytes_in_flight = 0;
     int64_t n_groups = 0, n_requests = 0, n_queries = 0, n_inserted = 0, max_in_flight = 0,
             admission_waits = 0;
@@ -127,13 +137,15 @@ struct Sched {
                 slot_state[(size_t)s] = SLOT_RUNNING;
                 g = std::move(slot_job[(size_t)s]);
             }
-            const pg_status st = run_group(s, g);
+            const pg_status st = g.insert ? run_insert(s, g.reqs[0]) : run_group(s, g);
+            g.pinned.reset();
             {
                 std::lock_guard<std::mutex> lk(mu);
                 complete(g.reqs, st);
                 slot_state[(size_t)s] = SLOT_IDLE;
                 --busy;
                 bytes_in_flight -= g.bytes;
+                if (g.insert) insert_running = false;
             }
             cv_free.notify_all();
         }
@@ -146,11 +158,11 @@ struct Sched {
             std::unique_lock<std::mutex> lk(mu);
             cv_work.wait(lk, [&] { return stopping || !queue.empty(); });
             if (queue.empty()) break;  // stopping and drained
-            // A group is formed only once it can start (a free worker; for an
-            // insertion, no group in flight), so requests that arrive while
-            // the workers are busy join it: batching follows the load.
+            // A group is formed only once it can start (a free worker), so
+            // requests that arrive while the workers are busy join it:
+            // batching follows the load.
             const bool insertion = queue.front().kind == 1;
-            auto can_start = [&] { return insertion ? busy == 0 : busy < nslots; };
+            auto can_start = [&] { return busy < nslots; };
             if (!can_start()) {
                 ++admission_waits;
                 cv_free.wait(lk, can_start);
@@ -159,10 +171,20 @@ struct Sched {
             g.rows = queue.front().rows;
             queue.pop_front();
             if (insertion) {
-                lk.unlock();
-                const pg_status st = run_insert(g.reqs[0]);
-                lk.lock();
-                complete(g.reqs, st);
+                // The insertion runs on a worker beside the query groups in
+                // flight, which search the version of the index they started
+                // on; it publishes the next version when it ends, and
+                // nothing submitted after it is dispatched before then.
+                g.insert = true;
+                int s = 0;
+                while (slot_state[(size_t)s] != SLOT_IDLE) ++s;
+                slot_state[(size_t)s] = SLOT_ASSIGNED;
+                slot_job[(size_t)s] = std::move(g);
+                ++busy;
+                max_in_flight = std::max<int64_t>(max_in_flight, busy);
+                insert_running = true;
+                cv_slot.notify_all();
+                cv_free.wait(lk, [&] { return !insert_running; });
                 continue;
             }
             while (!queue.empty() && mergeable(g.reqs[0], queue.front()) &&
@@ -181,6 +203,7 @@ struct Sched {
                 ++admission_waits;
                 cv_free.wait(lk, fits);
             }
+            if (pin) g.pinned = pin();
             int s = 0;
             while (slot_state[(size_t)s] != SLOT_IDLE) ++s;
             slot_state[(size_t)s] = SLOT_ASSIGNED;
@@ -312,7 +335,8 @@ size_t query_group_bytes(int d, const Group &g) {
     return (size_t)g.rows * ((size_t)d * 4 + (size_t)k * 8 + 12);
 }
 
-pg_status run_queries(pg_ctx *ctx, pg_index *index, int d, const Group &g) {
+pg_status run_queries(pg_ctx *ctx, int d, const Group &g) {
+    const IndexSnap &sn = *static_cast<const IndexSnap *>(g.pinned.get());
     const int64_t total = g.rows;
     const int k = g.reqs[0].k;
     Scratch<float> Q, dist;
@@ -326,8 +350,8 @@ pg_status run_queries(pg_ctx *ctx, pg_index *index, int d, const Group &g) {
                                          cudaMemcpyHostToDevice, ctx->stream));
         at += r.rows;
     }
-    PG_TRY(pg_search(ctx, index, Q.p, total, k, g.reqs[0].beam, g.reqs[0].upper_beam, 0,
-                     g.reqs[0].precision, ids.p, dist.p));
+    PG_TRY(pg_search_pinned(ctx, sn, Q.p, total, k, g.reqs[0].beam, g.reqs[0].upper_beam, 0,
+                            g.reqs[0].precision, ids.p, dist.p));
     at = 0;
     for (const Req &r : g.reqs) {
         PG_TRY_CUDA(ctx, cudaMemcpyAsync(r.out_ids, ids.p + at * k, (size_t)(r.rows * k) * 4,
@@ -339,8 +363,8 @@ pg_status run_queries(pg_ctx *ctx, pg_index *index, int d, const Group &g) {
     return pg_sync_check(ctx, "serve query");
 }
 
-pg_status run_insert(pg_server *s, const Req &r) {
-    pg_ctx *ctx = s->ctx;
+pg_status run_insert(pg_server *s, int slot, const Req &r) {
+    pg_ctx *ctx = s->slot_ctx[(size_t)slot];
     Scratch<float> X;
     PG_TRY(X.alloc(ctx, (size_t)(r.rows * s->d)));
     PG_TRY_CUDA(ctx, cudaMemcpyAsync(X.p, r.host, (size_t)(r.rows * s->d) * 4,
@@ -411,9 +435,10 @@ extern "C" pg_status pg_serve_start(pg_ctx *ctx, pg_index *index, int32_t max_ba
     const int d = s->d;
     q.group_bytes = [d](const Group &g) { return query_group_bytes(d, g); };
     q.run_group = [s](int slot, const Group &g) {
-        return run_queries(s->slot_ctx[(size_t)slot], s->index, s->d, g);
+        return run_queries(s->slot_ctx[(size_t)slot], s->d, g);
     };
-    q.run_insert = [s](const Req &r) { return run_insert(s, r); };
+    q.pin = [s]() -> std::shared_ptr<void> { return std::make_shared<IndexSnap>(s->index); };
+    q.run_insert = [s](int slot, const Req &r) { return run_insert(s, slot, r); };
     const int dev = s->device;
     q.thread_init = [dev] { cudaSetDevice(dev); };
     if (!q.start()) {
@@ -518,7 +543,7 @@ extern "C" pg_status pg_serve_simulate(int32_t slots, int32_t max_batch, int64_t
                                        const int32_t *shape, int32_t work_us,
                                        int64_t bytes_per_row, int64_t *start_seq,
                                        int64_t *end_seq, int32_t *slot_of, int64_t *group_of,
-                                       int64_t *host_stats6) {
+                                       int64_t *version_of, int64_t *host_stats6) {
     if (slots < 1 || slots > 16 || max_batch < 1 || budget_bytes < 0 || count < 0 ||
         work_us < 0 || work_us > 100000 || bytes_per_row < 0)
         return PG_ERR_INVALID_ARG;
@@ -526,7 +551,7 @@ extern "C" pg_status pg_serve_simulate(int32_t slots, int32_t max_batch, int64_t
         return PG_ERR_INVALID_ARG;
     for (int32_t i = 0; i < count; ++i)
         if ((kind[i] != 0 && kind[i] != 1) || rows[i] < 1) return PG_ERR_INVALID_ARG;
-    std::atomic<int64_t> seq{0}, group_id{0};
+    std::atomic<int64_t> seq{0}, group_id{0}, version{0};
     Sched q;
     q.nslots = slots;
     q.max_batch = max_batch;
@@ -535,10 +560,13 @@ extern "C" pg_status pg_serve_simulate(int32_t slots, int32_t max_batch, int64_t
         return a.kind == 0 && b.kind == 0 && a.shape == b.shape;
     };
     q.group_bytes = [bytes_per_row](const Group &g) { return (size_t)(g.rows * bytes_per_row); };
-    auto simulate = [&](int s, const std::vector<Req> &reqs, int64_t units) {
+    // an insertion publishes version + 1 when it ends; a query group
+    // records the version pinned when it was dispatched
+    auto simulate = [&](int s, const std::vector<Req> &reqs, int64_t units, int64_t ver) {
         const int64_t g = group_id++;
         const int64_t t0 = seq++;
         std::this_thread::sleep_for(std::chrono::microseconds((int64_t)work_us * (1 + units / 64)));
+        if (ver < 0) ver = ++version;
         const int64_t t1 = seq++;
         for (const Req &r : reqs) {
             const size_t i = (size_t)(r.ticket - 1);
@@ -546,11 +574,17 @@ extern "C" pg_status pg_serve_simulate(int32_t slots, int32_t max_batch, int64_t
             end_seq[i] = t1;
             slot_of[i] = s;
             group_of[i] = g;
+            if (version_of) version_of[i] = ver;
         }
         return PG_OK;
     };
-    q.run_group = [&](int s, const Group &g) { return simulate(s, g.reqs, g.rows); };
-    q.run_insert = [&](const Req &r) { return simulate(-1, std::vector<Req>{r}, r.rows); };
+    q.run_group = [&](int s, const Group &g) {
+        return simulate(s, g.reqs, g.rows, *static_cast<const int64_t *>(g.pinned.get()));
+    };
+    q.run_insert = [&](int slot, const Req &r) {
+        return simulate(slot, std::vector<Req>{r}, r.rows, -1);
+    };
+    q.pin = [&]() -> std::shared_ptr<void> { return std::make_shared<int64_t>(version.load()); };
     if (!q.start()) return PG_ERR_INTERNAL;
     std::vector<Req> reqs((size_t)count);
     for (int32_t i = 0; i < count; ++i) {

@@ -644,3 +644,53 @@ def test_serving_overlapped_groups_equal_single_searches(ctx, pg):
     for rows, k, beam, ub, t, ids, dist in reqs:
         gi, gd = b.search(dev(Q[rows]), k, beam, upper_beam=ub)
         assert (host(gi) == ids).all() and (host(gd) == dist).all()
+
+
+def test_serving_insertions_beside_queries_equal_the_same_calls_in_order(ctx, pg):
+    """Four workers, query shapes that never merge, insertions among them:
+    each insertion runs beside the query groups dispatched before it, which
+    search the version they pinned; every result equals the same call made
+    in submission order on a twin index, and the final graphs agree."""
+    D, Q, _ = synthetic.workload(1, n=4000, nq=160)
+    n0 = 2800
+    p = dict(K=24, L=48, R=32, M=16, alpha_deg=70.0, iters=1, seed=5)
+    a = pg.Index.build_nswg(ctx, dev(D[:n0]), metric="l2", **p)
+    ctx2 = pg.Context()
+    b = pg.Index.build_nswg(ctx2, dev(D[:n0]), metric="l2", **p)
+    a.reserve(4000)
+    b.reserve(4000)
+    shapes = [(10, 32, 1), (10, 48, 4), (5, 64, 16), (1, 16, 1)]
+    plan, at, ins = [], 0, n0
+    for i in range(48):
+        if i % 12 == 11:
+            plan.append(("i", ins, ins + 300))
+            ins += 300
+            continue
+        m = 1 + (i * 5) % 11
+        plan.append(("q", at, at + m, shapes[i % 4]))
+        at = (at + m) % 140
+    srv = pg.Server(b, max_batch=256, slots=4)
+    tickets = []
+    for e in plan:
+        if e[0] == "q":
+            k, beam, ub = e[3]
+            tickets.append(srv.submit_query(Q[e[1]:e[2]], k, beam, ub))
+        else:
+            tickets.append((srv.submit_insert(D[e[1]:e[2]], 40, 4), None, None))
+    assert srv.wait_all([t[0] for t in tickets], 180.0)
+    st = srv.stats()
+    srv.stop()
+    assert st["requests"] == len(plan) and st["inserted"] == 1200
+    assert st["max_in_flight"] >= 2
+    for e, (t, ids, dist) in zip(plan, tickets):
+        if e[0] == "i":
+            a.insert(dev(D[e[1]:e[2]]), 40, 4)
+            continue
+        k, beam, ub = e[3]
+        gi, gd = a.search(dev(Q[e[1]:e[2]]), k, beam, upper_beam=ub)
+        assert (host(gi) == ids).all() and (host(gd) == dist).all(), e
+    ia, ib = a.info(), b.info()
+    assert ia == ib and ia["n"] == 4000
+    for layer in range(ia["n_layers"]):
+        for x, y in zip(a.layer(layer), b.layer(layer)):
+            assert torch.equal(x, y)

@@ -1,8 +1,9 @@
 """The serving loop's scheduler on the host (pg_serve_simulate: the same
 scheduler code as pg_serve_start, with simulated work and no GPU).
 
-Checked from the event log: an insertion starts after every earlier request
-has ended and ends before every later request starts; query groups hold
+Checked from the event log: an insertion runs on a worker beside the
+query groups dispatched before it (they search the version they started
+on) and ends before every later request starts; query groups hold
 consecutive requests of one shape, never more than max_batch queries; with
 several workers groups overlap, with one they never do; the scratch of the
 groups in flight never exceeds the budget, and a group that can never fit
@@ -26,15 +27,23 @@ def overlaps(a0, a1, b0, b1):
 
 
 @pytest.mark.parametrize("seed,slots", [(0, 4), (1, 2), (2, 1), (3, 8)])
-def test_insertions_are_barriers(seed, slots):
+def test_insertions_publish_before_later_requests(seed, slots):
     kind, rows, shape = plan(seed)
     r = pg.serve_simulate(kind, rows, shape, slots=slots, max_batch=64, work_us=300)
     start, end = r["start"], r["end"]
     assert (start >= 0).all() and (end > start).all()
     for t in np.flatnonzero(kind == 1):
-        assert r["slot"][t] == -1
-        assert (end[:t] < start[t]).all(), t
+        assert 0 <= r["slot"][t] < slots
+        # nothing submitted later starts before it has published
         assert (start[t + 1:] > end[t]).all(), t
+        if slots == 1:
+            assert (end[:t] < start[t]).all(), t
+    # each query group searched the version left by the insertions submitted
+    # before it, wherever its worker started
+    before = np.cumsum(kind) - kind
+    q = kind == 0
+    assert (r["version"][q] == before[q]).all()
+    assert (r["version"][kind == 1] == before[kind == 1] + 1).all()
     st = r["stats"]
     assert st["requests"] == len(kind)
     assert st["queries"] == rows[kind == 0].sum() and st["inserted"] == rows[kind == 1].sum()
@@ -105,3 +114,17 @@ def test_simulation_rejects_bad_arguments():
         pg.serve_simulate([2], [1], [0])
     with pytest.raises(pg.PGError):
         pg.serve_simulate([0], [0], [0])
+
+
+def test_insertion_overlaps_the_groups_before_it():
+    # three long query groups of distinct shapes, then an insertion: with
+    # four workers it starts while they still run, and the query after it
+    # waits for its end
+    kind = np.array([0, 0, 0, 1, 0], np.int32)
+    rows = np.array([64, 64, 64, 4, 4], np.int32)
+    shape = np.array([0, 1, 2, 0, 0], np.int32)
+    r = pg.serve_simulate(kind, rows, shape, slots=4, max_batch=64, work_us=4000)
+    start, end = r["start"], r["end"]
+    assert any(overlaps(start[i], end[i], start[3], end[3]) for i in range(3))
+    assert start[4] > end[3]
+    assert r["stats"]["max_in_flight"] >= 2
