@@ -172,10 +172,13 @@ def reverse_union(nbr, deg):
     return off, ids[:tot]
 
 
-def medoid(D, metric: str = "l2") -> int:
-    """Point nearest the centroid (Section 3.1, search phase)."""
+def medoid(D, metric: str = "l2", return_centroid: bool = False):
+    """Point nearest the centroid (Section 3.1, search phase); with
+    return_centroid also the FP64 centroid it used."""
     D = _f32(D)
-    return int(_get().or_medoid(_p(D), D.shape[0], D.shape[1], METRICS[metric], None))
+    c = np.zeros(D.shape[1], np.float64)
+    ep = int(_get().or_medoid(_p(D), D.shape[0], D.shape[1], METRICS[metric], _p(c)))
+    return (ep, c) if return_centroid else ep
 
 
 def connect(D, nbr, deg, ep: int, metric: str = "l2"):

@@ -323,6 +323,33 @@ def test_medoid_is_point_nearest_exact_centroid():
     assert oracle.medoid(D) == best
 
 
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_medoid_on_real_rows_against_the_exact_centroid(seed):
+    """Non-integer rows: the FP64 centroid (summed in blocks) lies within
+    the summation's error bound of the exact rational centroid, and the
+    medoid is the exact argmin of the rational distances whenever the gap
+    between the two nearest points exceeds what that error can move."""
+    rs = np.random.default_rng(40 + seed)
+    n, d = 2500, 6
+    D = (rs.normal(size=(n, d)) * rs.uniform(0.1, 3.0, size=d)).astype(np.float32)
+    ep, c = oracle.medoid(D, return_centroid=True)
+    exact = [sum(Fraction(float(x)) for x in D[:, i]) / n for i in range(d)]
+    u = 2.0 ** -53
+    for i in range(d):
+        # n additions and one division, each relatively within u
+        bound = (n + 1) * u * float(np.abs(D[:, i].astype(np.float64)).sum()) / n + 1e-300
+        assert abs(Fraction(c[i]) - exact[i]) <= Fraction(bound)
+    dist = sorted((sum((Fraction(float(x)) - ci) ** 2 for x, ci in zip(D[v], exact)), v)
+                  for v in range(n))
+    (s0, v0), (s1, _) = dist[0], dist[1]
+    # the centroid's error moves each distance by at most 2 |x - c| e + e^2 per coordinate
+    e = max(abs(Fraction(c[i]) - exact[i]) for i in range(d))
+    spread = max(float(np.abs(D).max()), 1.0) * 2
+    move = 2 * d * (2 * Fraction(spread) * e + e * e) + Fraction(8 * d * u) * s1
+    assert s1 - s0 > move  # the draw is decidable
+    assert ep == v0
+
+
 def _reach(nbr, deg, src):
     seen = {src}
     st = [src]
