@@ -974,12 +974,37 @@ extern "C" pg_status pg_index_insert(pg_ctx *ctx, pg_index *idx, const float *X,
         return pg_fail(ctx, PG_ERR_CAPACITY, "insert: %lld points exceed the reserved capacity",
                        (long long)m);
     // the next version in copies of every layer's arrays: searches keep
-    // reading the published version meanwhile
-    std::vector<void *> fresh;
+    // reading the published version meanwhile.  The arrays of an earlier
+    // version that no search pins any more are reused (same layer sizes), so
+    // an insertion allocates (and synchronises the device) only when there
+    // is none, e.g. the first time.
+    auto bytes_of = [](int64_t count) { return (size_t)std::max<int64_t>(count, 1) * 4; };
+    std::vector<std::pair<void *, size_t>> spare, fresh, extra;
+    {
+        // one unpinned earlier version is reused, any other unpinned one freed
+        std::lock_guard<std::mutex> lk(idx->ver_mu);
+        for (auto it = idx->retired.begin(); it != idx->retired.end();) {
+            if (idx->readers.count(it->first) != 0) {
+                ++it;
+                continue;
+            }
+            auto &dst = spare.empty() ? spare : extra;
+            dst.insert(dst.end(), it->second.begin(), it->second.end());
+            it = idx->retired.erase(it);
+        }
+    }
+    for (auto &b : extra) cudaFree(b.first);
+    size_t next_spare = 0;
     auto copy_of = [&](int32_t *&ptr, int64_t count, int64_t keep) -> pg_status {
+        const size_t bytes = bytes_of(count);
         int32_t *q = nullptr;
-        PG_TRY_CUDA(ctx, cudaMalloc(&q, (size_t)std::max<int64_t>(count, 1) * 4));
-        fresh.push_back(q);
+        if (next_spare < spare.size() && spare[next_spare].second == bytes) {
+            q = static_cast<int32_t *>(spare[next_spare].first);
+            spare[next_spare++].first = nullptr;
+        } else {
+            PG_TRY_CUDA(ctx, cudaMalloc(&q, bytes));
+        }
+        fresh.push_back({q, bytes});
         if (keep > 0)
             PG_TRY_CUDA(ctx, cudaMemcpyAsync(q, ptr, (size_t)keep * 4, cudaMemcpyDeviceToDevice,
                                              ctx->stream));
@@ -993,32 +1018,28 @@ extern "C" pg_status pg_index_insert(pg_ctx *ctx, pg_index *idx, const float *X,
         if (st == PG_OK && l.gid) st = copy_of(l.gid, l.cap, l.count);
         if (st == PG_OK && l.rows) st = copy_of(l.rows, idx->capacity, idx->capacity);
     }
+    for (auto &b : spare) cudaFree(b.first);  // sizes that no longer match (cudaFree(NULL): no-op)
     DataFacts facts;
     if (st == PG_OK) st = insert_into(ctx, idx, L, n0, X, m, ef, upper_beam, &facts);
     if (st != PG_OK) {
         cudaStreamSynchronize(ctx->stream);
-        for (void *q : fresh) cudaFree(q);
+        for (auto &b : fresh) cudaFree(b.first);
         return st;
     }
-    // publish; the arrays of versions no search reads any more are freed
+    // publish; the old arrays wait for reuse until no search pins their version
     std::lock_guard<std::mutex> lk(idx->ver_mu);
-    std::vector<void *> old;
-    for (auto &l : idx->layers)
-        for (void *q : {(void *)l.nbr, (void *)l.deg, (void *)l.gid, (void *)l.rows})
-            if (q) old.push_back(q);
+    std::vector<std::pair<void *, size_t>> old;
+    for (auto &l : idx->layers) {
+        old.push_back({l.nbr, bytes_of(l.cap * l.R)});
+        old.push_back({l.deg, bytes_of(l.cap)});
+        if (l.gid) old.push_back({l.gid, bytes_of(l.cap)});
+        if (l.rows) old.push_back({l.rows, bytes_of(idx->capacity)});
+    }
     idx->retired.push_back({idx->version, std::move(old)});
     idx->layers = L;
     idx->n = n0 + m;
     idx->facts = facts;
     idx->has_facts = 1;
     idx->version += 1;
-    for (auto it = idx->retired.begin(); it != idx->retired.end();) {
-        if (idx->readers.count(it->first) == 0) {
-            for (void *q : it->second) cudaFree(q);
-            it = idx->retired.erase(it);
-        } else {
-            ++it;
-        }
-    }
     return PG_OK;
 }

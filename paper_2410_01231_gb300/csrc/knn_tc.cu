@@ -7,14 +7,18 @@
 // 2^24: then the BF16 copy is exact and the tensor-core sums are exact
 // integers, so the result equals the FP32 and FP64 definitions bit for bit.
 //
-// CTA = 6 warps.  The epilogue threads first write the 128-row query tile
-// into TMEM (one row per lane, two BF16 per 32-bit column), so the MMAs
-// read only the candidate tiles from shared memory.  Warp 0 issues TMA loads
-// (128B-swizzled K-major tiles) of 128-row candidate tiles through a
-// 3-stage ring.  Warp 1 owns the TMEM allocation and issues the MMAs
-// (M128 N128 K16 steps, A from TMEM) into a double-buffered FP32
-// accumulator (2 x 128 columns).  Warps 2-5 are the epilogue: thread t of the four owns query
-// row t; it reads its accumulator row with tcgen05.ld.32x32b.x32, screens
+// CTA = 10 warps for rows of at most 128 dims (6 for wider rows).  The
+// epilogue threads first write the CTA's two 128-row query tiles into TMEM
+// (one row per lane, two BF16 per 32-bit column), so the MMAs read only
+// the candidate tiles from shared memory and every candidate tile feeds
+// the MMAs of both query tiles (half the candidate bytes per product of a
+// one-tile CTA).  Warp 0 issues TMA loads (128B-swizzled K-major tiles) of
+// 128-row candidate tiles through a 3-stage ring.  Warp 1 owns the TMEM
+// allocation and issues the MMAs (M128 N128 K16 steps, A from TMEM) into
+// three FP32 accumulator buffers of 128 columns, rotating over the
+// (candidate tile, query tile) pairs.  Warps 2-9 are the epilogue, four per
+// query tile: thread t of a group owns query row t of its tile; it reads
+// its accumulator row with tcgen05.ld.32x32b.x32, screens
 // 32 columns at a time by their minimum against its current K-th distance
 // and keeps a private max-heap of its K best in shared memory (sorted once
 // at the end).  For the graph the points are spatially ordered first, and
@@ -289,32 +293,36 @@ struct TcLayout {
 // row and all 128 columns of a tile; 3 candidate stages.  H = 2: eight
 // epilogue warps, two per lane quarter taking 64 columns each, so two
 // threads and two heaps per row (merged at the end); 2 candidate stages.
+// QT = 2 (H = 1, dp <= 128): two 128-row query tiles per CTA, both in TMEM,
+// so that every candidate tile feeds twice the MMAs; eight epilogue warps,
+// one group of four per query tile; three accumulator buffers rotating
+// over the (candidate tile, query tile) pairs; 3 candidate stages.
 // KB (k-blocked, any dp): the query tile is not resident; every stage holds
 // one 64-column block of the query tile and of the candidate tile, and the
 // MMAs of a tile accumulate over the blocks; H = 1, 3 stages, K <= KTCK.
-__host__ __device__ constexpr int tc_threads(int H) { return 64 + 128 * H; }
+__host__ __device__ constexpr int tc_threads(int H, int QT = 1) { return 64 + 128 * H * QT; }
 __host__ __device__ constexpr int tc_stages(int H, bool KB = false) {
     return KB ? 3 : (H == 1 ? 3 : 2);
 }
 __host__ __device__ constexpr int tc_kcap(bool KB) { return KB ? KTCK : KTC; }
 constexpr uint32_t KB_STAGE = (uint32_t)(TM + TN) * 64 * 2;  // bytes of one k-blocked stage
 
-__host__ __device__ inline TcLayout tc_layout(int dp, int H, bool KB = false) {
+__host__ __device__ inline TcLayout tc_layout(int dp, int H, bool KB = false, int QT = 1) {
     TcLayout L;
     uint32_t o = 0;
-    L.a = o;  // unused: the resident query tile lives in TMEM
+    L.a = o;  // unused: the resident query tiles live in TMEM
     L.b = o;
     o += KB ? tc_stages(H, KB) * KB_STAGE : (uint32_t)tc_stages(H) * TN * dp * 2;
-    L.ls = o;  // H x [kcap][TM] per-row heaps: distances
-    o += (uint32_t)H * tc_kcap(KB) * TM * 4;
-    L.li = o;  // H x [kcap][TM] ids
-    o += (uint32_t)H * tc_kcap(KB) * TM * 4;
-    L.nbuf = o;
-    o += 2 * TN * 4;
+    L.ls = o;  // H x QT x [kcap][TM] per-row heaps: distances
+    o += (uint32_t)(H * QT) * tc_kcap(KB) * TM * 4;
+    L.li = o;  // H x QT x [kcap][TM] ids
+    o += (uint32_t)(H * QT) * tc_kcap(KB) * TM * 4;
+    L.nbuf = o;  // 32 column norms per epilogue warp
+    o += (uint32_t)(H * QT) * TM * 4;
     L.cnt = o;  // entries of the second heap of every row (H = 2)
     o += H == 2 ? TM * 4 : 0;
     L.bars = o;
-    o += 16 * 8;
+    o += 24 * 8;
     L.misc = o;
     o += 16;
     L.total = o;
@@ -324,8 +332,8 @@ __host__ __device__ inline TcLayout tc_layout(int dp, int H, bool KB = false) {
 // perm (nullable): position -> original id of spatially ordered points (Q
 // is D itself); lists hold original ids, rows are written back in original
 // order.  rotate: scan the tiles around the CTA's rows first.
-template <int H, bool KB>
-__global__ void __launch_bounds__(tc_threads(H), 1)
+template <int H, bool KB, int QT>
+__global__ void __launch_bounds__(tc_threads(H, QT), 1)
 k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUtensorMap mapX,
          const __nv_bfloat16 *__restrict__ qrows, int64_t nq, int64_t n, int dp,
          const float *__restrict__ qnorm,
@@ -334,25 +342,35 @@ k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUten
          unsigned long long *progress, int resident) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = reinterpret_cast<uint8_t *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    constexpr int STG = tc_stages(H, KB), NEPI = 128 * H, KCAP = tc_kcap(KB);
-    // resident variants: accumulators in columns [0, 256), the query tile in
-    // [256, 256 + dp / 2) (two BF16 of a row per 32-bit column)
+    static_assert(QT == 1 || (QT == 2 && H == 1 && !KB), "two query tiles: H = 1, resident");
+    constexpr int STG = tc_stages(H, KB), NEPI = 128 * H * QT, KCAP = tc_kcap(KB);
+    // accumulator buffers of TN columns: two (QT = 1) or three rotating over
+    // the (candidate tile, query tile) pairs (QT = 2)
+    constexpr int NACC = QT == 2 ? 3 : 2;
+    // resident variants: accumulators in columns [0, NACC TN), query tile qt
+    // in [ABASE + qt dp / 2, ...) (two BF16 of a row per 32-bit column);
+    // dp / 2 <= 64 when QT = 2
+    constexpr uint32_t ABASE = (uint32_t)NACC * TN;
     constexpr uint32_t TMEM_COLS = KB ? (uint32_t)ACC_COLS : 512u;
-    const TcLayout Ly = tc_layout(dp, H, KB);
+    const TcLayout Ly = tc_layout(dp, H, KB, QT);
     uint8_t *B = sm + Ly.b;
     float *Ls0 = reinterpret_cast<float *>(sm + Ly.ls);
     int *Li0 = reinterpret_cast<int *>(sm + Ly.li);
     float *nbuf = reinterpret_cast<float *>(sm + Ly.nbuf);
     int *cntbuf = reinterpret_cast<int *>(sm + Ly.cnt);
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + Ly.bars);
+    // acc_full[b * QT + qt]: buffer b holds a finished tile of query tile qt
+    // (one barrier per consumer group, so each group waits on every phase of
+    // its own barriers in order); acc_empty[b]: the group that read buffer b
+    // has released it
     uint64_t *a_full = bars, *b_full = bars + 1, *b_empty = bars + 1 + STG;
-    uint64_t *acc_full = bars + 1 + 2 * STG, *acc_empty = bars + 3 + 2 * STG;
-    uint64_t *drain = bars + 5 + 2 * STG;
+    uint64_t *acc_full = bars + 1 + 2 * STG, *acc_empty = acc_full + NACC * QT;
+    uint64_t *drain = acc_empty + NACC;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + Ly.misc);
     volatile int *abort = reinterpret_cast<volatile int *>(sm + Ly.misc + 4);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t row0 = (int64_t)blockIdx.x * TM;
+    const int64_t row0 = (int64_t)blockIdx.x * TM * QT;
     const int nkb = dp / 64;
     const int ntiles = (int)((n + TN - 1) / TN);
     const uint32_t b_bytes = (uint32_t)TN * dp * 2;
@@ -366,7 +384,8 @@ k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUten
     // tiles at about the same time and share them in L2.  Every role walks
     // the same order (the start is read once and shared).
     const int pre = rotate ? min(16, ntiles) : 0;
-    const int w0 = rotate ? max(0, min((int)(row0 / TN) - pre / 2, ntiles - pre)) : 0;
+    const int w0 =
+        rotate ? max(0, min((int)((row0 + TM * QT / 2) / TN) - pre / 2, ntiles - pre)) : 0;
     const int nrest = max(1, ntiles - pre);
     int *start_slot = reinterpret_cast<int *>(sm + Ly.misc + 8);
 
@@ -376,10 +395,8 @@ k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUten
             mbar_init(b_full + s, 1);
             mbar_init(b_empty + s, 1);
         }
-        for (int a = 0; a < 2; ++a) {
-            mbar_init(acc_full + a, 1);
-            mbar_init(acc_empty + a, NEPI);
-        }
+        for (int a = 0; a < NACC * QT; ++a) mbar_init(acc_full + a, 1);
+        for (int a = 0; a < NACC; ++a) mbar_init(acc_empty + a, NEPI / QT);
         mbar_init(drain, 1);
         *abort = 0;
         *start_slot = progress ? (int)((atomicAdd(progress, 0ull) / (unsigned long long)resident) %
@@ -481,20 +498,28 @@ k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUten
             }
         } else if (lane == 0) {  // ---------------- MMA issuer
             bool ok = mbar_wait(a_full, 0, abort, err, true);
-            int t = 0;
-            for (; ok && t < ntiles; ++t) {
-                const int s = t % STG, a = t & 1;
+            for (int t = 0; ok && t < ntiles; ++t) {
+                const int s = t % STG;
                 if (!mbar_wait(b_full + s, (t / STG) & 1, abort, err, true)) break;
-                if (!mbar_wait(acc_empty + a, ((t >> 1) & 1) ^ 1, abort, err, true)) break;
-                tc_fence_after();
                 const uint32_t b0 = saddr(B + (size_t)s * TN * dp * 2);
-                for (int k = 0; k < dp / 16; ++k) {
-                    const int kb = k >> 2, koff = (k & 3) * 32;
-                    umma_bf16_ts(tmem + a * TN, tmem + ACC_COLS + 8 * k,
-                                 sw128_desc(b0 + kb * TN * 128 + koff), k > 0 ? 1u : 0u);
+                for (int qt = 0; qt < QT; ++qt) {
+                    // pair j = QT t + qt goes to buffer j % NACC, its (j / NACC)-th use
+                    const int j = QT * t + qt, a = j % NACC;
+                    if (!mbar_wait(acc_empty + a, ((j / NACC) & 1) ^ 1, abort, err, true)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t aq = tmem + ABASE + (uint32_t)(qt * (dp / 2));
+                    for (int k = 0; k < dp / 16; ++k) {
+                        const int kb = k >> 2, koff = (k & 3) * 32;
+                        umma_bf16_ts(tmem + a * TN, aq + 8 * k,
+                                     sw128_desc(b0 + kb * TN * 128 + koff), k > 0 ? 1u : 0u);
+                    }
+                    umma_commit(acc_full + a * QT + qt);
                 }
+                if (!ok) break;
                 umma_commit(b_empty + s);
-                umma_commit(acc_full + a);
             }
             // every MMA issued above has completed once `drain` flips
             umma_commit(drain);
@@ -504,17 +529,19 @@ k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUten
         }
     } else {  // ---------------------------------------- epilogue
         const int q = warp & 3;               // TMEM lane quarter
-        const int half = (warp - 2) >> 2;     // column half (H = 2)
+        const int grp = (warp - 2) >> 2;      // group of four warps
+        const int half = QT == 1 ? grp : 0;   // column half (H = 2)
+        const int qt = QT == 1 ? 0 : grp;     // query tile (QT = 2)
         const int c_lo = half * (4 / H);
-        float *Ls = Ls0 + half * KCAP * TM;
-        int *Li = Li0 + half * KCAP * TM;
+        float *Ls = Ls0 + grp * KCAP * TM;
+        int *Li = Li0 + grp * KCAP * TM;
         const int row = q * 32 + lane;
-        const int64_t g = row0 + row;
+        const int64_t g = row0 + qt * TM + row;
         const bool live = g < nq;
         const float nqr = live ? qnorm[g] : 0.f;
         if (!KB) {
             // the query tile into TMEM: thread `row` writes its row (zeros
-            // past nq) to columns [256, 256 + dp / 2) of its lane
+            // past nq) to columns [ABASE + qt dp / 2, ... + dp / 2) of its lane
             if (half == 0) {
                 const uint4 *src = reinterpret_cast<const uint4 *>(qrows + (live ? g : 0) * dp);
                 for (int b = 0; b < dp / 64; ++b) {
@@ -527,7 +554,8 @@ k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUten
                         r[4 * c4 + 2] = v.z;
                         r[4 * c4 + 3] = v.w;
                     }
-                    tmem_st32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ACC_COLS + 32 * b), r);
+                    tmem_st32(tmem + ((uint32_t)(q * 32) << 16) +
+                                  (ABASE + (uint32_t)(qt * (dp / 2) + 32 * b)), r);
                 }
                 asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
             }
@@ -552,7 +580,8 @@ k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUten
 #pragma unroll
         for (int ci = 0; ci < NCH; ++ci) nxt[ci] = colnorm(0, c_lo + ci);
         for (int t = 0; t < ntiles; ++t) {
-            const int a = t & 1;
+            // the buffer of pair QT t + qt; this group's (t / NACC)-th use of it
+            const int a = (QT * t + qt) % NACC;
             const int64_t colbase = (int64_t)tile_at(t) * TN;
             float cur[NCH];
 #pragma unroll
@@ -560,7 +589,7 @@ k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUten
                 cur[ci] = nxt[ci];
                 nxt[ci] = colnorm(t + 1, c_lo + ci);
             }
-            mbar_wait(acc_full + a, (t >> 1) & 1, abort, err);
+            mbar_wait(acc_full + a * QT + qt, (t / NACC) & 1, abort, err);
             // a warp that sees the abort leaves; the others leave at their
             // next check (no epilogue barrier inside this loop)
             if (__any_sync(0xffffffffu, *abort != 0)) break;
@@ -654,7 +683,7 @@ k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUten
         if (half == 0) {
             for (int rr = 0; rr < 32; ++rr) {
                 const int r2 = q * 32 + rr;
-                const int64_t gp = row0 + r2;
+                const int64_t gp = row0 + qt * TM + r2;
                 const int cnt2 = __shfl_sync(0xffffffffu, count, rr);
                 if (gp >= nq) continue;
                 const int64_t g2 = perm ? (int64_t)perm[gp] : gp;
@@ -939,17 +968,21 @@ pg_status make_map(pg_ctx *ctx, CUtensorMap *map, const __nv_bfloat16 *base, int
 }  // namespace
 
 // Kernel variant for dp columns and K neighbours: the resident-query kernel
-// with two heaps per row, else with one, else the k-blocked kernel.
+// with two query tiles per CTA (both in TMEM: dp <= 128), else with one
+// query tile and one heap per row, else two heaps per row, else the
+// k-blocked kernel.
 struct TcVariant {
     int H;
     bool KB;
+    int QT;
 };
 
 static TcVariant tc_variant(int dp, int K) {
     const uint32_t cap = 227 * 1024 - 1024;
-    if (K <= KTC && tc_layout(dp, 1).total <= cap) return {1, false};
-    if (K <= KTC && tc_layout(dp, 2).total <= cap) return {2, false};
-    return {1, true};
+    if (K <= KTC && dp <= 128 && tc_layout(dp, 1, false, 2).total <= cap) return {1, false, 2};
+    if (K <= KTC && tc_layout(dp, 1).total <= cap) return {1, false, 1};
+    if (K <= KTC && tc_layout(dp, 2).total <= cap) return {2, false, 1};
+    return {1, true, 1};
 }
 
 bool pg_knn_tc_supported(int d, int K) {
@@ -1011,10 +1044,13 @@ static pg_status tc_knn_run(pg_ctx *ctx, Scratch<__nv_bfloat16> &xc,
     Scratch<int64_t> boff;
     const __nv_bfloat16 *qp = self ? (xq_sep ? xq_sep->p : xc.p) : qext;
     const TcVariant V = tc_variant(dp, K);
-    const size_t smem = tc_layout(dp, V.H, V.KB).total + 1024;
-    PG_TRY_CUDA(ctx, cudaFuncSetAttribute(V.KB ? k_knn_tc<1, true>
-                                               : (V.H == 2 ? k_knn_tc<2, false> : k_knn_tc<1, false>),
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const size_t smem = tc_layout(dp, V.H, V.KB, V.QT).total + 1024;
+    PG_TRY_CUDA(ctx, cudaFuncSetAttribute(
+                         V.KB ? k_knn_tc<1, true, 1>
+                              : (V.QT == 2 ? k_knn_tc<1, false, 2>
+                                           : (V.H == 2 ? k_knn_tc<2, false, 1> : k_knn_tc<1, false, 1>)),
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int rows_per_cta = TM * V.QT;
     // one launch of the chosen variant
     // tiles issued by all CTAs of a launch (the common start of each cycle)
     Scratch<unsigned long long> prog;
@@ -1026,20 +1062,21 @@ static pg_status tc_knn_run(pg_ctx *ctx, Scratch<__nv_bfloat16> &xc,
         PG_TRY_CUDA(ctx, cudaMemsetAsync(prog.p, 0, 8, ctx->stream));
         const int res = ctx->num_sms;  // one CTA per SM (shared memory)
         if (V.KB)
-            k_knn_tc<1, true><<<grid, tc_threads(1), smem, ctx->stream>>>(
+            k_knn_tc<1, true, 1><<<grid, tc_threads(1), smem, ctx->stream>>>(
                 mq_, mx_, qrows_, nq_, n_, dp, qn_, xn_, K_, self_, oi, os, ctx->d_err, perm_, rot,
-                prog.p,
-                res);
+                prog.p, res);
+        else if (V.QT == 2)
+            k_knn_tc<1, false, 2><<<grid, tc_threads(1, 2), smem, ctx->stream>>>(
+                mq_, mx_, qrows_, nq_, n_, dp, qn_, xn_, K_, self_, oi, os, ctx->d_err, perm_, rot,
+                prog.p, res);
         else if (V.H == 2)
-            k_knn_tc<2, false><<<grid, tc_threads(2), smem, ctx->stream>>>(
+            k_knn_tc<2, false, 1><<<grid, tc_threads(2), smem, ctx->stream>>>(
                 mq_, mx_, qrows_, nq_, n_, dp, qn_, xn_, K_, self_, oi, os, ctx->d_err, perm_, rot,
-                prog.p,
-                res);
+                prog.p, res);
         else
-            k_knn_tc<1, false><<<grid, tc_threads(1), smem, ctx->stream>>>(
+            k_knn_tc<1, false, 1><<<grid, tc_threads(1), smem, ctx->stream>>>(
                 mq_, mx_, qrows_, nq_, n_, dp, qn_, xn_, K_, self_, oi, os, ctx->d_err, perm_, rot,
-                prog.p,
-                res);
+                prog.p, res);
         return PG_OK;
     };
     const int32_t *permp = nullptr;
@@ -1063,8 +1100,8 @@ static pg_status tc_knn_run(pg_ctx *ctx, Scratch<__nv_bfloat16> &xc,
         CUtensorMap mqa, mpa;
         PG_TRY(make_map(ctx, &mqa, qp, n, dp));
         PG_TRY(make_map(ctx, &mpa, pb.p, P, dp));
-        PG_TRY(launch((unsigned)((n + TM - 1) / TM), mqa, mpa, qp, n, P, xnorm, pn.p, 1, 0,
-                      asg.p, adist.p, nullptr, 0));
+        PG_TRY(launch((unsigned)((n + rows_per_cta - 1) / rows_per_cta), mqa, mpa, qp, n, P, xnorm,
+                      pn.p, 1, 0, asg.p, adist.p, nullptr, 0));
         PG_LAUNCHED(ctx);
         PG_TRY(cnt.alloc(ctx, (size_t)P));
         PG_TRY(boff.alloc(ctx, (size_t)P + 1));
@@ -1102,7 +1139,7 @@ static pg_status tc_knn_run(pg_ctx *ctx, Scratch<__nv_bfloat16> &xc,
     CUtensorMap mq, mx;
     PG_TRY(make_map(ctx, &mx, xp, n, dp));
     PG_TRY(make_map(ctx, &mq, qp, self ? n : nq, dp));
-    const unsigned grid = (unsigned)((nq + TM - 1) / TM);
+    const unsigned grid = (unsigned)((nq + rows_per_cta - 1) / rows_per_cta);
     pg_timer_begin(ctx, TM_KNN);
     PG_TRY(launch(grid, mq, mx, qp, nq, n, qnp, xnp, K, self, ids, dist, permp, permp ? 1 : 0));
     PG_LAUNCHED(ctx);

@@ -99,13 +99,15 @@ struct pg_index {
     // Published versions of the layers (serving): a search takes a snapshot
     // of `layers`, `n` and the entry points under ver_mu and counts as a
     // reader of `version` until it has synchronised; an insertion builds the
-    // next version in copies of the layer arrays and publishes it; arrays of
-    // older versions are freed by a later insertion (or here) once no search
-    // reads them.
+    // next version in copies of the layer arrays and publishes it; the arrays
+    // of older versions are reused by a later insertion once no search pins
+    // them (freed here at the end).
     mutable std::mutex ver_mu;
     uint64_t version = 0;
     mutable std::map<uint64_t, int> readers;
-    std::vector<std::pair<uint64_t, std::vector<void *>>> retired;
+    // graph arrays (pointer, bytes) of earlier versions, kept for reuse by
+    // the next insertion once no search pins them
+    std::vector<std::pair<uint64_t, std::vector<std::pair<void *, size_t>>>> retired;
     ~pg_index() {
         cudaFree(owned);
         cudaFree(f8);
@@ -117,7 +119,7 @@ struct pg_index {
             cudaFree(l.rows);
         }
         for (auto &r : retired)
-            for (void *p : r.second) cudaFree(p);
+            for (auto &b : r.second) cudaFree(b.first);
     }
 };
 
