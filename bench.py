@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--no-screen", action="store_true")
     ap.add_argument("--sweep", action="store_true",
                     help="alpha / I sweep on the workload instead of the benchmark line")
+    ap.add_argument("--extra", choices=["nswg-1m-d96-cosine", "serve-2m-d384-ip"], default=None,
+                    help="the NSWG cosine or the 2M x 384 serving workload instead of the "
+                         "benchmark line")
     return ap.parse_args()
 
 
@@ -198,6 +201,90 @@ def job_rate(ms_local: float, n_per_rank: int, world: int, device: str = "cpu"):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     return ms, world * n_per_rank / (ms / 1e3)
+
+
+def serving_measure(pg, idx, Q, X, ins, k, beam, upper_beam, seed=7):
+    """The serving loop on a built index (groups of up to 1,024 queries on
+    SERVE_SLOTS workers, host buffers), request sizes drawn from {1, 8, 32,
+    128, 1024} queries, two insertion batches of `ins` points of X after
+    requests 100 and 200 of 300:
+      saturated: all 300 requests queued at once, with SERVE_SLOTS workers,
+      with one, and with SERVE_SLOTS workers and FP8-screened queries, for
+      requests/s and queries/s;
+      poisson: the same mix arriving as a Poisson process at 70% of the
+      saturated request rate, for the latency of each request from
+      submission to completion (p50 / p99, host clock);
+    then 200 single-query requests one at a time.  The index must have room
+    for 8 ins more points."""
+    Qh = np.asarray(Q)
+    nq = len(Qh)
+    rs = np.random.default_rng(seed)
+    sizes = rs.choice([1, 8, 32, 128, 1024], size=300)
+    cursor = {"q": 0, "x": 0}
+
+    def run_stream(srv, gaps=None):
+        tickets, queries, nqs = [], [], 0
+        t0 = time.perf_counter()
+        for r, sz in enumerate(sizes):
+            if gaps is not None:
+                due = t0 + gaps[r]
+                while True:
+                    left = due - time.perf_counter()
+                    if left <= 0:
+                        break
+                    time.sleep(left if left > 1e-3 else 0)
+            if r in (100, 200):
+                j = cursor["x"]
+                cursor["x"] += 1
+                tickets.append(srv.submit_insert(X[j * ins:(j + 1) * ins], 64, upper_beam))
+            rows = (cursor["q"] + np.arange(int(sz))) % nq
+            cursor["q"] += int(sz)
+            nqs += int(sz)
+            t, _, _ = srv.submit_query(Qh[rows], k, beam, upper_beam)
+            tickets.append(t)
+            queries.append(t)
+        assert srv.wait_all(tickets, 600.0)
+        secs = time.perf_counter() - t0
+        lat = [srv.latency(t) * 1e3 for t in queries]
+        return secs, nqs, lat
+
+    sat = {}
+    for slots, prec in ((SERVE_SLOTS, "fp32"), (1, "fp32"), (SERVE_SLOTS, "fp8")):
+        srv = pg.Server(idx, max_batch=1024, slots=slots)
+        srv.set_precision(prec)
+        secs, nqs, _ = run_stream(srv)
+        st = srv.stats()
+        srv.stop()
+        sat[(slots, prec)] = {"seconds": secs, "requests_per_s": len(sizes) / secs,
+                              "queries_per_s": nqs / secs, "groups": int(st["batches"]),
+                              "max_in_flight": int(st["max_in_flight"])}
+    rate = 0.7 * sat[(SERVE_SLOTS, "fp32")]["requests_per_s"]
+    gaps = np.cumsum(rs.exponential(1.0 / rate, size=len(sizes)))
+    srv = pg.Server(idx, max_batch=1024, slots=SERVE_SLOTS)
+    secs, nqs, lat = run_stream(srv, gaps)
+    st = srv.stats()
+    single = []
+    for i in range(200):
+        t1 = time.perf_counter()
+        tk, _, _ = srv.submit_query(Qh[i % nq:i % nq + 1], k, beam, upper_beam)
+        srv.wait(tk, 60.0)
+        single.append((time.perf_counter() - t1) * 1e3)
+    srv.stop()
+    return {"slots": SERVE_SLOTS, "requests": len(sizes), "queries": int(sizes.sum()),
+            "inserted_per_stream": 2 * ins,
+            "saturated": sat[(SERVE_SLOTS, "fp32")],
+            "saturated_one_worker": sat[(1, "fp32")],
+            "saturated_fp8_screen": sat[(SERVE_SLOTS, "fp8")],
+            "poisson": {"rate_requests_per_s": rate, "seconds": secs,
+                        "queries_per_s": nqs / secs, "groups": int(st["batches"]),
+                        "max_in_flight": int(st["max_in_flight"]),
+                        "admission_waits": int(st["admission_waits"]),
+                        "p50_ms": float(np.percentile(lat, 50)),
+                        "p99_ms": float(np.percentile(lat, 99))},
+            "single_query_p50_ms": float(np.percentile(single, 50)),
+            "single_query_p99_ms": float(np.percentile(single, 99)),
+            "stream": f"300 query requests of 1/8/32/128/1024 queries (k={k}, beam {beam}) "
+                      f"with two insertion batches of {ins} points, host buffers"}
 
 
 def run_reference(args):
@@ -387,78 +474,11 @@ def run_ours(args):
     if not args.no_serve:
         ins = max(100, n // 100)
         X = synthetic.inserts(WORKLOAD, 8 * ins)
-        Qh = Q if isinstance(Q, np.ndarray) else np.asarray(Q)
         idx = pg.Index.build_rng(ctx, Dd, **params)
         idx.reserve(n + 8 * ins)
-        rs = np.random.default_rng(7)
-        sizes = rs.choice([1, 8, 32, 128, 1024], size=300)
-        cursor = {"q": 0, "x": 0}
-
-        def run_stream(srv, gaps=None):
-            tickets, queries, nqs = [], [], 0
-            t0 = time.perf_counter()
-            for r, sz in enumerate(sizes):
-                if gaps is not None:
-                    due = t0 + gaps[r]
-                    while True:
-                        left = due - time.perf_counter()
-                        if left <= 0:
-                            break
-                        time.sleep(left if left > 1e-3 else 0)
-                if r in (100, 200):
-                    j = cursor["x"]
-                    cursor["x"] += 1
-                    tickets.append(srv.submit_insert(X[j * ins:(j + 1) * ins], 64, 16))
-                rows = (cursor["q"] + np.arange(int(sz))) % nq
-                cursor["q"] += int(sz)
-                nqs += int(sz)
-                t, _, _ = srv.submit_query(Qh[rows], w["k"], 48, 16)
-                tickets.append(t)
-                queries.append(t)
-            assert srv.wait_all(tickets, 600.0)
-            secs = time.perf_counter() - t0
-            lat = [srv.latency(t) * 1e3 for t in queries]
-            return secs, nqs, lat
-
         barrier()
-        sat = {}
-        for slots, prec in ((SERVE_SLOTS, "fp32"), (1, "fp32"), (SERVE_SLOTS, "fp8")):
-            srv = pg.Server(idx, max_batch=1024, slots=slots)
-            srv.set_precision(prec)
-            secs, nqs, _ = run_stream(srv)
-            st = srv.stats()
-            srv.stop()
-            sat[(slots, prec)] = {"seconds": secs, "requests_per_s": len(sizes) / secs,
-                                  "queries_per_s": nqs / secs, "groups": int(st["batches"]),
-                                  "max_in_flight": int(st["max_in_flight"])}
-        rate = 0.7 * sat[(SERVE_SLOTS, "fp32")]["requests_per_s"]
-        gaps = np.cumsum(rs.exponential(1.0 / rate, size=len(sizes)))
-        srv = pg.Server(idx, max_batch=1024, slots=SERVE_SLOTS)
-        secs, nqs, lat = run_stream(srv, gaps)
-        st = srv.stats()
-        single = []
-        for i in range(200):
-            t1 = time.perf_counter()
-            tk, _, _ = srv.submit_query(Qh[i:i + 1], w["k"], 48, 16)
-            srv.wait(tk, 60.0)
-            single.append((time.perf_counter() - t1) * 1e3)
-        srv.stop()
+        serve = serving_measure(pg, idx, Q, X, ins, w["k"], 48, 16)
         idx.close()
-        serve = {"slots": SERVE_SLOTS, "requests": len(sizes), "queries": int(sizes.sum()),
-                 "inserted_per_stream": 2 * ins,
-                 "saturated": sat[(SERVE_SLOTS, "fp32")],
-                 "saturated_one_worker": sat[(1, "fp32")],
-                 "saturated_fp8_screen": sat[(SERVE_SLOTS, "fp8")],
-                 "poisson": {"rate_requests_per_s": rate, "seconds": secs,
-                             "queries_per_s": nqs / secs, "groups": int(st["batches"]),
-                             "max_in_flight": int(st["max_in_flight"]),
-                             "admission_waits": int(st["admission_waits"]),
-                             "p50_ms": float(np.percentile(lat, 50)),
-                             "p99_ms": float(np.percentile(lat, 99))},
-                 "single_query_p50_ms": float(np.percentile(single, 50)),
-                 "single_query_p99_ms": float(np.percentile(single, 99)),
-                 "stream": "300 query requests of 1/8/32/128/1024 queries (k=10, beam 48) with "
-                           f"two insertion batches of {ins} points, host buffers"}
 
     # ------------------------------------- the 960-d real-valued workload
     # The 1M x 960 real-valued recipe (512 centres U[0,1]^960, sigma 0.1)
@@ -867,12 +887,113 @@ def run_sweep(args):
                       "iters": iters, "init": inits}), flush=True)
 
 
+def run_extra(args):
+    """One of the two other single-GPU workloads, printed as one JSON line:
+    nswg-1m-d96-cosine (unit Gaussian rows, NSWG, Algorithm 7) or
+    serve-2m-d384-ip (4,096-cluster sphere mixture, inner product, NSWG, then
+    the serving stream with insertions).  The NSWG build in the screened form
+    (K 64, L 200, R 32, M 16, I 2, alpha 66 / 60, edge replacement on) timed
+    with CUDA events after one warm-up build (none at 2M), with its phases,
+    layer sizes and the mean out-degree of layer 0; recall@10 against the
+    exact kNN of the queries (the library's FP32 tiles) and queries/s per
+    beam, FP32 and FP8-screened queries.  For the cosine workload also the
+    build with a final angle of 70 and 80 degrees (its out-degree and
+    recall), for the serving workload the serving stream of the benchmark
+    line on that index.  Clocks are sampled during the timed build."""
+    import torch
+    import paper_2410_01231_gb300 as pg
+
+    c = {"nswg-1m-d96-cosine": 4, "serve-2m-d384-ip": 5}[args.extra]
+    torch.cuda.set_device(0)
+    D, Q, w = synthetic.workload(c, n=args.n, nq=args.nq)
+    n, nq, k = w["n"], w["nq"], w["k"]
+    Dd, Qd = torch.from_numpy(D).cuda(), torch.from_numpy(Q).cuda()
+    stream = torch.cuda.current_stream()
+    ctx = pg.Context(stream)
+    ctx.set_autotune(True)
+    base = dict(metric=w["metric"], K=w["K"], L=w["L"], R=w["R"], M=w["M"], alpha_deg=66.0,
+                alpha_final_deg=60.0, iters=2, precision="bf16", seed=0)
+
+    def events():
+        return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed_build(prm, warm, clocks=None):
+        for _ in range(warm):
+            pg.Index.build_nswg(ctx, Dd, **prm).close()
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+        e0, e1 = events()
+        e0.record(stream)
+        idx = pg.Index.build_nswg(ctx, Dd, **prm)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop() if clocks else None
+        return idx, e0.elapsed_time(e1) / 1e3, clk
+
+    gt_i, gt_d = pg.knn_query(ctx, Dd, Qd, k)
+    kth = gt_d[:, k - 1].clone()
+
+    def recall(ids):
+        # squared chord of unit rows (cosine and inner product alike)
+        dq = (2.0 - 2.0 * (Qd[:, None, :] * Dd[ids.long().clamp(min=0)]).sum(-1)).clamp(min=0)
+        ok = (dq <= kth[:, None] * (1 + 1e-5) + 1e-6) & (ids >= 0)
+        return float(ok.sum(1).clamp(max=k).float().mean() / k)
+
+    def curve(idx, beams, prec="fp32"):
+        out = []
+        for beam in beams:
+            idx.search(Qd, k, beam, precision=prec)
+            e0, e1 = events()
+            e0.record(stream)
+            ids, _ = idx.search(Qd, k, beam, precision=prec)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            out.append({"beam": beam, "recall_at_10": recall(ids),
+                        "qps": nq / (e0.elapsed_time(e1) / 1e3)})
+        return out
+
+    def shape(idx):
+        info = idx.info()
+        sizes = [int(idx.layer(i)[0].numel()) for i in range(info["n_layers"])]
+        dg = idx.layer(0)[2]
+        return {"layer_sizes": sizes, "mean_out_degree_layer0": float(dg.float().mean())}
+
+    res = {"workload": w["name"], "n": n, "d": w["d"], "metric": w["metric"], "nq": nq,
+           "build_params": "K 64, L 200, R 32, M 16, I 2, alpha 66 / 60, bf16 screen, "
+                           "edge replacement", "data": "synthetic"}
+    idx, secs, clk = timed_build(base, 1 if n <= 1_000_000 else 0, Clocks(0))
+    res.update({"build_s": secs, "points_per_s": n / secs, "clocks": clk,
+                "phase_s": idx.phase_seconds(), **shape(idx),
+                "queries": curve(idx, w["beams"]),
+                "queries_fp8_screen": curve(idx, w["beams"], "fp8")})
+    if c == 4:
+        idx.close()
+        wider = []
+        for af in (70.0, 80.0):
+            ix, s2, _ = timed_build(dict(base, alpha_final_deg=af), 0)
+            wider.append({"alpha_final": af, "build_s": s2, **shape(ix),
+                          "queries": curve(ix, (64, 256))})
+            ix.close()
+        res["wider_final_alpha"] = wider
+    else:
+        ins = max(100, n // 100)
+        idx.reserve(n + 8 * ins)
+        X = synthetic.inserts(c, 8 * ins)
+        res["serving"] = serving_measure(pg, idx, Q, X, ins, k, 64, 16)
+        idx.close()
+    res["autotune"] = pg.autotune_report().splitlines()
+    print(json.dumps(res), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.sweep:
         run_sweep(args)
+    elif args.extra:
+        run_extra(args)
     else:
         run_ours(args)
 
