@@ -687,7 +687,11 @@ def run_ours(args):
                     continue
                 with open(os.path.join(ROOT, ent["source"]), "rb") as f:
                     if hashlib.sha256(f.read()).hexdigest() == ent["source_sha256"]:
-                        r["traffic"] = ent["dram_bytes_per_launch"]
+                        # per launch where `achieved` is one launch's, per step
+                        # where it is summed over the step's launches
+                        r["traffic"] = ent.get("dram_bytes_per_launch",
+                                               ent.get("dram_bytes_per_step"))
+                        r["traffic_per"] = "launch" if "dram_bytes_per_launch" in ent else "step"
                         r["traffic_note"] = ent["note"]
         except (OSError, ValueError, KeyError):
             pass
