@@ -337,7 +337,8 @@ __global__ void __launch_bounds__(tc_threads(H, QT), 1)
 k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUtensorMap mapX,
          const __nv_bfloat16 *__restrict__ qrows, int64_t nq, int64_t n, int dp,
          const float *__restrict__ qnorm,
-         const float *__restrict__ xnorm, int K, int self_exclude, int32_t *__restrict__ out_i,
+         const float *__restrict__ xnorm, const float *__restrict__ xcmin, int K,
+         int self_exclude, int32_t *__restrict__ out_i,
          float *__restrict__ out_s, int *err, const int32_t *__restrict__ perm, int rotate,
          unsigned long long *progress, int resident) {
     extern __shared__ uint8_t smem_raw[];
@@ -576,18 +577,28 @@ k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUten
             const int64_t col = (int64_t)tile_at(t) * TN + c * 32 + lane;
             return col < n ? xnorm[col] : INFINITY;
         };
-        float nxt[NCH];
+        // the smallest column norm of each 32-column chunk (one value for the
+        // whole warp), also one tile ahead
+        auto chunkmin = [&](int t, int c) -> float {
+            return t < ntiles ? xcmin[(int64_t)tile_at(t) * (TN / 32) + c] : INFINITY;
+        };
+        float nxt[NCH], nxm[NCH];
 #pragma unroll
-        for (int ci = 0; ci < NCH; ++ci) nxt[ci] = colnorm(0, c_lo + ci);
+        for (int ci = 0; ci < NCH; ++ci) {
+            nxt[ci] = colnorm(0, c_lo + ci);
+            nxm[ci] = chunkmin(0, c_lo + ci);
+        }
         for (int t = 0; t < ntiles; ++t) {
             // the buffer of pair QT t + qt; this group's (t / NACC)-th use of it
             const int a = (QT * t + qt) % NACC;
             const int64_t colbase = (int64_t)tile_at(t) * TN;
-            float cur[NCH];
+            float cur[NCH], cum[NCH];
 #pragma unroll
             for (int ci = 0; ci < NCH; ++ci) {
                 cur[ci] = nxt[ci];
+                cum[ci] = nxm[ci];
                 nxt[ci] = colnorm(t + 1, c_lo + ci);
+                nxm[ci] = chunkmin(t + 1, c_lo + ci);
             }
             mbar_wait(acc_full + a * QT + qt, (t / NACC) & 1, abort, err);
             // a warp that sees the abort leaves; the others leave at their
@@ -597,11 +608,25 @@ k_knn_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUten
 #pragma unroll
             for (int ci = 0; ci < NCH; ++ci) {
                 const int c = c_lo + ci;
+                __syncwarp();  // lanes that pushed into their heaps rejoin before the load
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * TN + c * 32), v);
+                // lower bound of the chunk's distances for this row: |q|^2 +
+                // (smallest column norm) - 2 (largest dot product).  Every
+                // operation is correctly rounded, hence monotone, so the bound
+                // never exceeds a column's computed distance: a chunk whose
+                // bound is above the K-th distance holds no candidate, and
+                // most chunks are dismissed by it without the column norms.
+                float vx[4] = {v[0], v[1], v[2], v[3]};
+#pragma unroll
+                for (int j = 4; j < 32; ++j) vx[j & 3] = fmaxf(vx[j & 3], v[j]);
+                const float vmax = fmaxf(fmaxf(vx[0], vx[1]), fmaxf(vx[2], vx[3]));
+                const bool need = live && nqr + fmaf(-2.f, vmax, cum[ci]) <= thr;
+                if (!__any_sync(0xffffffffu, need)) continue;
                 __syncwarp();
                 wn[lane] = cur[ci];
                 __syncwarp();
-                float v[32];
-                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * TN + c * 32), v);
+                if (!need) continue;
                 float nbv[32];
                 const float4 *nb4 = reinterpret_cast<const float4 *>(wn);
 #pragma unroll
@@ -1011,6 +1036,15 @@ __global__ void k_gather_f32(const float *__restrict__ src, const int32_t *__res
     if (t < m) dst[t] = src[idx[t]];
 }
 
+// smallest of each 32 consecutive column norms (+inf past n)
+__global__ void k_chunk_min(const float *__restrict__ xn, int64_t n, int64_t nch, float *out) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nch) return;
+    float m = INFINITY;
+    for (int64_t i = c * 32; i < min(n, c * 32 + 32); ++i) m = fminf(m, xn[i]);
+    out[c] = m;
+}
+
 __global__ void k_pivot_ids(int32_t *ids, int p, int64_t n) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < p) ids[t] = (int32_t)((int64_t)t * n / p);
@@ -1060,22 +1094,28 @@ static pg_status tc_knn_run(pg_ctx *ctx, Scratch<__nv_bfloat16> &xc,
                       const float *xn_, int K_, int self_, int32_t *oi, float *os,
                       const int32_t *perm_, int rot) -> pg_status {
         PG_TRY_CUDA(ctx, cudaMemsetAsync(prog.p, 0, 8, ctx->stream));
+        // chunk minima of the candidates' norms, padded to whole tiles
+        const int64_t nch = (n_ + TN - 1) / TN * (TN / 32);
+        Scratch<float> cmin;
+        PG_TRY(cmin.alloc(ctx, (size_t)nch));
+        k_chunk_min<<<(unsigned)((nch + 255) / 256), 256, 0, ctx->stream>>>(xn_, n_, nch, cmin.p);
+        PG_LAUNCHED(ctx);
         const int res = ctx->num_sms;  // one CTA per SM (shared memory)
         if (V.KB)
             k_knn_tc<1, true, 1><<<grid, tc_threads(1), smem, ctx->stream>>>(
-                mq_, mx_, qrows_, nq_, n_, dp, qn_, xn_, K_, self_, oi, os, ctx->d_err, perm_, rot,
+                mq_, mx_, qrows_, nq_, n_, dp, qn_, xn_, cmin.p, K_, self_, oi, os, ctx->d_err, perm_, rot,
                 prog.p, res);
         else if (V.QT == 2)
             k_knn_tc<1, false, 2><<<grid, tc_threads(1, 2), smem, ctx->stream>>>(
-                mq_, mx_, qrows_, nq_, n_, dp, qn_, xn_, K_, self_, oi, os, ctx->d_err, perm_, rot,
+                mq_, mx_, qrows_, nq_, n_, dp, qn_, xn_, cmin.p, K_, self_, oi, os, ctx->d_err, perm_, rot,
                 prog.p, res);
         else if (V.H == 2)
             k_knn_tc<2, false, 1><<<grid, tc_threads(2), smem, ctx->stream>>>(
-                mq_, mx_, qrows_, nq_, n_, dp, qn_, xn_, K_, self_, oi, os, ctx->d_err, perm_, rot,
+                mq_, mx_, qrows_, nq_, n_, dp, qn_, xn_, cmin.p, K_, self_, oi, os, ctx->d_err, perm_, rot,
                 prog.p, res);
         else
             k_knn_tc<1, false, 1><<<grid, tc_threads(1), smem, ctx->stream>>>(
-                mq_, mx_, qrows_, nq_, n_, dp, qn_, xn_, K_, self_, oi, os, ctx->d_err, perm_, rot,
+                mq_, mx_, qrows_, nq_, n_, dp, qn_, xn_, cmin.p, K_, self_, oi, os, ctx->d_err, perm_, rot,
                 prog.p, res);
         return PG_OK;
     };
