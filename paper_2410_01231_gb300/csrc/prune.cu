@@ -276,16 +276,7 @@ __device__ void prune_row(const PruneParams &P, int64_t row, const int32_t *cand
 #pragma unroll
         for (int c = 0; c < 8; ++c) kr[c] = make_uint4(0u, 0u, 0u, 0u);
         float ksl = 0.f;  // s(u, w) of this lane's kept point
-        int knrm = 0;       // |w|^2 of this lane's kept point
         bool kold = false;  // this lane's kept point is in N_prev(u) (K2P)
-        // s(v, w) = |v|^2 + |w|^2 - 2 <v, w> in integers (exact: at most
-        // 2 x 128 x 255^2 < 2^31), one __dp4a per four bytes
-        auto dot_u8 = [](uint4 a, uint4 b, unsigned acc) {
-            acc = __dp4a(a.x, b.x, acc);
-            acc = __dp4a(a.y, b.y, acc);
-            acc = __dp4a(a.z, b.z, acc);
-            return __dp4a(a.w, b.w, acc);
-        };
         for (; j < m && kept < P.R; ++j) {
             const int v = ci[j];
             const float suv = cs[j];
@@ -295,24 +286,17 @@ __device__ void prune_row(const PruneParams &P, int64_t row, const int32_t *cand
             const bool work = mine && ksl < suv;
             bool occ = false;
             const bool loaded = __any_sync(0xffffffffu, work);
-            int vn = 0;  // |v|^2, once the row is loaded
             if (loaded) {
-                unsigned pn = 0;
-                if (lane < nch16) {
-                    const uint4 x = __ldg(reinterpret_cast<const uint4 *>(D8 + (int64_t)v * d) + lane);
-                    vrow[lane] = x;
-                    pn = dot_u8(x, x, 0u);
-                }
-                pn = team8_sum_u(pn);  // lanes 0-7 hold the row's chunks
-                vn = (int)__shfl_sync(0xffffffffu, pn, 0);
+                if (lane < nch16)
+                    vrow[lane] = __ldg(reinterpret_cast<const uint4 *>(D8 + (int64_t)v * d) + lane);
                 __syncwarp();
             }
             if (work) {  // exact data: the comparisons are exact
                 unsigned acc = 0;
 #pragma unroll
                 for (int c = 0; c < 8; ++c)
-                    if (c < nch16) acc = dot_u8(vrow[c], kr[c], acc);
-                const float svw = (float)(vn + knrm - 2 * (int)acc);
+                    if (c < nch16) acc = sq_diff_u8(vrow[c], kr[c], acc);
+                const float svw = (float)acc;
                 st.tests++;
                 if (P.count_ties && near_tie(svw, suv)) st.ties++;
                 if (svw < suv) {
@@ -338,17 +322,11 @@ __device__ void prune_row(const PruneParams &P, int64_t row, const int32_t *cand
 #pragma unroll
                         for (int c = 0; c < 8; ++c)
                             if (c < nch16) kr[c] = vrow[c];
-                        knrm = vn;
                     } else {
                         const uint4 *xv = reinterpret_cast<const uint4 *>(D8 + (int64_t)v * d);
-                        unsigned kn = 0;
 #pragma unroll
                         for (int c = 0; c < 8; ++c)
-                            if (c < nch16) {
-                                kr[c] = __ldg(xv + c);
-                                kn = dot_u8(kr[c], kr[c], kn);
-                            }
-                        knrm = (int)kn;
+                            if (c < nch16) kr[c] = __ldg(xv + c);
                     }
                     ksl = suv;
                     kold = vold;

@@ -423,7 +423,26 @@ __device__ void search_one(const SearchParams &P, int64_t qi, unsigned char *ws,
             const unsigned live = __ballot_sync(0xffffffffu, id != INT_MAX);
             const int m2 = __popc(live);
             if (m2 == 0) continue;
-            if (m2 > 1) {
+            if (m2 > 1 && !cert && m2 <= 8) {
+                // few survivors: each takes its rank among them (ids are
+                // distinct, so (s, id) orders them strictly) and lane r then
+                // reads the survivor of rank r back from the staging area
+                int rank = 0;
+                for (unsigned bits = live; bits; bits &= bits - 1) {
+                    const int b = __ffs(bits) - 1;
+                    const float os = __shfl_sync(0xffffffffu, s, b);
+                    const int oi = __shfl_sync(0xffffffffu, id, b);
+                    rank += pair_less(os, oi, s, id) ? 1 : 0;
+                }
+                __syncwarp();
+                if (id != INT_MAX) {
+                    nd[rank] = s;
+                    ni[rank] = id;
+                }
+                __syncwarp();
+                s = lane < m2 ? nd[lane] : INFINITY;
+                id = lane < m2 ? ni[lane] : INT_MAX;
+            } else if (m2 > 1) {
                 if (cert) warp_sort32_exact(X, s, s64, id, cpos);
                 else warp_sort32(s, id);  // survivors first, ascending
             } else {
