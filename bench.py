@@ -642,6 +642,7 @@ def run_ours(args):
     # Kernels timed inside a seconds-long build take the sustained peaks.
     pk = peaks()
     hbm = pk.get("hbm_gbs", 6800.0)
+    pk_sms = torch.cuda.get_device_properties(0).multi_processor_count
 
     def rooflines_of(run, form):
         out = {}
@@ -693,6 +694,23 @@ def run_ours(args):
                                                ent.get("dram_bytes_per_step"))
                         r["traffic_per"] = "launch" if "dram_bytes_per_launch" in ent else "step"
                         r["traffic_note"] = ent["note"]
+                        # issue-bound kernels: the step's warp instructions (ncu)
+                        # against the issue rate of every SM sub-partition at
+                        # the clock sampled in the timed region
+                        w = ent.get("warp_instructions_per_step")
+                        name = {"k_search": "search", "k_prune": "prune"}.get(r["kernel"])
+                        mhz = (run.get("clocks") or {}).get("sm_mhz")
+                        if w and name and mhz:
+                            t_s = run["kt"][name][0] / steps / 1e3
+                            unit, per = (("evaluation", run["work"]["search_evaluations"])
+                                         if name == "search" else
+                                         ("candidate", run["work"]["prune_candidates"]))
+                            r["issue"] = {
+                                "warp_instructions_per_step": w,
+                                f"warp_instructions_per_{unit}": w / (per / steps) if per else None,
+                                "issue_rate_frac": w / (t_s * 4 * pk_sms * mhz * 1e6),
+                                "note": ("warp instructions from the same ncu capture; the peak is "
+                                         "one warp instruction per cycle per SM sub-partition")}
         except (OSError, ValueError, KeyError):
             pass
         return out
