@@ -912,7 +912,7 @@ static pg_status connect_exact(pg_ctx *ctx, const float *D, int64_t n, int32_t d
                                int32_t *deg, int32_t R, int *reached, int *queue,
                                const ConnState *init, int64_t *host_added) {
     TcArgmin tc;
-    PG_TRY(pg_tc_argmin_init(ctx, D, n, d, tc));
+    PG_TRY(pg_tc_argmin_init(ctx, D, n, d, deg, R, tc));
     Scratch<ConnX> st;
     Scratch<int> comp;
     PG_TRY(st.alloc(ctx, 1));

@@ -28,6 +28,7 @@
 #include <cuda.h>
 
 #include <climits>
+#include <cstring>
 
 #include "pg_internal.cuh"
 
@@ -763,7 +764,8 @@ __host__ __device__ inline ArgLayout arg_layout(int dp) {
 __global__ void __launch_bounds__(NTHREADS, 1)
 k_argmin_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUtensorMap mapX,
             const int *__restrict__ nrows_p, int64_t n, int dp, const float *__restrict__ qnorm,
-            const float *__restrict__ xnorm, const int *__restrict__ reached,
+            const float *__restrict__ xnorm, const int *__restrict__ cid,
+            const int *__restrict__ reached,
             const int32_t *__restrict__ deg, int R, int tiles_per_cta,
             unsigned long long *__restrict__ best, int *err) {
     const int ntiles_all = (int)((n + TN - 1) / TN);
@@ -871,8 +873,9 @@ k_argmin_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CU
         auto colval = [&](int t) -> float {
             const int64_t c = (int64_t)(t0 + t) * TN + row;
             if (t >= ntiles || c >= n) return INFINITY;
-            const int rc = reached[c];
-            const int dc = deg[c];
+            const int x = cid[c];
+            const int rc = reached[x];
+            const int dc = deg[x];
             const float xc = xnorm[c];
             return (rc && dc < R) ? xc : INFINITY;
         };
@@ -900,7 +903,7 @@ k_argmin_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CU
                     for (int j = 31; j >= 0; --j)
                         if (fmaf(-2.f, v[j], nbuf[a * TN + c * 32 + j]) == m) jm = j;
                     bs = nqr + m;
-                    bid = (int)(colbase + c * 32 + jm);
+                    bid = cid[colbase + c * 32 + jm];  // ascending ids: ties keep the smallest
                 }
             }
             tc_fence_before();
@@ -918,6 +921,35 @@ k_argmin_tc(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CU
                      "r"(ACC_COLS)
                      : "memory");
     }
+}
+
+__global__ void k_free_flags(const int32_t *deg, int64_t n, int R, int32_t *flag) {
+    const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x < n) flag[x] = deg[x] < R ? 1 : 0;
+}
+
+__global__ void k_free_scatter(const int32_t *flag, const int64_t *off, int64_t n, int *cid) {
+    const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x < n && flag[x]) cid[off[x]] = (int)x;
+}
+
+// rows ids[0..m) of D to BF16 [m][dp] (zero padded) with their FP32
+// squared norms; one warp per row
+__global__ void k_gather_bf16_rows(const float *__restrict__ D, int d, int dp, const int *ids,
+                                   int64_t m, __nv_bfloat16 *__restrict__ out,
+                                   float *__restrict__ norms) {
+    const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x & 31;
+    if (row >= m) return;
+    const float *src = D + (int64_t)ids[row] * d;
+    float acc = 0.f;
+    for (int c = lane; c < dp; c += 32) {
+        const float x = c < d ? src[c] : 0.f;
+        acc = fmaf(x, x, acc);
+        out[row * dp + c] = __float2bfloat16_rn(x);
+    }
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) norms[row] = acc;
 }
 
 // <= 128 rows ids[0..*count) of D to BF16 [128][dp] (zero rows past the
@@ -1227,20 +1259,40 @@ bool pg_tc_argmin_supported(int d) {
     return dp <= 256 && arg_layout(dp).total + 1024 <= 227 * 1024;
 }
 
-pg_status pg_tc_argmin_init(pg_ctx *ctx, const float *D, int64_t n, int32_t d, TcArgmin &t) {
-    t.n = n;
+pg_status pg_tc_argmin_init(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
+                            const int32_t *deg, int R, TcArgmin &t) {
     t.d = d;
     t.dp = (d + 63) / 64 * 64;
-    PG_TRY(t.xb.alloc(ctx, (size_t)(n * t.dp)));
-    PG_TRY(t.xn.alloc(ctx, (size_t)n));
+    // the points with a free slot, in ascending id order (flags, scan, scatter)
+    Scratch<int32_t> flag;
+    Scratch<int64_t> off;
+    PG_TRY(flag.alloc(ctx, (size_t)n));
+    PG_TRY(off.alloc(ctx, (size_t)n + 1));
+    k_free_flags<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(deg, n, R, flag.p);
+    PG_LAUNCHED(ctx);
+    PG_TRY(pg_scan_counts(ctx, flag.p, n, off.p));
+    PG_TRY_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned, off.p + n, sizeof(int64_t),
+                                     cudaMemcpyDeviceToHost, ctx->stream));
+    PG_TRY(pg_sync_check(ctx, "argmin candidates"));
+    int64_t m = 0;
+    memcpy(&m, ctx->h_pinned, sizeof m);
+    t.n = m;
+    const int64_t ma = std::max<int64_t>(m, 1);  // a tensor map needs a row
+    PG_TRY(t.cid.alloc(ctx, (size_t)ma));
+    PG_TRY(t.xb.alloc(ctx, (size_t)(ma * t.dp)));
+    PG_TRY(t.xn.alloc(ctx, (size_t)ma));
     PG_TRY(t.qb.alloc(ctx, (size_t)TM * t.dp));
     PG_TRY(t.qn.alloc(ctx, (size_t)TM));
-    k_to_bf16<<<(unsigned)((n * t.dp + 255) / 256), 256, 0, ctx->stream>>>(D, n, d, t.dp, t.xb.p);
+    if (m == 0) PG_TRY_CUDA(ctx, cudaMemsetAsync(t.xb.p, 0, (size_t)t.dp * 2, ctx->stream));
+    k_free_scatter<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(flag.p, off.p, n, t.cid.p);
     PG_LAUNCHED(ctx);
-    k_tc_norms<<<(unsigned)((n + 7) / 8), 256, 0, ctx->stream>>>(D, n, d, t.xn.p);
-    PG_LAUNCHED(ctx);
+    if (m > 0) {
+        k_gather_bf16_rows<<<(unsigned)((m + 7) / 8), 256, 0, ctx->stream>>>(D, d, t.dp, t.cid.p, m,
+                                                                             t.xb.p, t.xn.p);
+        PG_LAUNCHED(ctx);
+    }
     static_assert(sizeof(t.mapx) >= sizeof(CUtensorMap), "tensor map storage");
-    PG_TRY(make_map(ctx, reinterpret_cast<CUtensorMap *>(t.mapx), t.xb.p, n, t.dp));
+    PG_TRY(make_map(ctx, reinterpret_cast<CUtensorMap *>(t.mapx), t.xb.p, ma, t.dp));
     PG_TRY(make_map(ctx, reinterpret_cast<CUtensorMap *>(t.mapq), t.qb.p, TM, t.dp));
     const size_t smem = arg_layout(t.dp).total + 1024;
     PG_TRY_CUDA(ctx, cudaFuncSetAttribute(k_argmin_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1258,7 +1310,7 @@ pg_status pg_tc_argmin(pg_ctx *ctx, TcArgmin &t, const float *D, const int *ids,
     const size_t smem = arg_layout(t.dp).total + 1024;
     k_argmin_tc<<<(unsigned)grid, NTHREADS, smem, ctx->stream>>>(
         *reinterpret_cast<const CUtensorMap *>(t.mapq), *reinterpret_cast<const CUtensorMap *>(t.mapx),
-        count, t.n, t.dp, t.qn.p, t.xn.p, reached, deg, R, per, best, ctx->d_err);
+        count, t.n, t.dp, t.qn.p, t.xn.p, t.cid.p, reached, deg, R, per, best, ctx->d_err);
     PG_LAUNCHED(ctx);
     return PG_OK;
 }

@@ -314,8 +314,9 @@ inline bool pg_build_precision(pg_precision p) {
 // deg[c] < R of key(s(D[ids[i]], D[c]), c) for i < *count (device), where
 // key = FP32 bits << 32 | c; best[] must hold ~0 beforehand.
 struct TcArgmin {
-    Scratch<__nv_bfloat16> xb;  // BF16 copy of D, rows padded to dp
-    Scratch<float> xn;          // squared row norms
+    Scratch<__nv_bfloat16> xb;  // BF16 copy of the candidate rows of D, padded to dp
+    Scratch<float> xn;          // their squared row norms
+    Scratch<int> cid;           // candidate column -> point id (ascending)
     Scratch<__nv_bfloat16> qb;  // the <= 128 query rows
     Scratch<float> qn;
     alignas(64) unsigned char mapx[128];  // CUtensorMap of xb
@@ -324,7 +325,11 @@ struct TcArgmin {
     int d = 0, dp = 0;
 };
 bool pg_tc_argmin_supported(int d);
-pg_status pg_tc_argmin_init(pg_ctx *ctx, const float *D, int64_t n, int32_t d, TcArgmin &t);
+// The candidate columns are the points with deg < R when this is called
+// (degrees only grow during the connectivity step, so no later candidate
+// is missing); synchronises the stream once to size the copies.
+pg_status pg_tc_argmin_init(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
+                            const int32_t *deg, int R, TcArgmin &t);
 pg_status pg_tc_argmin(pg_ctx *ctx, TcArgmin &t, const float *D, const int *ids, const int *count,
                        const int *reached, const int32_t *deg, int R, unsigned long long *best);
 
