@@ -140,7 +140,72 @@ k_knn_fp32(const float *__restrict__ Q, int64_t nq, const float *__restrict__ X,
     __syncthreads();
 
     const int nkb = (d + BK - 1) / BK;
+    // The next k-block of A and B is read into registers while the current
+    // one is multiplied from shared memory (the last block of a column tile
+    // prefetches the first block of the next tile); the per-accumulator
+    // summation order is unchanged.
+    float4 ra[2], rb[2][2];
+    auto load_tiles = [&](int64_t c0, int kb) {
+        const int k0 = kb * BK;
+        {
+            const int r = tid >> 2, kq = tid & 3;
+            const int64_t g = row0 + r;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int kk = kq * 4 + h * 16;
+                ra[h] = (g < nq && k0 + kk < d)
+                            ? *reinterpret_cast<const float4 *>(Q + g * d + k0 + kk)
+                            : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int r = (tid >> 2) + h * 64, kq = tid & 3;
+            const int64_t g = c0 + r;
+#pragma unroll
+            for (int h2 = 0; h2 < 2; ++h2) {
+                const int kk = kq * 4 + h2 * 16;
+                rb[h][h2] = (g < n && k0 + kk < d)
+                                ? __ldg(reinterpret_cast<const float4 *>(X + g * d + k0 + kk))
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+    };
+    auto store_tiles = [&]() {
+        {
+            const int r = tid >> 2, kq = tid & 3;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int kk = kq * 4 + h * 16;
+                sm.As[kk + 0][r] = ra[h].x;
+                sm.As[kk + 1][r] = ra[h].y;
+                sm.As[kk + 2][r] = ra[h].z;
+                sm.As[kk + 3][r] = ra[h].w;
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int r = (tid >> 2) + h * 64, kq = tid & 3;
+#pragma unroll
+            for (int h2 = 0; h2 < 2; ++h2) {
+                const int kk = kq * 4 + h2 * 16;
+                sm.Bs[kk + 0][r] = rb[h][h2].x;
+                sm.Bs[kk + 1][r] = rb[h][h2].y;
+                sm.Bs[kk + 2][r] = rb[h][h2].z;
+                sm.Bs[kk + 3][r] = rb[h][h2].w;
+            }
+        }
+    };
+    load_tiles(0, 0);
     for (int64_t col0 = 0; col0 < n; col0 += BN) {
+        // column norms of this thread's eight columns, read before the tile
+        float xnv[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int cl = (j < 4) ? tx * 4 + j : 64 + tx * 4 + (j - 4);
+            const int64_t gc = col0 + cl;
+            xnv[j] = metric == 0 ? xnorm[gc < n ? gc : 0] : 0.f;
+        }
         float acc[4][8];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
@@ -148,41 +213,10 @@ k_knn_fp32(const float *__restrict__ Q, int64_t nq, const float *__restrict__ X,
             for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
 
         for (int kb = 0; kb < nkb; ++kb) {
-            const int k0 = kb * BK;
-            // A tile: 64 rows x 32 k, 4 threads per row, 2 float4 each
-            {
-                int r = tid >> 2, kq = tid & 3;
-                int64_t g = row0 + r;
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    int kk = kq * 4 + h * 16;
-                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (g < nq && k0 + kk < d)
-                        v = *reinterpret_cast<const float4 *>(Q + g * d + k0 + kk);
-                    sm.As[kk + 0][r] = v.x;
-                    sm.As[kk + 1][r] = v.y;
-                    sm.As[kk + 2][r] = v.z;
-                    sm.As[kk + 3][r] = v.w;
-                }
-            }
-            // B tile: 128 cols x 32 k
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                int r = (tid >> 2) + h * 64, kq = tid & 3;
-                int64_t g = col0 + r;
-#pragma unroll
-                for (int h2 = 0; h2 < 2; ++h2) {
-                    int kk = kq * 4 + h2 * 16;
-                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (g < n && k0 + kk < d)
-                        v = __ldg(reinterpret_cast<const float4 *>(X + g * d + k0 + kk));
-                    sm.Bs[kk + 0][r] = v.x;
-                    sm.Bs[kk + 1][r] = v.y;
-                    sm.Bs[kk + 2][r] = v.z;
-                    sm.Bs[kk + 3][r] = v.w;
-                }
-            }
+            store_tiles();
             __syncthreads();
+            if (kb + 1 < nkb) load_tiles(col0, kb + 1);
+            else if (col0 + BN < n) load_tiles(col0 + BN, 0);
 #pragma unroll 8
             for (int k = 0; k < BK; ++k) {
                 float4 a = *reinterpret_cast<const float4 *>(&sm.As[k][ty * 4]);
@@ -212,7 +246,7 @@ k_knn_fp32(const float *__restrict__ Q, int64_t nq, const float *__restrict__ X,
                 int cl = (j < 4) ? tx * 4 + j : 64 + tx * 4 + (j - 4);
                 int64_t gc = col0 + cl;
                 float s;
-                if (metric == 0) s = fmaxf(sm.qn[r] + xnorm[gc < n ? gc : 0] - 2.f * acc[i][j], 0.f);
+                if (metric == 0) s = fmaxf(sm.qn[r] + xnv[j] - 2.f * acc[i][j], 0.f);
                 else s = fmaxf(2.f - 2.f * acc[i][j], 0.f);
                 dv[i][j] = s;
                 bool ok = g < nq && gc < n && !(self_exclude && gc == g) && s <= thr;
