@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-queries", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-screen", action="store_true")
+    ap.add_argument("--no-quality", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="fixed launch configurations (no tuning launches, for ncu captures)")
     ap.add_argument("--sweep", action="store_true",
@@ -591,6 +592,22 @@ def run_ours(args):
         a.close()
         b.close()
 
+    # ------------------------------------------- quality examination
+    # One more (untimed) build with the quality examination of Section 5.2 on
+    # (Theorem 3's sample, eps 0.6, recall of the first K entries of C(u)):
+    # the loop of Algorithm 6 stops once the sampled k-CNA recall reaches the
+    # target, at most `iters` iterations; the iterations it chose and its
+    # estimates after each are reported.
+    quality = None
+    if not args.no_quality:
+        target = 0.999
+        qb = pg.Index.build_rng(ctx, Dd, **dict(params, quality_target=target, quality_eps=0.6))
+        it_run, ns, est = qb.quality()
+        qb.close()
+        quality = {"target": target, "eps": 0.6, "sample_size": ns, "iterations_run": it_run,
+                   "iterations_max": params["iters"], "estimates": est,
+                   "note": "k-CNA recall of the first K entries of C(u) on the Theorem 3 sample"}
+
     # --------------------------------------------------------- tie budget
     # One more (untimed) build of the main form with the pruning kernels'
     # tie accounting on: decisions of the occlusion test whose relative
@@ -769,6 +786,7 @@ def run_ours(args):
                           else f"inputs smaller than L2 ({D.nbytes >> 20} MB points; test size)"),
                    "parallelism": "replicas"},
         "forms": forms, "forms_identical_graph": identical, "tie_budget": tie,
+        "quality_examination": quality,
         "queries": qres, "serving": serve, "real_rows_d960": screen, "phase_s": phases_mean,
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
         "kernel_launches_per_step": {k: v[1] / args.steps for k, v in kt.items()},
