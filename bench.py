@@ -600,7 +600,7 @@ def run_ours(args):
     # estimates after each are reported.
     quality = None
     if not args.no_quality:
-        target = 0.999
+        target = 0.99
         qb = pg.Index.build_rng(ctx, Dd, **dict(params, quality_target=target, quality_eps=0.6))
         it_run, ns, est = qb.quality()
         qb.close()

@@ -113,6 +113,7 @@ __device__ void merge_row(KnnSmem &sm, int r, int wid, int K, float *top_s, int 
 }
 
 // self_exclude: column id == query row id is skipped (Q == D).
+static_assert(BM == 8 * (NT / 32) && BN == 128, "warp w owns rows 8w .. 8w + 7 over all columns");
 __global__ void __launch_bounds__(NT, 2)
 k_knn_fp32(const float *__restrict__ Q, int64_t nq, const float *__restrict__ X, int64_t n, int d,
            const float *__restrict__ qnorm, const float *__restrict__ xnorm, int metric, int K,
@@ -257,15 +258,18 @@ k_knn_fp32(const float *__restrict__ Q, int64_t nq, const float *__restrict__ X,
             }
             if (np) atomicAdd(&sm.pend[r], np);
         }
-        __syncthreads();
+        // warp wid holds every column of rows 8 wid .. 8 wid + 7 (its two ty
+        // values), so their buffers, counts and thresholds are its own: the
+        // filter, the merges and the appends synchronise the warp only
+        __syncwarp();
         // merge rows that could overflow
-        for (int r = wid; r < BM; r += NT / 32) {
+        for (int r = 8 * wid; r < 8 * wid + 8; ++r) {
             if (sm.cnt[r] + sm.pend[r] > BUF) {
                 int64_t g = row0 + r;
                 merge_row(sm, r, wid, K, out_s + g * K, out_i + g * K);
             }
         }
-        __syncthreads();
+        __syncwarp();
         // append survivors (re-test: a merge may have lowered the threshold)
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -282,15 +286,15 @@ k_knn_fp32(const float *__restrict__ Q, int64_t nq, const float *__restrict__ X,
                 sm.buf_i[r][slot] = (int)(col0 + cl);
             }
         }
-        __syncthreads();
-        for (int r = tid; r < BM; r += NT) sm.pend[r] = 0;
+        __syncwarp();
+        if (lane < 8) sm.pend[8 * wid + lane] = 0;
+        __syncwarp();
     }
     __syncthreads();
     for (int r = wid; r < BM; r += NT / 32) {
         int64_t g = row0 + r;
         if (g < nq) merge_row(sm, r, wid, K, out_s + g * K, out_i + g * K);
     }
-    (void)lane;
 }
 
 // Re-order near-tie runs of each sorted row by FP64 distance (one warp per
