@@ -153,36 +153,6 @@ __global__ void k_bfs_level(const int32_t *nbr, const int32_t *deg, int R, int64
     }
 }
 
-// Reachability finished by one block once the frontier is small: the
-// frontier fin[0..fcount) is copied to q and everything it reaches through
-// unreached nodes is appended behind it (at most n entries in all), so a
-// long thin graph takes one launch instead of one host round trip per level.
-__global__ void __launch_bounds__(1024) k_bfs_finish(const int32_t *nbr, const int32_t *deg, int R,
-                                                     int64_t n, int *reached, const int *fin,
-                                                     int fcount, int *q) {
-    __shared__ int s_tail;
-    for (int i = threadIdx.x; i < fcount; i += blockDim.x) q[i] = fin[i];
-    if (threadIdx.x == 0) s_tail = fcount;
-    __syncthreads();
-    int head = 0, tail = fcount;
-    while (head < tail) {
-        // one (node, edge) pair per thread
-        const int64_t pairs = (int64_t)(tail - head) * R;
-        for (int64_t t = threadIdx.x; t < pairs; t += blockDim.x) {
-            const int x = q[head + (int)(t / R)];
-            const int j = (int)(t % R);
-            if (j >= min(deg[x], R)) continue;
-            const int y = nbr[(int64_t)x * R + j];
-            if (y < 0 || y >= n || reached[y]) continue;
-            if (atomicCAS(&reached[y], 0, 1) == 0) q[atomicAdd(&s_tail, 1)] = y;
-        }
-        __syncthreads();
-        head = tail;
-        tail = s_tail;
-        __syncthreads();
-    }
-}
-
 // nodes that have a free slot when the step begins
 __global__ void k_free_list(const int32_t *deg, int64_t n, int R, int *list, ConnState *st) {
     int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1038,34 +1008,6 @@ static pg_status connect_exact(pg_ctx *ctx, const float *D, int64_t n, int32_t d
     }
 }
 
-// Reachability from the frontier fa[0] (one node, already marked): level by
-// level over the whole grid while the frontier is wide; once it has stayed
-// below 4,096 nodes for 8 levels (a long thin part of the graph, or the
-// tail) one block finishes it in a single launch.  fa and fb are disjoint
-// buffers of n ints each.  Only the reached set is used afterwards.
-static pg_status reach_levels(pg_ctx *ctx, const int32_t *nbr, const int32_t *deg, int R,
-                              int64_t n, int *reached, int *fa, int *fb, int *fcnt) {
-    int fcount = 1, small = 0;
-    while (fcount > 0) {
-        small = fcount < 4096 ? small + 1 : 0;
-        if (small > 8) {
-            k_bfs_finish<<<1, 1024, 0, ctx->stream>>>(nbr, deg, R, n, reached, fa, fcount, fb);
-            PG_LAUNCHED(ctx);
-            return PG_OK;
-        }
-        PG_TRY_CUDA(ctx, cudaMemsetAsync(fcnt, 0, sizeof(int), ctx->stream));
-        k_bfs_level<<<(fcount + 255) / 256, 256, 0, ctx->stream>>>(nbr, deg, R, n, reached, fa,
-                                                                   fcount, fb, fcnt);
-        PG_LAUNCHED(ctx);
-        PG_TRY_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned, fcnt, sizeof(int), cudaMemcpyDeviceToHost,
-                                         ctx->stream));
-        PG_TRY_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-        memcpy(&fcount, ctx->h_pinned, sizeof(int));
-        std::swap(fa, fb);
-    }
-    return PG_OK;
-}
-
 pg_status pg_connect_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d, pg_metric metric,
                               int32_t *nbr, int32_t *deg, int32_t R, int64_t ep,
                               const DataFacts &facts, const int32_t *knn, int32_t K,
@@ -1090,7 +1032,18 @@ pg_status pg_connect_internal(pg_ctx *ctx, const float *D, int64_t n, int32_t d,
     PG_TRY_CUDA(ctx, cudaMemcpyAsync(queue.p, &epi, sizeof(int), cudaMemcpyHostToDevice,
                                      ctx->stream));
     int *fa = queue.p, *fb = queue.p + n;
-    PG_TRY(reach_levels(ctx, nbr, deg, R, n, reached.p, fa, fb, fcnt.p));
+    int fcount = 1;
+    while (fcount > 0) {
+        PG_TRY_CUDA(ctx, cudaMemsetAsync(fcnt.p, 0, sizeof(int), ctx->stream));
+        k_bfs_level<<<(fcount + 255) / 256, 256, 0, ctx->stream>>>(nbr, deg, R, n, reached.p, fa,
+                                                                   fcount, fb, fcnt.p);
+        PG_LAUNCHED(ctx);
+        PG_TRY_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned, fcnt.p, sizeof(int),
+                                         cudaMemcpyDeviceToHost, ctx->stream));
+        PG_TRY_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        memcpy(&fcount, ctx->h_pinned, sizeof(int));
+        std::swap(fa, fb);
+    }
     k_connect_init<<<1, CT, 0, ctx->stream>>>(n, reached.p, st.p);
     PG_LAUNCHED(ctx);
     if (metric == PG_METRIC_L2SQ && facts.exact && facts.bf16_exact && pg_tc_argmin_supported(d)) {
@@ -1308,7 +1261,19 @@ pg_status pg_connect_replace_internal(pg_ctx *ctx, const float *D, int64_t n, in
         PG_TRY_CUDA(ctx, cudaMemsetAsync(reached.p, 0, (size_t)n * 4, ctx->stream));
         k_rep_mark<<<1, 32, 0, ctx->stream>>>(reached.p, ep, queue.p);
         PG_LAUNCHED(ctx);
-        PG_TRY(reach_levels(ctx, nbr, deg, R, n, reached.p, queue.p, queue.p + n, fcnt.p));
+        int *fa = queue.p, *fb = queue.p + n;
+        int fcount = 1;
+        while (fcount > 0) {
+            PG_TRY_CUDA(ctx, cudaMemsetAsync(fcnt.p, 0, sizeof(int), ctx->stream));
+            k_bfs_level<<<(fcount + 255) / 256, 256, 0, ctx->stream>>>(nbr, deg, R, n, reached.p,
+                                                                       fa, fcount, fb, fcnt.p);
+            PG_LAUNCHED(ctx);
+            PG_TRY_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned, fcnt.p, sizeof(int),
+                                             cudaMemcpyDeviceToHost, ctx->stream));
+            PG_TRY_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+            memcpy(&fcount, ctx->h_pinned, sizeof(int));
+            std::swap(fa, fb);
+        }
         // the reached node nearest to r that still holds an original edge
         RepState init{~0ull, ~0ull, INT_MAX};
         PG_TRY_CUDA(ctx, cudaMemcpyAsync(st.p, &init, sizeof init, cudaMemcpyHostToDevice,
