@@ -515,7 +515,12 @@ pg_status pg_index_reserve(pg_ctx *ctx, pg_index *index, int64_t capacity);
  * re-prunes N_i(v) | I_i(v) (the reverse-edge step of Algorithm 4); new
  * nodes are appended to the layers in id order.  Needs pg_index_reserve
  * with capacity >= n + m (else PG_ERR_CAPACITY); 1 <= ef, upper_beam <= 256.
- * Synchronous. */
+ * The batch is built in copies of the layers' graph arrays (those of an
+ * earlier version that no search reads any more are reused, else new ones
+ * are allocated) and published when it ends, so a search running meanwhile
+ * on another context (pg_search, pg_search_host, the serving loop) reads
+ * the version it started on.  Insertions into one index must not overlap
+ * each other (the serving loop runs them one at a time).  Synchronous. */
 pg_status pg_index_insert(pg_ctx *ctx, pg_index *index, const float *X, int64_t m, int32_t ef,
                           int32_t upper_beam);
 
