@@ -155,3 +155,23 @@ def test_the_lo_terms_are_needed_for_the_bound():
                 broke += abs(Fraction(s) - ex) > Fraction(screen_bound(float(norms[i]), nb, 128,
                                                                        384))
     assert broke > 0
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_chunk_lower_bound_never_exceeds_a_column(seed):
+    """The kNN tile epilogue dismisses a 32-column chunk for a row when
+    |q|^2 + fmaf(-2, max_j v_j, min_j |x_j|^2) exceeds the row's K-th
+    distance.  Correctly rounded operations are monotone, so that bound is at
+    most every column's |q|^2 + fmaf(-2, v_j, |x_j|^2): checked with exact
+    roundings on random and nearly tied columns."""
+    rng = np.random.default_rng(seed)
+    for _ in range(200):
+        nq = np.float32(rng.uniform(0, 1e7))
+        base = rng.uniform(-1e6, 1e6)
+        v = (base + rng.normal(0, rng.choice([1e-3, 1.0, 1e3]), 32)).astype(np.float32)
+        nb = np.abs(rng.normal(5e6, rng.choice([1e-2, 10.0, 1e5]), 32)).astype(np.float32)
+        fma = [round_f32(Fraction(float(b)) - 2 * Fraction(float(x))) for x, b in zip(v, nb)]
+        cols = [round_f32(Fraction(float(nq)) + f) for f in fma]
+        lb = round_f32(Fraction(float(nq)) +
+                       round_f32(Fraction(float(nb.min())) - 2 * Fraction(float(v.max()))))
+        assert lb <= min(cols)
